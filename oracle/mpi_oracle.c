@@ -1,0 +1,442 @@
+/*
+ * FP64 CPU oracle for the equilibrium (Langevin) MPI operators of
+ * "Fast Trajectory-Independent Model-Based Reconstruction Algorithm for
+ * Multi-Dimensional MPI" (Gapyak, Maerz, Weinmann).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * reference that the CUDA library is checked against.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or constant with the CUDA library.
+ *
+ * Everything is IEEE double.  Loops are written in the order of the
+ * definitions; the only parallelism is OpenMP over independent outputs, so
+ * every output is a sequential sum and the results do not depend on the
+ * thread count.
+ *
+ * Notation (Sec. 2 of the paper):
+ *   c[j][i]     particle concentration on the voxel centres
+ *               x_ij = (x0 + (i + 1/2) dx, y0 + (j + 1/2) dy), row-major, j = row
+ *   r[t][2]     FFP trajectory r(t), v[t][2] its velocity r'(t)
+ *   G[2][2]     selection-field gradient (row-major), H(x,t) = G (x - r(t))
+ *   beta        1 / (mu0 H_sat), so the Langevin argument is beta |H|
+ *   p[k][2]     receive-coil directions, s[k][t] the signal on channel k
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+typedef struct {
+    int nx, ny;
+    double x0, y0, dx, dy;
+} og_grid;
+
+typedef struct {
+    double beta;
+    double G[4];
+    int n_ch;
+    double p[4]; /* p[k*2 + m] */
+} og_model;
+
+/* ------------------------------------------------------------------------- */
+/* Langevin function family (Eq. momentum, with L = coth z - 1/z: the "cosh"
+ * printed in the paper is a typo, the Langevin function is coth z - 1/z).
+ *
+ *   L(z)   = coth z - 1/z
+ *   L'(z)  = 1/z^2 - 1/sinh^2 z
+ *   L''(z) = -2/z^3 + 2 cosh z / sinh^3 z
+ *   a(z)   = L(z)/z                 (transverse eigenvalue of K, Eq. kernel:matrix)
+ *   d(z)   = (L'(z) - a(z)) / z^2   (so that K(y) = a I + d y y^T)
+ *   e(z)   = L''(z) / z
+ *
+ * Near z = 0 the closed forms cancel catastrophically, so for z < 2 the
+ * oracle sums the Taylor series of coth:
+ *   coth z - 1/z = sum_{n>=1} c_n z^(2n-1),  c_n = 2 (-1)^(n+1) zeta(2n) / pi^(2n)
+ * (equivalently c_n = 2^(2n) B_2n / (2n)!).  Differentiating term by term:
+ *   a  = sum_n c_n u^(n-1),                 L' = sum_n (2n-1) c_n u^(n-1)
+ *   d  = sum_{n>=2} (2n-2) c_n u^(n-2),     e  = sum_{n>=2} (2n-1)(2n-2) c_n u^(n-2)
+ * with u = z^2.  The series converges for |z| < pi; at z = 2 the ratio of
+ * successive terms is 4/pi^2 ~ 0.41, so OG_NS terms reach far below 1e-16.
+ */
+#define OG_NS 72
+#define OG_ZSER 2.0
+
+static double og_c[OG_NS + 1];
+static int og_c_ready = 0;
+
+/* zeta(s) for even s >= 4 by direct summation plus the Euler-Maclaurin tail. */
+static double og_zeta(int s)
+{
+    const int K = 1000;
+    double acc = 0.0;
+    for (int k = K; k >= 1; --k) acc += pow((double)k, -(double)s);
+    double Kd = (double)K;
+    /* tail sum_{k>K} k^-s ~ int_K^inf x^-s dx - K^-s/2 + s K^-(s+1)/12 */
+    acc += pow(Kd, 1.0 - s) / (s - 1.0) - 0.5 * pow(Kd, -(double)s)
+         + s * pow(Kd, -(double)s - 1.0) / 12.0;
+    return acc;
+}
+
+static void og_init_series(void)
+{
+    if (og_c_ready) return;
+    og_c[0] = 0.0;
+    og_c[1] = 1.0 / 3.0; /* 2 zeta(2) / pi^2 = 1/3 exactly */
+    for (int n = 2; n <= OG_NS; ++n) {
+        double sgn = (n % 2 == 0) ? -1.0 : 1.0;
+        og_c[n] = 2.0 * sgn * og_zeta(2 * n) / pow(M_PI, 2.0 * n);
+    }
+    og_c_ready = 1;
+}
+
+/* All six functions at one argument z >= 0. */
+static void og_langevin6(double z, double *L, double *Lp, double *Lpp,
+                         double *a, double *d, double *e)
+{
+    if (z < OG_ZSER) {
+        double u = z * z;
+        double sa = 0.0, sl = 0.0, sd = 0.0, se = 0.0;
+        for (int n = OG_NS; n >= 1; --n) {
+            sa = sa * u + og_c[n];
+            sl = sl * u + (2.0 * n - 1.0) * og_c[n];
+        }
+        for (int n = OG_NS; n >= 2; --n) {
+            sd = sd * u + (2.0 * n - 2.0) * og_c[n];
+            se = se * u + (2.0 * n - 1.0) * (2.0 * n - 2.0) * og_c[n];
+        }
+        *a = sa; *Lp = sl; *d = sd; *e = se;
+        *L = z * sa; *Lpp = z * se;
+        return;
+    }
+    /* q = exp(-2z); coth z = (1+q)/(1-q); 1/sinh^2 z = 4q/(1-q)^2. */
+    double em = expm1(-2.0 * z); /* q - 1, in (-1, 0) */
+    double q = exp(-2.0 * z);
+    double coth = -(2.0 + em) / em;
+    double csch2 = 4.0 * q / (em * em);
+    double iz = 1.0 / z;
+    *L = coth - iz;
+    *Lp = iz * iz - csch2;
+    *Lpp = -2.0 * iz * iz * iz + 2.0 * coth * csch2;
+    *a = *L * iz;
+    *d = (*Lp - *a) * iz * iz;
+    *e = *Lpp * iz;
+}
+
+/* Vectorised export, for the tests. */
+void og_langevin(int64_t n, const double *z, double *L, double *Lp, double *Lpp,
+                 double *a, double *d, double *e)
+{
+    og_init_series();
+    for (int64_t k = 0; k < n; ++k)
+        og_langevin6(z[k], &L[k], &Lp[k], &Lpp[k], &a[k], &d[k], &e[k]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* MPI kernel matrix (Eq. kernel:matrix):
+ *   K(y) = L'(|y|) yy^T/|y|^2 + L(|y|)/|y| (I - yy^T/|y|^2) = a I + d y y^T.
+ * K(0) = I/3.  Returned row-major. */
+static void og_K(const double y[2], double K[4])
+{
+    double z = sqrt(y[0] * y[0] + y[1] * y[1]);
+    double L, Lp, Lpp, a, d, e;
+    og_langevin6(z, &L, &Lp, &Lpp, &a, &d, &e);
+    K[0] = a + d * y[0] * y[0];
+    K[1] = d * y[0] * y[1];
+    K[2] = d * y[1] * y[0];
+    K[3] = a + d * y[1] * y[1];
+}
+
+void og_kernel_matrix(int64_t n, const double *y, double *K)
+{
+    og_init_series();
+    for (int64_t k = 0; k < n; ++k) og_K(&y[2 * k], &K[4 * k]);
+}
+
+static inline void og_voxel_centre(const og_grid *g, int i, int j, double x[2])
+{
+    x[0] = g->x0 + (i + 0.5) * g->dx;
+    x[1] = g->y0 + (j + 0.5) * g->dy;
+}
+
+/* The response of one voxel at x to one trajectory sample (r, v):
+ *   J w = beta K(beta G (x - r)) G v,
+ * i.e. the Jacobian of H -> L(beta |H|) H/|H| at H = G(x - r), applied to
+ * G r' (the time derivative of the magnetisation with the sign of
+ * dH/dt = -G r' dropped together with the constant -mu0 m R, as Eq.
+ * core:formula does). */
+static void og_pair(const og_model *m, const double x[2], const double r[2],
+                    const double v[2], double Jw[2])
+{
+    double dxr[2] = {x[0] - r[0], x[1] - r[1]};
+    double H[2] = {m->G[0] * dxr[0] + m->G[1] * dxr[1],
+                   m->G[2] * dxr[0] + m->G[3] * dxr[1]};
+    double y[2] = {m->beta * H[0], m->beta * H[1]};
+    double w[2] = {m->G[0] * v[0] + m->G[1] * v[1],
+                   m->G[2] * v[0] + m->G[3] * v[1]};
+    double K[4];
+    og_K(y, K);
+    Jw[0] = m->beta * (K[0] * w[0] + K[1] * w[1]);
+    Jw[1] = m->beta * (K[2] * w[0] + K[3] * w[1]);
+}
+
+void og_pair_export(const og_model *m, const double *x, const double *r,
+                    const double *v, double *Jw)
+{
+    og_init_series();
+    og_pair(m, x, r, v, Jw);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Forward operator A (Eq. core:formula, discretised on the voxel grid):
+ *   s_k(t) = sum_{j,i} c_ij p_k^T J(x_ij, t) w_t.
+ * s is [n_ch][T].  Voxels are summed row-major in FP64. */
+void og_forward(const og_model *m, const og_grid *g, int64_t T, const double *r,
+                const double *v, const double *c, double *s)
+{
+    og_init_series();
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < T; ++t) {
+        double acc[2] = {0.0, 0.0};
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                double x[2], Jw[2];
+                og_voxel_centre(g, i, j, x);
+                og_pair(m, x, &r[2 * t], &v[2 * t], Jw);
+                double cij = c[(int64_t)j * g->nx + i];
+                for (int k = 0; k < m->n_ch; ++k)
+                    acc[k] += cij * (m->p[2 * k] * Jw[0] + m->p[2 * k + 1] * Jw[1]);
+            }
+        for (int k = 0; k < m->n_ch; ++k) s[(int64_t)k * T + t] = acc[k];
+    }
+}
+
+/* Adjoint A^T at a list of voxels (all voxels when sel == NULL):
+ *   g_ij = sum_t sum_k s_k(t) p_k^T J(x_ij, t) w_t, summed over t in order. */
+void og_adjoint_sel(const og_model *m, const og_grid *g, int64_t T, const double *r,
+                    const double *v, const double *s, int64_t n_sel,
+                    const int64_t *sel, double *out)
+{
+    og_init_series();
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < n_sel; ++q) {
+        int64_t idx = sel ? sel[q] : q;
+        int i = (int)(idx % g->nx), j = (int)(idx / g->nx);
+        double x[2];
+        og_voxel_centre(g, i, j, x);
+        double acc = 0.0;
+        for (int64_t t = 0; t < T; ++t) {
+            double Jw[2];
+            og_pair(m, x, &r[2 * t], &v[2 * t], Jw);
+            for (int k = 0; k < m->n_ch; ++k)
+                acc += s[(int64_t)k * T + t] * (m->p[2 * k] * Jw[0] + m->p[2 * k + 1] * Jw[1]);
+        }
+        out[q] = acc;
+    }
+}
+
+void og_adjoint(const og_model *m, const og_grid *g, int64_t T, const double *r,
+                const double *v, const double *s, double *out)
+{
+    og_adjoint_sel(m, g, T, r, v, s, (int64_t)g->nx * g->ny, NULL, out);
+}
+
+/* d/dbeta of <gs, A(c; beta)>:
+ *   sum_t sum_k gs_k(t) sum_x c_x p_k^T d/dbeta[beta K(beta y0)] w_t,
+ * y0 = G(x - r_t).  Writing y = beta y0, z = |y| and using a + z a' = L',
+ * 3d + z d' = L''/z:
+ *   d/dbeta[beta K(beta y0)] w = L'(z) w + (L''(z)/z) (y.w) y.
+ * Per-sample contributions are summed in sample order. */
+void og_dbeta(const og_model *m, const og_grid *g, int64_t T, const double *r,
+              const double *v, const double *c, const double *gs, double *contrib,
+              double *out)
+{
+    og_init_series();
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < T; ++t) {
+        double acc = 0.0;
+        const double *rt = &r[2 * t], *vt = &v[2 * t];
+        double w[2] = {m->G[0] * vt[0] + m->G[1] * vt[1],
+                       m->G[2] * vt[0] + m->G[3] * vt[1]};
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                double x[2];
+                og_voxel_centre(g, i, j, x);
+                double dxr[2] = {x[0] - rt[0], x[1] - rt[1]};
+                double y[2] = {m->beta * (m->G[0] * dxr[0] + m->G[1] * dxr[1]),
+                               m->beta * (m->G[2] * dxr[0] + m->G[3] * dxr[1])};
+                double z = sqrt(y[0] * y[0] + y[1] * y[1]);
+                double L, Lp, Lpp, a, d, e;
+                og_langevin6(z, &L, &Lp, &Lpp, &a, &d, &e);
+                double yw = y[0] * w[0] + y[1] * w[1];
+                double D[2] = {Lp * w[0] + e * yw * y[0], Lp * w[1] + e * yw * y[1]};
+                double cij = c[(int64_t)j * g->nx + i];
+                for (int k = 0; k < m->n_ch; ++k)
+                    acc += gs[(int64_t)k * T + t] * cij * (m->p[2 * k] * D[0] + m->p[2 * k + 1] * D[1]);
+            }
+        contrib[t] = acc;
+    }
+    double tot = 0.0;
+    for (int64_t t = 0; t < T; ++t) tot += contrib[t];
+    *out = tot;
+}
+
+/* sum over all (voxel, sample, channel) of (p_k^T J w)^2: the squared
+ * Frobenius norm of the dense matrix of A. */
+double og_frob2(const og_model *m, const og_grid *g, int64_t T, const double *r,
+                const double *v, double *contrib)
+{
+    og_init_series();
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < T; ++t) {
+        double acc = 0.0;
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                double x[2], Jw[2];
+                og_voxel_centre(g, i, j, x);
+                og_pair(m, x, &r[2 * t], &v[2 * t], Jw);
+                for (int k = 0; k < m->n_ch; ++k) {
+                    double e = m->p[2 * k] * Jw[0] + m->p[2 * k + 1] * Jw[1];
+                    acc += e * e;
+                }
+            }
+        contrib[t] = acc;
+    }
+    double tot = 0.0;
+    for (int64_t t = 0; t < T; ++t) tot += contrib[t];
+    return tot;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cosine interpolation (Eq. first:step; the scheme of the Core Stage).
+ * Nodes are the voxel centres.  Along one axis, a position p falls between
+ * nodes k and k+1 at fraction f in [0,1]; node k+1 gets weight
+ * (1 - cos(pi f))/2 and node k the rest.  Positions outside the node hull are
+ * clamped to the nearest edge node.  The 2-D scheme is the tensor product. */
+static void og_axis(double p, double p0, double h, int n, int *k0, double *w0, double *w1)
+{
+    if (n == 1) { *k0 = 0; *w0 = 1.0; *w1 = 0.0; return; }
+    double fi = (p - p0) / h - 0.5;       /* continuous node index */
+    if (fi <= 0.0) { *k0 = 0; *w0 = 1.0; *w1 = 0.0; return; }
+    if (fi >= n - 1) { *k0 = n - 2; *w0 = 0.0; *w1 = 1.0; return; }
+    int k = (int)floor(fi);
+    if (k > n - 2) k = n - 2;
+    double f = fi - k;
+    *k0 = k;
+    *w1 = 0.5 * (1.0 - cos(M_PI * f));
+    *w0 = 1.0 - *w1;
+}
+
+/* s_k(t) = sum_m I[Ahat_km](r_t) v_m(t), k = 0, 1.  Ahat is [4][ny][nx] with
+ * component index 2k+m.  s is [2][T]. */
+void og_interp(const og_grid *g, int64_t T, const double *r, const double *v,
+               const double *Ahat, double *s)
+{
+    int64_t N = (int64_t)g->nx * g->ny;
+    for (int64_t t = 0; t < T; ++t) {
+        int i0, j0;
+        double wx0, wx1, wy0, wy1;
+        og_axis(r[2 * t], g->x0, g->dx, g->nx, &i0, &wx0, &wx1);
+        og_axis(r[2 * t + 1], g->y0, g->dy, g->ny, &j0, &wy0, &wy1);
+        int i1 = (g->nx > 1) ? i0 + 1 : i0, j1 = (g->ny > 1) ? j0 + 1 : j0;
+        for (int k = 0; k < 2; ++k) {
+            double acc = 0.0;
+            for (int mm = 0; mm < 2; ++mm) {
+                const double *F = &Ahat[(2 * k + mm) * N];
+                double val = wy0 * (wx0 * F[(int64_t)j0 * g->nx + i0] + wx1 * F[(int64_t)j0 * g->nx + i1])
+                           + wy1 * (wx0 * F[(int64_t)j1 * g->nx + i0] + wx1 * F[(int64_t)j1 * g->nx + i1]);
+                acc += val * v[2 * t + mm];
+            }
+            s[(int64_t)k * T + t] = acc;
+        }
+    }
+}
+
+/* Exact transpose of og_interp: Ahat_km += weight * v_m(t) * s_k(t), in
+ * sample order. */
+void og_interp_T(const og_grid *g, int64_t T, const double *r, const double *v,
+                 const double *s, double *Ahat)
+{
+    int64_t N = (int64_t)g->nx * g->ny;
+    memset(Ahat, 0, sizeof(double) * 4 * N);
+    for (int64_t t = 0; t < T; ++t) {
+        int i0, j0;
+        double wx0, wx1, wy0, wy1;
+        og_axis(r[2 * t], g->x0, g->dx, g->nx, &i0, &wx0, &wx1);
+        og_axis(r[2 * t + 1], g->y0, g->dy, g->ny, &j0, &wy0, &wy1);
+        int i1 = (g->nx > 1) ? i0 + 1 : i0, j1 = (g->ny > 1) ? j0 + 1 : j0;
+        for (int k = 0; k < 2; ++k)
+            for (int mm = 0; mm < 2; ++mm) {
+                double coef = s[(int64_t)k * T + t] * v[2 * t + mm];
+                double *F = &Ahat[(2 * k + mm) * N];
+                F[(int64_t)j0 * g->nx + i0] += wy0 * wx0 * coef;
+                F[(int64_t)j0 * g->nx + i1] += wy0 * wx1 * coef;
+                F[(int64_t)j1 * g->nx + i0] += wy1 * wx0 * coef;
+                F[(int64_t)j1 * g->nx + i1] += wy1 * wx1 * coef;
+            }
+    }
+}
+
+/* 5-point discrete Laplacian with replicated (Neumann) boundary on one
+ * [ny][nx] field: the regulariser of the Core Stage (Eq. first:step). */
+void og_laplacian(const og_grid *g, const double *f, double *out)
+{
+    int nx = g->nx, ny = g->ny;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int im = i > 0 ? i - 1 : 0, ip = i < nx - 1 ? i + 1 : nx - 1;
+            int jm = j > 0 ? j - 1 : 0, jp = j < ny - 1 ? j + 1 : ny - 1;
+            double c0 = f[(int64_t)j * nx + i];
+            out[(int64_t)j * nx + i] = f[(int64_t)j * nx + im] + f[(int64_t)j * nx + ip]
+                                     + f[(int64_t)jm * nx + i] + f[(int64_t)jp * nx + i] - 4.0 * c0;
+        }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sampled trace kernel (Eq. convolution:trace / kernel:trace), read with the
+ * resolution scaling and the gradient that multiply v in the forward model:
+ *   kappa_G(y) = beta tr(K(beta G y) G),
+ * sampled on all voxel offsets y = (ii dx, jj dy), |ii| < nx, |jj| < ny.
+ * kern is [(2ny-1)][(2nx-1)], offset (0,0) at (ny-1, nx-1). */
+void og_conv_kernel(const og_model *m, const og_grid *g, double *kern)
+{
+    og_init_series();
+    int KX = 2 * g->nx - 1, KY = 2 * g->ny - 1;
+    for (int jj = 0; jj < KY; ++jj)
+        for (int ii = 0; ii < KX; ++ii) {
+            double off[2] = {(ii - (g->nx - 1)) * g->dx, (jj - (g->ny - 1)) * g->dy};
+            double y[2] = {m->beta * (m->G[0] * off[0] + m->G[1] * off[1]),
+                           m->beta * (m->G[2] * off[0] + m->G[3] * off[1])};
+            double K[4];
+            og_K(y, K);
+            /* tr(K G) = sum_ab K_ab G_ba */
+            double tr = K[0] * m->G[0] + K[1] * m->G[2] + K[2] * m->G[1] + K[3] * m->G[3];
+            kern[(int64_t)jj * KX + ii] = m->beta * tr;
+        }
+}
+
+/* Linear (zero-padded) convolution with the sampled kernel (the matrix C_h of
+ * Eq. dec:sub:tik):  out_ij = sum_{j'i'} kappa(x_ij - x_i'j') in_i'j'. */
+void og_conv(const og_grid *g, const double *kern, const double *in, double *out)
+{
+    int nx = g->nx, ny = g->ny, KX = 2 * nx - 1;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double acc = 0.0;
+            for (int jq = 0; jq < ny; ++jq)
+                for (int iq = 0; iq < nx; ++iq)
+                    acc += kern[(int64_t)(j - jq + ny - 1) * KX + (i - iq + nx - 1)]
+                         * in[(int64_t)jq * nx + iq];
+            out[(int64_t)j * nx + i] = acc;
+        }
+}
+
+int og_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

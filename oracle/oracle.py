@@ -1,0 +1,412 @@
+"""FP64 CPU oracle for the MPI reconstruction path (test infrastructure only).
+
+This module and ``mpi_oracle.c`` are the plain, slow, obviously correct
+reference the CUDA library is checked against.  Only the test suite, the smoke
+check and the CPU-baseline leg of the benchmark may import it; the library
+never does, and the two share no code.  Inputs are numpy arrays; a ``model`` is
+a mapping with ``beta`` (1/T), ``G`` (2x2, T per length unit) and ``p``
+(n_ch x 2 receive directions); a ``grid`` is a mapping with ``nx, ny, x0, y0,
+dx, dy`` (voxel centre (x0 + (i+1/2)dx, y0 + (j+1/2)dy)).
+
+The pair sums (A, A^T, d/dbeta, the convolution) live in C for speed; the
+iterations (CG, the ZeroShot-PnP loop of Algorithm 1, the Core Stage solve)
+are written here step by step in numpy FP64.
+
+Parity status per function (what pins each one lives in tests/test_oracle_*):
+  langevin, kernel_matrix, pair, forward, adjoint, dbeta, frob2,
+  interp, interp_T, laplacian, conv_kernel, conv, conv_fft, cg,
+  percentile_clamp, variance, gaussian5, core_stage: pinned.
+  pnp: pinned step by step (identity-operator closed form, Algorithm 1
+  bookkeeping); the full reconstruction has no printed example in the paper,
+  so its end-to-end values are "parity unpinned" at paper level.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpi_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libmpi_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile mpi_oracle.c with gcc (-O2, OpenMP, IEEE semantics)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC",
+           "-fno-fast-math", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("G", ctypes.c_double * 4),
+                ("n_ch", ctypes.c_int), ("p", ctypes.c_double * 4)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.c_int64
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            lib.og_langevin.argtypes = [_I64, _D, _D, _D, _D, _D, _D, _D]
+            lib.og_kernel_matrix.argtypes = [_I64, _D, _D]
+            lib.og_pair_export.argtypes = [P(_Model), _D, _D, _D, _D]
+            lib.og_forward.argtypes = [P(_Model), P(_Grid), _I64, _D, _D, _D, _D]
+            lib.og_adjoint_sel.argtypes = [P(_Model), P(_Grid), _I64, _D, _D, _D, _I64,
+                                           P(_I64), _D]
+            lib.og_dbeta.argtypes = [P(_Model), P(_Grid), _I64, _D, _D, _D, _D, _D, _D]
+            lib.og_frob2.argtypes = [P(_Model), P(_Grid), _I64, _D, _D, _D]
+            lib.og_frob2.restype = ctypes.c_double
+            lib.og_interp.argtypes = [P(_Grid), _I64, _D, _D, _D, _D]
+            lib.og_interp_T.argtypes = [P(_Grid), _I64, _D, _D, _D, _D]
+            lib.og_laplacian.argtypes = [P(_Grid), _D, _D]
+            lib.og_conv_kernel.argtypes = [P(_Model), P(_Grid), _D]
+            lib.og_conv.argtypes = [P(_Grid), _D, _D, _D]
+            lib.og_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _grid(g) -> _Grid:
+    return _Grid(int(g["nx"]), int(g["ny"]), float(g["x0"]), float(g["y0"]),
+                 float(g["dx"]), float(g["dy"]))
+
+
+def _model(m) -> _Model:
+    G = np.asarray(m["G"], dtype=np.float64).reshape(4)
+    p = np.asarray(m["p"], dtype=np.float64).reshape(-1, 2)
+    n_ch = p.shape[0]
+    if n_ch not in (1, 2):
+        raise ValueError("n_ch must be 1 or 2")
+    pp = np.zeros(4)
+    pp[: 2 * n_ch] = p.reshape(-1)
+    return _Model(float(m["beta"]), (ctypes.c_double * 4)(*G), n_ch,
+                  (ctypes.c_double * 4)(*pp))
+
+
+def num_threads() -> int:
+    return int(_load().og_num_threads())
+
+
+# ---------------------------------------------------------------------------
+# Langevin family and the MPI kernel (Eq. momentum, Eq. kernel:matrix)
+
+def langevin(z) -> dict:
+    """L, L', L'', a = L/z, d = (L' - a)/z^2, e = L''/z at z >= 0."""
+    z = _f64(np.atleast_1d(z))
+    out = {k: np.empty_like(z) for k in ("L", "Lp", "Lpp", "a", "d", "e")}
+    _load().og_langevin(z.size, _ptr(z), _ptr(out["L"]), _ptr(out["Lp"]),
+                        _ptr(out["Lpp"]), _ptr(out["a"]), _ptr(out["d"]), _ptr(out["e"]))
+    return out
+
+
+def kernel_matrix(y) -> np.ndarray:
+    """K(y) of Eq. kernel:matrix for y of shape [..., 2] -> [..., 2, 2]."""
+    y = _f64(y)
+    flat = y.reshape(-1, 2)
+    K = np.empty((flat.shape[0], 4))
+    _load().og_kernel_matrix(flat.shape[0], _ptr(flat), _ptr(K))
+    return K.reshape(y.shape[:-1] + (2, 2))
+
+
+def pair(model, x, r, v) -> np.ndarray:
+    """J w = beta K(beta G(x - r)) G v for one voxel/sample pair."""
+    x, r, v = _f64(x), _f64(r), _f64(v)
+    out = np.empty(2)
+    _load().og_pair_export(ctypes.byref(_model(model)), _ptr(x), _ptr(r), _ptr(v), _ptr(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The operators
+
+def forward(model, grid, r, v, c) -> np.ndarray:
+    """A c: s[k][t] = sum_x c_x p_k^T J(x, t) w_t (Eq. core:formula)."""
+    r, v, c = _f64(r), _f64(v), _f64(c)
+    T = r.shape[0]
+    n_ch = np.asarray(model["p"]).reshape(-1, 2).shape[0]
+    s = np.empty((n_ch, T))
+    _load().og_forward(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)), T,
+                       _ptr(r), _ptr(v), _ptr(c), _ptr(s))
+    return s
+
+
+def adjoint(model, grid, r, v, s, sel=None) -> np.ndarray:
+    """A^T s on all voxels ([ny, nx]) or on the flat voxel indices ``sel``."""
+    r, v, s = _f64(r), _f64(v), _f64(s)
+    T = r.shape[0]
+    lib = _load()
+    if sel is None:
+        out = np.empty((int(grid["ny"]), int(grid["nx"])))
+        lib.og_adjoint_sel(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)), T,
+                           _ptr(r), _ptr(v), _ptr(s), out.size, None, _ptr(out))
+        return out
+    sel = np.ascontiguousarray(sel, dtype=np.int64)
+    out = np.empty(sel.size)
+    lib.og_adjoint_sel(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)), T,
+                       _ptr(r), _ptr(v), _ptr(s), sel.size,
+                       sel.ctypes.data_as(ctypes.POINTER(_I64)), _ptr(out))
+    return out
+
+
+def dbeta(model, grid, r, v, c, gs) -> float:
+    """d/dbeta <gs, A(c; beta)> (the particle-parameter gradient)."""
+    r, v, c, gs = _f64(r), _f64(v), _f64(c), _f64(gs)
+    T = r.shape[0]
+    contrib = np.empty(T)
+    out = np.empty(1)
+    _load().og_dbeta(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)), T, _ptr(r),
+                     _ptr(v), _ptr(c), _ptr(gs), _ptr(contrib), _ptr(out))
+    return float(out[0])
+
+
+def frob2(model, grid, r, v) -> float:
+    """||A||_F^2 (sum of squares of all entries of the dense matrix of A)."""
+    r, v = _f64(r), _f64(v)
+    contrib = np.empty(r.shape[0])
+    return float(_load().og_frob2(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)),
+                                  r.shape[0], _ptr(r), _ptr(v), _ptr(contrib)))
+
+
+def nu0_from_frob2(frob2_value: float, n_vox: int) -> float:
+    """nu0 = 1e-3 * ||O||_F^2 / N: the mean diagonal of O^T O times 1e-3.
+
+    The paper's nu0 values (1e-5 / 1e-6 / 4e-2, Sec. 2.2 and Sec. 3.6) are in
+    its own data units; synthetic data take this scale-free reading."""
+    return 1e-3 * frob2_value / n_vox
+
+
+def interp(grid, r, v, Ahat) -> np.ndarray:
+    """M[Ahat]_t = I[Ahat](r_t) v_t, cosine interpolation (Eq. first:step)."""
+    r, v, Ahat = _f64(r), _f64(v), _f64(Ahat)
+    s = np.empty((2, r.shape[0]))
+    _load().og_interp(ctypes.byref(_grid(grid)), r.shape[0], _ptr(r), _ptr(v),
+                      _ptr(Ahat), _ptr(s))
+    return s
+
+
+def interp_T(grid, r, v, s) -> np.ndarray:
+    r, v, s = _f64(r), _f64(v), _f64(s)
+    out = np.empty((4, int(grid["ny"]), int(grid["nx"])))
+    _load().og_interp_T(ctypes.byref(_grid(grid)), r.shape[0], _ptr(r), _ptr(v),
+                        _ptr(s), _ptr(out))
+    return out
+
+
+def laplacian(grid, f) -> np.ndarray:
+    """5-point Laplacian with replicated boundary, one [ny, nx] field."""
+    f = _f64(f)
+    out = np.empty_like(f)
+    _load().og_laplacian(ctypes.byref(_grid(grid)), _ptr(f), _ptr(out))
+    return out
+
+
+def conv_kernel(model, grid) -> np.ndarray:
+    """kappa_G(y) = beta tr(K(beta G y) G) on all voxel offsets."""
+    out = np.empty((2 * int(grid["ny"]) - 1, 2 * int(grid["nx"]) - 1))
+    _load().og_conv_kernel(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)), _ptr(out))
+    return out
+
+
+def conv(grid, kern, x) -> np.ndarray:
+    """Direct linear convolution C x with the sampled kernel."""
+    kern, x = _f64(kern), _f64(x)
+    out = np.empty_like(x)
+    _load().og_conv(ctypes.byref(_grid(grid)), _ptr(kern), _ptr(x), _ptr(out))
+    return out
+
+
+def conv_fft(kern, x) -> np.ndarray:
+    """Second route for C x: zero-padded FFT convolution (the Toeplitz/FFT
+    realisation the paper uses for C_h), cropped to the 'valid' centre."""
+    ny, nx = x.shape
+    KY, KX = kern.shape
+    sy, sx = KY + ny - 1, KX + nx - 1
+    F = np.fft.rfft2(_f64(kern), (sy, sx)) * np.fft.rfft2(_f64(x), (sy, sx))
+    full = np.fft.irfft2(F, (sy, sx))
+    return full[ny - 1: 2 * ny - 1, nx - 1: 2 * nx - 1]
+
+
+# ---------------------------------------------------------------------------
+# Iterations
+
+def cg(apply, b, x0, n_iter, rel_tol=None):
+    """Textbook conjugate gradient (Hestenes-Stiefel) on an SPD operator.
+
+    Runs n_iter steps after the initial residual; with rel_tol it stops as
+    soon as ||r|| <= rel_tol ||b|| (checked before each step).  It also stops
+    if r^T r == 0 or p^T A p == 0 (the residual has vanished to round-off).  Returns (x, history of ||r||, operator applications)."""
+    x = _f64(x0).copy()
+    r = b - apply(x)
+    n_app = 1
+    p = r.copy()
+    rr = float(np.dot(r.ravel(), r.ravel()))
+    bn = float(np.sqrt(np.dot(b.ravel(), b.ravel())))
+    hist = [np.sqrt(rr)]
+    for _ in range(n_iter):
+        if rr == 0.0:
+            break
+        if rel_tol is not None and np.sqrt(rr) <= rel_tol * bn:
+            break
+        q = apply(p)
+        n_app += 1
+        pq = float(np.dot(p.ravel(), q.ravel()))
+        if pq == 0.0:  # only when r vanished to round-off: nothing left to do
+            break
+        alpha = rr / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = float(np.dot(r.ravel(), r.ravel()))
+        beta = rr_new / rr
+        p = r + beta * p
+        rr = rr_new
+        hist.append(np.sqrt(rr))
+    return x, hist, n_app
+
+
+def percentile_value(x, pct) -> float:
+    """Linear-interpolated percentile of the values of x (numpy's default
+    rule): position h = (N-1) pct/100 in the sorted values."""
+    srt = np.sort(_f64(x).ravel())
+    n = srt.size
+    h = (n - 1) * pct / 100.0
+    lo = int(np.floor(h))
+    hi = min(lo + 1, n - 1)
+    frac = h - lo
+    return float(srt[lo] + frac * (srt[hi] - srt[lo]))
+
+
+def percentile_clamp(x, pct):
+    """Percentile trimming (Sec. 3.3): values below the pct-th percentile are
+    raised to it."""
+    P = percentile_value(x, pct)
+    return np.maximum(_f64(x), P)
+
+
+def variance(x) -> float:
+    """Population variance, two passes in FP64 (noise estimate, Sec. 2.2)."""
+    x = _f64(x).ravel()
+    mean = float(np.sum(x)) / x.size
+    dev = x - mean
+    return float(np.dot(dev, dev) / x.size)
+
+
+def _reflect(i: int, n: int) -> int:
+    """'reflect' boundary (d c b a | a b c d), periodic with period 2n."""
+    i %= 2 * n
+    return 2 * n - 1 - i if i >= n else i
+
+
+def gaussian5(img) -> np.ndarray:
+    """Built-in denoiser: separable 5-tap Gaussian, sigma = 1 px, weights
+    exp(-m^2/2)/sum for m = -2..2, reflect boundary; rows first, then
+    columns."""
+    img = _f64(img)
+    ny, nx = img.shape
+    w = np.exp(-0.5 * np.arange(-2, 3, dtype=np.float64) ** 2)
+    w /= w.sum()
+    tmp = np.zeros_like(img)
+    for i in range(nx):
+        for m in range(-2, 3):
+            tmp[:, i] += w[m + 2] * img[:, _reflect(i + m, nx)]
+    out = np.zeros_like(img)
+    for j in range(ny):
+        for m in range(-2, 3):
+            out[j, :] += w[m + 2] * tmp[_reflect(j + m, ny), :]
+    return out
+
+
+def pnp(op, opT, data, shape, n_it, n_cg, nu0, clip_pct=5.0, denoise=None,
+        record=None):
+    """ZeroShot-PnP deconvolution, Algorithm 1, with operator O (op / opT).
+
+    rho2 <- 0; for k = 0 .. n_it-1:
+      rho1 <- CG(O^T O + nu_k I, O^T data + nu_k rho2, x0 = rho2), n_cg steps
+      rho1 <- max(rho1, P_clip(rho1))         (percentile trimming, Sec. 3.3)
+      sigma <- sqrt(Var(rho1))                (noise estimate)
+      lambda <- nu0 sigma^2 if k == 0
+      rho2 <- Denoise(rho1, sigma)
+      nu <- lambda / sigma^2 (unchanged if sigma == 0)
+    return rho2.
+    """
+    if denoise is None:
+        denoise = lambda img, sigma: gaussian5(img)
+    b0 = _f64(opT(data)).reshape(shape)
+    rho2 = np.zeros(shape)
+    nu = float(nu0)
+    lam = None
+    for k in range(n_it):
+        nu_k = nu
+        rhs = b0 + nu_k * rho2
+        apply = lambda x, nu_k=nu_k: _f64(opT(op(x))).reshape(shape) + nu_k * x
+        rho1, hist, _ = cg(apply, rhs, rho2, n_cg)
+        if clip_pct is not None and clip_pct >= 0:
+            rho1 = percentile_clamp(rho1, clip_pct)
+        sigma = float(np.sqrt(variance(rho1)))
+        if k == 0:
+            lam = nu0 * sigma * sigma
+        rho2 = _f64(denoise(rho1, sigma)).reshape(shape)
+        if sigma > 0.0:
+            nu = lam / (sigma * sigma)
+        if record is not None:
+            record.append({"sigma": sigma, "nu": nu, "cg_resid": float(hist[-1]),
+                           "nu_used": nu_k})
+    return rho2
+
+
+def core_stage(grid, r, v, s, gamma, max_iter, rel_tol=None):
+    """Core Stage (Eq. first:step): CG on the Euler-Lagrange equations
+        ((1/L) M^T M + gamma Lap^T Lap) Ahat = (1/L) M^T s,   L = T,
+    with M the cosine-interpolation measurement operator and Lap the
+    replicated-boundary 5-point Laplacian on each of the 4 components (it is
+    symmetric, so Lap^T Lap = Lap Lap).  Starts from 0.  Returns (Ahat
+    [4, ny, nx], trace u = Ahat_00 + Ahat_11, residual history)."""
+    T = r.shape[0]
+    ny, nx = int(grid["ny"]), int(grid["nx"])
+
+    def lap4(x):
+        return np.stack([laplacian(grid, x[m]) for m in range(4)])
+
+    def apply(x):
+        return interp_T(grid, r, v, interp(grid, r, v, x)) / T + gamma * lap4(lap4(x))
+
+    b = interp_T(grid, r, v, s) / T
+    x, hist, _ = cg(apply, b, np.zeros((4, ny, nx)), max_iter, rel_tol=rel_tol)
+    return x, x[0] + x[3], hist
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))
