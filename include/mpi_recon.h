@@ -1,0 +1,206 @@
+/*
+ * mpi_recon.h -- C ABI of the GB300 (sm_103a) library for equilibrium-model
+ * (Langevin) magnetic particle imaging reconstruction, after
+ * "Fast Trajectory-Independent Model-Based Reconstruction Algorithm for
+ * Multi-Dimensional Magnetic Particle Imaging" (Gapyak, Maerz, Weinmann).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Every array argument is DEVICE memory owned by the caller, contiguous,
+ *    row-major, in the dtype named by the call (MPI_F32: float,
+ *    MPI_F64: double), unless the comment says "host".
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Argument errors are detected on the host and returned before
+ *    anything is enqueued.  Device-side errors surface as MPI_ERR_CUDA from
+ *    this or a later call.  On error the outputs are unspecified.
+ *  - The library allocates only scratch, stream-ordered on `stream`
+ *    (cudaMallocAsync / cudaFreeAsync), and releases it before the call
+ *    returns (plans release theirs on destroy).
+ *  - No exception crosses the ABI.  mpi_last_error_message() gives a
+ *    human-readable reason for the last failure on the calling host thread.
+ *
+ * Model (Sec. 2 of the paper)
+ * ---------------------------
+ *  Voxel (i, j) has centre x_ij = (x0 + (i+1/2) dx, y0 + (j+1/2) dy) and
+ *  concentration c[j][i].  The field-free point moves along r(t), t = 0..T-1
+ *  (r[t][2], velocity v[t][2] = dr/dt per sample).  The applied field is
+ *  H(x,t) = G (x - r(t)) (Sec. 2, FFP configuration).  With
+ *  beta = 1/(mu0 H_sat) (Eq. hsat) the transfer-function-corrected signal on
+ *  receive channel k with coil direction p_k is (Eq. core:formula)
+ *      s_k(t) = sum_ij c_ij p_k^T beta K(beta G (x_ij - r_t)) G v_t,
+ *  where K is the MPI kernel matrix of Eq. kernel:matrix,
+ *      K(y) = L'(|y|) yy^T/|y|^2 + L(|y|)/|y| (I - yy^T/|y|^2),
+ *  L(z) = coth z - 1/z the Langevin function (Eq. momentum).  The constant
+ *  -mu0 m R and the minus sign of dH/dt = -G r' are dropped, as the paper's
+ *  proportionality does.  Units are the caller's: G in T per length unit,
+ *  positions in that length unit, beta in 1/T.
+ */
+#ifndef MPI_RECON_H
+#define MPI_RECON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MPI_OK = 0,
+    MPI_ERR_INVALID = -1,     /* bad argument (checked before any launch) */
+    MPI_ERR_CUDA = -2,        /* a CUDA call failed */
+    MPI_ERR_NOMEM = -3,       /* scratch allocation failed */
+    MPI_ERR_CALLBACK = -4,    /* the denoiser callback returned nonzero */
+    MPI_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    MPI_ERR_UNSUPPORTED = -6  /* valid but not supported (e.g. too many frames) */
+} mpi_status;
+
+typedef enum { MPI_F32 = 0, MPI_F64 = 1 } mpi_dtype;
+
+/* Operator of the PnP data-fidelity step: the forward operator A (data are
+ * samples s[n_ch][T]) or the trace-kernel convolution C_h (data are the trace
+ * image u[ny][nx], Eq. dec:sub:tik). */
+typedef enum { MPI_OP_FORWARD = 0, MPI_OP_CONV = 1 } mpi_op;
+
+/* Voxel grid: nx columns, ny rows, centres (x0+(i+1/2)dx, y0+(j+1/2)dy). */
+typedef struct {
+    int nx, ny;
+    double x0, y0, dx, dy;
+} mpi_grid_desc;
+
+/* Physics: beta = 1/(mu0 H_sat) [1/T]; G row-major 2x2 [T per length unit];
+ * n_ch receive channels (1 or 2) with directions p[k*2 + m]. */
+typedef struct {
+    double beta;
+    double G[4];
+    int n_ch;
+    double p[4];
+} mpi_model;
+
+/* Trajectory: T samples, r[T][2] and v[T][2] (device, dtype of the call). */
+typedef struct {
+    int64_t T;
+    const void *r;
+    const void *v;
+} mpi_traj;
+
+/* ---- Operators ---------------------------------------------------------- */
+
+/* Forward operator A (Eq. core:formula):  s[k][t] = sum_ij c[j][i] p_k^T
+ * beta K(beta G(x_ij - r_t)) G v_t.  c is [ny][nx], s is [n_ch][T].  The sum
+ * over voxels is a direct (exact, untruncated) sum, reduced deterministically:
+ * the same inputs give bit-identical outputs.  T == 0 is a no-op; a grid with
+ * no voxels writes zeros. */
+int mpi_forward(const mpi_model *model, const mpi_grid_desc *grid,
+                const mpi_traj *traj, mpi_dtype dtype, const void *c, void *s,
+                void *stream);
+
+/* Adjoint A^T:  c_out[j][i] = sum_t sum_k s[k][t] p_k^T beta K(beta G(x_ij -
+ * r_t)) G v_t.  Deterministic like mpi_forward.  T == 0 writes zeros. */
+int mpi_adjoint(const mpi_model *model, const mpi_grid_desc *grid,
+                const mpi_traj *traj, mpi_dtype dtype, const void *s, void *c_out,
+                void *stream);
+
+/* Gradient of <g, A(c; beta)> with respect to beta, written as one FP64 value
+ * to the DEVICE pointer dbeta_dev.  With y = beta G(x - r), z = |y|:
+ *   d/dbeta [beta K(beta G(x-r))] G v = L'(z) G v + (L''(z)/z) (y . G v) y.
+ * g is [n_ch][T] (dtype of the call); c is [ny][nx]. */
+int mpi_dbeta(const mpi_model *model, const mpi_grid_desc *grid,
+              const mpi_traj *traj, mpi_dtype dtype, const void *c, const void *g,
+              double *dbeta_dev, void *stream);
+
+/* Convolution with the sampled trace kernel (Eq. convolution:trace,
+ * Eq. kernel:trace, the matrix C_h of Eq. dec:sub:tik), read with the
+ * resolution scaling and gradient of the forward model:
+ *   out[j][i] = sum_{j'i'} kappa_G(x_ij - x_i'j') in[j'][i'],
+ *   kappa_G(y) = beta tr(K(beta G y) G)
+ * as a linear (zero-padded) convolution over all voxel offsets.  C is
+ * symmetric.  in/out are [ny][nx] and must not overlap. */
+int mpi_conv(const mpi_model *model, const mpi_grid_desc *grid, mpi_dtype dtype,
+             const void *in, void *out, void *stream);
+
+/* Cosine interpolation of the Core Stage (Eq. first:step):
+ *   s[k][t] = sum_m I[Ahat_km](r_t) v_m(t),  k = 0, 1,
+ * Ahat is [4][ny][nx] (component 2k+m), s is [2][T].  Along each axis a
+ * position between nodes k and k+1 at fraction f gives node k+1 the weight
+ * (1 - cos(pi f))/2; nodes are the voxel centres and positions outside the
+ * node hull are clamped to the edge.  mpi_interp_adjoint is the exact
+ * transpose (deterministic, no float atomics). */
+int mpi_interp(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
+               const void *Ahat, void *s, void *stream);
+int mpi_interp_adjoint(const mpi_grid_desc *grid, const mpi_traj *traj,
+                       mpi_dtype dtype, const void *s, void *Ahat, void *stream);
+
+/* ---- Core Stage (Eq. first:step) ---------------------------------------- */
+
+typedef struct {
+    double gamma;    /* weight of the Laplacian regulariser (paper: 1e-7) */
+    int max_iter;    /* CG iteration limit (paper: 10000) */
+    double rel_tol;  /* stop when ||r|| <= rel_tol ||b|| (paper: 1e-3); <= 0: run max_iter */
+} mpi_grid_opts;
+
+/* Solves ((1/T) M^T M + gamma Lap^T Lap) Ahat = (1/T) M^T s by CG from
+ * Ahat = 0, with M the cosine-interpolation measurement operator above and Lap
+ * the 5-point Laplacian with replicated boundary on each of the 4 components.
+ * s is [2][T]; outputs Ahat [4][ny][nx] and trace [ny][nx] = Ahat_00 + Ahat_11.
+ * If n_iter_out (HOST) is not NULL the call synchronises the stream and stores
+ * the number of CG steps taken. */
+int mpi_grid(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
+             const void *s, const mpi_grid_opts *opts, void *Ahat, void *trace,
+             int *n_iter_out, void *stream);
+
+/* ---- ZeroShot-PnP (Algorithm 1) ------------------------------------------ */
+
+/* Denoiser callback: read in[ny][nx], write out[ny][nx] (device, dtype as
+ * given).  sigma_dev is a DEVICE pointer to the FP64 noise level estimated for
+ * this iteration.  It must only enqueue work on `stream` (no host
+ * synchronisation), and return 0 on success; any other value aborts the
+ * solve with MPI_ERR_CALLBACK. */
+typedef int (*mpi_denoise_fn)(const void *in, void *out, int nx, int ny,
+                              mpi_dtype dtype, const double *sigma_dev,
+                              void *stream, void *user);
+
+/* Built-in denoiser: separable 5-tap Gaussian (sigma = 1 px, weights
+ * exp(-m^2/2)/sum, m = -2..2) with reflect boundary (d c b a | a b c d).  It
+ * ignores sigma_dev.  in and out must not overlap. */
+int mpi_denoise_gaussian5(const void *in, void *out, int nx, int ny, mpi_dtype dtype,
+                          const double *sigma_dev, void *stream, void *user);
+
+typedef struct {
+    mpi_op op;        /* MPI_OP_FORWARD (data s[n_ch][T]) or MPI_OP_CONV (data u[ny][nx]) */
+    int n_iter;       /* outer iterations (Algorithm 1 runs exactly n_iter) */
+    int n_cg;         /* CG steps per data-fidelity solve (after the initial residual) */
+    double nu0;       /* initial Tikhonov weight nu_0 */
+    double clip_pct;  /* percentile trimming below this percentile (paper: 5); < 0 disables */
+} mpi_pnp_opts;
+
+typedef struct {
+    double sigma;     /* noise estimate sqrt(Var(rho1)) of this iteration */
+    double nu;        /* nu_{k+1} = lambda / sigma^2 */
+    double cg_resid;  /* ||r|| after the last CG step */
+} mpi_pnp_iter_info;
+
+/* Algorithm 1: rho2 <- 0; for k < n_iter: rho1 <- CG(O^T O + nu_k I,
+ * O^T data + nu_k rho2, x0 = rho2); rho1 <- max(rho1, P_clip(rho1));
+ * sigma <- sqrt(Var rho1); lambda <- nu0 sigma^2 (k = 0); rho2 <- denoise(rho1,
+ * sigma); nu <- lambda/sigma^2 (kept if sigma == 0).  Writes the last rho2 to
+ * rho_out [ny][nx].  The operator runs in the call's dtype; CG vectors, inner
+ * products, norms and the PnP scalars are FP64 in both precisions.  denoise
+ * NULL selects mpi_denoise_gaussian5.  info (HOST, n_iter entries) is
+ * optional: when given, the call synchronises the stream at the end. */
+int mpi_pnp_solve(const mpi_model *model, const mpi_grid_desc *grid,
+                  const mpi_traj *traj, mpi_dtype dtype, const void *data,
+                  const mpi_pnp_opts *opts, mpi_denoise_fn denoise, void *user,
+                  void *rho_out, mpi_pnp_iter_info *info, void *stream);
+
+/* ---- Diagnostics --------------------------------------------------------- */
+
+const char *mpi_status_string(int status);
+const char *mpi_last_error_message(void);
+/* Library version as 10000*major + 100*minor + patch. */
+int mpi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPI_RECON_H */

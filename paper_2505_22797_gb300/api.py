@@ -1,0 +1,333 @@
+"""Thin ctypes binding of ``libmpi_recon.so`` (declared in include/mpi_recon.h).
+
+Functions carry the C entry-point names and only marshal arguments: every
+array is a CUDA ``torch.Tensor`` (float32 or float64, contiguous) whose device
+pointer is passed through, and the call is enqueued on the current torch CUDA
+stream.  There is no CPU path: if the library cannot be loaded, or a tensor is
+not on a CUDA device, the call raises.
+
+``model`` and ``grid`` are mappings (or objects) with the fields of
+``mpi_model`` (beta, G 2x2, p n_ch x 2) and ``mpi_grid_desc`` (nx, ny, x0, y0,
+dx, dy).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpi_recon.so")
+
+MPI_OK = 0
+MPI_ERR_INVALID = -1
+MPI_ERR_CUDA = -2
+MPI_ERR_NOMEM = -3
+MPI_ERR_CALLBACK = -4
+MPI_ERR_TIMEOUT = -5
+MPI_ERR_UNSUPPORTED = -6
+MPI_F32, MPI_F64 = 0, 1
+MPI_OP_FORWARD, MPI_OP_CONV = 0, 1
+
+
+class MPIError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x0", ctypes.c_double),
+                ("y0", ctypes.c_double), ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("G", ctypes.c_double * 4), ("n_ch", ctypes.c_int),
+                ("p", ctypes.c_double * 4)]
+
+
+class Traj(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int64), ("r", ctypes.c_void_p), ("v", ctypes.c_void_p)]
+
+
+class GridOpts(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("max_iter", ctypes.c_int), ("rel_tol", ctypes.c_double)]
+
+
+class PnPOpts(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("n_iter", ctypes.c_int), ("n_cg", ctypes.c_int),
+                ("nu0", ctypes.c_double), ("clip_pct", ctypes.c_double)]
+
+
+class PnPIterInfo(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("nu", ctypes.c_double), ("cg_resid", ctypes.c_double)]
+
+
+DENOISE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                              ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "mpi_forward": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_adjoint": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_dbeta": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 4,
+    "mpi_conv": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_interp": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_interp_adjoint": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_grid": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 6,
+    "mpi_denoise_gaussian5": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "mpi_pnp_solve": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
+                     + [DENOISE_FN] + [ctypes.c_void_p] * 4,
+    "mpi_status_string": [ctypes.c_int],
+    "mpi_last_error_message": [],
+    "mpi_version": [],
+}
+
+
+def load(path: str | None = None):
+    """Load libmpi_recon.so (build it first with paper_2505_22797_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: run paper_2505_22797_gb300.build.build() first "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(p)
+        for name, args in _SIGS.items():
+            if hasattr(lib, name):
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+        lib.mpi_status_string.restype = ctypes.c_char_p
+        lib.mpi_last_error_message.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    lib = load()
+    return {name for name in _SIGS if hasattr(lib, name)}
+
+
+def _check(status: int):
+    if status != MPI_OK:
+        lib = load()
+        msg = lib.mpi_last_error_message().decode(errors="replace")
+        raise MPIError(status, f"{lib.mpi_status_string(status).decode()}: {msg}")
+
+
+def _get(obj, key):
+    return obj[key] if isinstance(obj, dict) else getattr(obj, key)
+
+
+def make_grid(grid) -> GridDesc:
+    return GridDesc(int(_get(grid, "nx")), int(_get(grid, "ny")), float(_get(grid, "x0")),
+                    float(_get(grid, "y0")), float(_get(grid, "dx")), float(_get(grid, "dy")))
+
+
+def make_model(model) -> Model:
+    G = [float(x) for row in _get(model, "G") for x in row]
+    P = [[float(x) for x in row] for row in _get(model, "p")]
+    flat = [x for row in P for x in row] + [0.0] * (4 - 2 * len(P))
+    return Model(float(_get(model, "beta")), (ctypes.c_double * 4)(*G), len(P),
+                 (ctypes.c_double * 4)(*flat))
+
+
+def _dtype(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return MPI_F32
+    if t.dtype == torch.float64:
+        return MPI_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _dev(t: torch.Tensor, dtype=None, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _traj(r: torch.Tensor, v: torch.Tensor, dt) -> Traj:
+    if r.shape != v.shape or r.dim() != 2 or r.shape[1] != 2:
+        raise ValueError("r and v must both be [T, 2]")
+    T = r.shape[0]
+    return Traj(T, _dev(r, dt, "r") if T else None, _dev(v, dt, "v") if T else None)
+
+
+def mpi_forward(model, grid, r, v, c, s=None, stream=None):
+    """s[k][t] = (A c)_k(t); returns s ([n_ch, T], dtype of c)."""
+    dt = c.dtype
+    n_ch = len(_get(model, "p"))
+    if s is None:
+        s = torch.empty((n_ch, r.shape[0]), dtype=dt, device=c.device)
+    tr = _traj(r, v, dt)
+    m, g = make_model(model), make_grid(grid)
+    _check(load().mpi_forward(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(c),
+                              _dev(c, dt, "c"), _dev(s, dt, "s") if s.numel() else None,
+                              _stream(stream)))
+    return s
+
+
+def mpi_adjoint(model, grid, r, v, s, c_out=None, stream=None):
+    """c_out = A^T s ([ny, nx], dtype of s)."""
+    dt = s.dtype
+    g = make_grid(grid)
+    if c_out is None:
+        c_out = torch.empty((g.ny, g.nx), dtype=dt, device=s.device)
+    tr = _traj(r, v, dt)
+    m = make_model(model)
+    _check(load().mpi_adjoint(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(s),
+                              _dev(s, dt, "s") if s.numel() else None, _dev(c_out, dt, "c_out"),
+                              _stream(stream)))
+    return c_out
+
+
+def mpi_dbeta(model, grid, r, v, c, g_s, out=None, stream=None):
+    """d/dbeta <g_s, A(c; beta)> as a 0-d float64 CUDA tensor."""
+    dt = c.dtype
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=c.device)
+    tr = _traj(r, v, dt)
+    m, g = make_model(model), make_grid(grid)
+    _check(load().mpi_dbeta(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(c),
+                            _dev(c, dt, "c"), _dev(g_s, dt, "g") if g_s.numel() else None,
+                            _dev(out, torch.float64, "out"), _stream(stream)))
+    return out
+
+
+def mpi_conv(model, grid, x, out=None, stream=None):
+    dt = x.dtype
+    if out is None:
+        out = torch.empty_like(x)
+    m, g = make_model(model), make_grid(grid)
+    _check(load().mpi_conv(ctypes.byref(m), ctypes.byref(g), _dtype(x), _dev(x, dt, "in"),
+                           _dev(out, dt, "out"), _stream(stream)))
+    return out
+
+
+def mpi_interp(grid, r, v, Ahat, s=None, stream=None):
+    dt = Ahat.dtype
+    if s is None:
+        s = torch.empty((2, r.shape[0]), dtype=dt, device=Ahat.device)
+    tr = _traj(r, v, dt)
+    g = make_grid(grid)
+    _check(load().mpi_interp(ctypes.byref(g), ctypes.byref(tr), _dtype(Ahat), _dev(Ahat, dt, "Ahat"),
+                             _dev(s, dt, "s") if s.numel() else None, _stream(stream)))
+    return s
+
+
+def mpi_interp_adjoint(grid, r, v, s, Ahat=None, stream=None):
+    dt = s.dtype
+    g = make_grid(grid)
+    if Ahat is None:
+        Ahat = torch.empty((4, g.ny, g.nx), dtype=dt, device=s.device)
+    tr = _traj(r, v, dt)
+    _check(load().mpi_interp_adjoint(ctypes.byref(g), ctypes.byref(tr), _dtype(s),
+                                     _dev(s, dt, "s") if s.numel() else None,
+                                     _dev(Ahat, dt, "Ahat"), _stream(stream)))
+    return Ahat
+
+
+def mpi_grid(grid, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=None, trace=None,
+             return_iters=False, stream=None):
+    dt = s.dtype
+    g = make_grid(grid)
+    if Ahat is None:
+        Ahat = torch.empty((4, g.ny, g.nx), dtype=dt, device=s.device)
+    if trace is None:
+        trace = torch.empty((g.ny, g.nx), dtype=dt, device=s.device)
+    tr = _traj(r, v, dt)
+    opts = GridOpts(float(gamma), int(max_iter), float(rel_tol))
+    n_it = ctypes.c_int(-1)
+    _check(load().mpi_grid(ctypes.byref(g), ctypes.byref(tr), _dtype(s),
+                           _dev(s, dt, "s") if s.numel() else None, ctypes.byref(opts),
+                           _dev(Ahat, dt, "Ahat"), _dev(trace, dt, "trace"),
+                           ctypes.byref(n_it) if return_iters else None, _stream(stream)))
+    if return_iters:
+        return Ahat, trace, n_it.value
+    return Ahat, trace
+
+
+def mpi_denoise_gaussian5(x, out=None, stream=None):
+    dt = x.dtype
+    if out is None:
+        out = torch.empty_like(x)
+    ny, nx = x.shape
+    _check(load().mpi_denoise_gaussian5(_dev(x, dt, "in"), _dev(out, dt, "out"), nx, ny, _dtype(x),
+                                        None, _stream(stream), None))
+    return out
+
+
+def mpi_pnp_solve(model, grid, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, op=MPI_OP_FORWARD,
+                  denoise=None, rho_out=None, with_info=False, stream=None):
+    """Algorithm 1.  ``denoise`` is None (built-in Gaussian) or a Python
+    callable (in_tensor, out_tensor, sigma_dev_tensor) -> None that enqueues
+    on the current stream."""
+    dt = data.dtype
+    g = make_grid(grid)
+    if rho_out is None:
+        rho_out = torch.empty((g.ny, g.nx), dtype=dt, device=data.device)
+    if op == MPI_OP_FORWARD:
+        tr = _traj(r, v, dt)
+    else:
+        tr = Traj(0, None, None) if r is None else _traj(r, v, dt)
+    m = make_model(model)
+    opts = PnPOpts(int(op), int(n_iter), int(n_cg), float(nu0), float(clip_pct))
+    info = (PnPIterInfo * max(1, n_iter))() if with_info else None
+    cb = DENOISE_FN(0)
+    keep = None
+    if denoise is not None:
+        dev = data.device
+
+        def _cb(pin, pout, nx, ny, dtype, sig, strm, user):
+            try:
+                tdt = torch.float32 if dtype == MPI_F32 else torch.float64
+                tin = _wrap(pin, (ny, nx), tdt, dev)
+                tout = _wrap(pout, (ny, nx), tdt, dev)
+                tsig = _wrap(sig, (), torch.float64, dev)
+                denoise(tin, tout, tsig)
+                return 0
+            except Exception:  # noqa: BLE001 - reported as MPI_ERR_CALLBACK
+                return 1
+        cb = DENOISE_FN(_cb)
+        keep = cb
+    _check(load().mpi_pnp_solve(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(data),
+                                _dev(data, dt, "data"), ctypes.byref(opts), cb, None,
+                                _dev(rho_out, dt, "rho_out"), info, _stream(stream)))
+    del keep
+    if with_info:
+        return rho_out, [(i.sigma, i.nu, i.cg_resid) for i in info[:n_iter]]
+    return rho_out
+
+
+def _wrap(ptr, shape, dtype, device):
+    """A tensor view of library-owned device memory (no copy), through the
+    CUDA array interface."""
+    n = 1
+    for s in shape:
+        n *= s
+    if n == 0 or not ptr:
+        return torch.empty(shape, dtype=dtype, device=device)
+
+    class _CAI:
+        __cuda_array_interface__ = {
+            "shape": (n,), "typestr": {torch.float32: "<f4", torch.float64: "<f8"}[dtype],
+            "data": (ptr, False), "version": 3, "strides": None, "stream": None}
+    return torch.as_tensor(_CAI(), device=device).view(shape)

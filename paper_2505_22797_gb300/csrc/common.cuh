@@ -1,0 +1,138 @@
+// Shared host/device helpers of the sm_103a MPI reconstruction library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "mpi_recon.h"
+
+namespace mpi {
+
+// ---------------------------------------------------------------------------
+// Error reporting (host).  Every entry point returns an mpi_status; the
+// reason of the last failure on this host thread is kept for
+// mpi_last_error_message().
+void set_error(const char *fmt, ...);
+const char *last_error();
+
+#define MPI_TRY_CUDA(expr)                                                        \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            ::mpi::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                             __FILE__, __LINE__);                                 \
+            return MPI_ERR_CUDA;                                                  \
+        }                                                                         \
+    } while (0)
+
+#define MPI_TRY(expr)                        \
+    do {                                     \
+        int st_ = (expr);                    \
+        if (st_ != MPI_OK) return st_;       \
+    } while (0)
+
+#define MPI_CHECK_LAUNCH() MPI_TRY_CUDA(cudaGetLastError())
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Stream-ordered scratch: one cudaMallocAsync carved into aligned pieces, freed
+// (stream-ordered) when the object goes out of scope.
+class Scratch {
+  public:
+    explicit Scratch(cudaStream_t s) : stream_(s) {}
+    ~Scratch() { release(); }
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    // Reserve `bytes` (rounded up to 256) and return its offset.
+    size_t reserve(size_t bytes) {
+        size_t off = total_;
+        total_ += (bytes + 255) & ~size_t(255);
+        return off;
+    }
+    int allocate();
+    template <typename T>
+    T *at(size_t off) const { return reinterpret_cast<T *>(base_ + off); }
+    void release();
+    size_t total() const { return total_; }
+
+  private:
+    cudaStream_t stream_;
+    char *base_ = nullptr;
+    size_t total_ = 0;
+};
+
+int device_sm_count();
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+
+template <typename R> struct V2 { R x, y; };
+template <typename R> struct V4 { R x, y, z, w; };
+template <> struct alignas(8) V2<float> { float x, y; };
+template <> struct alignas(16) V4<float> { float x, y, z, w; };
+template <> struct alignas(16) V2<double> { double x, y; };
+template <> struct alignas(16) V4<double> { double x, y, z, w; };
+
+#ifdef __CUDACC__
+// PTX approximate transcendental instructions (flush-to-zero forms).  Their
+// errors are a few units in the last place of FP32; the callers' accuracy
+// budget is derived with them in place.
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Compensated (Kahan) accumulation: sum += x with running compensation.
+template <typename R>
+__device__ __forceinline__ void kahan_add(R &sum, R &comp, R x)
+{
+    R y = x - comp;
+    R t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed shuffle tree, then warps in order).  All
+// threads of the block must call it; the result is valid in thread 0.
+template <typename R, int NT>
+__device__ __forceinline__ R block_sum(R v, R *sh /* >= NT/32 */)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    R t = R(0);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t += sh[w];
+    }
+    __syncthreads();
+    return t;
+}
+#endif
+
+}  // namespace mpi

@@ -1,0 +1,357 @@
+// Device kernels of the pair sums (forward A, adjoint A^T, d/dbeta).
+//
+// Every (voxel, sample) pair evaluates the Langevin kernel once; there is no
+// contraction to hand to the tensor cores (one FMA per pair per channel), so
+// the kernels are bound by the FP32 and MUFU (XU) pipes: per pair 3 MUFU
+// operations (rsqrt, exp2, rcp) and ~18 FP32 operations.
+//
+// Both kernels take a frame table by value, so one launch can cover many
+// frames of different sizes: blockIdx.x enumerates work items of all frames
+// (frame f owns items [item0_f, item0_f + n_items_f)).
+#pragma once
+
+#include "langevin.cuh"
+#include "pair_ops.cuh"
+
+namespace mpi {
+
+constexpr int kFwdThreads = 128;
+constexpr int kFwdS = 2;  // samples per thread
+constexpr int kFwdTile = kFwdThreads * kFwdS;
+
+constexpr int kAdjThreads = 128;  // 4 warps
+constexpr int kAdjV = 8;          // voxels (rows) per thread
+constexpr int kAdjTileX = 32;
+constexpr int kAdjTileY = 4 * kAdjV;
+constexpr int kAdjBlock = 256;    // samples staged per shared-memory block
+
+template <typename R>
+struct PairFrame {
+    const V4<R> *rw;
+    const V2<R> *xcol;
+    const V2<R> *yrow;
+    const void *in;   // forward: c [ny][nx]; adjoint: s [n_ch][T]; dbeta: c
+    const void *in2;  // dbeta: g [n_ch][T]
+    void *part;       // partial sums
+    int64_t T;
+    int64_t item0;
+    int nx, ny;
+    int n_ch;
+    int n_tiles;      // forward: sample tiles; adjoint: voxel tiles
+    int tiles_x;      // adjoint only
+    int chunk;        // forward: rows per chunk; adjoint: samples per chunk
+    R p[4];
+};
+
+template <typename R, int MAXF>
+struct PairBatch {
+    int n_frames;
+    PairFrame<R> f[MAXF];
+};
+
+#ifdef __CUDACC__
+
+template <typename R, int MAXF>
+__device__ __forceinline__ int find_frame(const PairBatch<R, MAXF> &B, int64_t item)
+{
+    int f = 0;
+#pragma unroll 1
+    for (int q = 1; q < B.n_frames; ++q)
+        if (item >= B.f[q].item0) f = q;
+    return f;
+}
+
+// ---------------------------------------------------------------------------
+// Forward A.  Work item = (tile of kFwdTile samples, chunk of rows).  Each
+// thread owns kFwdS samples and sums over the chunk's voxels row by row:
+//   O(t) = sum_x c_x [a W + d (y.W) y] = Sa W + V,   W = beta G v,
+// with the row structure used twice: y_y (diagonal G) is constant along a row,
+// so V_y = y_y sum_row f; and rows far from every sample of the warp skip the
+// near-FFP series test entirely.  Row sums are folded into the chunk sums with
+// compensated additions.  The item writes p_k . O(t) to its partial slot.
+template <typename R, typename CIN, bool DIAG, int MAXF>
+__global__ void __launch_bounds__(kFwdThreads)
+k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t item = blockIdx.x;
+    const PairFrame<R> &F = B.f[find_frame(B, item)];
+    const int64_t local = item - F.item0;
+    const int chunk = (int)(local / F.n_tiles);
+    const int tile = (int)(local % F.n_tiles);
+    const int nx = F.nx;
+    const int j0 = chunk * F.chunk;
+    const int nr = min(F.chunk, F.ny - j0);
+
+    V2<R> *s_x = reinterpret_cast<V2<R> *>(smem_raw);
+    V2<R> *s_y = s_x + nx;
+    R *s_c = reinterpret_cast<R *>(s_y + F.chunk);
+    const CIN *cin = reinterpret_cast<const CIN *>(F.in);
+    for (int k = threadIdx.x; k < nr * nx; k += kFwdThreads)
+        s_c[k] = R(cin[(int64_t)j0 * nx + k]);
+    for (int k = threadIdx.x; k < nx; k += kFwdThreads) s_x[k] = F.xcol[k];
+    for (int k = threadIdx.x; k < nr; k += kFwdThreads) s_y[k] = F.yrow[j0 + k];
+    __syncthreads();
+
+    R Rx[kFwdS], Ry[kFwdS], Wx[kFwdS], Wy[kFwdS];
+    int64_t t[kFwdS];
+#pragma unroll
+    for (int s = 0; s < kFwdS; ++s) {
+        t[s] = (int64_t)tile * kFwdTile + s * kFwdThreads + threadIdx.x;
+        const V4<R> q = F.rw[t[s] < F.T ? t[s] : F.T - 1];
+        Rx[s] = q.x; Ry[s] = q.y; Wx[s] = q.z; Wy[s] = q.w;
+    }
+    R Sa[kFwdS], Vx[kFwdS], Vy[kFwdS], cSa[kFwdS], cVx[kFwdS], cVy[kFwdS];
+#pragma unroll
+    for (int s = 0; s < kFwdS; ++s) Sa[s] = Vx[s] = Vy[s] = cSa[s] = cVx[s] = cVy[s] = R(0);
+
+#pragma unroll 1
+    for (int r = 0; r < nr; ++r) {
+        const V2<R> yr = s_y[r];
+        const R *crow = s_c + r * nx;
+        R oy[kFwdS], ox[kFwdS], yy2[kFwdS], yyW[kFwdS];
+        R sa[kFwdS], vx[kFwdS], fy[kFwdS];
+        bool near = false;
+#pragma unroll
+        for (int s = 0; s < kFwdS; ++s) {
+            oy[s] = yr.y - Ry[s];
+            ox[s] = yr.x - Rx[s];
+            yy2[s] = oy[s] * oy[s];
+            yyW[s] = oy[s] * Wy[s];
+            near |= yy2[s] < Lang<R>::near_u;
+            sa[s] = vx[s] = fy[s] = R(0);
+        }
+        if (DIAG && !__any_sync(0xffffffffu, near)) {
+            // Every pair of this row has u >= yy2 >= near_u: closed form only.
+#pragma unroll 4
+            for (int i = 0; i < nx; ++i) {
+                const R xi = s_x[i].x;
+                const R ci = crow[i];
+#pragma unroll
+                for (int s = 0; s < kFwdS; ++s) {
+                    const R yx = xi - Rx[s];
+                    const R u = yx * yx + yy2[s];
+                    R a, d;
+                    lang_far<R, false>(u, a, d);
+                    sa[s] += ci * a;
+                    const R f = ci * d * (yx * Wx[s] + yyW[s]);
+                    vx[s] += f * yx;
+                    fy[s] += f;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < kFwdS; ++s) {
+                kahan_add(Sa[s], cSa[s], sa[s]);
+                kahan_add(Vx[s], cVx[s], vx[s]);
+                kahan_add(Vy[s], cVy[s], oy[s] * fy[s]);
+            }
+        } else {
+            // General case: near-FFP pairs possible (or a non-diagonal G).
+#pragma unroll 2
+            for (int i = 0; i < nx; ++i) {
+                const V2<R> xi = s_x[i];
+                const R ci = crow[i];
+#pragma unroll
+                for (int s = 0; s < kFwdS; ++s) {
+                    const R yx = xi.x + ox[s];
+                    const R yy = DIAG ? oy[s] : xi.y + oy[s];
+                    const R u = yx * yx + yy * yy;
+                    R a, d;
+                    lang_checked<R, false>(u, a, d);
+                    sa[s] += ci * a;
+                    const R f = ci * d * (yx * Wx[s] + yy * Wy[s]);
+                    vx[s] += f * yx;
+                    fy[s] += f * yy;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < kFwdS; ++s) {
+                kahan_add(Sa[s], cSa[s], sa[s]);
+                kahan_add(Vx[s], cVx[s], vx[s]);
+                kahan_add(Vy[s], cVy[s], fy[s]);
+            }
+        }
+    }
+
+    R *part = reinterpret_cast<R *>(F.part);
+#pragma unroll
+    for (int s = 0; s < kFwdS; ++s) {
+        if (t[s] < F.T) {
+            const R Ox = Sa[s] * Wx[s] + Vx[s];
+            const R Oy = Sa[s] * Wy[s] + Vy[s];
+            for (int k = 0; k < F.n_ch; ++k)
+                part[((int64_t)chunk * F.n_ch + k) * F.T + t[s]] = F.p[2 * k] * Ox + F.p[2 * k + 1] * Oy;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint A^T (DBETA = false) and the beta-derivative (DBETA = true).
+// Work item = (tile of 32 x 32 voxels, chunk of samples).  Lane = column, each
+// thread owns kAdjV consecutive rows of its column.  Samples are staged in
+// shared memory kAdjBlock at a time as
+//   (B r_t) and (u.W, W_x u_x, W_x u_y + W_y u_x, W_y u_y),  u = sum_k s_k p_k,
+// so that the pair term u^T J w = a (u.W) + d (y.W)(y.u) is
+//   f1 uW + f2 (yx^2 Sxx + yx yy S2xy + yy^2 Syy)
+// with (f1, f2) = (a, d) for A^T and (L', L''/z) for d/dbeta.  Per warp and
+// staged block a ballot marks the samples whose distance to the warp's voxel
+// box keeps every pair in the closed-form range.
+template <typename R, bool DIAG, bool DBETA, int MAXF>
+__global__ void __launch_bounds__(kAdjThreads)
+k_adjoint(const __grid_constant__ PairBatch<R, MAXF> B)
+{
+    __shared__ V2<R> s_r[kAdjBlock];
+    __shared__ V4<R> s_q[kAdjBlock];
+    __shared__ uint32_t s_far[4][kAdjBlock / 32];
+    __shared__ double s_red[kAdjThreads / 32];
+
+    const int64_t item = blockIdx.x;
+    const PairFrame<R> &F = B.f[find_frame(B, item)];
+    const int64_t local = item - F.item0;
+    const int chunk = (int)(local / F.n_tiles);
+    const int tile = (int)(local % F.n_tiles);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = (tile % F.tiles_x) * kAdjTileX + lane;
+    const int jb = (tile / F.tiles_x) * kAdjTileY + warp * kAdjV;
+    const int ic = min(i, F.nx - 1);
+
+    const V2<R> xc = F.xcol[ic];
+    R yrow_y[kAdjV], yrow_x[kAdjV];
+#pragma unroll
+    for (int v = 0; v < kAdjV; ++v) {
+        const V2<R> q = F.yrow[min(jb + v, F.ny - 1)];
+        yrow_x[v] = q.x;
+        yrow_y[v] = q.y;
+    }
+    // Voxel box of this warp in prescaled coordinates (conservative).
+    R bx_lo = xc.x, bx_hi = xc.x, by_lo = xc.y, by_hi = xc.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bx_lo = min(bx_lo, __shfl_xor_sync(0xffffffffu, bx_lo, o));
+        bx_hi = max(bx_hi, __shfl_xor_sync(0xffffffffu, bx_hi, o));
+        by_lo = min(by_lo, __shfl_xor_sync(0xffffffffu, by_lo, o));
+        by_hi = max(by_hi, __shfl_xor_sync(0xffffffffu, by_hi, o));
+    }
+    {
+        R ry_lo = yrow_y[0], ry_hi = yrow_y[0], rx_lo = yrow_x[0], rx_hi = yrow_x[0];
+#pragma unroll
+        for (int v = 1; v < kAdjV; ++v) {
+            ry_lo = min(ry_lo, yrow_y[v]); ry_hi = max(ry_hi, yrow_y[v]);
+            rx_lo = min(rx_lo, yrow_x[v]); rx_hi = max(rx_hi, yrow_x[v]);
+        }
+        bx_lo += rx_lo; bx_hi += rx_hi; by_lo += ry_lo; by_hi += ry_hi;
+    }
+
+    const int64_t t0 = (int64_t)chunk * F.chunk;
+    const int64_t t1 = min(F.T, t0 + F.chunk);
+    const R *sin = reinterpret_cast<const R *>(DBETA ? F.in2 : F.in);
+
+    R acc[kAdjV], comp[kAdjV];
+#pragma unroll
+    for (int v = 0; v < kAdjV; ++v) acc[v] = comp[v] = R(0);
+
+#pragma unroll 1
+    for (int64_t tb = t0; tb < t1; tb += kAdjBlock) {
+        const int nb = (int)min((int64_t)kAdjBlock, t1 - tb);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nb; k += kAdjThreads) {
+            const int64_t t = tb + k;
+            const V4<R> q = F.rw[t];
+            R ux = R(0), uy = R(0);
+            for (int c = 0; c < F.n_ch; ++c) {
+                const R sv = sin[(int64_t)c * F.T + t];
+                ux += sv * F.p[2 * c];
+                uy += sv * F.p[2 * c + 1];
+            }
+            s_r[k] = V2<R>{q.x, q.y};
+            s_q[k] = V4<R>{ux * q.z + uy * q.w, q.z * ux, q.z * uy + q.w * ux, q.w * uy};
+        }
+        __syncthreads();
+        // Far flags of this warp for the staged samples.
+        for (int m = 0; m < kAdjBlock / 32; ++m) {
+            const int k = m * 32 + lane;
+            bool far = true;
+            if (k < nb) {
+                const V2<R> q = s_r[k];
+                const R ddx = max(R(0), max(bx_lo - q.x, q.x - bx_hi));
+                const R ddy = max(R(0), max(by_lo - q.y, q.y - by_hi));
+                far = ddx * ddx + ddy * ddy >= Lang<R>::near_u;
+            }
+            const uint32_t bits = __ballot_sync(0xffffffffu, far);
+            if (lane == 0) s_far[warp][m] = bits;
+        }
+        __syncwarp();
+
+        R blk[kAdjV];
+#pragma unroll
+        for (int v = 0; v < kAdjV; ++v) blk[v] = R(0);
+#pragma unroll 1
+        for (int k = 0; k < nb; ++k) {
+            const V2<R> rr = s_r[k];
+            const V4<R> q = s_q[k];
+            const bool far = (s_far[warp][k >> 5] >> (k & 31)) & 1u;
+            if (DIAG) {
+                const R yx = xc.x - rr.x;
+                const R yx2 = yx * yx;
+                const R Q0 = q.y * yx2, Q1 = q.z * yx;
+                if (far) {
+#pragma unroll
+                    for (int v = 0; v < kAdjV; ++v) {
+                        const R yy = yrow_y[v] - rr.y;
+                        const R u = yy * yy + yx2;
+                        R f1, f2;
+                        lang_far<R, DBETA>(u, f1, f2);
+                        blk[v] += f1 * q.x + f2 * (yy * (q.w * yy + Q1) + Q0);
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < kAdjV; ++v) {
+                        const R yy = yrow_y[v] - rr.y;
+                        const R u = yy * yy + yx2;
+                        R f1, f2;
+                        lang_checked<R, DBETA>(u, f1, f2);
+                        blk[v] += f1 * q.x + f2 * (yy * (q.w * yy + Q1) + Q0);
+                    }
+                }
+            } else {
+                const R ox = xc.x - rr.x, oy = xc.y - rr.y;
+#pragma unroll
+                for (int v = 0; v < kAdjV; ++v) {
+                    const R yx = ox + yrow_x[v];
+                    const R yy = oy + yrow_y[v];
+                    const R u = yx * yx + yy * yy;
+                    R f1, f2;
+                    if (far) lang_far<R, DBETA>(u, f1, f2);
+                    else lang_checked<R, DBETA>(u, f1, f2);
+                    blk[v] += f1 * q.x + f2 * (yx * (q.y * yx + q.z * yy) + q.w * yy * yy);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kAdjV; ++v) kahan_add(acc[v], comp[v], blk[v]);
+    }
+
+    if constexpr (!DBETA) {
+        R *part = reinterpret_cast<R *>(F.part);
+        const int64_t N = (int64_t)F.nx * F.ny;
+        if (i < F.nx) {
+#pragma unroll
+            for (int v = 0; v < kAdjV; ++v)
+                if (jb + v < F.ny) part[(int64_t)chunk * N + (int64_t)(jb + v) * F.nx + i] = acc[v];
+        }
+    } else {
+        const R *c = reinterpret_cast<const R *>(F.in);
+        double sum = 0.0;
+        if (i < F.nx) {
+#pragma unroll
+            for (int v = 0; v < kAdjV; ++v)
+                if (jb + v < F.ny) sum += double(c[(int64_t)(jb + v) * F.nx + i]) * double(acc[v]);
+        }
+        sum = block_sum<double, kAdjThreads>(sum, s_red);
+        if (threadIdx.x == 0) reinterpret_cast<double *>(F.part)[local] = sum;
+    }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace mpi

@@ -1,0 +1,377 @@
+// Host launchers of the pair sums, the geometry preparation and the
+// deterministic partial-sum reductions.
+#include <algorithm>
+#include <cmath>
+
+#include "pair_kernels.cuh"
+
+namespace mpi {
+
+// ---------------------------------------------------------------------------
+// Geometry preparation: beta G applied to sample positions/velocities and to
+// voxel-centre coordinates, in FP64, rounded once to R.
+
+template <typename R, typename IN>
+__global__ void k_prepare_samples(const IN *__restrict__ r, const IN *__restrict__ v, int64_t T,
+                                  double b00, double b01, double b10, double b11,
+                                  V4<R> *__restrict__ rw)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double rx = double(r[2 * t]), ry = double(r[2 * t + 1]);
+        const double vx = double(v[2 * t]), vy = double(v[2 * t + 1]);
+        rw[t] = V4<R>{R(b00 * rx + b01 * ry), R(b10 * rx + b11 * ry),
+                      R(b00 * vx + b01 * vy), R(b10 * vx + b11 * vy)};
+    }
+}
+
+template <typename R>
+__global__ void k_prepare_grid(int nx, int ny, double x0, double y0, double dx, double dy,
+                               double b00, double b01, double b10, double b11,
+                               V2<R> *__restrict__ xcol, V2<R> *__restrict__ yrow)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nx) {
+        const double x = x0 + (k + 0.5) * dx;
+        xcol[k] = V2<R>{R(b00 * x), R(b10 * x)};
+    }
+    if (k < ny) {
+        const double y = y0 + (k + 0.5) * dy;
+        yrow[k] = V2<R>{R(b01 * y), R(b11 * y)};
+    }
+}
+
+template <typename R>
+size_t geometry_bytes(int64_t T, int nx, int ny)
+{
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return up(sizeof(V4<R>) * size_t(std::max<int64_t>(T, 1))) + up(sizeof(V2<R>) * nx) +
+           up(sizeof(V2<R>) * ny);
+}
+
+template <typename R>
+Geometry<R> geometry_carve(void *base, int64_t T, int nx, int ny)
+{
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char *p = static_cast<char *>(base);
+    Geometry<R> g;
+    g.rw = reinterpret_cast<V4<R> *>(p);
+    p += up(sizeof(V4<R>) * size_t(std::max<int64_t>(T, 1)));
+    g.xcol = reinterpret_cast<V2<R> *>(p);
+    p += up(sizeof(V2<R>) * nx);
+    g.yrow = reinterpret_cast<V2<R> *>(p);
+    return g;
+}
+
+template <typename R>
+int prepare_geometry(const ModelH &m, const GridH &g, int64_t T, const void *r, const void *v,
+                     const Geometry<R> &geo, cudaStream_t st)
+{
+    const double b00 = m.beta * m.G[0], b01 = m.beta * m.G[1];
+    const double b10 = m.beta * m.G[2], b11 = m.beta * m.G[3];
+    if (T > 0) {
+        const int blocks = (int)std::min<int64_t>((T + 255) / 256, 4096);
+        k_prepare_samples<R, R><<<blocks, 256, 0, st>>>(static_cast<const R *>(r),
+                                                        static_cast<const R *>(v), T, b00, b01,
+                                                        b10, b11, geo.rw);
+        MPI_CHECK_LAUNCH();
+    }
+    const int n = std::max(g.nx, g.ny);
+    k_prepare_grid<R><<<(n + 127) / 128, 128, 0, st>>>(g.nx, g.ny, g.x0, g.y0, g.dx, g.dy, b00,
+                                                       b01, b10, b11, geo.xcol, geo.yrow);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Work decomposition.
+
+int default_target_items() { return 8 * 4 * device_sm_count(); }
+
+static constexpr size_t kFwdSmemBudget = 96 * 1024;
+
+FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_items)
+{
+    FwdSplit sp;
+    sp.n_tiles = (int)std::max<int64_t>(1, (T + kFwdTile - 1) / kFwdTile);
+    int want = (target_items + sp.n_tiles - 1) / sp.n_tiles;
+    want = std::max(1, std::min(want, ny));
+    int rows = (ny + want - 1) / want;
+    // shared memory: xcol (nx) + yrow (rows) + c rows
+    const size_t fixed = size_t(2 * elem_bytes) * nx;
+    const size_t per_row = size_t(elem_bytes) * nx + 2 * elem_bytes;
+    const int max_rows = (int)std::max<size_t>(1, (kFwdSmemBudget - std::min(fixed, kFwdSmemBudget)) / per_row);
+    rows = std::max(1, std::min(rows, max_rows));
+    sp.chunk_rows = rows;
+    sp.n_chunks = (ny + rows - 1) / rows;
+    return sp;
+}
+
+AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items)
+{
+    AdjSplit sp;
+    sp.tiles_x = (nx + kAdjTileX - 1) / kAdjTileX;
+    sp.tiles_y = (ny + kAdjTileY - 1) / kAdjTileY;
+    const int n_tiles = sp.tiles_x * sp.tiles_y;
+    const int64_t blocks = std::max<int64_t>(1, (T + kAdjBlock - 1) / kAdjBlock);
+    int64_t want = (target_items + n_tiles - 1) / n_tiles;
+    want = std::max<int64_t>(1, std::min(want, blocks));
+    const int64_t per = (blocks + want - 1) / want;  // staged blocks per chunk
+    sp.chunk_len = (int)(per * kAdjBlock);
+    sp.n_chunks = (int)std::max<int64_t>(1, (T + sp.chunk_len - 1) / sp.chunk_len);
+    return sp;
+}
+
+template <typename R>
+size_t forward_partial_bytes(const FwdSplit &sp, int n_ch, int64_t T)
+{
+    return sizeof(R) * size_t(sp.n_chunks) * n_ch * size_t(std::max<int64_t>(T, 1));
+}
+template <typename R>
+size_t adjoint_partial_bytes(const AdjSplit &sp, int nx, int ny)
+{
+    return sizeof(R) * size_t(sp.n_chunks) * size_t(nx) * ny;
+}
+size_t dbeta_partial_bytes(const AdjSplit &sp)
+{
+    return sizeof(double) * size_t(sp.n_chunks) * sp.tiles_x * sp.tiles_y;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions over chunks, in FP64 and in a fixed order.
+
+template <typename R, typename OUT>
+__global__ void k_reduce_chunks(const R *__restrict__ part, int n_chunks, int64_t len,
+                                OUT *__restrict__ out)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < n_chunks; ++c) acc += double(part[(int64_t)c * len + e]);
+        out[e] = OUT(acc);
+    }
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kDotPerBlock = 2048;  // elements per block of the CG epilogue
+
+int adjoint_dot_blocks(int nx, int ny)
+{
+    return (int)(((int64_t)nx * ny + kDotPerBlock - 1) / kDotPerBlock);
+}
+
+// out = sum_chunks part + nu * p  (CG operator application), and per-block
+// partial sums of <p, out>.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_chunks_cg(const R *__restrict__ part, int n_chunks, int64_t len,
+                   const double *__restrict__ p, const double *__restrict__ nu_dev,
+                   double *__restrict__ out, double *__restrict__ dot_part)
+{
+    __shared__ double sh[kRedThreads / 32];
+    const double nu = *nu_dev;
+    const int64_t e0 = (int64_t)blockIdx.x * kDotPerBlock;
+    const int64_t e1 = min(len, e0 + kDotPerBlock);
+    double dot = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
+        double acc = 0.0;
+        for (int c = 0; c < n_chunks; ++c) acc += double(part[(int64_t)c * len + e]);
+        const double pe = p[e];
+        acc += nu * pe;
+        out[e] = acc;
+        dot += pe * acc;
+    }
+    dot = block_sum<double, kRedThreads>(dot, sh);
+    if (threadIdx.x == 0) dot_part[blockIdx.x] = dot;
+}
+
+__global__ void k_sum_fixed(const double *__restrict__ part, int n, double scale,
+                            double *__restrict__ out)
+{
+    __shared__ double sh[kRedThreads / 32];
+    double acc = 0.0;
+    // fixed assignment of parts to threads, fixed tree: deterministic
+    for (int k = threadIdx.x; k < n; k += kRedThreads) acc += part[k];
+    acc = block_sum<double, kRedThreads>(acc, sh);
+    if (threadIdx.x == 0) *out = acc * scale;
+}
+
+static int reduce_grid(int64_t len)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((len + kRedThreads - 1) / kRedThreads,
+                                                       (int64_t)device_sm_count() * 8));
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+
+static bool is_diag(const ModelH &m) { return m.G[1] == 0.0 && m.G[2] == 0.0; }
+
+template <typename R>
+static PairFrame<R> base_frame(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo)
+{
+    PairFrame<R> f{};
+    f.rw = geo.rw;
+    f.xcol = geo.xcol;
+    f.yrow = geo.yrow;
+    f.T = T;
+    f.item0 = 0;
+    f.nx = g.nx;
+    f.ny = g.ny;
+    f.n_ch = m.n_ch;
+    for (int k = 0; k < 4; ++k) f.p[k] = R(m.p[k]);
+    return f;
+}
+
+template <typename Kern>
+static int set_smem(Kern k, size_t bytes)
+{
+    if (bytes > 48 * 1024)
+        MPI_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return MPI_OK;
+}
+
+template <typename R, typename CIN, typename OUT>
+int launch_forward(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo,
+                   const FwdSplit &sp, const CIN *c, R *part, OUT *s_out, cudaStream_t st)
+{
+    if (T == 0) return MPI_OK;
+    PairBatch<R, 1> B;
+    B.n_frames = 1;
+    B.f[0] = base_frame(m, g, T, geo);
+    B.f[0].in = c;
+    B.f[0].part = part;
+    B.f[0].n_tiles = sp.n_tiles;
+    B.f[0].chunk = sp.chunk_rows;
+    const size_t smem = sizeof(V2<R>) * (g.nx + sp.chunk_rows) + sizeof(R) * size_t(sp.chunk_rows) * g.nx;
+    const int64_t items = (int64_t)sp.n_tiles * sp.n_chunks;
+    if (is_diag(m)) {
+        MPI_TRY(set_smem(k_forward<R, CIN, true, 1>, smem));
+        k_forward<R, CIN, true, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
+    } else {
+        MPI_TRY(set_smem(k_forward<R, CIN, false, 1>, smem));
+        k_forward<R, CIN, false, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
+    }
+    MPI_CHECK_LAUNCH();
+    const int64_t len = (int64_t)m.n_ch * T;
+    k_reduce_chunks<R, OUT><<<reduce_grid(len), kRedThreads, 0, st>>>(part, sp.n_chunks, len, s_out);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+template <typename R, typename OUT>
+int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo,
+                   const AdjSplit &sp, const R *s, R *part, OUT *out, const double *cg_p,
+                   const double *nu_dev, double *dot_part, cudaStream_t st)
+{
+    const int64_t N = (int64_t)g.nx * g.ny;
+    if (T > 0) {
+        PairBatch<R, 1> B;
+        B.n_frames = 1;
+        B.f[0] = base_frame(m, g, T, geo);
+        B.f[0].in = s;
+        B.f[0].part = part;
+        B.f[0].n_tiles = sp.tiles_x * sp.tiles_y;
+        B.f[0].tiles_x = sp.tiles_x;
+        B.f[0].chunk = sp.chunk_len;
+        const int64_t items = (int64_t)sp.tiles_x * sp.tiles_y * sp.n_chunks;
+        if (is_diag(m))
+            k_adjoint<R, true, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+        else
+            k_adjoint<R, false, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+        MPI_CHECK_LAUNCH();
+    } else {
+        MPI_TRY_CUDA(cudaMemsetAsync(part, 0, sizeof(R) * N, st));
+    }
+    const int nch = T > 0 ? sp.n_chunks : 1;
+    if (cg_p) {
+        if constexpr (sizeof(OUT) == sizeof(double)) {
+            k_reduce_chunks_cg<R><<<adjoint_dot_blocks(g.nx, g.ny), kRedThreads, 0, st>>>(
+                part, nch, N, cg_p, nu_dev, reinterpret_cast<double *>(out), dot_part);
+        } else {
+            set_error("internal: CG epilogue needs FP64 output");
+            return MPI_ERR_INVALID;
+        }
+    } else {
+        k_reduce_chunks<R, OUT><<<reduce_grid(N), kRedThreads, 0, st>>>(part, nch, N, out);
+    }
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+template <typename R>
+int launch_dbeta(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo,
+                 const AdjSplit &sp, const R *c, const R *gs, double *part, double *out_dev,
+                 cudaStream_t st)
+{
+    if (T == 0) {
+        MPI_TRY_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(double), st));
+        return MPI_OK;
+    }
+    PairBatch<R, 1> B;
+    B.n_frames = 1;
+    B.f[0] = base_frame(m, g, T, geo);
+    B.f[0].in = c;
+    B.f[0].in2 = gs;
+    B.f[0].part = part;
+    B.f[0].n_tiles = sp.tiles_x * sp.tiles_y;
+    B.f[0].tiles_x = sp.tiles_x;
+    B.f[0].chunk = sp.chunk_len;
+    const int64_t items = (int64_t)sp.tiles_x * sp.tiles_y * sp.n_chunks;
+    if (is_diag(m))
+        k_adjoint<R, true, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+    else
+        k_adjoint<R, false, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+    MPI_CHECK_LAUNCH();
+    // The kernel sums u . (beta D) with W = beta G v; divide by beta.
+    k_sum_fixed<<<1, kRedThreads, 0, st>>>(part, (int)items, 1.0 / m.beta, out_dev);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Instantiations.
+
+template size_t geometry_bytes<float>(int64_t, int, int);
+template size_t geometry_bytes<double>(int64_t, int, int);
+template Geometry<float> geometry_carve<float>(void *, int64_t, int, int);
+template Geometry<double> geometry_carve<double>(void *, int64_t, int, int);
+template int prepare_geometry<float>(const ModelH &, const GridH &, int64_t, const void *,
+                                     const void *, const Geometry<float> &, cudaStream_t);
+template int prepare_geometry<double>(const ModelH &, const GridH &, int64_t, const void *,
+                                      const void *, const Geometry<double> &, cudaStream_t);
+template size_t forward_partial_bytes<float>(const FwdSplit &, int, int64_t);
+template size_t forward_partial_bytes<double>(const FwdSplit &, int, int64_t);
+template size_t adjoint_partial_bytes<float>(const AdjSplit &, int, int);
+template size_t adjoint_partial_bytes<double>(const AdjSplit &, int, int);
+
+template int launch_forward<float, float, float>(const ModelH &, const GridH &, int64_t,
+                                                 const Geometry<float> &, const FwdSplit &,
+                                                 const float *, float *, float *, cudaStream_t);
+template int launch_forward<float, double, float>(const ModelH &, const GridH &, int64_t,
+                                                  const Geometry<float> &, const FwdSplit &,
+                                                  const double *, float *, float *, cudaStream_t);
+template int launch_forward<double, double, double>(const ModelH &, const GridH &, int64_t,
+                                                    const Geometry<double> &, const FwdSplit &,
+                                                    const double *, double *, double *,
+                                                    cudaStream_t);
+template int launch_adjoint<float, float>(const ModelH &, const GridH &, int64_t,
+                                          const Geometry<float> &, const AdjSplit &, const float *,
+                                          float *, float *, const double *, const double *,
+                                          double *, cudaStream_t);
+template int launch_adjoint<float, double>(const ModelH &, const GridH &, int64_t,
+                                           const Geometry<float> &, const AdjSplit &,
+                                           const float *, float *, double *, const double *,
+                                           const double *, double *, cudaStream_t);
+template int launch_adjoint<double, double>(const ModelH &, const GridH &, int64_t,
+                                            const Geometry<double> &, const AdjSplit &,
+                                            const double *, double *, double *, const double *,
+                                            const double *, double *, cudaStream_t);
+template int launch_dbeta<float>(const ModelH &, const GridH &, int64_t, const Geometry<float> &,
+                                 const AdjSplit &, const float *, const float *, double *,
+                                 double *, cudaStream_t);
+template int launch_dbeta<double>(const ModelH &, const GridH &, int64_t,
+                                  const Geometry<double> &, const AdjSplit &, const double *,
+                                  const double *, double *, double *, cudaStream_t);
+
+}  // namespace mpi

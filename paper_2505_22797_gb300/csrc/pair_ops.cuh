@@ -1,0 +1,82 @@
+// Internal interface of the pair kernels (forward A, adjoint A^T, d/dbeta).
+#pragma once
+
+#include "common.cuh"
+
+namespace mpi {
+
+struct ModelH {
+    double beta;
+    double G[4];
+    int n_ch;
+    double p[4];
+};
+struct GridH {
+    int nx, ny;
+    double x0, y0, dx, dy;
+};
+
+// Prepared geometry of one frame (device scratch, filled by prepare_geometry):
+//   rw[t]   = (B r_t, B v_t)            B = beta G, one float4/double4 per sample
+//   xcol[i] = B (x0 + (i+1/2)dx, 0)     per column
+//   yrow[j] = B (0, y0 + (j+1/2)dy)     per row
+// so beta G (x_ij - r_t) = xcol[i] + yrow[j] - B r_t.  For a diagonal G the
+// second component of xcol and the first of yrow are exactly 0.
+template <typename R>
+struct Geometry {
+    V4<R> *rw;
+    V2<R> *xcol;
+    V2<R> *yrow;
+};
+
+template <typename R>
+size_t geometry_bytes(int64_t T, int nx, int ny);
+template <typename R>
+Geometry<R> geometry_carve(void *base, int64_t T, int nx, int ny);
+
+template <typename R>
+int prepare_geometry(const ModelH &m, const GridH &g, int64_t T, const void *r, const void *v,
+                     const Geometry<R> &geo, cudaStream_t st);
+
+// Work decomposition of one operator application on one frame.
+struct FwdSplit {
+    int n_tiles, n_chunks, chunk_rows;
+};
+struct AdjSplit {
+    int tiles_x, tiles_y, n_chunks, chunk_len;
+};
+FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_items);
+AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items);
+int default_target_items();
+
+// Partial-sum scratch sizes (bytes).
+template <typename R>
+size_t forward_partial_bytes(const FwdSplit &sp, int n_ch, int64_t T);
+template <typename R>
+size_t adjoint_partial_bytes(const AdjSplit &sp, int nx, int ny);
+size_t dbeta_partial_bytes(const AdjSplit &sp);
+
+// One application of A: c (R or double, [ny][nx]) -> s_out ([n_ch][T]); the
+// output type is OUT (float or double).  `part` is forward_partial_bytes of
+// scratch.  Deterministic.
+template <typename R, typename CIN, typename OUT>
+int launch_forward(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo,
+                   const FwdSplit &sp, const CIN *c, R *part, OUT *s_out, cudaStream_t st);
+
+// One application of A^T: s ([n_ch][T], type R) -> out ([ny][nx], OUT).
+// If cg_p != nullptr the epilogue instead writes out = A^T s + nu * cg_p
+// (OUT must be double) and per-block partial sums of <cg_p, out> into
+// dot_part (see adjoint_dot_blocks).
+template <typename R, typename OUT>
+int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo,
+                   const AdjSplit &sp, const R *s, R *part, OUT *out, const double *cg_p,
+                   const double *nu_dev, double *dot_part, cudaStream_t st);
+int adjoint_dot_blocks(int nx, int ny);
+
+// d/dbeta <g, A(c; beta)>: c [ny][nx] (R), g [n_ch][T] (R) -> *out_dev (FP64).
+template <typename R>
+int launch_dbeta(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo,
+                 const AdjSplit &sp, const R *c, const R *gs, double *part, double *out_dev,
+                 cudaStream_t st);
+
+}  // namespace mpi
