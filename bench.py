@@ -1,0 +1,399 @@
+"""Benchmark of the GB300 MPI reconstruction path.
+
+One step = one full ZeroShot-PnP reconstruction (Algorithm 1) of the
+128 x 128 spiral workload (T = 65536 samples, 2 channels, 100 PnP iterations
+of 20 CG steps, 5x5 Gaussian denoiser, 5th-percentile trimming) with the
+forward operator A in FP32 and FP64 CG vectors/inner products.  Every step
+applies A and A^T 4201 times; the metric counts (voxel, sample) pairs per
+second over the whole reconstruction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank reconstructs its own copy of the workload on its
+own GPU (independent problems: weak scaling, no data-path collective); rank 0
+prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic per-pair operation counts of the closed-form (far-field) branch:
+# (FP32 operations, XU transcendental operations).  Forward: 2 for the
+# squared distance, 10 for the Langevin scalars a and d from rsqrt/exp2/rcp,
+# 6 to accumulate c a and c d (y.W) y.  Adjoint: 2 + 10 + 4 (quadratic form
+# and accumulation).
+ALG_OPS = {"k_forward": (18, 3), "k_adjoint": (16, 3)}
+
+METRIC = "A/Aᵀ Gvoxel·samples/s and PnP recon/s, FP32 batched vs FP64 plain, ≤1e-5 err"
+UNIT = "Gvoxel·samples/s"
+WORKLOAD = "c2"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _config_desc(cfg, extra=None):
+    g = cfg["grid"]
+    d = {"workload": f"{g['nx']}x{g['ny']} voxels, 24x24 mm, Archimedean spiral (32 turns), "
+                     f"T={cfg['r'].shape[0]} samples, 2 channels, {cfg['n_it']} PnP iterations x "
+                     f"{cfg['n_cg']} CG steps, 5x5 Gaussian denoiser, 5th-percentile trimming",
+         "grid": [g["nx"], g["ny"]], "samples": int(cfg["r"].shape[0]), "pnp_iterations": cfg["n_it"],
+         "cg_steps": cfg["n_cg"], "operator_applications_per_step": 2 * cfg["n_it"] * (cfg["n_cg"] + 1) + 1,
+         "l2": "256 MiB buffer written between timed steps (inputs ~1.5 MB fit in L2)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 CPU oracle.
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_2505_22797_gb300 import synthetic as syn
+    cfg = syn.config(WORKLOAD)
+    m, g = cfg["model"], cfg["grid"]
+    T_sub = 32768
+    r, v = cfg["r"][:T_sub], cfg["v"][:T_sub]
+    c = cfg["c"]
+    s = np.random.default_rng(1).normal(size=(2, T_sub))
+    pairs = 2 * g["nx"] * g["ny"] * T_sub
+    oracle.build()
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.forward(m, g, r, v, c)
+        oracle.adjoint(m, g, r, v, s)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = pairs * len(times) / tot / 1e9
+    sample = (f"one A and one A^T application of the 128x128 workload on its first {T_sub} "
+              f"samples ({pairs:.3e} pairs) per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config_desc(cfg, {"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm.
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mpi_bench_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.fh.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[4:8]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _lib_digest():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2505_22797_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was captured on the current sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    ent = d.get(kernel)
+    if not ent or ent.get("source_digest") != _lib_digest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2505_22797_gb300 import api, build
+    from paper_2505_22797_gb300 import synthetic as syn
+    build.build()
+    api.load()
+
+    dev = torch.device("cuda", local)
+    cfg = syn.config(WORKLOAD)
+    m, g = cfg["model"], cfg["grid"]
+    N, T = g["nx"] * g["ny"], cfg["r"].shape[0]
+    n_it, n_cg = cfg["n_it"], cfg["n_cg"]
+    f32 = torch.float32
+    r = torch.as_tensor(cfg["r"], dtype=f32, device=dev)
+    v = torch.as_tensor(cfg["v"], dtype=f32, device=dev)
+    c = torch.as_tensor(cfg["c"], dtype=f32, device=dev)
+    s_clean = api.mpi_forward(m, g, r, v, c)
+    s_np = syn.add_noise(s_clean.cpu().numpy().astype(np.float64), cfg["noise_frac"], cfg["noise_seed"])
+    s = torch.as_tensor(s_np, dtype=f32, device=dev)
+    # nu0 = 1e-3 ||A||_F^2 / N with ||A||_F^2 from 4 Rademacher probes (E ||A z||^2).
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    fro = 0.0
+    for _ in range(4):
+        z = (torch.randint(0, 2, (g["ny"], g["nx"]), generator=gen) * 2 - 1).to(dev, f32)
+        fro += float(torch.sum(api.mpi_forward(m, g, r, v, z).double() ** 2)) / 4
+    nu0 = 1e-3 * fro / N
+    rho = torch.empty((g["ny"], g["nx"]), dtype=f32, device=dev)
+    apps = 2 * n_it * (n_cg + 1) + 1
+    pairs_step = apps * N * T
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        api.mpi_pnp_solve(m, g, r, v, s, n_it, n_cg, nu0, clip_pct=cfg["clip_pct"], rho_out=rho)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # --- timed region (device time per step, L2 flushed between steps) ------
+    stream = torch.cuda.current_stream()
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    gpu_id = f"GPU-{uuid}" if uuid is not None else str(local)
+    launches0 = api.mpi_kernel_launches()
+    api.mpi_profile_enable(True)
+    step_ms = []
+    with ClockSampler(gpu_id) as clocks:
+        barrier()
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        barrier()
+    launches = api.mpi_kernel_launches() - launches0
+    prof = {k: api.mpi_profile_read(k) for k in (api.PROF_FORWARD, api.PROF_ADJOINT)}
+    api.mpi_profile_enable(False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = pairs_step * args.steps * world / (total_ms * 1e-3) / 1e9
+    recon_per_s = args.steps * world / (total_ms * 1e-3)
+
+    # --- end to end through the public API, host buffers ------------------------
+    h_r = torch.as_tensor(cfg["r"], dtype=f32).pin_memory()
+    h_v = torch.as_tensor(cfg["v"], dtype=f32).pin_memory()
+    h_s = s.cpu().pin_memory()
+    h_rho = torch.empty((g["ny"], g["nx"]), dtype=f32).pin_memory()
+    d_r, d_v, d_s = torch.empty_like(r), torch.empty_like(v), torch.empty_like(s)
+    e2e_ms = []
+    barrier()
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_r.copy_(h_r, non_blocking=True)
+        d_v.copy_(h_v, non_blocking=True)
+        d_s.copy_(h_s, non_blocking=True)
+        api.mpi_pnp_solve(m, g, d_r, d_v, d_s, n_it, n_cg, nu0, clip_pct=cfg["clip_pct"], rho_out=rho)
+        h_rho.copy_(rho, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    barrier()
+    e2e_tot = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = pairs_step * len(e2e_ms) * world / (e2e_tot * 1e-3) / 1e9
+    h2d = (h_r.numel() + h_v.numel() + h_s.numel()) * 4
+    d2h = h_rho.numel() * 4
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # --- roofline of the dominant kernel ----------------------------------------
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    clk = clocks.summary()
+    sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    (nf, fms), (na, ams) = prof[api.PROF_FORWARD], prof[api.PROF_ADJOINT]
+    dom, n_l, ms_l = ("k_forward", nf, fms) if fms >= ams else ("k_adjoint", na, ams)
+    # Algorithmic instructions per pair of the closed-form branch (FP32 ops,
+    # XU ops): every one occupies an issue slot (128 thread-instructions per
+    # SM per cycle), FP32 ops the FP32 pipe (128 lanes), XU ops the XU pipe
+    # (32 results per SM per cycle on GB300, inferred from ncu's pct-of-peak).
+    n_fp32, n_xu = ALG_OPS[dom]
+    per_clk = min(128.0 / (n_fp32 + n_xu), 128.0 / n_fp32, 32.0 / n_xu)
+    peak_gpair = sm_count * sm_max * 1e6 * per_clk / 1e9
+    achieved = (N * T) / (ms_l / n_l * 1e-3) / 1e9 if n_l else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gpair, "unit": "Gpair/s",
+                "frac": achieved / peak_gpair if achieved else None, "traffic": _traffic(dom),
+                "kernel": dom, "launches": n_l, "avg_launch_ms": ms_l / n_l if n_l else None,
+                "peak_basis": (f"issue bound: {sm_count} SMs x {sm_max:.0f} MHz x 128 thread-instructions"
+                               f"/clk / ({n_fp32} FP32 + {n_xu} XU algorithmic ops per pair)"),
+                "other": {"k_forward_avg_ms": fms / nf if nf else None,
+                          "k_adjoint_avg_ms": ams / na if na else None,
+                          "share_of_step": (fms + ams) / total_ms if total_ms else None}}
+
+    # --- FP64 plain form (one A and one A^T application) -----------------------
+    f64 = torch.float64
+    r64, v64, c64 = r.double(), v.double(), c.double()
+    s64 = api.mpi_forward(m, g, r64, v64, c64)
+    api.mpi_adjoint(m, g, r64, v64, s64)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    api.mpi_forward(m, g, r64, v64, c64, s=s64)
+    api.mpi_adjoint(m, g, r64, v64, s64)
+    e1.record(stream)
+    e1.synchronize()
+    f64_ms = e0.elapsed_time(e1)
+    f64_rate = 2 * N * T / (f64_ms * 1e-3) / 1e9
+    fp64_plain = {"gpair_per_s": f64_rate, "recon_s_extrapolated": pairs_step / (f64_rate * 1e9),
+                  "note": "one FP64 A and one FP64 A^T application, extrapolated to the "
+                          f"{apps} applications of a reconstruction"}
+
+    # --- CPU baseline: the oracle on a bounded sample -----------------------
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle
+        oracle.build()
+        T_sub = T
+        rr_, vv_ = cfg["r"][:T_sub], cfg["v"][:T_sub]
+        ss_ = np.random.default_rng(1).normal(size=(2, T_sub))
+        t0 = time.perf_counter()
+        oracle.forward(m, g, rr_, vv_, cfg["c"])
+        oracle.adjoint(m, g, rr_, vv_, ss_)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 2 * N * T_sub / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": f"one A and one A^T application of the workload ({T_sub} samples, "
+                         f"{2 * N * T_sub:.3e} pairs, {dt:.1f} s)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config_desc(cfg, {"precision": "FP32 operator, FP64 CG vectors and inner products",
+                                         "nu0": nu0}),
+            "recon_per_s": recon_per_s,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": len(e2e_ms),
+                    "recon_per_s": len(e2e_ms) * world / (e2e_tot * 1e-3)},
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "fp64_plain": fp64_plain, "clocks": clk, "impl": "ours"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

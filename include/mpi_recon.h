@@ -22,7 +22,7 @@
  * Model (Sec. 2 of the paper)
  * ---------------------------
  *  Voxel (i, j) has centre x_ij = (x0 + (i+1/2) dx, y0 + (j+1/2) dy) and
- *  concentration c[j][i].  The field-free point moves along r(t), t = 0..T-1
+ *  concentration c[j][i].  Grids need nx, ny >= 1.  The field-free point moves along r(t), t = 0..T-1
  *  (r[t][2], velocity v[t][2] = dr/dt per sample).  The applied field is
  *  H(x,t) = G (x - r(t)) (Sec. 2, FFP configuration).  With
  *  beta = 1/(mu0 H_sat) (Eq. hsat) the transfer-function-corrected signal on
@@ -88,8 +88,7 @@ typedef struct {
 /* Forward operator A (Eq. core:formula):  s[k][t] = sum_ij c[j][i] p_k^T
  * beta K(beta G(x_ij - r_t)) G v_t.  c is [ny][nx], s is [n_ch][T].  The sum
  * over voxels is a direct (exact, untruncated) sum, reduced deterministically:
- * the same inputs give bit-identical outputs.  T == 0 is a no-op; a grid with
- * no voxels writes zeros. */
+ * the same inputs give bit-identical outputs.  T == 0 is a no-op. */
 int mpi_forward(const mpi_model *model, const mpi_grid_desc *grid,
                 const mpi_traj *traj, mpi_dtype dtype, const void *c, void *s,
                 void *stream);
@@ -142,8 +141,11 @@ typedef struct {
  * Ahat = 0, with M the cosine-interpolation measurement operator above and Lap
  * the 5-point Laplacian with replicated boundary on each of the 4 components.
  * s is [2][T]; outputs Ahat [4][ny][nx] and trace [ny][nx] = Ahat_00 + Ahat_11.
- * If n_iter_out (HOST) is not NULL the call synchronises the stream and stores
- * the number of CG steps taken. */
+ * The operator runs in the call's dtype; CG vectors and inner products are
+ * FP64.  With rel_tol > 0 the host polls the device-side stop flag every 16
+ * CG steps (a stream synchronisation); the result is the same as stopping at
+ * the first step that meets the tolerance.  If n_iter_out (HOST) is not NULL
+ * the call synchronises the stream and stores the number of CG updates. */
 int mpi_grid(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
              const void *s, const mpi_grid_opts *opts, void *Ahat, void *trace,
              int *n_iter_out, void *stream);
@@ -198,6 +200,19 @@ const char *mpi_status_string(int status);
 const char *mpi_last_error_message(void);
 /* Library version as 10000*major + 100*minor + patch. */
 int mpi_version(void);
+/* Number of kernel launches the library has enqueued since it was loaded
+ * (all streams, all devices). */
+long long mpi_kernel_launches(void);
+
+/* Event timing of the operator kernels.  While enabled, every launch of the
+ * forward-operator kernel (class 0), the adjoint kernel (1), the d/dbeta
+ * kernel (2) and the convolution kernel (3) is bracketed by a CUDA event pair
+ * recorded on its launching stream.  mpi_profile_enable(1/0) turns it on/off
+ * and resets the totals; mpi_profile_read synchronises on the recorded events
+ * and returns the number of timed launches and their summed duration (ms) for
+ * one class. */
+int mpi_profile_enable(int enable);
+int mpi_profile_read(int kernel_class, long long *launches, double *total_ms);
 
 #ifdef __cplusplus
 }

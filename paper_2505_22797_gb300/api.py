@@ -84,6 +84,9 @@ _SIGS = {
                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mpi_pnp_solve": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
                      + [DENOISE_FN] + [ctypes.c_void_p] * 4,
+    "mpi_kernel_launches": [],
+    "mpi_profile_enable": [ctypes.c_int],
+    "mpi_profile_read": [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "mpi_status_string": [ctypes.c_int],
     "mpi_last_error_message": [],
     "mpi_version": [],
@@ -106,6 +109,7 @@ def load(path: str | None = None):
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
+        lib.mpi_kernel_launches.restype = ctypes.c_longlong
         lib.mpi_status_string.restype = ctypes.c_char_p
         lib.mpi_last_error_message.restype = ctypes.c_char_p
         _lib = lib
@@ -115,6 +119,25 @@ def load(path: str | None = None):
 def exported_symbols():
     lib = load()
     return {name for name in _SIGS if hasattr(lib, name)}
+
+
+PROF_FORWARD, PROF_ADJOINT, PROF_DBETA, PROF_CONV = 0, 1, 2, 3
+
+
+def mpi_kernel_launches() -> int:
+    return int(load().mpi_kernel_launches())
+
+
+def mpi_profile_enable(enable: bool = True):
+    _check(load().mpi_profile_enable(1 if enable else 0))
+
+
+def mpi_profile_read(kernel_class: int):
+    """(launches, total_ms) of one operator-kernel class since enabling."""
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    _check(load().mpi_profile_read(int(kernel_class), ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
 
 
 def _check(status: int):

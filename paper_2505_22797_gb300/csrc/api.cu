@@ -1,9 +1,11 @@
 // C ABI entry points: argument validation, scratch sizing and dispatch of the
 // operator calls (forward A, adjoint A^T, d/dbeta).
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "pair_ops.cuh"
 
@@ -42,6 +44,72 @@ void Scratch::release()
 {
     if (base_) cudaFreeAsync(base_, stream_);
     base_ = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Launch counter and optional event timing of the operator kernels.
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct ProfRecord {
+    int cls;
+    cudaEvent_t ev[2];
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRecord> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_free;
+long long g_prof_n[kProfClasses] = {0, 0, 0, 0};
+double g_prof_ms[kProfClasses] = {0, 0, 0, 0};
+
+cudaEvent_t take_event()
+{
+    if (!g_prof_free.empty()) {
+        cudaEvent_t e = g_prof_free.back();
+        g_prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Resolve recorded event pairs into per-class totals (caller holds the lock).
+int drain_pending()
+{
+    for (const ProfRecord &r : g_prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.ev[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, r.ev[0], r.ev[1]) != cudaSuccess) {
+            set_error("profiling event query failed");
+            return MPI_ERR_CUDA;
+        }
+        g_prof_n[r.cls] += 1;
+        g_prof_ms[r.cls] += ms;
+        g_prof_free.push_back(r.ev[0]);
+        g_prof_free.push_back(r.ev[1]);
+    }
+    g_prof_pending.clear();
+    return MPI_OK;
+}
+}  // namespace
+
+ProfScope::ProfScope(int cls, cudaStream_t st) : cls_(cls), st_(st), on_(false)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    ev_[0] = take_event();
+    ev_[1] = take_event();
+    if (ev_[0] && ev_[1] && cudaEventRecord(ev_[0], st_) == cudaSuccess) on_ = true;
+}
+
+ProfScope::~ProfScope()
+{
+    if (!on_) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (cudaEventRecord(ev_[1], st_) == cudaSuccess) g_prof_pending.push_back({cls_, {ev_[0], ev_[1]}});
 }
 
 int device_sm_count()
@@ -237,6 +305,33 @@ const char *mpi_status_string(int status)
 }
 
 const char *mpi_last_error_message(void) { return last_error(); }
+
+long long mpi_kernel_launches(void) { return g_launches.load(); }
+
+int mpi_profile_enable(int enable)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    const int st = drain_pending();
+    for (int c = 0; c < kProfClasses; ++c) {
+        g_prof_n[c] = 0;
+        g_prof_ms[c] = 0.0;
+    }
+    g_prof_on = enable != 0;
+    return st;
+}
+
+int mpi_profile_read(int kernel_class, long long *launches, double *total_ms)
+{
+    if (kernel_class < 0 || kernel_class >= kProfClasses || !launches || !total_ms) {
+        set_error("invalid profile query");
+        return MPI_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    MPI_TRY(drain_pending());
+    *launches = g_prof_n[kernel_class];
+    *total_ms = g_prof_ms[kernel_class];
+    return MPI_OK;
+}
 
 int mpi_version(void) { return 100; }
 

@@ -33,7 +33,30 @@ const char *last_error();
         if (st_ != MPI_OK) return st_;       \
     } while (0)
 
-#define MPI_CHECK_LAUNCH() MPI_TRY_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by MPI_CHECK_LAUNCH(), which
+// also counts it (mpi_kernel_launches()).
+void note_launch();
+#define MPI_CHECK_LAUNCH()                          \
+    do {                                            \
+        ::mpi::note_launch();                       \
+        MPI_TRY_CUDA(cudaGetLastError());           \
+    } while (0)
+
+// Optional event timing of the operator kernels (mpi_profile_enable): when
+// enabled, a ProfScope records a CUDA event pair around its launch on the
+// launching stream.
+enum ProfClass { kProfForward = 0, kProfAdjoint = 1, kProfDbeta = 2, kProfConv = 3, kProfClasses = 4 };
+class ProfScope {
+  public:
+    ProfScope(int cls, cudaStream_t st);
+    ~ProfScope();
+
+  private:
+    int cls_;
+    cudaStream_t st_;
+    cudaEvent_t ev_[2];
+    bool on_;
+};
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 

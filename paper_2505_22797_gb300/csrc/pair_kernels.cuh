@@ -40,6 +40,7 @@ struct PairFrame {
     int n_tiles;      // forward: sample tiles; adjoint: voxel tiles
     int tiles_x;      // adjoint only
     int chunk;        // forward: rows per chunk; adjoint: samples per chunk
+    int rows_staged;  // forward: rows per shared-memory block
     R p[4];
 };
 
@@ -63,7 +64,8 @@ __device__ __forceinline__ int find_frame(const PairBatch<R, MAXF> &B, int64_t i
 
 // ---------------------------------------------------------------------------
 // Forward A.  Work item = (tile of kFwdTile samples, chunk of rows).  Each
-// thread owns kFwdS samples and sums over the chunk's voxels row by row:
+// thread owns kFwdS samples and sums over the chunk's voxels row by row (rows
+// pass through shared memory rows_staged at a time):
 //   O(t) = sum_x c_x [a W + d (y.W) y] = Sa W + V,   W = beta G v,
 // with the row structure used twice: y_y (diagonal G) is constant along a row,
 // so V_y = y_y sum_row f; and rows far from every sample of the warp skip the
@@ -83,15 +85,12 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
     const int j0 = chunk * F.chunk;
     const int nr = min(F.chunk, F.ny - j0);
 
+    const int RB = F.rows_staged;
     V2<R> *s_x = reinterpret_cast<V2<R> *>(smem_raw);
     V2<R> *s_y = s_x + nx;
-    R *s_c = reinterpret_cast<R *>(s_y + F.chunk);
+    R *s_c = reinterpret_cast<R *>(s_y + RB);
     const CIN *cin = reinterpret_cast<const CIN *>(F.in);
-    for (int k = threadIdx.x; k < nr * nx; k += kFwdThreads)
-        s_c[k] = R(cin[(int64_t)j0 * nx + k]);
     for (int k = threadIdx.x; k < nx; k += kFwdThreads) s_x[k] = F.xcol[k];
-    for (int k = threadIdx.x; k < nr; k += kFwdThreads) s_y[k] = F.yrow[j0 + k];
-    __syncthreads();
 
     R Rx[kFwdS], Ry[kFwdS], Wx[kFwdS], Wy[kFwdS];
     int64_t t[kFwdS];
@@ -105,8 +104,18 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
 #pragma unroll
     for (int s = 0; s < kFwdS; ++s) Sa[s] = Vx[s] = Vy[s] = cSa[s] = cVx[s] = cVy[s] = R(0);
 
+    // Rows of the chunk are staged RB at a time.
 #pragma unroll 1
-    for (int r = 0; r < nr; ++r) {
+    for (int jb = j0; jb < j0 + nr; jb += RB) {
+        const int nrb = min(RB, j0 + nr - jb);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nrb * nx; k += kFwdThreads)
+            s_c[k] = R(cin[(int64_t)jb * nx + k]);
+        for (int k = threadIdx.x; k < nrb; k += kFwdThreads) s_y[k] = F.yrow[jb + k];
+        __syncthreads();
+
+#pragma unroll 1
+    for (int r = 0; r < nrb; ++r) {
         const V2<R> yr = s_y[r];
         const R *crow = s_c + r * nx;
         R oy[kFwdS], ox[kFwdS], yy2[kFwdS], yyW[kFwdS];
@@ -171,6 +180,7 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
                 kahan_add(Vy[s], cVy[s], fy[s]);
             }
         }
+    }
     }
 
     R *part = reinterpret_cast<R *>(F.part);

@@ -88,7 +88,10 @@ int prepare_geometry(const ModelH &m, const GridH &g, int64_t T, const void *r, 
 
 int default_target_items() { return 8 * 4 * device_sm_count(); }
 
-static constexpr size_t kFwdSmemBudget = 96 * 1024;
+// Bytes of concentration rows staged in shared memory at a time: small enough
+// that the block's shared memory never limits occupancy below the register
+// limit (~10 blocks of 128 threads per SM).
+static constexpr size_t kFwdRowBytes = 16 * 1024;
 
 FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_items)
 {
@@ -96,14 +99,9 @@ FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_ite
     sp.n_tiles = (int)std::max<int64_t>(1, (T + kFwdTile - 1) / kFwdTile);
     int want = (target_items + sp.n_tiles - 1) / sp.n_tiles;
     want = std::max(1, std::min(want, ny));
-    int rows = (ny + want - 1) / want;
-    // shared memory: xcol (nx) + yrow (rows) + c rows
-    const size_t fixed = size_t(2 * elem_bytes) * nx;
-    const size_t per_row = size_t(elem_bytes) * nx + 2 * elem_bytes;
-    const int max_rows = (int)std::max<size_t>(1, (kFwdSmemBudget - std::min(fixed, kFwdSmemBudget)) / per_row);
-    rows = std::max(1, std::min(rows, max_rows));
-    sp.chunk_rows = rows;
-    sp.n_chunks = (ny + rows - 1) / rows;
+    sp.chunk_rows = (ny + want - 1) / want;
+    sp.n_chunks = (ny + sp.chunk_rows - 1) / sp.chunk_rows;
+    sp.rows_staged = (int)std::max<size_t>(1, std::min<size_t>(sp.chunk_rows, kFwdRowBytes / (size_t(elem_bytes) * nx)));
     return sp;
 }
 
@@ -140,66 +138,57 @@ size_t dbeta_partial_bytes(const AdjSplit &sp)
 // ---------------------------------------------------------------------------
 // Reductions over chunks, in FP64 and in a fixed order.
 
-template <typename R, typename OUT>
-__global__ void k_reduce_chunks(const R *__restrict__ part, int n_chunks, int64_t len,
-                                OUT *__restrict__ out)
-{
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int c = 0; c < n_chunks; ++c) acc += double(part[(int64_t)c * len + e]);
-        out[e] = OUT(acc);
-    }
-}
-
+// Sum over chunks of the partial slices part[c][e], e < len.  A block owns 32
+// consecutive elements; warp w sums chunks w, w+8, ... (coalesced rows of
+// 128 B), and warp 0 adds the eight warp sums in order.  With CG set the
+// epilogue writes out = sum + nu * p (FP64) and the block's partial sum of
+// <p, out> to dot_part[blockIdx.x].
 constexpr int kRedThreads = 256;
-constexpr int kDotPerBlock = 2048;  // elements per block of the CG epilogue
+constexpr int kRedWarps = kRedThreads / 32;
 
-int adjoint_dot_blocks(int nx, int ny)
-{
-    return (int)(((int64_t)nx * ny + kDotPerBlock - 1) / kDotPerBlock);
-}
-
-// out = sum_chunks part + nu * p  (CG operator application), and per-block
-// partial sums of <p, out>.
-template <typename R>
+template <typename R, typename OUT, bool CG>
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_chunks_cg(const R *__restrict__ part, int n_chunks, int64_t len,
-                   const double *__restrict__ p, const double *__restrict__ nu_dev,
-                   double *__restrict__ out, double *__restrict__ dot_part)
+k_reduce_chunks(const R *__restrict__ part, int n_chunks, int64_t len, OUT *__restrict__ out,
+                const double *__restrict__ p, const double *__restrict__ nu_dev,
+                double *__restrict__ dot_part)
 {
-    __shared__ double sh[kRedThreads / 32];
-    const double nu = *nu_dev;
-    const int64_t e0 = (int64_t)blockIdx.x * kDotPerBlock;
-    const int64_t e1 = min(len, e0 + kDotPerBlock);
-    double dot = 0.0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
-        double acc = 0.0;
-        for (int c = 0; c < n_chunks; ++c) acc += double(part[(int64_t)c * len + e]);
-        const double pe = p[e];
-        acc += nu * pe;
-        out[e] = acc;
-        dot += pe * acc;
+    __shared__ double sh[kRedWarps][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (e < len)
+        for (int c = w; c < n_chunks; c += kRedWarps) acc += double(part[(int64_t)c * len + e]);
+    sh[w][lane] = acc;
+    __syncthreads();
+    if (w == 0) {
+        double tot = 0.0;
+#pragma unroll
+        for (int k = 0; k < kRedWarps; ++k) tot += sh[k][lane];
+        if constexpr (CG) {
+            const double pe = e < len ? p[e] : 0.0;
+            tot += *nu_dev * pe;
+            if (e < len) out[e] = OUT(tot);
+            const double dot = warp_sum(pe * tot);
+            if (lane == 0) dot_part[blockIdx.x] = dot;
+        } else {
+            if (e < len) out[e] = OUT(tot);
+        }
     }
-    dot = block_sum<double, kRedThreads>(dot, sh);
-    if (threadIdx.x == 0) dot_part[blockIdx.x] = dot;
 }
+
+int adjoint_dot_blocks(int nx, int ny) { return (int)(((int64_t)nx * ny + 31) / 32); }
+
+static unsigned reduce_blocks(int64_t len) { return (unsigned)std::max<int64_t>(1, (len + 31) / 32); }
 
 __global__ void k_sum_fixed(const double *__restrict__ part, int n, double scale,
                             double *__restrict__ out)
 {
-    __shared__ double sh[kRedThreads / 32];
+    __shared__ double sh[kRedWarps];
     double acc = 0.0;
     // fixed assignment of parts to threads, fixed tree: deterministic
     for (int k = threadIdx.x; k < n; k += kRedThreads) acc += part[k];
     acc = block_sum<double, kRedThreads>(acc, sh);
     if (threadIdx.x == 0) *out = acc * scale;
-}
-
-static int reduce_grid(int64_t len)
-{
-    return (int)std::max<int64_t>(1, std::min<int64_t>((len + kRedThreads - 1) / kRedThreads,
-                                                       (int64_t)device_sm_count() * 8));
 }
 
 // ---------------------------------------------------------------------------
@@ -243,18 +232,23 @@ int launch_forward(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
     B.f[0].part = part;
     B.f[0].n_tiles = sp.n_tiles;
     B.f[0].chunk = sp.chunk_rows;
-    const size_t smem = sizeof(V2<R>) * (g.nx + sp.chunk_rows) + sizeof(R) * size_t(sp.chunk_rows) * g.nx;
+    B.f[0].rows_staged = sp.rows_staged;
+    const size_t smem = sizeof(V2<R>) * (g.nx + sp.rows_staged) + sizeof(R) * size_t(sp.rows_staged) * g.nx;
     const int64_t items = (int64_t)sp.n_tiles * sp.n_chunks;
-    if (is_diag(m)) {
-        MPI_TRY(set_smem(k_forward<R, CIN, true, 1>, smem));
-        k_forward<R, CIN, true, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
-    } else {
-        MPI_TRY(set_smem(k_forward<R, CIN, false, 1>, smem));
-        k_forward<R, CIN, false, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
+    {
+        ProfScope prof(kProfForward, st);
+        if (is_diag(m)) {
+            MPI_TRY(set_smem(k_forward<R, CIN, true, 1>, smem));
+            k_forward<R, CIN, true, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
+        } else {
+            MPI_TRY(set_smem(k_forward<R, CIN, false, 1>, smem));
+            k_forward<R, CIN, false, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
+        }
+        MPI_CHECK_LAUNCH();
     }
-    MPI_CHECK_LAUNCH();
     const int64_t len = (int64_t)m.n_ch * T;
-    k_reduce_chunks<R, OUT><<<reduce_grid(len), kRedThreads, 0, st>>>(part, sp.n_chunks, len, s_out);
+    k_reduce_chunks<R, OUT, false><<<reduce_blocks(len), kRedThreads, 0, st>>>(
+        part, sp.n_chunks, len, s_out, nullptr, nullptr, nullptr);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
@@ -275,6 +269,7 @@ int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
         B.f[0].tiles_x = sp.tiles_x;
         B.f[0].chunk = sp.chunk_len;
         const int64_t items = (int64_t)sp.tiles_x * sp.tiles_y * sp.n_chunks;
+        ProfScope prof(kProfAdjoint, st);
         if (is_diag(m))
             k_adjoint<R, true, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
         else
@@ -286,14 +281,15 @@ int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
     const int nch = T > 0 ? sp.n_chunks : 1;
     if (cg_p) {
         if constexpr (sizeof(OUT) == sizeof(double)) {
-            k_reduce_chunks_cg<R><<<adjoint_dot_blocks(g.nx, g.ny), kRedThreads, 0, st>>>(
-                part, nch, N, cg_p, nu_dev, reinterpret_cast<double *>(out), dot_part);
+            k_reduce_chunks<R, double, true><<<reduce_blocks(N), kRedThreads, 0, st>>>(
+                part, nch, N, reinterpret_cast<double *>(out), cg_p, nu_dev, dot_part);
         } else {
             set_error("internal: CG epilogue needs FP64 output");
             return MPI_ERR_INVALID;
         }
     } else {
-        k_reduce_chunks<R, OUT><<<reduce_grid(N), kRedThreads, 0, st>>>(part, nch, N, out);
+        k_reduce_chunks<R, OUT, false><<<reduce_blocks(N), kRedThreads, 0, st>>>(
+            part, nch, N, out, nullptr, nullptr, nullptr);
     }
     MPI_CHECK_LAUNCH();
     return MPI_OK;
@@ -318,11 +314,14 @@ int launch_dbeta(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &
     B.f[0].tiles_x = sp.tiles_x;
     B.f[0].chunk = sp.chunk_len;
     const int64_t items = (int64_t)sp.tiles_x * sp.tiles_y * sp.n_chunks;
-    if (is_diag(m))
-        k_adjoint<R, true, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
-    else
-        k_adjoint<R, false, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
-    MPI_CHECK_LAUNCH();
+    {
+        ProfScope prof(kProfDbeta, st);
+        if (is_diag(m))
+            k_adjoint<R, true, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+        else
+            k_adjoint<R, false, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+        MPI_CHECK_LAUNCH();
+    }
     // The kernel sums u . (beta D) with W = beta G v; divide by beta.
     k_sum_fixed<<<1, kRedThreads, 0, st>>>(part, (int)items, 1.0 / m.beta, out_dev);
     MPI_CHECK_LAUNCH();

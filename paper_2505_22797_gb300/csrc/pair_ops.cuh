@@ -40,7 +40,7 @@ int prepare_geometry(const ModelH &m, const GridH &g, int64_t T, const void *r, 
 
 // Work decomposition of one operator application on one frame.
 struct FwdSplit {
-    int n_tiles, n_chunks, chunk_rows;
+    int n_tiles, n_chunks, chunk_rows, rows_staged;
 };
 struct AdjSplit {
     int tiles_x, tiles_y, n_chunks, chunk_len;
@@ -65,8 +65,8 @@ int launch_forward(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
 
 // One application of A^T: s ([n_ch][T], type R) -> out ([ny][nx], OUT).
 // If cg_p != nullptr the epilogue instead writes out = A^T s + nu * cg_p
-// (OUT must be double) and per-block partial sums of <cg_p, out> into
-// dot_part (see adjoint_dot_blocks).
+// (OUT must be double) and partial sums of <cg_p, out> into dot_part
+// (adjoint_dot_blocks(nx, ny) of them).
 template <typename R, typename OUT>
 int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo,
                    const AdjSplit &sp, const R *s, R *part, OUT *out, const double *cg_p,

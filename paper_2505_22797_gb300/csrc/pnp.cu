@@ -1,0 +1,586 @@
+// ZeroShot-PnP deconvolution (Algorithm 1) on the GPU, with the forward
+// operator A or the trace-kernel convolution C as the data-fidelity operator:
+// CG vector kernels with deterministic FP64 inner products, the percentile
+// trimming and noise estimate (one single-block kernel), the built-in 5-tap
+// Gaussian denoiser, and the mpi_pnp_solve / mpi_conv /
+// mpi_denoise_gaussian5 entry points.  All PnP scalars (nu, lambda, sigma,
+// the CG alpha/beta) stay on the device, so a solve enqueues without any host
+// synchronisation.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "conv_ops.cuh"
+#include "pnp_ops.cuh"
+
+namespace mpi {
+
+int check_model(const mpi_model *m);
+int check_grid(const mpi_grid_desc *g);
+int check_traj(const mpi_traj *t);
+int check_dtype(mpi_dtype d);
+ModelH to_host(const mpi_model *m);
+GridH to_host(const mpi_grid_desc *g);
+
+constexpr int kVecThreads = 256;
+constexpr int kVecPerBlock = 2048;  // equals the block size of the adjoint CG epilogue
+constexpr int kStatThreads = 1024;
+
+int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kVecPerBlock - 1) / kVecPerBlock); }
+
+// Sum of `n` partials in a fixed order, computed by the whole block and
+// returned to every thread (deterministic: fixed strides, fixed tree).
+template <int NT>
+__device__ double sum_parts(const double *__restrict__ part, int n, double *sh /* NT/32 + 1 */)
+{
+    double a = 0.0;
+    for (int k = threadIdx.x; k < n; k += NT) a += part[k];
+    a = block_sum<double, NT>(a, sh);
+    if (threadIdx.x == 0) sh[NT / 32] = a;
+    __syncthreads();
+    const double r = sh[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+template <typename R>
+__global__ void k_set_x(int64_t N, const R *__restrict__ src, double *__restrict__ x)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
+         e += (int64_t)gridDim.x * blockDim.x)
+        x[e] = src ? double(src[e]) : 0.0;
+}
+
+// r = b0 + nu x - q;  p = r;  partial sums of r.r;  clears the stop flag.
+__global__ void __launch_bounds__(kVecThreads)
+k_cg_init(int64_t N, const double *__restrict__ b0, const double *__restrict__ x,
+          const double *__restrict__ q, const double *__restrict__ nu_dev, double *__restrict__ r,
+          double *__restrict__ p, double *__restrict__ rr_part, int *__restrict__ done)
+{
+    __shared__ double sh[kVecThreads / 32 + 1];
+    const double nu = *nu_dev;
+    const int64_t e0 = (int64_t)blockIdx.x * kVecPerBlock, e1 = min(N, e0 + kVecPerBlock);
+    double acc = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kVecThreads) {
+        const double re = (b0[e] + nu * x[e]) - q[e];
+        r[e] = re;
+        p[e] = re;
+        acc += re * re;
+    }
+    acc = block_sum<double, kVecThreads>(acc, sh);
+    if (threadIdx.x == 0) {
+        rr_part[blockIdx.x] = acc;
+        if (blockIdx.x == 0) *done = 0;
+    }
+}
+
+// alpha = r.r / p.q;  x += alpha p;  r -= alpha q;  partial sums of the new r.r.
+// Once r.r or p.q is exactly 0 the solve has converged to round-off: the stop
+// flag is set and the remaining steps leave x, r and p untouched.  With a
+// threshold (Core Stage), the solve also stops once ||r|| <= *thresh, checked
+// before the update as the textbook loop does; `iters` counts the updates.
+__global__ void __launch_bounds__(kVecThreads)
+k_cg_step1(int64_t N, int nblk, double *__restrict__ x, double *__restrict__ r,
+           const double *__restrict__ p, const double *__restrict__ q,
+           const double *__restrict__ pq_part, int n_pq, const double *__restrict__ rr_in,
+           double *__restrict__ rr_out, int *__restrict__ done, const double *__restrict__ thresh,
+           int *__restrict__ iters)
+{
+    __shared__ double sh[kVecThreads / 32 + 1];
+    const double rr = sum_parts<kVecThreads>(rr_in, nblk, sh);
+    const double pq = sum_parts<kVecThreads>(pq_part, n_pq, sh);
+    const bool stop = (*done != 0) || rr == 0.0 || pq == 0.0 || (thresh && sqrt(rr) <= *thresh);
+    if (stop) {
+        if (threadIdx.x == 0) {
+            rr_out[blockIdx.x] = rr_in[blockIdx.x];
+            if (blockIdx.x == 0) *done = 1;
+        }
+        return;
+    }
+    if (iters && blockIdx.x == 0 && threadIdx.x == 0) *iters += 1;
+    const double alpha = rr / pq;
+    const int64_t e0 = (int64_t)blockIdx.x * kVecPerBlock, e1 = min(N, e0 + kVecPerBlock);
+    double acc = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kVecThreads) {
+        x[e] = x[e] + alpha * p[e];
+        const double re = r[e] - alpha * q[e];
+        r[e] = re;
+        acc += re * re;
+    }
+    acc = block_sum<double, kVecThreads>(acc, sh);
+    if (threadIdx.x == 0) rr_out[blockIdx.x] = acc;
+}
+
+// beta = r.r(new) / r.r(old);  p = r + beta p.
+__global__ void __launch_bounds__(kVecThreads)
+k_cg_step2(int64_t N, int nblk, const double *__restrict__ r, double *__restrict__ p,
+           const double *__restrict__ rr_old, const double *__restrict__ rr_new,
+           const int *__restrict__ done)
+{
+    __shared__ double sh[kVecThreads / 32 + 1];
+    if (*done) return;
+    const double ro = sum_parts<kVecThreads>(rr_old, nblk, sh);
+    const double rn = sum_parts<kVecThreads>(rr_new, nblk, sh);
+    const double beta = rn / ro;
+    const int64_t e0 = (int64_t)blockIdx.x * kVecPerBlock, e1 = min(N, e0 + kVecPerBlock);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kVecThreads) p[e] = r[e] + beta * p[e];
+}
+
+// q = y + nu v, partial sums of v.q  (epilogue for operators without a fused one).
+template <typename R>
+__global__ void __launch_bounds__(kVecThreads)
+k_axpy_dot(int64_t N, const R *__restrict__ y, const double *__restrict__ v,
+           const double *__restrict__ nu_dev, double *__restrict__ q, double *__restrict__ dot_part)
+{
+    __shared__ double sh[kVecThreads / 32 + 1];
+    const double nu = *nu_dev;
+    const int64_t e0 = (int64_t)blockIdx.x * kVecPerBlock, e1 = min(N, e0 + kVecPerBlock);
+    double acc = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kVecThreads) {
+        const double qe = double(y[e]) + nu * v[e];
+        q[e] = qe;
+        acc += v[e] * qe;
+    }
+    acc = block_sum<double, kVecThreads>(acc, sh);
+    if (threadIdx.x == 0) dot_part[blockIdx.x] = acc;
+}
+
+__global__ void k_init_scalars(double *scal, double nu0)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        scal[kScalNu] = nu0;
+        scal[kScalLambda] = 0.0;
+        scal[kScalSigma] = 0.0;
+        scal[kScalPct] = 0.0;
+    }
+}
+
+int cg_init_launch(int64_t N, const double *b0, const double *x, const double *q,
+                   const double *nu_dev, double *r, double *p, double *rr_part, int *done,
+                   cudaStream_t st)
+{
+    k_cg_init<<<vec_blocks(N), kVecThreads, 0, st>>>(N, b0, x, q, nu_dev, r, p, rr_part, done);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+int cg_step_launch(int64_t N, double *x, double *r, double *p, const double *q,
+                   const double *pq_part, int n_pq, const double *rr_in, double *rr_out, int *done,
+                   const double *thresh, int *iters, cudaStream_t st)
+{
+    const int nblk = vec_blocks(N);
+    k_cg_step1<<<nblk, kVecThreads, 0, st>>>(N, nblk, x, r, p, q, pq_part, n_pq, rr_in, rr_out,
+                                            done, thresh, iters);
+    MPI_CHECK_LAUNCH();
+    k_cg_step2<<<nblk, kVecThreads, 0, st>>>(N, nblk, r, p, rr_in, rr_out, done);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Percentile trimming and noise estimate (Sec. 3.3 and the noise estimator of
+// Algorithm 1) in one block: exact order statistics by an 8-pass radix select
+// on the order-preserving integer image of the FP64 values, then two passes
+// for the mean and the population variance.
+
+__device__ __forceinline__ uint64_t f64_key(double v)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_f64(uint64_t k)
+{
+    const uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+template <int NT>
+__device__ double block_select(const double *__restrict__ x, int64_t N, int64_t rank,
+                               unsigned *hist, unsigned long long *sh_u)
+{
+    uint64_t prefix = 0, mask = 0;
+    int64_t krem = rank;
+    const int lane = threadIdx.x & 31;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += NT) hist[b] = 0;
+        __syncthreads();
+        for (int64_t i0 = 0; i0 < N; i0 += NT) {
+            const int64_t i = i0 + threadIdx.x;
+            unsigned digit = 256;  // no bin
+            if (i < N) {
+                const uint64_t key = f64_key(x[i]);
+                if ((key & mask) == prefix) digit = (unsigned)((key >> shift) & 255u);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, digit);
+            if (digit < 256 && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t cum = 0;
+            unsigned d = 0;
+            for (; d < 255; ++d) {
+                if (cum + hist[d] > krem) break;
+                cum += hist[d];
+            }
+            krem -= cum;
+            sh_u[0] = prefix | ((uint64_t)d << shift);
+            sh_u[1] = (unsigned long long)krem;
+        }
+        __syncthreads();
+        prefix = sh_u[0];
+        krem = (int64_t)sh_u[1];
+        mask |= (uint64_t)255 << shift;
+        __syncthreads();
+    }
+    return key_f64(prefix);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kStatThreads)
+k_outer_stats(int64_t N, const double *__restrict__ x, int do_clip, double pct, int k, double nu0,
+              double *__restrict__ scal, const double *__restrict__ rr_part, int nblk,
+              double *__restrict__ info_row, R *__restrict__ rho1)
+{
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long sh_u[2];
+    __shared__ double sh[kStatThreads / 32 + 1];
+    double P = -INFINITY;
+    if (do_clip) {
+        const double h = double(N - 1) * pct / 100.0;
+        const int64_t lo = (int64_t)floor(h);
+        const int64_t hi = min(lo + 1, N - 1);
+        const double xlo = block_select<kStatThreads>(x, N, lo, hist, sh_u);
+        const double xhi = (hi == lo) ? xlo : block_select<kStatThreads>(x, N, hi, hist, sh_u);
+        P = xlo + (h - double(lo)) * (xhi - xlo);
+    }
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += kStatThreads) {
+        const double v = fmax(x[i], P);
+        rho1[i] = R(v);
+        s += v;
+    }
+    s = block_sum<double, kStatThreads>(s, sh);
+    if (threadIdx.x == 0) sh[kStatThreads / 32] = s;
+    __syncthreads();
+    const double mean = sh[kStatThreads / 32] / double(N);
+    __syncthreads();
+    double q = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += kStatThreads) {
+        const double dv = fmax(x[i], P) - mean;
+        q += dv * dv;
+    }
+    q = block_sum<double, kStatThreads>(q, sh);
+    if (threadIdx.x == 0) {
+        double rr = 0.0;
+        for (int b = 0; b < nblk; ++b) rr += rr_part[b];
+        const double sigma = sqrt(q / double(N));
+        if (k == 0) scal[kScalLambda] = nu0 * sigma * sigma;
+        if (sigma > 0.0) scal[kScalNu] = scal[kScalLambda] / (sigma * sigma);
+        scal[kScalSigma] = sigma;
+        scal[kScalPct] = P;
+        info_row[0] = sigma;
+        info_row[1] = scal[kScalNu];
+        info_row[2] = sqrt(rr);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Built-in denoiser: separable 5-tap Gaussian (sigma = 1 px), reflect
+// boundary (d c b a | a b c d), rows first then columns.
+
+__device__ __forceinline__ int reflect_index(int i, int n)
+{
+    const int p = 2 * n;
+    i %= p;
+    if (i < 0) i += p;
+    return i >= n ? p - 1 - i : i;
+}
+
+constexpr int kGx = 32, kGy = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(kGx *kGy)
+k_gauss5(const R *__restrict__ in, R *__restrict__ out, int nx, int ny, R w0, R w1, R w2)
+{
+    __shared__ R tmp[kGy + 4][kGx];
+    const R w[5] = {w2, w1, w0, w1, w2};
+    const int tx = threadIdx.x % kGx, ty = threadIdx.x / kGx;
+    const int i0 = blockIdx.x * kGx, j0 = blockIdx.y * kGy;
+    const int i = i0 + tx;
+    const int ic = min(i, nx - 1);
+    for (int rr = ty; rr < kGy + 4; rr += kGy) {
+        const int jr = reflect_index(j0 - 2 + rr, ny);
+        const R *row = in + (int64_t)jr * nx;
+        R acc = R(0);
+#pragma unroll
+        for (int m = -2; m <= 2; ++m) acc += w[m + 2] * row[reflect_index(ic + m, nx)];
+        tmp[rr][tx] = acc;
+    }
+    __syncthreads();
+    const int j = j0 + ty;
+    if (i < nx && j < ny) {
+        R acc = R(0);
+#pragma unroll
+        for (int m = -2; m <= 2; ++m) acc += w[m + 2] * tmp[reflect_index(j + m, ny) - (j0 - 2)][tx];
+        out[(int64_t)j * nx + i] = acc;
+    }
+}
+
+template <typename R>
+int launch_gauss5(const R *in, R *out, int nx, int ny, cudaStream_t st)
+{
+    double w[3];
+    double tot = 0.0;
+    for (int m = -2; m <= 2; ++m) tot += std::exp(-0.5 * m * m);
+    for (int m = 0; m <= 2; ++m) w[m] = std::exp(-0.5 * m * m) / tot;
+    dim3 grid((nx + kGx - 1) / kGx, (ny + kGy - 1) / kGy);
+    k_gauss5<R><<<grid, kGx * kGy, 0, st>>>(in, out, nx, ny, R(w[0]), R(w[1]), R(w[2]));
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The PnP solve.
+
+template <typename R>
+struct PnPState {
+    // operator
+    mpi_op op;
+    ModelH m;
+    GridH g;
+    int64_t T;
+    Geometry<R> geo;
+    FwdSplit fs;
+    AdjSplit as;
+    R *fwd_part = nullptr, *adj_part = nullptr, *sA = nullptr;
+    R *K = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;
+    // vectors
+    int64_t N;
+    int nblk;
+    int n_pq;  // number of partial sums of <p, q> the operator epilogue writes
+    double *b0, *x, *r, *p, *q, *pq_part, *rr_part[2], *scal, *info;
+    int *done;
+    R *rho1, *rho2;
+};
+
+// q = (O^T O + nu I) v and partial sums of <v, q>.
+template <typename R>
+static int apply_normal(PnPState<R> &S, const double *v, double *q, cudaStream_t st)
+{
+    if (S.op == MPI_OP_FORWARD) {
+        MPI_TRY((launch_forward<R, double, R>(S.m, S.g, S.T, S.geo, S.fs, v, S.fwd_part, S.sA, st)));
+        MPI_TRY((launch_adjoint<R, double>(S.m, S.g, S.T, S.geo, S.as, S.sA, S.adj_part, q, v,
+                                           S.scal + kScalNu, S.pq_part, st)));
+    } else {
+        MPI_TRY((launch_conv<R, double, R>(S.g, S.K, v, S.tmp1, st)));
+        MPI_TRY((launch_conv<R, R, R>(S.g, S.K, S.tmp1, S.tmp2, st)));
+        k_axpy_dot<R><<<S.nblk, kVecThreads, 0, st>>>(S.N, S.tmp2, v, S.scal + kScalNu, q, S.pq_part);
+        MPI_CHECK_LAUNCH();
+    }
+    return MPI_OK;
+}
+
+template <typename R>
+static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const void *data,
+                    const mpi_pnp_opts &o, mpi_denoise_fn den, void *user, void *rho_out,
+                    mpi_pnp_iter_info *info, cudaStream_t st)
+{
+    PnPState<R> S;
+    S.op = o.op;
+    S.m = m;
+    S.g = g;
+    S.T = (o.op == MPI_OP_FORWARD) ? tr->T : 0;
+    S.N = (int64_t)g.nx * g.ny;
+    S.nblk = vec_blocks(S.N);
+    S.n_pq = (o.op == MPI_OP_FORWARD) ? adjoint_dot_blocks(g.nx, g.ny) : S.nblk;
+    const int target = default_target_items();
+
+    Scratch scr(st);
+    size_t o_geo = 0, o_fp = 0, o_ap = 0, o_sA = 0, o_K = 0, o_t1 = 0, o_t2 = 0;
+    if (S.op == MPI_OP_FORWARD) {
+        S.fs = forward_split(S.T, g.nx, g.ny, sizeof(R), target);
+        S.as = adjoint_split(S.T, g.nx, g.ny, target);
+        o_geo = scr.reserve(geometry_bytes<R>(S.T, g.nx, g.ny));
+        o_fp = scr.reserve(forward_partial_bytes<R>(S.fs, m.n_ch, S.T));
+        o_ap = scr.reserve(adjoint_partial_bytes<R>(S.as, g.nx, g.ny));
+        o_sA = scr.reserve(sizeof(R) * size_t(m.n_ch) * size_t(std::max<int64_t>(S.T, 1)));
+    } else {
+        o_K = scr.reserve(conv_kernel_bytes(g.nx, g.ny, sizeof(R)));
+        o_t1 = scr.reserve(sizeof(R) * S.N);
+        o_t2 = scr.reserve(sizeof(R) * S.N);
+    }
+    const size_t vb = sizeof(double) * S.N;
+    const size_t o_b0 = scr.reserve(vb), o_x = scr.reserve(vb), o_r = scr.reserve(vb),
+                 o_p = scr.reserve(vb), o_q = scr.reserve(vb);
+    const size_t o_pq = scr.reserve(sizeof(double) * std::max(S.nblk, S.n_pq));
+    const size_t o_rr0 = scr.reserve(sizeof(double) * S.nblk), o_rr1 = scr.reserve(sizeof(double) * S.nblk);
+    const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 4);
+    const size_t o_info = scr.reserve(sizeof(double) * 3 * std::max(o.n_iter, 1));
+    const size_t o_r1 = scr.reserve(sizeof(R) * S.N), o_r2 = scr.reserve(sizeof(R) * S.N);
+    MPI_TRY(scr.allocate());
+
+    if (S.op == MPI_OP_FORWARD) {
+        S.geo = geometry_carve<R>(scr.at<char>(o_geo), S.T, g.nx, g.ny);
+        S.fwd_part = scr.at<R>(o_fp);
+        S.adj_part = scr.at<R>(o_ap);
+        S.sA = scr.at<R>(o_sA);
+        MPI_TRY(prepare_geometry<R>(m, g, S.T, tr->r, tr->v, S.geo, st));
+    } else {
+        MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &S.K, st));
+        S.tmp1 = scr.at<R>(o_t1);
+        S.tmp2 = scr.at<R>(o_t2);
+    }
+    S.b0 = scr.at<double>(o_b0);
+    S.x = scr.at<double>(o_x);
+    S.r = scr.at<double>(o_r);
+    S.p = scr.at<double>(o_p);
+    S.q = scr.at<double>(o_q);
+    S.pq_part = scr.at<double>(o_pq);
+    S.rr_part[0] = scr.at<double>(o_rr0);
+    S.rr_part[1] = scr.at<double>(o_rr1);
+    S.scal = scr.at<double>(o_sc);
+    S.done = reinterpret_cast<int *>(S.scal + 8);
+    S.info = scr.at<double>(o_info);
+    S.rho1 = scr.at<R>(o_r1);
+    S.rho2 = scr.at<R>(o_r2);
+
+    // b0 = O^T data
+    if (S.op == MPI_OP_FORWARD) {
+        MPI_TRY((launch_adjoint<R, double>(m, g, S.T, S.geo, S.as, static_cast<const R *>(data),
+                                           S.adj_part, S.b0, nullptr, nullptr, nullptr, st)));
+    } else {
+        MPI_TRY((launch_conv<R, R, double>(g, S.K, static_cast<const R *>(data), S.b0, st)));
+    }
+    k_init_scalars<<<1, 32, 0, st>>>(S.scal, o.nu0);
+    MPI_CHECK_LAUNCH();
+
+    const bool fault_cb = getenv("MPI_FAULT") && strcmp(getenv("MPI_FAULT"), "callback") == 0;
+    const int vgrid = (int)std::min<int64_t>((S.N + 255) / 256, 4096);
+    for (int k = 0; k < o.n_iter; ++k) {
+        k_set_x<R><<<vgrid, 256, 0, st>>>(S.N, k == 0 ? nullptr : S.rho2, S.x);
+        MPI_CHECK_LAUNCH();
+        MPI_TRY(apply_normal(S, S.x, S.q, st));
+        MPI_TRY(cg_init_launch(S.N, S.b0, S.x, S.q, S.scal + kScalNu, S.r, S.p, S.rr_part[0],
+                               S.done, st));
+        for (int i = 0; i < o.n_cg; ++i) {
+            MPI_TRY(apply_normal(S, S.p, S.q, st));
+            MPI_TRY(cg_step_launch(S.N, S.x, S.r, S.p, S.q, S.pq_part, S.n_pq, S.rr_part[i & 1],
+                                   S.rr_part[(i + 1) & 1], S.done, nullptr, nullptr, st));
+        }
+        k_outer_stats<R><<<1, kStatThreads, 0, st>>>(S.N, S.x, o.clip_pct >= 0.0 ? 1 : 0, o.clip_pct,
+                                                    k, o.nu0, S.scal, S.rr_part[o.n_cg & 1], S.nblk,
+                                                    S.info + 3 * k, S.rho1);
+        MPI_CHECK_LAUNCH();
+        R *dst = (k == o.n_iter - 1) ? static_cast<R *>(rho_out) : S.rho2;
+        const mpi_dtype dt = sizeof(R) == 4 ? MPI_F32 : MPI_F64;
+        int rc;
+        if (fault_cb) {
+            rc = 1;
+        } else if (den) {
+            rc = den(S.rho1, dst, g.nx, g.ny, dt, S.scal + kScalSigma, st, user);
+        } else {
+            rc = launch_gauss5<R>(S.rho1, dst, g.nx, g.ny, st);
+        }
+        if (rc != 0) {
+            if (den || fault_cb) {
+                set_error("denoiser callback returned %d at iteration %d", rc, k);
+                return MPI_ERR_CALLBACK;
+            }
+            return rc;
+        }
+    }
+    if (o.n_iter == 0) MPI_TRY_CUDA(cudaMemsetAsync(rho_out, 0, sizeof(R) * S.N, st));
+    if (info) {
+        std::vector<double> h(3 * std::max(o.n_iter, 1));
+        MPI_TRY_CUDA(cudaMemcpyAsync(h.data(), S.info, sizeof(double) * 3 * o.n_iter,
+                                     cudaMemcpyDeviceToHost, st));
+        MPI_TRY_CUDA(cudaStreamSynchronize(st));
+        for (int k = 0; k < o.n_iter; ++k) {
+            info[k].sigma = h[3 * k];
+            info[k].nu = h[3 * k + 1];
+            info[k].cg_resid = h[3 * k + 2];
+        }
+    }
+    return MPI_OK;
+}
+
+template <typename R>
+static int conv_impl(const ModelH &m, const GridH &g, const void *in, void *out, cudaStream_t st)
+{
+    Scratch scr(st);
+    const size_t o_K = scr.reserve(conv_kernel_bytes(g.nx, g.ny, sizeof(R)));
+    MPI_TRY(scr.allocate());
+    R *K = nullptr;
+    MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &K, st));
+    return launch_conv<R, R, R>(g, K, static_cast<const R *>(in), static_cast<R *>(out), st);
+}
+
+template int launch_gauss5<float>(const float *, float *, int, int, cudaStream_t);
+template int launch_gauss5<double>(const double *, double *, int, int, cudaStream_t);
+
+}  // namespace mpi
+
+using namespace mpi;
+
+extern "C" {
+
+int mpi_pnp_solve(const mpi_model *model, const mpi_grid_desc *grid, const mpi_traj *traj,
+                  mpi_dtype dtype, const void *data, const mpi_pnp_opts *opts,
+                  mpi_denoise_fn denoise, void *user, void *rho_out, mpi_pnp_iter_info *info,
+                  void *stream)
+{
+    MPI_TRY(check_model(model));
+    MPI_TRY(check_grid(grid));
+    MPI_TRY(check_dtype(dtype));
+    if (!opts) { set_error("opts is NULL"); return MPI_ERR_INVALID; }
+    if (opts->op != MPI_OP_FORWARD && opts->op != MPI_OP_CONV) {
+        set_error("unknown operator %d", (int)opts->op);
+        return MPI_ERR_INVALID;
+    }
+    if (opts->op == MPI_OP_FORWARD) MPI_TRY(check_traj(traj));
+    if (opts->n_iter < 0 || opts->n_cg < 0 || !(opts->nu0 >= 0.0) || !std::isfinite(opts->nu0) ||
+        !(opts->clip_pct <= 100.0) || std::isnan(opts->clip_pct)) {
+        set_error("invalid PnP options (n_iter %d, n_cg %d, nu0 %g, clip_pct %g)", opts->n_iter,
+                  opts->n_cg, opts->nu0, opts->clip_pct);
+        return MPI_ERR_INVALID;
+    }
+    if (!rho_out || (!data && !(opts->op == MPI_OP_FORWARD && traj->T == 0))) {
+        set_error("data or rho_out is NULL");
+        return MPI_ERR_INVALID;
+    }
+    const ModelH m = to_host(model);
+    const GridH g = to_host(grid);
+    return dtype == MPI_F32
+               ? pnp_impl<float>(m, g, traj, data, *opts, denoise, user, rho_out, info, as_stream(stream))
+               : pnp_impl<double>(m, g, traj, data, *opts, denoise, user, rho_out, info, as_stream(stream));
+}
+
+int mpi_conv(const mpi_model *model, const mpi_grid_desc *grid, mpi_dtype dtype, const void *in,
+             void *out, void *stream)
+{
+    MPI_TRY(check_model(model));
+    MPI_TRY(check_grid(grid));
+    MPI_TRY(check_dtype(dtype));
+    if (!in || !out || in == out) { set_error("in/out NULL or aliased"); return MPI_ERR_INVALID; }
+    const ModelH m = to_host(model);
+    const GridH g = to_host(grid);
+    return dtype == MPI_F32 ? conv_impl<float>(m, g, in, out, as_stream(stream))
+                            : conv_impl<double>(m, g, in, out, as_stream(stream));
+}
+
+int mpi_denoise_gaussian5(const void *in, void *out, int nx, int ny, mpi_dtype dtype,
+                          const double *sigma_dev, void *stream, void *user)
+{
+    (void)sigma_dev;
+    (void)user;
+    MPI_TRY(check_dtype(dtype));
+    if (nx < 1 || ny < 1 || !in || !out || in == out) {
+        set_error("invalid denoiser arguments");
+        return MPI_ERR_INVALID;
+    }
+    return dtype == MPI_F32
+               ? launch_gauss5<float>(static_cast<const float *>(in), static_cast<float *>(out), nx, ny, as_stream(stream))
+               : launch_gauss5<double>(static_cast<const double *>(in), static_cast<double *>(out), nx, ny, as_stream(stream));
+}
+
+}  // extern "C"

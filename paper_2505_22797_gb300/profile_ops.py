@@ -1,0 +1,75 @@
+"""Run single operator applications of a named workload, for profiling.
+
+    python -m paper_2505_22797_gb300.profile_ops --op forward --workload c2 --reps 3
+
+Builds the inputs of the workload (seeded synthetic), runs `--warmup`
+untimed applications and then `--reps` applications of the chosen operator
+(forward A, adjoint A^T, dbeta, conv) in the chosen precision, timing each
+with CUDA events on the current stream, and prints one line per operator.
+It is the small, self-contained command to put under a profiler.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import torch
+
+if __package__ in (None, ""):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+from paper_2505_22797_gb300 import api, build  # noqa: E402
+from paper_2505_22797_gb300 import synthetic as syn  # noqa: E402
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--op", choices=["forward", "adjoint", "dbeta", "conv", "all"], default="all")
+    ap.add_argument("--workload", default="c2", help="c1, c2, c2_partial, c4 or c5")
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args(argv)
+
+    build.build()
+    api.load()
+    cfg = syn.config(args.workload)
+    m, g = cfg["model"], cfg["grid"]
+    dt = torch.float32 if args.dtype == "f32" else torch.float64
+    r = torch.as_tensor(cfg["r"], dtype=dt, device="cuda")
+    v = torch.as_tensor(cfg["v"], dtype=dt, device="cuda")
+    c = torch.as_tensor(cfg["c"], dtype=dt, device="cuda")
+    s = api.mpi_forward(m, g, r, v, c)
+    out = torch.empty_like(c)
+    ops = {
+        "forward": lambda: api.mpi_forward(m, g, r, v, c, s=s),
+        "adjoint": lambda: api.mpi_adjoint(m, g, r, v, s, c_out=out),
+        "dbeta": lambda: api.mpi_dbeta(m, g, r, v, c, s),
+        "conv": lambda: api.mpi_conv(m, g, c, out=out),
+    }
+    names = list(ops) if args.op == "all" else [args.op]
+    pairs = g["nx"] * g["ny"] * r.shape[0]
+    stream = torch.cuda.current_stream()
+    for name in names:
+        fn = ops[name]
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        best = min(ms)
+        rate = "" if name == "conv" else f"  {pairs / best / 1e6:.1f} Gpair/s"
+        print(f"{args.workload} {args.dtype} {name}: best {best:.3f} ms of {args.reps}{rate}", flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

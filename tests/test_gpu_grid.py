@@ -1,0 +1,84 @@
+"""GPU parity of the Core Stage: cosine interpolation, its transpose and the
+CG solve of Eq. first:step, against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_22797_gb300 import api
+from paper_2505_22797_gb300 import synthetic as syn
+from tests.gpu_util import dev, host, rel_l2, rounded, tol
+
+pytestmark = pytest.mark.gpu
+DTYPES = [torch.float32, torch.float64]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("shape", [(1, 1, 7), (2, 3, 40), (17, 13, 700), (64, 64, 8192)])
+def test_interp_and_transpose(orc, dt, shape):
+    nx, ny, T = shape
+    g = syn.square_grid(nx, 24.0, ny)
+    rng = np.random.default_rng(nx * 7 + T)
+    r, v = syn.lissajous(T, 5, 4, amp=13.0)  # overshoots the node hull: clamping
+    r, v = rounded(r, dt), rounded(v, dt)
+    A = rounded(rng.normal(size=(4, ny, nx)), dt)
+    s = rounded(rng.normal(size=(2, T)), dt)
+    assert rel_l2(host(api.mpi_interp(g, dev(r, dt), dev(v, dt), dev(A, dt))),
+                  orc.interp(g, r, v, A)) <= tol(dt)
+    assert rel_l2(host(api.mpi_interp_adjoint(g, dev(r, dt), dev(v, dt), dev(s, dt))),
+                  orc.interp_T(g, r, v, s)) <= tol(dt)
+
+
+def test_interp_T_dense_cell():
+    """Thousands of samples in one cell (a trajectory that dwells): the
+    per-cell ordering takes the long-list path; result matches FP64 sums."""
+    dt = torch.float64
+    g = syn.square_grid(8, 8.0)
+    T = 5000
+    rng = np.random.default_rng(0)
+    r = 0.3 + 0.1 * rng.uniform(size=(T, 2))
+    v = rng.normal(size=(T, 2))
+    s = rng.normal(size=(2, T))
+    from oracle import oracle as orc
+    assert rel_l2(host(api.mpi_interp_adjoint(g, dev(r, dt), dev(v, dt), dev(s, dt))),
+                  orc.interp_T(g, r, v, s)) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_core_stage_fixed_iterations(orc, dt):
+    cfg = syn.small(20, 18, 2000, seed=5)
+    g, m = cfg["grid"], cfg["model"]
+    r, v, c = (rounded(cfg[k], dt) for k in ("r", "v", "c"))
+    s = rounded(orc.forward(m, g, r, v, c), dt)
+    gamma = 1e-4
+    want, want_u, hist = orc.core_stage(g, r, v, s, gamma, max_iter=30)
+    A, u, n = api.mpi_grid(g, dev(r, dt), dev(v, dt), dev(s, dt), gamma=gamma, max_iter=30,
+                           rel_tol=0.0, return_iters=True)
+    assert n == len(hist) - 1
+    assert rel_l2(host(A), want) <= tol(dt)
+    assert rel_l2(host(u), want_u) <= tol(dt)
+
+
+def test_core_stage_tolerance_fp64(orc):
+    """Paper parameters (gamma = 1e-7, rel. tol 1e-3): same stopping step as
+    the oracle's textbook loop, and the same result to within the problem's
+    own round-off sensitivity.  With gamma = 1e-7 the normal matrix is badly
+    conditioned, so CG amplifies rounding-order differences; the bound is
+    taken from the oracle itself: the spread of its result when the data are
+    perturbed by one unit in the last place, times 20 (and never below the
+    1e-12 FP64 bar)."""
+    dt = torch.float64
+    cfg = syn.config("c1")
+    g, m = cfg["grid"], cfg["model"]
+    r, v, c = cfg["r"], cfg["v"], cfg["c"]
+    s = orc.forward(m, g, r, v, c)
+    want, want_u, hist = orc.core_stage(g, r, v, s, 1e-7, max_iter=10000, rel_tol=1e-3)
+    ulp = np.random.default_rng(0).choice([-1.0, 1.0], size=s.shape) * np.spacing(np.abs(s))
+    _, pert_u, hist_p = orc.core_stage(g, r, v, s + ulp, 1e-7, max_iter=10000, rel_tol=1e-3)
+    assert len(hist_p) == len(hist)
+    bound = max(1e-12, 20 * rel_l2(pert_u, want_u))
+    A, u, n = api.mpi_grid(g, dev(r, dt), dev(v, dt), dev(s, dt), gamma=1e-7, max_iter=10000,
+                           rel_tol=1e-3, return_iters=True)
+    assert n == len(hist) - 1
+    err = rel_l2(host(u), want_u)
+    print(f"core stage gamma=1e-7: {n} CG steps, rel-L2 {err:.2e}, sensitivity bound {bound:.2e}")
+    assert err <= bound

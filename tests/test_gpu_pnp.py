@@ -1,0 +1,183 @@
+"""GPU parity of the ZeroShot-PnP solve (Algorithm 1), the trace-kernel
+convolution, the built-in denoiser and its callback path, against the FP64
+oracle on seeded synthetic inputs."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_22797_gb300 import api
+from paper_2505_22797_gb300 import synthetic as syn
+from tests.gpu_util import dev, host, rel_l2, rounded, tol
+
+pytestmark = pytest.mark.gpu
+DTYPES = [torch.float32, torch.float64]
+
+
+def _data(orc, cfg, dt):
+    m, g = cfg["model"], cfg["grid"]
+    r, v, c = (rounded(cfg[k], dt) for k in ("r", "v", "c"))
+    s = rounded(syn.add_noise(orc.forward(m, g, r, v, c), cfg["noise_frac"], cfg["noise_seed"]), dt)
+    nu0 = orc.nu0_from_frob2(orc.frob2(m, g, r, v), g["nx"] * g["ny"])
+    return m, g, r, v, s, nu0
+
+
+def _oracle_pnp(orc, m, g, r, v, s, n_it, n_cg, nu0, clip=5.0, record=None):
+    shape = (g["ny"], g["nx"])
+    return orc.pnp(lambda x: orc.forward(m, g, r, v, x), lambda y: orc.adjoint(m, g, r, v, y), s,
+                   shape, n_it, n_cg, nu0, clip_pct=clip, record=record)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("shape", [(24, 20, 900), (37, 29, 1500)])
+def test_pnp_forward_small(orc, dt, shape):
+    cfg = syn.small(*shape, traj="spiral", seed=21)
+    m, g, r, v, s, nu0 = _data(orc, cfg, dt)
+    rec = []
+    want = _oracle_pnp(orc, m, g, r, v, s, 4, 4, nu0, record=rec)
+    got, info = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), 4, 4, nu0,
+                                  with_info=True)
+    assert rel_l2(host(got), want) <= tol(dt)
+    for k in range(4):
+        assert abs(info[k][0] - rec[k]["sigma"]) <= 10 * tol(dt) * rec[k]["sigma"]
+        assert abs(info[k][1] - rec[k]["nu"]) <= 10 * tol(dt) * rec[k]["nu"]
+
+
+def _roundoff_spread(orc, m, g, r, v, s, n_it, n_cg, nu0, dt):
+    """How far round-off alone moves the oracle's own reconstruction.
+
+    The oracle is rerun with a dense copy of A (its entries from the oracle's
+    pair term; A x then sums in another order) and with the data moved by one
+    unit in the last place; for FP32 every operator application is further
+    perturbed by relative noise of FP32 size (6e-8).  CG iterates on
+    (A^T A + nu I) are not continuous at round-off level once the Krylov
+    basis loses orthogonality, so this spread, not 1e-12, is the floor of any
+    comparison of whole reconstructions at these settings."""
+    ny, nx = g["ny"], g["nx"]
+    n = nx * ny
+    A = np.stack([orc.forward(m, g, r, v, np.eye(n)[k].reshape(ny, nx)).reshape(-1)
+                  for k in range(n)], 1)
+    rng = np.random.default_rng(99)
+    eps = 6e-8 if dt == torch.float32 else 0.0
+
+    def noisy(y):
+        return y * (1.0 + eps * rng.standard_normal(y.shape)) if eps else y
+    op = lambda x: noisy((A @ x.reshape(-1)).reshape(s.shape))  # noqa: E731
+    opT = lambda y: noisy((A.T @ y.reshape(-1)).reshape(ny, nx))  # noqa: E731
+    base = orc.pnp(op, opT, s, (ny, nx), n_it, n_cg, nu0)
+    ulp = rng.choice([-1.0, 1.0], size=s.shape) * np.spacing(np.abs(s))
+    pert = orc.pnp(op, opT, s + ulp, (ny, nx), n_it, n_cg, nu0)
+    ref = _oracle_pnp(orc, m, g, r, v, s, n_it, n_cg, nu0)
+    return max(rel_l2(pert, base), rel_l2(base, ref))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_pnp_c1_well_posed(orc, dt):
+    """The 32x32 Lissajous workload, 50 PnP iterations of 5 CG steps: the
+    setting where the iteration is stable under round-off (the oracle's own
+    1-ulp spread is ~1e-14), held to the strict 1e-5 / 1e-12 bar."""
+    cfg = syn.config("c1")
+    m, g, r, v, s, nu0 = _data(orc, cfg, dt)
+    want = _oracle_pnp(orc, m, g, r, v, s, cfg["n_it"], 5, nu0)
+    got = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), cfg["n_it"], 5, nu0)
+    err = rel_l2(host(got), want)
+    print(f"c1 PnP 50x5 {dt}: rel-L2 vs oracle {err:.3e}")
+    assert err <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_pnp_c1_full(orc, dt):
+    """The 32x32 Lissajous workload as configured: 50 PnP iterations of 20 CG
+    steps.  The error against the oracle is held to ten times the oracle's
+    own round-off spread at the same precision (never below the 1e-5 / 1e-12
+    bar)."""
+    cfg = syn.config("c1")
+    m, g, r, v, s, nu0 = _data(orc, cfg, dt)
+    want = _oracle_pnp(orc, m, g, r, v, s, cfg["n_it"], cfg["n_cg"], nu0)
+    got = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), cfg["n_it"], cfg["n_cg"], nu0)
+    err = rel_l2(host(got), want)
+    spread = _roundoff_spread(orc, m, g, r, v, s, cfg["n_it"], cfg["n_cg"], nu0, dt)
+    print(f"c1 PnP 50x20 {dt}: rel-L2 vs oracle {err:.3e}, oracle round-off spread {spread:.3e}")
+    assert err <= max(tol(dt), 10 * spread)
+
+
+def test_pnp_no_clip_zero_iters_and_deterministic(orc):
+    dt = torch.float32
+    cfg = syn.small(16, 16, 600, seed=4)
+    m, g, r, v, s, nu0 = _data(orc, cfg, dt)
+    want = _oracle_pnp(orc, m, g, r, v, s, 2, 3, nu0, clip=-1.0)
+    args = (m, g, dev(r, dt), dev(v, dt), dev(s, dt))
+    a = host(api.mpi_pnp_solve(*args, 2, 3, nu0, clip_pct=-1.0))
+    b = host(api.mpi_pnp_solve(*args, 2, 3, nu0, clip_pct=-1.0))
+    assert rel_l2(a, want) <= tol(dt)
+    assert np.array_equal(a, b)
+    z = host(api.mpi_pnp_solve(*args, 0, 3, nu0))
+    assert not z.any()
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_pnp_conv_operator(orc, dt):
+    """Algorithm 1 with C_h (the paper's deconvolution stage) on a trace image."""
+    cfg = syn.small(19, 14, 10, seed=9)
+    m, g = cfg["model"], cfg["grid"]
+    K = orc.conv_kernel(m, g)
+    c = rounded(cfg["c"], dt)
+    u = rounded(orc.conv(g, K, c) + 0.01 * np.random.default_rng(3).normal(size=c.shape), dt)
+    nu0 = 1e-3 * np.sum(K * K)
+    want = orc.pnp(lambda x: orc.conv(g, K, x), lambda y: orc.conv(g, K, y), u, c.shape, 3, 5, nu0)
+    got = api.mpi_pnp_solve(m, g, None, None, dev(u, dt), 3, 5, nu0, op=api.MPI_OP_CONV)
+    assert rel_l2(host(got), want) <= tol(dt)
+
+
+def test_pnp_callback_and_errors(orc):
+    dt = torch.float32
+    cfg = syn.small(12, 10, 300, seed=2)
+    m, g, r, v, s, nu0 = _data(orc, cfg, dt)
+    seen = []
+
+    def halve(x, out, sigma):
+        seen.append(float(sigma.item()))
+        out.copy_(x * 0.5)
+    got = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), 2, 3, nu0, denoise=halve)
+    want = orc.pnp(lambda x: orc.forward(m, g, r, v, x), lambda y: orc.adjoint(m, g, r, v, y), s,
+                   (10, 12), 2, 3, nu0, denoise=lambda img, sig: img * 0.5)
+    assert len(seen) == 2
+    assert rel_l2(host(got), want) <= tol(dt)
+
+    def broken(x, out, sigma):
+        raise RuntimeError("denoiser failure")
+    with pytest.raises(api.MPIError) as e:
+        api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), 2, 3, nu0, denoise=broken)
+    assert e.value.status == api.MPI_ERR_CALLBACK
+    os.environ["MPI_FAULT"] = "alloc"
+    try:
+        with pytest.raises(api.MPIError) as e:
+            api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), 2, 3, nu0)
+        assert e.value.status == api.MPI_ERR_NOMEM
+    finally:
+        del os.environ["MPI_FAULT"]
+    # the library still works after the injected failures
+    again = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), 2, 3, nu0)
+    assert np.isfinite(host(again)).all()
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("shape", [(1, 1), (5, 3), (33, 17), (64, 64)])
+def test_conv_and_denoiser(orc, dt, shape):
+    nx, ny = shape
+    g = syn.square_grid(nx, 24.0, ny)
+    m = syn.default_model()
+    x = rounded(np.random.default_rng(nx).normal(size=(ny, nx)), dt)
+    want = orc.conv(g, orc.conv_kernel(m, g), x)
+    assert rel_l2(host(api.mpi_conv(m, g, dev(x, dt))), want) <= tol(dt)
+    assert rel_l2(host(api.mpi_denoise_gaussian5(dev(x, dt))), orc.gaussian5(x)) <= tol(dt)
+
+
+def test_conv_non_diagonal_gradient(orc):
+    dt = torch.float64
+    g = syn.square_grid(21, 24.0, 13)
+    m = dict(syn.default_model(), G=[[2.1e-3, 4e-4], [4e-4, -2.6e-3]])
+    x = np.random.default_rng(1).normal(size=(13, 21))
+    want = orc.conv(g, orc.conv_kernel(m, g), x)
+    assert rel_l2(host(api.mpi_conv(m, g, dev(x, dt))), want) <= tol(dt)
