@@ -93,6 +93,25 @@ int mpi_forward(const mpi_model *model, const mpi_grid_desc *grid,
                 const mpi_traj *traj, mpi_dtype dtype, const void *c, void *s,
                 void *stream);
 
+/* mpi_forward without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory while they run (a scan loop with a memory budget fixed at
+ * start-up, a framework that owns all device memory through its own pool, code
+ * that must avoid the implicit synchronisation of cudaFree).  Same inputs,
+ * outputs and results as mpi_forward; its scratch is a fixed 32 MiB array in
+ * device global memory that every GPU loading the library keeps until the
+ * process exits.  Problems whose scratch does not fit are rejected with
+ * MPI_ERR_UNSUPPORTED before anything is enqueued: the limit is about
+ * 32 MiB / (16 + 4 n_ch) bytes per sample in FP32 (1.39 million samples with
+ * two channels) and half that in FP64.  The first call on a device looks up
+ * the array's device address once (with that device current); make that
+ * first call before any stream capture.  All calls share the array and keep
+ * nothing across calls that a later call relies on; calls that overlap on the
+ * GPU (other streams or host threads at the same time) race on it. */
+int mpi_forward_noalloc(const mpi_model *model, const mpi_grid_desc *grid,
+                        const mpi_traj *traj, mpi_dtype dtype, const void *c, void *s,
+                        void *stream);
+
 /* Adjoint A^T:  c_out[j][i] = sum_t sum_k s[k][t] p_k^T beta K(beta G(x_ij -
  * r_t)) G v_t.  Deterministic like mpi_forward.  T == 0 writes zeros. */
 int mpi_adjoint(const mpi_model *model, const mpi_grid_desc *grid,

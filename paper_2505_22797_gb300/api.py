@@ -74,6 +74,7 @@ _lock = threading.Lock()
 
 _SIGS = {
     "mpi_forward": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_forward_noalloc": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_adjoint": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_dbeta": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 4,
     "mpi_conv": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
@@ -205,6 +206,24 @@ def mpi_forward(model, grid, r, v, c, s=None, stream=None):
     _check(load().mpi_forward(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(c),
                               _dev(c, dt, "c"), _dev(s, dt, "s") if s.numel() else None,
                               _stream(stream)))
+    return s
+
+
+def mpi_forward_noalloc(model, grid, r, v, c, s=None, stream=None):
+    """Like mpi_forward, for callers that cannot let the library allocate
+    device memory while they run: the library's scratch is a fixed 32 MiB
+    device array (see include/mpi_recon.h for the size limit and the rule
+    that overlapping calls race).  ``s`` should be preallocated by such a
+    caller; it is created here only for convenience."""
+    dt = c.dtype
+    n_ch = len(_get(model, "p"))
+    if s is None:
+        s = torch.empty((n_ch, r.shape[0]), dtype=dt, device=c.device)
+    tr = _traj(r, v, dt)
+    m, g = make_model(model), make_grid(grid)
+    _check(load().mpi_forward_noalloc(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr),
+                                      _dtype(c), _dev(c, dt, "c"),
+                                      _dev(s, dt, "s") if s.numel() else None, _stream(stream)))
     return s
 
 
