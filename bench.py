@@ -18,7 +18,6 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import glob
 import json
 import os
 import statistics
@@ -162,23 +161,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _lib_digest():
+# Sources that define the operator kernels and their launch configuration.
+KERNEL_SOURCES = ["common.cuh", "langevin.cuh", "pair_kernels.cuh", "pair_ops.cuh", "pair_ops.cu"]
+
+
+def kernel_digest():
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2505_22797_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2505_22797_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was captured on the current sources; else None."""
+    was captured on the current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
     ent = d.get(kernel)
-    if not ent or ent.get("source_digest") != _lib_digest():
+    if not ent or ent.get("source_digest") != kernel_digest():
         return None
     return ent.get("dram_bytes_per_launch")
 
