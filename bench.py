@@ -186,6 +186,105 @@ def _traffic(kernel):
     return ent.get("dram_bytes_per_launch")
 
 
+def measure_batched(api, syn, dev, stream, n_it_timed=1):
+    """The 64-frame workload (grids 64^2..256^2, T in [8192, 131072], FP32,
+    20 CG steps per PnP iteration) through one batch plan: one untimed run
+    that autotunes and captures the graph, then one timed run of
+    `n_it_timed` PnP iterations (after A^T of the data).  The full 50-iteration
+    reconstruction rate is extrapolated from the per-iteration time."""
+    import torch
+    frames = syn.batch_frames(64)
+    f32 = torch.float32
+    r, v, s_list, specs, nu0 = [], [], [], [], []
+    pairs_app = 0
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    for fr in frames:
+        m, g = fr["model"], fr["grid"]
+        rr = torch.as_tensor(fr["r"], dtype=f32, device=dev)
+        vv = torch.as_tensor(fr["v"], dtype=f32, device=dev)
+        cc = torch.as_tensor(fr["c"], dtype=f32, device=dev)
+        sc = api.mpi_forward(m, g, rr, vv, cc)
+        sn = syn.add_noise(sc.cpu().numpy().astype(np.float64), fr["noise_frac"], fr["noise_seed"])
+        z = (torch.randint(0, 2, (g["ny"], g["nx"]), generator=gen) * 2 - 1).to(dev, f32)
+        fro = float(torch.sum(api.mpi_forward(m, g, rr, vv, z).double() ** 2))
+        N = g["nx"] * g["ny"]
+        nu0.append(1e-3 * fro / N)
+        r.append(rr)
+        v.append(vv)
+        s_list.append(torch.as_tensor(sn, dtype=f32, device=dev))
+        specs.append((m, g, rr.shape[0]))
+        pairs_app += N * rr.shape[0]
+    n_cg = frames[0]["n_cg"]
+    plan = api.BatchPlan(specs, nu0, n_it_timed, n_cg, flags=api.MPI_BATCH_AUTOTUNE)
+    rho = plan.run(r, v, s_list)  # tunes, captures
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.run(r, v, s_list, rho_out=rho)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    info = plan.info()
+    plan.close()
+    apps = 2 * n_it_timed * (n_cg + 1) + 1
+    rate = pairs_app * apps / (ms * 1e-3)
+    n_it_full = frames[0]["n_it"]
+    recon_s = pairs_app * (2 * n_it_full * (n_cg + 1) + 1) / rate
+    return {"frames": len(frames), "pairs_per_application": pairs_app,
+            "timed": f"{n_it_timed} PnP iteration(s) x {n_cg} CG steps + A^T of the data, all frames",
+            "ms": ms, "gpair_per_s": rate / 1e9,
+            "recon_per_s_extrapolated": len(frames) / recon_s,
+            "batch_s_extrapolated": recon_s, "plan": info}
+
+
+def measure_paper_pipeline(api, syn, dev, stream):
+    """The paper's two-stage reconstruction (Core Stage with gamma = 1e-7 and
+    CG to 1e-3 relative residual, then ZeroShot-PnP with the trace-kernel
+    convolution, 10 iterations of 20 CG steps) on the scanner-shaped
+    synthetic scan (Lissajous 17/16, 1632 samples, 24 mm FoV) at the paper's
+    21x21 and 100x100 grids, FP32, timed end to end on the device.  The
+    paper's times (Table runtimes: CPU 0.46 s / 5.84 s, RTX A6000 1.56 s /
+    3.36 s, with a DRUNet denoiser) are context only."""
+    import torch
+    f32 = torch.float32
+    out = {}
+    paper = {21: (0.46, 1.56), 100: (5.84, 3.36)}
+    for n in (21, 100):
+        g = syn.square_grid(n)
+        m = syn.default_model()
+        r_np, v_np = syn.lissajous(1632, 17, 16)
+        c_np = syn.ellipses(g, np.random.default_rng(101))
+        r = torch.as_tensor(r_np, dtype=f32, device=dev)
+        v = torch.as_tensor(v_np, dtype=f32, device=dev)
+        s_clean = api.mpi_forward(m, g, r, v, torch.as_tensor(c_np, dtype=f32, device=dev))
+        s = torch.as_tensor(syn.add_noise(s_clean.cpu().numpy().astype(np.float64), 0.01, 201),
+                            dtype=f32, device=dev)
+        gen = torch.Generator(device="cpu").manual_seed(5)
+        fro = 0.0
+        for _ in range(4):
+            z = (torch.randint(0, 2, (n, n), generator=gen) * 2 - 1).to(dev, f32)
+            fro += float(torch.sum(api.mpi_conv(m, g, z).double() ** 2)) / 4
+        nu0 = 1e-3 * fro / (n * n)
+
+        def once():
+            _, u, it = api.mpi_grid(g, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3,
+                                    return_iters=True)
+            rho = api.mpi_pnp_solve(m, g, None, None, u.contiguous(), 10, 20, nu0, op=api.MPI_OP_CONV)
+            return it, rho
+        once()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, _ = once()
+        e1.record(stream)
+        e1.synchronize()
+        out[f"{n}x{n}"] = {"s": e0.elapsed_time(e1) * 1e-3, "core_stage_cg_steps": it,
+                           "paper_cpu_s": paper[n][0], "paper_rtx_a6000_s": paper[n][1]}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -349,6 +448,16 @@ def run_ours(args):
                   "note": "one FP64 A and one FP64 A^T application, extrapolated to the "
                           f"{apps} applications of a reconstruction"}
 
+    # --- batched form: 64 frames of uneven size in one plan ----------------------
+    batched = None
+    if world == 1 and not args.no_batch:
+        batched = measure_batched(api, syn, dev, stream)
+
+    # --- the paper's own two-stage pipeline, for context ------------------------
+    paper_pipeline = None
+    if world == 1 and not args.no_batch:
+        paper_pipeline = measure_paper_pipeline(api, syn, dev, stream)
+
     # --- CPU baseline: the oracle on a bounded sample -----------------------
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -376,7 +485,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "steps": len(e2e_ms),
                     "recon_per_s": len(e2e_ms) * world / (e2e_tot * 1e-3)},
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-            "fp64_plain": fp64_plain, "clocks": clk, "impl": "ours"}
+            "fp64_plain": fp64_plain, "batched": batched, "paper_pipeline": paper_pipeline,
+            "clocks": clk, "impl": "ours"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -390,6 +500,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame batched measurement")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -213,6 +213,54 @@ int mpi_pnp_solve(const mpi_model *model, const mpi_grid_desc *grid,
                   const mpi_pnp_opts *opts, mpi_denoise_fn denoise, void *user,
                   void *rho_out, mpi_pnp_iter_info *info, void *stream);
 
+/* ---- Batched reconstructions --------------------------------------------- */
+
+/* A plan runs Algorithm 1 with the forward operator (FP32 operator, FP64 CG
+ * vectors, inner products and PnP scalars, built-in Gaussian denoiser) for up
+ * to MPI_BATCH_MAX_FRAMES independent frames of different grid sizes and
+ * trajectory lengths at once: every operator application over all frames is
+ * one launch of the pair kernel over a frame table, the CG, percentile and
+ * denoiser steps are batched the same way, and one PnP iteration of all frames
+ * is captured once as a CUDA graph and replayed n_iter times.  Each frame
+ * has its own model, grid, T and nu0 (host arrays of n_frames entries); opts
+ * gives n_iter, n_cg and clip_pct for all frames (op must be MPI_OP_FORWARD).
+ * The plan owns its device memory (cudaMalloc at create, cudaFree at
+ * destroy).  Flags: MPI_BATCH_AUTOTUNE times candidate work-item sizes and
+ * launch forms (one block per item, or a persistent grid pulling items from a
+ * device counter) on the first run, which then synchronises the stream once;
+ * the choice is cached in the file named by $MPI_AUTOTUNE_CACHE when set.
+ * MPI_BATCH_MATCH_SINGLE splits every frame exactly as mpi_pnp_solve does,
+ * so each frame's result is bit-identical to its single-frame solve. */
+#define MPI_BATCH_MAX_FRAMES 64
+#define MPI_BATCH_AUTOTUNE 1
+#define MPI_BATCH_MATCH_SINGLE 2
+
+typedef struct mpi_batch_plan mpi_batch_plan;
+
+typedef struct {
+    int n_frames;
+    int tuned;                    /* the split in use is the tuned one (or was fixed) */
+    long long item_pairs_forward; /* work-item budget (pairs) of the forward launch */
+    long long item_pairs_adjoint;
+    int persistent_forward;       /* launch form chosen: 1 = persistent grid */
+    int persistent_adjoint;
+    long long forward_items;      /* work items per forward / adjoint launch */
+    long long adjoint_items;
+    long long device_bytes;       /* device memory owned by the plan */
+    long long graph_nodes;        /* kernels in the captured PnP iteration (0 before the first run) */
+} mpi_batch_info;
+
+int mpi_batch_plan_create(int n_frames, const mpi_model *models, const mpi_grid_desc *grids,
+                          const int64_t *T, const double *nu0, const mpi_pnp_opts *opts,
+                          int flags, mpi_batch_plan **plan);
+/* r[f], v[f]: [T_f][2], s[f]: [n_ch_f][T_f], rho_out[f]: [ny_f][nx_f] (device,
+ * float; host arrays of n_frames pointers).  Asynchronous on `stream` except
+ * for the tuning run. */
+int mpi_batch_pnp_run(mpi_batch_plan *plan, const void *const *r, const void *const *v,
+                      const void *const *s, void *const *rho_out, void *stream);
+int mpi_batch_plan_info(const mpi_batch_plan *plan, mpi_batch_info *info);
+int mpi_batch_plan_destroy(mpi_batch_plan *plan);
+
 /* ---- Diagnostics --------------------------------------------------------- */
 
 const char *mpi_status_string(int status);

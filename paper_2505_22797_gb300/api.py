@@ -65,6 +65,18 @@ class PnPIterInfo(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("nu", ctypes.c_double), ("cg_resid", ctypes.c_double)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_frames", ctypes.c_int), ("tuned", ctypes.c_int),
+                ("item_pairs_forward", ctypes.c_longlong), ("item_pairs_adjoint", ctypes.c_longlong),
+                ("persistent_forward", ctypes.c_int), ("persistent_adjoint", ctypes.c_int),
+                ("forward_items", ctypes.c_longlong), ("adjoint_items", ctypes.c_longlong),
+                ("device_bytes", ctypes.c_longlong), ("graph_nodes", ctypes.c_longlong)]
+
+
+MPI_BATCH_MAX_FRAMES = 64
+MPI_BATCH_AUTOTUNE = 1
+MPI_BATCH_MATCH_SINGLE = 2
+
 DENOISE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p)
@@ -85,6 +97,11 @@ _SIGS = {
                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mpi_pnp_solve": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
                      + [DENOISE_FN] + [ctypes.c_void_p] * 4,
+    "mpi_batch_plan_create": [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "mpi_batch_pnp_run": [ctypes.c_void_p] * 6,
+    "mpi_batch_plan_info": [ctypes.c_void_p, ctypes.c_void_p],
+    "mpi_batch_plan_destroy": [ctypes.c_void_p],
     "mpi_kernel_launches": [],
     "mpi_profile_enable": [ctypes.c_int],
     "mpi_profile_read": [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
@@ -373,3 +390,50 @@ def _wrap(ptr, shape, dtype, device):
             "shape": (n,), "typestr": {torch.float32: "<f4", torch.float64: "<f8"}[dtype],
             "data": (ptr, False), "version": 3, "strides": None, "stream": None}
     return torch.as_tensor(_CAI(), device=device).view(shape)
+
+
+class BatchPlan:
+    """mpi_batch_plan: batched Algorithm 1 (FP32) over frames of different
+    sizes.  ``frames`` is a list of (model, grid, T); ``nu0`` one value per
+    frame."""
+
+    def __init__(self, frames, nu0, n_iter, n_cg, clip_pct=5.0, flags=MPI_BATCH_AUTOTUNE):
+        n = len(frames)
+        self.n = n
+        self._models = (Model * n)(*[make_model(m) for m, _, _ in frames])
+        self._grids = (GridDesc * n)(*[make_grid(g) for _, g, _ in frames])
+        self._T = (ctypes.c_int64 * n)(*[int(T) for _, _, T in frames])
+        self._nu0 = (ctypes.c_double * n)(*[float(x) for x in nu0])
+        opts = PnPOpts(MPI_OP_FORWARD, int(n_iter), int(n_cg), 0.0, float(clip_pct))
+        self._plan = ctypes.c_void_p()
+        _check(load().mpi_batch_plan_create(n, self._models, self._grids, self._T, self._nu0,
+                                            ctypes.byref(opts), int(flags), ctypes.byref(self._plan)))
+        self.shapes = [(int(_get(g, "ny")), int(_get(g, "nx"))) for _, g, _ in frames]
+
+    def run(self, r, v, s, rho_out=None, stream=None):
+        n = self.n
+        if rho_out is None:
+            rho_out = [torch.empty(sh, dtype=torch.float32, device=s[0].device) for sh in self.shapes]
+        P = ctypes.c_void_p * n
+        rr = P(*[_dev(t, torch.float32, "r") for t in r])
+        vv = P(*[_dev(t, torch.float32, "v") for t in v])
+        ss = P(*[_dev(t, torch.float32, "s") for t in s])
+        oo = P(*[_dev(t, torch.float32, "rho_out") for t in rho_out])
+        _check(load().mpi_batch_pnp_run(self._plan, rr, vv, ss, oo, _stream(stream)))
+        return rho_out
+
+    def info(self) -> dict:
+        inf = BatchInfo()
+        _check(load().mpi_batch_plan_info(self._plan, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in BatchInfo._fields_}
+
+    def close(self):
+        if self._plan:
+            load().mpi_batch_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass

@@ -51,6 +51,7 @@ void Scratch::release()
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 struct ProfRecord {
@@ -100,6 +101,8 @@ ProfScope::ProfScope(int cls, cudaStream_t st) : cls_(cls), st_(st), on_(false)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     ev_[0] = take_event();
     ev_[1] = take_event();
     if (ev_[0] && ev_[1] && cudaEventRecord(ev_[0], st_) == cudaSuccess) on_ = true;

@@ -36,6 +36,7 @@ const char *last_error();
 // Every kernel launch of the library is followed by MPI_CHECK_LAUNCH(), which
 // also counts it (mpi_kernel_launches()).
 void note_launch();
+void note_launches(long long n);
 #define MPI_CHECK_LAUNCH()                          \
     do {                                            \
         ::mpi::note_launch();                       \
@@ -120,6 +121,11 @@ __device__ __forceinline__ float ex2_approx(float x)
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+
+// Fused multiply-add with the product fixed by the call (never left to the
+// compiler's contraction choice), so every kernel instantiation rounds alike.
+__device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Compensated (Kahan) accumulation: sum += x with running compensation.
 template <typename R>

@@ -16,11 +16,17 @@
 namespace mpi {
 
 constexpr int kFwdThreads = 128;
-constexpr int kFwdS = 2;  // samples per thread
+#ifndef MPI_FWD_S
+#define MPI_FWD_S 2
+#endif
+constexpr int kFwdS = MPI_FWD_S;  // samples per thread
 constexpr int kFwdTile = kFwdThreads * kFwdS;
 
 constexpr int kAdjThreads = 128;  // 4 warps
-constexpr int kAdjV = 8;          // voxels (rows) per thread
+#ifndef MPI_ADJ_V
+#define MPI_ADJ_V 8
+#endif
+constexpr int kAdjV = MPI_ADJ_V;  // voxels (rows) per thread
 constexpr int kAdjTileX = 32;
 constexpr int kAdjTileY = 4 * kAdjV;
 constexpr int kAdjBlock = 256;    // samples staged per shared-memory block
@@ -41,6 +47,8 @@ struct PairFrame {
     int tiles_x;      // adjoint only
     int chunk;        // forward: rows per chunk; adjoint: samples per chunk
     int rows_staged;  // forward: rows per shared-memory block
+    int near_cols;    // forward: column half-width that can hold a near pair
+    int diag;         // G is diagonal (selects the kernel branch in mixed batches)
     R p[4];
 };
 
@@ -63,6 +71,65 @@ __device__ __forceinline__ int find_frame(const PairBatch<R, MAXF> &B, int64_t i
 }
 
 // ---------------------------------------------------------------------------
+// One staged row of the forward sum for this thread's samples (diagonal G):
+// sa += c a, vx += f y_x, fy += f with f = c d (y.W).  With CLAMP the
+// Langevin scalars are evaluated at max(u, near_u), valid for the closed form.
+template <typename R, bool CLAMP>
+__device__ __forceinline__ void fwd_row_far(int nx, const V2<R> *__restrict__ xc,
+                                            const R (&Rx)[kFwdS],
+                                            const R (&yy2)[kFwdS], const R (&Wx)[kFwdS],
+                                            const R (&yyW)[kFwdS], R (&sa)[kFwdS], R (&vx)[kFwdS],
+                                            R (&fy)[kFwdS])
+{
+#pragma unroll 4
+    for (int i = 0; i < nx; ++i) {
+        const V2<R> q = xc[i];  // (x_i, c_i) in one load
+        const R xi = q.x, ci = q.y;
+#pragma unroll
+        for (int s = 0; s < kFwdS; ++s) {
+            const R yx = xi - Rx[s];
+            R u = fmx(yx, yx, yy2[s]);
+            if (CLAMP) u = max(u, Lang<R>::near_u);
+            R a, d;
+            lang_far<R, false>(u, a, d);
+            sa[s] = fmx(ci, a, sa[s]);
+            const R f = ci * d * fmx(yx, Wx[s], yyW[s]);
+            vx[s] = fmx(f, yx, vx[s]);
+            fy[s] += f;
+        }
+    }
+}
+
+// Replace, for the pairs of one sample on one row with u < near_u, the clamped
+// closed-form values (A1, D1) by the Taylor series.  Only columns within
+// `win` of the sample's nearest column can qualify (xcol is linear in i).
+template <typename R>
+__device__ __forceinline__ void fwd_near_fix(int nx, const V2<R> *__restrict__ xc, R Rx, R yy2,
+                                             R Wx, R yyW,
+                                             R A1, R D1, int win, R &sa, R &vx, R &fy)
+{
+    const R x0 = xc[0].x;
+    const R step = nx > 1 ? xc[1].x - x0 : R(1);
+    R fi = (Rx - x0) / step;
+    fi = min(max(fi, R(-2 * win - 2)), R(nx + 2 * win + 2));
+    const int ic = (int)rint(fi);
+    const int i0 = max(0, ic - win), i1 = min(nx - 1, ic + win);
+    for (int i = i0; i <= i1; ++i) {
+        const R yx = xc[i].x - Rx;
+        const R u = fmx(yx, yx, yy2);
+        if (u < Lang<R>::near_u) {
+            R a, d;
+            Lang<R>::ad_near(u, a, d);
+            const R ci = xc[i].y;
+            sa = fmx(ci, a - A1, sa);
+            const R f = ci * (d - D1) * fmx(yx, Wx, yyW);
+            vx = fmx(f, yx, vx);
+            fy += f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Forward A.  Work item = (tile of kFwdTile samples, chunk of rows).  Each
 // thread owns kFwdS samples and sums over the chunk's voxels row by row (rows
 // pass through shared memory rows_staged at a time):
@@ -72,11 +139,9 @@ __device__ __forceinline__ int find_frame(const PairBatch<R, MAXF> &B, int64_t i
 // near-FFP series test entirely.  Row sums are folded into the chunk sums with
 // compensated additions.  The item writes p_k . O(t) to its partial slot.
 template <typename R, typename CIN, bool DIAG, int MAXF>
-__global__ void __launch_bounds__(kFwdThreads)
-k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
+__device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_t item,
+                                             unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int64_t item = blockIdx.x;
     const PairFrame<R> &F = B.f[find_frame(B, item)];
     const int64_t local = item - F.item0;
     const int chunk = (int)(local / F.n_tiles);
@@ -86,9 +151,12 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
     const int nr = min(F.chunk, F.ny - j0);
 
     const int RB = F.rows_staged;
+    R A1, D1;  // the closed form at u = near_u (what clamped pairs received)
+    Lang<R>::ad_far(Lang<R>::near_u, A1, D1);
+    // Shared memory: xcol [nx], yrow [RB], and RB rows of (x_i, c_ji) pairs.
     V2<R> *s_x = reinterpret_cast<V2<R> *>(smem_raw);
     V2<R> *s_y = s_x + nx;
-    R *s_c = reinterpret_cast<R *>(s_y + RB);
+    V2<R> *s_xc = s_y + RB;
     const CIN *cin = reinterpret_cast<const CIN *>(F.in);
     for (int k = threadIdx.x; k < nx; k += kFwdThreads) s_x[k] = F.xcol[k];
 
@@ -110,14 +178,14 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
         const int nrb = min(RB, j0 + nr - jb);
         __syncthreads();
         for (int k = threadIdx.x; k < nrb * nx; k += kFwdThreads)
-            s_c[k] = R(cin[(int64_t)jb * nx + k]);
+            s_xc[k] = V2<R>{s_x[k % nx].x, R(cin[(int64_t)jb * nx + k])};
         for (int k = threadIdx.x; k < nrb; k += kFwdThreads) s_y[k] = F.yrow[jb + k];
         __syncthreads();
 
 #pragma unroll 1
     for (int r = 0; r < nrb; ++r) {
         const V2<R> yr = s_y[r];
-        const R *crow = s_c + r * nx;
+        const V2<R> *xcrow = s_xc + r * nx;
         R oy[kFwdS], ox[kFwdS], yy2[kFwdS], yyW[kFwdS];
         R sa[kFwdS], vx[kFwdS], fy[kFwdS];
         bool near = false;
@@ -130,23 +198,19 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
             near |= yy2[s] < Lang<R>::near_u;
             sa[s] = vx[s] = fy[s] = R(0);
         }
-        if (DIAG && !__any_sync(0xffffffffu, near)) {
-            // Every pair of this row has u >= yy2 >= near_u: closed form only.
-#pragma unroll 4
-            for (int i = 0; i < nx; ++i) {
-                const R xi = s_x[i].x;
-                const R ci = crow[i];
+        if (DIAG) {
+            if (!__any_sync(0xffffffffu, near)) {
+                // Every pair of this row has u >= yy2 >= near_u: closed form only.
+                fwd_row_far<R, false>(nx, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
+            } else {
+                // Closed form with u clamped to near_u, then the exact series
+                // for the few pairs of this thread that are really near.
+                fwd_row_far<R, true>(nx, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
 #pragma unroll
-                for (int s = 0; s < kFwdS; ++s) {
-                    const R yx = xi - Rx[s];
-                    const R u = yx * yx + yy2[s];
-                    R a, d;
-                    lang_far<R, false>(u, a, d);
-                    sa[s] += ci * a;
-                    const R f = ci * d * (yx * Wx[s] + yyW[s]);
-                    vx[s] += f * yx;
-                    fy[s] += f;
-                }
+                for (int s = 0; s < kFwdS; ++s)
+                    if (yy2[s] < Lang<R>::near_u)
+                        fwd_near_fix<R>(nx, xcrow, Rx[s], yy2[s], Wx[s], yyW[s], A1, D1,
+                                        F.near_cols, sa[s], vx[s], fy[s]);
             }
 #pragma unroll
             for (int s = 0; s < kFwdS; ++s) {
@@ -159,18 +223,18 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
 #pragma unroll 2
             for (int i = 0; i < nx; ++i) {
                 const V2<R> xi = s_x[i];
-                const R ci = crow[i];
+                const R ci = xcrow[i].y;
 #pragma unroll
                 for (int s = 0; s < kFwdS; ++s) {
                     const R yx = xi.x + ox[s];
                     const R yy = DIAG ? oy[s] : xi.y + oy[s];
-                    const R u = yx * yx + yy * yy;
+                    const R u = fmx(yx, yx, yy * yy);
                     R a, d;
                     lang_checked<R, false>(u, a, d);
-                    sa[s] += ci * a;
-                    const R f = ci * d * (yx * Wx[s] + yy * Wy[s]);
-                    vx[s] += f * yx;
-                    fy[s] += f * yy;
+                    sa[s] = fmx(ci, a, sa[s]);
+                    const R f = ci * d * fmx(yx, Wx[s], yy * Wy[s]);
+                    vx[s] = fmx(f, yx, vx[s]);
+                    fy[s] = fmx(f, yy, fy[s]);
                 }
             }
 #pragma unroll
@@ -207,15 +271,13 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
 // staged block a ballot marks the samples whose distance to the warp's voxel
 // box keeps every pair in the closed-form range.
 template <typename R, bool DIAG, bool DBETA, int MAXF>
-__global__ void __launch_bounds__(kAdjThreads)
-k_adjoint(const __grid_constant__ PairBatch<R, MAXF> B)
+__device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_t item)
 {
     __shared__ V2<R> s_r[kAdjBlock];
     __shared__ V4<R> s_q[kAdjBlock];
     __shared__ uint32_t s_far[4][kAdjBlock / 32];
     __shared__ double s_red[kAdjThreads / 32];
 
-    const int64_t item = blockIdx.x;
     const PairFrame<R> &F = B.f[find_frame(B, item)];
     const int64_t local = item - F.item0;
     const int chunk = (int)(local / F.n_tiles);
@@ -308,19 +370,19 @@ k_adjoint(const __grid_constant__ PairBatch<R, MAXF> B)
 #pragma unroll
                     for (int v = 0; v < kAdjV; ++v) {
                         const R yy = yrow_y[v] - rr.y;
-                        const R u = yy * yy + yx2;
+                        const R u = fmx(yy, yy, yx2);
                         R f1, f2;
                         lang_far<R, DBETA>(u, f1, f2);
-                        blk[v] += f1 * q.x + f2 * (yy * (q.w * yy + Q1) + Q0);
+                        blk[v] += fmx(f1, q.x, f2 * fmx(yy, fmx(q.w, yy, Q1), Q0));
                     }
                 } else {
 #pragma unroll
                     for (int v = 0; v < kAdjV; ++v) {
                         const R yy = yrow_y[v] - rr.y;
-                        const R u = yy * yy + yx2;
+                        const R u = fmx(yy, yy, yx2);
                         R f1, f2;
                         lang_checked<R, DBETA>(u, f1, f2);
-                        blk[v] += f1 * q.x + f2 * (yy * (q.w * yy + Q1) + Q0);
+                        blk[v] += fmx(f1, q.x, f2 * fmx(yy, fmx(q.w, yy, Q1), Q0));
                     }
                 }
             } else {
@@ -329,11 +391,12 @@ k_adjoint(const __grid_constant__ PairBatch<R, MAXF> B)
                 for (int v = 0; v < kAdjV; ++v) {
                     const R yx = ox + yrow_x[v];
                     const R yy = oy + yrow_y[v];
-                    const R u = yx * yx + yy * yy;
+                    const R u = fmx(yx, yx, yy * yy);
                     R f1, f2;
                     if (far) lang_far<R, DBETA>(u, f1, f2);
                     else lang_checked<R, DBETA>(u, f1, f2);
-                    blk[v] += f1 * q.x + f2 * (yx * (q.y * yx + q.z * yy) + q.w * yy * yy);
+                    const R quad = fmx(yx, fmx(q.y, yx, q.z * yy), q.w * yy * yy);
+                    blk[v] += fmx(f1, q.x, f2 * quad);
                 }
             }
         }
@@ -360,6 +423,105 @@ k_adjoint(const __grid_constant__ PairBatch<R, MAXF> B)
         sum = block_sum<double, kAdjThreads>(sum, s_red);
         if (threadIdx.x == 0) reinterpret_cast<double *>(F.part)[local] = sum;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Launch forms.  One block per work item (the hardware block scheduler hands
+// out items), or persistent: gridDim.x resident blocks pull item indices from
+// a device counter until the items run out; the last block to leave resets
+// the counter for the next launch (no block ever waits for another).  Both
+// give identical results: an item's arithmetic does not depend on which block
+// runs it.
+
+__device__ __forceinline__ bool queue_next(unsigned long long *queue, int64_t n_items,
+                                           long long *s_item, int64_t &item)
+{
+    if (threadIdx.x == 0) *s_item = (long long)atomicAdd(&queue[0], 1ull);
+    __syncthreads();
+    item = *s_item;
+    __syncthreads();
+    return item < n_items;
+}
+
+__device__ __forceinline__ void queue_leave(unsigned long long *queue)
+{
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&queue[1], 1ull) == gridDim.x - 1) {
+            queue[0] = 0;
+            queue[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// DM selects the pair-math branch: 0 = general G, 1 = diagonal G, 2 = per
+// frame (mixed batches; the frame's `diag` flag picks, uniformly per block).
+template <typename R, typename CIN, int DM, int MAXF>
+__device__ __forceinline__ void forward_dispatch(const PairBatch<R, MAXF> &B, int64_t item,
+                                                 unsigned char *smem_raw)
+{
+    if constexpr (DM == 2) {
+        if (B.f[find_frame(B, item)].diag) forward_item<R, CIN, true, MAXF>(B, item, smem_raw);
+        else forward_item<R, CIN, false, MAXF>(B, item, smem_raw);
+    } else {
+        forward_item<R, CIN, DM == 1, MAXF>(B, item, smem_raw);
+    }
+}
+
+template <typename R, int DM, bool DBETA, int MAXF>
+__device__ __forceinline__ void adjoint_dispatch(const PairBatch<R, MAXF> &B, int64_t item)
+{
+    if constexpr (DM == 2) {
+        if (B.f[find_frame(B, item)].diag) adjoint_item<R, true, DBETA, MAXF>(B, item);
+        else adjoint_item<R, false, DBETA, MAXF>(B, item);
+    } else {
+        adjoint_item<R, DM == 1, DBETA, MAXF>(B, item);
+    }
+}
+
+template <typename R, typename CIN, int DM, int MAXF>
+__global__ void __launch_bounds__(kFwdThreads)
+k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    forward_dispatch<R, CIN, DM, MAXF>(B, blockIdx.x, smem_raw);
+}
+
+template <typename R, typename CIN, int DM, int MAXF>
+__global__ void __launch_bounds__(kFwdThreads)
+k_forward_persistent(const __grid_constant__ PairBatch<R, MAXF> B, int64_t n_items,
+                     unsigned long long *queue)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    int64_t item;
+    while (queue_next(queue, n_items, &s_item, item)) {
+        forward_dispatch<R, CIN, DM, MAXF>(B, item, smem_raw);
+        __syncthreads();
+    }
+    queue_leave(queue);
+}
+
+template <typename R, int DM, bool DBETA, int MAXF>
+__global__ void __launch_bounds__(kAdjThreads)
+k_adjoint(const __grid_constant__ PairBatch<R, MAXF> B)
+{
+    adjoint_dispatch<R, DM, DBETA, MAXF>(B, blockIdx.x);
+}
+
+template <typename R, int DM, bool DBETA, int MAXF>
+__global__ void __launch_bounds__(kAdjThreads)
+k_adjoint_persistent(const __grid_constant__ PairBatch<R, MAXF> B, int64_t n_items,
+                     unsigned long long *queue)
+{
+    __shared__ long long s_item;
+    int64_t item;
+    while (queue_next(queue, n_items, &s_item, item)) {
+        adjoint_dispatch<R, DM, DBETA, MAXF>(B, item);
+        __syncthreads();
+    }
+    queue_leave(queue);
 }
 
 #endif  // __CUDACC__

@@ -101,7 +101,7 @@ FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_ite
     want = std::max(1, std::min(want, ny));
     sp.chunk_rows = (ny + want - 1) / want;
     sp.n_chunks = (ny + sp.chunk_rows - 1) / sp.chunk_rows;
-    sp.rows_staged = (int)std::max<size_t>(1, std::min<size_t>(sp.chunk_rows, kFwdRowBytes / (size_t(elem_bytes) * nx)));
+    sp.rows_staged = (int)std::max<size_t>(1, std::min<size_t>(sp.chunk_rows, kFwdRowBytes / (2 * size_t(elem_bytes) * nx)));
     return sp;
 }
 
@@ -196,6 +196,17 @@ __global__ void k_sum_fixed(const double *__restrict__ part, int n, double scale
 
 static bool is_diag(const ModelH &m) { return m.G[1] == 0.0 && m.G[2] == 0.0; }
 
+// Half-width (in columns) of the window around a sample that can hold a pair
+// with u < near_u: sqrt(near_u) / |beta G_00 dx|, plus one for rounding.
+template <typename R>
+int near_columns(const ModelH &m, const GridH &g)
+{
+    const double pitch = std::fabs(m.beta * m.G[0] * g.dx);
+    const double w = std::sqrt(double(Lang<R>::near_u)) / std::max(pitch, 1e-300);
+    return (int)std::min<double>(std::ceil(w) + 1.0, (double)g.nx);
+}
+template int near_columns<float>(const ModelH &, const GridH &);
+
 template <typename R>
 static PairFrame<R> base_frame(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo)
 {
@@ -233,16 +244,17 @@ int launch_forward(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
     B.f[0].n_tiles = sp.n_tiles;
     B.f[0].chunk = sp.chunk_rows;
     B.f[0].rows_staged = sp.rows_staged;
-    const size_t smem = sizeof(V2<R>) * (g.nx + sp.rows_staged) + sizeof(R) * size_t(sp.rows_staged) * g.nx;
+    B.f[0].near_cols = near_columns<R>(m, g);
+    const size_t smem = sizeof(V2<R>) * (g.nx + sp.rows_staged + size_t(sp.rows_staged) * g.nx);
     const int64_t items = (int64_t)sp.n_tiles * sp.n_chunks;
     {
         ProfScope prof(kProfForward, st);
         if (is_diag(m)) {
-            MPI_TRY(set_smem(k_forward<R, CIN, true, 1>, smem));
-            k_forward<R, CIN, true, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
+            MPI_TRY(set_smem(k_forward<R, CIN, 1, 1>, smem));
+            k_forward<R, CIN, 1, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
         } else {
-            MPI_TRY(set_smem(k_forward<R, CIN, false, 1>, smem));
-            k_forward<R, CIN, false, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
+            MPI_TRY(set_smem(k_forward<R, CIN, 0, 1>, smem));
+            k_forward<R, CIN, 0, 1><<<(unsigned)items, kFwdThreads, smem, st>>>(B);
         }
         MPI_CHECK_LAUNCH();
     }
@@ -271,9 +283,9 @@ int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
         const int64_t items = (int64_t)sp.tiles_x * sp.tiles_y * sp.n_chunks;
         ProfScope prof(kProfAdjoint, st);
         if (is_diag(m))
-            k_adjoint<R, true, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+            k_adjoint<R, 1, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
         else
-            k_adjoint<R, false, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+            k_adjoint<R, 0, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
         MPI_CHECK_LAUNCH();
     } else {
         MPI_TRY_CUDA(cudaMemsetAsync(part, 0, sizeof(R) * N, st));
@@ -317,9 +329,9 @@ int launch_dbeta(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &
     {
         ProfScope prof(kProfDbeta, st);
         if (is_diag(m))
-            k_adjoint<R, true, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+            k_adjoint<R, 1, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
         else
-            k_adjoint<R, false, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+            k_adjoint<R, 0, true, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
         MPI_CHECK_LAUNCH();
     }
     // The kernel sums u . (beta D) with W = beta G v; divide by beta.

@@ -48,6 +48,9 @@ struct AdjSplit {
 FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_items);
 AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items);
 int default_target_items();
+// Column half-width around a sample that can hold a near-FFP pair (forward).
+template <typename R>
+int near_columns(const ModelH &m, const GridH &g);
 
 // Partial-sum scratch sizes (bytes).
 template <typename R>

@@ -11,7 +11,7 @@
 #include <vector>
 
 #include "conv_ops.cuh"
-#include "pnp_ops.cuh"
+#include "pnp_device.cuh"
 
 namespace mpi {
 
@@ -22,26 +22,7 @@ int check_dtype(mpi_dtype d);
 ModelH to_host(const mpi_model *m);
 GridH to_host(const mpi_grid_desc *g);
 
-constexpr int kVecThreads = 256;
-constexpr int kVecPerBlock = 2048;  // equals the block size of the adjoint CG epilogue
-constexpr int kStatThreads = 1024;
-
 int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kVecPerBlock - 1) / kVecPerBlock); }
-
-// Sum of `n` partials in a fixed order, computed by the whole block and
-// returned to every thread (deterministic: fixed strides, fixed tree).
-template <int NT>
-__device__ double sum_parts(const double *__restrict__ part, int n, double *sh /* NT/32 + 1 */)
-{
-    double a = 0.0;
-    for (int k = threadIdx.x; k < n; k += NT) a += part[k];
-    a = block_sum<double, NT>(a, sh);
-    if (threadIdx.x == 0) sh[NT / 32] = a;
-    __syncthreads();
-    const double r = sh[NT / 32];
-    __syncthreads();
-    return r;
-}
 
 template <typename R>
 __global__ void k_set_x(int64_t N, const R *__restrict__ src, double *__restrict__ x)
@@ -177,162 +158,27 @@ int cg_step_launch(int64_t N, double *x, double *r, double *p, const double *q,
     return MPI_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Percentile trimming and noise estimate (Sec. 3.3 and the noise estimator of
-// Algorithm 1) in one block: exact order statistics by an 8-pass radix select
-// on the order-preserving integer image of the FP64 values, then two passes
-// for the mean and the population variance.
-
-__device__ __forceinline__ uint64_t f64_key(double v)
-{
-    const uint64_t b = (uint64_t)__double_as_longlong(v);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double key_f64(uint64_t k)
-{
-    const uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
-    return __longlong_as_double((long long)b);
-}
-
-template <int NT>
-__device__ double block_select(const double *__restrict__ x, int64_t N, int64_t rank,
-                               unsigned *hist, unsigned long long *sh_u)
-{
-    uint64_t prefix = 0, mask = 0;
-    int64_t krem = rank;
-    const int lane = threadIdx.x & 31;
-    for (int shift = 56; shift >= 0; shift -= 8) {
-        for (int b = threadIdx.x; b < 256; b += NT) hist[b] = 0;
-        __syncthreads();
-        for (int64_t i0 = 0; i0 < N; i0 += NT) {
-            const int64_t i = i0 + threadIdx.x;
-            unsigned digit = 256;  // no bin
-            if (i < N) {
-                const uint64_t key = f64_key(x[i]);
-                if ((key & mask) == prefix) digit = (unsigned)((key >> shift) & 255u);
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, digit);
-            if (digit < 256 && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int64_t cum = 0;
-            unsigned d = 0;
-            for (; d < 255; ++d) {
-                if (cum + hist[d] > krem) break;
-                cum += hist[d];
-            }
-            krem -= cum;
-            sh_u[0] = prefix | ((uint64_t)d << shift);
-            sh_u[1] = (unsigned long long)krem;
-        }
-        __syncthreads();
-        prefix = sh_u[0];
-        krem = (int64_t)sh_u[1];
-        mask |= (uint64_t)255 << shift;
-        __syncthreads();
-    }
-    return key_f64(prefix);
-}
-
 template <typename R>
 __global__ void __launch_bounds__(kStatThreads)
 k_outer_stats(int64_t N, const double *__restrict__ x, int do_clip, double pct, int k, double nu0,
               double *__restrict__ scal, const double *__restrict__ rr_part, int nblk,
               double *__restrict__ info_row, R *__restrict__ rho1)
 {
-    __shared__ unsigned hist[256];
-    __shared__ unsigned long long sh_u[2];
-    __shared__ double sh[kStatThreads / 32 + 1];
-    double P = -INFINITY;
-    if (do_clip) {
-        const double h = double(N - 1) * pct / 100.0;
-        const int64_t lo = (int64_t)floor(h);
-        const int64_t hi = min(lo + 1, N - 1);
-        const double xlo = block_select<kStatThreads>(x, N, lo, hist, sh_u);
-        const double xhi = (hi == lo) ? xlo : block_select<kStatThreads>(x, N, hi, hist, sh_u);
-        P = xlo + (h - double(lo)) * (xhi - xlo);
-    }
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += kStatThreads) {
-        const double v = fmax(x[i], P);
-        rho1[i] = R(v);
-        s += v;
-    }
-    s = block_sum<double, kStatThreads>(s, sh);
-    if (threadIdx.x == 0) sh[kStatThreads / 32] = s;
-    __syncthreads();
-    const double mean = sh[kStatThreads / 32] / double(N);
-    __syncthreads();
-    double q = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += kStatThreads) {
-        const double dv = fmax(x[i], P) - mean;
-        q += dv * dv;
-    }
-    q = block_sum<double, kStatThreads>(q, sh);
-    if (threadIdx.x == 0) {
-        double rr = 0.0;
-        for (int b = 0; b < nblk; ++b) rr += rr_part[b];
-        const double sigma = sqrt(q / double(N));
-        if (k == 0) scal[kScalLambda] = nu0 * sigma * sigma;
-        if (sigma > 0.0) scal[kScalNu] = scal[kScalLambda] / (sigma * sigma);
-        scal[kScalSigma] = sigma;
-        scal[kScalPct] = P;
-        info_row[0] = sigma;
-        info_row[1] = scal[kScalNu];
-        info_row[2] = sqrt(rr);
-    }
+    outer_stats_block<R>(N, x, do_clip, pct, k == 0, nu0, scal, rr_part, nblk, info_row, rho1);
 }
-
-// ---------------------------------------------------------------------------
-// Built-in denoiser: separable 5-tap Gaussian (sigma = 1 px), reflect
-// boundary (d c b a | a b c d), rows first then columns.
-
-__device__ __forceinline__ int reflect_index(int i, int n)
-{
-    const int p = 2 * n;
-    i %= p;
-    if (i < 0) i += p;
-    return i >= n ? p - 1 - i : i;
-}
-
-constexpr int kGx = 32, kGy = 8;
 
 template <typename R>
 __global__ void __launch_bounds__(kGx *kGy)
 k_gauss5(const R *__restrict__ in, R *__restrict__ out, int nx, int ny, R w0, R w1, R w2)
 {
-    __shared__ R tmp[kGy + 4][kGx];
-    const R w[5] = {w2, w1, w0, w1, w2};
-    const int tx = threadIdx.x % kGx, ty = threadIdx.x / kGx;
-    const int i0 = blockIdx.x * kGx, j0 = blockIdx.y * kGy;
-    const int i = i0 + tx;
-    const int ic = min(i, nx - 1);
-    for (int rr = ty; rr < kGy + 4; rr += kGy) {
-        const int jr = reflect_index(j0 - 2 + rr, ny);
-        const R *row = in + (int64_t)jr * nx;
-        R acc = R(0);
-#pragma unroll
-        for (int m = -2; m <= 2; ++m) acc += w[m + 2] * row[reflect_index(ic + m, nx)];
-        tmp[rr][tx] = acc;
-    }
-    __syncthreads();
-    const int j = j0 + ty;
-    if (i < nx && j < ny) {
-        R acc = R(0);
-#pragma unroll
-        for (int m = -2; m <= 2; ++m) acc += w[m + 2] * tmp[reflect_index(j + m, ny) - (j0 - 2)][tx];
-        out[(int64_t)j * nx + i] = acc;
-    }
+    gauss5_tile<R>(in, out, nx, ny, blockIdx.x * kGx, blockIdx.y * kGy, w0, w1, w2);
 }
 
 template <typename R>
 int launch_gauss5(const R *in, R *out, int nx, int ny, cudaStream_t st)
 {
     double w[3];
-    double tot = 0.0;
-    for (int m = -2; m <= 2; ++m) tot += std::exp(-0.5 * m * m);
-    for (int m = 0; m <= 2; ++m) w[m] = std::exp(-0.5 * m * m) / tot;
+    gauss5_weights(w);
     dim3 grid((nx + kGx - 1) / kGx, (ny + kGy - 1) / kGy);
     k_gauss5<R><<<grid, kGx * kGy, 0, st>>>(in, out, nx, ny, R(w[0]), R(w[1]), R(w[2]));
     MPI_CHECK_LAUNCH();

@@ -12,6 +12,7 @@ constexpr int kScalSigma = 2;
 constexpr int kScalPct = 3;
 constexpr int kScalBnorm = 4;
 constexpr int kScalTol = 5;
+constexpr int kScalIter = 6;  // batched solves: PnP iterations completed
 
 int vec_blocks(int64_t n);
 

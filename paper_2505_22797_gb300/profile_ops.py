@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--kernel", action="store_true",
+                    help="report the operator kernel alone (library event timing, mean of reps)")
     args = ap.parse_args(argv)
 
     build.build()
@@ -67,7 +69,20 @@ def main(argv=None):
             ms.append(e0.elapsed_time(e1))
         best = min(ms)
         rate = "" if name == "conv" else f"  {pairs / best / 1e6:.1f} Gpair/s"
-        print(f"{args.workload} {args.dtype} {name}: best {best:.3f} ms of {args.reps}{rate}", flush=True)
+        line = f"{args.workload} {args.dtype} {name}: best {best:.3f} ms of {args.reps}{rate}"
+        if args.kernel:
+            cls = {"forward": api.PROF_FORWARD, "adjoint": api.PROF_ADJOINT,
+                   "dbeta": api.PROF_DBETA, "conv": api.PROF_CONV}[name]
+            api.mpi_profile_enable(True)
+            for _ in range(args.reps):
+                fn()
+            n, tot = api.mpi_profile_read(cls)
+            api.mpi_profile_enable(False)
+            kms = tot / max(n, 1)
+            line += f" | kernel {kms:.4f} ms"
+            if name != "conv":
+                line += f" = {pairs / kms / 1e6:.1f} Gpair/s"
+        print(line, flush=True)
     return 0
 
 

@@ -162,3 +162,23 @@ def test_c5_sampled_rows(orc):
     vox = np.random.default_rng(15).choice(512 * 512, 64, replace=False)
     got_g = host(api.mpi_adjoint(m, g, dev(r, dt), dev(v, dt), dev(s, dt))).reshape(-1)[vox]
     assert rel_l2(got_g, orc.adjoint(m, g, r, v, s, sel=vox)) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_samples_on_voxel_centres(orc, dt):
+    """Samples exactly on voxel centres (u = 0 for one pair each) and within a
+    fraction of a voxel of them: the near-FFP series path of both kernels."""
+    g = syn.square_grid(48, 24.0, 40)
+    m = syn.default_model()
+    xs, ys = syn.voxel_centres(g)
+    rng = np.random.default_rng(31)
+    ii, jj = rng.integers(0, 48, 600), rng.integers(0, 40, 600)
+    jitter = rng.choice([0.0, 0.0, 0.01, 0.05, 0.2], size=(600, 2)) * rng.normal(size=(600, 2))
+    r = rounded(np.stack([xs[ii], ys[jj]], 1) + jitter, dt)
+    v = rounded(rng.normal(size=(600, 2)) * 0.05, dt)
+    c = rounded(rng.uniform(size=(40, 48)), dt)
+    want = orc.forward(m, g, r, v, c)
+    assert rel_l2(host(api.mpi_forward(m, g, dev(r, dt), dev(v, dt), dev(c, dt))), want) <= tol(dt)
+    s = rounded(rng.normal(size=(2, 600)), dt)
+    assert rel_l2(host(api.mpi_adjoint(m, g, dev(r, dt), dev(v, dt), dev(s, dt))),
+                  orc.adjoint(m, g, r, v, s)) <= tol(dt)

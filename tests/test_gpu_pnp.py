@@ -9,7 +9,7 @@ import torch
 
 from paper_2505_22797_gb300 import api
 from paper_2505_22797_gb300 import synthetic as syn
-from tests.gpu_util import dev, host, rel_l2, rounded, tol
+from tests.gpu_util import dev, host, rel_l2, roundoff_spread, rounded, tol
 
 pytestmark = pytest.mark.gpu
 DTYPES = [torch.float32, torch.float64]
@@ -44,34 +44,6 @@ def test_pnp_forward_small(orc, dt, shape):
         assert abs(info[k][1] - rec[k]["nu"]) <= 10 * tol(dt) * rec[k]["nu"]
 
 
-def _roundoff_spread(orc, m, g, r, v, s, n_it, n_cg, nu0, dt):
-    """How far round-off alone moves the oracle's own reconstruction.
-
-    The oracle is rerun with a dense copy of A (its entries from the oracle's
-    pair term; A x then sums in another order) and with the data moved by one
-    unit in the last place; for FP32 every operator application is further
-    perturbed by relative noise of FP32 size (6e-8).  CG iterates on
-    (A^T A + nu I) are not continuous at round-off level once the Krylov
-    basis loses orthogonality, so this spread, not 1e-12, is the floor of any
-    comparison of whole reconstructions at these settings."""
-    ny, nx = g["ny"], g["nx"]
-    n = nx * ny
-    A = np.stack([orc.forward(m, g, r, v, np.eye(n)[k].reshape(ny, nx)).reshape(-1)
-                  for k in range(n)], 1)
-    rng = np.random.default_rng(99)
-    eps = 6e-8 if dt == torch.float32 else 0.0
-
-    def noisy(y):
-        return y * (1.0 + eps * rng.standard_normal(y.shape)) if eps else y
-    op = lambda x: noisy((A @ x.reshape(-1)).reshape(s.shape))  # noqa: E731
-    opT = lambda y: noisy((A.T @ y.reshape(-1)).reshape(ny, nx))  # noqa: E731
-    base = orc.pnp(op, opT, s, (ny, nx), n_it, n_cg, nu0)
-    ulp = rng.choice([-1.0, 1.0], size=s.shape) * np.spacing(np.abs(s))
-    pert = orc.pnp(op, opT, s + ulp, (ny, nx), n_it, n_cg, nu0)
-    ref = _oracle_pnp(orc, m, g, r, v, s, n_it, n_cg, nu0)
-    return max(rel_l2(pert, base), rel_l2(base, ref))
-
-
 @pytest.mark.parametrize("dt", DTYPES)
 def test_pnp_c1_well_posed(orc, dt):
     """The 32x32 Lissajous workload, 50 PnP iterations of 5 CG steps: the
@@ -97,7 +69,7 @@ def test_pnp_c1_full(orc, dt):
     want = _oracle_pnp(orc, m, g, r, v, s, cfg["n_it"], cfg["n_cg"], nu0)
     got = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), cfg["n_it"], cfg["n_cg"], nu0)
     err = rel_l2(host(got), want)
-    spread = _roundoff_spread(orc, m, g, r, v, s, cfg["n_it"], cfg["n_cg"], nu0, dt)
+    spread = roundoff_spread(orc, m, g, r, v, s, cfg["n_it"], cfg["n_cg"], nu0, dt)
     print(f"c1 PnP 50x20 {dt}: rel-L2 vs oracle {err:.3e}, oracle round-off spread {spread:.3e}")
     assert err <= max(tol(dt), 10 * spread)
 
