@@ -26,6 +26,21 @@ constexpr int kAdjThreads = 128;  // 4 warps
 #ifndef MPI_ADJ_V
 #define MPI_ADJ_V 8
 #endif
+// Tuning knobs (compile time), chosen by timing variants on GB300: minimum
+// resident blocks per SM requested from the register allocator for the FP32
+// kernels (fewer, fatter warps win: more registers let the compiler overlap
+// the three MUFU latencies of a pair), and the unroll depth of the forward
+// column loop.  The FP64 kernels request 2 blocks per SM (no spills).
+#ifndef MPI_FWD_MINB
+#define MPI_FWD_MINB 6
+#endif
+#ifndef MPI_ADJ_MINB
+#define MPI_ADJ_MINB 4
+#endif
+#ifndef MPI_FWD_UNROLL
+#define MPI_FWD_UNROLL 8
+#endif
+constexpr int kFwdUnroll = MPI_FWD_UNROLL;
 constexpr int kAdjV = MPI_ADJ_V;  // voxels (rows) per thread
 constexpr int kAdjTileX = 32;
 constexpr int kAdjTileY = 4 * kAdjV;
@@ -81,7 +96,7 @@ __device__ __forceinline__ void fwd_row_far(int nx, const V2<R> *__restrict__ xc
                                             const R (&yyW)[kFwdS], R (&sa)[kFwdS], R (&vx)[kFwdS],
                                             R (&fy)[kFwdS])
 {
-#pragma unroll 4
+#pragma unroll kFwdUnroll
     for (int i = 0; i < nx; ++i) {
         const V2<R> q = xc[i];  // (x_i, c_i) in one load
         const R xi = q.x, ci = q.y;
@@ -260,6 +275,44 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
 }
 
 // ---------------------------------------------------------------------------
+// One staged sample against this thread's kAdjV voxels of a column (adjoint /
+// beta-derivative): blk[v] += f1 (u.W) + f2 y^T S y.  FAR: the warp's voxel
+// box is provably outside the near-FFP range for this sample.
+template <typename R, bool DIAG, bool DBETA, bool FAR>
+__device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const V2<R> xc,
+                                           const R (&yrow_x)[kAdjV], const R (&yrow_y)[kAdjV],
+                                           R (&blk)[kAdjV])
+{
+    if (DIAG) {
+        const R yx = xc.x - rr.x;
+        const R yx2 = yx * yx;
+        const R Q0 = q.y * yx2, Q1 = q.z * yx;
+#pragma unroll
+        for (int v = 0; v < kAdjV; ++v) {
+            const R yy = yrow_y[v] - rr.y;
+            const R u = fmx(yy, yy, yx2);
+            R f1, f2;
+            if (FAR) lang_far<R, DBETA>(u, f1, f2);
+            else lang_checked<R, DBETA>(u, f1, f2);
+            blk[v] += fmx(f1, q.x, f2 * fmx(yy, fmx(q.w, yy, Q1), Q0));
+        }
+    } else {
+        const R ox = xc.x - rr.x, oy = xc.y - rr.y;
+#pragma unroll
+        for (int v = 0; v < kAdjV; ++v) {
+            const R yx = ox + yrow_x[v];
+            const R yy = oy + yrow_y[v];
+            const R u = fmx(yx, yx, yy * yy);
+            R f1, f2;
+            if (FAR) lang_far<R, DBETA>(u, f1, f2);
+            else lang_checked<R, DBETA>(u, f1, f2);
+            const R quad = fmx(yx, fmx(q.y, yx, q.z * yy), q.w * yy * yy);
+            blk[v] += fmx(f1, q.x, f2 * quad);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint A^T (DBETA = false) and the beta-derivative (DBETA = true).
 // Work item = (tile of 32 x 32 voxels, chunk of samples).  Lane = column, each
 // thread owns kAdjV consecutive rows of its column.  Samples are staged in
@@ -357,46 +410,23 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
         R blk[kAdjV];
 #pragma unroll
         for (int v = 0; v < kAdjV; ++v) blk[v] = R(0);
+        // 32 staged samples share one word of far flags: runs of 32 far
+        // samples take a loop without per-sample tests.
 #pragma unroll 1
-        for (int k = 0; k < nb; ++k) {
-            const V2<R> rr = s_r[k];
-            const V4<R> q = s_q[k];
-            const bool far = (s_far[warp][k >> 5] >> (k & 31)) & 1u;
-            if (DIAG) {
-                const R yx = xc.x - rr.x;
-                const R yx2 = yx * yx;
-                const R Q0 = q.y * yx2, Q1 = q.z * yx;
-                if (far) {
-#pragma unroll
-                    for (int v = 0; v < kAdjV; ++v) {
-                        const R yy = yrow_y[v] - rr.y;
-                        const R u = fmx(yy, yy, yx2);
-                        R f1, f2;
-                        lang_far<R, DBETA>(u, f1, f2);
-                        blk[v] += fmx(f1, q.x, f2 * fmx(yy, fmx(q.w, yy, Q1), Q0));
-                    }
-                } else {
-#pragma unroll
-                    for (int v = 0; v < kAdjV; ++v) {
-                        const R yy = yrow_y[v] - rr.y;
-                        const R u = fmx(yy, yy, yx2);
-                        R f1, f2;
-                        lang_checked<R, DBETA>(u, f1, f2);
-                        blk[v] += fmx(f1, q.x, f2 * fmx(yy, fmx(q.w, yy, Q1), Q0));
-                    }
-                }
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+            const uint32_t mask = s_far[warp][k0 >> 5];
+            const int kn = min(32, nb - k0);
+            if (kn == 32 && mask == 0xffffffffu) {
+#pragma unroll 2
+                for (int k = k0; k < k0 + 32; ++k)
+                    adj_sample<R, DIAG, DBETA, true>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
             } else {
-                const R ox = xc.x - rr.x, oy = xc.y - rr.y;
-#pragma unroll
-                for (int v = 0; v < kAdjV; ++v) {
-                    const R yx = ox + yrow_x[v];
-                    const R yy = oy + yrow_y[v];
-                    const R u = fmx(yx, yx, yy * yy);
-                    R f1, f2;
-                    if (far) lang_far<R, DBETA>(u, f1, f2);
-                    else lang_checked<R, DBETA>(u, f1, f2);
-                    const R quad = fmx(yx, fmx(q.y, yx, q.z * yy), q.w * yy * yy);
-                    blk[v] += fmx(f1, q.x, f2 * quad);
+#pragma unroll 1
+                for (int k = k0; k < k0 + kn; ++k) {
+                    if ((mask >> (k - k0)) & 1u)
+                        adj_sample<R, DIAG, DBETA, true>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
+                    else
+                        adj_sample<R, DIAG, DBETA, false>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
                 }
             }
         }
@@ -481,7 +511,7 @@ __device__ __forceinline__ void adjoint_dispatch(const PairBatch<R, MAXF> &B, in
 }
 
 template <typename R, typename CIN, int DM, int MAXF>
-__global__ void __launch_bounds__(kFwdThreads)
+__global__ void __launch_bounds__(kFwdThreads, sizeof(R) == 4 ? MPI_FWD_MINB : 2)
 k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -489,7 +519,7 @@ k_forward(const __grid_constant__ PairBatch<R, MAXF> B)
 }
 
 template <typename R, typename CIN, int DM, int MAXF>
-__global__ void __launch_bounds__(kFwdThreads)
+__global__ void __launch_bounds__(kFwdThreads, sizeof(R) == 4 ? MPI_FWD_MINB : 2)
 k_forward_persistent(const __grid_constant__ PairBatch<R, MAXF> B, int64_t n_items,
                      unsigned long long *queue)
 {
@@ -504,14 +534,14 @@ k_forward_persistent(const __grid_constant__ PairBatch<R, MAXF> B, int64_t n_ite
 }
 
 template <typename R, int DM, bool DBETA, int MAXF>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, sizeof(R) == 4 ? MPI_ADJ_MINB : 2)
 k_adjoint(const __grid_constant__ PairBatch<R, MAXF> B)
 {
     adjoint_dispatch<R, DM, DBETA, MAXF>(B, blockIdx.x);
 }
 
 template <typename R, int DM, bool DBETA, int MAXF>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, sizeof(R) == 4 ? MPI_ADJ_MINB : 2)
 k_adjoint_persistent(const __grid_constant__ PairBatch<R, MAXF> B, int64_t n_items,
                      unsigned long long *queue)
 {
