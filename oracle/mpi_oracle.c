@@ -397,7 +397,11 @@ void og_laplacian(const og_grid *g, const double *f, double *out)
  *   kappa_G(y) = beta tr(K(beta G y) G),
  * sampled on all voxel offsets y = (ii dx, jj dy), |ii| < nx, |jj| < ny.
  * kern is [(2ny-1)][(2nx-1)], offset (0,0) at (ny-1, nx-1). */
-void og_conv_kernel(const og_model *m, const og_grid *g, double *kern)
+/* comp < 0: the trace kernel above.  comp = 2a + b: the entry (a, b) of
+ * beta K(beta G y) G instead; with only channel a measured (Sec. 3.6) the
+ * deconvolution uses the (a, a) entry, the kernel of the diagonal
+ * core-operator component that the single-channel Core Stage recovers. */
+void og_conv_kernel_component(const og_model *m, const og_grid *g, int comp, double *kern)
 {
     og_init_series();
     int KX = 2 * g->nx - 1, KY = 2 * g->ny - 1;
@@ -408,10 +412,17 @@ void og_conv_kernel(const og_model *m, const og_grid *g, double *kern)
                            m->beta * (m->G[2] * off[0] + m->G[3] * off[1])};
             double K[4];
             og_K(y, K);
-            /* tr(K G) = sum_ab K_ab G_ba */
-            double tr = K[0] * m->G[0] + K[1] * m->G[2] + K[2] * m->G[1] + K[3] * m->G[3];
-            kern[(int64_t)jj * KX + ii] = m->beta * tr;
+            /* (K G)_ab = sum_c K_ac G_cb */
+            double KG[4] = {K[0] * m->G[0] + K[1] * m->G[2], K[0] * m->G[1] + K[1] * m->G[3],
+                            K[2] * m->G[0] + K[3] * m->G[2], K[2] * m->G[1] + K[3] * m->G[3]};
+            double val = comp < 0 ? KG[0] + KG[3] : KG[comp];
+            kern[(int64_t)jj * KX + ii] = m->beta * val;
         }
+}
+
+void og_conv_kernel(const og_model *m, const og_grid *g, double *kern)
+{
+    og_conv_kernel_component(m, g, -1, kern);
 }
 
 /* Linear (zero-padded) convolution with the sampled kernel (the matrix C_h of

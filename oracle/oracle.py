@@ -86,6 +86,7 @@ def _load():
             lib.og_interp_T.argtypes = [P(_Grid), _I64, _D, _D, _D, _D]
             lib.og_laplacian.argtypes = [P(_Grid), _D, _D]
             lib.og_conv_kernel.argtypes = [P(_Model), P(_Grid), _D]
+            lib.og_conv_kernel_component.argtypes = [P(_Model), P(_Grid), ctypes.c_int, _D]
             lib.og_conv.argtypes = [P(_Grid), _D, _D, _D]
             lib.og_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -234,10 +235,14 @@ def laplacian(grid, f) -> np.ndarray:
     return out
 
 
-def conv_kernel(model, grid) -> np.ndarray:
-    """kappa_G(y) = beta tr(K(beta G y) G) on all voxel offsets."""
+def conv_kernel(model, grid, component=None) -> np.ndarray:
+    """kappa_G(y) = beta tr(K(beta G y) G) on all voxel offsets, or, with
+    component = (a, b), the entry beta (K(beta G y) G)_ab (the single-channel
+    deconvolution kernel of Sec. 3.6 is the (0, 0) entry)."""
     out = np.empty((2 * int(grid["ny"]) - 1, 2 * int(grid["nx"]) - 1))
-    _load().og_conv_kernel(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)), _ptr(out))
+    comp = -1 if component is None else 2 * int(component[0]) + int(component[1])
+    _load().og_conv_kernel_component(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)),
+                                     comp, _ptr(out))
     return out
 
 
@@ -385,6 +390,41 @@ def pnp(op, opT, data, shape, n_it, n_cg, nu0, clip_pct=5.0, denoise=None,
             record.append({"sigma": sigma, "nu": nu, "cg_resid": float(hist[-1]),
                            "nu_used": nu_k})
     return rho2
+
+
+def core_stage_channel(grid, r, v, s_k, k, gamma, max_iter, rel_tol=None):
+    """Core Stage with only receive channel k measured (Sec. 3.6):
+        s_k(t) = I[A_k0](r_t) v_x(t) + I[A_k1](r_t) v_y(t),
+    the two components (A_k0, A_k1) solved as in Eq. first:step with the
+    Laplacian regulariser on each.  The measurement operator is the channel-k
+    row of the two-channel one (the other channel's components held at zero).
+    Returns (A [2, ny, nx], A_kk, residual history)."""
+    T = r.shape[0]
+    ny, nx = int(grid["ny"]), int(grid["nx"])
+    s_k = _f64(s_k).reshape(-1)
+
+    def embed(A2):
+        A4 = np.zeros((4, ny, nx))
+        A4[2 * k:2 * k + 2] = A2
+        return A4
+
+    def M(A2):
+        return interp(grid, r, v, embed(A2))[k]
+
+    def MT(y):
+        s2 = np.zeros((2, T))
+        s2[k] = y
+        return interp_T(grid, r, v, s2)[2 * k:2 * k + 2]
+
+    def lap2(x):
+        return np.stack([laplacian(grid, x[m]) for m in range(2)])
+
+    def apply(x):
+        return MT(M(x)) / T + gamma * lap2(lap2(x))
+
+    b = MT(s_k) / T
+    x, hist, _ = cg(apply, b, np.zeros((2, ny, nx)), max_iter, rel_tol=rel_tol)
+    return x, x[k], hist
 
 
 def core_stage(grid, r, v, s, gamma, max_iter, rel_tol=None):

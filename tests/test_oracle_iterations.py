@@ -126,3 +126,37 @@ def test_core_stage_vs_dense_solve(orc):
     assert np.allclose(u, Ahat[0] + Ahat[3])
     Ahat2, _, hist2 = orc.core_stage(grid, r, v, s, gamma, max_iter=10000, rel_tol=1e-3)
     assert hist2[-1] <= 1e-3 * np.linalg.norm(b) and len(hist2) < 400
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_core_stage_single_channel_vs_dense_solve(orc, k):
+    """Sec. 3.6: only channel k measured; the two components (A_k0, A_k1) from
+    CG equal the dense normal-equation solution."""
+    grid = syn.square_grid(5, 10.0, 4)
+    rng = np.random.default_rng(7 + k)
+    T = 70
+    r, v = syn.lissajous(T, 3, 2, amp=5.0)
+    s_k = rng.normal(size=T)
+    gamma = 1e-2
+    N = 20
+    cols = []
+    for q in range(2 * N):
+        e = np.zeros(2 * N)
+        e[q] = 1
+        E = e.reshape(2, 4, 5)
+        E4 = np.zeros((4, 4, 5))
+        E4[2 * k:2 * k + 2] = E
+        Ms = orc.interp(grid, r, v, E4)[k]
+        s2 = np.zeros((2, T))
+        s2[k] = Ms
+        MtM = orc.interp_T(grid, r, v, s2)[2 * k:2 * k + 2] / T
+        lap = np.stack([orc.laplacian(grid, orc.laplacian(grid, E[m])) for m in range(2)])
+        cols.append((MtM + gamma * lap).reshape(-1))
+    Mn = np.stack(cols, 1)
+    s2 = np.zeros((2, T))
+    s2[k] = s_k
+    b = (orc.interp_T(grid, r, v, s2)[2 * k:2 * k + 2] / T).reshape(-1)
+    want = np.linalg.solve(Mn, b)
+    A, Akk, _ = orc.core_stage_channel(grid, r, v, s_k, k, gamma, max_iter=300)
+    assert np.allclose(A.reshape(-1), want, rtol=1e-7, atol=1e-9 * np.abs(want).max())
+    assert np.array_equal(Akk, A[k])

@@ -301,3 +301,23 @@ def test_conv_direct_vs_fft(orc):
     assert np.allclose(d, full[7:15, 10:21], rtol=1e-12, atol=1e-12 * np.abs(d).max())
     y = np.random.default_rng(7).normal(size=(8, 11))
     assert abs(np.sum(orc.conv(grid, K, x) * y) - np.sum(x * orc.conv(grid, K, y))) < 1e-11
+
+
+def test_conv_kernel_components(orc):
+    """Entry (a, b) of beta K(beta G y) G: the (0,0) + (1,1) entries give the
+    trace kernel, and each entry is the forward model's matrix entry at voxel
+    centres (channel a with v = e_b), also for a non-diagonal G."""
+    grid, model, _, _, c = _tiny(nx=5, ny=4, G=[[-1e-3, 4e-4], [4e-4, 2e-3]])
+    model["p"] = [[1.0, 0.0], [0.0, 1.0]]
+    K = {(a, b): orc.conv_kernel(model, grid, component=(a, b)) for a in range(2) for b in range(2)}
+    assert np.allclose(K[0, 0] + K[1, 1], orc.conv_kernel(model, grid), rtol=1e-13, atol=1e-16)
+    xs = grid["x0"] + (np.arange(5) + 0.5) * grid["dx"]
+    ys = grid["y0"] + (np.arange(4) + 0.5) * grid["dy"]
+    for (a, b), Kab in K.items():
+        u = orc.conv(grid, Kab, c)
+        for j in range(4):
+            for i in range(5):
+                r = np.array([[xs[i], ys[j]]])
+                v = np.eye(2)[b][None]
+                s = orc.forward(model, grid, r, v, c)
+                assert abs(u[j, i] - s[a, 0]) <= 1e-12 * max(1.0, abs(u[j, i]))
