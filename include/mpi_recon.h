@@ -136,6 +136,13 @@ int mpi_dbeta(const mpi_model *model, const mpi_grid_desc *grid,
 int mpi_conv(const mpi_model *model, const mpi_grid_desc *grid, mpi_dtype dtype,
              const void *in, void *out, void *stream);
 
+/* Like mpi_conv with one entry of the kernel matrix instead of its trace:
+ * kappa_ab(y) = beta (K(beta G y) G)_ab, component = 2a + b (0..3).  The
+ * single-channel deconvolution of Sec. 3.6 uses the diagonal entry (a, a) of
+ * the measured channel.  component = -1 gives the trace kernel (mpi_conv). */
+int mpi_conv_component(const mpi_model *model, const mpi_grid_desc *grid, mpi_dtype dtype,
+                       int component, const void *in, void *out, void *stream);
+
 /* Cosine interpolation of the Core Stage (Eq. first:step):
  *   s[k][t] = sum_m I[Ahat_km](r_t) v_m(t),  k = 0, 1,
  * Ahat is [4][ny][nx] (component 2k+m), s is [2][T].  Along each axis a
@@ -154,12 +161,18 @@ typedef struct {
     double gamma;    /* weight of the Laplacian regulariser (paper: 1e-7) */
     int max_iter;    /* CG iteration limit (paper: 10000) */
     double rel_tol;  /* stop when ||r|| <= rel_tol ||b|| (paper: 1e-3); <= 0: run max_iter */
+    int channel;     /* 0: both channels measured; 1 or 2: only channel x (k = 0) or
+                        y (k = 1) measured, the partial-data setting of Sec. 3.6 */
 } mpi_grid_opts;
 
 /* Solves ((1/T) M^T M + gamma Lap^T Lap) Ahat = (1/T) M^T s by CG from
  * Ahat = 0, with M the cosine-interpolation measurement operator above and Lap
  * the 5-point Laplacian with replicated boundary on each of the 4 components.
  * s is [2][T]; outputs Ahat [4][ny][nx] and trace [ny][nx] = Ahat_00 + Ahat_11.
+ * With opts->channel = k + 1 only channel k is measured: s is [1][T] (that
+ * channel), the unknowns are the two components (A_k0, A_k1) of the row k,
+ * Ahat is [2][ny][nx] and `trace` receives the diagonal component A_kk, the
+ * input of the single-channel deconvolution (mpi_conv_component).
  * The operator runs in the call's dtype; CG vectors and inner products are
  * FP64.  With rel_tol > 0 the host polls the device-side stop flag every 16
  * CG steps (a stream synchronisation); the result is the same as stopping at
@@ -192,6 +205,8 @@ typedef struct {
     int n_cg;         /* CG steps per data-fidelity solve (after the initial residual) */
     double nu0;       /* initial Tikhonov weight nu_0 */
     double clip_pct;  /* percentile trimming below this percentile (paper: 5); < 0 disables */
+    int kernel_component; /* MPI_OP_CONV only: 0 = trace kernel; 1 + 2a + b = entry (a, b)
+                             of beta K(beta G y) G (1: channel-x deconvolution, Sec. 3.6) */
 } mpi_pnp_opts;
 
 typedef struct {

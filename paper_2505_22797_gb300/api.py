@@ -53,12 +53,14 @@ class Traj(ctypes.Structure):
 
 
 class GridOpts(ctypes.Structure):
-    _fields_ = [("gamma", ctypes.c_double), ("max_iter", ctypes.c_int), ("rel_tol", ctypes.c_double)]
+    _fields_ = [("gamma", ctypes.c_double), ("max_iter", ctypes.c_int), ("rel_tol", ctypes.c_double),
+                ("channel", ctypes.c_int)]
 
 
 class PnPOpts(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("n_iter", ctypes.c_int), ("n_cg", ctypes.c_int),
-                ("nu0", ctypes.c_double), ("clip_pct", ctypes.c_double)]
+                ("nu0", ctypes.c_double), ("clip_pct", ctypes.c_double),
+                ("kernel_component", ctypes.c_int)]
 
 
 class PnPIterInfo(ctypes.Structure):
@@ -90,6 +92,7 @@ _SIGS = {
     "mpi_adjoint": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_dbeta": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 4,
     "mpi_conv": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_conv_component": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 3,
     "mpi_interp": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_interp_adjoint": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_grid": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 6,
@@ -281,6 +284,18 @@ def mpi_conv(model, grid, x, out=None, stream=None):
     return out
 
 
+def mpi_conv_component(model, grid, component, x, out=None, stream=None):
+    """Convolution with entry ``component`` = 2a + b of beta K(beta G y) G
+    (-1: the trace kernel, as mpi_conv)."""
+    dt = x.dtype
+    if out is None:
+        out = torch.empty_like(x)
+    m, g = make_model(model), make_grid(grid)
+    _check(load().mpi_conv_component(ctypes.byref(m), ctypes.byref(g), _dtype(x), int(component),
+                                     _dev(x, dt, "in"), _dev(out, dt, "out"), _stream(stream)))
+    return out
+
+
 def mpi_interp(grid, r, v, Ahat, s=None, stream=None):
     dt = Ahat.dtype
     if s is None:
@@ -305,15 +320,20 @@ def mpi_interp_adjoint(grid, r, v, s, Ahat=None, stream=None):
 
 
 def mpi_grid(grid, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=None, trace=None,
-             return_iters=False, stream=None):
+             return_iters=False, channel=None, stream=None):
+    """Core Stage.  ``channel`` None: s is [2][T] and Ahat [4][ny][nx];
+    channel k (0 or 1): only that channel was measured, s is [T] (or [1][T])
+    and Ahat holds (A_k0, A_k1), trace = A_kk."""
     dt = s.dtype
     g = make_grid(grid)
+    nc = 4 if channel is None else 2
     if Ahat is None:
-        Ahat = torch.empty((4, g.ny, g.nx), dtype=dt, device=s.device)
+        Ahat = torch.empty((nc, g.ny, g.nx), dtype=dt, device=s.device)
     if trace is None:
         trace = torch.empty((g.ny, g.nx), dtype=dt, device=s.device)
     tr = _traj(r, v, dt)
-    opts = GridOpts(float(gamma), int(max_iter), float(rel_tol))
+    opts = GridOpts(float(gamma), int(max_iter), float(rel_tol),
+                    0 if channel is None else int(channel) + 1)
     n_it = ctypes.c_int(-1)
     _check(load().mpi_grid(ctypes.byref(g), ctypes.byref(tr), _dtype(s),
                            _dev(s, dt, "s") if s.numel() else None, ctypes.byref(opts),
@@ -335,10 +355,11 @@ def mpi_denoise_gaussian5(x, out=None, stream=None):
 
 
 def mpi_pnp_solve(model, grid, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, op=MPI_OP_FORWARD,
-                  denoise=None, rho_out=None, with_info=False, stream=None):
+                  denoise=None, rho_out=None, with_info=False, kernel_component=None, stream=None):
     """Algorithm 1.  ``denoise`` is None (built-in Gaussian) or a Python
     callable (in_tensor, out_tensor, sigma_dev_tensor) -> None that enqueues
-    on the current stream."""
+    on the current stream.  ``kernel_component`` (MPI_OP_CONV only): None for
+    the trace kernel, else 2a + b of the kernel-matrix entry to deconvolve."""
     dt = data.dtype
     g = make_grid(grid)
     if rho_out is None:
@@ -348,7 +369,8 @@ def mpi_pnp_solve(model, grid, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, op=M
     else:
         tr = Traj(0, None, None) if r is None else _traj(r, v, dt)
     m = make_model(model)
-    opts = PnPOpts(int(op), int(n_iter), int(n_cg), float(nu0), float(clip_pct))
+    opts = PnPOpts(int(op), int(n_iter), int(n_cg), float(nu0), float(clip_pct),
+                   0 if kernel_component is None else int(kernel_component) + 1)
     info = (PnPIterInfo * max(1, n_iter))() if with_info else None
     cb = DENOISE_FN(0)
     keep = None
@@ -404,7 +426,7 @@ class BatchPlan:
         self._grids = (GridDesc * n)(*[make_grid(g) for _, g, _ in frames])
         self._T = (ctypes.c_int64 * n)(*[int(T) for _, _, T in frames])
         self._nu0 = (ctypes.c_double * n)(*[float(x) for x in nu0])
-        opts = PnPOpts(MPI_OP_FORWARD, int(n_iter), int(n_cg), 0.0, float(clip_pct))
+        opts = PnPOpts(MPI_OP_FORWARD, int(n_iter), int(n_cg), 0.0, float(clip_pct), 0)
         self._plan = ctypes.c_void_p()
         _check(load().mpi_batch_plan_create(n, self._models, self._grids, self._T, self._nu0,
                                             ctypes.byref(opts), int(flags), ctypes.byref(self._plan)))

@@ -17,7 +17,7 @@ namespace mpi {
 constexpr int kConvT = 16;  // output / input tile edge
 
 __global__ void k_conv_kernel_sample(int nx, int ny, double dx, double dy, double beta,
-                                     double g00, double g01, double g10, double g11,
+                                     double g00, double g01, double g10, double g11, int comp,
                                      double *__restrict__ K)
 {
     const int KX = 2 * nx - 1, KY = 2 * ny - 1;
@@ -31,9 +31,18 @@ __global__ void k_conv_kernel_sample(int nx, int ny, double dx, double dy, doubl
         const double u = yx * yx + yy * yy;
         double a, d;
         lang_checked<double, false>(u, a, d);
-        // K = a I + d y y^T;  tr(K G) = a tr G + d y^T G y
-        const double tr = a * (g00 + g11) + d * (yx * (g00 * yx + g01 * yy) + yy * (g10 * yx + g11 * yy));
-        K[e] = beta * tr;
+        // K = a I + d y y^T;  (K G)_ab = a G_ab + d y_a (G^T y)_b
+        double val;
+        if (comp < 0) {  // tr(K G) = a tr G + d y^T G y
+            val = a * (g00 + g11) + d * (yx * (g00 * yx + g01 * yy) + yy * (g10 * yx + g11 * yy));
+        } else {
+            const int ra = comp >> 1, cb = comp & 1;
+            const double Gab = ra == 0 ? (cb == 0 ? g00 : g01) : (cb == 0 ? g10 : g11);
+            const double ya = ra == 0 ? yx : yy;
+            const double gty = cb == 0 ? g00 * yx + g10 * yy : g01 * yx + g11 * yy;
+            val = a * Gab + d * ya * gty;
+        }
+        K[e] = beta * val;
     }
 }
 
@@ -51,13 +60,14 @@ size_t conv_kernel_bytes(int nx, int ny, int elem_bytes)
 }
 
 template <typename R>
-int conv_prepare_kernel(const ModelH &m, const GridH &g, void *scratch, R **K_out, cudaStream_t st)
+int conv_prepare_kernel(const ModelH &m, const GridH &g, void *scratch, R **K_out, cudaStream_t st,
+                        int comp)
 {
     const int64_t n = (int64_t)(2 * g.nx - 1) * (2 * g.ny - 1);
     double *K64 = static_cast<double *>(scratch);
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
     k_conv_kernel_sample<<<blocks, 256, 0, st>>>(g.nx, g.ny, g.dx, g.dy, m.beta, m.G[0], m.G[1],
-                                                 m.G[2], m.G[3], K64);
+                                                 m.G[2], m.G[3], comp, K64);
     MPI_CHECK_LAUNCH();
     if constexpr (sizeof(R) == sizeof(double)) {
         *K_out = reinterpret_cast<R *>(K64);
@@ -124,8 +134,8 @@ int launch_conv(const GridH &g, const R *K, const IN *in, OUT *out, cudaStream_t
     return MPI_OK;
 }
 
-template int conv_prepare_kernel<float>(const ModelH &, const GridH &, void *, float **, cudaStream_t);
-template int conv_prepare_kernel<double>(const ModelH &, const GridH &, void *, double **, cudaStream_t);
+template int conv_prepare_kernel<float>(const ModelH &, const GridH &, void *, float **, cudaStream_t, int);
+template int conv_prepare_kernel<double>(const ModelH &, const GridH &, void *, double **, cudaStream_t, int);
 template int launch_conv<float, float, float>(const GridH &, const float *, const float *, float *, cudaStream_t);
 template int launch_conv<float, double, float>(const GridH &, const float *, const double *, float *, cudaStream_t);
 template int launch_conv<float, float, double>(const GridH &, const float *, const float *, double *, cudaStream_t);

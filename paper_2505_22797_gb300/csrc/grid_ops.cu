@@ -52,8 +52,10 @@ static AxisMap make_axis(double p0, double h, int n)
     return AxisMap{1.0 / h, -p0 / h - 0.5, n};
 }
 
-// s[k][t] = sum_m I[Ahat_{2k+m}](r_t) v_m(t)   (Ahat of type AT, s of type R)
-template <typename R, typename AT>
+// s[k][t] = sum_m I[Ahat_{2k+m}](r_t) v_m(t)   (Ahat of type AT, s of type R).
+// CH < 0: both channels, Ahat has 4 components, s 2 rows.  CH = k: only
+// channel k, Ahat holds (A_k0, A_k1) and s one row.
+template <typename R, typename AT, int CH>
 __global__ void k_interp(int64_t T, const R *__restrict__ r, const R *__restrict__ v,
                          const AT *__restrict__ A, AxisMap ax, AxisMap ay, R *__restrict__ s)
 {
@@ -67,12 +69,13 @@ __global__ void k_interp(int64_t T, const R *__restrict__ r, const R *__restrict
         axis_weights<R>(r[2 * t + 1], ay, j0, wy0, wy1);
         const int i1 = ax.n > 1 ? i0 + 1 : i0, j1 = ay.n > 1 ? j0 + 1 : j0;
         const R vx = v[2 * t], vy = v[2 * t + 1];
+        constexpr int K = CH < 0 ? 2 : 1;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < K; ++k) {
             R acc = R(0);
 #pragma unroll
             for (int m = 0; m < 2; ++m) {
-                const AT *F = A + (2 * k + m) * N;
+                const AT *F = A + (CH < 0 ? 2 * k + m : m) * N;
                 const R val = wy0 * (wx0 * R(F[(int64_t)j0 * nx + i0]) + wx1 * R(F[(int64_t)j0 * nx + i1])) +
                               wy1 * (wx0 * R(F[(int64_t)j1 * nx + i0]) + wx1 * R(F[(int64_t)j1 * nx + i1]));
                 acc += val * (m == 0 ? vx : vy);
@@ -170,8 +173,9 @@ __global__ void k_cell_sort(int n_cells, const int *__restrict__ offset, int *__
 }
 
 // Ahat_{2k+m}(node) = sum over samples t of the adjacent cells of
-// w_node(t) v_m(t) s_k(t).
-template <typename R, typename OUT>
+// w_node(t) v_m(t) s_k(t).  CH = k: only channel k (s one row), output the two
+// components (A_k0, A_k1).
+template <typename R, typename OUT, int CH>
 __global__ void k_interp_T(const R *__restrict__ r, const R *__restrict__ v, const R *__restrict__ s,
                            int64_t T, AxisMap ax, AxisMap ay, int ncx, int ncy,
                            const int *__restrict__ offset, const int *__restrict__ list,
@@ -179,10 +183,13 @@ __global__ void k_interp_T(const R *__restrict__ r, const R *__restrict__ v, con
 {
     const int nx = ax.n, ny = ay.n;
     const int64_t N = (int64_t)nx * ny;
+    constexpr int NC = CH < 0 ? 4 : 2;
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < N;
          node += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(node % nx), j = (int)(node / nx);
-        R acc[4] = {R(0), R(0), R(0), R(0)};
+        R acc[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) acc[m] = R(0);
         for (int cj = j - 1; cj <= j; ++cj) {
             if (cj < 0 || cj >= ncy) continue;
             for (int ci = i - 1; ci <= i; ++ci) {
@@ -197,17 +204,23 @@ __global__ void k_interp_T(const R *__restrict__ r, const R *__restrict__ v, con
                     const R wx = (i == i0) ? wx0 : wx1;
                     const R wy = (j == j0) ? wy0 : wy1;
                     const R w = wy * wx;
-                    const R s0 = s[t], s1 = s[T + t];
                     const R vx = v[2 * t], vy = v[2 * t + 1];
-                    acc[0] += w * (vx * s0);
-                    acc[1] += w * (vy * s0);
-                    acc[2] += w * (vx * s1);
-                    acc[3] += w * (vy * s1);
+                    if constexpr (CH < 0) {
+                        const R s0 = s[t], s1 = s[T + t];
+                        acc[0] += w * (vx * s0);
+                        acc[1] += w * (vy * s0);
+                        acc[2] += w * (vx * s1);
+                        acc[3] += w * (vy * s1);
+                    } else {
+                        const R sk = s[t];
+                        acc[0] += w * (vx * sk);
+                        acc[1] += w * (vy * sk);
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int m = 0; m < 4; ++m) A[m * N + node] = OUT(double(acc[m]) * scale);
+        for (int m = 0; m < NC; ++m) A[m * N + node] = OUT(double(acc[m]) * scale);
     }
 }
 
@@ -265,34 +278,40 @@ static int build_bins(const GridH &g, int64_t T, const R *r, const Bins &b, cuda
 
 template <typename R, typename AT>
 static int launch_interp(const GridH &g, int64_t T, const R *r, const R *v, const AT *A, R *s,
-                         cudaStream_t st)
+                         cudaStream_t st, int ch = -1)
 {
     if (T == 0) return MPI_OK;
     const AxisMap ax = make_axis(g.x0, g.dx, g.nx), ay = make_axis(g.y0, g.dy, g.ny);
-    k_interp<R, AT><<<grid_blocks(T), 256, 0, st>>>(T, r, v, A, ax, ay, s);
+    if (ch < 0) k_interp<R, AT, -1><<<grid_blocks(T), 256, 0, st>>>(T, r, v, A, ax, ay, s);
+    else if (ch == 0) k_interp<R, AT, 0><<<grid_blocks(T), 256, 0, st>>>(T, r, v, A, ax, ay, s);
+    else k_interp<R, AT, 1><<<grid_blocks(T), 256, 0, st>>>(T, r, v, A, ax, ay, s);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
 
 template <typename R, typename OUT>
 static int launch_interp_T(const GridH &g, int64_t T, const R *r, const R *v, const R *s,
-                           const Bins &b, OUT *A, double scale, cudaStream_t st)
+                           const Bins &b, OUT *A, double scale, cudaStream_t st, int ch = -1)
 {
     const AxisMap ax = make_axis(g.x0, g.dx, g.nx), ay = make_axis(g.y0, g.dy, g.ny);
     const int64_t N = (int64_t)g.nx * g.ny;
-    k_interp_T<R, OUT><<<grid_blocks(N), 256, 0, st>>>(r, v, s, T, ax, ay, b.ncx, b.ncy, b.offset,
-                                                      b.list, A, scale);
+    if (ch < 0)
+        k_interp_T<R, OUT, -1><<<grid_blocks(N), 256, 0, st>>>(r, v, s, T, ax, ay, b.ncx, b.ncy, b.offset,
+                                                              b.list, A, scale);
+    else
+        k_interp_T<R, OUT, 0><<<grid_blocks(N), 256, 0, st>>>(r, v, s, T, ax, ay, b.ncx, b.ncy, b.offset,
+                                                             b.list, A, scale);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
 
 // --- Laplacian and the Core Stage operator ---------------------------------
 
-// out_m = Lap x_m for the 4 components (replicated boundary), FP64.
-__global__ void k_lap4(int nx, int ny, const double *__restrict__ x, double *__restrict__ out)
+// out_m = Lap x_m for the nc components (replicated boundary), FP64.
+__global__ void k_lap(int nx, int ny, int nc, const double *__restrict__ x, double *__restrict__ out)
 {
     const int64_t N = (int64_t)nx * ny;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 4 * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * N;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = e / N, k = e % N;
         const int i = (int)(k % nx), j = (int)(k / nx);
@@ -332,13 +351,17 @@ __global__ void k_norm_thresh(const double *__restrict__ part, int n, double tol
     }
 }
 
+// Ahat and its trace (both channels: A_00 + A_11; one channel k: A_kk,
+// which is component k of the stored pair (A_k0, A_k1)).
 template <typename R>
-__global__ void k_grid_output(int64_t N, const double *__restrict__ x, R *__restrict__ A, R *__restrict__ tr)
+__global__ void k_grid_output(int64_t N, int ch, const double *__restrict__ x, R *__restrict__ A,
+                              R *__restrict__ tr)
 {
+    const int nc = ch < 0 ? 4 : 2;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
          e += (int64_t)gridDim.x * blockDim.x) {
-        for (int m = 0; m < 4; ++m) A[m * N + e] = R(x[m * N + e]);
-        tr[e] = R(x[e] + x[3 * N + e]);
+        for (int m = 0; m < nc; ++m) A[m * N + e] = R(x[m * N + e]);
+        tr[e] = ch < 0 ? R(x[e] + x[3 * N + e]) : R(x[ch * N + e]);
     }
 }
 
@@ -347,14 +370,16 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
                      void *Ahat, void *trace, int *n_iter_out, cudaStream_t st)
 {
     const int64_t T = tr->T;
-    const int64_t N = (int64_t)g.nx * g.ny, n4 = 4 * N;
+    const int ch = o.channel - 1;  // -1: both channels; 0 / 1: that channel only
+    const int nc = ch < 0 ? 4 : 2;
+    const int64_t N = (int64_t)g.nx * g.ny, n4 = nc * N;
     const int nblk = vec_blocks(n4);
     const R *r = static_cast<const R *>(tr->r), *v = static_cast<const R *>(tr->v);
     const R *s = static_cast<const R *>(s_in);
 
     Scratch scr(st);
     const size_t o_bins = scr.reserve(bins_bytes(T, g.nx, g.ny));
-    const size_t o_s = scr.reserve(sizeof(R) * 2 * std::max<int64_t>(T, 1));
+    const size_t o_s = scr.reserve(sizeof(R) * (ch < 0 ? 2 : 1) * std::max<int64_t>(T, 1));
     const size_t vb = sizeof(double) * n4;
     const size_t o_b = scr.reserve(vb), o_x = scr.reserve(vb), o_r = scr.reserve(vb),
                  o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_y = scr.reserve(vb),
@@ -374,7 +399,7 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     MPI_TRY(build_bins<R>(g, T, r, bins, st));
     const double invT = T > 0 ? 1.0 / double(T) : 0.0;
     // b = (1/T) M^T s
-    MPI_TRY((launch_interp_T<R, double>(g, T, r, v, s, bins, b, invT, st)));
+    MPI_TRY((launch_interp_T<R, double>(g, T, r, v, s, bins, b, invT, st, ch)));
     MPI_TRY_CUDA(cudaMemsetAsync(x, 0, vb, st));
     MPI_TRY_CUDA(cudaMemsetAsync(q, 0, vb, st));
     MPI_TRY_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 + sizeof(int) * 8, st));
@@ -395,11 +420,11 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     const int poll = 16;
     for (int it = 0; it < o.max_iter; ++it) {
         // q = (1/T) M^T M p + gamma Lap Lap p
-        MPI_TRY((launch_interp<R, double>(g, T, r, v, p, s_tmp, st)));
-        MPI_TRY((launch_interp_T<R, double>(g, T, r, v, s_tmp, bins, y, invT, st)));
-        k_lap4<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, p, l1);
+        MPI_TRY((launch_interp<R, double>(g, T, r, v, p, s_tmp, st, ch)));
+        MPI_TRY((launch_interp_T<R, double>(g, T, r, v, s_tmp, bins, y, invT, st, ch)));
+        k_lap<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, nc, p, l1);
         MPI_CHECK_LAUNCH();
-        k_lap4<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, l1, l2);
+        k_lap<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, nc, l1, l2);
         MPI_CHECK_LAUNCH();
         k_grid_epilogue<<<nblk, kEpiThreads, 0, st>>>(n4, y, l2, o.gamma, p, q, pq_part);
         MPI_CHECK_LAUNCH();
@@ -412,7 +437,7 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
         }
     }
     const int vgrid = grid_blocks(N);
-    k_grid_output<R><<<vgrid, 256, 0, st>>>(N, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
+    k_grid_output<R><<<vgrid, 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
     MPI_CHECK_LAUNCH();
     if (n_iter_out) {
         int hi = 0;
@@ -487,7 +512,7 @@ int mpi_grid(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype, c
 {
     MPI_TRY(check_interp_args(grid, traj, dtype));
     if (!opts || !(opts->gamma >= 0.0) || !std::isfinite(opts->gamma) || opts->max_iter < 0 ||
-        std::isnan(opts->rel_tol)) {
+        std::isnan(opts->rel_tol) || opts->channel < 0 || opts->channel > 2) {
         set_error("invalid Core Stage options");
         return MPI_ERR_INVALID;
     }

@@ -272,7 +272,7 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
         S.sA = scr.at<R>(o_sA);
         MPI_TRY(prepare_geometry<R>(m, g, S.T, tr->r, tr->v, S.geo, st));
     } else {
-        MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &S.K, st));
+        MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &S.K, st, o.kernel_component - 1));
         S.tmp1 = scr.at<R>(o_t1);
         S.tmp2 = scr.at<R>(o_t2);
     }
@@ -351,13 +351,14 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
 }
 
 template <typename R>
-static int conv_impl(const ModelH &m, const GridH &g, const void *in, void *out, cudaStream_t st)
+static int conv_impl(const ModelH &m, const GridH &g, const void *in, void *out, cudaStream_t st,
+                     int comp = -1)
 {
     Scratch scr(st);
     const size_t o_K = scr.reserve(conv_kernel_bytes(g.nx, g.ny, sizeof(R)));
     MPI_TRY(scr.allocate());
     R *K = nullptr;
-    MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &K, st));
+    MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &K, st, comp));
     return launch_conv<R, R, R>(g, K, static_cast<const R *>(in), static_cast<R *>(out), st);
 }
 
@@ -385,7 +386,8 @@ int mpi_pnp_solve(const mpi_model *model, const mpi_grid_desc *grid, const mpi_t
     }
     if (opts->op == MPI_OP_FORWARD) MPI_TRY(check_traj(traj));
     if (opts->n_iter < 0 || opts->n_cg < 0 || !(opts->nu0 >= 0.0) || !std::isfinite(opts->nu0) ||
-        !(opts->clip_pct <= 100.0) || std::isnan(opts->clip_pct)) {
+        !(opts->clip_pct <= 100.0) || std::isnan(opts->clip_pct) || opts->kernel_component < 0 ||
+        opts->kernel_component > 4) {
         set_error("invalid PnP options (n_iter %d, n_cg %d, nu0 %g, clip_pct %g)", opts->n_iter,
                   opts->n_cg, opts->nu0, opts->clip_pct);
         return MPI_ERR_INVALID;
@@ -412,6 +414,20 @@ int mpi_conv(const mpi_model *model, const mpi_grid_desc *grid, mpi_dtype dtype,
     const GridH g = to_host(grid);
     return dtype == MPI_F32 ? conv_impl<float>(m, g, in, out, as_stream(stream))
                             : conv_impl<double>(m, g, in, out, as_stream(stream));
+}
+
+int mpi_conv_component(const mpi_model *model, const mpi_grid_desc *grid, mpi_dtype dtype,
+                       int component, const void *in, void *out, void *stream)
+{
+    MPI_TRY(check_model(model));
+    MPI_TRY(check_grid(grid));
+    MPI_TRY(check_dtype(dtype));
+    if (component < -1 || component > 3) { set_error("component must be in [-1, 3]"); return MPI_ERR_INVALID; }
+    if (!in || !out || in == out) { set_error("in/out NULL or aliased"); return MPI_ERR_INVALID; }
+    const ModelH m = to_host(model);
+    const GridH g = to_host(grid);
+    return dtype == MPI_F32 ? conv_impl<float>(m, g, in, out, as_stream(stream), component)
+                            : conv_impl<double>(m, g, in, out, as_stream(stream), component);
 }
 
 int mpi_denoise_gaussian5(const void *in, void *out, int nx, int ny, mpi_dtype dtype,

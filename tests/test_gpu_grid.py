@@ -82,3 +82,51 @@ def test_core_stage_tolerance_fp64(orc):
     err = rel_l2(host(u), want_u)
     print(f"core stage gamma=1e-7: {n} CG steps, rel-L2 {err:.2e}, sensitivity bound {bound:.2e}")
     assert err <= bound
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("k", [0, 1])
+def test_core_stage_single_channel(orc, dt, k):
+    """Sec. 3.6: only channel k measured.  The two components (A_k0, A_k1)
+    and the diagonal A_kk after a fixed number of CG steps match the oracle's
+    single-channel Core Stage."""
+    cfg = syn.small(19, 17, 1500, seed=11 + k)
+    g, m = cfg["grid"], cfg["model"]
+    r, v, c = (rounded(cfg[key], dt) for key in ("r", "v", "c"))
+    s_k = rounded(orc.forward(m, g, r, v, c)[k], dt)
+    gamma = 1e-4
+    want, want_kk, hist = orc.core_stage_channel(g, r, v, s_k, k, gamma, max_iter=25)
+    A, akk, n = api.mpi_grid(g, dev(r, dt), dev(v, dt), dev(s_k, dt), gamma=gamma, max_iter=25,
+                             rel_tol=0.0, return_iters=True, channel=k)
+    assert A.shape == (2, 17, 19)
+    assert n == len(hist) - 1
+    assert rel_l2(host(A), want) <= tol(dt)
+    assert rel_l2(host(akk), want_kk) <= tol(dt)
+
+
+def test_core_stage_single_channel_tolerance(orc):
+    """Single channel at the paper's parameters (gamma = 1e-7, rel. tol 1e-3),
+    FP64: same stopping step as the oracle; result within the oracle's own
+    one-ulp sensitivity (times 20, never below the 1e-12 bar)."""
+    dt = torch.float64
+    cfg = syn.small(24, 24, 3000, seed=21)
+    g, m = cfg["grid"], cfg["model"]
+    r, v, c = cfg["r"], cfg["v"], cfg["c"]
+    s_k = orc.forward(m, g, r, v, c)[0]
+    want, want_kk, hist = orc.core_stage_channel(g, r, v, s_k, 0, 1e-7, 10000, rel_tol=1e-3)
+    ulp = np.random.default_rng(1).choice([-1.0, 1.0], size=s_k.shape) * np.spacing(np.abs(s_k))
+    _, pert_kk, hist_p = orc.core_stage_channel(g, r, v, s_k + ulp, 0, 1e-7, 10000, rel_tol=1e-3)
+    assert len(hist_p) == len(hist)
+    bound = max(1e-12, 20 * rel_l2(pert_kk, want_kk))
+    _, akk, n = api.mpi_grid(g, dev(r, dt), dev(v, dt), dev(s_k, dt), gamma=1e-7, max_iter=10000,
+                             rel_tol=1e-3, return_iters=True, channel=0)
+    assert n == len(hist) - 1
+    assert rel_l2(host(akk), want_kk) <= bound
+
+
+def test_core_stage_channel_rejects_bad_selector():
+    g = syn.square_grid(4, 8.0)
+    r = torch.zeros((3, 2), dtype=torch.float64, device="cuda")
+    s = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(api.MPIError):
+        api.mpi_grid(g, r, r, s, max_iter=1, channel=2)

@@ -153,3 +153,46 @@ def test_conv_non_diagonal_gradient(orc):
     x = np.random.default_rng(1).normal(size=(13, 21))
     want = orc.conv(g, orc.conv_kernel(m, g), x)
     assert rel_l2(host(api.mpi_conv(m, g, dev(x, dt))), want) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("comp", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_conv_kernel_component(orc, dt, comp):
+    """Entry (a, b) of beta K(beta G y) G as convolution kernel (Sec. 3.6),
+    non-diagonal G so that all four entries differ."""
+    g = syn.square_grid(23, 24.0, 14)
+    m = dict(syn.default_model(), G=[[2.1e-3, 4e-4], [-3e-4, -2.6e-3]])
+    x = rounded(np.random.default_rng(5).normal(size=(14, 23)), dt)
+    want = orc.conv(g, orc.conv_kernel(m, g, component=comp), x)
+    got = api.mpi_conv_component(m, g, 2 * comp[0] + comp[1], dev(x, dt))
+    assert rel_l2(host(got), want) <= tol(dt)
+    tr = api.mpi_conv_component(m, g, -1, dev(x, dt))
+    assert rel_l2(host(tr), orc.conv(g, orc.conv_kernel(m, g), x)) <= tol(dt)
+
+
+def test_pnp_single_channel_deconvolution(orc):
+    """Algorithm 1 on the (0, 0) kernel entry (channel-x data, Sec. 3.6),
+    FP64, few steps so that CG round-off stays at the FP64 bar."""
+    dt = torch.float64
+    g = syn.square_grid(21, 24.0)
+    m = syn.default_model()
+    u = np.random.default_rng(8).normal(size=(21, 21))
+    kern = orc.conv_kernel(m, g, component=(0, 0))
+    op = lambda x: orc.conv(g, kern, x)  # noqa: E731
+    want = orc.pnp(op, op, u, (21, 21), 3, 4, 0.05)
+    got = api.mpi_pnp_solve(m, g, None, None, dev(u, dt), 3, 4, 0.05, op=api.MPI_OP_CONV,
+                            kernel_component=0)
+    assert rel_l2(host(got), want) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_pnp_forward_single_channel(orc, dt):
+    """Algorithm 1 with the direct operator on channel x only (p = [(1, 0)],
+    the partial-data setting of Sec. 3.6): s has one row."""
+    cfg = syn.small(26, 22, 1100, traj="spiral", seed=31)
+    cfg["model"] = dict(cfg["model"], p=[[1.0, 0.0]])
+    m, g, r, v, s, nu0 = _data(orc, cfg, dt)
+    assert s.shape == (1, 1100)
+    want = _oracle_pnp(orc, m, g, r, v, s, 4, 4, nu0)
+    got = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), 4, 4, nu0)
+    assert rel_l2(host(got), want) <= tol(dt)
