@@ -451,3 +451,201 @@ int og_num_threads(void)
     return 1;
 #endif
 }
+
+/* ========================================================================= */
+/* Three-dimensional field-free point (the model of Sec. 2 with n = 3).
+ *
+ * The kernel matrix of Eq. kernel:matrix is stated for y in R^n; with n = 3
+ * it is the 3x3 matrix K(y) = a I + d y y^T with the same scalars a, d.  The
+ * signal of Eq. core:formula becomes
+ *   s_k(t) = sum_{l,j,i} c_lji p_k^T beta K(beta G (x_lji - r_t)) G v_t
+ * for a 3x3 gradient G (the paper's standard choice G = diag(-1, -1, 2) in
+ * units of T/(mu0 m)), r_t, v_t in R^3 and up to three receive directions p_k.
+ * The trace kernel of Eq. kernel:trace carries (n - 1) = 2:
+ *   tr K(y) = L'(|y|) + 2 L(|y|)/|y|.
+ * Voxel centres x_lji = (x0 + (i+1/2)dx, y0 + (j+1/2)dy, z0 + (l+1/2)dz);
+ * arrays are [nz][ny][nx], r and v [T][3], s [n_ch][T].
+ */
+typedef struct {
+    int nx, ny, nz;
+    double x0, y0, z0, dx, dy, dz;
+} og_grid3;
+
+typedef struct {
+    double beta;
+    double G[9];
+    int n_ch;
+    double p[9]; /* p[k*3 + m] */
+} og_model3;
+
+static void og_K3(const double y[3], double K[9])
+{
+    double z = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+    double L, Lp, Lpp, a, d, e;
+    og_langevin6(z, &L, &Lp, &Lpp, &a, &d, &e);
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) K[3 * r + q] = (r == q ? a : 0.0) + d * y[r] * y[q];
+}
+
+void og_kernel_matrix3(int64_t n, const double *y, double *K)
+{
+    og_init_series();
+    for (int64_t k = 0; k < n; ++k) og_K3(&y[3 * k], &K[9 * k]);
+}
+
+static inline void og_voxel_centre3(const og_grid3 *g, int i, int j, int l, double x[3])
+{
+    x[0] = g->x0 + (i + 0.5) * g->dx;
+    x[1] = g->y0 + (j + 0.5) * g->dy;
+    x[2] = g->z0 + (l + 0.5) * g->dz;
+}
+
+static void og_matvec3(const double M[9], const double u[3], double out[3])
+{
+    for (int r = 0; r < 3; ++r) out[r] = M[3 * r] * u[0] + M[3 * r + 1] * u[1] + M[3 * r + 2] * u[2];
+}
+
+/* J w = beta K(beta G (x - r)) G v, as og_pair in three dimensions. */
+static void og_pair3(const og_model3 *m, const double x[3], const double r[3],
+                     const double v[3], double Jw[3])
+{
+    double dxr[3] = {x[0] - r[0], x[1] - r[1], x[2] - r[2]};
+    double H[3], w[3], K[9], Kw[3];
+    og_matvec3(m->G, dxr, H);
+    double y[3] = {m->beta * H[0], m->beta * H[1], m->beta * H[2]};
+    og_matvec3(m->G, v, w);
+    og_K3(y, K);
+    og_matvec3(K, w, Kw);
+    for (int q = 0; q < 3; ++q) Jw[q] = m->beta * Kw[q];
+}
+
+void og_pair3_export(const og_model3 *m, const double *x, const double *r, const double *v,
+                     double *Jw)
+{
+    og_init_series();
+    og_pair3(m, x, r, v, Jw);
+}
+
+static inline double og_pdot3(const og_model3 *m, int k, const double Jw[3])
+{
+    return m->p[3 * k] * Jw[0] + m->p[3 * k + 1] * Jw[1] + m->p[3 * k + 2] * Jw[2];
+}
+
+/* s_k(t) = sum over voxels (l, j, i in row-major order) of c p_k^T J w. */
+void og_forward3(const og_model3 *m, const og_grid3 *g, int64_t T, const double *r,
+                 const double *v, const double *c, double *s)
+{
+    og_init_series();
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < T; ++t) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int l = 0; l < g->nz; ++l)
+            for (int j = 0; j < g->ny; ++j)
+                for (int i = 0; i < g->nx; ++i) {
+                    double x[3], Jw[3];
+                    og_voxel_centre3(g, i, j, l, x);
+                    og_pair3(m, x, &r[3 * t], &v[3 * t], Jw);
+                    double cv = c[((int64_t)l * g->ny + j) * g->nx + i];
+                    for (int k = 0; k < m->n_ch; ++k) acc[k] += cv * og_pdot3(m, k, Jw);
+                }
+        for (int k = 0; k < m->n_ch; ++k) s[(int64_t)k * T + t] = acc[k];
+    }
+}
+
+/* A^T at a list of voxels (flat index (l ny + j) nx + i; all when sel == NULL). */
+void og_adjoint3_sel(const og_model3 *m, const og_grid3 *g, int64_t T, const double *r,
+                     const double *v, const double *s, int64_t n_sel, const int64_t *sel,
+                     double *out)
+{
+    og_init_series();
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < n_sel; ++q) {
+        int64_t idx = sel ? sel[q] : q;
+        int i = (int)(idx % g->nx), j = (int)((idx / g->nx) % g->ny), l = (int)(idx / ((int64_t)g->nx * g->ny));
+        double x[3];
+        og_voxel_centre3(g, i, j, l, x);
+        double acc = 0.0;
+        for (int64_t t = 0; t < T; ++t) {
+            double Jw[3];
+            og_pair3(m, x, &r[3 * t], &v[3 * t], Jw);
+            for (int k = 0; k < m->n_ch; ++k) acc += s[(int64_t)k * T + t] * og_pdot3(m, k, Jw);
+        }
+        out[q] = acc;
+    }
+}
+
+void og_adjoint3(const og_model3 *m, const og_grid3 *g, int64_t T, const double *r,
+                 const double *v, const double *s, double *out)
+{
+    og_adjoint3_sel(m, g, T, r, v, s, (int64_t)g->nx * g->ny * g->nz, NULL, out);
+}
+
+/* ||A||_F^2 = sum over (voxel, sample, channel) of (p_k^T J w)^2. */
+double og_frob2_3(const og_model3 *m, const og_grid3 *g, int64_t T, const double *r,
+                  const double *v)
+{
+    og_init_series();
+    const int64_t N = (int64_t)g->nx * g->ny * g->nz;
+    double tot = 0.0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : tot)
+    for (int64_t idx = 0; idx < N; ++idx) {
+        int i = (int)(idx % g->nx), j = (int)((idx / g->nx) % g->ny), l = (int)(idx / ((int64_t)g->nx * g->ny));
+        double x[3];
+        og_voxel_centre3(g, i, j, l, x);
+        double acc = 0.0;
+        for (int64_t t = 0; t < T; ++t) {
+            double Jw[3];
+            og_pair3(m, x, &r[3 * t], &v[3 * t], Jw);
+            for (int k = 0; k < m->n_ch; ++k) {
+                double e = og_pdot3(m, k, Jw);
+                acc += e * e;
+            }
+        }
+        tot += acc;
+    }
+    return tot;
+}
+
+/* Sampled trace kernel in three dimensions, kappa_G(y) = beta tr(K(beta G y) G)
+ * on all voxel offsets; kern is [(2nz-1)][(2ny-1)][(2nx-1)] with offset 0 at
+ * (nz-1, ny-1, nx-1).  For G = g I it is beta g (L' + 2 L/z), z = beta g |y|:
+ * Eq. kernel:trace with n - 1 = 2. */
+void og_conv_kernel3(const og_model3 *m, const og_grid3 *g, double *kern)
+{
+    og_init_series();
+    int KX = 2 * g->nx - 1, KY = 2 * g->ny - 1, KZ = 2 * g->nz - 1;
+    for (int ll = 0; ll < KZ; ++ll)
+        for (int jj = 0; jj < KY; ++jj)
+            for (int ii = 0; ii < KX; ++ii) {
+                double off[3] = {(ii - (g->nx - 1)) * g->dx, (jj - (g->ny - 1)) * g->dy,
+                                 (ll - (g->nz - 1)) * g->dz};
+                double H[3], K[9];
+                og_matvec3(m->G, off, H);
+                double y[3] = {m->beta * H[0], m->beta * H[1], m->beta * H[2]};
+                og_K3(y, K);
+                /* tr(K G) = sum_{a,c} K_ac G_ca */
+                double tr = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int q = 0; q < 3; ++q) tr += K[3 * a + q] * m->G[3 * q + a];
+                kern[((int64_t)ll * KY + jj) * KX + ii] = m->beta * tr;
+            }
+}
+
+/* Linear (zero-padded) 3-D convolution with the sampled kernel. */
+void og_conv3(const og_grid3 *g, const double *kern, const double *in, double *out)
+{
+    int nx = g->nx, ny = g->ny, nz = g->nz, KX = 2 * nx - 1, KY = 2 * ny - 1;
+#pragma omp parallel for schedule(static)
+    for (int l = 0; l < nz; ++l)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double acc = 0.0;
+                for (int lq = 0; lq < nz; ++lq)
+                    for (int jq = 0; jq < ny; ++jq)
+                        for (int iq = 0; iq < nx; ++iq)
+                            acc += kern[((int64_t)(l - lq + nz - 1) * KY + (j - jq + ny - 1)) * KX +
+                                        (i - iq + nx - 1)] *
+                                   in[((int64_t)lq * ny + jq) * nx + iq];
+                out[((int64_t)l * ny + j) * nx + i] = acc;
+            }
+}

@@ -16,6 +16,8 @@ Parity status per function (what pins each one lives in tests/test_oracle_*):
   langevin, kernel_matrix, pair, forward, adjoint, dbeta, frob2,
   interp, interp_T, laplacian, conv_kernel, conv, conv_fft, cg,
   percentile_clamp, variance, gaussian5, core_stage: pinned.
+  kernel_matrix3, pair3, forward3, adjoint3, frob2_3, conv_kernel3, conv3,
+  gaussian5_3d (three-dimensional FFP): pinned.
   pnp: pinned step by step (identity-operator closed form, Algorithm 1
   bookkeeping); the full reconstruction has no printed example in the paper,
   so its end-to-end values are "parity unpinned" at paper level.
@@ -63,6 +65,17 @@ class _Model(ctypes.Structure):
                 ("n_ch", ctypes.c_int), ("p", ctypes.c_double * 4)]
 
 
+class _Grid3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+class _Model3(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("G", ctypes.c_double * 9),
+                ("n_ch", ctypes.c_int), ("p", ctypes.c_double * 9)]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.c_int64
 
@@ -89,6 +102,15 @@ def _load():
             lib.og_conv_kernel_component.argtypes = [P(_Model), P(_Grid), ctypes.c_int, _D]
             lib.og_conv.argtypes = [P(_Grid), _D, _D, _D]
             lib.og_num_threads.restype = ctypes.c_int
+            lib.og_kernel_matrix3.argtypes = [_I64, _D, _D]
+            lib.og_pair3_export.argtypes = [P(_Model3), _D, _D, _D, _D]
+            lib.og_forward3.argtypes = [P(_Model3), P(_Grid3), _I64, _D, _D, _D, _D]
+            lib.og_adjoint3_sel.argtypes = [P(_Model3), P(_Grid3), _I64, _D, _D, _D, _I64,
+                                            ctypes.POINTER(_I64), _D]
+            lib.og_frob2_3.argtypes = [P(_Model3), P(_Grid3), _I64, _D, _D]
+            lib.og_frob2_3.restype = ctypes.c_double
+            lib.og_conv_kernel3.argtypes = [P(_Model3), P(_Grid3), _D]
+            lib.og_conv3.argtypes = [P(_Grid3), _D, _D, _D]
             _lib = lib
     return _lib
 
@@ -116,6 +138,22 @@ def _model(m) -> _Model:
     pp[: 2 * n_ch] = p.reshape(-1)
     return _Model(float(m["beta"]), (ctypes.c_double * 4)(*G), n_ch,
                   (ctypes.c_double * 4)(*pp))
+
+
+def _grid3(g) -> _Grid3:
+    return _Grid3(int(g["nx"]), int(g["ny"]), int(g["nz"]), float(g["x0"]), float(g["y0"]),
+                  float(g["z0"]), float(g["dx"]), float(g["dy"]), float(g["dz"]))
+
+
+def _model3(m) -> _Model3:
+    G = np.asarray(m["G"], dtype=np.float64).reshape(9)
+    p = np.asarray(m["p"], dtype=np.float64).reshape(-1, 3)
+    n_ch = p.shape[0]
+    if n_ch not in (1, 2, 3):
+        raise ValueError("n_ch must be 1, 2 or 3")
+    pp = np.zeros(9)
+    pp[: 3 * n_ch] = p.reshape(-1)
+    return _Model3(float(m["beta"]), (ctypes.c_double * 9)(*G), n_ch, (ctypes.c_double * 9)(*pp))
 
 
 def num_threads() -> int:
@@ -450,3 +488,100 @@ def core_stage(grid, r, v, s, gamma, max_iter, rel_tol=None):
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+# ---------------------------------------------------------------------------
+# Three-dimensional field-free point (Sec. 2 with n = 3).  A ``grid3`` has
+# nx, ny, nz, x0, y0, z0, dx, dy, dz; a ``model3`` has beta, G (3x3) and p
+# (n_ch x 3).  Concentrations are [nz, ny, nx], r and v [T, 3].
+
+def kernel_matrix3(y) -> np.ndarray:
+    """K(y) of Eq. kernel:matrix for y of shape [..., 3] -> [..., 3, 3]."""
+    y = _f64(y)
+    flat = y.reshape(-1, 3)
+    K = np.empty((flat.shape[0], 9))
+    _load().og_kernel_matrix3(flat.shape[0], _ptr(flat), _ptr(K))
+    return K.reshape(y.shape[:-1] + (3, 3))
+
+
+def pair3(model3, x, r, v) -> np.ndarray:
+    """J w = beta K(beta G(x - r)) G v in three dimensions."""
+    x, r, v = _f64(x), _f64(r), _f64(v)
+    out = np.empty(3)
+    _load().og_pair3_export(ctypes.byref(_model3(model3)), _ptr(x), _ptr(r), _ptr(v), _ptr(out))
+    return out
+
+
+def forward3(model3, grid3, r, v, c) -> np.ndarray:
+    """A c in three dimensions: s[k][t] = sum_x c_x p_k^T J(x, t) w_t."""
+    r, v, c = _f64(r), _f64(v), _f64(c)
+    T = r.shape[0]
+    n_ch = np.asarray(model3["p"]).reshape(-1, 3).shape[0]
+    s = np.empty((n_ch, T))
+    _load().og_forward3(ctypes.byref(_model3(model3)), ctypes.byref(_grid3(grid3)), T,
+                        _ptr(r), _ptr(v), _ptr(c), _ptr(s))
+    return s
+
+
+def adjoint3(model3, grid3, r, v, s, sel=None) -> np.ndarray:
+    """A^T s in three dimensions, on all voxels ([nz, ny, nx]) or on the flat
+    voxel indices ``sel``."""
+    r, v, s = _f64(r), _f64(v), _f64(s)
+    T = r.shape[0]
+    lib = _load()
+    if sel is None:
+        out = np.empty((int(grid3["nz"]), int(grid3["ny"]), int(grid3["nx"])))
+        lib.og_adjoint3_sel(ctypes.byref(_model3(model3)), ctypes.byref(_grid3(grid3)), T,
+                            _ptr(r), _ptr(v), _ptr(s), out.size, None, _ptr(out))
+        return out
+    sel = np.ascontiguousarray(sel, dtype=np.int64)
+    out = np.empty(sel.size)
+    lib.og_adjoint3_sel(ctypes.byref(_model3(model3)), ctypes.byref(_grid3(grid3)), T,
+                        _ptr(r), _ptr(v), _ptr(s), sel.size,
+                        sel.ctypes.data_as(ctypes.POINTER(_I64)), _ptr(out))
+    return out
+
+
+def frob2_3(model3, grid3, r, v) -> float:
+    """||A||_F^2 of the three-dimensional forward operator."""
+    r, v = _f64(r), _f64(v)
+    return float(_load().og_frob2_3(ctypes.byref(_model3(model3)), ctypes.byref(_grid3(grid3)),
+                                    r.shape[0], _ptr(r), _ptr(v)))
+
+
+def conv_kernel3(model3, grid3) -> np.ndarray:
+    """kappa_G(y) = beta tr(K(beta G y) G) on all 3-D voxel offsets,
+    [2nz-1, 2ny-1, 2nx-1] (Eq. kernel:trace with n - 1 = 2)."""
+    out = np.empty((2 * int(grid3["nz"]) - 1, 2 * int(grid3["ny"]) - 1, 2 * int(grid3["nx"]) - 1))
+    _load().og_conv_kernel3(ctypes.byref(_model3(model3)), ctypes.byref(_grid3(grid3)), _ptr(out))
+    return out
+
+
+def conv3(grid3, kern, x) -> np.ndarray:
+    """Direct linear 3-D convolution with the sampled kernel."""
+    kern, x = _f64(kern), _f64(x)
+    out = np.empty_like(x)
+    _load().og_conv3(ctypes.byref(_grid3(grid3)), _ptr(kern), _ptr(x), _ptr(out))
+    return out
+
+
+def gaussian5_3d(vol) -> np.ndarray:
+    """The built-in denoiser on a volume: the 5-tap Gaussian (sigma = 1 voxel,
+    reflect boundary) along x, then y, then z."""
+    vol = _f64(vol)
+    nz, ny, nx = vol.shape
+    w = np.exp(-0.5 * np.arange(-2, 3, dtype=np.float64) ** 2)
+    w /= w.sum()
+    a = np.zeros_like(vol)
+    for i in range(nx):
+        for m in range(-2, 3):
+            a[:, :, i] += w[m + 2] * vol[:, :, _reflect(i + m, nx)]
+    b = np.zeros_like(vol)
+    for j in range(ny):
+        for m in range(-2, 3):
+            b[:, j, :] += w[m + 2] * a[:, _reflect(j + m, ny), :]
+    out = np.zeros_like(vol)
+    for k in range(nz):
+        for m in range(-2, 3):
+            out[k, :, :] += w[m + 2] * b[_reflect(k + m, nz), :, :]
+    return out
