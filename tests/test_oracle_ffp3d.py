@@ -11,6 +11,13 @@ import pytest
 
 mp = pytest.importorskip("mpmath")
 
+
+@pytest.fixture(autouse=True)
+def _mp_precision():
+    """40 significant digits for every mpmath reference here, restored after."""
+    with mp.workdps(40):
+        yield
+
 G3_STD = [[-1.25e-3, 0.0, 0.0], [0.0, -1.25e-3, 0.0], [0.0, 0.0, 2.5e-3]]
 G3_GEN = [[-1.1e-3, 3e-4, -2e-4], [3e-4, -1.4e-3, 1e-4], [-2e-4, 1e-4, 2.3e-3]]
 
@@ -44,7 +51,6 @@ def _mp_M3(H, beta):
 @pytest.mark.parametrize("H", [(3e-4, -1e-4, 2e-4), (2e-3, 5e-3, -1e-3), (1e-6, -2e-6, 5e-7)])
 def test_kernel3_is_jacobian_of_magnetisation(orc, H):
     """beta K(beta H) = d/dH [L(beta|H|) H/|H|] for H in R^3."""
-    mp.mp.dps = 40
     beta = 2331.350896656040
     J = np.zeros((3, 3))
     for b in range(3):
@@ -83,7 +89,6 @@ def test_forward3_is_time_derivative_of_magnetisation(orc, G):
     """s_k(t) = -d/dt sum_x c_x p_k^T L(beta|H|) H/|H|, H = G(x - r(t)), for a
     3-D Lissajous trajectory (mpmath derivative), three channels, the paper's
     G = diag(-1, -1, 2) shape and a general symmetric G."""
-    mp.mp.dps = 40
     grid, model, _, _, c = _tiny3(G=G)
     amp, fr, ph = (2.0, 1.6, 0.9), (0.013, 0.011, 0.007), (0.0, 0.3, 1.1)
 
@@ -160,7 +165,6 @@ def test_forward3_adjoint3_brute_force(orc, n_ch):
 
 def test_pair3_vs_mpmath(orc):
     """J w for a general G against mpmath's Jacobian applied to G v."""
-    mp.mp.dps = 40
     model = {"beta": 600.0, "G": G3_GEN, "p": np.eye(3).tolist()}
     x, r, v = np.array([1.2, -0.4, 0.3]), np.array([-0.3, 0.9, -0.2]), np.array([0.05, -0.02, 0.03])
     G = np.array(G3_GEN)
@@ -179,7 +183,6 @@ def test_pair3_vs_mpmath(orc):
 def test_conv_kernel3_isotropic_closed_form(orc):
     """G = g I: kappa_G(y) = beta g (L'(z) + 2 L(z)/z), z = beta g |y|, the
     trace kernel of Eq. kernel:trace with n - 1 = 2 (2/3 + 1/3 = 1 at y = 0)."""
-    mp.mp.dps = 40
     g, beta = 2.5e-3, 2331.350896656040
     grid = {"nx": 4, "ny": 3, "nz": 3, "x0": 0.0, "y0": 0.0, "z0": 0.0, "dx": 0.4, "dy": 0.5, "dz": 0.3}
     model = {"beta": beta, "G": (g * np.eye(3)).tolist(), "p": np.eye(3).tolist()}

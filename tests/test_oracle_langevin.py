@@ -7,7 +7,13 @@ import numpy as np
 import pytest
 
 mp = pytest.importorskip("mpmath")
-mp.mp.dps = 90
+
+
+@pytest.fixture(autouse=True)
+def _mp_precision():
+    """90 significant digits for every mpmath reference here, restored after."""
+    with mp.workdps(90):
+        yield
 
 
 def _mp_family(z):

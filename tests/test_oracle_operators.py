@@ -13,6 +13,13 @@ from paper_2505_22797_gb300 import synthetic as syn
 mp = pytest.importorskip("mpmath")
 
 
+@pytest.fixture(autouse=True)
+def _mp_precision():
+    """40 significant digits for every mpmath reference here, restored after."""
+    with mp.workdps(40):
+        yield
+
+
 def _tiny(nx=4, ny=3, T=6, seed=0, G=None, p=None, beta=900.0, fov=6.0):
     rng = np.random.default_rng(seed)
     grid = {"nx": nx, "ny": ny, "x0": -fov / 2, "y0": -fov / 2 + 0.3,
@@ -51,7 +58,6 @@ def test_forward_is_time_derivative_of_magnetisation(orc, G):
     (Eq. signal and the time-derivative identity of Sec. 2 with dH/dt = -G r';
     the constant -mu0 m R is dropped as in Eq. core:formula, which leaves the
     minus sign of dH/dt).  Analytic Lissajous trajectory, mpmath derivative."""
-    mp.mp.dps = 40
     grid, model, _, _, c = _tiny(G=G)
     model["p"] = [[1.0, 0.0], [0.0, 1.0]]
     Ax, Ay, fx, fy = 2.5, 2.0, 0.013, 0.011
@@ -169,7 +175,6 @@ def _mp_forward(model, grid, r, v, c, beta):
 def test_dbeta_vs_mpmath_derivative(orc):
     """d/dbeta <g, A(c; beta)> against mpmath's numerical derivative of an
     independent high-precision forward."""
-    mp.mp.dps = 40
     grid, model, r, v, c = _tiny(nx=3, ny=3, T=4, seed=11, beta=700.0)
     gs = np.random.default_rng(4).normal(size=(2, 4))
 
@@ -257,7 +262,6 @@ def test_laplacian_vs_scipy(orc):
 
 def test_conv_kernel_isotropic_closed_form(orc):
     """For G = g I: kappa_G(y) = beta g kappa(beta g |y|), kappa = L' + L/z."""
-    mp.mp.dps = 40
     grid = syn.square_grid(5, 5.0, 4)
     model = syn.default_model()
     g, beta = model["G"][0][0], model["beta"]
