@@ -228,6 +228,62 @@ int mpi_pnp_solve(const mpi_model *model, const mpi_grid_desc *grid,
                   const mpi_pnp_opts *opts, mpi_denoise_fn denoise, void *user,
                   void *rho_out, mpi_pnp_iter_info *info, void *stream);
 
+/* ---- Three-dimensional field-free point (Sec. 2 with n = 3) -------------- */
+
+/* Voxel centres x_lji = (x0 + (i+1/2)dx, y0 + (j+1/2)dy, z0 + (l+1/2)dz);
+ * volumes are row-major [nz][ny][nx]. */
+typedef struct {
+    int nx, ny, nz;
+    double x0, y0, z0;
+    double dx, dy, dz;
+} mpi_grid3_desc;
+
+/* beta = 1/(mu0 H_sat) (Eq. hsat); G the 3x3 selection-field gradient,
+ * row-major (the paper's standard choice is proportional to diag(-1, -1, 2));
+ * p[k*3 + m] the n_ch (1..3) receive directions. */
+typedef struct {
+    double beta;
+    double G[9];
+    int n_ch;
+    double p[9];
+} mpi_model3;
+
+/* Forward operator in three dimensions (Eq. core:formula with the 3x3 kernel
+ * matrix of Eq. kernel:matrix):  s[k][t] = sum_lji c[l][j][i] p_k^T
+ * beta K(beta G(x_lji - r_t)) G v_t.  traj->r and traj->v are [T][3] (dtype of
+ * the call), c is [nz][ny][nx], s is [n_ch][T].  Exact direct sum, reduced
+ * deterministically.  T == 0 is a no-op. */
+int mpi_forward3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_traj *traj,
+                 mpi_dtype dtype, const void *c, void *s, void *stream);
+
+/* Adjoint in three dimensions: c_out[l][j][i] = sum_t sum_k s[k][t] p_k^T
+ * beta K(beta G(x_lji - r_t)) G v_t.  T == 0 writes zeros. */
+int mpi_adjoint3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_traj *traj,
+                 mpi_dtype dtype, const void *s, void *c_out, void *stream);
+
+/* out = C in with the sampled 3-D trace kernel kappa_G(y) = beta tr(K(beta G
+ * y) G) (Eq. kernel:trace with n - 1 = 2), linear (zero-padded) over all
+ * voxel offsets.  in and out [nz][ny][nx], must not overlap. */
+int mpi_conv3(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, const void *in,
+              void *out, void *stream);
+
+/* Volume denoiser callback: as mpi_denoise_fn on [nz][ny][nx]. */
+typedef int (*mpi_denoise3_fn)(const void *in, void *out, int nx, int ny, int nz, mpi_dtype dtype,
+                               const double *sigma_dev, void *stream, void *user);
+
+/* Built-in volume denoiser: the 5-tap Gaussian of mpi_denoise_gaussian5 along
+ * x, then y, then z (reflect boundary).  Allocates one volume of scratch. */
+int mpi_denoise_gaussian5_3d(const void *in, void *out, int nx, int ny, int nz, mpi_dtype dtype,
+                             const double *sigma_dev, void *stream, void *user);
+
+/* Algorithm 1 in three dimensions (the loop of mpi_pnp_solve) with the 3-D
+ * forward operator (data s[n_ch][T]) or the 3-D convolution (data
+ * u[nz][ny][nx]); opts->kernel_component must be 0.  denoise NULL selects
+ * mpi_denoise_gaussian5_3d.  rho_out is [nz][ny][nx]. */
+int mpi_pnp_solve3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_traj *traj,
+                   mpi_dtype dtype, const void *data, const mpi_pnp_opts *opts, mpi_denoise3_fn denoise,
+                   void *user, void *rho_out, mpi_pnp_iter_info *info, void *stream);
+
 /* ---- Batched reconstructions --------------------------------------------- */
 
 /* A plan runs Algorithm 1 with the forward operator (FP32 operator, FP64 CG

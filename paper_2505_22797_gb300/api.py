@@ -63,6 +63,17 @@ class PnPOpts(ctypes.Structure):
                 ("kernel_component", ctypes.c_int)]
 
 
+class Grid3Desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+class Model3(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("G", ctypes.c_double * 9), ("n_ch", ctypes.c_int),
+                ("p", ctypes.c_double * 9)]
+
+
 class PnPIterInfo(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("nu", ctypes.c_double), ("cg_resid", ctypes.c_double)]
 
@@ -82,6 +93,9 @@ MPI_BATCH_MATCH_SINGLE = 2
 DENOISE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p)
+DENOISE3_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p)
 
 _lib = None
 _lock = threading.Lock()
@@ -100,6 +114,13 @@ _SIGS = {
                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mpi_pnp_solve": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
                      + [DENOISE_FN] + [ctypes.c_void_p] * 4,
+    "mpi_forward3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_adjoint3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_conv3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_denoise_gaussian5_3d": [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 4
+                                + [ctypes.c_void_p] * 3,
+    "mpi_pnp_solve3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
+                      + [DENOISE3_FN] + [ctypes.c_void_p] * 4,
     "mpi_batch_plan_create": [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "mpi_batch_pnp_run": [ctypes.c_void_p] * 6,
@@ -177,6 +198,21 @@ def make_grid(grid) -> GridDesc:
                     float(_get(grid, "y0")), float(_get(grid, "dx")), float(_get(grid, "dy")))
 
 
+def make_grid3(grid) -> Grid3Desc:
+    return Grid3Desc(*(int(_get(grid, k)) for k in ("nx", "ny", "nz")),
+                     *(float(_get(grid, k)) for k in ("x0", "y0", "z0", "dx", "dy", "dz")))
+
+
+def make_model3(model) -> Model3:
+    G = [float(x) for row in _get(model, "G") for x in row]
+    P = [[float(x) for x in row] for row in _get(model, "p")]
+    if len(G) != 9 or not 1 <= len(P) <= 3 or any(len(row) != 3 for row in P):
+        raise ValueError("a 3-D model needs G 3x3 and 1..3 receive directions of length 3")
+    flat = [x for row in P for x in row] + [0.0] * (9 - 3 * len(P))
+    return Model3(float(_get(model, "beta")), (ctypes.c_double * 9)(*G), len(P),
+                  (ctypes.c_double * 9)(*flat))
+
+
 def make_model(model) -> Model:
     G = [float(x) for row in _get(model, "G") for x in row]
     P = [[float(x) for x in row] for row in _get(model, "p")]
@@ -208,9 +244,9 @@ def _stream(stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def _traj(r: torch.Tensor, v: torch.Tensor, dt) -> Traj:
-    if r.shape != v.shape or r.dim() != 2 or r.shape[1] != 2:
-        raise ValueError("r and v must both be [T, 2]")
+def _traj(r: torch.Tensor, v: torch.Tensor, dt, dim: int = 2) -> Traj:
+    if r.shape != v.shape or r.dim() != 2 or r.shape[1] != dim:
+        raise ValueError(f"r and v must both be [T, {dim}]")
     T = r.shape[0]
     return Traj(T, _dev(r, dt, "r") if T else None, _dev(v, dt, "v") if T else None)
 
@@ -459,3 +495,94 @@ class BatchPlan:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+# ---------------------------------------------------------------------------
+# Three-dimensional field-free point (Sec. 2 with n = 3).  A ``grid3`` has nx,
+# ny, nz, x0, y0, z0, dx, dy, dz; a ``model3`` has beta, G (3x3) and p (n_ch x
+# 3).  Volumes are [nz, ny, nx]; r and v are [T, 3].
+
+def mpi_forward3(model3, grid3, r, v, c, s=None, stream=None):
+    dt = c.dtype
+    n_ch = len(_get(model3, "p"))
+    if s is None:
+        s = torch.empty((n_ch, r.shape[0]), dtype=dt, device=c.device)
+    tr = _traj(r, v, dt, 3)
+    m, g = make_model3(model3), make_grid3(grid3)
+    _check(load().mpi_forward3(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(c),
+                               _dev(c, dt, "c"), _dev(s, dt, "s") if s.numel() else None,
+                               _stream(stream)))
+    return s
+
+
+def mpi_adjoint3(model3, grid3, r, v, s, c_out=None, stream=None):
+    dt = s.dtype
+    g = make_grid3(grid3)
+    if c_out is None:
+        c_out = torch.empty((g.nz, g.ny, g.nx), dtype=dt, device=s.device)
+    tr = _traj(r, v, dt, 3)
+    m = make_model3(model3)
+    _check(load().mpi_adjoint3(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(s),
+                               _dev(s, dt, "s") if s.numel() else None, _dev(c_out, dt, "c_out"),
+                               _stream(stream)))
+    return c_out
+
+
+def mpi_conv3(model3, grid3, x, out=None, stream=None):
+    dt = x.dtype
+    if out is None:
+        out = torch.empty_like(x)
+    m, g = make_model3(model3), make_grid3(grid3)
+    _check(load().mpi_conv3(ctypes.byref(m), ctypes.byref(g), _dtype(x), _dev(x, dt, "in"),
+                            _dev(out, dt, "out"), _stream(stream)))
+    return out
+
+
+def mpi_denoise_gaussian5_3d(x, out=None, stream=None):
+    dt = x.dtype
+    if out is None:
+        out = torch.empty_like(x)
+    nz, ny, nx = x.shape
+    _check(load().mpi_denoise_gaussian5_3d(_dev(x, dt, "in"), _dev(out, dt, "out"), nx, ny, nz,
+                                           _dtype(x), None, _stream(stream), None))
+    return out
+
+
+def mpi_pnp_solve3(model3, grid3, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, op=MPI_OP_FORWARD,
+                   denoise=None, rho_out=None, with_info=False, stream=None):
+    """Algorithm 1 in three dimensions.  ``denoise`` is None (built-in volume
+    Gaussian) or a callable (in_tensor, out_tensor, sigma_dev_tensor) -> None
+    on [nz, ny, nx] volumes that enqueues on the current stream."""
+    dt = data.dtype
+    g = make_grid3(grid3)
+    if rho_out is None:
+        rho_out = torch.empty((g.nz, g.ny, g.nx), dtype=dt, device=data.device)
+    if op == MPI_OP_FORWARD:
+        tr = _traj(r, v, dt, 3)
+    else:
+        tr = Traj(0, None, None) if r is None else _traj(r, v, dt, 3)
+    m = make_model3(model3)
+    opts = PnPOpts(int(op), int(n_iter), int(n_cg), float(nu0), float(clip_pct), 0)
+    info = (PnPIterInfo * max(1, n_iter))() if with_info else None
+    cb = DENOISE3_FN(0)
+    keep = None
+    if denoise is not None:
+        dev = data.device
+
+        def _cb(pin, pout, nx, ny, nz, dtype, sig, strm, user):
+            try:
+                tdt = torch.float32 if dtype == MPI_F32 else torch.float64
+                denoise(_wrap(pin, (nz, ny, nx), tdt, dev), _wrap(pout, (nz, ny, nx), tdt, dev),
+                        _wrap(sig, (), torch.float64, dev))
+                return 0
+            except Exception:  # noqa: BLE001 - reported as MPI_ERR_CALLBACK
+                return 1
+        cb = DENOISE3_FN(_cb)
+        keep = cb
+    _check(load().mpi_pnp_solve3(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(data),
+                                 _dev(data, dt, "data"), ctypes.byref(opts), cb, None,
+                                 _dev(rho_out, dt, "rho_out"), info, _stream(stream)))
+    del keep
+    if with_info:
+        return rho_out, [(i.sigma, i.nu, i.cg_resid) for i in info[:n_iter]]
+    return rho_out

@@ -1,0 +1,920 @@
+// Three-dimensional field-free point: the model of Sec. 2 with n = 3.
+//
+// The kernel matrix of Eq. kernel:matrix is K(y) = a I + d y y^T with the same
+// scalars a = L/z, d = (L' - a)/z^2 as in two dimensions, now 3 x 3; the
+// signal of Eq. core:formula is
+//   s_k(t) = sum_v c_v p_k^T beta K(beta G (x_v - r_t)) G v_t
+// for a 3 x 3 gradient G (the paper's standard choice is diag(-1, -1, 2)),
+// r_t, v_t in R^3 and up to three receive directions p_k.  The trace kernel of
+// Eq. kernel:trace carries (n - 1) = 2.
+//
+// Kernels:
+//   k_forward3   one work item = 512 samples (4 per thread) x a chunk of
+//                voxels; voxels (prescaled position + concentration) stream
+//                through shared memory 512 at a time; per-chunk partials,
+//                reduced in FP64 in a fixed order.
+//   k_adjoint3   one work item = 1024 voxels (8 per thread) x a chunk of
+//                samples; each staged sample carries (B r, B v, U = sum_k s_k
+//                p_k, U.B v) so a pair costs two dot products.
+//   Both test the near field once per staged pass: the gap between the
+//   bounding box of the pass's prescaled voxel positions and that of the
+//   samples (precomputed per 512 voxels / 256 samples) decides whether the
+//   closed form alone is valid for every pair of the pass.
+//   k_conv3_*    the sampled trace kernel and the direct zero-padded 3-D
+//                convolution (8 x 8 x 4 output tiles).
+//   k_gauss3     the built-in denoiser along one axis (5 taps, reflect).
+// PnP (Algorithm 1) runs the shared driver pnp_run with a 3-D operator.
+#include <algorithm>
+#include <cmath>
+
+#include "langevin.cuh"
+#include "pnp_device.cuh"
+#include "pnp_ops.cuh"
+
+namespace mpi {
+
+int check_traj(const mpi_traj *t);
+int check_dtype(mpi_dtype d);
+
+struct Model3H {
+    double beta;
+    double G[9];
+    int n_ch;
+    double p[9];
+};
+struct Grid3H {
+    int nx, ny, nz;
+    double x0, y0, z0, dx, dy, dz;
+    __host__ __device__ int64_t n() const { return (int64_t)nx * ny * nz; }
+};
+struct Mat3 {
+    double a[9];
+};
+
+constexpr int k3Threads = 128;
+constexpr int k3FwdS = 4;                        // samples per thread (forward)
+constexpr int k3FwdTile = k3Threads * k3FwdS;    // samples per forward work item
+constexpr int k3Piece = 512;                     // voxels per staged pass / per voxel box
+constexpr int k3AdjV = 8;                        // voxels per thread (adjoint)
+constexpr int k3AdjTile = k3Threads * k3AdjV;    // voxels per adjoint work item
+constexpr int k3Batch = 256;                     // samples per staged pass / per sample box
+static_assert(k3FwdTile % k3Batch == 0 && k3AdjTile % k3Piece == 0, "box tiling");
+
+// Prepared geometry of one 3-D problem (device scratch):
+//   rs[t] = B r_t, ws[t] = B v_t, vox[v] = B x_v  (B = beta G; w unused)
+//   sbox / vbox: (lo, hi) of rs over each k3Batch samples / of vox over each
+//   k3Piece voxels.
+template <typename R>
+struct Geo3 {
+    V4<R> *rs, *ws, *vox, *sbox, *vbox;
+};
+
+__host__ __device__ inline int64_t n_boxes(int64_t n, int per) { return (n + per - 1) / per; }
+
+template <typename R>
+static size_t geo3_bytes(int64_t T, int64_t N)
+{
+    const size_t e = sizeof(V4<R>);
+    return e * (2 * T + N + 2 * n_boxes(T, k3Batch) + 2 * n_boxes(N, k3Piece)) + 5 * 256;
+}
+
+template <typename R>
+static Geo3<R> geo3_carve(void *base, int64_t T, int64_t N)
+{
+    char *p = static_cast<char *>(base);
+    auto take = [&](int64_t n) {
+        V4<R> *q = reinterpret_cast<V4<R> *>(p);
+        p += (sizeof(V4<R>) * n + 255) & ~size_t(255);
+        return q;
+    };
+    Geo3<R> g;
+    g.rs = take(T);
+    g.ws = take(T);
+    g.vox = take(N);
+    g.sbox = take(2 * n_boxes(T, k3Batch));
+    g.vbox = take(2 * n_boxes(N, k3Piece));
+    return g;
+}
+
+template <typename R, typename IN>
+__global__ void k_prep3_samples(int64_t T, const IN *__restrict__ r, const IN *__restrict__ v, Mat3 B,
+                                V4<R> *__restrict__ rs, V4<R> *__restrict__ ws)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double rr[3] = {double(r[3 * t]), double(r[3 * t + 1]), double(r[3 * t + 2])};
+        const double vv[3] = {double(v[3 * t]), double(v[3 * t + 1]), double(v[3 * t + 2])};
+        double br[3], bv[3];
+        for (int q = 0; q < 3; ++q) {
+            br[q] = B.a[3 * q] * rr[0] + B.a[3 * q + 1] * rr[1] + B.a[3 * q + 2] * rr[2];
+            bv[q] = B.a[3 * q] * vv[0] + B.a[3 * q + 1] * vv[1] + B.a[3 * q + 2] * vv[2];
+        }
+        rs[t] = V4<R>{R(br[0]), R(br[1]), R(br[2]), R(0)};
+        ws[t] = V4<R>{R(bv[0]), R(bv[1]), R(bv[2]), R(0)};
+    }
+}
+
+template <typename R>
+__global__ void k_prep3_voxels(Grid3H g, Mat3 B, V4<R> *__restrict__ vox)
+{
+    const int64_t N = g.n();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % g.nx), j = (int)((e / g.nx) % g.ny), l = (int)(e / ((int64_t)g.nx * g.ny));
+        const double x[3] = {g.x0 + (i + 0.5) * g.dx, g.y0 + (j + 0.5) * g.dy, g.z0 + (l + 0.5) * g.dz};
+        double bx[3];
+        for (int q = 0; q < 3; ++q) bx[q] = B.a[3 * q] * x[0] + B.a[3 * q + 1] * x[1] + B.a[3 * q + 2] * x[2];
+        vox[e] = V4<R>{R(bx[0]), R(bx[1]), R(bx[2]), R(0)};
+    }
+}
+
+// One warp per box: lo/hi of pts[b*per, min(n, (b+1)*per)).
+template <typename R>
+__global__ void k_box3(const V4<R> *__restrict__ pts, int64_t n, int per, int64_t n_box,
+                       V4<R> *__restrict__ box)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (b >= n_box) return;
+    const int64_t a0 = b * per, a1 = std::min<int64_t>(n, a0 + per);
+    V4<R> lo = pts[a0], hi = pts[a0];
+    for (int64_t e = a0 + lane; e < a1; e += 32) {
+        const V4<R> q = pts[e];
+        lo.x = min(lo.x, q.x), lo.y = min(lo.y, q.y), lo.z = min(lo.z, q.z);
+        hi.x = max(hi.x, q.x), hi.y = max(hi.y, q.y), hi.z = max(hi.z, q.z);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo.x = min(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+        lo.y = min(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+        lo.z = min(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+        hi.x = max(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+        hi.y = max(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        hi.z = max(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+    }
+    if (lane == 0) {
+        box[2 * b] = lo;
+        box[2 * b + 1] = hi;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void box_union(V4<R> &lo, V4<R> &hi, const V4<R> &l2, const V4<R> &h2)
+{
+    lo.x = min(lo.x, l2.x), lo.y = min(lo.y, l2.y), lo.z = min(lo.z, l2.z);
+    hi.x = max(hi.x, h2.x), hi.y = max(hi.y, h2.y), hi.z = max(hi.z, h2.z);
+}
+
+// Lower bound of u = |P - Q|^2 over P in box a, Q in box b, rounded the way
+// the pair loops round it (same operations, monotone in each component).
+template <typename R>
+__device__ __forceinline__ R box_gap2(const V4<R> &alo, const V4<R> &ahi, const V4<R> &blo,
+                                      const V4<R> &bhi)
+{
+    const R gx = max(R(0), max(alo.x - bhi.x, blo.x - ahi.x));
+    const R gy = max(R(0), max(alo.y - bhi.y, blo.y - ahi.y));
+    const R gz = max(R(0), max(alo.z - bhi.z, blo.z - ahi.z));
+    return fmx(gz, gz, fmx(gy, gy, gx * gx));
+}
+
+template <typename R>
+__device__ __forceinline__ bool far_field(R gap2)
+{
+    return gap2 >= Lang<R>::near_u * R(1.0001);
+}
+
+// ---------------------------------------------------------------------------
+// Forward operator.
+
+template <typename R, typename CIN>
+struct Fwd3Args {
+    const V4<R> *rs, *ws, *vox, *sbox, *vbox;
+    const CIN *c;
+    R *part;
+    int64_t T, N, chunk_len;
+    int n_tiles, n_ch;
+    R p[9];
+};
+
+template <typename R, bool FAR>
+__device__ __forceinline__ void fwd3_pass(const V4<R> *sv, int cnt, const R (&Rx)[k3FwdS],
+                                          const R (&Ry)[k3FwdS], const R (&Rz)[k3FwdS],
+                                          const R (&Wx)[k3FwdS], const R (&Wy)[k3FwdS],
+                                          const R (&Wz)[k3FwdS], R (&sa)[k3FwdS], R (&Sx)[k3FwdS],
+                                          R (&Sy)[k3FwdS], R (&Sz)[k3FwdS])
+{
+#pragma unroll 2
+    for (int e = 0; e < cnt; ++e) {
+        const V4<R> P = sv[e];
+#pragma unroll
+        for (int s = 0; s < k3FwdS; ++s) {
+            const R yx = P.x - Rx[s], yy = P.y - Ry[s], yz = P.z - Rz[s];
+            const R u = fmx(yz, yz, fmx(yy, yy, yx * yx));
+            R a, d;
+            if constexpr (FAR) lang_far<R, false>(u, a, d);
+            else lang_checked<R, false>(u, a, d);
+            const R yW = fmx(yz, Wz[s], fmx(yy, Wy[s], yx * Wx[s]));
+            const R t = (P.w * d) * yW;
+            Sx[s] = fmx(t, yx, Sx[s]);
+            Sy[s] = fmx(t, yy, Sy[s]);
+            Sz[s] = fmx(t, yz, Sz[s]);
+            sa[s] = fmx(P.w, a, sa[s]);
+        }
+    }
+}
+
+template <typename R, typename CIN>
+__global__ void __launch_bounds__(k3Threads, sizeof(R) == 4 ? 4 : 2)
+k_forward3(const __grid_constant__ Fwd3Args<R, CIN> a)
+{
+    __shared__ V4<R> sv[k3Piece];
+    const int tile = (int)(blockIdx.x % a.n_tiles);
+    const int64_t chunk = blockIdx.x / a.n_tiles;
+    const int64_t t0 = (int64_t)tile * k3FwdTile;
+    R Rx[k3FwdS], Ry[k3FwdS], Rz[k3FwdS], Wx[k3FwdS], Wy[k3FwdS], Wz[k3FwdS];
+    R sa[k3FwdS], Sx[k3FwdS], Sy[k3FwdS], Sz[k3FwdS];
+#pragma unroll
+    for (int s = 0; s < k3FwdS; ++s) {
+        const int64_t t = std::min<int64_t>(t0 + threadIdx.x + s * k3Threads, a.T - 1);
+        const V4<R> r = a.rs[t], w = a.ws[t];
+        Rx[s] = r.x, Ry[s] = r.y, Rz[s] = r.z;
+        Wx[s] = w.x, Wy[s] = w.y, Wz[s] = w.z;
+        sa[s] = Sx[s] = Sy[s] = Sz[s] = R(0);
+    }
+    // bounding box of this item's samples
+    const int64_t nb = n_boxes(a.T, k3Batch);
+    const int64_t b0 = t0 / k3Batch;
+    V4<R> slo = a.sbox[2 * b0], shi = a.sbox[2 * b0 + 1];
+    for (int64_t b = b0 + 1; b < std::min<int64_t>(nb, b0 + k3FwdTile / k3Batch); ++b)
+        box_union(slo, shi, a.sbox[2 * b], a.sbox[2 * b + 1]);
+
+    const int64_t v0 = chunk * a.chunk_len, v1 = std::min<int64_t>(a.N, v0 + a.chunk_len);
+    for (int64_t vp = v0; vp < v1; vp += k3Piece) {
+        const int cnt = (int)std::min<int64_t>(k3Piece, v1 - vp);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt; e += k3Threads) {
+            V4<R> P = a.vox[vp + e];
+            P.w = R(a.c[vp + e]);
+            sv[e] = P;
+        }
+        __syncthreads();
+        const int64_t pb = vp / k3Piece;
+        if (far_field(box_gap2(a.vbox[2 * pb], a.vbox[2 * pb + 1], slo, shi)))
+            fwd3_pass<R, true>(sv, cnt, Rx, Ry, Rz, Wx, Wy, Wz, sa, Sx, Sy, Sz);
+        else
+            fwd3_pass<R, false>(sv, cnt, Rx, Ry, Rz, Wx, Wy, Wz, sa, Sx, Sy, Sz);
+    }
+    // s_k = p_k^T (W sum c a + sum c d (y.W) y)
+#pragma unroll
+    for (int s = 0; s < k3FwdS; ++s) {
+        const int64_t t = t0 + threadIdx.x + s * k3Threads;
+        if (t >= a.T) continue;
+        const R ox = fmx(Wx[s], sa[s], Sx[s]), oy = fmx(Wy[s], sa[s], Sy[s]), oz = fmx(Wz[s], sa[s], Sz[s]);
+        for (int k = 0; k < a.n_ch; ++k)
+            a.part[(chunk * a.n_ch + k) * a.T + t] = fmx(a.p[3 * k + 2], oz, fmx(a.p[3 * k + 1], oy, a.p[3 * k] * ox));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint operator.
+
+template <typename R>
+struct Adj3Args {
+    const V4<R> *rs, *ws, *vox, *sbox, *vbox;
+    const R *s;
+    R *part;
+    int64_t T, N, chunk_len;
+    int n_vt, n_ch;
+    R p[9];
+};
+
+template <typename R, bool FAR>
+__device__ __forceinline__ void adj3_pass(const V4<R> *sR, const V4<R> *sW, const V4<R> *sU, int cnt,
+                                          const R (&Px)[k3AdjV], const R (&Py)[k3AdjV],
+                                          const R (&Pz)[k3AdjV], R (&acc)[k3AdjV])
+{
+#pragma unroll 1
+    for (int e = 0; e < cnt; ++e) {
+        const V4<R> Q = sR[e], W = sW[e], U = sU[e];
+#pragma unroll
+        for (int m = 0; m < k3AdjV; ++m) {
+            const R yx = Px[m] - Q.x, yy = Py[m] - Q.y, yz = Pz[m] - Q.z;
+            const R u = fmx(yz, yz, fmx(yy, yy, yx * yx));
+            R a, d;
+            if constexpr (FAR) lang_far<R, false>(u, a, d);
+            else lang_checked<R, false>(u, a, d);
+            const R yU = fmx(yz, U.z, fmx(yy, U.y, yx * U.x));
+            const R yW = fmx(yz, W.z, fmx(yy, W.y, yx * W.x));
+            // U^T K W = a (U.W) + d (y.U)(y.W)
+            acc[m] = fmx(d * yU, yW, fmx(a, W.w, acc[m]));
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(k3Threads, sizeof(R) == 4 ? 4 : 2)
+k_adjoint3(const __grid_constant__ Adj3Args<R> a)
+{
+    __shared__ V4<R> sR[k3Batch], sW[k3Batch], sU[k3Batch];
+    const int vt = (int)(blockIdx.x % a.n_vt);
+    const int64_t chunk = blockIdx.x / a.n_vt;
+    const int64_t vbase = (int64_t)vt * k3AdjTile;
+    R Px[k3AdjV], Py[k3AdjV], Pz[k3AdjV], acc[k3AdjV];
+#pragma unroll
+    for (int m = 0; m < k3AdjV; ++m) {
+        const int64_t v = std::min<int64_t>(vbase + threadIdx.x + m * k3Threads, a.N - 1);
+        const V4<R> P = a.vox[v];
+        Px[m] = P.x, Py[m] = P.y, Pz[m] = P.z;
+        acc[m] = R(0);
+    }
+    const int64_t npb = n_boxes(a.N, k3Piece);
+    const int64_t p0 = vbase / k3Piece;
+    V4<R> vlo = a.vbox[2 * p0], vhi = a.vbox[2 * p0 + 1];
+    for (int64_t b = p0 + 1; b < std::min<int64_t>(npb, p0 + k3AdjTile / k3Piece); ++b)
+        box_union(vlo, vhi, a.vbox[2 * b], a.vbox[2 * b + 1]);
+
+    const int64_t tb0 = chunk * a.chunk_len, tb1 = std::min<int64_t>(a.T, tb0 + a.chunk_len);
+    for (int64_t tb = tb0; tb < tb1; tb += k3Batch) {
+        const int cnt = (int)std::min<int64_t>(k3Batch, tb1 - tb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt; e += k3Threads) {
+            const int64_t t = tb + e;
+            const V4<R> Q = a.rs[t], W = a.ws[t];
+            R ux = R(0), uy = R(0), uz = R(0);
+            for (int k = 0; k < a.n_ch; ++k) {
+                const R sk = a.s[k * a.T + t];
+                ux = fmx(sk, a.p[3 * k], ux);
+                uy = fmx(sk, a.p[3 * k + 1], uy);
+                uz = fmx(sk, a.p[3 * k + 2], uz);
+            }
+            sR[e] = Q;
+            sW[e] = V4<R>{W.x, W.y, W.z, fmx(uz, W.z, fmx(uy, W.y, ux * W.x))};
+            sU[e] = V4<R>{ux, uy, uz, R(0)};
+        }
+        __syncthreads();
+        const int64_t sb = tb / k3Batch;
+        if (far_field(box_gap2(vlo, vhi, a.sbox[2 * sb], a.sbox[2 * sb + 1])))
+            adj3_pass<R, true>(sR, sW, sU, cnt, Px, Py, Pz, acc);
+        else
+            adj3_pass<R, false>(sR, sW, sU, cnt, Px, Py, Pz, acc);
+    }
+#pragma unroll
+    for (int m = 0; m < k3AdjV; ++m) {
+        const int64_t v = vbase + threadIdx.x + m * k3Threads;
+        if (v < a.N) a.part[chunk * a.N + v] = acc[m];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side of the pair operators.
+
+struct Split3 {
+    int n_tiles;        // forward: sample tiles; adjoint: voxel tiles
+    int64_t chunk_len;  // forward: voxels per chunk; adjoint: samples per chunk
+    int n_chunks;
+};
+
+static Split3 split3(int64_t n_tiled, int tile, int64_t n_chunked, int align, int target)
+{
+    Split3 s;
+    s.n_tiles = (int)std::max<int64_t>(1, (n_tiled + tile - 1) / tile);
+    const int64_t want = std::max<int64_t>(1, (target + s.n_tiles - 1) / s.n_tiles);
+    int64_t len = (std::max<int64_t>(n_chunked, 1) + want - 1) / want;
+    len = std::max<int64_t>(align, (len + align - 1) / align * align);
+    s.chunk_len = len;
+    s.n_chunks = (int)std::max<int64_t>(1, (n_chunked + len - 1) / len);
+    return s;
+}
+
+template <typename R>
+struct Op3 {
+    Model3H m;
+    Grid3H g;
+    int64_t T = 0, N = 0;
+    Geo3<R> geo{};
+    Split3 fs{}, as{};
+    R *fwd_part = nullptr, *adj_part = nullptr;
+
+    size_t scratch_bytes() const
+    {
+        return geo3_bytes<R>(T, N) + sizeof(R) * (size_t(fs.n_chunks) * m.n_ch * T + 256) +
+               sizeof(R) * (size_t(as.n_chunks) * N + 256) + 512;
+    }
+    void plan(const Model3H &mm, const Grid3H &gg, int64_t TT)
+    {
+        m = mm;
+        g = gg;
+        T = TT;
+        N = gg.n();
+        const int target = default_target_items();
+        fs = split3(T, k3FwdTile, N, k3Piece, target);
+        as = split3(N, k3AdjTile, T, k3Batch, target);
+    }
+    void carve(char *base)
+    {
+        geo = geo3_carve<R>(base, T, N);
+        char *p = base + ((geo3_bytes<R>(T, N) + 255) & ~size_t(255));
+        fwd_part = reinterpret_cast<R *>(p);
+        p += (sizeof(R) * (size_t(fs.n_chunks) * m.n_ch * T + 256) + 255) & ~size_t(255);
+        adj_part = reinterpret_cast<R *>(p);
+    }
+    Mat3 bmat() const
+    {
+        Mat3 B;
+        for (int q = 0; q < 9; ++q) B.a[q] = m.beta * m.G[q];
+        return B;
+    }
+    template <typename IN>
+    int prepare(const IN *r, const IN *v, cudaStream_t st)
+    {
+        const Mat3 B = bmat();
+        if (T > 0) {
+            k_prep3_samples<R, IN><<<(unsigned)std::min<int64_t>((T + 255) / 256, 4096), 256, 0, st>>>(
+                T, r, v, B, geo.rs, geo.ws);
+            MPI_CHECK_LAUNCH();
+            const int64_t nb = n_boxes(T, k3Batch);
+            k_box3<R><<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(geo.rs, T, k3Batch, nb, geo.sbox);
+            MPI_CHECK_LAUNCH();
+        }
+        k_prep3_voxels<R><<<(unsigned)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, st>>>(g, B, geo.vox);
+        MPI_CHECK_LAUNCH();
+        const int64_t np = n_boxes(N, k3Piece);
+        k_box3<R><<<(unsigned)((np * 32 + 255) / 256), 256, 0, st>>>(geo.vox, N, k3Piece, np, geo.vbox);
+        MPI_CHECK_LAUNCH();
+        return MPI_OK;
+    }
+    template <typename CIN, typename OUT>
+    int forward(const CIN *c, OUT *s, cudaStream_t st)
+    {
+        if (T == 0) return MPI_OK;
+        Fwd3Args<R, CIN> a;
+        a.rs = geo.rs, a.ws = geo.ws, a.vox = geo.vox, a.sbox = geo.sbox, a.vbox = geo.vbox;
+        a.c = c;
+        a.part = fwd_part;
+        a.T = T, a.N = N, a.chunk_len = fs.chunk_len;
+        a.n_tiles = fs.n_tiles, a.n_ch = m.n_ch;
+        for (int q = 0; q < 9; ++q) a.p[q] = R(m.p[q]);
+        {
+            ProfScope prof(kProfForward, st);
+            k_forward3<R, CIN><<<(unsigned)((int64_t)fs.n_tiles * fs.n_chunks), k3Threads, 0, st>>>(a);
+            MPI_CHECK_LAUNCH();
+        }
+        return reduce_chunks<R, OUT>(fwd_part, fs.n_chunks, (int64_t)m.n_ch * T, s, nullptr, nullptr,
+                                     nullptr, st);
+    }
+    // out = A^T s; with cg_p: out = A^T s + nu cg_p and partial sums of <cg_p, out>.
+    template <typename OUT>
+    int adjoint(const R *s, OUT *out, const double *cg_p, const double *nu_dev, double *dot_part,
+                cudaStream_t st)
+    {
+        int nch = as.n_chunks;
+        if (T > 0) {
+            Adj3Args<R> a;
+            a.rs = geo.rs, a.ws = geo.ws, a.vox = geo.vox, a.sbox = geo.sbox, a.vbox = geo.vbox;
+            a.s = s;
+            a.part = adj_part;
+            a.T = T, a.N = N, a.chunk_len = as.chunk_len;
+            a.n_vt = as.n_tiles, a.n_ch = m.n_ch;
+            for (int q = 0; q < 9; ++q) a.p[q] = R(m.p[q]);
+            ProfScope prof(kProfAdjoint, st);
+            k_adjoint3<R><<<(unsigned)((int64_t)as.n_tiles * as.n_chunks), k3Threads, 0, st>>>(a);
+            MPI_CHECK_LAUNCH();
+        } else {
+            MPI_TRY_CUDA(cudaMemsetAsync(adj_part, 0, sizeof(R) * N, st));
+            nch = 1;
+        }
+        return reduce_chunks<R, OUT>(adj_part, nch, N, out, cg_p, nu_dev, dot_part, st);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Convolution with the 3-D sampled trace kernel.
+
+constexpr int kC3x = 8, kC3y = 8, kC3z = 4;  // output / input tile
+constexpr int kC3Kx = 2 * kC3x - 1, kC3Ky = 2 * kC3y - 1, kC3Kz = 2 * kC3z - 1;
+
+// kappa_G(o) = beta tr(K(beta G o) G) = beta (a tr G + d y^T G y), y = beta G o.
+__global__ void k_conv3_kernel_sample(Grid3H g, double beta, Mat3 G, double *__restrict__ K)
+{
+    const int KX = 2 * g.nx - 1, KY = 2 * g.ny - 1, KZ = 2 * g.nz - 1;
+    const int64_t n = (int64_t)KX * KY * KZ;
+    const double trG = G.a[0] + G.a[4] + G.a[8];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ii = (int)(e % KX), jj = (int)((e / KX) % KY), ll = (int)(e / ((int64_t)KX * KY));
+        const double o[3] = {(ii - (g.nx - 1)) * g.dx, (jj - (g.ny - 1)) * g.dy, (ll - (g.nz - 1)) * g.dz};
+        double y[3];
+        for (int q = 0; q < 3; ++q) y[q] = beta * (G.a[3 * q] * o[0] + G.a[3 * q + 1] * o[1] + G.a[3 * q + 2] * o[2]);
+        double a, d;
+        lang_checked<double, false>(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], a, d);
+        double yGy = 0.0;
+        for (int q = 0; q < 3; ++q)
+            yGy += y[q] * (G.a[3 * q] * y[0] + G.a[3 * q + 1] * y[1] + G.a[3 * q + 2] * y[2]);
+        K[e] = beta * (a * trG + d * yGy);
+    }
+}
+
+template <typename R>
+__global__ void k_round3(const double *__restrict__ in, R *__restrict__ out, int64_t n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = R(in[e]);
+}
+
+static size_t conv3_kernel_bytes(const Grid3H &g, int elem)
+{
+    return size_t(2 * g.nx - 1) * size_t(2 * g.ny - 1) * size_t(2 * g.nz - 1) * (sizeof(double) + elem) + 512;
+}
+
+template <typename R>
+static int conv3_prepare(const Model3H &m, const Grid3H &g, void *scratch, R **K_out, cudaStream_t st)
+{
+    const int64_t n = (int64_t)(2 * g.nx - 1) * (2 * g.ny - 1) * (2 * g.nz - 1);
+    double *K64 = static_cast<double *>(scratch);
+    Mat3 G;
+    for (int q = 0; q < 9; ++q) G.a[q] = m.G[q];
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    k_conv3_kernel_sample<<<blocks, 256, 0, st>>>(g, m.beta, G, K64);
+    MPI_CHECK_LAUNCH();
+    if constexpr (sizeof(R) == sizeof(double)) {
+        *K_out = reinterpret_cast<R *>(K64);
+    } else {
+        R *K = reinterpret_cast<R *>(static_cast<char *>(scratch) + ((sizeof(double) * n + 255) & ~size_t(255)));
+        k_round3<R><<<blocks, 256, 0, st>>>(K64, K, n);
+        MPI_CHECK_LAUNCH();
+        *K_out = K;
+    }
+    return MPI_OK;
+}
+
+// out = C in over all voxel offsets; one 8 x 8 x 4 output tile per block,
+// input walked in tiles of the same shape with the matching kernel window in
+// shared memory; per-tile sums folded with compensated additions.
+template <typename R, typename IN, typename OUT>
+__global__ void __launch_bounds__(kC3x *kC3y *kC3z)
+k_conv3_direct(int nx, int ny, int nz, const R *__restrict__ K, const IN *__restrict__ in,
+               OUT *__restrict__ out)
+{
+    __shared__ R s_in[kC3z][kC3y][kC3x];
+    __shared__ R s_k[kC3Kz][kC3Ky][kC3Kx + 1];
+    const int tx = threadIdx.x % kC3x, ty = (threadIdx.x / kC3x) % kC3y, tz = threadIdx.x / (kC3x * kC3y);
+    const int i0 = blockIdx.x * kC3x, j0 = blockIdx.y * kC3y, l0 = blockIdx.z * kC3z;
+    const int i = i0 + tx, j = j0 + ty, l = l0 + tz;
+    const int KX = 2 * nx - 1, KY = 2 * ny - 1;
+    R acc = R(0), comp = R(0);
+    for (int lq0 = 0; lq0 < nz; lq0 += kC3z)
+        for (int jq0 = 0; jq0 < ny; jq0 += kC3y)
+            for (int iq0 = 0; iq0 < nx; iq0 += kC3x) {
+                __syncthreads();
+                {
+                    const int iq = iq0 + tx, jq = jq0 + ty, lq = lq0 + tz;
+                    s_in[tz][ty][tx] = (iq < nx && jq < ny && lq < nz)
+                                           ? R(in[((int64_t)lq * ny + jq) * nx + iq]) : R(0);
+                }
+                for (int e = threadIdx.x; e < kC3Kx * kC3Ky * kC3Kz; e += kC3x * kC3y * kC3z) {
+                    const int ex = e % kC3Kx, ey = (e / kC3Kx) % kC3Ky, ez = e / (kC3Kx * kC3Ky);
+                    const int oi = i0 - iq0 - (kC3x - 1) + ex;
+                    const int oj = j0 - jq0 - (kC3y - 1) + ey;
+                    const int ol = l0 - lq0 - (kC3z - 1) + ez;
+                    const bool ok = oi > -nx && oi < nx && oj > -ny && oj < ny && ol > -nz && ol < nz;
+                    s_k[ez][ey][ex] = ok ? K[((int64_t)(ol + nz - 1) * KY + (oj + ny - 1)) * KX + (oi + nx - 1)] : R(0);
+                }
+                __syncthreads();
+                R part = R(0);
+                for (int c = 0; c < kC3z; ++c)
+#pragma unroll 2
+                    for (int b = 0; b < kC3y; ++b)
+#pragma unroll
+                        for (int q = 0; q < kC3x; ++q)
+                            part = fmx(s_k[tz - c + kC3z - 1][ty - b + kC3y - 1][tx - q + kC3x - 1], s_in[c][b][q], part);
+                kahan_add(acc, comp, part);
+            }
+    if (i < nx && j < ny && l < nz) out[((int64_t)l * ny + j) * nx + i] = OUT(acc);
+}
+
+template <typename R, typename IN, typename OUT>
+static int launch_conv3(const Grid3H &g, const R *K, const IN *in, OUT *out, cudaStream_t st)
+{
+    dim3 grid((g.nx + kC3x - 1) / kC3x, (g.ny + kC3y - 1) / kC3y, (g.nz + kC3z - 1) / kC3z);
+    ProfScope prof(kProfConv, st);
+    k_conv3_direct<R, IN, OUT><<<grid, kC3x * kC3y * kC3z, 0, st>>>(g.nx, g.ny, g.nz, K, in, out);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Built-in denoiser on a volume: the 5-tap Gaussian along x, then y, then z.
+
+template <typename R>
+__global__ void k_gauss3(const R *__restrict__ in, R *__restrict__ out, int nx, int ny, int nz, int axis,
+                         R w0, R w1, R w2)
+{
+    const int64_t N = (int64_t)nx * ny * nz;
+    const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    const int64_t stride = axis == 0 ? 1 : (axis == 1 ? nx : (int64_t)nx * ny);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)((e / stride) % n);
+        const int64_t base = e - (int64_t)k * stride;
+        const R w[5] = {w2, w1, w0, w1, w2};
+        R acc = R(0);
+#pragma unroll
+        for (int m = -2; m <= 2; ++m) acc = fmx(w[m + 2], in[base + (int64_t)reflect_index(k + m, n) * stride], acc);
+        out[e] = acc;
+    }
+}
+
+template <typename R>
+static int launch_gauss3(const R *in, R *out, R *tmp, int nx, int ny, int nz, cudaStream_t st)
+{
+    double w[3];
+    gauss5_weights(w);
+    const int64_t N = (int64_t)nx * ny * nz;
+    const unsigned blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 8192);
+    k_gauss3<R><<<blocks, 256, 0, st>>>(in, out, nx, ny, nz, 0, R(w[0]), R(w[1]), R(w[2]));
+    MPI_CHECK_LAUNCH();
+    k_gauss3<R><<<blocks, 256, 0, st>>>(out, tmp, nx, ny, nz, 1, R(w[0]), R(w[1]), R(w[2]));
+    MPI_CHECK_LAUNCH();
+    k_gauss3<R><<<blocks, 256, 0, st>>>(tmp, out, nx, ny, nz, 2, R(w[0]), R(w[1]), R(w[2]));
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// PnP (Algorithm 1) with the 3-D operators.
+
+template <typename R>
+struct PnPOp3D final : PnPOperator<R> {
+    mpi_op op;
+    Op3<R> A;
+    Grid3H g;
+    int64_t N = 0;
+    R *sA = nullptr, *K = nullptr, *tmp1 = nullptr, *tmp2 = nullptr, *gtmp = nullptr;
+    mpi_denoise3_fn den = nullptr;
+    void *user = nullptr;
+
+    int rhs(const R *data, double *b0, cudaStream_t st) override
+    {
+        if (op == MPI_OP_FORWARD) return A.template adjoint<double>(data, b0, nullptr, nullptr, nullptr, st);
+        return launch_conv3<R, R, double>(g, K, data, b0, st);
+    }
+    int apply_normal(const double *v, double *q, const double *nu_dev, double *pq_part,
+                     cudaStream_t st) override
+    {
+        if (op == MPI_OP_FORWARD) {
+            MPI_TRY((A.template forward<double, R>(v, sA, st)));
+            return A.template adjoint<double>(sA, q, v, nu_dev, pq_part, st);
+        }
+        MPI_TRY((launch_conv3<R, double, R>(g, K, v, tmp1, st)));
+        MPI_TRY((launch_conv3<R, R, R>(g, K, tmp1, tmp2, st)));
+        return axpy_dot_launch<R>(N, tmp2, v, nu_dev, q, pq_part, st);
+    }
+    int n_pq() const override { return op == MPI_OP_FORWARD ? reduce_dot_blocks(N) : vec_blocks(N); }
+    int denoise(const R *in, R *out, const double *sigma_dev, cudaStream_t st) override
+    {
+        if (den) return den(in, out, g.nx, g.ny, g.nz, sizeof(R) == 4 ? MPI_F32 : MPI_F64, sigma_dev, st, user);
+        return launch_gauss3<R>(in, out, gtmp, g.nx, g.ny, g.nz, st);
+    }
+    bool has_callback() const override { return den != nullptr; }
+};
+
+template <typename R>
+static int pnp3_impl(const Model3H &m, const Grid3H &g, const mpi_traj *tr, const void *data,
+                     const mpi_pnp_opts &o, mpi_denoise3_fn den, void *user, void *rho_out,
+                     mpi_pnp_iter_info *info, cudaStream_t st)
+{
+    PnPOp3D<R> S;
+    S.op = o.op;
+    S.g = g;
+    S.N = g.n();
+    S.den = den;
+    S.user = user;
+    Scratch scr(st);
+    size_t o_A = 0, o_sA = 0, o_K = 0, o_t1 = 0, o_t2 = 0;
+    if (o.op == MPI_OP_FORWARD) {
+        S.A.plan(m, g, tr->T);
+        o_A = scr.reserve(S.A.scratch_bytes());
+        o_sA = scr.reserve(sizeof(R) * size_t(m.n_ch) * size_t(std::max<int64_t>(tr->T, 1)));
+    } else {
+        o_K = scr.reserve(conv3_kernel_bytes(g, sizeof(R)));
+        o_t1 = scr.reserve(sizeof(R) * S.N);
+        o_t2 = scr.reserve(sizeof(R) * S.N);
+    }
+    const size_t o_g = scr.reserve(sizeof(R) * S.N);
+    MPI_TRY(scr.allocate());
+    S.gtmp = scr.at<R>(o_g);
+    if (o.op == MPI_OP_FORWARD) {
+        S.A.carve(scr.at<char>(o_A));
+        S.sA = scr.at<R>(o_sA);
+        MPI_TRY(S.A.prepare(static_cast<const R *>(tr->r), static_cast<const R *>(tr->v), st));
+    } else {
+        MPI_TRY(conv3_prepare<R>(m, g, scr.at<char>(o_K), &S.K, st));
+        S.tmp1 = scr.at<R>(o_t1);
+        S.tmp2 = scr.at<R>(o_t2);
+    }
+    return pnp_run<R>(S, S.N, data, o, rho_out, info, st);
+}
+
+// ---------------------------------------------------------------------------
+// Validation and entry points.
+
+static int check_model3(const mpi_model3 *m)
+{
+    if (!m) { set_error("model is NULL"); return MPI_ERR_INVALID; }
+    if (!(m->beta > 0.0) || !std::isfinite(m->beta)) {
+        set_error("beta must be positive and finite (got %g)", m->beta);
+        return MPI_ERR_INVALID;
+    }
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(m->G[k])) { set_error("G has a non-finite entry"); return MPI_ERR_INVALID; }
+    const double *G = m->G;
+    const double det = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                       G[2] * (G[3] * G[7] - G[4] * G[6]);
+    if (det == 0.0) { set_error("G is singular"); return MPI_ERR_INVALID; }
+    if (m->n_ch < 1 || m->n_ch > 3) {
+        set_error("n_ch must be 1, 2 or 3 (got %d)", m->n_ch);
+        return MPI_ERR_INVALID;
+    }
+    for (int k = 0; k < 3 * m->n_ch; ++k)
+        if (!std::isfinite(m->p[k])) { set_error("p has a non-finite entry"); return MPI_ERR_INVALID; }
+    return MPI_OK;
+}
+
+static int check_grid3(const mpi_grid3_desc *g)
+{
+    if (!g) { set_error("grid is NULL"); return MPI_ERR_INVALID; }
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) {
+        set_error("grid must have nx, ny, nz >= 1 (got %d x %d x %d)", g->nx, g->ny, g->nz);
+        return MPI_ERR_INVALID;
+    }
+    if ((int64_t)g->nx * g->ny * g->nz > (int64_t)1 << 28) {
+        set_error("grid of %d x %d x %d voxels is larger than supported (2^28)", g->nx, g->ny, g->nz);
+        return MPI_ERR_UNSUPPORTED;
+    }
+    const double v[6] = {g->x0, g->y0, g->z0, g->dx, g->dy, g->dz};
+    for (double q : v)
+        if (!std::isfinite(q)) { set_error("grid origin and spacing must be finite"); return MPI_ERR_INVALID; }
+    if (g->dx == 0.0 || g->dy == 0.0 || g->dz == 0.0) {
+        set_error("grid spacing must be nonzero");
+        return MPI_ERR_INVALID;
+    }
+    return MPI_OK;
+}
+
+static Model3H to_host3(const mpi_model3 *m)
+{
+    Model3H h;
+    h.beta = m->beta;
+    for (int k = 0; k < 9; ++k) h.G[k] = m->G[k];
+    h.n_ch = m->n_ch;
+    for (int k = 0; k < 9; ++k) h.p[k] = k < 3 * m->n_ch ? m->p[k] : 0.0;
+    return h;
+}
+static Grid3H to_host3(const mpi_grid3_desc *g)
+{
+    return Grid3H{g->nx, g->ny, g->nz, g->x0, g->y0, g->z0, g->dx, g->dy, g->dz};
+}
+
+template <typename R>
+static int forward3_impl(const Model3H &m, const Grid3H &g, const mpi_traj *tr, const void *c, void *s,
+                         cudaStream_t st)
+{
+    if (tr->T == 0) return MPI_OK;
+    Op3<R> A;
+    A.plan(m, g, tr->T);
+    Scratch scr(st);
+    const size_t o = scr.reserve(A.scratch_bytes());
+    MPI_TRY(scr.allocate());
+    A.carve(scr.at<char>(o));
+    MPI_TRY(A.prepare(static_cast<const R *>(tr->r), static_cast<const R *>(tr->v), st));
+    return A.template forward<R, R>(static_cast<const R *>(c), static_cast<R *>(s), st);
+}
+
+template <typename R>
+static int adjoint3_impl(const Model3H &m, const Grid3H &g, const mpi_traj *tr, const void *s, void *c_out,
+                         cudaStream_t st)
+{
+    Op3<R> A;
+    A.plan(m, g, tr->T);
+    Scratch scr(st);
+    const size_t o = scr.reserve(A.scratch_bytes());
+    MPI_TRY(scr.allocate());
+    A.carve(scr.at<char>(o));
+    MPI_TRY(A.prepare(static_cast<const R *>(tr->r), static_cast<const R *>(tr->v), st));
+    return A.template adjoint<R>(static_cast<const R *>(s), static_cast<R *>(c_out), nullptr, nullptr,
+                                 nullptr, st);
+}
+
+template <typename R>
+static int conv3_impl(const Model3H &m, const Grid3H &g, const void *in, void *out, cudaStream_t st)
+{
+    Scratch scr(st);
+    const size_t o_K = scr.reserve(conv3_kernel_bytes(g, sizeof(R)));
+    MPI_TRY(scr.allocate());
+    R *K = nullptr;
+    MPI_TRY(conv3_prepare<R>(m, g, scr.at<char>(o_K), &K, st));
+    return launch_conv3<R, R, R>(g, K, static_cast<const R *>(in), static_cast<R *>(out), st);
+}
+
+template <typename R>
+static int gauss3_impl(const void *in, void *out, int nx, int ny, int nz, cudaStream_t st)
+{
+    Scratch scr(st);
+    const size_t o_t = scr.reserve(sizeof(R) * (size_t)nx * ny * nz);
+    MPI_TRY(scr.allocate());
+    return launch_gauss3<R>(static_cast<const R *>(in), static_cast<R *>(out), scr.at<R>(o_t), nx, ny, nz, st);
+}
+
+}  // namespace mpi
+
+using namespace mpi;
+
+extern "C" {
+
+int mpi_forward3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_traj *traj,
+                 mpi_dtype dtype, const void *c, void *s, void *stream)
+{
+    MPI_TRY(check_model3(model));
+    MPI_TRY(check_grid3(grid));
+    MPI_TRY(check_traj(traj));
+    MPI_TRY(check_dtype(dtype));
+    if (traj->T > 0 && (!c || !s)) { set_error("c or s is NULL"); return MPI_ERR_INVALID; }
+    const Model3H m = to_host3(model);
+    const Grid3H g = to_host3(grid);
+    return dtype == MPI_F32 ? forward3_impl<float>(m, g, traj, c, s, as_stream(stream))
+                            : forward3_impl<double>(m, g, traj, c, s, as_stream(stream));
+}
+
+int mpi_adjoint3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_traj *traj,
+                 mpi_dtype dtype, const void *s, void *c_out, void *stream)
+{
+    MPI_TRY(check_model3(model));
+    MPI_TRY(check_grid3(grid));
+    MPI_TRY(check_traj(traj));
+    MPI_TRY(check_dtype(dtype));
+    if (!c_out || (traj->T > 0 && !s)) { set_error("s or c_out is NULL"); return MPI_ERR_INVALID; }
+    const Model3H m = to_host3(model);
+    const Grid3H g = to_host3(grid);
+    return dtype == MPI_F32 ? adjoint3_impl<float>(m, g, traj, s, c_out, as_stream(stream))
+                            : adjoint3_impl<double>(m, g, traj, s, c_out, as_stream(stream));
+}
+
+int mpi_conv3(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, const void *in,
+              void *out, void *stream)
+{
+    MPI_TRY(check_model3(model));
+    MPI_TRY(check_grid3(grid));
+    MPI_TRY(check_dtype(dtype));
+    if (!in || !out || in == out) { set_error("in/out NULL or aliased"); return MPI_ERR_INVALID; }
+    const Model3H m = to_host3(model);
+    const Grid3H g = to_host3(grid);
+    return dtype == MPI_F32 ? conv3_impl<float>(m, g, in, out, as_stream(stream))
+                            : conv3_impl<double>(m, g, in, out, as_stream(stream));
+}
+
+int mpi_denoise_gaussian5_3d(const void *in, void *out, int nx, int ny, int nz, mpi_dtype dtype,
+                             const double *sigma_dev, void *stream, void *user)
+{
+    (void)sigma_dev;
+    (void)user;
+    MPI_TRY(check_dtype(dtype));
+    if (nx < 1 || ny < 1 || nz < 1 || !in || !out || in == out) {
+        set_error("invalid denoiser arguments");
+        return MPI_ERR_INVALID;
+    }
+    return dtype == MPI_F32 ? gauss3_impl<float>(in, out, nx, ny, nz, as_stream(stream))
+                            : gauss3_impl<double>(in, out, nx, ny, nz, as_stream(stream));
+}
+
+int mpi_pnp_solve3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_traj *traj,
+                   mpi_dtype dtype, const void *data, const mpi_pnp_opts *opts, mpi_denoise3_fn denoise,
+                   void *user, void *rho_out, mpi_pnp_iter_info *info, void *stream)
+{
+    MPI_TRY(check_model3(model));
+    MPI_TRY(check_grid3(grid));
+    MPI_TRY(check_dtype(dtype));
+    if (!opts) { set_error("opts is NULL"); return MPI_ERR_INVALID; }
+    if (opts->op != MPI_OP_FORWARD && opts->op != MPI_OP_CONV) {
+        set_error("unknown operator %d", (int)opts->op);
+        return MPI_ERR_INVALID;
+    }
+    if (opts->op == MPI_OP_FORWARD) MPI_TRY(check_traj(traj));
+    if (opts->n_iter < 0 || opts->n_cg < 0 || !(opts->nu0 >= 0.0) || !std::isfinite(opts->nu0) ||
+        !(opts->clip_pct <= 100.0) || std::isnan(opts->clip_pct) || opts->kernel_component != 0) {
+        set_error("invalid PnP options (n_iter %d, n_cg %d, nu0 %g, clip_pct %g, kernel_component %d)",
+                  opts->n_iter, opts->n_cg, opts->nu0, opts->clip_pct, opts->kernel_component);
+        return MPI_ERR_INVALID;
+    }
+    if (!rho_out || (!data && !(opts->op == MPI_OP_FORWARD && traj->T == 0))) {
+        set_error("data or rho_out is NULL");
+        return MPI_ERR_INVALID;
+    }
+    const Model3H m = to_host3(model);
+    const Grid3H g = to_host3(grid);
+    return dtype == MPI_F32
+               ? pnp3_impl<float>(m, g, traj, data, *opts, denoise, user, rho_out, info, as_stream(stream))
+               : pnp3_impl<double>(m, g, traj, data, *opts, denoise, user, rho_out, info, as_stream(stream));
+}
+
+}  // extern "C"

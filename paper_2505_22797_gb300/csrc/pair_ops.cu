@@ -177,8 +177,36 @@ k_reduce_chunks(const R *__restrict__ part, int n_chunks, int64_t len, OUT *__re
 }
 
 int adjoint_dot_blocks(int nx, int ny) { return (int)(((int64_t)nx * ny + 31) / 32); }
+int reduce_dot_blocks(int64_t len) { return (int)((len + 31) / 32); }
 
 static unsigned reduce_blocks(int64_t len) { return (unsigned)std::max<int64_t>(1, (len + 31) / 32); }
+
+template <typename R, typename OUT>
+int reduce_chunks(const R *part, int n_chunks, int64_t len, OUT *out, const double *cg_p,
+                  const double *nu_dev, double *dot_part, cudaStream_t st)
+{
+    if (cg_p) {
+        if constexpr (sizeof(OUT) == sizeof(double)) {
+            k_reduce_chunks<R, double, true><<<reduce_blocks(len), kRedThreads, 0, st>>>(
+                part, n_chunks, len, reinterpret_cast<double *>(out), cg_p, nu_dev, dot_part);
+        } else {
+            set_error("internal: CG epilogue needs FP64 output");
+            return MPI_ERR_INVALID;
+        }
+    } else {
+        k_reduce_chunks<R, OUT, false><<<reduce_blocks(len), kRedThreads, 0, st>>>(
+            part, n_chunks, len, out, nullptr, nullptr, nullptr);
+    }
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+template int reduce_chunks<float, float>(const float *, int, int64_t, float *, const double *,
+                                         const double *, double *, cudaStream_t);
+template int reduce_chunks<float, double>(const float *, int, int64_t, double *, const double *,
+                                          const double *, double *, cudaStream_t);
+template int reduce_chunks<double, double>(const double *, int, int64_t, double *, const double *,
+                                           const double *, double *, cudaStream_t);
 
 __global__ void k_sum_fixed(const double *__restrict__ part, int n, double scale,
                             double *__restrict__ out)

@@ -76,6 +76,15 @@ int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
                    const double *nu_dev, double *dot_part, cudaStream_t st);
 int adjoint_dot_blocks(int nx, int ny);
 
+// Reduction of per-chunk partial sums (pair operators): out[e] = sum over
+// chunks of part[c][e] in a fixed order, FP64.  With cg_p the epilogue writes
+// out = sum + nu cg_p (OUT double) and partial sums of <cg_p, out>
+// (reduce_dot_blocks(len) of them) into dot_part.
+template <typename R, typename OUT>
+int reduce_chunks(const R *part, int n_chunks, int64_t len, OUT *out, const double *cg_p,
+                  const double *nu_dev, double *dot_part, cudaStream_t st);
+int reduce_dot_blocks(int64_t len);
+
 // d/dbeta <g, A(c; beta)>: c [ny][nx] (R), g [n_ch][T] (R) -> *out_dev (FP64).
 template <typename R>
 int launch_dbeta(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &geo,

@@ -126,6 +126,19 @@ k_axpy_dot(int64_t N, const R *__restrict__ y, const double *__restrict__ v,
     if (threadIdx.x == 0) dot_part[blockIdx.x] = acc;
 }
 
+template <typename R>
+int axpy_dot_launch(int64_t N, const R *y, const double *v, const double *nu_dev, double *q,
+                    double *dot_part, cudaStream_t st)
+{
+    k_axpy_dot<R><<<vec_blocks(N), kVecThreads, 0, st>>>(N, y, v, nu_dev, q, dot_part);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+template int axpy_dot_launch<float>(int64_t, const float *, const double *, const double *, double *,
+                                    double *, cudaStream_t);
+template int axpy_dot_launch<double>(int64_t, const double *, const double *, const double *, double *,
+                                     double *, cudaStream_t);
+
 __global__ void k_init_scalars(double *scal, double nu0)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -186,59 +199,136 @@ int launch_gauss5(const R *in, R *out, int nx, int ny, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
-// The PnP solve.
+// The PnP solve: one driver (pnp_run) over an operator interface.
 
 template <typename R>
-struct PnPState {
-    // operator
-    mpi_op op;
-    ModelH m;
-    GridH g;
-    int64_t T;
-    Geometry<R> geo;
-    FwdSplit fs;
-    AdjSplit as;
-    R *fwd_part = nullptr, *adj_part = nullptr, *sA = nullptr;
-    R *K = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;
-    // vectors
-    int64_t N;
-    int nblk;
-    int n_pq;  // number of partial sums of <p, q> the operator epilogue writes
-    double *b0, *x, *r, *p, *q, *pq_part, *rr_part[2], *scal, *info;
-    int *done;
-    R *rho1, *rho2;
-};
-
-// q = (O^T O + nu I) v and partial sums of <v, q>.
-template <typename R>
-static int apply_normal(PnPState<R> &S, const double *v, double *q, cudaStream_t st)
+int pnp_run(PnPOperator<R> &op, int64_t N, const void *data, const mpi_pnp_opts &o, void *rho_out,
+            mpi_pnp_iter_info *info, cudaStream_t st)
 {
-    if (S.op == MPI_OP_FORWARD) {
-        MPI_TRY((launch_forward<R, double, R>(S.m, S.g, S.T, S.geo, S.fs, v, S.fwd_part, S.sA, st)));
-        MPI_TRY((launch_adjoint<R, double>(S.m, S.g, S.T, S.geo, S.as, S.sA, S.adj_part, q, v,
-                                           S.scal + kScalNu, S.pq_part, st)));
-    } else {
-        MPI_TRY((launch_conv<R, double, R>(S.g, S.K, v, S.tmp1, st)));
-        MPI_TRY((launch_conv<R, R, R>(S.g, S.K, S.tmp1, S.tmp2, st)));
-        k_axpy_dot<R><<<S.nblk, kVecThreads, 0, st>>>(S.N, S.tmp2, v, S.scal + kScalNu, q, S.pq_part);
+    const int nblk = vec_blocks(N);
+    const int n_pq = op.n_pq();
+    Scratch scr(st);
+    const size_t vb = sizeof(double) * N;
+    const size_t o_b0 = scr.reserve(vb), o_x = scr.reserve(vb), o_r = scr.reserve(vb),
+                 o_p = scr.reserve(vb), o_q = scr.reserve(vb);
+    const size_t o_pq = scr.reserve(sizeof(double) * std::max(nblk, n_pq));
+    const size_t o_rr0 = scr.reserve(sizeof(double) * nblk), o_rr1 = scr.reserve(sizeof(double) * nblk);
+    const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 4);
+    const size_t o_info = scr.reserve(sizeof(double) * 3 * std::max(o.n_iter, 1));
+    const size_t o_r1 = scr.reserve(sizeof(R) * N), o_r2 = scr.reserve(sizeof(R) * N);
+    MPI_TRY(scr.allocate());
+    double *b0 = scr.at<double>(o_b0), *x = scr.at<double>(o_x), *r = scr.at<double>(o_r),
+           *p = scr.at<double>(o_p), *q = scr.at<double>(o_q), *pq_part = scr.at<double>(o_pq);
+    double *rr_part[2] = {scr.at<double>(o_rr0), scr.at<double>(o_rr1)};
+    double *scal = scr.at<double>(o_sc), *inf = scr.at<double>(o_info);
+    int *done = reinterpret_cast<int *>(scal + 8);
+    R *rho1 = scr.at<R>(o_r1), *rho2 = scr.at<R>(o_r2);
+
+    // b0 = O^T data
+    MPI_TRY(op.rhs(static_cast<const R *>(data), b0, st));
+    k_init_scalars<<<1, 32, 0, st>>>(scal, o.nu0);
+    MPI_CHECK_LAUNCH();
+
+    const bool fault_cb = getenv("MPI_FAULT") && strcmp(getenv("MPI_FAULT"), "callback") == 0;
+    const int vgrid = (int)std::min<int64_t>((N + 255) / 256, 4096);
+    for (int k = 0; k < o.n_iter; ++k) {
+        // rho1 <- CG(O^T O + nu I, O^T data + nu rho2, x0 = rho2), n_cg steps
+        k_set_x<R><<<vgrid, 256, 0, st>>>(N, k == 0 ? nullptr : rho2, x);
         MPI_CHECK_LAUNCH();
+        MPI_TRY(op.apply_normal(x, q, scal + kScalNu, pq_part, st));
+        MPI_TRY(cg_init_launch(N, b0, x, q, scal + kScalNu, r, p, rr_part[0], done, st));
+        for (int i = 0; i < o.n_cg; ++i) {
+            MPI_TRY(op.apply_normal(p, q, scal + kScalNu, pq_part, st));
+            MPI_TRY(cg_step_launch(N, x, r, p, q, pq_part, n_pq, rr_part[i & 1], rr_part[(i + 1) & 1],
+                                   done, nullptr, nullptr, st));
+        }
+        // trimming, sigma, lambda (k = 0), nu
+        k_outer_stats<R><<<1, kStatThreads, 0, st>>>(N, x, o.clip_pct >= 0.0 ? 1 : 0, o.clip_pct, k,
+                                                    o.nu0, scal, rr_part[o.n_cg & 1], nblk,
+                                                    inf + 3 * k, rho1);
+        MPI_CHECK_LAUNCH();
+        R *dst = (k == o.n_iter - 1) ? static_cast<R *>(rho_out) : rho2;
+        const int rc = fault_cb ? 1 : op.denoise(rho1, dst, scal + kScalSigma, st);
+        if (rc != 0) {
+            if (op.has_callback() || fault_cb) {
+                set_error("denoiser callback returned %d at iteration %d", rc, k);
+                return MPI_ERR_CALLBACK;
+            }
+            return rc;
+        }
+    }
+    if (o.n_iter == 0) MPI_TRY_CUDA(cudaMemsetAsync(rho_out, 0, sizeof(R) * N, st));
+    if (info) {
+        std::vector<double> h(3 * std::max(o.n_iter, 1));
+        MPI_TRY_CUDA(cudaMemcpyAsync(h.data(), inf, sizeof(double) * 3 * o.n_iter,
+                                     cudaMemcpyDeviceToHost, st));
+        MPI_TRY_CUDA(cudaStreamSynchronize(st));
+        for (int k = 0; k < o.n_iter; ++k) {
+            info[k].sigma = h[3 * k];
+            info[k].nu = h[3 * k + 1];
+            info[k].cg_resid = h[3 * k + 2];
+        }
     }
     return MPI_OK;
 }
+
+// The 2-D operators: A (direct pair sums over the trajectory) or C (the
+// sampled-kernel convolution), and the 2-D denoiser.
+template <typename R>
+struct PnPOp2D final : PnPOperator<R> {
+    mpi_op op;
+    ModelH m;
+    GridH g;
+    int64_t T = 0;
+    Geometry<R> geo{};
+    FwdSplit fs{};
+    AdjSplit as{};
+    R *fwd_part = nullptr, *adj_part = nullptr, *sA = nullptr;
+    R *K = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;
+    int64_t N = 0;
+    mpi_denoise_fn den = nullptr;
+    void *user = nullptr;
+
+    int rhs(const R *data, double *b0, cudaStream_t st) override
+    {
+        if (op == MPI_OP_FORWARD)
+            return launch_adjoint<R, double>(m, g, T, geo, as, data, adj_part, b0, nullptr, nullptr,
+                                             nullptr, st);
+        return launch_conv<R, R, double>(g, K, data, b0, st);
+    }
+    int apply_normal(const double *v, double *q, const double *nu_dev, double *pq_part,
+                     cudaStream_t st) override
+    {
+        if (op == MPI_OP_FORWARD) {
+            MPI_TRY((launch_forward<R, double, R>(m, g, T, geo, fs, v, fwd_part, sA, st)));
+            return launch_adjoint<R, double>(m, g, T, geo, as, sA, adj_part, q, v, nu_dev, pq_part, st);
+        }
+        MPI_TRY((launch_conv<R, double, R>(g, K, v, tmp1, st)));
+        MPI_TRY((launch_conv<R, R, R>(g, K, tmp1, tmp2, st)));
+        return axpy_dot_launch<R>(N, tmp2, v, nu_dev, q, pq_part, st);
+    }
+    int n_pq() const override { return op == MPI_OP_FORWARD ? adjoint_dot_blocks(g.nx, g.ny) : vec_blocks(N); }
+    int denoise(const R *in, R *out, const double *sigma_dev, cudaStream_t st) override
+    {
+        if (den) return den(in, out, g.nx, g.ny, sizeof(R) == 4 ? MPI_F32 : MPI_F64, sigma_dev, st, user);
+        return launch_gauss5<R>(in, out, g.nx, g.ny, st);
+    }
+    bool has_callback() const override { return den != nullptr; }
+};
 
 template <typename R>
 static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const void *data,
                     const mpi_pnp_opts &o, mpi_denoise_fn den, void *user, void *rho_out,
                     mpi_pnp_iter_info *info, cudaStream_t st)
 {
-    PnPState<R> S;
+    PnPOp2D<R> S;
     S.op = o.op;
     S.m = m;
     S.g = g;
     S.T = (o.op == MPI_OP_FORWARD) ? tr->T : 0;
     S.N = (int64_t)g.nx * g.ny;
-    S.nblk = vec_blocks(S.N);
-    S.n_pq = (o.op == MPI_OP_FORWARD) ? adjoint_dot_blocks(g.nx, g.ny) : S.nblk;
+    S.den = den;
+    S.user = user;
     const int target = default_target_items();
 
     Scratch scr(st);
@@ -255,16 +345,7 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
         o_t1 = scr.reserve(sizeof(R) * S.N);
         o_t2 = scr.reserve(sizeof(R) * S.N);
     }
-    const size_t vb = sizeof(double) * S.N;
-    const size_t o_b0 = scr.reserve(vb), o_x = scr.reserve(vb), o_r = scr.reserve(vb),
-                 o_p = scr.reserve(vb), o_q = scr.reserve(vb);
-    const size_t o_pq = scr.reserve(sizeof(double) * std::max(S.nblk, S.n_pq));
-    const size_t o_rr0 = scr.reserve(sizeof(double) * S.nblk), o_rr1 = scr.reserve(sizeof(double) * S.nblk);
-    const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 4);
-    const size_t o_info = scr.reserve(sizeof(double) * 3 * std::max(o.n_iter, 1));
-    const size_t o_r1 = scr.reserve(sizeof(R) * S.N), o_r2 = scr.reserve(sizeof(R) * S.N);
     MPI_TRY(scr.allocate());
-
     if (S.op == MPI_OP_FORWARD) {
         S.geo = geometry_carve<R>(scr.at<char>(o_geo), S.T, g.nx, g.ny);
         S.fwd_part = scr.at<R>(o_fp);
@@ -276,78 +357,7 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
         S.tmp1 = scr.at<R>(o_t1);
         S.tmp2 = scr.at<R>(o_t2);
     }
-    S.b0 = scr.at<double>(o_b0);
-    S.x = scr.at<double>(o_x);
-    S.r = scr.at<double>(o_r);
-    S.p = scr.at<double>(o_p);
-    S.q = scr.at<double>(o_q);
-    S.pq_part = scr.at<double>(o_pq);
-    S.rr_part[0] = scr.at<double>(o_rr0);
-    S.rr_part[1] = scr.at<double>(o_rr1);
-    S.scal = scr.at<double>(o_sc);
-    S.done = reinterpret_cast<int *>(S.scal + 8);
-    S.info = scr.at<double>(o_info);
-    S.rho1 = scr.at<R>(o_r1);
-    S.rho2 = scr.at<R>(o_r2);
-
-    // b0 = O^T data
-    if (S.op == MPI_OP_FORWARD) {
-        MPI_TRY((launch_adjoint<R, double>(m, g, S.T, S.geo, S.as, static_cast<const R *>(data),
-                                           S.adj_part, S.b0, nullptr, nullptr, nullptr, st)));
-    } else {
-        MPI_TRY((launch_conv<R, R, double>(g, S.K, static_cast<const R *>(data), S.b0, st)));
-    }
-    k_init_scalars<<<1, 32, 0, st>>>(S.scal, o.nu0);
-    MPI_CHECK_LAUNCH();
-
-    const bool fault_cb = getenv("MPI_FAULT") && strcmp(getenv("MPI_FAULT"), "callback") == 0;
-    const int vgrid = (int)std::min<int64_t>((S.N + 255) / 256, 4096);
-    for (int k = 0; k < o.n_iter; ++k) {
-        k_set_x<R><<<vgrid, 256, 0, st>>>(S.N, k == 0 ? nullptr : S.rho2, S.x);
-        MPI_CHECK_LAUNCH();
-        MPI_TRY(apply_normal(S, S.x, S.q, st));
-        MPI_TRY(cg_init_launch(S.N, S.b0, S.x, S.q, S.scal + kScalNu, S.r, S.p, S.rr_part[0],
-                               S.done, st));
-        for (int i = 0; i < o.n_cg; ++i) {
-            MPI_TRY(apply_normal(S, S.p, S.q, st));
-            MPI_TRY(cg_step_launch(S.N, S.x, S.r, S.p, S.q, S.pq_part, S.n_pq, S.rr_part[i & 1],
-                                   S.rr_part[(i + 1) & 1], S.done, nullptr, nullptr, st));
-        }
-        k_outer_stats<R><<<1, kStatThreads, 0, st>>>(S.N, S.x, o.clip_pct >= 0.0 ? 1 : 0, o.clip_pct,
-                                                    k, o.nu0, S.scal, S.rr_part[o.n_cg & 1], S.nblk,
-                                                    S.info + 3 * k, S.rho1);
-        MPI_CHECK_LAUNCH();
-        R *dst = (k == o.n_iter - 1) ? static_cast<R *>(rho_out) : S.rho2;
-        const mpi_dtype dt = sizeof(R) == 4 ? MPI_F32 : MPI_F64;
-        int rc;
-        if (fault_cb) {
-            rc = 1;
-        } else if (den) {
-            rc = den(S.rho1, dst, g.nx, g.ny, dt, S.scal + kScalSigma, st, user);
-        } else {
-            rc = launch_gauss5<R>(S.rho1, dst, g.nx, g.ny, st);
-        }
-        if (rc != 0) {
-            if (den || fault_cb) {
-                set_error("denoiser callback returned %d at iteration %d", rc, k);
-                return MPI_ERR_CALLBACK;
-            }
-            return rc;
-        }
-    }
-    if (o.n_iter == 0) MPI_TRY_CUDA(cudaMemsetAsync(rho_out, 0, sizeof(R) * S.N, st));
-    if (info) {
-        std::vector<double> h(3 * std::max(o.n_iter, 1));
-        MPI_TRY_CUDA(cudaMemcpyAsync(h.data(), S.info, sizeof(double) * 3 * o.n_iter,
-                                     cudaMemcpyDeviceToHost, st));
-        MPI_TRY_CUDA(cudaStreamSynchronize(st));
-        for (int k = 0; k < o.n_iter; ++k) {
-            info[k].sigma = h[3 * k];
-            info[k].nu = h[3 * k + 1];
-            info[k].cg_resid = h[3 * k + 2];
-        }
-    }
-    return MPI_OK;
+    return pnp_run<R>(S, S.N, data, o, rho_out, info, st);
 }
 
 template <typename R>
@@ -364,6 +374,10 @@ static int conv_impl(const ModelH &m, const GridH &g, const void *in, void *out,
 
 template int launch_gauss5<float>(const float *, float *, int, int, cudaStream_t);
 template int launch_gauss5<double>(const double *, double *, int, int, cudaStream_t);
+template int pnp_run<float>(PnPOperator<float> &, int64_t, const void *, const mpi_pnp_opts &, void *,
+                            mpi_pnp_iter_info *, cudaStream_t);
+template int pnp_run<double>(PnPOperator<double> &, int64_t, const void *, const mpi_pnp_opts &, void *,
+                             mpi_pnp_iter_info *, cudaStream_t);
 
 }  // namespace mpi
 

@@ -32,4 +32,37 @@ int cg_step_launch(int64_t N, double *x, double *r, double *p, const double *q,
 template <typename R>
 int launch_gauss5(const R *in, R *out, int nx, int ny, cudaStream_t st);
 
+// q = y + nu v and vec_blocks(N) partial sums of <v, q> (the epilogue of
+// operators without a fused one).
+template <typename R>
+int axpy_dot_launch(int64_t N, const R *y, const double *v, const double *nu_dev, double *q,
+                    double *dot_part, cudaStream_t st);
+
+// The data-fidelity operator O of one ZeroShot-PnP solve (Algorithm 1): the
+// solve driver below is written against this interface, so the 2-D operators
+// (A, the convolution C) and the 3-D ones share one loop.  Every method only
+// enqueues on `st`.
+template <typename R>
+struct PnPOperator {
+    virtual ~PnPOperator() = default;
+    // b0 = O^T data (FP64, N values).
+    virtual int rhs(const R *data, double *b0, cudaStream_t st) = 0;
+    // q = (O^T O + nu I) v and `n_pq()` partial sums of <v, q> in pq_part.
+    virtual int apply_normal(const double *v, double *q, const double *nu_dev, double *pq_part,
+                             cudaStream_t st) = 0;
+    virtual int n_pq() const = 0;
+    // The denoiser step (Algorithm 1, "Denoise"): the built-in Gaussian or a
+    // user callback; returns the callback's status (nonzero = failure).
+    virtual int denoise(const R *in, R *out, const double *sigma_dev, cudaStream_t st) = 0;
+    virtual bool has_callback() const = 0;
+};
+
+// Algorithm 1 with operator O on N unknowns and the data of O's range (type
+// R): rho_out (R, N values), optional
+// per-iteration (sigma, nu, CG residual) in info.
+template <typename R>
+int pnp_run(PnPOperator<R> &op, int64_t N, const void *data, const mpi_pnp_opts &o, void *rho_out,
+            mpi_pnp_iter_info *info, cudaStream_t st);
+
+
 }  // namespace mpi

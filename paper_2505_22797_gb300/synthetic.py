@@ -245,3 +245,77 @@ def small(nx: int, ny: int, T: int, traj: str = "lissajous", seed: int = 7,
         c[ny // 2, nx // 2] = 1.0
     return dict(name=f"small_{nx}x{ny}_{T}_{traj}", grid=g, model=m, r=r, v=v, c=c,
                 n_it=3, n_cg=5, noise_frac=0.01, noise_seed=seed + 100, clip_pct=5.0)
+
+
+# ---------------------------------------------------------------------------
+# Three-dimensional field-free point.  The gradient has the paper's shape
+# G = g diag(-1/2, -1/2, 1) (diag(-1, -1, 2) up to scale), g = 2.5 T/m along z,
+# so the field of view along z is half that along x and y for the same drive
+# amplitude in tesla.
+
+def default_model3(beta: float = BETA_1MM, g: float = G_MM, n_ch: int = 3) -> dict:
+    G = [[-0.5 * g, 0.0, 0.0], [0.0, -0.5 * g, 0.0], [0.0, 0.0, g]]
+    p = [[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]][:n_ch]
+    return {"beta": beta, "G": G, "p": p}
+
+
+def box_grid3(nx: int, ny: int, nz: int, fov_xy: float = 24.0, fov_z: float = 12.0) -> dict:
+    """Voxel grid centred on the origin: fov_xy x fov_xy x fov_z mm."""
+    return {"nx": nx, "ny": ny, "nz": nz, "x0": -fov_xy / 2, "y0": -fov_xy / 2, "z0": -fov_z / 2,
+            "dx": fov_xy / nx, "dy": fov_xy / ny, "dz": fov_z / nz}
+
+
+def lissajous3(T: int, fx: float, fy: float, fz: float, amp=(12.0, 12.0, 6.0)):
+    """r(t) = (ax sin(2 pi fx t/T), ay sin(2 pi fy t/T), az sin(2 pi fz t/T)),
+    the 3-D Lissajous drive; v = dr/dt per sample."""
+    t = np.arange(T, dtype=np.float64)
+    w = [2 * math.pi * f / T for f in (fx, fy, fz)]
+    r = np.stack([amp[q] * np.sin(w[q] * t) for q in range(3)], axis=1)
+    v = np.stack([amp[q] * w[q] * np.cos(w[q] * t) for q in range(3)], axis=1)
+    return r, v
+
+
+def ellipsoids(grid3: dict, rng, n: int | None = None, semi=(1.5, 5.0)) -> np.ndarray:
+    """Seeded phantom of axis-aligned ellipsoids (centres uniform in the
+    central 70 %, semi-axes uniform in `semi` mm, scaled by half along z,
+    values U[0, 1], later ones overwrite)."""
+    xs = grid3["x0"] + (np.arange(grid3["nx"]) + 0.5) * grid3["dx"]
+    ys = grid3["y0"] + (np.arange(grid3["ny"]) + 0.5) * grid3["dy"]
+    zs = grid3["z0"] + (np.arange(grid3["nz"]) + 0.5) * grid3["dz"]
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    fov = [grid3["nx"] * grid3["dx"], grid3["ny"] * grid3["dy"], grid3["nz"] * grid3["dz"]]
+    cen = [grid3["x0"] + fov[0] / 2, grid3["y0"] + fov[1] / 2, grid3["z0"] + fov[2] / 2]
+    if n is None:
+        n = int(rng.integers(3, 7))
+    c = np.zeros((grid3["nz"], grid3["ny"], grid3["nx"]))
+    for _ in range(n):
+        e = [cen[q] + rng.uniform(-0.5, 0.5) * 0.7 * fov[q] for q in range(3)]
+        a, b, h = rng.uniform(*semi), rng.uniform(*semi), 0.5 * rng.uniform(*semi)
+        val = rng.uniform(0, 1)
+        c[((X - e[0]) / a) ** 2 + ((Y - e[1]) / b) ** 2 + ((Z - e[2]) / h) ** 2 <= 1.0] = val
+    return c
+
+
+def config3(name: str = "3d") -> dict:
+    """The 3-D FFP workload: 48 x 48 x 24 voxels over 24 x 24 x 12 mm, a 3-D
+    Lissajous with 17 / 16 / 15 periods per T = 65 536 samples, three
+    channels, 1 % noise."""
+    if name != "3d":
+        raise ValueError(f"unknown 3-D config {name!r}")
+    g = box_grid3(48, 48, 24)
+    r, v = lissajous3(65536, 17, 16, 15)
+    c = ellipsoids(g, np.random.default_rng(106))
+    return dict(name=name, grid=g, model=default_model3(), r=r, v=v, c=c, n_it=20, n_cg=20,
+                noise_frac=0.01, noise_seed=206, clip_pct=5.0)
+
+
+def small3(nx: int, ny: int, nz: int, T: int, seed: int = 9, n_ch: int = 3) -> dict:
+    """A small 3-D case for parity tests."""
+    g = box_grid3(nx, ny, nz)
+    big = T > 60
+    r, v = lissajous3(T, 17 if big else 3, 16 if big else 2, 15 if big else 1)
+    c = ellipsoids(g, np.random.default_rng(seed))
+    if not c.any():
+        c[nz // 2, ny // 2, nx // 2] = 1.0
+    return dict(name=f"small3_{nx}x{ny}x{nz}_{T}", grid=g, model=default_model3(n_ch=n_ch), r=r,
+                v=v, c=c, noise_frac=0.01, noise_seed=seed + 100, clip_pct=5.0)
