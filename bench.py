@@ -242,46 +242,146 @@ def measure_paper_pipeline(api, syn, dev, stream):
     """The paper's two-stage reconstruction (Core Stage with gamma = 1e-7 and
     CG to 1e-3 relative residual, then ZeroShot-PnP with the trace-kernel
     convolution, 10 iterations of 20 CG steps) on the scanner-shaped
-    synthetic scan (Lissajous 17/16, 1632 samples, 24 mm FoV) at the paper's
-    21x21 and 100x100 grids, FP32, timed end to end on the device.  The
-    paper's times (Table runtimes: CPU 0.46 s / 5.84 s, RTX A6000 1.56 s /
+    synthetic scan (Lissajous 17/16, 1632 samples, 24 mm FoV, 1 % noise) at
+    the paper's 21x21 and 100x100 grids, FP32, timed end to end on the
+    device.  Beside it, on the same data: the direct-operator PnP (A instead
+    of Core Stage + C, same 10 x 20 iterations) and the single-channel form
+    (channel x only: one-channel Core Stage, then PnP with the (0, 0) entry of
+    the kernel matrix).  Quality is the relative L2 distance to the phantom.
+    The paper's times (Table runtimes: CPU 0.46 s / 5.84 s, RTX A6000 1.56 s /
     3.36 s, with a DRUNet denoiser) are context only."""
     import torch
     f32 = torch.float32
     out = {}
     paper = {21: (0.46, 1.56), 100: (5.84, 3.36)}
+
+    def frob2(apply, n, probes=4):
+        gen = torch.Generator(device="cpu").manual_seed(5)
+        acc = 0.0
+        for _ in range(probes):
+            z = (torch.randint(0, 2, (n, n), generator=gen) * 2 - 1).to(dev, f32)
+            acc += float(torch.sum(apply(z).double() ** 2)) / probes
+        return acc
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3, res
+
     for n in (21, 100):
         g = syn.square_grid(n)
         m = syn.default_model()
         r_np, v_np = syn.lissajous(1632, 17, 16)
         c_np = syn.ellipses(g, np.random.default_rng(101))
+        c_t = torch.as_tensor(c_np, dtype=torch.float64)
         r = torch.as_tensor(r_np, dtype=f32, device=dev)
         v = torch.as_tensor(v_np, dtype=f32, device=dev)
         s_clean = api.mpi_forward(m, g, r, v, torch.as_tensor(c_np, dtype=f32, device=dev))
         s = torch.as_tensor(syn.add_noise(s_clean.cpu().numpy().astype(np.float64), 0.01, 201),
                             dtype=f32, device=dev)
-        gen = torch.Generator(device="cpu").manual_seed(5)
-        fro = 0.0
-        for _ in range(4):
-            z = (torch.randint(0, 2, (n, n), generator=gen) * 2 - 1).to(dev, f32)
-            fro += float(torch.sum(api.mpi_conv(m, g, z).double() ** 2)) / 4
-        nu0 = 1e-3 * fro / (n * n)
+        N = n * n
+        nu_c = 1e-3 * frob2(lambda z: api.mpi_conv(m, g, z), n) / N
+        nu_c00 = 1e-3 * frob2(lambda z: api.mpi_conv_component(m, g, 0, z), n) / N
+        nu_a = 1e-3 * frob2(lambda z: api.mpi_forward(m, g, r, v, z), n) / N
 
-        def once():
+        def err(rho):
+            return float(torch.linalg.norm(rho.double().cpu() - c_t) / torch.linalg.norm(c_t))
+
+        def two_stage():
             _, u, it = api.mpi_grid(g, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3,
                                     return_iters=True)
-            rho = api.mpi_pnp_solve(m, g, None, None, u.contiguous(), 10, 20, nu0, op=api.MPI_OP_CONV)
-            return it, rho
-        once()
+            return it, api.mpi_pnp_solve(m, g, None, None, u.contiguous(), 10, 20, nu_c,
+                                         op=api.MPI_OP_CONV)
+
+        def direct():
+            return api.mpi_pnp_solve(m, g, r, v, s, 10, 20, nu_a)
+
+        s_x = s[0].contiguous()
+
+        def single_x():
+            _, a00, it = api.mpi_grid(g, r, v, s_x, gamma=1e-7, max_iter=10000, rel_tol=1e-3,
+                                      return_iters=True, channel=0)
+            return it, api.mpi_pnp_solve(m, g, None, None, a00.contiguous(), 10, 20, nu_c00,
+                                         op=api.MPI_OP_CONV, kernel_component=0)
+
+        t2, (it2, rho2) = timed(two_stage)
+        td, rhod = timed(direct)
+        t1, (it1, rho1) = timed(single_x)
+        out[f"{n}x{n}"] = {
+            "s": t2, "core_stage_cg_steps": it2, "rel_err_vs_phantom": err(rho2),
+            "direct_A_pnp": {"s": td, "rel_err_vs_phantom": err(rhod)},
+            "single_channel_x": {"s": t1, "core_stage_cg_steps": it1, "rel_err_vs_phantom": err(rho1)},
+            "paper_cpu_s": paper[n][0], "paper_rtx_a6000_s": paper[n][1]}
+    return out
+
+
+ALG_OPS_3D = {"k_forward3": (25, 3), "k_adjoint3": (25, 3)}
+
+
+def measure_ffp3d(api, syn, dev, stream, sm_count, sm_max):
+    """The 3-D FFP workload (48 x 48 x 24 voxels, 3-D Lissajous, T = 65 536,
+    three channels): kernel-only rates of A and A^T (library event timing,
+    mean of 5 applications each) against their issue bound, and one
+    ZeroShot-PnP reconstruction (20 iterations x 20 CG steps, FP32) timed on
+    the device."""
+    import torch
+    f32 = torch.float32
+    cfg = syn.config3("3d")
+    m, g = cfg["model"], cfg["grid"]
+    r = torch.as_tensor(cfg["r"], dtype=f32, device=dev)
+    v = torch.as_tensor(cfg["v"], dtype=f32, device=dev)
+    c = torch.as_tensor(cfg["c"], dtype=f32, device=dev)
+    N, T = cfg["c"].size, cfg["r"].shape[0]
+    s_clean = api.mpi_forward3(m, g, r, v, c)
+    s = torch.as_tensor(syn.add_noise(s_clean.cpu().numpy().astype(np.float64), cfg["noise_frac"],
+                                      cfg["noise_seed"]), dtype=f32, device=dev)
+    out = {}
+    cout = torch.empty_like(c)
+    for name, cls, fn in (("k_forward3", api.PROF_FORWARD, lambda: api.mpi_forward3(m, g, r, v, c, s=s_clean)),
+                          ("k_adjoint3", api.PROF_ADJOINT, lambda: api.mpi_adjoint3(m, g, r, v, s, c_out=cout))):
+        fn()
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, _ = once()
-        e1.record(stream)
-        e1.synchronize()
-        out[f"{n}x{n}"] = {"s": e0.elapsed_time(e1) * 1e-3, "core_stage_cg_steps": it,
-                           "paper_cpu_s": paper[n][0], "paper_rtx_a6000_s": paper[n][1]}
+        api.mpi_profile_enable(True)
+        for _ in range(5):
+            fn()
+        n, tot = api.mpi_profile_read(cls)
+        api.mpi_profile_enable(False)
+        ms = tot / max(n, 1)
+        n_fp32, n_xu = ALG_OPS_3D[name]
+        per_clk = min(128.0 / (n_fp32 + n_xu), 128.0 / n_fp32, 32.0 / n_xu)
+        peak = sm_count * sm_max * 1e6 * per_clk / 1e9
+        rate = N * T / (ms * 1e-3) / 1e9
+        out[name] = {"avg_launch_ms": ms, "gpair_per_s": rate, "peak": peak, "frac": rate / peak,
+                     "peak_basis": f"issue bound, {n_fp32} FP32 + {n_xu} XU algorithmic ops per pair"}
+    gen = torch.Generator(device="cpu").manual_seed(5)
+    fro = 0.0
+    for _ in range(4):
+        z = (torch.randint(0, 2, tuple(c.shape), generator=gen) * 2 - 1).to(dev, f32)
+        fro += float(torch.sum(api.mpi_forward3(m, g, r, v, z).double() ** 2)) / 4
+    nu0 = 1e-3 * fro / N
+    n_it, n_cg = cfg["n_it"], cfg["n_cg"]
+    rho = torch.empty_like(c)
+    api.mpi_pnp_solve3(m, g, r, v, s, 1, 1, nu0, rho_out=rho)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    api.mpi_pnp_solve3(m, g, r, v, s, n_it, n_cg, nu0, rho_out=rho)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    apps = 1 + n_it * (2 * (n_cg + 1))
+    c64 = torch.as_tensor(cfg["c"], dtype=torch.float64)
+    out["pnp"] = {"iterations": n_it, "cg_steps": n_cg, "s": ms * 1e-3,
+                  "gpair_per_s": apps * N * T / (ms * 1e-3) / 1e9,
+                  "rel_err_vs_phantom": float(torch.linalg.norm(rho.double().cpu() - c64) / torch.linalg.norm(c64))}
+    out["workload"] = "48x48x24 voxels, 24x24x12 mm, G = 2.5 T/m diag(-1/2, -1/2, 1), 3-D Lissajous 17/16/15, T=65536, 3 channels"
     return out
 
 
@@ -458,6 +558,11 @@ def run_ours(args):
     if world == 1 and not args.no_batch:
         paper_pipeline = measure_paper_pipeline(api, syn, dev, stream)
 
+    # --- the three-dimensional FFP --------------------------------------------
+    ffp3d = None
+    if world == 1 and not args.no_batch:
+        ffp3d = measure_ffp3d(api, syn, dev, stream, sm_count, sm_max)
+
     # --- CPU baseline: the oracle on a bounded sample -----------------------
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -486,6 +591,7 @@ def run_ours(args):
                     "recon_per_s": len(e2e_ms) * world / (e2e_tot * 1e-3)},
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "fp64_plain": fp64_plain, "batched": batched, "paper_pipeline": paper_pipeline,
+            "ffp3d": ffp3d,
             "clocks": clk, "impl": "ours"}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -500,7 +606,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame batched measurement")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the secondary measurements (64-frame batch, paper pipeline, 3-D FFP)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

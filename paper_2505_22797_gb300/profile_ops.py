@@ -26,7 +26,7 @@ from paper_2505_22797_gb300 import synthetic as syn  # noqa: E402
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--op", choices=["forward", "adjoint", "dbeta", "conv", "all"], default="all")
-    ap.add_argument("--workload", default="c2", help="c1, c2, c2_partial, c4 or c5")
+    ap.add_argument("--workload", default="c2", help="c1, c2, c2_partial, c4, c5 or 3d")
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
@@ -36,22 +36,31 @@ def main(argv=None):
 
     build.build()
     api.load()
-    cfg = syn.config(args.workload)
+    three = args.workload == "3d"
+    cfg = syn.config3("3d") if three else syn.config(args.workload)
     m, g = cfg["model"], cfg["grid"]
     dt = torch.float32 if args.dtype == "f32" else torch.float64
     r = torch.as_tensor(cfg["r"], dtype=dt, device="cuda")
     v = torch.as_tensor(cfg["v"], dtype=dt, device="cuda")
     c = torch.as_tensor(cfg["c"], dtype=dt, device="cuda")
-    s = api.mpi_forward(m, g, r, v, c)
     out = torch.empty_like(c)
-    ops = {
-        "forward": lambda: api.mpi_forward(m, g, r, v, c, s=s),
-        "adjoint": lambda: api.mpi_adjoint(m, g, r, v, s, c_out=out),
-        "dbeta": lambda: api.mpi_dbeta(m, g, r, v, c, s),
-        "conv": lambda: api.mpi_conv(m, g, c, out=out),
-    }
+    if three:
+        s = api.mpi_forward3(m, g, r, v, c)
+        ops = {
+            "forward": lambda: api.mpi_forward3(m, g, r, v, c, s=s),
+            "adjoint": lambda: api.mpi_adjoint3(m, g, r, v, s, c_out=out),
+            "conv": lambda: api.mpi_conv3(m, g, c, out=out),
+        }
+    else:
+        s = api.mpi_forward(m, g, r, v, c)
+        ops = {
+            "forward": lambda: api.mpi_forward(m, g, r, v, c, s=s),
+            "adjoint": lambda: api.mpi_adjoint(m, g, r, v, s, c_out=out),
+            "dbeta": lambda: api.mpi_dbeta(m, g, r, v, c, s),
+            "conv": lambda: api.mpi_conv(m, g, c, out=out),
+        }
     names = list(ops) if args.op == "all" else [args.op]
-    pairs = g["nx"] * g["ny"] * r.shape[0]
+    pairs = c.numel() * r.shape[0]
     stream = torch.cuda.current_stream()
     for name in names:
         fn = ops[name]
