@@ -18,6 +18,8 @@ Parity status per function (what pins each one lives in tests/test_oracle_*):
   percentile_clamp, variance, gaussian5, core_stage: pinned.
   kernel_matrix3, pair3, forward3, adjoint3, frob2_3, conv_kernel3, conv3,
   gaussian5_3d (three-dimensional FFP): pinned.
+  transfer_correct (DFT division by the transfer function, SNR
+  thresholding): pinned.
   pnp: pinned step by step (identity-operator closed form, Algorithm 1
   bookkeeping); the full reconstruction has no printed example in the paper,
   so its end-to-end values are "parity unpinned" at paper level.
@@ -584,4 +586,32 @@ def gaussian5_3d(vol) -> np.ndarray:
     for k in range(nz):
         for m in range(-2, 3):
             out[k, :, :] += w[m + 2] * b[_reflect(k + m, nz), :, :]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Transfer-function correction (Eq. core:formula:conva -> Eq. core:formula and
+# the preprocessing of Sec. 3.2).  The measured signal is the model signal
+# convolved in time with the receive chain's impulse response a; over one
+# period of a periodic trajectory (T samples) that is a circular convolution,
+# so its DFT is the product s_hat * a_hat.  The correction divides by a_hat
+# bin by bin and drops the bins whose SNR is below the channel's threshold
+# (and bins where a_hat vanishes).  DFT convention: numpy's rfft / irfft over
+# the T samples of one period (F = T//2 + 1 bins).
+
+def transfer_correct(s_raw, a_hat, snr=None, theta=None) -> np.ndarray:
+    """s_raw [n_ch, T] real, a_hat [n_ch, F] complex, snr [n_ch, F] (or None:
+    no thresholding), theta [n_ch] -> corrected signal [n_ch, T]."""
+    s_raw = np.atleast_2d(_f64(s_raw))
+    n_ch, T = s_raw.shape
+    a_hat = np.atleast_2d(np.asarray(a_hat, dtype=np.complex128))
+    out = np.empty_like(s_raw)
+    for k in range(n_ch):
+        S = np.fft.rfft(s_raw[k])
+        keep = np.abs(a_hat[k]) > 0
+        if snr is not None:
+            keep &= np.asarray(snr, dtype=np.float64)[k] >= float(theta[k])
+        Y = np.zeros_like(S)
+        Y[keep] = S[keep] / a_hat[k][keep]
+        out[k] = np.fft.irfft(Y, n=T)
     return out

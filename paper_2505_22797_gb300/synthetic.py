@@ -319,3 +319,40 @@ def small3(nx: int, ny: int, nz: int, T: int, seed: int = 9, n_ch: int = 3) -> d
         c[nz // 2, ny // 2, nx // 2] = 1.0
     return dict(name=f"small3_{nx}x{ny}x{nz}_{T}", grid=g, model=default_model3(n_ch=n_ch), r=r,
                 v=v, c=c, noise_frac=0.01, noise_seed=seed + 100, clip_pct=5.0)
+
+
+# ---------------------------------------------------------------------------
+# Receive chain (the time convolution with a of Eq. core:formula:conva).  The
+# measured system matrix from which the paper estimates a_hat and the SNR is
+# not available; a synthetic chain stands in: a first-order high-pass (corner
+# f_hp bins, so the DC bin is zero), a first-order low-pass (corner f_lp bins)
+# and a delay of `delay` samples, per channel with different corners.
+
+def transfer_function(T: int, n_ch: int = 2, f_hp=(3.0, 4.0), f_lp=(900.0, 700.0),
+                      delay=(2.5, 3.0)) -> np.ndarray:
+    """a_hat [n_ch, T//2 + 1] complex on the DFT bins of one period."""
+    f = np.arange(T // 2 + 1, dtype=np.float64)
+    out = np.empty((n_ch, f.size), dtype=np.complex128)
+    for k in range(n_ch):
+        hp = (1j * f / f_hp[k]) / (1 + 1j * f / f_hp[k])
+        lp = 1 / (1 + 1j * f / f_lp[k])
+        out[k] = hp * lp * np.exp(-2j * np.pi * f * delay[k] / T)
+    if T % 2 == 0:  # the Nyquist bin of a real impulse response is real
+        out[:, -1] = out[:, -1].real
+    return out
+
+
+def measured_signal(s_model: np.ndarray, a_hat: np.ndarray, noise_frac: float, seed: int):
+    """The raw signal of a chain with transfer function a_hat: the model
+    signal circularly convolved with a (one period), plus white noise of
+    standard deviation noise_frac * max|raw|.  Returns (raw, snr) with the
+    per-bin SNR |a_hat s_hat|^2 / (T sigma^2) (signal power over the noise
+    power in that bin), the quantity thresholded in Sec. 3.2."""
+    s_model = np.atleast_2d(s_model)
+    T = s_model.shape[1]
+    S = np.fft.rfft(s_model, axis=1) * a_hat
+    clean = np.fft.irfft(S, n=T, axis=1)
+    sig = noise_frac * np.abs(clean).max()
+    raw = clean + np.random.default_rng(seed).normal(0.0, sig, size=clean.shape)
+    snr = np.abs(S) ** 2 / (T * sig * sig) if sig > 0 else np.full(S.shape, np.inf)
+    return raw, snr
