@@ -155,6 +155,27 @@ int mpi_interp(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
 int mpi_interp_adjoint(const mpi_grid_desc *grid, const mpi_traj *traj,
                        mpi_dtype dtype, const void *s, void *Ahat, void *stream);
 
+/* ---- Preprocessing: transfer-function correction ------------------------- */
+
+/* The measured signal is the model signal convolved in time with the receive
+ * chain's impulse response a (Eq. core:formula:conva); over one period of T
+ * samples (a periodic trajectory) the convolution is circular, and the
+ * correction of Sec. 3.2 divides by the transfer function in the DFT domain
+ * (Eq. core:formula) and drops unreliable frequencies:
+ *   s_out[k] = IDFT_T( M_k(f) DFT_T(s_raw[k])(f) / a_hat[k](f) ),
+ *   M_k(f) = 1 if snr[k][f] >= theta[k] and a_hat[k](f) != 0, else 0,
+ * on the F = T/2 + 1 non-negative bins f (the output is real; the negative
+ * bins mirror these).  DFT_T(x)(f) = sum_t x_t exp(-2 pi i f t / T).
+ * s_raw, s_out: [n_ch][T] device arrays of the call's dtype (may be the same
+ * array).  a_hat: device, FP64 complex interleaved [n_ch][F][2].  snr: device
+ * FP64 [n_ch][F], or NULL for no thresholding.  theta: HOST [n_ch] (read only
+ * when snr is given).  1 <= n_ch <= 8, 0 <= T <= 2^26 (any length: lengths
+ * with a prime factor above 127 use Bluestein's algorithm).  The DFTs run in
+ * FP64 on the device.  Allocates scratch (a few complex FP64 copies). */
+int mpi_transfer_correct(int n_ch, int64_t T, mpi_dtype dtype, const void *s_raw,
+                         const double *a_hat, const double *snr, const double *theta,
+                         void *s_out, void *stream);
+
 /* ---- Core Stage (Eq. first:step) ---------------------------------------- */
 
 typedef struct {

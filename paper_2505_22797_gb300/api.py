@@ -114,6 +114,7 @@ _SIGS = {
                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mpi_pnp_solve": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
                      + [DENOISE_FN] + [ctypes.c_void_p] * 4,
+    "mpi_transfer_correct": [ctypes.c_int, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 6,
     "mpi_forward3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_adjoint3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_conv3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
@@ -586,3 +587,34 @@ def mpi_pnp_solve3(model3, grid3, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, o
     if with_info:
         return rho_out, [(i.sigma, i.nu, i.cg_resid) for i in info[:n_iter]]
     return rho_out
+
+
+# ---------------------------------------------------------------------------
+# Preprocessing
+
+def mpi_transfer_correct(s_raw, a_hat, snr=None, theta=None, out=None, stream=None):
+    """Transfer-function correction: s_raw [n_ch, T] (FP32/FP64, device),
+    a_hat [n_ch, T//2 + 1] complex128 (device), snr [n_ch, T//2 + 1] float64
+    (device) or None, theta: n_ch thresholds (host sequence)."""
+    dt = s_raw.dtype
+    if s_raw.dim() != 2:
+        raise ValueError("s_raw must be [n_ch, T]")
+    n_ch, T = s_raw.shape
+    if a_hat.dtype != torch.complex128 or tuple(a_hat.shape) != (n_ch, T // 2 + 1):
+        raise ValueError("a_hat must be complex128 [n_ch, T//2 + 1]")
+    if out is None:
+        out = torch.empty_like(s_raw)
+    a_ri = torch.view_as_real(a_hat.contiguous())
+    th = None
+    if snr is not None:
+        if snr.dtype != torch.float64 or tuple(snr.shape) != (n_ch, T // 2 + 1):
+            raise ValueError("snr must be float64 [n_ch, T//2 + 1]")
+        if theta is None or len(theta) != n_ch:
+            raise ValueError("theta needs one threshold per channel")
+        th = (ctypes.c_double * n_ch)(*[float(x) for x in theta])
+    _check(load().mpi_transfer_correct(n_ch, T, _dtype(s_raw),
+                                       _dev(s_raw, dt, "s_raw") if T else None,
+                                       _dev(a_ri, torch.float64, "a_hat") if T else None,
+                                       _dev(snr, torch.float64, "snr") if snr is not None else None,
+                                       th, _dev(out, dt, "out") if T else None, _stream(stream)))
+    return out
