@@ -45,12 +45,41 @@ constexpr float kNearU32 = 1.0f;
 // FP64: series for u < 0.25 (z < 0.5); 14 terms reach (0.25/pi^2)^14 ~ 5e-23.
 constexpr double kNearU64 = 0.25;
 
+// Far from the FFP, q = exp(-2z) drops below the working precision and the
+// closed forms reduce to their asymptotic parts (coth z -> 1, csch^2 z -> 0):
+//     a = 1/z - 1/z^2,   d = (2/z^2 - 1/z)/z^2,   L' = 1/z^2,   e = -2/z^4.
+// The terms dropped are about 2q relative in a, 4 z q in d, 4 z^2 q in L'
+// and 4 z^3 q in e.  With z >= 12 (u >= 144) a and d lose less than 2e-9
+// relative; the beta-derivative pair (L', e) uses z >= 14 (u >= 196), where
+// both lose less than 8e-9: the reduced forms are exact to FP32 there.  FP64
+// uses z >= 21 / 24 (dropped terms below 5e-17 / 8e-17).  One XU operation
+// (rsqrt) instead of three.
+constexpr float kVfarU32 = 144.0f, kVfarU32Beta = 196.0f;
+constexpr double kVfarU64 = 441.0, kVfarU64Beta = 576.0;
+
 #ifdef __CUDACC__
 
 template <typename R> struct Lang;
 
 template <> struct Lang<float> {
     static constexpr float near_u = kNearU32;
+    static constexpr float vfar_u = kVfarU32, vfar_u_beta = kVfarU32Beta;
+
+    // a, d for u >= vfar_u (asymptotic form, exact to FP32 there).
+    static __device__ __forceinline__ void ad_vfar(float u, float &a, float &d)
+    {
+        const float iz = rsqrt_approx(u);
+        const float iz2 = iz * iz;
+        a = iz - iz2;
+        d = fmaf(iz2, 2.0f, -iz) * iz2;
+    }
+    // L', e = L''/z for u >= vfar_u_beta.
+    static __device__ __forceinline__ void le_vfar(float u, float &lp, float &e)
+    {
+        const float iz = rsqrt_approx(u);
+        lp = iz * iz;
+        e = -2.0f * lp * lp;
+    }
 
     // a, d by the closed form (valid for u >= near_u; any u > 0 is finite).
     static __device__ __forceinline__ void ad_far(float u, float &a, float &d)
@@ -104,6 +133,20 @@ template <> struct Lang<float> {
 
 template <> struct Lang<double> {
     static constexpr double near_u = kNearU64;
+    static constexpr double vfar_u = kVfarU64, vfar_u_beta = kVfarU64Beta;
+
+    static __device__ __forceinline__ void ad_vfar(double u, double &a, double &d)
+    {
+        const double iz = 1.0 / sqrt(u), iz2 = iz * iz;
+        a = iz - iz2;
+        d = fma(iz2, 2.0, -iz) * iz2;
+    }
+    static __device__ __forceinline__ void le_vfar(double u, double &lp, double &e)
+    {
+        const double iz = 1.0 / sqrt(u);
+        lp = iz * iz;
+        e = -2.0 * lp * lp;
+    }
 
     static __device__ __forceinline__ void ad_far(double u, double &a, double &d)
     {
@@ -185,6 +228,20 @@ __device__ __forceinline__ void lang_far(R u, R &f1, R &f2)
 {
     if constexpr (DBETA) Lang<R>::le_far(u, f1, f2);
     else Lang<R>::ad_far(u, f1, f2);
+}
+
+// The asymptotic form, valid for u >= vfar_threshold<R, DBETA>().
+template <typename R, bool DBETA>
+__device__ __forceinline__ void lang_vfar(R u, R &f1, R &f2)
+{
+    if constexpr (DBETA) Lang<R>::le_vfar(u, f1, f2);
+    else Lang<R>::ad_vfar(u, f1, f2);
+}
+template <typename R, bool DBETA>
+__host__ __device__ constexpr R vfar_threshold()
+{
+    return DBETA ? (sizeof(R) == 4 ? R(kVfarU32Beta) : R(kVfarU64Beta))
+                 : (sizeof(R) == 4 ? R(kVfarU32) : R(kVfarU64));
 }
 
 #endif  // __CUDACC__

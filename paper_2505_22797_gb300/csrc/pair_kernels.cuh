@@ -90,14 +90,14 @@ __device__ __forceinline__ int find_frame(const PairBatch<R, MAXF> &B, int64_t i
 // sa += c a, vx += f y_x, fy += f with f = c d (y.W).  With CLAMP the
 // Langevin scalars are evaluated at max(u, near_u), valid for the closed form.
 template <typename R, bool CLAMP>
-__device__ __forceinline__ void fwd_row_far(int nx, const V2<R> *__restrict__ xc,
+__device__ __forceinline__ void fwd_row_far(int i0, int i1, const V2<R> *__restrict__ xc,
                                             const R (&Rx)[kFwdS],
                                             const R (&yy2)[kFwdS], const R (&Wx)[kFwdS],
                                             const R (&yyW)[kFwdS], R (&sa)[kFwdS], R (&vx)[kFwdS],
                                             R (&fy)[kFwdS])
 {
 #pragma unroll kFwdUnroll
-    for (int i = 0; i < nx; ++i) {
+    for (int i = i0; i < i1; ++i) {
         const V2<R> q = xc[i];  // (x_i, c_i) in one load
         const R xi = q.x, ci = q.y;
 #pragma unroll
@@ -107,6 +107,32 @@ __device__ __forceinline__ void fwd_row_far(int nx, const V2<R> *__restrict__ xc
             if (CLAMP) u = max(u, Lang<R>::near_u);
             R a, d;
             lang_far<R, false>(u, a, d);
+            sa[s] = fmx(ci, a, sa[s]);
+            const R f = ci * d * fmx(yx, Wx[s], yyW[s]);
+            vx[s] = fmx(f, yx, vx[s]);
+            fy[s] += f;
+        }
+    }
+}
+
+// The same sums over columns [i0, i1) whose pairs all have u >= vfar_u: the
+// asymptotic closed form (one rsqrt per pair).
+template <typename R>
+__device__ __forceinline__ void fwd_row_vfar(int i0, int i1, const V2<R> *__restrict__ xc,
+                                             const R (&Rx)[kFwdS], const R (&yy2)[kFwdS],
+                                             const R (&Wx)[kFwdS], const R (&yyW)[kFwdS],
+                                             R (&sa)[kFwdS], R (&vx)[kFwdS], R (&fy)[kFwdS])
+{
+#pragma unroll kFwdUnroll
+    for (int i = i0; i < i1; ++i) {
+        const V2<R> q = xc[i];
+        const R xi = q.x, ci = q.y;
+#pragma unroll
+        for (int s = 0; s < kFwdS; ++s) {
+            const R yx = xi - Rx[s];
+            const R u = fmx(yx, yx, yy2[s]);
+            R a, d;
+            Lang<R>::ad_vfar(u, a, d);
             sa[s] = fmx(ci, a, sa[s]);
             const R f = ci * d * fmx(yx, Wx[s], yyW[s]);
             vx[s] = fmx(f, yx, vx[s]);
@@ -186,6 +212,21 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
     R Sa[kFwdS], Vx[kFwdS], Vy[kFwdS], cSa[kFwdS], cVx[kFwdS], cVy[kFwdS];
 #pragma unroll
     for (int s = 0; s < kFwdS; ++s) Sa[s] = Vx[s] = Vy[s] = cSa[s] = cVx[s] = cVy[s] = R(0);
+    // Extent of the warp's samples (prescaled), for the far-field segments.
+    R wx_lo = Rx[0], wx_hi = Rx[0], wy_lo = Ry[0], wy_hi = Ry[0];
+#pragma unroll
+    for (int s = 1; s < kFwdS; ++s) {
+        wx_lo = min(wx_lo, Rx[s]); wx_hi = max(wx_hi, Rx[s]);
+        wy_lo = min(wy_lo, Ry[s]); wy_hi = max(wy_hi, Ry[s]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wx_lo = min(wx_lo, __shfl_xor_sync(0xffffffffu, wx_lo, o));
+        wx_hi = max(wx_hi, __shfl_xor_sync(0xffffffffu, wx_hi, o));
+        wy_lo = min(wy_lo, __shfl_xor_sync(0xffffffffu, wy_lo, o));
+        wy_hi = max(wy_hi, __shfl_xor_sync(0xffffffffu, wy_hi, o));
+    }
+    constexpr R kUv = vfar_threshold<R, false>();
 
     // Rows of the chunk are staged RB at a time.
 #pragma unroll 1
@@ -214,18 +255,43 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
             sa[s] = vx[s] = fy[s] = R(0);
         }
         if (DIAG) {
-            if (!__any_sync(0xffffffffu, near)) {
-                // Every pair of this row has u >= yy2 >= near_u: closed form only.
-                fwd_row_far<R, false>(nx, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
+            // Columns [lo, hi] may hold a pair of this warp with u < vfar_u
+            // (widened by one column and a relative margin on each side);
+            // outside them every pair takes the asymptotic form.
+            int lo = 1, hi = 0;  // empty
+            {
+                const R gy = max(R(0), max(wy_lo - yr.y, yr.y - wy_hi));
+                const R gy2 = gy * gy;
+                if (gy2 < kUv) {
+                    const R w = sqrt(kUv - gy2) * R(1.0001);
+                    const R x0c = s_x[0].x;
+                    const R h = nx > 1 ? s_x[1].x - x0c : R(1);
+                    const R ia = (wx_lo - w - x0c) / h, ib = (wx_hi + w - x0c) / h;
+                    const R fl = min(max(floor(min(ia, ib)) - R(1), R(0)), R(nx));
+                    const R fh = min(max(ceil(max(ia, ib)) + R(1), R(-1)), R(nx - 1));
+                    lo = (int)fl;
+                    hi = (int)fh;
+                }
+            }
+            if (lo > hi) {
+                fwd_row_vfar<R>(0, nx, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
             } else {
-                // Closed form with u clamped to near_u, then the exact series
-                // for the few pairs of this thread that are really near.
-                fwd_row_far<R, true>(nx, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
+                fwd_row_vfar<R>(0, lo, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
+                if (!__any_sync(0xffffffffu, near)) {
+                    // Every pair of this row has u >= yy2 >= near_u: closed form only.
+                    fwd_row_far<R, false>(lo, hi + 1, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
+                } else {
+                    // Closed form with u clamped to near_u, then the exact series
+                    // for the few pairs of this thread that are really near
+                    // (all inside [lo, hi]: u < near_u < vfar_u).
+                    fwd_row_far<R, true>(lo, hi + 1, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
 #pragma unroll
-                for (int s = 0; s < kFwdS; ++s)
-                    if (yy2[s] < Lang<R>::near_u)
-                        fwd_near_fix<R>(nx, xcrow, Rx[s], yy2[s], Wx[s], yyW[s], A1, D1,
-                                        F.near_cols, sa[s], vx[s], fy[s]);
+                    for (int s = 0; s < kFwdS; ++s)
+                        if (yy2[s] < Lang<R>::near_u)
+                            fwd_near_fix<R>(nx, xcrow, Rx[s], yy2[s], Wx[s], yyW[s], A1, D1,
+                                            F.near_cols, sa[s], vx[s], fy[s]);
+                }
+                fwd_row_vfar<R>(hi + 1, nx, xcrow, Rx, yy2, Wx, yyW, sa, vx, fy);
             }
 #pragma unroll
             for (int s = 0; s < kFwdS; ++s) {
@@ -278,7 +344,17 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
 // One staged sample against this thread's kAdjV voxels of a column (adjoint /
 // beta-derivative): blk[v] += f1 (u.W) + f2 y^T S y.  FAR: the warp's voxel
 // box is provably outside the near-FFP range for this sample.
-template <typename R, bool DIAG, bool DBETA, bool FAR>
+template <typename R, bool DBETA, int MODE>
+__device__ __forceinline__ void lang_mode(R u, R &f1, R &f2)
+{
+    if constexpr (MODE == 2) lang_vfar<R, DBETA>(u, f1, f2);
+    else if constexpr (MODE == 1) lang_far<R, DBETA>(u, f1, f2);
+    else lang_checked<R, DBETA>(u, f1, f2);
+}
+
+// MODE 2: the warp's voxel box is provably in the asymptotic range for this
+// sample; 1: in the closed-form range; 0: near pairs possible.
+template <typename R, bool DIAG, bool DBETA, int MODE>
 __device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const V2<R> xc,
                                            const R (&yrow_x)[kAdjV], const R (&yrow_y)[kAdjV],
                                            R (&blk)[kAdjV])
@@ -292,8 +368,7 @@ __device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const 
             const R yy = yrow_y[v] - rr.y;
             const R u = fmx(yy, yy, yx2);
             R f1, f2;
-            if (FAR) lang_far<R, DBETA>(u, f1, f2);
-            else lang_checked<R, DBETA>(u, f1, f2);
+            lang_mode<R, DBETA, MODE>(u, f1, f2);
             blk[v] += fmx(f1, q.x, f2 * fmx(yy, fmx(q.w, yy, Q1), Q0));
         }
     } else {
@@ -304,8 +379,7 @@ __device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const 
             const R yy = oy + yrow_y[v];
             const R u = fmx(yx, yx, yy * yy);
             R f1, f2;
-            if (FAR) lang_far<R, DBETA>(u, f1, f2);
-            else lang_checked<R, DBETA>(u, f1, f2);
+            lang_mode<R, DBETA, MODE>(u, f1, f2);
             const R quad = fmx(yx, fmx(q.y, yx, q.z * yy), q.w * yy * yy);
             blk[v] += fmx(f1, q.x, f2 * quad);
         }
@@ -329,6 +403,7 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
     __shared__ V2<R> s_r[kAdjBlock];
     __shared__ V4<R> s_q[kAdjBlock];
     __shared__ uint32_t s_far[4][kAdjBlock / 32];
+    __shared__ uint32_t s_vfar[4][kAdjBlock / 32];
     __shared__ double s_red[kAdjThreads / 32];
 
     const PairFrame<R> &F = B.f[find_frame(B, item)];
@@ -392,18 +467,24 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
             s_q[k] = V4<R>{ux * q.z + uy * q.w, q.z * ux, q.z * uy + q.w * ux, q.w * uy};
         }
         __syncthreads();
-        // Far flags of this warp for the staged samples.
+        // Far / very-far flags of this warp for the staged samples.
         for (int m = 0; m < kAdjBlock / 32; ++m) {
             const int k = m * 32 + lane;
-            bool far = true;
+            bool far = true, vfar = true;
             if (k < nb) {
                 const V2<R> q = s_r[k];
                 const R ddx = max(R(0), max(bx_lo - q.x, q.x - bx_hi));
                 const R ddy = max(R(0), max(by_lo - q.y, q.y - by_hi));
-                far = ddx * ddx + ddy * ddy >= Lang<R>::near_u;
+                const R d2 = fmx(ddy, ddy, ddx * ddx);
+                far = d2 >= Lang<R>::near_u;
+                vfar = d2 >= vfar_threshold<R, DBETA>();
             }
             const uint32_t bits = __ballot_sync(0xffffffffu, far);
-            if (lane == 0) s_far[warp][m] = bits;
+            const uint32_t vbits = __ballot_sync(0xffffffffu, vfar);
+            if (lane == 0) {
+                s_far[warp][m] = bits;
+                s_vfar[warp][m] = vbits;
+            }
         }
         __syncwarp();
 
@@ -415,18 +496,25 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
 #pragma unroll 1
         for (int k0 = 0; k0 < nb; k0 += 32) {
             const uint32_t mask = s_far[warp][k0 >> 5];
+            const uint32_t vmask = s_vfar[warp][k0 >> 5];
             const int kn = min(32, nb - k0);
-            if (kn == 32 && mask == 0xffffffffu) {
+            if (kn == 32 && vmask == 0xffffffffu) {
 #pragma unroll 2
                 for (int k = k0; k < k0 + 32; ++k)
-                    adj_sample<R, DIAG, DBETA, true>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
+                    adj_sample<R, DIAG, DBETA, 2>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
+            } else if (kn == 32 && mask == 0xffffffffu) {
+#pragma unroll 2
+                for (int k = k0; k < k0 + 32; ++k)
+                    adj_sample<R, DIAG, DBETA, 1>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
             } else {
 #pragma unroll 1
                 for (int k = k0; k < k0 + kn; ++k) {
-                    if ((mask >> (k - k0)) & 1u)
-                        adj_sample<R, DIAG, DBETA, true>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
+                    if ((vmask >> (k - k0)) & 1u)
+                        adj_sample<R, DIAG, DBETA, 2>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
+                    else if ((mask >> (k - k0)) & 1u)
+                        adj_sample<R, DIAG, DBETA, 1>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
                     else
-                        adj_sample<R, DIAG, DBETA, false>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
+                        adj_sample<R, DIAG, DBETA, 0>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
                 }
             }
         }
