@@ -18,8 +18,9 @@
 //                p_k, U.B v) so a pair costs two dot products.
 //   Both test the near field once per staged pass: the gap between the
 //   bounding box of the pass's prescaled voxel positions and that of the
-//   samples (precomputed per 512 voxels / 256 samples) decides whether the
-//   closed form alone is valid for every pair of the pass.
+//   samples (precomputed per 512 voxels / 256 samples) decides whether every
+//   pair of the pass is in the asymptotic range (one rsqrt per pair), in the
+//   closed-form range, or may need the near-FFP series.
 //   k_conv3_*    the sampled trace kernel and the direct zero-padded 3-D
 //                convolution (8 x 8 x 4 output tiles).
 //   k_gauss3     the built-in denoiser along one axis (5 taps, reflect).
@@ -196,7 +197,17 @@ struct Fwd3Args {
     R p[9];
 };
 
-template <typename R, bool FAR>
+// MODE 2: every pair of the pass in the asymptotic range (u >= vfar_u);
+// 1: every pair in the closed-form range; 0: near pairs possible.
+template <typename R, bool DBETA, int MODE>
+__device__ __forceinline__ void lang3(R u, R &f1, R &f2)
+{
+    if constexpr (MODE == 2) lang_vfar<R, DBETA>(u, f1, f2);
+    else if constexpr (MODE == 1) lang_far<R, DBETA>(u, f1, f2);
+    else lang_checked<R, DBETA>(u, f1, f2);
+}
+
+template <typename R, int MODE>
 __device__ __forceinline__ void fwd3_pass(const V4<R> *sv, int cnt, const R (&Rx)[k3FwdS],
                                           const R (&Ry)[k3FwdS], const R (&Rz)[k3FwdS],
                                           const R (&Wx)[k3FwdS], const R (&Wy)[k3FwdS],
@@ -211,8 +222,7 @@ __device__ __forceinline__ void fwd3_pass(const V4<R> *sv, int cnt, const R (&Rx
             const R yx = P.x - Rx[s], yy = P.y - Ry[s], yz = P.z - Rz[s];
             const R u = fmx(yz, yz, fmx(yy, yy, yx * yx));
             R a, d;
-            if constexpr (FAR) lang_far<R, false>(u, a, d);
-            else lang_checked<R, false>(u, a, d);
+            lang3<R, false, MODE>(u, a, d);
             const R yW = fmx(yz, Wz[s], fmx(yy, Wy[s], yx * Wx[s]));
             const R t = (P.w * d) * yW;
             Sx[s] = fmx(t, yx, Sx[s]);
@@ -259,10 +269,13 @@ k_forward3(const __grid_constant__ Fwd3Args<R, CIN> a)
         }
         __syncthreads();
         const int64_t pb = vp / k3Piece;
-        if (far_field(box_gap2(a.vbox[2 * pb], a.vbox[2 * pb + 1], slo, shi)))
-            fwd3_pass<R, true>(sv, cnt, Rx, Ry, Rz, Wx, Wy, Wz, sa, Sx, Sy, Sz);
+        const R gap2 = box_gap2(a.vbox[2 * pb], a.vbox[2 * pb + 1], slo, shi);
+        if (gap2 >= vfar_threshold<R, false>())
+            fwd3_pass<R, 2>(sv, cnt, Rx, Ry, Rz, Wx, Wy, Wz, sa, Sx, Sy, Sz);
+        else if (far_field(gap2))
+            fwd3_pass<R, 1>(sv, cnt, Rx, Ry, Rz, Wx, Wy, Wz, sa, Sx, Sy, Sz);
         else
-            fwd3_pass<R, false>(sv, cnt, Rx, Ry, Rz, Wx, Wy, Wz, sa, Sx, Sy, Sz);
+            fwd3_pass<R, 0>(sv, cnt, Rx, Ry, Rz, Wx, Wy, Wz, sa, Sx, Sy, Sz);
     }
     // s_k = p_k^T (W sum c a + sum c d (y.W) y)
 #pragma unroll
@@ -288,7 +301,7 @@ struct Adj3Args {
     R p[9];
 };
 
-template <typename R, bool FAR>
+template <typename R, int MODE>
 __device__ __forceinline__ void adj3_pass(const V4<R> *sR, const V4<R> *sW, const V4<R> *sU, int cnt,
                                           const R (&Px)[k3AdjV], const R (&Py)[k3AdjV],
                                           const R (&Pz)[k3AdjV], R (&acc)[k3AdjV])
@@ -301,8 +314,7 @@ __device__ __forceinline__ void adj3_pass(const V4<R> *sR, const V4<R> *sW, cons
             const R yx = Px[m] - Q.x, yy = Py[m] - Q.y, yz = Pz[m] - Q.z;
             const R u = fmx(yz, yz, fmx(yy, yy, yx * yx));
             R a, d;
-            if constexpr (FAR) lang_far<R, false>(u, a, d);
-            else lang_checked<R, false>(u, a, d);
+            lang3<R, false, MODE>(u, a, d);
             const R yU = fmx(yz, U.z, fmx(yy, U.y, yx * U.x));
             const R yW = fmx(yz, W.z, fmx(yy, W.y, yx * W.x));
             // U^T K W = a (U.W) + d (y.U)(y.W)
@@ -353,10 +365,13 @@ k_adjoint3(const __grid_constant__ Adj3Args<R> a)
         }
         __syncthreads();
         const int64_t sb = tb / k3Batch;
-        if (far_field(box_gap2(vlo, vhi, a.sbox[2 * sb], a.sbox[2 * sb + 1])))
-            adj3_pass<R, true>(sR, sW, sU, cnt, Px, Py, Pz, acc);
+        const R gap2 = box_gap2(vlo, vhi, a.sbox[2 * sb], a.sbox[2 * sb + 1]);
+        if (gap2 >= vfar_threshold<R, false>())
+            adj3_pass<R, 2>(sR, sW, sU, cnt, Px, Py, Pz, acc);
+        else if (far_field(gap2))
+            adj3_pass<R, 1>(sR, sW, sU, cnt, Px, Py, Pz, acc);
         else
-            adj3_pass<R, false>(sR, sW, sU, cnt, Px, Py, Pz, acc);
+            adj3_pass<R, 0>(sR, sW, sU, cnt, Px, Py, Pz, acc);
     }
 #pragma unroll
     for (int m = 0; m < k3AdjV; ++m) {

@@ -41,10 +41,19 @@ constexpr int kAdjThreads = 128;  // 4 warps
 #define MPI_FWD_UNROLL 8
 #endif
 constexpr int kFwdUnroll = MPI_FWD_UNROLL;
+// Unroll depth of the full closed-form column loops (a few percent of the
+// pairs once the asymptotic tier takes the rest: kept short for code size).
+#ifndef MPI_FWD_UNROLL_FAR
+#define MPI_FWD_UNROLL_FAR 2
+#endif
+constexpr int kFwdUnrollFar = MPI_FWD_UNROLL_FAR;
 constexpr int kAdjV = MPI_ADJ_V;  // voxels (rows) per thread
 constexpr int kAdjTileX = 32;
 constexpr int kAdjTileY = 4 * kAdjV;
-constexpr int kAdjBlock = 256;    // samples staged per shared-memory block
+#ifndef MPI_ADJ_BLOCK
+#define MPI_ADJ_BLOCK 256
+#endif
+constexpr int kAdjBlock = MPI_ADJ_BLOCK;  // samples staged per shared-memory block
 
 template <typename R>
 struct PairFrame {
@@ -96,7 +105,7 @@ __device__ __forceinline__ void fwd_row_far(int i0, int i1, const V2<R> *__restr
                                             const R (&yyW)[kFwdS], R (&sa)[kFwdS], R (&vx)[kFwdS],
                                             R (&fy)[kFwdS])
 {
-#pragma unroll kFwdUnroll
+#pragma unroll kFwdUnrollFar
     for (int i = i0; i < i1; ++i) {
         const V2<R> q = xc[i];  // (x_i, c_i) in one load
         const R xi = q.x, ci = q.y;

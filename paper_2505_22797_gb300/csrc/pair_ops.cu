@@ -86,7 +86,12 @@ int prepare_geometry(const ModelH &m, const GridH &g, int64_t T, const void *r, 
 // ---------------------------------------------------------------------------
 // Work decomposition.
 
-int default_target_items() { return 8 * 4 * device_sm_count(); }
+// Work items per operator launch: enough that the blocks' uneven costs (near
+// pairs cost more than far ones) leave little idle time at the end.
+#ifndef MPI_TARGET_MULT
+#define MPI_TARGET_MULT 64
+#endif
+int default_target_items() { return MPI_TARGET_MULT * device_sm_count(); }
 
 // Bytes of concentration rows staged in shared memory at a time: small enough
 // that the block's shared memory never limits occupancy below the register
