@@ -199,13 +199,15 @@ static int forward_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, con
 {
     const int64_t T = tr->T;
     if (T == 0) return MPI_OK;
-    const FwdSplit sp = forward_split(T, g.nx, g.ny, sizeof(R), default_target_items());
+    FwdSplit sp = forward_split(T, g.nx, g.ny, sizeof(R), default_target_items());
     Scratch scr(st);
     const size_t o_geo = scr.reserve(geometry_bytes<R>(T, g.nx, g.ny));
     const size_t o_part = scr.reserve(forward_partial_bytes<R>(sp, m.n_ch, T));
+    const size_t o_ord = scr.reserve(item_order_bytes<R>(&sp, nullptr));
     MPI_TRY(scr.allocate());
     const Geometry<R> geo = geometry_carve<R>(scr.at<char>(o_geo), T, g.nx, g.ny);
     MPI_TRY(prepare_geometry<R>(m, g, T, tr->r, tr->v, geo, st));
+    MPI_TRY(prepare_item_orders<R>(g, T, geo, &sp, nullptr, scr.at<char>(o_ord), st));
     return launch_forward<R, R, R>(m, g, T, geo, sp, static_cast<const R *>(c), scr.at<R>(o_part),
                                    static_cast<R *>(s), st);
 }
@@ -215,13 +217,15 @@ static int adjoint_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, con
                         cudaStream_t st)
 {
     const int64_t T = tr->T;
-    const AdjSplit sp = adjoint_split(T, g.nx, g.ny, default_target_items());
+    AdjSplit sp = adjoint_split(T, g.nx, g.ny, default_target_items());
     Scratch scr(st);
     const size_t o_geo = scr.reserve(geometry_bytes<R>(T, g.nx, g.ny));
     const size_t o_part = scr.reserve(adjoint_partial_bytes<R>(sp, g.nx, g.ny));
+    const size_t o_ord = scr.reserve(item_order_bytes<R>(nullptr, &sp));
     MPI_TRY(scr.allocate());
     const Geometry<R> geo = geometry_carve<R>(scr.at<char>(o_geo), T, g.nx, g.ny);
     MPI_TRY(prepare_geometry<R>(m, g, T, tr->r, tr->v, geo, st));
+    MPI_TRY(prepare_item_orders<R>(g, T, geo, nullptr, &sp, scr.at<char>(o_ord), st));
     return launch_adjoint<R, R>(m, g, T, geo, sp, static_cast<const R *>(s), scr.at<R>(o_part),
                                 static_cast<R *>(c), nullptr, nullptr, nullptr, st);
 }
@@ -231,13 +235,15 @@ static int dbeta_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const
                       const void *gs, double *out, cudaStream_t st)
 {
     const int64_t T = tr->T;
-    const AdjSplit sp = adjoint_split(T, g.nx, g.ny, default_target_items());
+    AdjSplit sp = adjoint_split(T, g.nx, g.ny, default_target_items());
     Scratch scr(st);
     const size_t o_geo = scr.reserve(geometry_bytes<R>(T, g.nx, g.ny));
     const size_t o_part = scr.reserve(dbeta_partial_bytes(sp));
+    const size_t o_ord = scr.reserve(item_order_bytes<R>(nullptr, &sp));
     MPI_TRY(scr.allocate());
     const Geometry<R> geo = geometry_carve<R>(scr.at<char>(o_geo), T, g.nx, g.ny);
     MPI_TRY(prepare_geometry<R>(m, g, T, tr->r, tr->v, geo, st));
+    MPI_TRY(prepare_item_orders<R>(g, T, geo, nullptr, &sp, scr.at<char>(o_ord), st));
     return launch_dbeta<R>(m, g, T, geo, sp, static_cast<const R *>(c), static_cast<const R *>(gs),
                            scr.at<double>(o_part), out, st);
 }

@@ -73,6 +73,7 @@ struct PairFrame {
     int rows_staged;  // forward: rows per shared-memory block
     int near_cols;    // forward: column half-width that can hold a near pair
     int diag;         // G is diagonal (selects the kernel branch in mixed batches)
+    const int *order; // nullable: local item index dispatched by local block index
     R p[4];
 };
 
@@ -193,7 +194,7 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
                                              unsigned char *smem_raw)
 {
     const PairFrame<R> &F = B.f[find_frame(B, item)];
-    const int64_t local = item - F.item0;
+    const int64_t local = F.order ? F.order[item - F.item0] : item - F.item0;
     const int chunk = (int)(local / F.n_tiles);
     const int tile = (int)(local % F.n_tiles);
     const int nx = F.nx;
@@ -416,7 +417,7 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
     __shared__ double s_red[kAdjThreads / 32];
 
     const PairFrame<R> &F = B.f[find_frame(B, item)];
-    const int64_t local = item - F.item0;
+    const int64_t local = F.order ? F.order[item - F.item0] : item - F.item0;
     const int chunk = (int)(local / F.n_tiles);
     const int tile = (int)(local % F.n_tiles);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -125,6 +125,167 @@ AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items)
     return sp;
 }
 
+// ---------------------------------------------------------------------------
+// Item dispatch orders (heavy items first).
+
+// Box of the prescaled sample positions B r_t over each `per` samples:
+// (lo.x, lo.y, hi.x, hi.y).  One warp per box.
+template <typename R>
+__global__ void k_sample_boxes(const V4<R> *__restrict__ rw, int64_t T, int64_t per, int64_t n_box,
+                               V4<R> *__restrict__ box)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (b >= n_box) return;
+    const int64_t a0 = b * per, a1 = std::min<int64_t>(T, a0 + per);
+    const V4<R> q0 = rw[a0];
+    R lx = q0.x, ly = q0.y, hx = q0.x, hy = q0.y;
+    for (int64_t t = a0 + lane; t < a1; t += 32) {
+        const V4<R> q = rw[t];
+        lx = min(lx, q.x), ly = min(ly, q.y), hx = max(hx, q.x), hy = max(hy, q.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = min(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = min(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        hx = max(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        hy = max(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+    }
+    if (lane == 0) box[b] = V4<R>{lx, ly, hx, hy};
+}
+
+// Box of the prescaled voxel positions xcol[i] + yrow[j] over columns
+// [i0, i1] and rows [j0, j1] (both maps are affine: the ends bound them).
+template <typename R>
+__device__ __forceinline__ V4<R> voxel_box(const V2<R> *xcol, const V2<R> *yrow, int i0, int i1,
+                                           int j0, int j1)
+{
+    const V2<R> a = xcol[i0], b = xcol[i1], c = yrow[j0], d = yrow[j1];
+    return V4<R>{min(a.x, b.x) + min(c.x, d.x), min(a.y, b.y) + min(c.y, d.y),
+                 max(a.x, b.x) + max(c.x, d.x), max(a.y, b.y) + max(c.y, d.y)};
+}
+
+constexpr int kOrderThreads = 1024;
+
+// Stable partition of the n items: heavy (sample box within the asymptotic
+// radius of the voxel box) first.  ADJ selects the adjoint item layout
+// (tile = 32 x kAdjTileY voxels, chunk = chunk_len samples) or the forward
+// one (tile = kFwdTile samples, chunk = chunk_rows rows of all columns).
+template <typename R, bool ADJ>
+__global__ void __launch_bounds__(kOrderThreads)
+k_item_order(int64_t n, int n_tiles, int tiles_x, int chunk, int nx, int ny,
+             const V2<R> *__restrict__ xcol, const V2<R> *__restrict__ yrow,
+             const V4<R> *__restrict__ sbox, int *__restrict__ order)
+{
+    __shared__ int s_h[32], s_l[32];
+    __shared__ int s_base[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    auto heavy = [&](int64_t it) -> bool {
+        const int c = (int)(it / n_tiles), tile = (int)(it % n_tiles);
+        V4<R> vb, sb;
+        if (ADJ) {
+            const int tx = tile % tiles_x, ty = tile / tiles_x;
+            const int i0 = tx * kAdjTileX, j0 = ty * kAdjTileY;
+            vb = voxel_box(xcol, yrow, i0, min(nx - 1, i0 + kAdjTileX - 1), j0, min(ny - 1, j0 + kAdjTileY - 1));
+            sb = sbox[c];
+        } else {
+            const int j0 = c * chunk;
+            vb = voxel_box(xcol, yrow, 0, nx - 1, j0, min(ny - 1, j0 + chunk - 1));
+            sb = sbox[tile];
+        }
+        const R gx = max(R(0), max(vb.x - sb.z, sb.x - vb.z));
+        const R gy = max(R(0), max(vb.y - sb.w, sb.y - vb.w));
+        return gx * gx + gy * gy < vfar_threshold<R, false>();
+    };
+    int n_heavy = 0;
+    for (int64_t b = 0; b < n; b += kOrderThreads) {
+        const int64_t it = b + threadIdx.x;
+        n_heavy += __syncthreads_count(it < n && heavy(it));
+    }
+    if (threadIdx.x == 0) s_base[0] = 0, s_base[1] = n_heavy;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t b = 0; b < n; b += kOrderThreads) {
+        const int64_t it = b + threadIdx.x;
+        const bool valid = it < n;
+        const bool hv = valid && heavy(it);
+        const unsigned hb = __ballot_sync(0xffffffffu, hv), lb = __ballot_sync(0xffffffffu, valid && !hv);
+        if (lane == 0) s_h[w] = __popc(hb), s_l[w] = __popc(lb);
+        __syncthreads();
+        int hpre = 0, lpre = 0, htot = 0, ltot = 0;
+        for (int k = 0; k < kOrderThreads / 32; ++k) {
+            if (k < w) hpre += s_h[k], lpre += s_l[k];
+            htot += s_h[k], ltot += s_l[k];
+        }
+        if (hv) order[s_base[0] + hpre + __popc(hb & lt)] = (int)it;
+        else if (valid) order[s_base[1] + lpre + __popc(lb & lt)] = (int)it;
+        __syncthreads();
+        if (threadIdx.x == 0) s_base[0] += htot, s_base[1] += ltot;
+        __syncthreads();
+    }
+}
+
+template <typename R>
+size_t item_order_bytes(const FwdSplit *fs, const AdjSplit *as)
+{
+    size_t b = 4 * 256;
+    if (fs) b += sizeof(int) * size_t(fs->n_tiles) * fs->n_chunks + sizeof(V4<R>) * fs->n_tiles;
+    if (as) b += sizeof(int) * size_t(as->tiles_x) * as->tiles_y * as->n_chunks + sizeof(V4<R>) * as->n_chunks;
+    return b;
+}
+
+template <typename R>
+int prepare_item_orders(const GridH &g, int64_t T, const Geometry<R> &geo, FwdSplit *fs, AdjSplit *as,
+                        void *scratch, cudaStream_t st)
+{
+    if (fs) fs->order = nullptr;
+    if (as) as->order = nullptr;
+    if (T == 0) return MPI_OK;
+    char *p = static_cast<char *>(scratch);
+    auto take = [&](size_t b) {
+        char *q = p;
+        p += (b + 255) & ~size_t(255);
+        return q;
+    };
+    if (fs) {
+        const int64_t nf = (int64_t)fs->n_tiles * fs->n_chunks;
+        int *fo = reinterpret_cast<int *>(take(sizeof(int) * nf));
+        V4<R> *fb = reinterpret_cast<V4<R> *>(take(sizeof(V4<R>) * fs->n_tiles));
+        if (nf <= INT32_MAX) {
+            k_sample_boxes<R><<<(unsigned)((int64_t(fs->n_tiles) * 32 + 255) / 256), 256, 0, st>>>(
+                geo.rw, T, kFwdTile, fs->n_tiles, fb);
+            MPI_CHECK_LAUNCH();
+            k_item_order<R, false><<<1, kOrderThreads, 0, st>>>(nf, fs->n_tiles, 0, fs->chunk_rows, g.nx,
+                                                                g.ny, geo.xcol, geo.yrow, fb, fo);
+            MPI_CHECK_LAUNCH();
+            fs->order = fo;
+        }
+    }
+    if (as) {
+        const int64_t na = (int64_t)as->tiles_x * as->tiles_y * as->n_chunks;
+        int *ao = reinterpret_cast<int *>(take(sizeof(int) * na));
+        V4<R> *ab = reinterpret_cast<V4<R> *>(take(sizeof(V4<R>) * as->n_chunks));
+        if (na <= INT32_MAX) {
+            k_sample_boxes<R><<<(unsigned)((int64_t(as->n_chunks) * 32 + 255) / 256), 256, 0, st>>>(
+                geo.rw, T, as->chunk_len, as->n_chunks, ab);
+            MPI_CHECK_LAUNCH();
+            k_item_order<R, true><<<1, kOrderThreads, 0, st>>>(na, as->tiles_x * as->tiles_y, as->tiles_x,
+                                                               as->chunk_len, g.nx, g.ny, geo.xcol,
+                                                               geo.yrow, ab, ao);
+            MPI_CHECK_LAUNCH();
+            as->order = ao;
+        }
+    }
+    return MPI_OK;
+}
+
+template size_t item_order_bytes<float>(const FwdSplit *, const AdjSplit *);
+template size_t item_order_bytes<double>(const FwdSplit *, const AdjSplit *);
+template int prepare_item_orders<float>(const GridH &, int64_t, const Geometry<float> &, FwdSplit *,
+                                        AdjSplit *, void *, cudaStream_t);
+template int prepare_item_orders<double>(const GridH &, int64_t, const Geometry<double> &, FwdSplit *,
+                                         AdjSplit *, void *, cudaStream_t);
+
 template <typename R>
 size_t forward_partial_bytes(const FwdSplit &sp, int n_ch, int64_t T)
 {
@@ -278,6 +439,7 @@ int launch_forward(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
     B.f[0].chunk = sp.chunk_rows;
     B.f[0].rows_staged = sp.rows_staged;
     B.f[0].near_cols = near_columns<R>(m, g);
+    B.f[0].order = sp.order;
     const size_t smem = sizeof(V2<R>) * (g.nx + sp.rows_staged + size_t(sp.rows_staged) * g.nx);
     const int64_t items = (int64_t)sp.n_tiles * sp.n_chunks;
     {
@@ -313,6 +475,7 @@ int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
         B.f[0].n_tiles = sp.tiles_x * sp.tiles_y;
         B.f[0].tiles_x = sp.tiles_x;
         B.f[0].chunk = sp.chunk_len;
+        B.f[0].order = sp.order;
         const int64_t items = (int64_t)sp.tiles_x * sp.tiles_y * sp.n_chunks;
         ProfScope prof(kProfAdjoint, st);
         if (is_diag(m))
@@ -358,6 +521,7 @@ int launch_dbeta(const ModelH &m, const GridH &g, int64_t T, const Geometry<R> &
     B.f[0].n_tiles = sp.tiles_x * sp.tiles_y;
     B.f[0].tiles_x = sp.tiles_x;
     B.f[0].chunk = sp.chunk_len;
+    B.f[0].order = sp.order;
     const int64_t items = (int64_t)sp.tiles_x * sp.tiles_y * sp.n_chunks;
     {
         ProfScope prof(kProfDbeta, st);

@@ -39,11 +39,15 @@ int prepare_geometry(const ModelH &m, const GridH &g, int64_t T, const void *r, 
                      const Geometry<R> &geo, cudaStream_t st);
 
 // Work decomposition of one operator application on one frame.
+// `order` (device, nullable): the dispatch order of the work items (block b
+// runs item order[b]); see prepare_item_orders.
 struct FwdSplit {
     int n_tiles, n_chunks, chunk_rows, rows_staged;
+    const int *order = nullptr;
 };
 struct AdjSplit {
     int tiles_x, tiles_y, n_chunks, chunk_len;
+    const int *order = nullptr;
 };
 FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_items);
 AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items);
@@ -51,6 +55,18 @@ int default_target_items();
 // Column half-width around a sample that can hold a near-FFP pair (forward).
 template <typename R>
 int near_columns(const ModelH &m, const GridH &g);
+
+// Dispatch orders of the work items of one frame: items whose samples come
+// within the asymptotic radius (u < 144) of their voxels cost up to ~1.7x the
+// others, so they are dispatched first (stable partition by a bounding-box
+// test on the prepared geometry) and the cheap ones fill the end of the
+// launch.  The order changes no result: every item writes its own slot.
+// Scratch: item_order_bytes; fills fs->order / as->order (either may be NULL).
+template <typename R>
+size_t item_order_bytes(const FwdSplit *fs, const AdjSplit *as);
+template <typename R>
+int prepare_item_orders(const GridH &g, int64_t T, const Geometry<R> &geo, FwdSplit *fs,
+                        AdjSplit *as, void *scratch, cudaStream_t st);
 
 // Partial-sum scratch sizes (bytes).
 template <typename R>

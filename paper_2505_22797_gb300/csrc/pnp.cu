@@ -332,11 +332,12 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
     const int target = default_target_items();
 
     Scratch scr(st);
-    size_t o_geo = 0, o_fp = 0, o_ap = 0, o_sA = 0, o_K = 0, o_t1 = 0, o_t2 = 0;
+    size_t o_geo = 0, o_fp = 0, o_ap = 0, o_sA = 0, o_K = 0, o_t1 = 0, o_t2 = 0, o_ord = 0;
     if (S.op == MPI_OP_FORWARD) {
         S.fs = forward_split(S.T, g.nx, g.ny, sizeof(R), target);
         S.as = adjoint_split(S.T, g.nx, g.ny, target);
         o_geo = scr.reserve(geometry_bytes<R>(S.T, g.nx, g.ny));
+        o_ord = scr.reserve(item_order_bytes<R>(&S.fs, &S.as));
         o_fp = scr.reserve(forward_partial_bytes<R>(S.fs, m.n_ch, S.T));
         o_ap = scr.reserve(adjoint_partial_bytes<R>(S.as, g.nx, g.ny));
         o_sA = scr.reserve(sizeof(R) * size_t(m.n_ch) * size_t(std::max<int64_t>(S.T, 1)));
@@ -352,6 +353,7 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
         S.adj_part = scr.at<R>(o_ap);
         S.sA = scr.at<R>(o_sA);
         MPI_TRY(prepare_geometry<R>(m, g, S.T, tr->r, tr->v, S.geo, st));
+        MPI_TRY(prepare_item_orders<R>(g, S.T, S.geo, &S.fs, &S.as, scr.at<char>(o_ord), st));
     } else {
         MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &S.K, st, o.kernel_component - 1));
         S.tmp1 = scr.at<R>(o_t1);
