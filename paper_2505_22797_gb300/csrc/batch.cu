@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(256) k_reduce_batch(const __grid_constant__ Re
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = b * 32 + lane;
     double acc = 0.0;
-    if (e < F.len)
+    if (e < F.len) {
+#pragma unroll 8
         for (int c = w; c < F.n_chunks; c += 8) acc += double(F.part[(int64_t)c * F.len + e]);
+    }
     sh[w][lane] = acc;
     __syncthreads();
     if (w == 0) {

@@ -52,35 +52,69 @@ static AxisMap make_axis(double p0, double h, int n)
     return AxisMap{1.0 / h, -p0 / h - 0.5, n};
 }
 
+// Interpolation record of one sample: its cell (i0, j0) and the upper-node
+// cosine weights along x and y (the lower ones are 1 - w).  Fixed for a
+// trajectory, so the Core Stage computes them once per solve.
+template <typename R>
+struct alignas(2 * sizeof(R) + 8 > 16 ? 8 : 16) InterpRec {
+    int i0, j0;
+    R wx1, wy1;
+};
+
+template <typename R>
+__device__ __forceinline__ InterpRec<R> make_rec(R px, R py, const AxisMap &ax, const AxisMap &ay)
+{
+    InterpRec<R> q;
+    R w0;
+    axis_weights<R>(px, ax, q.i0, w0, q.wx1);
+    axis_weights<R>(py, ay, q.j0, w0, q.wy1);
+    return q;
+}
+
+constexpr int kInterpSPT = 4;  // samples per thread (independent gathers in flight)
+
 // s[k][t] = sum_m I[Ahat_{2k+m}](r_t) v_m(t)   (Ahat of type AT, s of type R).
 // CH < 0: both channels, Ahat has 4 components, s 2 rows.  CH = k: only
-// channel k, Ahat holds (A_k0, A_k1) and s one row.
-template <typename R, typename AT, int CH>
-__global__ void k_interp(int64_t T, const R *__restrict__ r, const R *__restrict__ v,
-                         const AT *__restrict__ A, AxisMap ax, AxisMap ay, R *__restrict__ s)
+// channel k, Ahat holds (A_k0, A_k1) and s one row.  PRE: the records come
+// precomputed (rec), else they are formed from r.  Each thread handles
+// kInterpSPT samples a block apart, so its gathers are independent.
+template <typename R, typename AT, int CH, bool PRE>
+__global__ void __launch_bounds__(256)
+k_interp(int64_t T, const R *__restrict__ r, const InterpRec<R> *__restrict__ rec,
+         const R *__restrict__ v, const AT *__restrict__ A, AxisMap ax, AxisMap ay, R *__restrict__ s)
 {
     const int nx = ax.n;
     const int64_t N = (int64_t)ax.n * ay.n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int i0, j0;
-        R wx0, wx1, wy0, wy1;
-        axis_weights<R>(r[2 * t], ax, i0, wx0, wx1);
-        axis_weights<R>(r[2 * t + 1], ay, j0, wy0, wy1);
-        const int i1 = ax.n > 1 ? i0 + 1 : i0, j1 = ay.n > 1 ? j0 + 1 : j0;
-        const R vx = v[2 * t], vy = v[2 * t + 1];
-        constexpr int K = CH < 0 ? 2 : 1;
+    constexpr int K = CH < 0 ? 2 : 1;
+    const int64_t span = (int64_t)blockDim.x * kInterpSPT;
+    for (int64_t base = blockIdx.x * span + threadIdx.x; base < T; base += (int64_t)gridDim.x * span) {
+        InterpRec<R> q[kInterpSPT];
+        V2<R> vv[kInterpSPT];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            R acc = R(0);
+        for (int u = 0; u < kInterpSPT; ++u) {
+            const int64_t t = min(base + u * (int64_t)blockDim.x, T - 1);
+            if constexpr (PRE) q[u] = rec[t];
+            else q[u] = make_rec<R>(r[2 * t], r[2 * t + 1], ax, ay);
+            vv[u] = V2<R>{v[2 * t], v[2 * t + 1]};
+        }
 #pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const AT *F = A + (CH < 0 ? 2 * k + m : m) * N;
-                const R val = wy0 * (wx0 * R(F[(int64_t)j0 * nx + i0]) + wx1 * R(F[(int64_t)j0 * nx + i1])) +
-                              wy1 * (wx0 * R(F[(int64_t)j1 * nx + i0]) + wx1 * R(F[(int64_t)j1 * nx + i1]));
-                acc += val * (m == 0 ? vx : vy);
+        for (int u = 0; u < kInterpSPT; ++u) {
+            const int64_t t = base + u * (int64_t)blockDim.x;
+            const int i0 = q[u].i0, j0 = q[u].j0;
+            const int i1 = ax.n > 1 ? i0 + 1 : i0, j1 = ay.n > 1 ? j0 + 1 : j0;
+            const R wx1 = q[u].wx1, wy1 = q[u].wy1, wx0 = R(1) - wx1, wy0 = R(1) - wy1;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                R acc = R(0);
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const AT *F = A + (CH < 0 ? 2 * k + m : m) * N;
+                    const R val = wy0 * (wx0 * R(F[(int64_t)j0 * nx + i0]) + wx1 * R(F[(int64_t)j0 * nx + i1])) +
+                                  wy1 * (wx0 * R(F[(int64_t)j1 * nx + i0]) + wx1 * R(F[(int64_t)j1 * nx + i1]));
+                    acc += val * (m == 0 ? vv[u].x : vv[u].y);
+                }
+                if (t < T) s[(int64_t)k * T + t] = acc;
             }
-            s[(int64_t)k * T + t] = acc;
         }
     }
 }
@@ -89,15 +123,14 @@ __global__ void k_interp(int64_t T, const R *__restrict__ r, const R *__restrict
 
 template <typename R>
 __global__ void k_cell_count(int64_t T, const R *__restrict__ r, AxisMap ax, AxisMap ay, int ncx,
-                             int *__restrict__ cell_of, int *__restrict__ count)
+                             int *__restrict__ cell_of, int *__restrict__ count,
+                             InterpRec<R> *__restrict__ rec)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
          t += (int64_t)gridDim.x * blockDim.x) {
-        int i0, j0;
-        R w0, w1;
-        axis_weights<R>(r[2 * t], ax, i0, w0, w1);
-        axis_weights<R>(r[2 * t + 1], ay, j0, w0, w1);
-        const int c = j0 * ncx + i0;
+        const InterpRec<R> q = make_rec<R>(r[2 * t], r[2 * t + 1], ax, ay);
+        rec[t] = q;
+        const int c = q.j0 * ncx + q.i0;
         cell_of[t] = c;
         atomicAdd(&count[c], 1);
     }
@@ -173,71 +206,173 @@ __global__ void k_cell_sort(int n_cells, const int *__restrict__ offset, int *__
 }
 
 // Ahat_{2k+m}(node) = sum over samples t of the adjacent cells of
-// w_node(t) v_m(t) s_k(t).  CH = k: only channel k (s one row), output the two
-// components (A_k0, A_k1).
-template <typename R, typename OUT, int CH>
-__global__ void k_interp_T(const R *__restrict__ r, const R *__restrict__ v, const R *__restrict__ s,
-                           int64_t T, AxisMap ax, AxisMap ay, int ncx, int ncy,
-                           const int *__restrict__ offset, const int *__restrict__ list,
-                           OUT *__restrict__ A, double scale)
+// w_node(t) v_m(t) s_k(t), with rec, vs and s in list (cell) order.  CH = k:
+// only channel k (s one row), output the two components (A_k0, A_k1).  One warp per node: the lanes stride over the
+// samples of the node's (up to) four cells, then a fixed butterfly sums the
+// lanes, so a node whose cells hold many samples (a trajectory that dwells)
+// costs one warp a longer loop instead of stalling 31 other nodes.
+// The transpose is organised in work units of at most kUnitLen consecutive
+// entries of a node's samples (its four cells' runs, in cell order), so a
+// node next to cells where the trajectory dwells (thousands of samples)
+// spreads over many units instead of keeping one group of lanes busy alone.
+// Unit sums are combined per node in unit order (deterministic).
+constexpr int kUnitLen = 128;
+constexpr int kUnitLanes = 8;     // lanes per unit
+constexpr int kUnitThreads = 256;
+
+// Samples in the (up to) four cells around node (i, j), in cell order.
+__device__ __forceinline__ int node_cells(int i, int j, int ncx, int ncy, int c[4])
 {
-    const int nx = ax.n, ny = ay.n;
-    const int64_t N = (int64_t)nx * ny;
+    int n = 0;
+    for (int cj = j - 1; cj <= j; ++cj) {
+        if (cj < 0 || cj >= ncy) continue;
+        for (int ci = i - 1; ci <= i; ++ci) {
+            if (ci < 0 || ci >= ncx) continue;
+            c[n++] = cj * ncx + ci;
+        }
+    }
+    return n;
+}
+
+__global__ void k_unit_count(int nx, int ny, int ncx, int ncy, const int *__restrict__ offset,
+                             int *__restrict__ unit_cnt)
+{
+    const int N = nx * ny;
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
+        int c[4];
+        const int nc = node_cells(node % nx, node / nx, ncx, ncy, c);
+        int tot = 0;
+        for (int k = 0; k < nc; ++k) tot += offset[c[k] + 1] - offset[c[k]];
+        unit_cnt[node] = max(1, (tot + kUnitLen - 1) / kUnitLen);
+    }
+}
+
+__global__ void k_unit_fill(int N, const int *__restrict__ unit_off, int *__restrict__ unit_node)
+{
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x)
+        for (int w = unit_off[node]; w < unit_off[node + 1]; ++w) unit_node[w] = node;
+}
+
+// Partial sums of one unit: sum over its entries of w_node(t) v_m(t) s_k(t),
+// with rec, vs and s in list (cell) order.  CH = k: only channel k (s one row,
+// two components).  n_iter: the unit bound rounded up to whole blocks, so
+// every warp runs the same iterations and its shuffles see full warps.
+template <typename R, int CH>
+__global__ void __launch_bounds__(kUnitThreads)
+k_interp_T_units(const InterpRec<R> *__restrict__ rec, const R *__restrict__ vs, const R *__restrict__ s,
+                 int64_t T, int nx, int ncx, int ncy, const int *__restrict__ offset,
+                 const int *__restrict__ unit_off, const int *__restrict__ unit_node, int N, int n_iter,
+                 R *__restrict__ unit_part)
+{
     constexpr int NC = CH < 0 ? 4 : 2;
-    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < N;
-         node += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(node % nx), j = (int)(node / nx);
+    constexpr int G = kUnitLanes;
+    constexpr int per_block = kUnitThreads / G;
+    const int sub = threadIdx.x % G;
+    const int n_units = unit_off[N];
+    for (int base = blockIdx.x * per_block; base < n_iter; base += gridDim.x * per_block) {
+        const int w = base + (int)threadIdx.x / G;
         R acc[NC];
 #pragma unroll
         for (int m = 0; m < NC; ++m) acc[m] = R(0);
-        for (int cj = j - 1; cj <= j; ++cj) {
-            if (cj < 0 || cj >= ncy) continue;
-            for (int ci = i - 1; ci <= i; ++ci) {
-                if (ci < 0 || ci >= ncx) continue;
-                const int c = cj * ncx + ci;
-                for (int q = offset[c]; q < offset[c + 1]; ++q) {
-                    const int64_t t = list[q];
-                    int i0, j0;
-                    R wx0, wx1, wy0, wy1;
-                    axis_weights<R>(r[2 * t], ax, i0, wx0, wx1);
-                    axis_weights<R>(r[2 * t + 1], ay, j0, wy0, wy1);
-                    const R wx = (i == i0) ? wx0 : wx1;
-                    const R wy = (j == j0) ? wy0 : wy1;
-                    const R w = wy * wx;
-                    const R vx = v[2 * t], vy = v[2 * t + 1];
+        if (w < n_units) {
+            const int node = unit_node[w];
+            const int i = node % nx, j = node / nx;
+            const int p0 = (w - unit_off[node]) * kUnitLen, p1 = p0 + kUnitLen;
+            int c[4];
+            const int nc = node_cells(i, j, ncx, ncy, c);
+            int pos = 0;
+            for (int k = 0; k < nc; ++k) {
+                const int q_base = offset[c[k]], cnt = offset[c[k] + 1] - q_base;
+                const int lo = max(p0, pos), hi = min(p1, pos + cnt);
+#pragma unroll 4
+                for (int pp = lo + sub; pp < hi; pp += G) {
+                    const int q = q_base + (pp - pos);
+                    const InterpRec<R> rc = rec[q];
+                    const R wx = (i == rc.i0) ? R(1) - rc.wx1 : rc.wx1;
+                    const R wy = (j == rc.j0) ? R(1) - rc.wy1 : rc.wy1;
+                    const R wt = wy * wx;
+                    const R vx = vs[2 * q], vy = vs[2 * q + 1];
                     if constexpr (CH < 0) {
-                        const R s0 = s[t], s1 = s[T + t];
-                        acc[0] += w * (vx * s0);
-                        acc[1] += w * (vy * s0);
-                        acc[2] += w * (vx * s1);
-                        acc[3] += w * (vy * s1);
+                        const R s0 = s[q], s1 = s[T + q];
+                        acc[0] += wt * (vx * s0);
+                        acc[1] += wt * (vy * s0);
+                        acc[2] += wt * (vx * s1);
+                        acc[3] += wt * (vy * s1);
                     } else {
-                        const R sk = s[t];
-                        acc[0] += w * (vx * sk);
-                        acc[1] += w * (vy * sk);
+                        const R sk = s[q];
+                        acc[0] += wt * (vx * sk);
+                        acc[1] += wt * (vy * sk);
                     }
                 }
+                pos += cnt;
             }
         }
 #pragma unroll
-        for (int m = 0; m < NC; ++m) A[m * N + node] = OUT(double(acc[m]) * scale);
+        for (int m = 0; m < NC; ++m) {
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+        }
+        if (sub == 0 && w < n_units) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) unit_part[(int64_t)w * NC + m] = acc[m];
+        }
+    }
+}
+
+// Ahat_m(node) = scale * sum of the node's unit partials, in unit order.
+template <typename R, typename OUT, int NC>
+__global__ void k_interp_T_combine(int N, const int *__restrict__ unit_off, const R *__restrict__ unit_part,
+                                   OUT *__restrict__ A, double scale)
+{
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
+        double acc[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) acc[m] = 0.0;
+        for (int w = unit_off[node]; w < unit_off[node + 1]; ++w)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) acc[m] += double(unit_part[(int64_t)w * NC + m]);
+#pragma unroll
+        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(acc[m] * scale);
     }
 }
 
 // Binning scratch for a trajectory on a grid.
+// Samples binned by interpolation cell.  list: sample indices sorted by cell
+// (ascending index within a cell); offset: start of each cell's run.  rec /
+// vs: the samples' interpolation records and velocities in list order, so a
+// cell's samples are one contiguous run of every per-sample array (the Core
+// Stage keeps its sample vectors in this order as well).
 struct Bins {
     int *cell_of, *count, *offset, *cursor, *list;
+    void *rec_t;  // InterpRec<R>[T], sample order (scratch of the binning)
+    void *rec;    // InterpRec<R>[T], list order
+    void *vs;     // R[T][2], list order
+    // Work units of the transpose (see kUnitLen): per node unit_off[node] ..
+    // unit_off[node + 1]; the node of each unit; 4 partial sums per unit.
+    int *unit_cnt, *unit_off, *unit_cursor, *unit_node;
+    void *unit_part;
+    int n_units_max;
     int ncx, ncy;
 };
 
+static int units_bound(int64_t T, int nx, int ny)
+{
+    return (int)std::min<int64_t>(INT32_MAX, (int64_t)nx * ny + (4 * T + kUnitLen - 1) / kUnitLen + 1);
+}
+
+template <typename R>
 static size_t bins_bytes(int64_t T, int nx, int ny)
 {
     const size_t nc = size_t(std::max(nx - 1, 1)) * std::max(ny - 1, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t N = size_t(nx) * ny, U = size_t(units_bound(T, nx, ny));
     return up(sizeof(int) * std::max<int64_t>(T, 1)) * 2 + up(sizeof(int) * nc) * 2 +
-           up(sizeof(int) * (nc + 1));
+           up(sizeof(int) * (nc + 1)) + 2 * up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1)) +
+           up(2 * sizeof(R) * std::max<int64_t>(T, 1)) + up(sizeof(int) * N) * 2 + up(sizeof(int) * (N + 1)) +
+           up(sizeof(int) * U) + up(4 * sizeof(R) * U);
 }
 
+template <typename R>
 static Bins bins_carve(char *p, int64_t T, int nx, int ny)
 {
     Bins b;
@@ -249,20 +384,57 @@ static Bins bins_carve(char *p, int64_t T, int nx, int ny)
     b.list = reinterpret_cast<int *>(p); p += up(sizeof(int) * std::max<int64_t>(T, 1));
     b.count = reinterpret_cast<int *>(p); p += up(sizeof(int) * nc);
     b.cursor = reinterpret_cast<int *>(p); p += up(sizeof(int) * nc);
-    b.offset = reinterpret_cast<int *>(p);
+    b.offset = reinterpret_cast<int *>(p); p += up(sizeof(int) * (nc + 1));
+    b.rec_t = p; p += up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1));
+    b.rec = p; p += up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1));
+    b.vs = p; p += up(2 * sizeof(R) * std::max<int64_t>(T, 1));
+    const size_t N = size_t(nx) * ny;
+    b.n_units_max = units_bound(T, nx, ny);
+    b.unit_cnt = reinterpret_cast<int *>(p); p += up(sizeof(int) * N);
+    b.unit_cursor = reinterpret_cast<int *>(p); p += up(sizeof(int) * N);
+    b.unit_off = reinterpret_cast<int *>(p); p += up(sizeof(int) * (N + 1));
+    b.unit_node = reinterpret_cast<int *>(p); p += up(sizeof(int) * size_t(b.n_units_max));
+    b.unit_part = p;
     return b;
 }
 
 static int grid_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
 
 template <typename R>
-static int build_bins(const GridH &g, int64_t T, const R *r, const Bins &b, cudaStream_t st)
+__global__ void k_sort_records(int64_t T, const int *__restrict__ list, const InterpRec<R> *__restrict__ rec_t,
+                               const R *__restrict__ v, InterpRec<R> *__restrict__ rec, R *__restrict__ vs)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = list[q];
+        rec[q] = rec_t[t];
+        vs[2 * q] = v[2 * t];
+        vs[2 * q + 1] = v[2 * t + 1];
+    }
+}
+
+template <typename R>
+__global__ void k_gather_rows(int64_t T, int n_rows, const int *__restrict__ list, const R *__restrict__ in,
+                              R *__restrict__ out)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = list[q];
+        for (int k = 0; k < n_rows; ++k) out[(int64_t)k * T + q] = in[(int64_t)k * T + t];
+    }
+}
+
+// Bins the samples, orders their records and velocities by cell and builds
+// the transpose's work units.
+template <typename R>
+static int build_bins(const GridH &g, int64_t T, const R *r, const R *v, const Bins &b, cudaStream_t st)
 {
     const AxisMap ax = make_axis(g.x0, g.dx, g.nx), ay = make_axis(g.y0, g.dy, g.ny);
     const int nc = b.ncx * b.ncy;
     MPI_TRY_CUDA(cudaMemsetAsync(b.count, 0, sizeof(int) * nc, st));
     if (T > 0) {
-        k_cell_count<R><<<grid_blocks(T), 256, 0, st>>>(T, r, ax, ay, b.ncx, b.cell_of, b.count);
+        k_cell_count<R><<<grid_blocks(T), 256, 0, st>>>(T, r, ax, ay, b.ncx, b.cell_of, b.count,
+                                                         static_cast<InterpRec<R> *>(b.rec_t));
         MPI_CHECK_LAUNCH();
     }
     k_scan<<<1, kScanThreads, 0, st>>>(b.count, nc, b.offset, b.cursor);
@@ -272,35 +444,75 @@ static int build_bins(const GridH &g, int64_t T, const R *r, const Bins &b, cuda
         MPI_CHECK_LAUNCH();
         k_cell_sort<<<(nc + 127) / 128, 128, 0, st>>>(nc, b.offset, b.list);
         MPI_CHECK_LAUNCH();
+        k_sort_records<R><<<grid_blocks(T), 256, 0, st>>>(T, b.list, static_cast<const InterpRec<R> *>(b.rec_t),
+                                                          v, static_cast<InterpRec<R> *>(b.rec),
+                                                          static_cast<R *>(b.vs));
+        MPI_CHECK_LAUNCH();
     }
-    return MPI_OK;
-}
-
-template <typename R, typename AT>
-static int launch_interp(const GridH &g, int64_t T, const R *r, const R *v, const AT *A, R *s,
-                         cudaStream_t st, int ch = -1)
-{
-    if (T == 0) return MPI_OK;
-    const AxisMap ax = make_axis(g.x0, g.dx, g.nx), ay = make_axis(g.y0, g.dy, g.ny);
-    if (ch < 0) k_interp<R, AT, -1><<<grid_blocks(T), 256, 0, st>>>(T, r, v, A, ax, ay, s);
-    else if (ch == 0) k_interp<R, AT, 0><<<grid_blocks(T), 256, 0, st>>>(T, r, v, A, ax, ay, s);
-    else k_interp<R, AT, 1><<<grid_blocks(T), 256, 0, st>>>(T, r, v, A, ax, ay, s);
+    // Work units of the transpose.
+    const int N = g.nx * g.ny;
+    k_unit_count<<<grid_blocks(N), 256, 0, st>>>(g.nx, g.ny, b.ncx, b.ncy, b.offset, b.unit_cnt);
+    MPI_CHECK_LAUNCH();
+    k_scan<<<1, kScanThreads, 0, st>>>(b.unit_cnt, N, b.unit_off, b.unit_cursor);
+    MPI_CHECK_LAUNCH();
+    k_unit_fill<<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, b.unit_node);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
 
-template <typename R, typename OUT>
-static int launch_interp_T(const GridH &g, int64_t T, const R *r, const R *v, const R *s,
-                           const Bins &b, OUT *A, double scale, cudaStream_t st, int ch = -1)
+// out[k][q] = in[k][list[q]] for the n_rows rows of a [n_rows][T] array.
+template <typename R>
+static int gather_rows(int64_t T, int n_rows, const int *list, const R *in, R *out, cudaStream_t st)
 {
+    if (T == 0) return MPI_OK;
+    k_gather_rows<R><<<grid_blocks(T), 256, 0, st>>>(T, n_rows, list, in, out);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// rec (nullable): precomputed records of the samples (Core Stage).
+template <typename R, typename AT>
+static int launch_interp(const GridH &g, int64_t T, const R *r, const R *v, const AT *A, R *s,
+                         cudaStream_t st, int ch = -1, const InterpRec<R> *rec = nullptr)
+{
+    if (T == 0) return MPI_OK;
     const AxisMap ax = make_axis(g.x0, g.dx, g.nx), ay = make_axis(g.y0, g.dy, g.ny);
-    const int64_t N = (int64_t)g.nx * g.ny;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((T + 256 * kInterpSPT - 1) / (256 * kInterpSPT), 8192));
+    if (rec) {
+        if (ch < 0) k_interp<R, AT, -1, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+        else if (ch == 0) k_interp<R, AT, 0, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+        else k_interp<R, AT, 1, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+    } else {
+        if (ch < 0) k_interp<R, AT, -1, false><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+        else if (ch == 0) k_interp<R, AT, 0, false><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+        else k_interp<R, AT, 1, false><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+    }
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// s_sorted: the samples' values in list order ([rows][T]).
+// s_sorted: the samples' values in list order ([rows][T]).
+template <typename R, typename OUT>
+static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const Bins &b, OUT *A, double scale,
+                           cudaStream_t st, int ch = -1)
+{
+    const int N = g.nx * g.ny;
+    constexpr int per_block = kUnitThreads / kUnitLanes;
+    const int n_iter = (b.n_units_max + per_block - 1) / per_block * per_block;
+    const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, 65535));
+    const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(b.rec);
+    const R *vs = static_cast<const R *>(b.vs);
+    R *part = static_cast<R *>(b.unit_part);
     if (ch < 0)
-        k_interp_T<R, OUT, -1><<<grid_blocks(N), 256, 0, st>>>(r, v, s, T, ax, ay, b.ncx, b.ncy, b.offset,
-                                                              b.list, A, scale);
+        k_interp_T_units<R, -1><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, g.nx, b.ncx, b.ncy, b.offset,
+                                                                 b.unit_off, b.unit_node, N, n_iter, part);
     else
-        k_interp_T<R, OUT, 0><<<grid_blocks(N), 256, 0, st>>>(r, v, s, T, ax, ay, b.ncx, b.ncy, b.offset,
-                                                             b.list, A, scale);
+        k_interp_T_units<R, 0><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, g.nx, b.ncx, b.ncy, b.offset,
+                                                                b.unit_off, b.unit_node, N, n_iter, part);
+    MPI_CHECK_LAUNCH();
+    if (ch < 0) k_interp_T_combine<R, OUT, 4><<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, part, A, scale);
+    else k_interp_T_combine<R, OUT, 2><<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, part, A, scale);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
@@ -378,8 +590,9 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     const R *s = static_cast<const R *>(s_in);
 
     Scratch scr(st);
-    const size_t o_bins = scr.reserve(bins_bytes(T, g.nx, g.ny));
+    const size_t o_bins = scr.reserve(bins_bytes<R>(T, g.nx, g.ny));
     const size_t o_s = scr.reserve(sizeof(R) * (ch < 0 ? 2 : 1) * std::max<int64_t>(T, 1));
+    const size_t o_sd = scr.reserve(sizeof(R) * (ch < 0 ? 2 : 1) * std::max<int64_t>(T, 1));
     const size_t vb = sizeof(double) * n4;
     const size_t o_b = scr.reserve(vb), o_x = scr.reserve(vb), o_r = scr.reserve(vb),
                  o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_y = scr.reserve(vb),
@@ -387,7 +600,7 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     const size_t o_parts = scr.reserve(sizeof(double) * 3 * nblk);
     const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 8);
     MPI_TRY(scr.allocate());
-    const Bins bins = bins_carve(scr.at<char>(o_bins), T, g.nx, g.ny);
+    const Bins bins = bins_carve<R>(scr.at<char>(o_bins), T, g.nx, g.ny);
     R *s_tmp = scr.at<R>(o_s);
     double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x), *rr = scr.at<double>(o_r),
            *p = scr.at<double>(o_p), *q = scr.at<double>(o_q), *y = scr.at<double>(o_y),
@@ -396,10 +609,13 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     double *scal = scr.at<double>(o_sc);
     int *done = reinterpret_cast<int *>(scal + 8), *iters = done + 1;
 
-    MPI_TRY(build_bins<R>(g, T, r, bins, st));
+    MPI_TRY(build_bins<R>(g, T, r, v, bins, st));
     const double invT = T > 0 ? 1.0 / double(T) : 0.0;
+    // The sample vectors of the solve live in list (cell) order.
+    R *s_data = scr.at<R>(o_sd);
+    MPI_TRY(gather_rows<R>(T, ch < 0 ? 2 : 1, bins.list, s, s_data, st));
     // b = (1/T) M^T s
-    MPI_TRY((launch_interp_T<R, double>(g, T, r, v, s, bins, b, invT, st, ch)));
+    MPI_TRY((launch_interp_T<R, double>(g, T, s_data, bins, b, invT, st, ch)));
     MPI_TRY_CUDA(cudaMemsetAsync(x, 0, vb, st));
     MPI_TRY_CUDA(cudaMemsetAsync(q, 0, vb, st));
     MPI_TRY_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 + sizeof(int) * 8, st));
@@ -420,8 +636,9 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     const int poll = 16;
     for (int it = 0; it < o.max_iter; ++it) {
         // q = (1/T) M^T M p + gamma Lap Lap p
-        MPI_TRY((launch_interp<R, double>(g, T, r, v, p, s_tmp, st, ch)));
-        MPI_TRY((launch_interp_T<R, double>(g, T, r, v, s_tmp, bins, y, invT, st, ch)));
+        MPI_TRY((launch_interp<R, double>(g, T, r, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
+                                          static_cast<const InterpRec<R> *>(bins.rec))));
+        MPI_TRY((launch_interp_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch)));
         k_lap<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, nc, p, l1);
         MPI_CHECK_LAUNCH();
         k_lap<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, nc, l1, l2);
@@ -461,12 +678,14 @@ static int interp_T_impl(const GridH &g, const mpi_traj *tr, const void *s, void
 {
     const int64_t T = tr->T;
     Scratch scr(st);
-    const size_t o_bins = scr.reserve(bins_bytes(T, g.nx, g.ny));
+    const size_t o_bins = scr.reserve(bins_bytes<R>(T, g.nx, g.ny));
+    const size_t o_ss = scr.reserve(sizeof(R) * 2 * std::max<int64_t>(T, 1));
     MPI_TRY(scr.allocate());
-    const Bins bins = bins_carve(scr.at<char>(o_bins), T, g.nx, g.ny);
-    MPI_TRY(build_bins<R>(g, T, static_cast<const R *>(tr->r), bins, st));
-    return launch_interp_T<R, R>(g, T, static_cast<const R *>(tr->r), static_cast<const R *>(tr->v),
-                                 static_cast<const R *>(s), bins, static_cast<R *>(A), 1.0, st);
+    const Bins bins = bins_carve<R>(scr.at<char>(o_bins), T, g.nx, g.ny);
+    R *s_sorted = scr.at<R>(o_ss);
+    MPI_TRY(build_bins<R>(g, T, static_cast<const R *>(tr->r), static_cast<const R *>(tr->v), bins, st));
+    MPI_TRY(gather_rows<R>(T, 2, bins.list, static_cast<const R *>(s), s_sorted, st));
+    return launch_interp_T<R, R>(g, T, s_sorted, bins, static_cast<R *>(A), 1.0, st);
 }
 
 static int check_interp_args(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype)

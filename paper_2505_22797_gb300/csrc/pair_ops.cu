@@ -322,8 +322,12 @@ k_reduce_chunks(const R *__restrict__ part, int n_chunks, int64_t len, OUT *__re
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * 32 + lane;
     double acc = 0.0;
-    if (e < len)
+    if (e < len) {
+        // Sequential sum over this warp's chunks; the unroll only lets the
+        // loads run ahead (the additions keep their order).
+#pragma unroll 8
         for (int c = w; c < n_chunks; c += kRedWarps) acc += double(part[(int64_t)c * len + e]);
+    }
     sh[w][lane] = acc;
     __syncthreads();
     if (w == 0) {

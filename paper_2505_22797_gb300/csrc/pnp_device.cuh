@@ -10,7 +10,9 @@
 namespace mpi {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecPerBlock = 2048;  // equals the block size of the adjoint CG epilogue
+// Elements per block of the CG vector kernels (and so the number of partial
+// sums of r.r): small enough that a 128 x 128 problem spreads over 32 blocks.
+constexpr int kVecPerBlock = 512;
 constexpr int kStatThreads = 1024;
 
 // Sum of `n` partials in a fixed order, computed by the whole block and

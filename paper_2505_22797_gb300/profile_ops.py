@@ -25,7 +25,8 @@ from paper_2505_22797_gb300 import synthetic as syn  # noqa: E402
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--op", choices=["forward", "adjoint", "dbeta", "conv", "all"], default="all")
+    ap.add_argument("--op", choices=["forward", "adjoint", "dbeta", "conv", "interp", "interp_T", "grid",
+                                     "all"], default="all")
     ap.add_argument("--workload", default="c2", help="c1, c2, c2_partial, c4, c5 or 3d")
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--warmup", type=int, default=2)
@@ -53,11 +54,16 @@ def main(argv=None):
         }
     else:
         s = api.mpi_forward(m, g, r, v, c)
+        field = torch.stack([c, 0.5 * c, 0.25 * c, c]).contiguous()
+        s2 = torch.empty_like(s)
         ops = {
             "forward": lambda: api.mpi_forward(m, g, r, v, c, s=s),
             "adjoint": lambda: api.mpi_adjoint(m, g, r, v, s, c_out=out),
             "dbeta": lambda: api.mpi_dbeta(m, g, r, v, c, s),
             "conv": lambda: api.mpi_conv(m, g, c, out=out),
+            "interp": lambda: api.mpi_interp(g, r, v, field, s=s2),
+            "interp_T": lambda: api.mpi_interp_adjoint(g, r, v, s, Ahat=field),
+            "grid": lambda: api.mpi_grid(g, r, v, s, gamma=1e-7, max_iter=2, rel_tol=0.0),
         }
     names = list(ops) if args.op == "all" else [args.op]
     pairs = c.numel() * r.shape[0]
@@ -77,9 +83,9 @@ def main(argv=None):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         best = min(ms)
-        rate = "" if name == "conv" else f"  {pairs / best / 1e6:.1f} Gpair/s"
+        rate = "" if name in ("conv", "interp", "interp_T", "grid") else f"  {pairs / best / 1e6:.1f} Gpair/s"
         line = f"{args.workload} {args.dtype} {name}: best {best:.3f} ms of {args.reps}{rate}"
-        if args.kernel:
+        if args.kernel and name in ("forward", "adjoint", "dbeta", "conv"):
             cls = {"forward": api.PROF_FORWARD, "adjoint": api.PROF_ADJOINT,
                    "dbeta": api.PROF_DBETA, "conv": api.PROF_CONV}[name]
             api.mpi_profile_enable(True)
