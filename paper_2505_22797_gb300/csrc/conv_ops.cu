@@ -3,13 +3,24 @@
 // exact linear (zero-padded) convolution over all voxel offsets:
 //   out[j][i] = sum_{j'i'} kappa_G(x_ij - x_i'j') in[j'][i'],
 //   kappa_G(y) = beta tr(K(beta G y) G).
-// The kernel is sampled once per call in FP64 and rounded to the call's type.
-// The direct sum costs N^2 FMAs; each block computes a 16 x 16 output tile
-// and walks the input in 16 x 16 tiles staged with the matching kernel window
-// in shared memory.  Per-tile sums are folded with compensated additions.
+// The kernel is sampled once per call in FP64.  Two routes compute the same
+// sum:
+//  * direct (small grids): N^2 FMAs in the call's type; each block computes a
+//    16 x 16 output tile and walks the input in 16 x 16 tiles staged with the
+//    matching kernel window in shared memory; per-tile sums are folded with
+//    compensated additions;
+//  * FFT (N >= MPI_CONV_FFT_MIN_N, 80 x 80 and up, where it overtakes the
+//    direct sum on GB300): the kernel placed circularly on an NY x NX grid,
+//    NX and NY the powers of two >= 2 nx - 1 and 2 ny - 1,
+//    so the circular convolution of the zero-padded input equals the linear
+//    one on the nx x ny window; 2-D DFTs in FP64 (row passes of the Stockham
+//    FFT, a tiled transpose, row passes again), the kernel's spectrum kept in
+//    the transposed layout, the inverse by the conjugation identity
+//    IDFT(Y) = conj(DFT(conj Y)) / n.  O(N log N) instead of N^2.
 #include <algorithm>
 
 #include "conv_ops.cuh"
+#include "fft.cuh"
 #include "langevin.cuh"
 
 namespace mpi {
@@ -133,6 +144,186 @@ int launch_conv(const GridH &g, const R *K, const IN *in, OUT *out, cudaStream_t
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
+
+// ---------------------------------------------------------------------------
+// FFT route.
+
+#ifndef MPI_CONV_FFT_MIN_N
+#define MPI_CONV_FFT_MIN_N 6400
+#endif
+
+// Padded length: the power of two >= n (radix-4/2 passes only; measured on
+// GB300 faster than the shortest 7-smooth length, whose radix-5/7 passes take
+// the generic butterfly).
+static int nice_length(int n)
+{
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    return p2;
+}
+
+bool conv_uses_fft(int nx, int ny) { return (int64_t)nx * ny >= MPI_CONV_FFT_MIN_N; }
+
+// The sampled kernel placed circularly: kc[dj mod NY][di mod NX] = K[dj][di].
+__global__ void k_conv_circ(int nx, int ny, int NX, int NY, const double *__restrict__ K,
+                            double2 *__restrict__ kc)
+{
+    const int KX = 2 * nx - 1;
+    const int64_t n = (int64_t)NX * NY;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % NX), j = (int)(e / NX);
+        const int di = i < nx ? i : i - NX, dj = j < ny ? j : j - NY;
+        double v = 0.0;
+        if (di > -nx && di < nx && dj > -ny && dj < ny) v = K[(int64_t)(dj + ny - 1) * KX + (di + nx - 1)];
+        kc[e] = make_double2(v, 0.0);
+    }
+}
+
+template <typename IN>
+__global__ void k_conv_load(int nx, int ny, int NX, int NY, const IN *__restrict__ in, double2 *__restrict__ a)
+{
+    const int64_t n = (int64_t)NX * NY;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % NX), j = (int)(e / NX);
+        a[e] = make_double2(i < nx && j < ny ? double(in[(int64_t)j * nx + i]) : 0.0, 0.0);
+    }
+}
+
+// dst[c][r] = src[r][c] for a rows x cols complex matrix (32 x 32 tiles).
+__global__ void __launch_bounds__(32 * 8)
+k_transpose_c(int rows, int cols, const double2 *__restrict__ src, double2 *__restrict__ dst)
+{
+    __shared__ double2 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = src[(int64_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[(int64_t)c * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
+__global__ void k_spec_mul_conj(int64_t n, double2 *__restrict__ t, const double2 *__restrict__ kh)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 p = cmul(t[e], kh[e]);
+        t[e] = make_double2(p.x, -p.y);
+    }
+}
+
+template <typename OUT>
+__global__ void k_conv_crop(int nx, int ny, int NX, const double2 *__restrict__ a, double scale,
+                            OUT *__restrict__ out)
+{
+    const int64_t n = (int64_t)nx * ny;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % nx), j = (int)(e / nx);
+        out[e] = OUT(a[(int64_t)j * NX + i].x * scale);
+    }
+}
+
+static unsigned elem_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
+
+static int transpose_c(int rows, int cols, const double2 *src, double2 *dst, cudaStream_t st)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    k_transpose_c<<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, dst);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// 2-D DFT of a [NY][NX] (in a); result transposed, [NX][NY], in t.  a is
+// clobbered (it is the ping-pong partner of the column passes).
+template <typename R>
+static int dft2_to_t(const ConvPlan<R> &P, double2 *a, double2 *t, cudaStream_t st)
+{
+    MPI_TRY(fft_run(P.px, a, t, P.NY, P.NX, P.WX, st));
+    MPI_TRY(transpose_c(P.NY, P.NX, a, t, st));
+    return fft_run(P.py, t, a, P.NX, P.NY, P.WY, st);
+}
+
+size_t conv_plan_bytes(int nx, int ny, int elem_bytes)
+{
+    size_t b = conv_kernel_bytes(nx, ny, elem_bytes);
+    if (conv_uses_fft(nx, ny)) {
+        const size_t NX = nice_length(2 * nx - 1), NY = nice_length(2 * ny - 1);
+        b += sizeof(double2) * (NX + NY + 3 * NX * NY) + 6 * 256;
+    }
+    return b;
+}
+
+template <typename R>
+int conv_plan_prepare(const ModelH &m, const GridH &g, void *scratch, ConvPlan<R> &P, cudaStream_t st, int comp)
+{
+    P.nx = g.nx;
+    P.ny = g.ny;
+    P.fft = conv_uses_fft(g.nx, g.ny);
+    R *K = nullptr;
+    MPI_TRY(conv_prepare_kernel<R>(m, g, scratch, &K, st, comp));
+    P.K = K;
+    if (!P.fft) return MPI_OK;
+    P.NX = nice_length(2 * g.nx - 1);
+    P.NY = nice_length(2 * g.ny - 1);
+    plan_fft(P.NX, P.px);
+    plan_fft(P.NY, P.py);
+    char *p = static_cast<char *>(scratch) + ((conv_kernel_bytes(g.nx, g.ny, sizeof(R)) + 255) & ~size_t(255));
+    auto take = [&](size_t n) {
+        double2 *q = reinterpret_cast<double2 *>(p);
+        p += (sizeof(double2) * n + 255) & ~size_t(255);
+        return q;
+    };
+    const int64_t n = (int64_t)P.NX * P.NY;
+    P.WX = take(P.NX);
+    P.WY = take(P.NY);
+    P.Kh = take(n);
+    P.a = take(n);
+    P.t = take(n);
+    MPI_TRY(fft_twiddles(P.NX, P.WX, st));
+    MPI_TRY(fft_twiddles(P.NY, P.WY, st));
+    // The sampled kernel in FP64 is the first piece of the scratch.
+    k_conv_circ<<<elem_blocks(n), 256, 0, st>>>(g.nx, g.ny, P.NX, P.NY, static_cast<const double *>(scratch), P.a);
+    MPI_CHECK_LAUNCH();
+    return dft2_to_t(P, P.a, P.Kh, st);
+}
+
+template <typename R, typename IN, typename OUT>
+int conv_apply(const ConvPlan<R> &P, const IN *in, OUT *out, cudaStream_t st)
+{
+    if (!P.fft) {
+        GridH g{};
+        g.nx = P.nx;
+        g.ny = P.ny;
+        return launch_conv<R, IN, OUT>(g, P.K, in, out, st);
+    }
+    const int64_t n = (int64_t)P.NX * P.NY;
+    ProfScope prof(kProfConv, st);
+    k_conv_load<IN><<<elem_blocks(n), 256, 0, st>>>(P.nx, P.ny, P.NX, P.NY, in, P.a);
+    MPI_CHECK_LAUNCH();
+    MPI_TRY(dft2_to_t(P, P.a, P.t, st));
+    k_spec_mul_conj<<<elem_blocks(n), 256, 0, st>>>(n, P.t, P.Kh);
+    MPI_CHECK_LAUNCH();
+    // DFT of the conjugated product: columns (rows of t), transpose back, rows.
+    MPI_TRY(fft_run(P.py, P.t, P.a, P.NX, P.NY, P.WY, st));
+    MPI_TRY(transpose_c(P.NX, P.NY, P.t, P.a, st));
+    MPI_TRY(fft_run(P.px, P.a, P.t, P.NY, P.NX, P.WX, st));
+    k_conv_crop<OUT><<<elem_blocks((int64_t)P.nx * P.ny), 256, 0, st>>>(P.nx, P.ny, P.NX, P.a, 1.0 / double(n), out);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+template int conv_plan_prepare<float>(const ModelH &, const GridH &, void *, ConvPlan<float> &, cudaStream_t, int);
+template int conv_plan_prepare<double>(const ModelH &, const GridH &, void *, ConvPlan<double> &, cudaStream_t, int);
+template int conv_apply<float, float, float>(const ConvPlan<float> &, const float *, float *, cudaStream_t);
+template int conv_apply<float, double, float>(const ConvPlan<float> &, const double *, float *, cudaStream_t);
+template int conv_apply<float, float, double>(const ConvPlan<float> &, const float *, double *, cudaStream_t);
+template int conv_apply<double, double, double>(const ConvPlan<double> &, const double *, double *, cudaStream_t);
 
 template int conv_prepare_kernel<float>(const ModelH &, const GridH &, void *, float **, cudaStream_t, int);
 template int conv_prepare_kernel<double>(const ModelH &, const GridH &, void *, double **, cudaStream_t, int);

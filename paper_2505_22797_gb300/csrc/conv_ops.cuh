@@ -1,6 +1,7 @@
 // Internal interface of the sampled-trace-kernel convolution C.
 #pragma once
 
+#include "fft.cuh"
 #include "pair_ops.cuh"
 
 namespace mpi {
@@ -18,5 +19,26 @@ int conv_prepare_kernel(const ModelH &m, const GridH &g, void *scratch, R **K_ou
 // out = C in  (in: IN [ny][nx], out: OUT [ny][nx], must not overlap).
 template <typename R, typename IN, typename OUT>
 int launch_conv(const GridH &g, const R *K, const IN *in, OUT *out, cudaStream_t st);
+
+// The operator C of one grid, by the direct sum (small grids) or by FFT
+// (N >= MPI_CONV_FFT_MIN_N); scratch: conv_plan_bytes.
+template <typename R>
+struct ConvPlan {
+    int nx = 0, ny = 0;
+    bool fft = false;
+    const R *K = nullptr;  // direct route: the sampled kernel
+    int NX = 0, NY = 0;    // FFT route: circular grid
+    FftPlan px, py;
+    double2 *WX = nullptr, *WY = nullptr, *Kh = nullptr, *a = nullptr, *t = nullptr;
+};
+bool conv_uses_fft(int nx, int ny);
+size_t conv_plan_bytes(int nx, int ny, int elem_bytes);
+template <typename R>
+int conv_plan_prepare(const ModelH &m, const GridH &g, void *scratch, ConvPlan<R> &P, cudaStream_t st,
+                      int comp = -1);
+// out = C in.  The FFT route uses the plan's buffers: one application at a
+// time per plan (calls on one stream are ordered).
+template <typename R, typename IN, typename OUT>
+int conv_apply(const ConvPlan<R> &P, const IN *in, OUT *out, cudaStream_t st);
 
 }  // namespace mpi

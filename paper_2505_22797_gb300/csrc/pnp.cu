@@ -284,7 +284,8 @@ struct PnPOp2D final : PnPOperator<R> {
     FwdSplit fs{};
     AdjSplit as{};
     R *fwd_part = nullptr, *adj_part = nullptr, *sA = nullptr;
-    R *K = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;
+    ConvPlan<R> C;
+    R *tmp1 = nullptr, *tmp2 = nullptr;
     int64_t N = 0;
     mpi_denoise_fn den = nullptr;
     void *user = nullptr;
@@ -294,7 +295,7 @@ struct PnPOp2D final : PnPOperator<R> {
         if (op == MPI_OP_FORWARD)
             return launch_adjoint<R, double>(m, g, T, geo, as, data, adj_part, b0, nullptr, nullptr,
                                              nullptr, st);
-        return launch_conv<R, R, double>(g, K, data, b0, st);
+        return conv_apply<R, R, double>(C, data, b0, st);
     }
     int apply_normal(const double *v, double *q, const double *nu_dev, double *pq_part,
                      cudaStream_t st) override
@@ -303,8 +304,8 @@ struct PnPOp2D final : PnPOperator<R> {
             MPI_TRY((launch_forward<R, double, R>(m, g, T, geo, fs, v, fwd_part, sA, st)));
             return launch_adjoint<R, double>(m, g, T, geo, as, sA, adj_part, q, v, nu_dev, pq_part, st);
         }
-        MPI_TRY((launch_conv<R, double, R>(g, K, v, tmp1, st)));
-        MPI_TRY((launch_conv<R, R, R>(g, K, tmp1, tmp2, st)));
+        MPI_TRY((conv_apply<R, double, R>(C, v, tmp1, st)));
+        MPI_TRY((conv_apply<R, R, R>(C, tmp1, tmp2, st)));
         return axpy_dot_launch<R>(N, tmp2, v, nu_dev, q, pq_part, st);
     }
     int n_pq() const override { return op == MPI_OP_FORWARD ? adjoint_dot_blocks(g.nx, g.ny) : vec_blocks(N); }
@@ -342,7 +343,7 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
         o_ap = scr.reserve(adjoint_partial_bytes<R>(S.as, g.nx, g.ny));
         o_sA = scr.reserve(sizeof(R) * size_t(m.n_ch) * size_t(std::max<int64_t>(S.T, 1)));
     } else {
-        o_K = scr.reserve(conv_kernel_bytes(g.nx, g.ny, sizeof(R)));
+        o_K = scr.reserve(conv_plan_bytes(g.nx, g.ny, sizeof(R)));
         o_t1 = scr.reserve(sizeof(R) * S.N);
         o_t2 = scr.reserve(sizeof(R) * S.N);
     }
@@ -355,7 +356,7 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
         MPI_TRY(prepare_geometry<R>(m, g, S.T, tr->r, tr->v, S.geo, st));
         MPI_TRY(prepare_item_orders<R>(g, S.T, S.geo, &S.fs, &S.as, scr.at<char>(o_ord), st));
     } else {
-        MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &S.K, st, o.kernel_component - 1));
+        MPI_TRY(conv_plan_prepare<R>(m, g, scr.at<char>(o_K), S.C, st, o.kernel_component - 1));
         S.tmp1 = scr.at<R>(o_t1);
         S.tmp2 = scr.at<R>(o_t2);
     }
@@ -367,11 +368,11 @@ static int conv_impl(const ModelH &m, const GridH &g, const void *in, void *out,
                      int comp = -1)
 {
     Scratch scr(st);
-    const size_t o_K = scr.reserve(conv_kernel_bytes(g.nx, g.ny, sizeof(R)));
+    const size_t o_K = scr.reserve(conv_plan_bytes(g.nx, g.ny, sizeof(R)));
     MPI_TRY(scr.allocate());
-    R *K = nullptr;
-    MPI_TRY(conv_prepare_kernel<R>(m, g, scr.at<char>(o_K), &K, st, comp));
-    return launch_conv<R, R, R>(g, K, static_cast<const R *>(in), static_cast<R *>(out), st);
+    ConvPlan<R> C;
+    MPI_TRY(conv_plan_prepare<R>(m, g, scr.at<char>(o_K), C, st, comp));
+    return conv_apply<R, R, R>(C, static_cast<const R *>(in), static_cast<R *>(out), st);
 }
 
 template int launch_gauss5<float>(const float *, float *, int, int, cudaStream_t);

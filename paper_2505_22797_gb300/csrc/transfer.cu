@@ -9,9 +9,7 @@
 //
 // The DFTs run in FP64 on the device (they are a negligible share of a
 // reconstruction, and the division by a_hat amplifies round-off where
-// |a_hat| is small): a Stockham autosort FFT with one launch per radix pass
-// (radices 4, 2 and every prime up to kMaxRadix, each pass a generic radix-R
-// butterfly with twiddles from a per-length table), and Bluestein's chirp-z
+// |a_hat| is small): the Stockham FFT of fft.cu, and Bluestein's chirp-z
 // algorithm (Bluestein 1970: a length-T DFT as a convolution with the chirp
 // exp(-i pi m^2 / T), evaluated with power-of-two FFTs) for lengths with a
 // larger prime factor.  Channels run as the y dimension of every launch.
@@ -19,118 +17,11 @@
 #include <cmath>
 #include <vector>
 
-#include "common.cuh"
+#include "fft.cuh"
 
 namespace mpi {
 
 int check_dtype(mpi_dtype d);
-
-constexpr int kMaxRadix = 127;
-constexpr int kFftThreads = 256;
-
-struct FftPlan {
-    int64_t n = 0;
-    std::vector<int> radix;  // product = n
-};
-
-static bool plan_fft(int64_t n, FftPlan &p)
-{
-    p.n = n;
-    p.radix.clear();
-    int64_t m = n;
-    while (m % 4 == 0) p.radix.push_back(4), m /= 4;
-    if (m % 2 == 0) p.radix.push_back(2), m /= 2;
-    for (int q = 3; q <= kMaxRadix && m > 1; q += 2)
-        while (m % q == 0) p.radix.push_back(q), m /= q;
-    return m == 1;
-}
-
-// W[m] = exp(-2 pi i m / n), m < n.
-__global__ void k_twiddles(int64_t n, double2 *__restrict__ W)
-{
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n;
-         m += (int64_t)gridDim.x * blockDim.x) {
-        double s, c;
-        sincospi(-2.0 * double(m) / double(n), &s, &c);
-        W[m] = make_double2(c, s);
-    }
-}
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
-{
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-
-// One Stockham pass of radix R after passes whose radices multiply to Ns:
-// butterfly j (k = j mod Ns) reads x[j + i n/R], i < R, and writes
-//   y[(j/Ns) Ns R + k + q Ns] = sum_i x[j + i n/R] W^{i (k + q Ns) n/(Ns R)}.
-// `dist` is the distance between channels (blockIdx.y).
-__global__ void __launch_bounds__(kFftThreads)
-k_fft_pass(const double2 *__restrict__ x, double2 *__restrict__ y, int64_t n, int R, int64_t Ns,
-           const double2 *__restrict__ W, int64_t dist)
-{
-    const double2 *xc = x + blockIdx.y * dist;
-    double2 *yc = y + blockIdx.y * dist;
-    const int64_t nb = n / R;
-    const int64_t NsR = Ns * R;
-    const int64_t step = n / NsR;  // table stride for the NsR-th roots
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nb;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = j % Ns;
-        const int64_t out0 = (j / Ns) * NsR + k;
-        if (R == 2) {
-            const double2 a = xc[j], b = cmul(xc[j + nb], W[k * step]);
-            yc[out0] = make_double2(a.x + b.x, a.y + b.y);
-            yc[out0 + Ns] = make_double2(a.x - b.x, a.y - b.y);
-        } else if (R == 4) {
-            const double2 a0 = xc[j];
-            const double2 a1 = cmul(xc[j + nb], W[k * step]);
-            const double2 a2 = cmul(xc[j + 2 * nb], W[2 * k * step]);
-            const double2 a3 = cmul(xc[j + 3 * nb], W[3 * k * step]);
-            const double2 s02 = make_double2(a0.x + a2.x, a0.y + a2.y);
-            const double2 d02 = make_double2(a0.x - a2.x, a0.y - a2.y);
-            const double2 s13 = make_double2(a1.x + a3.x, a1.y + a3.y);
-            const double2 d13 = make_double2(a1.x - a3.x, a1.y - a3.y);
-            // omega_4 = -i:  d13 * (-i) = (d13.y, -d13.x)
-            yc[out0] = make_double2(s02.x + s13.x, s02.y + s13.y);
-            yc[out0 + Ns] = make_double2(d02.x + d13.y, d02.y - d13.x);
-            yc[out0 + 2 * Ns] = make_double2(s02.x - s13.x, s02.y - s13.y);
-            yc[out0 + 3 * Ns] = make_double2(d02.x - d13.y, d02.y + d13.x);
-        } else {
-            for (int q = 0; q < R; ++q) {
-                const int64_t e = k + (int64_t)q * Ns;  // exponent base over NsR
-                double2 acc = make_double2(0.0, 0.0);
-                for (int i = 0; i < R; ++i) {
-                    const int64_t m = ((int64_t)i * e) % NsR;
-                    const double2 t = cmul(xc[j + i * nb], W[m * step]);
-                    acc.x += t.x;
-                    acc.y += t.y;
-                }
-                yc[out0 + q * Ns] = acc;
-            }
-        }
-    }
-}
-
-static unsigned fft_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + kFftThreads - 1) / kFftThreads, 4096)); }
-
-// In-place in the sense of buffers: the transform of `a` ends in `a` (b is
-// scratch of the same size).  n_ch channels at distance `dist`.
-static int fft_run(const FftPlan &p, double2 *a, double2 *b, int n_ch, int64_t dist,
-                   const double2 *W, cudaStream_t st)
-{
-    double2 *src = a, *dst = b;
-    int64_t Ns = 1;
-    for (int R : p.radix) {
-        dim3 grid(fft_blocks(p.n / R), n_ch);
-        k_fft_pass<<<grid, kFftThreads, 0, st>>>(src, dst, p.n, R, Ns, W, dist);
-        MPI_CHECK_LAUNCH();
-        Ns *= R;
-        std::swap(src, dst);
-    }
-    if (src != a) MPI_TRY_CUDA(cudaMemcpyAsync(a, src, sizeof(double2) * (n_ch * dist), cudaMemcpyDeviceToDevice, st));
-    return MPI_OK;
-}
 
 // ---------------------------------------------------------------------------
 // Bluestein: X_k = c_k sum_m (x_m c_m) conj(c_{k-m}),  c_m = exp(-i pi m^2 / n).
@@ -243,13 +134,8 @@ struct Dft {
     }
     int prepare(cudaStream_t st)
     {
-        if (!blue) {
-            k_twiddles<<<fft_blocks(n), kFftThreads, 0, st>>>(n, W);
-            MPI_CHECK_LAUNCH();
-            return MPI_OK;
-        }
-        k_twiddles<<<fft_blocks(M), kFftThreads, 0, st>>>(M, WM);
-        MPI_CHECK_LAUNCH();
+        if (!blue) return fft_twiddles(n, W, st);
+        MPI_TRY(fft_twiddles(M, WM, st));
         k_chirp<<<fft_blocks(n), kFftThreads, 0, st>>>(n, chirp);
         MPI_CHECK_LAUNCH();
         k_bluestein_b<<<fft_blocks(M), kFftThreads, 0, st>>>(n, M, chirp, Bq);

@@ -196,3 +196,32 @@ def test_pnp_forward_single_channel(orc, dt):
     want = _oracle_pnp(orc, m, g, r, v, s, 4, 4, nu0)
     got = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), 4, 4, nu0)
     assert rel_l2(host(got), want) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("shape", [(80, 80), (128, 128), (97, 113), (181, 64)])
+def test_conv_fft_route(orc, dt, shape):
+    """Grids of 6400 voxels and more take the FFT route (circular convolution
+    on a padded grid): same linear convolution as the oracle's direct sum."""
+    nx, ny = shape
+    g = syn.square_grid(nx, 24.0, ny)
+    for m in (syn.default_model(), dict(syn.default_model(), G=[[2.1e-3, 4e-4], [4e-4, -2.6e-3]])):
+        x = rounded(np.random.default_rng(nx + ny).normal(size=(ny, nx)), dt)
+        want = orc.conv(g, orc.conv_kernel(m, g), x)
+        assert rel_l2(host(api.mpi_conv(m, g, dev(x, dt))), want) <= tol(dt)
+    comp = orc.conv_kernel(m, g, component=(1, 0))
+    got = api.mpi_conv_component(m, g, 2, dev(x, dt))
+    assert rel_l2(host(got), orc.conv(g, comp, x)) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_pnp_conv_fft_route(orc, dt):
+    """Algorithm 1 with C on a 100 x 100 grid (FFT route), few steps."""
+    g = syn.square_grid(100, 24.0)
+    m = syn.default_model()
+    u = rounded(np.random.default_rng(12).normal(size=(100, 100)) + 1.0, dt)
+    kern = orc.conv_kernel(m, g)
+    op = lambda x: orc.conv(g, kern, x)  # noqa: E731
+    want = orc.pnp(op, op, u, (100, 100), 2, 3, 0.05)
+    got = api.mpi_pnp_solve(m, g, None, None, dev(u, dt), 2, 3, 0.05, op=api.MPI_OP_CONV)
+    assert rel_l2(host(got), want) <= tol(dt)
