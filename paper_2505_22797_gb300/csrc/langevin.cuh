@@ -131,19 +131,33 @@ template <> struct Lang<float> {
     }
 };
 
+// 1/sqrt(u) in FP64 by Newton's method for f(y) = 1/y^2 - u (the classical
+// inverse-square-root iteration y <- y + y (1 - u y^2)/2), started from the
+// FP32 hardware estimate: each step squares the relative error (2^-22 ->
+// ~2^-43 -> below FP64 rounding), with FMAs only.  Valid for u in the FP32
+// normal range (the asymptotic forms use it for u >= 441).
+__device__ __forceinline__ double rsqrt_newton(double u)
+{
+    double y = double(rsqrt_approx(float(u)));
+    double h = fma(-u * y, y, 1.0);
+    y = fma(0.5 * y, h, y);
+    h = fma(-u * y, y, 1.0);
+    return fma(0.5 * y, h, y);
+}
+
 template <> struct Lang<double> {
     static constexpr double near_u = kNearU64;
     static constexpr double vfar_u = kVfarU64, vfar_u_beta = kVfarU64Beta;
 
     static __device__ __forceinline__ void ad_vfar(double u, double &a, double &d)
     {
-        const double iz = 1.0 / sqrt(u), iz2 = iz * iz;
+        const double iz = rsqrt_newton(u), iz2 = iz * iz;
         a = iz - iz2;
         d = fma(iz2, 2.0, -iz) * iz2;
     }
     static __device__ __forceinline__ void le_vfar(double u, double &lp, double &e)
     {
-        const double iz = 1.0 / sqrt(u);
+        const double iz = rsqrt_newton(u);
         lp = iz * iz;
         e = -2.0 * lp * lp;
     }
