@@ -133,10 +133,11 @@ int mpi_dbeta(const mpi_model *model, const mpi_grid_desc *grid,
  *   kappa_G(y) = beta tr(K(beta G y) G)
  * as a linear (zero-padded) convolution over all voxel offsets.  C is
  * symmetric.  in/out are [ny][nx] and must not overlap.  Grids below 6400
- * voxels use the direct sum in the call's dtype; larger ones the FFT route
- * (circular convolution on a padded grid, FP64 DFTs), the same operator up to
- * round-off.  Allocates scratch (the sampled kernel; for the FFT route three
- * complex FP64 copies of the padded grid). */
+ * voxels (FP32) or 1024 voxels (FP64) use the direct sum in the call's
+ * dtype; larger ones the FFT route
+ * (circular convolution on a padded grid, DFTs in the call's precision), the
+ * same operator up to round-off.  Allocates scratch (the sampled kernel; for
+ * the FFT route three complex copies of the padded grid). */
 int mpi_conv(const mpi_model *model, const mpi_grid_desc *grid, mpi_dtype dtype,
              const void *in, void *out, void *stream);
 

@@ -9,12 +9,14 @@
 //    16 x 16 output tile and walks the input in 16 x 16 tiles staged with the
 //    matching kernel window in shared memory; per-tile sums are folded with
 //    compensated additions;
-//  * FFT (N >= MPI_CONV_FFT_MIN_N, 80 x 80 and up, where it overtakes the
+//  * FFT (from 80 x 80 in FP32 and 32 x 32 in FP64, where it overtakes the
 //    direct sum on GB300): the kernel placed circularly on an NY x NX grid,
 //    NX and NY the powers of two >= 2 nx - 1 and 2 ny - 1,
 //    so the circular convolution of the zero-padded input equals the linear
-//    one on the nx x ny window; 2-D DFTs in FP64 (row passes of the Stockham
-//    FFT, a tiled transpose, row passes again), the kernel's spectrum kept in
+//    one on the nx x ny window; 2-D DFTs in the call's precision (FP32 for
+//    FP32 calls: GB300's FP64 pipe bounds FP64 passes), as row passes of the
+//    Stockham FFT, a tiled transpose and row passes again; the kernel's
+//    spectrum kept in
 //    the transposed layout, the inverse by the conjugation identity
 //    IDFT(Y) = conj(DFT(conj Y)) / n.  O(N log N) instead of N^2.
 #include <algorithm>
@@ -148,8 +150,14 @@ int launch_conv(const GridH &g, const R *K, const IN *in, OUT *out, cudaStream_t
 // ---------------------------------------------------------------------------
 // FFT route.
 
+// Smallest grid (voxels) for the FFT route: where it overtook the direct sum
+// on GB300 (FP32: 80 x 80; FP64, whose direct sum runs on the slow FP64 pipe:
+// 32 x 32).
 #ifndef MPI_CONV_FFT_MIN_N
 #define MPI_CONV_FFT_MIN_N 6400
+#endif
+#ifndef MPI_CONV_FFT_MIN_N64
+#define MPI_CONV_FFT_MIN_N64 1024
 #endif
 
 // Padded length: the power of two >= n (radix-4/2 passes only; measured on
@@ -162,11 +170,15 @@ static int nice_length(int n)
     return p2;
 }
 
-bool conv_uses_fft(int nx, int ny) { return (int64_t)nx * ny >= MPI_CONV_FFT_MIN_N; }
+bool conv_uses_fft(int nx, int ny, int elem_bytes)
+{
+    return (int64_t)nx * ny >= (elem_bytes == 8 ? MPI_CONV_FFT_MIN_N64 : MPI_CONV_FFT_MIN_N);
+}
 
 // The sampled kernel placed circularly: kc[dj mod NY][di mod NX] = K[dj][di].
+template <typename C>
 __global__ void k_conv_circ(int nx, int ny, int NX, int NY, const double *__restrict__ K,
-                            double2 *__restrict__ kc)
+                            C *__restrict__ kc)
 {
     const int KX = 2 * nx - 1;
     const int64_t n = (int64_t)NX * NY;
@@ -176,26 +188,27 @@ __global__ void k_conv_circ(int nx, int ny, int NX, int NY, const double *__rest
         const int di = i < nx ? i : i - NX, dj = j < ny ? j : j - NY;
         double v = 0.0;
         if (di > -nx && di < nx && dj > -ny && dj < ny) v = K[(int64_t)(dj + ny - 1) * KX + (di + nx - 1)];
-        kc[e] = make_double2(v, 0.0);
+        kc[e] = make_cx<C>(v, 0.0);
     }
 }
 
-template <typename IN>
-__global__ void k_conv_load(int nx, int ny, int NX, int NY, const IN *__restrict__ in, double2 *__restrict__ a)
+template <typename IN, typename C>
+__global__ void k_conv_load(int nx, int ny, int NX, int NY, const IN *__restrict__ in, C *__restrict__ a)
 {
     const int64_t n = (int64_t)NX * NY;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % NX), j = (int)(e / NX);
-        a[e] = make_double2(i < nx && j < ny ? double(in[(int64_t)j * nx + i]) : 0.0, 0.0);
+        a[e] = make_cx<C>(i < nx && j < ny ? double(in[(int64_t)j * nx + i]) : 0.0, 0.0);
     }
 }
 
 // dst[c][r] = src[r][c] for a rows x cols complex matrix (32 x 32 tiles).
+template <typename C>
 __global__ void __launch_bounds__(32 * 8)
-k_transpose_c(int rows, int cols, const double2 *__restrict__ src, double2 *__restrict__ dst)
+k_transpose_c(int rows, int cols, const C *__restrict__ src, C *__restrict__ dst)
 {
-    __shared__ double2 tile[32][33];
+    __shared__ C tile[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += 8) {
         const int r = r0 + k, c = c0 + threadIdx.x;
@@ -208,33 +221,35 @@ k_transpose_c(int rows, int cols, const double2 *__restrict__ src, double2 *__re
     }
 }
 
-__global__ void k_spec_mul_conj(int64_t n, double2 *__restrict__ t, const double2 *__restrict__ kh)
+template <typename C>
+__global__ void k_spec_mul_conj(int64_t n, C *__restrict__ t, const C *__restrict__ kh)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const double2 p = cmul(t[e], kh[e]);
-        t[e] = make_double2(p.x, -p.y);
+        const C p = cmul(t[e], kh[e]);
+        t[e] = cxv(p.x, -p.y);
     }
 }
 
-template <typename OUT>
-__global__ void k_conv_crop(int nx, int ny, int NX, const double2 *__restrict__ a, double scale,
+template <typename OUT, typename C>
+__global__ void k_conv_crop(int nx, int ny, int NX, const C *__restrict__ a, double scale,
                             OUT *__restrict__ out)
 {
     const int64_t n = (int64_t)nx * ny;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % nx), j = (int)(e / nx);
-        out[e] = OUT(a[(int64_t)j * NX + i].x * scale);
+        out[e] = OUT(double(a[(int64_t)j * NX + i].x) * scale);
     }
 }
 
 static unsigned elem_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
 
-static int transpose_c(int rows, int cols, const double2 *src, double2 *dst, cudaStream_t st)
+template <typename C>
+static int transpose_c(int rows, int cols, const C *src, C *dst, cudaStream_t st)
 {
     dim3 grid((cols + 31) / 32, (rows + 31) / 32);
-    k_transpose_c<<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, dst);
+    k_transpose_c<C><<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, dst);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
@@ -242,7 +257,8 @@ static int transpose_c(int rows, int cols, const double2 *src, double2 *dst, cud
 // 2-D DFT of a [NY][NX] (in a); result transposed, [NX][NY], in t.  a is
 // clobbered (it is the ping-pong partner of the column passes).
 template <typename R>
-static int dft2_to_t(const ConvPlan<R> &P, double2 *a, double2 *t, cudaStream_t st)
+static int dft2_to_t(const ConvPlan<R> &P, typename ConvPlan<R>::C2 *a, typename ConvPlan<R>::C2 *t,
+                     cudaStream_t st)
 {
     MPI_TRY(fft_run(P.px, a, t, P.NY, P.NX, P.WX, st));
     MPI_TRY(transpose_c(P.NY, P.NX, a, t, st));
@@ -252,9 +268,9 @@ static int dft2_to_t(const ConvPlan<R> &P, double2 *a, double2 *t, cudaStream_t 
 size_t conv_plan_bytes(int nx, int ny, int elem_bytes)
 {
     size_t b = conv_kernel_bytes(nx, ny, elem_bytes);
-    if (conv_uses_fft(nx, ny)) {
+    if (conv_uses_fft(nx, ny, elem_bytes)) {
         const size_t NX = nice_length(2 * nx - 1), NY = nice_length(2 * ny - 1);
-        b += sizeof(double2) * (NX + NY + 3 * NX * NY) + 6 * 256;
+        b += 2 * size_t(elem_bytes) * (NX + NY + 3 * NX * NY) + 6 * 256;
     }
     return b;
 }
@@ -264,7 +280,7 @@ int conv_plan_prepare(const ModelH &m, const GridH &g, void *scratch, ConvPlan<R
 {
     P.nx = g.nx;
     P.ny = g.ny;
-    P.fft = conv_uses_fft(g.nx, g.ny);
+    P.fft = conv_uses_fft(g.nx, g.ny, sizeof(R));
     R *K = nullptr;
     MPI_TRY(conv_prepare_kernel<R>(m, g, scratch, &K, st, comp));
     P.K = K;
@@ -274,9 +290,10 @@ int conv_plan_prepare(const ModelH &m, const GridH &g, void *scratch, ConvPlan<R
     plan_fft(P.NX, P.px);
     plan_fft(P.NY, P.py);
     char *p = static_cast<char *>(scratch) + ((conv_kernel_bytes(g.nx, g.ny, sizeof(R)) + 255) & ~size_t(255));
+    using C2 = typename ConvPlan<R>::C2;
     auto take = [&](size_t n) {
-        double2 *q = reinterpret_cast<double2 *>(p);
-        p += (sizeof(double2) * n + 255) & ~size_t(255);
+        C2 *q = reinterpret_cast<C2 *>(p);
+        p += (sizeof(C2) * n + 255) & ~size_t(255);
         return q;
     };
     const int64_t n = (int64_t)P.NX * P.NY;
@@ -288,7 +305,7 @@ int conv_plan_prepare(const ModelH &m, const GridH &g, void *scratch, ConvPlan<R
     MPI_TRY(fft_twiddles(P.NX, P.WX, st));
     MPI_TRY(fft_twiddles(P.NY, P.WY, st));
     // The sampled kernel in FP64 is the first piece of the scratch.
-    k_conv_circ<<<elem_blocks(n), 256, 0, st>>>(g.nx, g.ny, P.NX, P.NY, static_cast<const double *>(scratch), P.a);
+    k_conv_circ<C2><<<elem_blocks(n), 256, 0, st>>>(g.nx, g.ny, P.NX, P.NY, static_cast<const double *>(scratch), P.a);
     MPI_CHECK_LAUNCH();
     return dft2_to_t(P, P.a, P.Kh, st);
 }
@@ -304,16 +321,17 @@ int conv_apply(const ConvPlan<R> &P, const IN *in, OUT *out, cudaStream_t st)
     }
     const int64_t n = (int64_t)P.NX * P.NY;
     ProfScope prof(kProfConv, st);
-    k_conv_load<IN><<<elem_blocks(n), 256, 0, st>>>(P.nx, P.ny, P.NX, P.NY, in, P.a);
+    using C2 = typename ConvPlan<R>::C2;
+    k_conv_load<IN, C2><<<elem_blocks(n), 256, 0, st>>>(P.nx, P.ny, P.NX, P.NY, in, P.a);
     MPI_CHECK_LAUNCH();
     MPI_TRY(dft2_to_t(P, P.a, P.t, st));
-    k_spec_mul_conj<<<elem_blocks(n), 256, 0, st>>>(n, P.t, P.Kh);
+    k_spec_mul_conj<C2><<<elem_blocks(n), 256, 0, st>>>(n, P.t, P.Kh);
     MPI_CHECK_LAUNCH();
     // DFT of the conjugated product: columns (rows of t), transpose back, rows.
     MPI_TRY(fft_run(P.py, P.t, P.a, P.NX, P.NY, P.WY, st));
     MPI_TRY(transpose_c(P.NX, P.NY, P.t, P.a, st));
     MPI_TRY(fft_run(P.px, P.a, P.t, P.NY, P.NX, P.WX, st));
-    k_conv_crop<OUT><<<elem_blocks((int64_t)P.nx * P.ny), 256, 0, st>>>(P.nx, P.ny, P.NX, P.a, 1.0 / double(n), out);
+    k_conv_crop<OUT, C2><<<elem_blocks((int64_t)P.nx * P.ny), 256, 0, st>>>(P.nx, P.ny, P.NX, P.a, 1.0 / double(n), out);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }

@@ -21,17 +21,18 @@ template <typename R, typename IN, typename OUT>
 int launch_conv(const GridH &g, const R *K, const IN *in, OUT *out, cudaStream_t st);
 
 // The operator C of one grid, by the direct sum (small grids) or by FFT
-// (N >= MPI_CONV_FFT_MIN_N); scratch: conv_plan_bytes.
+// (N >= MPI_CONV_FFT_MIN_N, DFTs in the precision R); scratch: conv_plan_bytes.
 template <typename R>
 struct ConvPlan {
+    using C2 = typename CxOf<R>::type;
     int nx = 0, ny = 0;
     bool fft = false;
     const R *K = nullptr;  // direct route: the sampled kernel
     int NX = 0, NY = 0;    // FFT route: circular grid
     FftPlan px, py;
-    double2 *WX = nullptr, *WY = nullptr, *Kh = nullptr, *a = nullptr, *t = nullptr;
+    C2 *WX = nullptr, *WY = nullptr, *Kh = nullptr, *a = nullptr, *t = nullptr;
 };
-bool conv_uses_fft(int nx, int ny);
+bool conv_uses_fft(int nx, int ny, int elem_bytes);
 size_t conv_plan_bytes(int nx, int ny, int elem_bytes);
 template <typename R>
 int conv_plan_prepare(const ModelH &m, const GridH &g, void *scratch, ConvPlan<R> &P, cudaStream_t st,

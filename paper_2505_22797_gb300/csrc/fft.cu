@@ -1,4 +1,4 @@
-// Stockham autosort FFT in FP64 (see fft.cuh).
+// Stockham autosort FFT in FP32 or FP64 (see fft.cuh).
 #include <algorithm>
 
 #include "fft.cuh"
@@ -18,14 +18,15 @@ bool plan_fft(int64_t n, FftPlan &p)
     return m == 1;
 }
 
-// W[m] = exp(-2 pi i m / n), m < n.
-__global__ void k_twiddles(int64_t n, double2 *__restrict__ W)
+// W[m] = exp(-2 pi i m / n), m < n, formed in FP64 and rounded to C.
+template <typename C>
+__global__ void k_twiddles(int64_t n, C *__restrict__ W)
 {
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n;
          m += (int64_t)gridDim.x * blockDim.x) {
         double s, c;
         sincospi(-2.0 * double(m) / double(n), &s, &c);
-        W[m] = make_double2(c, s);
+        W[m] = make_cx<C>(c, s);
     }
 }
 
@@ -33,12 +34,13 @@ __global__ void k_twiddles(int64_t n, double2 *__restrict__ W)
 // butterfly j (k = j mod Ns) reads x[j + i n/R], i < R, and writes
 //   y[(j/Ns) Ns R + k + q Ns] = sum_i x[j + i n/R] W^{i (k + q Ns) n/(Ns R)}.
 // `dist` is the distance between channels (blockIdx.y).
+template <typename C>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_pass(const double2 *__restrict__ x, double2 *__restrict__ y, int64_t n, int R, int64_t Ns,
-           const double2 *__restrict__ W, int64_t dist)
+k_fft_pass(const C *__restrict__ x, C *__restrict__ y, int64_t n, int R, int64_t Ns,
+           const C *__restrict__ W, int64_t dist)
 {
-    const double2 *xc = x + blockIdx.y * dist;
-    double2 *yc = y + blockIdx.y * dist;
+    const C *xc = x + blockIdx.y * dist;
+    C *yc = y + blockIdx.y * dist;
     const int64_t nb = n / R;
     const int64_t NsR = Ns * R;
     const int64_t step = n / NsR;  // table stride for the NsR-th roots
@@ -47,30 +49,30 @@ k_fft_pass(const double2 *__restrict__ x, double2 *__restrict__ y, int64_t n, in
         const int64_t k = j % Ns;
         const int64_t out0 = (j / Ns) * NsR + k;
         if (R == 2) {
-            const double2 a = xc[j], b = cmul(xc[j + nb], W[k * step]);
-            yc[out0] = make_double2(a.x + b.x, a.y + b.y);
-            yc[out0 + Ns] = make_double2(a.x - b.x, a.y - b.y);
+            const C a = xc[j], b = cmul(xc[j + nb], W[k * step]);
+            yc[out0] = cxv(a.x + b.x, a.y + b.y);
+            yc[out0 + Ns] = cxv(a.x - b.x, a.y - b.y);
         } else if (R == 4) {
-            const double2 a0 = xc[j];
-            const double2 a1 = cmul(xc[j + nb], W[k * step]);
-            const double2 a2 = cmul(xc[j + 2 * nb], W[2 * k * step]);
-            const double2 a3 = cmul(xc[j + 3 * nb], W[3 * k * step]);
-            const double2 s02 = make_double2(a0.x + a2.x, a0.y + a2.y);
-            const double2 d02 = make_double2(a0.x - a2.x, a0.y - a2.y);
-            const double2 s13 = make_double2(a1.x + a3.x, a1.y + a3.y);
-            const double2 d13 = make_double2(a1.x - a3.x, a1.y - a3.y);
+            const C a0 = xc[j];
+            const C a1 = cmul(xc[j + nb], W[k * step]);
+            const C a2 = cmul(xc[j + 2 * nb], W[2 * k * step]);
+            const C a3 = cmul(xc[j + 3 * nb], W[3 * k * step]);
+            const C s02 = cxv(a0.x + a2.x, a0.y + a2.y);
+            const C d02 = cxv(a0.x - a2.x, a0.y - a2.y);
+            const C s13 = cxv(a1.x + a3.x, a1.y + a3.y);
+            const C d13 = cxv(a1.x - a3.x, a1.y - a3.y);
             // omega_4 = -i:  d13 * (-i) = (d13.y, -d13.x)
-            yc[out0] = make_double2(s02.x + s13.x, s02.y + s13.y);
-            yc[out0 + Ns] = make_double2(d02.x + d13.y, d02.y - d13.x);
-            yc[out0 + 2 * Ns] = make_double2(s02.x - s13.x, s02.y - s13.y);
-            yc[out0 + 3 * Ns] = make_double2(d02.x - d13.y, d02.y + d13.x);
+            yc[out0] = cxv(s02.x + s13.x, s02.y + s13.y);
+            yc[out0 + Ns] = cxv(d02.x + d13.y, d02.y - d13.x);
+            yc[out0 + 2 * Ns] = cxv(s02.x - s13.x, s02.y - s13.y);
+            yc[out0 + 3 * Ns] = cxv(d02.x - d13.y, d02.y + d13.x);
         } else {
             for (int q = 0; q < R; ++q) {
                 const int64_t e = k + (int64_t)q * Ns;  // exponent base over NsR, e < NsR
-                double2 acc = make_double2(0.0, 0.0);
+                C acc = {0, 0};
                 int64_t m = 0;                          // i e mod NsR, stepped
                 for (int i = 0; i < R; ++i) {
-                    const double2 t = cmul(xc[j + i * nb], W[m * step]);
+                    const C t = cmul(xc[j + i * nb], W[m * step]);
                     acc.x += t.x;
                     acc.y += t.y;
                     m += e;
@@ -86,27 +88,39 @@ unsigned fft_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<
 
 // In-place in the sense of buffers: the transform of `a` ends in `a` (b is
 // scratch of the same size).  n_ch channels at distance `dist`.
-int fft_run(const FftPlan &p, double2 *a, double2 *b, int n_ch, int64_t dist,
-                   const double2 *W, cudaStream_t st)
+template <typename C>
+static int fft_run_t(const FftPlan &p, C *a, C *b, int n_ch, int64_t dist, const C *W, cudaStream_t st)
 {
-    double2 *src = a, *dst = b;
+    C *src = a, *dst = b;
     int64_t Ns = 1;
     for (int R : p.radix) {
         dim3 grid(fft_blocks(p.n / R), n_ch);
-        k_fft_pass<<<grid, kFftThreads, 0, st>>>(src, dst, p.n, R, Ns, W, dist);
+        k_fft_pass<C><<<grid, kFftThreads, 0, st>>>(src, dst, p.n, R, Ns, W, dist);
         MPI_CHECK_LAUNCH();
         Ns *= R;
         std::swap(src, dst);
     }
-    if (src != a) MPI_TRY_CUDA(cudaMemcpyAsync(a, src, sizeof(double2) * (n_ch * dist), cudaMemcpyDeviceToDevice, st));
+    if (src != a) MPI_TRY_CUDA(cudaMemcpyAsync(a, src, sizeof(C) * (n_ch * dist), cudaMemcpyDeviceToDevice, st));
     return MPI_OK;
 }
 
-int fft_twiddles(int64_t n, double2 *W, cudaStream_t st)
+template <typename C>
+static int fft_twiddles_t(int64_t n, C *W, cudaStream_t st)
 {
-    k_twiddles<<<fft_blocks(n), kFftThreads, 0, st>>>(n, W);
+    k_twiddles<C><<<fft_blocks(n), kFftThreads, 0, st>>>(n, W);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
+
+int fft_run(const FftPlan &p, double2 *a, double2 *b, int n_ch, int64_t dist, const double2 *W, cudaStream_t st)
+{
+    return fft_run_t(p, a, b, n_ch, dist, W, st);
+}
+int fft_run(const FftPlan &p, float2 *a, float2 *b, int n_ch, int64_t dist, const float2 *W, cudaStream_t st)
+{
+    return fft_run_t(p, a, b, n_ch, dist, W, st);
+}
+int fft_twiddles(int64_t n, double2 *W, cudaStream_t st) { return fft_twiddles_t(n, W, st); }
+int fft_twiddles(int64_t n, float2 *W, cudaStream_t st) { return fft_twiddles_t(n, W, st); }
 
 }  // namespace mpi
