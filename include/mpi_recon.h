@@ -289,7 +289,10 @@ int mpi_adjoint3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_
 
 /* out = C in with the sampled 3-D trace kernel kappa_G(y) = beta tr(K(beta G
  * y) G) (Eq. kernel:trace with n - 1 = 2), linear (zero-padded) over all
- * voxel offsets.  in and out [nz][ny][nx], must not overlap. */
+ * voxel offsets.  in and out [nz][ny][nx], must not overlap.  Volumes from
+ * 8192 voxels (FP32) or 512 voxels (FP64) take the FFT route (circular
+ * convolution on a padded power-of-two grid, DFTs in the call's precision):
+ * the same operator up to round-off. */
 int mpi_conv3(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, const void *in,
               void *out, void *stream);
 

@@ -336,6 +336,24 @@ int conv_apply(const ConvPlan<R> &P, const IN *in, OUT *out, cudaStream_t st)
     return MPI_OK;
 }
 
+int transpose_cx(int rows, int cols, const float2 *src, float2 *dst, cudaStream_t st)
+{
+    return transpose_c(rows, cols, src, dst, st);
+}
+int transpose_cx(int rows, int cols, const double2 *src, double2 *dst, cudaStream_t st)
+{
+    return transpose_c(rows, cols, src, dst, st);
+}
+template <typename C>
+static int spec_mul_conj_t(int64_t n, C *t, const C *kh, cudaStream_t st)
+{
+    k_spec_mul_conj<C><<<elem_blocks(n), 256, 0, st>>>(n, t, kh);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+int spec_mul_conj(int64_t n, float2 *t, const float2 *kh, cudaStream_t st) { return spec_mul_conj_t(n, t, kh, st); }
+int spec_mul_conj(int64_t n, double2 *t, const double2 *kh, cudaStream_t st) { return spec_mul_conj_t(n, t, kh, st); }
+
 template int conv_plan_prepare<float>(const ModelH &, const GridH &, void *, ConvPlan<float> &, cudaStream_t, int);
 template int conv_plan_prepare<double>(const ModelH &, const GridH &, void *, ConvPlan<double> &, cudaStream_t, int);
 template int conv_apply<float, float, float>(const ConvPlan<float> &, const float *, float *, cudaStream_t);

@@ -37,6 +37,13 @@ size_t conv_plan_bytes(int nx, int ny, int elem_bytes);
 template <typename R>
 int conv_plan_prepare(const ModelH &m, const GridH &g, void *scratch, ConvPlan<R> &P, cudaStream_t st,
                       int comp = -1);
+// Building blocks of the FFT routes (2-D here, 3-D in ffp3.cu):
+// dst[c][r] = src[r][c] for a rows x cols complex matrix; t = conj(t kh).
+int transpose_cx(int rows, int cols, const float2 *src, float2 *dst, cudaStream_t st);
+int transpose_cx(int rows, int cols, const double2 *src, double2 *dst, cudaStream_t st);
+int spec_mul_conj(int64_t n, float2 *t, const float2 *kh, cudaStream_t st);
+int spec_mul_conj(int64_t n, double2 *t, const double2 *kh, cudaStream_t st);
+
 // out = C in.  The FFT route uses the plan's buffers: one application at a
 // time per plan (calls on one stream are ordered).
 template <typename R, typename IN, typename OUT>

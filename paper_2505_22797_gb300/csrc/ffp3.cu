@@ -22,12 +22,17 @@
 //   pair of the pass is in the asymptotic range (one rsqrt per pair), in the
 //   closed-form range, or may need the near-FFP series.
 //   k_conv3_*    the sampled trace kernel and the direct zero-padded 3-D
-//                convolution (8 x 8 x 4 output tiles).
+//                convolution (8 x 8 x 4 output tiles) for small volumes; from
+//                8192 voxels (FP32) / 512 (FP64) the FFT route: the kernel
+//                placed circularly on a power-of-two NZ x NY x NX grid, DFTs
+//                along x, y and z as Stockham row passes with transposes in
+//                between, in the call's precision.
 //   k_gauss3     the built-in denoiser along one axis (5 taps, reflect).
 // PnP (Algorithm 1) runs the shared driver pnp_run with a 3-D operator.
 #include <algorithm>
 #include <cmath>
 
+#include "conv_ops.cuh"
 #include "langevin.cuh"
 #include "pnp_device.cuh"
 #include "pnp_ops.cuh"
@@ -618,6 +623,164 @@ static int launch_conv3(const Grid3H &g, const R *K, const IN *in, OUT *out, cud
     return MPI_OK;
 }
 
+
+// --- FFT route ---------------------------------------------------------------
+
+static int pow2_at_least(int n)
+{
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+template <typename R>
+struct Conv3Plan {
+    using C2 = typename CxOf<R>::type;
+    Grid3H g{};
+    bool fft = false;
+    const R *K = nullptr;
+    int NX = 0, NY = 0, NZ = 0;
+    FftPlan px, py, pz;
+    C2 *WX = nullptr, *WY = nullptr, *WZ = nullptr, *Kh = nullptr, *a = nullptr, *t = nullptr;
+};
+
+static bool conv3_uses_fft(const Grid3H &g, int elem)
+{
+    // where it overtook the direct sum on GB300 (FP32 between 24x24x12 and
+    // 48x48x24; FP64 already at 12x12x6)
+    if (g.n() < (elem == 8 ? 512 : 8192)) return false;
+    const int64_t NX = pow2_at_least(2 * g.nx - 1), NY = pow2_at_least(2 * g.ny - 1),
+                  NZ = pow2_at_least(2 * g.nz - 1);
+    // batch counts of the row passes run as the grid's y dimension
+    return NZ * NY <= 65535 && NX * NZ <= 65535 && NY * NX <= 65535;
+}
+
+static size_t conv3_plan_bytes(const Grid3H &g, int elem)
+{
+    size_t b = conv3_kernel_bytes(g, elem);
+    if (conv3_uses_fft(g, elem)) {
+        const size_t NX = pow2_at_least(2 * g.nx - 1), NY = pow2_at_least(2 * g.ny - 1),
+                     NZ = pow2_at_least(2 * g.nz - 1);
+        b += 2 * size_t(elem) * (NX + NY + NZ + 3 * NX * NY * NZ) + 8 * 256;
+    }
+    return b;
+}
+
+template <typename C>
+__global__ void k_conv3_circ(Grid3H g, int NX, int NY, int NZ, const double *__restrict__ K, C *__restrict__ kc)
+{
+    const int KX = 2 * g.nx - 1, KY = 2 * g.ny - 1;
+    const int64_t n = (int64_t)NX * NY * NZ;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % NX), j = (int)((e / NX) % NY), l = (int)(e / ((int64_t)NX * NY));
+        const int di = i < g.nx ? i : i - NX, dj = j < g.ny ? j : j - NY, dl = l < g.nz ? l : l - NZ;
+        double v = 0.0;
+        if (di > -g.nx && di < g.nx && dj > -g.ny && dj < g.ny && dl > -g.nz && dl < g.nz)
+            v = K[((int64_t)(dl + g.nz - 1) * KY + (dj + g.ny - 1)) * KX + (di + g.nx - 1)];
+        kc[e] = make_cx<C>(v, 0.0);
+    }
+}
+
+template <typename IN, typename C>
+__global__ void k_conv3_load(Grid3H g, int NX, int NY, int NZ, const IN *__restrict__ in, C *__restrict__ a)
+{
+    const int64_t n = (int64_t)NX * NY * NZ;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % NX), j = (int)((e / NX) % NY), l = (int)(e / ((int64_t)NX * NY));
+        const bool inside = i < g.nx && j < g.ny && l < g.nz;
+        a[e] = make_cx<C>(inside ? double(in[((int64_t)l * g.ny + j) * g.nx + i]) : 0.0, 0.0);
+    }
+}
+
+template <typename OUT, typename C>
+__global__ void k_conv3_crop(Grid3H g, int NX, int NY, const C *__restrict__ a, double scale, OUT *__restrict__ out)
+{
+    const int64_t n = g.n();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % g.nx), j = (int)((e / g.nx) % g.ny), l = (int)(e / ((int64_t)g.nx * g.ny));
+        out[e] = OUT(double(a[((int64_t)l * NY + j) * NX + i].x) * scale);
+    }
+}
+
+static unsigned conv3_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
+
+// 3-D DFT of a ([NZ][NY][NX]); the result ends in a in the layout
+// [NY][NX][NZ]; t is clobbered.
+template <typename R>
+static int dft3(const Conv3Plan<R> &P, typename Conv3Plan<R>::C2 *a, typename Conv3Plan<R>::C2 *t,
+                cudaStream_t st)
+{
+    MPI_TRY(fft_run(P.px, a, t, P.NZ * P.NY, P.NX, P.WX, st));   // along x
+    MPI_TRY(transpose_cx(P.NZ * P.NY, P.NX, a, t, st));           // t: [NX][NZ][NY]
+    MPI_TRY(fft_run(P.py, t, a, P.NX * P.NZ, P.NY, P.WY, st));   // along y
+    MPI_TRY(transpose_cx(P.NX * P.NZ, P.NY, t, a, st));           // a: [NY][NX][NZ]
+    return fft_run(P.pz, a, t, P.NY * P.NX, P.NZ, P.WZ, st);     // along z
+}
+
+template <typename R>
+static int conv3_plan_prepare(const Model3H &m, const Grid3H &g, void *scratch, Conv3Plan<R> &P, cudaStream_t st)
+{
+    using C2 = typename Conv3Plan<R>::C2;
+    P.g = g;
+    P.fft = conv3_uses_fft(g, sizeof(R));
+    R *K = nullptr;
+    MPI_TRY(conv3_prepare<R>(m, g, scratch, &K, st));
+    P.K = K;
+    if (!P.fft) return MPI_OK;
+    P.NX = pow2_at_least(2 * g.nx - 1);
+    P.NY = pow2_at_least(2 * g.ny - 1);
+    P.NZ = pow2_at_least(2 * g.nz - 1);
+    plan_fft(P.NX, P.px);
+    plan_fft(P.NY, P.py);
+    plan_fft(P.NZ, P.pz);
+    char *p = static_cast<char *>(scratch) + ((conv3_kernel_bytes(g, sizeof(R)) + 255) & ~size_t(255));
+    auto take = [&](size_t n) {
+        C2 *q = reinterpret_cast<C2 *>(p);
+        p += (sizeof(C2) * n + 255) & ~size_t(255);
+        return q;
+    };
+    const int64_t n = (int64_t)P.NX * P.NY * P.NZ;
+    P.WX = take(P.NX);
+    P.WY = take(P.NY);
+    P.WZ = take(P.NZ);
+    P.Kh = take(n);
+    P.a = take(n);
+    P.t = take(n);
+    MPI_TRY(fft_twiddles(P.NX, P.WX, st));
+    MPI_TRY(fft_twiddles(P.NY, P.WY, st));
+    MPI_TRY(fft_twiddles(P.NZ, P.WZ, st));
+    // The sampled kernel in FP64 is the first piece of the scratch.
+    k_conv3_circ<C2><<<conv3_blocks(n), 256, 0, st>>>(g, P.NX, P.NY, P.NZ, static_cast<const double *>(scratch), P.Kh);
+    MPI_CHECK_LAUNCH();
+    return dft3(P, P.Kh, P.a, st);
+}
+
+// out = C in (3-D), by the direct sum or the FFT route of the plan.
+template <typename R, typename IN, typename OUT>
+static int conv3_apply(const Conv3Plan<R> &P, const IN *in, OUT *out, cudaStream_t st)
+{
+    if (!P.fft) return launch_conv3<R, IN, OUT>(P.g, P.K, in, out, st);
+    using C2 = typename Conv3Plan<R>::C2;
+    const int64_t n = (int64_t)P.NX * P.NY * P.NZ;
+    ProfScope prof(kProfConv, st);
+    k_conv3_load<IN, C2><<<conv3_blocks(n), 256, 0, st>>>(P.g, P.NX, P.NY, P.NZ, in, P.a);
+    MPI_CHECK_LAUNCH();
+    MPI_TRY(dft3(P, P.a, P.t, st));
+    MPI_TRY(spec_mul_conj(n, P.a, P.Kh, st));
+    // DFT of the conjugated product back through the axes in reverse order.
+    MPI_TRY(fft_run(P.pz, P.a, P.t, P.NY * P.NX, P.NZ, P.WZ, st));   // along z
+    MPI_TRY(transpose_cx(P.NY, P.NX * P.NZ, P.a, P.t, st));           // t: [NX][NZ][NY]
+    MPI_TRY(fft_run(P.py, P.t, P.a, P.NX * P.NZ, P.NY, P.WY, st));   // along y
+    MPI_TRY(transpose_cx(P.NX, P.NZ * P.NY, P.t, P.a, st));           // a: [NZ][NY][NX]
+    MPI_TRY(fft_run(P.px, P.a, P.t, P.NZ * P.NY, P.NX, P.WX, st));   // along x
+    k_conv3_crop<OUT, C2><<<conv3_blocks(P.g.n()), 256, 0, st>>>(P.g, P.NX, P.NY, P.a, 1.0 / double(n), out);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Built-in denoiser on a volume: the 5-tap Gaussian along x, then y, then z.
 
@@ -665,14 +828,15 @@ struct PnPOp3D final : PnPOperator<R> {
     Op3<R> A;
     Grid3H g;
     int64_t N = 0;
-    R *sA = nullptr, *K = nullptr, *tmp1 = nullptr, *tmp2 = nullptr, *gtmp = nullptr;
+    Conv3Plan<R> C;
+    R *sA = nullptr, *tmp1 = nullptr, *tmp2 = nullptr, *gtmp = nullptr;
     mpi_denoise3_fn den = nullptr;
     void *user = nullptr;
 
     int rhs(const R *data, double *b0, cudaStream_t st) override
     {
         if (op == MPI_OP_FORWARD) return A.template adjoint<double>(data, b0, nullptr, nullptr, nullptr, st);
-        return launch_conv3<R, R, double>(g, K, data, b0, st);
+        return conv3_apply<R, R, double>(C, data, b0, st);
     }
     int apply_normal(const double *v, double *q, const double *nu_dev, double *pq_part,
                      cudaStream_t st) override
@@ -681,8 +845,8 @@ struct PnPOp3D final : PnPOperator<R> {
             MPI_TRY((A.template forward<double, R>(v, sA, st)));
             return A.template adjoint<double>(sA, q, v, nu_dev, pq_part, st);
         }
-        MPI_TRY((launch_conv3<R, double, R>(g, K, v, tmp1, st)));
-        MPI_TRY((launch_conv3<R, R, R>(g, K, tmp1, tmp2, st)));
+        MPI_TRY((conv3_apply<R, double, R>(C, v, tmp1, st)));
+        MPI_TRY((conv3_apply<R, R, R>(C, tmp1, tmp2, st)));
         return axpy_dot_launch<R>(N, tmp2, v, nu_dev, q, pq_part, st);
     }
     int n_pq() const override { return op == MPI_OP_FORWARD ? reduce_dot_blocks(N) : vec_blocks(N); }
@@ -712,7 +876,7 @@ static int pnp3_impl(const Model3H &m, const Grid3H &g, const mpi_traj *tr, cons
         o_A = scr.reserve(S.A.scratch_bytes());
         o_sA = scr.reserve(sizeof(R) * size_t(m.n_ch) * size_t(std::max<int64_t>(tr->T, 1)));
     } else {
-        o_K = scr.reserve(conv3_kernel_bytes(g, sizeof(R)));
+        o_K = scr.reserve(conv3_plan_bytes(g, sizeof(R)));
         o_t1 = scr.reserve(sizeof(R) * S.N);
         o_t2 = scr.reserve(sizeof(R) * S.N);
     }
@@ -724,7 +888,7 @@ static int pnp3_impl(const Model3H &m, const Grid3H &g, const mpi_traj *tr, cons
         S.sA = scr.at<R>(o_sA);
         MPI_TRY(S.A.prepare(static_cast<const R *>(tr->r), static_cast<const R *>(tr->v), st));
     } else {
-        MPI_TRY(conv3_prepare<R>(m, g, scr.at<char>(o_K), &S.K, st));
+        MPI_TRY(conv3_plan_prepare<R>(m, g, scr.at<char>(o_K), S.C, st));
         S.tmp1 = scr.at<R>(o_t1);
         S.tmp2 = scr.at<R>(o_t2);
     }
@@ -825,11 +989,11 @@ template <typename R>
 static int conv3_impl(const Model3H &m, const Grid3H &g, const void *in, void *out, cudaStream_t st)
 {
     Scratch scr(st);
-    const size_t o_K = scr.reserve(conv3_kernel_bytes(g, sizeof(R)));
+    const size_t o_K = scr.reserve(conv3_plan_bytes(g, sizeof(R)));
     MPI_TRY(scr.allocate());
-    R *K = nullptr;
-    MPI_TRY(conv3_prepare<R>(m, g, scr.at<char>(o_K), &K, st));
-    return launch_conv3<R, R, R>(g, K, static_cast<const R *>(in), static_cast<R *>(out), st);
+    Conv3Plan<R> C;
+    MPI_TRY(conv3_plan_prepare<R>(m, g, scr.at<char>(o_K), C, st));
+    return conv3_apply<R, R, R>(C, static_cast<const R *>(in), static_cast<R *>(out), st);
 }
 
 template <typename R>

@@ -168,3 +168,28 @@ def test_bad_arguments3():
         api.mpi_forward3(syn.default_model3(), dict(g, nz=0), r, r, c)
     with pytest.raises(ValueError):
         api.mpi_forward3(syn.default_model3(), g, r[:, :2].contiguous(), r[:, :2].contiguous(), c)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("shape", [(24, 20, 18), (65, 9, 16)])
+def test_conv3_fft_route(orc, dt, shape):
+    """Volumes of 8192 voxels and more (FP32; 512 in FP64) take the FFT
+    route: the same linear 3-D convolution as the oracle's direct sum."""
+    nx, ny, nz = shape
+    g = syn.box_grid3(nx, ny, nz)
+    for m in (syn.default_model3(), dict(syn.default_model3(), G=G_GEN)):
+        x = rounded(np.random.default_rng(nx * ny).normal(size=(nz, ny, nx)), dt)
+        want = orc.conv3(g, orc.conv_kernel3(m, g), x)
+        assert rel_l2(host(api.mpi_conv3(m, g, dev(x, dt))), want) <= tol(dt)
+
+
+def test_pnp3_conv_fft_route(orc):
+    dt = torch.float32
+    g = syn.box_grid3(24, 20, 18)
+    m = syn.default_model3()
+    u = rounded(np.random.default_rng(13).normal(size=(18, 20, 24)) + 1.0, dt)
+    kern = orc.conv_kernel3(m, g)
+    op = lambda x: orc.conv3(g, kern, x)  # noqa: E731
+    want = orc.pnp(op, op, u, (18, 20, 24), 2, 3, 0.05, denoise=lambda x, sig: orc.gaussian5_3d(x))
+    got = api.mpi_pnp_solve3(m, g, None, None, dev(u, dt), 2, 3, 0.05, op=api.MPI_OP_CONV)
+    assert rel_l2(host(got), want) <= tol(dt)
