@@ -132,7 +132,7 @@ int mpi_dbeta(const mpi_model *model, const mpi_grid_desc *grid,
  *   out[j][i] = sum_{j'i'} kappa_G(x_ij - x_i'j') in[j'][i'],
  *   kappa_G(y) = beta tr(K(beta G y) G)
  * as a linear (zero-padded) convolution over all voxel offsets.  C is
- * symmetric.  in/out are [ny][nx] and must not overlap.  Grids below 6400
+ * symmetric.  in/out are [ny][nx] and must not overlap.  Grids below 4096
  * voxels (FP32) or 1024 voxels (FP64) use the direct sum in the call's
  * dtype; larger ones the FFT route
  * (circular convolution on a padded grid, DFTs in the call's precision), the

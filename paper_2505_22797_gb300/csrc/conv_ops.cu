@@ -9,7 +9,7 @@
 //    16 x 16 output tile and walks the input in 16 x 16 tiles staged with the
 //    matching kernel window in shared memory; per-tile sums are folded with
 //    compensated additions;
-//  * FFT (from 80 x 80 in FP32 and 32 x 32 in FP64, where it overtakes the
+//  * FFT (from 64 x 64 in FP32 and 32 x 32 in FP64, where it overtakes the
 //    direct sum on GB300): the kernel placed circularly on an NY x NX grid,
 //    NX and NY the powers of two >= 2 nx - 1 and 2 ny - 1,
 //    so the circular convolution of the zero-padded input equals the linear
@@ -151,10 +151,10 @@ int launch_conv(const GridH &g, const R *K, const IN *in, OUT *out, cudaStream_t
 // FFT route.
 
 // Smallest grid (voxels) for the FFT route: where it overtook the direct sum
-// on GB300 (FP32: 80 x 80; FP64, whose direct sum runs on the slow FP64 pipe:
+// on GB300 (FP32: 64 x 64; FP64, whose direct sum runs on the slow FP64 pipe:
 // 32 x 32).
 #ifndef MPI_CONV_FFT_MIN_N
-#define MPI_CONV_FFT_MIN_N 6400
+#define MPI_CONV_FFT_MIN_N 4096
 #endif
 #ifndef MPI_CONV_FFT_MIN_N64
 #define MPI_CONV_FFT_MIN_N64 1024

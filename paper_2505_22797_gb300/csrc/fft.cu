@@ -30,10 +30,55 @@ __global__ void k_twiddles(int64_t n, C *__restrict__ W)
     }
 }
 
-// One Stockham pass of radix R after passes whose radices multiply to Ns:
-// butterfly j (k = j mod Ns) reads x[j + i n/R], i < R, and writes
+// One butterfly j (k = j mod Ns) of a Stockham pass of radix R after passes
+// whose radices multiply to Ns: reads x[j + i n/R], i < R, and writes
 //   y[(j/Ns) Ns R + k + q Ns] = sum_i x[j + i n/R] W^{i (k + q Ns) n/(Ns R)}.
-// `dist` is the distance between channels (blockIdx.y).
+template <typename C, typename I>
+__device__ __forceinline__ void butterfly(const C *__restrict__ xc, C *__restrict__ yc, I n, int R, I Ns,
+                                          const C *__restrict__ W, I j)
+{
+    const I nb = n / R;
+    const I NsR = Ns * R;
+    const I step = n / NsR;  // table stride for the NsR-th roots
+    const I k = j % Ns;
+    const I out0 = (j / Ns) * NsR + k;
+    if (R == 2) {
+        const C a = xc[j], b = cmul(xc[j + nb], W[k * step]);
+        yc[out0] = cxv(a.x + b.x, a.y + b.y);
+        yc[out0 + Ns] = cxv(a.x - b.x, a.y - b.y);
+    } else if (R == 4) {
+        const C a0 = xc[j];
+        const C a1 = cmul(xc[j + nb], W[k * step]);
+        const C a2 = cmul(xc[j + 2 * nb], W[2 * k * step]);
+        const C a3 = cmul(xc[j + 3 * nb], W[3 * k * step]);
+        const C s02 = cxv(a0.x + a2.x, a0.y + a2.y);
+        const C d02 = cxv(a0.x - a2.x, a0.y - a2.y);
+        const C s13 = cxv(a1.x + a3.x, a1.y + a3.y);
+        const C d13 = cxv(a1.x - a3.x, a1.y - a3.y);
+        // omega_4 = -i:  d13 * (-i) = (d13.y, -d13.x)
+        yc[out0] = cxv(s02.x + s13.x, s02.y + s13.y);
+        yc[out0 + Ns] = cxv(d02.x + d13.y, d02.y - d13.x);
+        yc[out0 + 2 * Ns] = cxv(s02.x - s13.x, s02.y - s13.y);
+        yc[out0 + 3 * Ns] = cxv(d02.x - d13.y, d02.y + d13.x);
+    } else {
+        for (int q = 0; q < R; ++q) {
+            const I e = k + (I)q * Ns;  // exponent base over NsR, e < NsR
+            C acc = {0, 0};
+            I m = 0;                    // i e mod NsR, stepped
+            for (int i = 0; i < R; ++i) {
+                const C t = cmul(xc[j + i * nb], W[m * step]);
+                acc.x += t.x;
+                acc.y += t.y;
+                m += e;
+                if (m >= NsR) m -= NsR;
+            }
+            yc[out0 + q * Ns] = acc;
+        }
+    }
+}
+
+// One Stockham pass over global memory; `dist` is the distance between
+// channels (blockIdx.y).
 template <typename C>
 __global__ void __launch_bounds__(kFftThreads)
 k_fft_pass(const C *__restrict__ x, C *__restrict__ y, int64_t n, int R, int64_t Ns,
@@ -42,55 +87,66 @@ k_fft_pass(const C *__restrict__ x, C *__restrict__ y, int64_t n, int R, int64_t
     const C *xc = x + blockIdx.y * dist;
     C *yc = y + blockIdx.y * dist;
     const int64_t nb = n / R;
-    const int64_t NsR = Ns * R;
-    const int64_t step = n / NsR;  // table stride for the NsR-th roots
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nb;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = j % Ns;
-        const int64_t out0 = (j / Ns) * NsR + k;
-        if (R == 2) {
-            const C a = xc[j], b = cmul(xc[j + nb], W[k * step]);
-            yc[out0] = cxv(a.x + b.x, a.y + b.y);
-            yc[out0 + Ns] = cxv(a.x - b.x, a.y - b.y);
-        } else if (R == 4) {
-            const C a0 = xc[j];
-            const C a1 = cmul(xc[j + nb], W[k * step]);
-            const C a2 = cmul(xc[j + 2 * nb], W[2 * k * step]);
-            const C a3 = cmul(xc[j + 3 * nb], W[3 * k * step]);
-            const C s02 = cxv(a0.x + a2.x, a0.y + a2.y);
-            const C d02 = cxv(a0.x - a2.x, a0.y - a2.y);
-            const C s13 = cxv(a1.x + a3.x, a1.y + a3.y);
-            const C d13 = cxv(a1.x - a3.x, a1.y - a3.y);
-            // omega_4 = -i:  d13 * (-i) = (d13.y, -d13.x)
-            yc[out0] = cxv(s02.x + s13.x, s02.y + s13.y);
-            yc[out0 + Ns] = cxv(d02.x + d13.y, d02.y - d13.x);
-            yc[out0 + 2 * Ns] = cxv(s02.x - s13.x, s02.y - s13.y);
-            yc[out0 + 3 * Ns] = cxv(d02.x - d13.y, d02.y + d13.x);
-        } else {
-            for (int q = 0; q < R; ++q) {
-                const int64_t e = k + (int64_t)q * Ns;  // exponent base over NsR, e < NsR
-                C acc = {0, 0};
-                int64_t m = 0;                          // i e mod NsR, stepped
-                for (int i = 0; i < R; ++i) {
-                    const C t = cmul(xc[j + i * nb], W[m * step]);
-                    acc.x += t.x;
-                    acc.y += t.y;
-                    m += e;
-                    if (m >= NsR) m -= NsR;
-                }
-                yc[out0 + q * Ns] = acc;
-            }
-        }
+         j += (int64_t)gridDim.x * blockDim.x)
+        butterfly<C, int64_t>(xc, yc, n, R, Ns, W, j);
+}
+
+// Every pass of one sequence in shared memory: block b loads sequence b,
+// runs the same butterflies pass by pass between two shared buffers and
+// writes the result back in place (one global read and write per transform
+// instead of one per pass).
+constexpr int kSmemFftMaxPasses = 24;
+struct RadixList {
+    int n_pass;
+    int r[kSmemFftMaxPasses];
+};
+
+template <typename C>
+__global__ void __launch_bounds__(kFftThreads)
+k_fft_smem(C *__restrict__ x, int n, RadixList rl, const C *__restrict__ W, int64_t dist)
+{
+    extern __shared__ __align__(16) unsigned char fft_smem[];
+    C *A = reinterpret_cast<C *>(fft_smem);
+    C *B = A + n;
+    C *xc = x + blockIdx.x * dist;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) A[e] = xc[e];
+    __syncthreads();
+    C *src = A, *dst = B;
+    int Ns = 1;
+    for (int p = 0; p < rl.n_pass; ++p) {
+        const int R = rl.r[p];
+        for (int j = threadIdx.x; j < n / R; j += blockDim.x) butterfly<C, int>(src, dst, n, R, Ns, W, j);
+        __syncthreads();
+        C *tmp = src;
+        src = dst;
+        dst = tmp;
+        Ns *= R;
     }
+    for (int e = threadIdx.x; e < n; e += blockDim.x) xc[e] = src[e];
 }
 
 unsigned fft_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + kFftThreads - 1) / kFftThreads, 4096)); }
 
 // In-place in the sense of buffers: the transform of `a` ends in `a` (b is
-// scratch of the same size).  n_ch channels at distance `dist`.
+// scratch of the same size).  n_ch channels at distance `dist`.  Sequences
+// of up to 64 KB per two copies run in shared memory, longer ones pass by
+// pass through global memory; both apply the same butterflies.
 template <typename C>
 static int fft_run_t(const FftPlan &p, C *a, C *b, int n_ch, int64_t dist, const C *W, cudaStream_t st)
 {
+    if (p.radix.empty()) return MPI_OK;
+    const size_t smem = 2 * sizeof(C) * size_t(p.n);
+    if (smem <= 64 * 1024 && (int)p.radix.size() <= kSmemFftMaxPasses) {
+        if (smem > 48 * 1024)  // opt in above the default limit (set on the current device)
+            MPI_TRY_CUDA(cudaFuncSetAttribute(k_fft_smem<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RadixList rl{};
+        rl.n_pass = (int)p.radix.size();
+        for (int q = 0; q < rl.n_pass; ++q) rl.r[q] = p.radix[q];
+        k_fft_smem<C><<<(unsigned)n_ch, kFftThreads, smem, st>>>(a, (int)p.n, rl, W, dist);
+        MPI_CHECK_LAUNCH();
+        return MPI_OK;
+    }
     C *src = a, *dst = b;
     int64_t Ns = 1;
     for (int R : p.radix) {
