@@ -504,9 +504,10 @@ def run_ours(args):
     def step():
         api.mpi_pnp_solve(m, g, r, v, s, n_it, n_cg, nu0, clip_pct=cfg["clip_pct"], rho_out=rho)
 
+    from paper_2505_22797_gb300 import multirank
+
     def barrier():
-        if world > 1:
-            dist.barrier()
+        multirank.barrier()
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
@@ -535,13 +536,12 @@ def run_ours(args):
     launches = api.mpi_kernel_launches() - launches0
     prof = {k: api.mpi_profile_read(k) for k in (api.PROF_FORWARD, api.PROF_ADJOINT)}
     api.mpi_profile_enable(False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = pairs_step * args.steps * world / (total_ms * 1e-3) / 1e9
-    recon_per_s = args.steps * world / (total_ms * 1e-3)
+    # every rank reconstructs its own problem: all ranks' units over the
+    # slowest rank's time
+    local_s = sum(step_ms) * 1e-3
+    total_ms = multirank.max_over_ranks(local_s) * 1e3
+    value = multirank.job_rate(pairs_step * args.steps, local_s) / 1e9
+    recon_per_s = multirank.job_rate(args.steps, local_s)
 
     # --- end to end through the public API, host buffers ------------------------
     h_r = torch.as_tensor(cfg["r"], dtype=f32).pin_memory()
@@ -565,12 +565,9 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     barrier()
-    e2e_tot = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = pairs_step * len(e2e_ms) * world / (e2e_tot * 1e-3) / 1e9
+    e2e_local_s = sum(e2e_ms) * 1e-3
+    e2e_tot = multirank.max_over_ranks(e2e_local_s) * 1e3
+    e2e_value = multirank.job_rate(pairs_step * len(e2e_ms), e2e_local_s) / 1e9
     h2d = (h_r.numel() + h_v.numel() + h_s.numel()) * 4
     d2h = h_rho.numel() * 4
 
