@@ -83,3 +83,25 @@ def test_batch_invalid():
         api.BatchPlan([(m, g, 0)], [1.0], 1, 1)
     with pytest.raises(api.MPIError):
         api.BatchPlan([(m, g, 10)], [-1.0], 1, 1)
+
+
+@pytest.mark.slow
+def test_batch_full_size_vs_single_frames():
+    """The 64-frame workload (grids 64^2..256^2, T in [8192, 131072]) in the
+    configuration the benchmark times (autotuned split, persistent or block
+    launches, one PnP iteration in a CUDA graph), checked frame by frame
+    against the single-frame solve (itself held to the FP64 oracle by the
+    other tests) on seeded random data: one PnP iteration of 2 CG steps."""
+    frames = syn.batch_frames(64)
+    rng = np.random.default_rng(5)
+    r = [dev(rounded(f["r"], F32), F32) for f in frames]
+    v = [dev(rounded(f["v"], F32), F32) for f in frames]
+    s = [dev(rounded(rng.normal(size=(2, f["r"].shape[0])), F32), F32) for f in frames]
+    nu0 = [1e-2] * len(frames)
+    plan = api.BatchPlan([(f["model"], f["grid"], f["r"].shape[0]) for f in frames], nu0, 1, 2,
+                         flags=api.MPI_BATCH_AUTOTUNE)
+    got = [host(x) for x in plan.run(r, v, s)]
+    for k in range(0, 64, 9):
+        f = frames[k]
+        single = host(api.mpi_pnp_solve(f["model"], f["grid"], r[k], v[k], s[k], 1, 2, nu0[k]))
+        assert rel_l2(got[k], single) <= tol(F32), k
