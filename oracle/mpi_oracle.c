@@ -649,3 +649,89 @@ void og_conv3(const og_grid3 *g, const double *kern, const double *in, double *o
                 out[((int64_t)l * ny + j) * nx + i] = acc;
             }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Core Stage in three dimensions (Eq. first:step with n = 3).  The core
+ * operator at a point is the n_ch x 3 matrix Ahat_km (receive channel k,
+ * velocity component m); the measurement is
+ *   s_k(t) = sum_m I[Ahat_km](r_t) v_m(t),
+ * with I the tensor product of the one-dimensional cosine interpolation of
+ * og_axis along x, y and z (nodes at the voxel centres, clamped outside the
+ * node hull).  Ahat is [n_ch*3][nz][ny][nx] with component index 3k+m; s is
+ * [n_ch][T]; r and v are [T][3]. */
+void og_interp3(const og_grid3 *g, int n_ch, int64_t T, const double *r, const double *v,
+                const double *Ahat, double *s)
+{
+    int64_t N = (int64_t)g->nx * g->ny * g->nz;
+    for (int64_t t = 0; t < T; ++t) {
+        int ix[2], iy[2], iz[2];
+        double wx[2], wy[2], wz[2];
+        og_axis(r[3 * t], g->x0, g->dx, g->nx, &ix[0], &wx[0], &wx[1]);
+        og_axis(r[3 * t + 1], g->y0, g->dy, g->ny, &iy[0], &wy[0], &wy[1]);
+        og_axis(r[3 * t + 2], g->z0, g->dz, g->nz, &iz[0], &wz[0], &wz[1]);
+        ix[1] = g->nx > 1 ? ix[0] + 1 : ix[0];
+        iy[1] = g->ny > 1 ? iy[0] + 1 : iy[0];
+        iz[1] = g->nz > 1 ? iz[0] + 1 : iz[0];
+        for (int k = 0; k < n_ch; ++k) {
+            double acc = 0.0;
+            for (int mm = 0; mm < 3; ++mm) {
+                const double *F = &Ahat[(3 * k + mm) * N];
+                double val = 0.0;
+                for (int c = 0; c < 2; ++c)
+                    for (int b = 0; b < 2; ++b)
+                        for (int a = 0; a < 2; ++a)
+                            val += wz[c] * wy[b] * wx[a] *
+                                   F[((int64_t)iz[c] * g->ny + iy[b]) * g->nx + ix[a]];
+                acc += val * v[3 * t + mm];
+            }
+            s[(int64_t)k * T + t] = acc;
+        }
+    }
+}
+
+/* Exact transpose of og_interp3, accumulated in sample order. */
+void og_interp3_T(const og_grid3 *g, int n_ch, int64_t T, const double *r, const double *v,
+                  const double *s, double *Ahat)
+{
+    int64_t N = (int64_t)g->nx * g->ny * g->nz;
+    memset(Ahat, 0, sizeof(double) * 3 * n_ch * N);
+    for (int64_t t = 0; t < T; ++t) {
+        int ix[2], iy[2], iz[2];
+        double wx[2], wy[2], wz[2];
+        og_axis(r[3 * t], g->x0, g->dx, g->nx, &ix[0], &wx[0], &wx[1]);
+        og_axis(r[3 * t + 1], g->y0, g->dy, g->ny, &iy[0], &wy[0], &wy[1]);
+        og_axis(r[3 * t + 2], g->z0, g->dz, g->nz, &iz[0], &wz[0], &wz[1]);
+        ix[1] = g->nx > 1 ? ix[0] + 1 : ix[0];
+        iy[1] = g->ny > 1 ? iy[0] + 1 : iy[0];
+        iz[1] = g->nz > 1 ? iz[0] + 1 : iz[0];
+        for (int k = 0; k < n_ch; ++k)
+            for (int mm = 0; mm < 3; ++mm) {
+                double coef = s[(int64_t)k * T + t] * v[3 * t + mm];
+                double *F = &Ahat[(3 * k + mm) * N];
+                for (int c = 0; c < 2; ++c)
+                    for (int b = 0; b < 2; ++b)
+                        for (int a = 0; a < 2; ++a)
+                            F[((int64_t)iz[c] * g->ny + iy[b]) * g->nx + ix[a]] +=
+                                wz[c] * wy[b] * wx[a] * coef;
+            }
+    }
+}
+
+/* 7-point discrete Laplacian with replicated boundary on one [nz][ny][nx]
+ * volume (the regulariser of Eq. first:step in three dimensions). */
+void og_laplacian3(const og_grid3 *g, const double *f, double *out)
+{
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    for (int l = 0; l < nz; ++l)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int im = i > 0 ? i - 1 : 0, ip = i < nx - 1 ? i + 1 : nx - 1;
+                int jm = j > 0 ? j - 1 : 0, jp = j < ny - 1 ? j + 1 : ny - 1;
+                int lm = l > 0 ? l - 1 : 0, lp = l < nz - 1 ? l + 1 : nz - 1;
+#define OG_AT(ll, jj, ii) f[((int64_t)(ll) * ny + (jj)) * nx + (ii)]
+                out[((int64_t)l * ny + j) * nx + i] =
+                    OG_AT(l, j, im) + OG_AT(l, j, ip) + OG_AT(l, jm, i) + OG_AT(l, jp, i) +
+                    OG_AT(lm, j, i) + OG_AT(lp, j, i) - 6.0 * OG_AT(l, j, i);
+#undef OG_AT
+            }
+}

@@ -18,6 +18,7 @@ Parity status per function (what pins each one lives in tests/test_oracle_*):
   percentile_clamp, variance, gaussian5, core_stage: pinned.
   kernel_matrix3, pair3, forward3, adjoint3, frob2_3, conv_kernel3, conv3,
   gaussian5_3d (three-dimensional FFP): pinned.
+  interp3, interp3_T, laplacian3, core_stage3 (Core Stage with n = 3): pinned.
   transfer_correct (DFT division by the transfer function, SNR
   thresholding): pinned.
   pnp: pinned step by step (identity-operator closed form, Algorithm 1
@@ -113,6 +114,9 @@ def _load():
             lib.og_frob2_3.restype = ctypes.c_double
             lib.og_conv_kernel3.argtypes = [P(_Model3), P(_Grid3), _D]
             lib.og_conv3.argtypes = [P(_Grid3), _D, _D, _D]
+            lib.og_interp3.argtypes = [P(_Grid3), ctypes.c_int, _I64, _D, _D, _D, _D]
+            lib.og_interp3_T.argtypes = [P(_Grid3), ctypes.c_int, _I64, _D, _D, _D, _D]
+            lib.og_laplacian3.argtypes = [P(_Grid3), _D, _D]
             _lib = lib
     return _lib
 
@@ -587,6 +591,65 @@ def gaussian5_3d(vol) -> np.ndarray:
         for m in range(-2, 3):
             out[k, :, :] += w[m + 2] * b[_reflect(k + m, nz), :, :]
     return out
+
+
+def interp3(grid3, r, v, Ahat) -> np.ndarray:
+    """Core Stage measurement in three dimensions (Eq. first:step, n = 3):
+    s_k(t) = sum_m I[Ahat_km](r_t) v_m(t), I the tensor-product cosine
+    interpolation.  Ahat is [n_ch*3, nz, ny, nx] (component 3k+m); returns
+    s [n_ch, T]."""
+    r, v, Ahat = _f64(r), _f64(v), _f64(Ahat)
+    n_ch = Ahat.shape[0] // 3
+    s = np.empty((n_ch, r.shape[0]))
+    _load().og_interp3(ctypes.byref(_grid3(grid3)), n_ch, r.shape[0], _ptr(r), _ptr(v),
+                       _ptr(Ahat), _ptr(s))
+    return s
+
+
+def interp3_T(grid3, r, v, s) -> np.ndarray:
+    """Exact transpose of interp3: s [n_ch, T] -> [n_ch*3, nz, ny, nx]."""
+    r, v, s = _f64(r), _f64(v), _f64(s)
+    s = s.reshape(-1, r.shape[0])
+    n_ch = s.shape[0]
+    out = np.empty((3 * n_ch, int(grid3["nz"]), int(grid3["ny"]), int(grid3["nx"])))
+    _load().og_interp3_T(ctypes.byref(_grid3(grid3)), n_ch, r.shape[0], _ptr(r), _ptr(v),
+                         _ptr(s), _ptr(out))
+    return out
+
+
+def laplacian3(grid3, f) -> np.ndarray:
+    """7-point Laplacian with replicated boundary, one [nz, ny, nx] volume."""
+    f = _f64(f)
+    out = np.empty_like(f)
+    _load().og_laplacian3(ctypes.byref(_grid3(grid3)), _ptr(f), _ptr(out))
+    return out
+
+
+def core_stage3(grid3, r, v, s, gamma, max_iter, rel_tol=None, channel=None):
+    """Core Stage in three dimensions (Eq. first:step with n = 3): CG from 0 on
+        ((1/T) M^T M + gamma Lap Lap) Ahat = (1/T) M^T s
+    for the 9 components Ahat_km (3 channels x 3 velocity components), Lap the
+    7-point replicated-boundary Laplacian on each component.  channel = k:
+    only channel k was measured (s [T] or [1, T]); the unknowns are the row
+    (A_k0, A_k1, A_k2), solved with channel k's row of M (Sec. 3.6 in three
+    dimensions).  Returns (Ahat [9 or 3, nz, ny, nx], trace, residual
+    history); the trace is A_00 + A_11 + A_22, or A_kk for one channel."""
+    T = r.shape[0]
+    nz, ny, nx = int(grid3["nz"]), int(grid3["ny"]), int(grid3["nx"])
+    s = _f64(s).reshape(-1, T)
+    nc = 9 if channel is None else 3
+
+    def lapn(x):
+        return np.stack([laplacian3(grid3, x[m]) for m in range(nc)])
+
+    def apply(x):
+        return interp3_T(grid3, r, v, interp3(grid3, r, v, x)) / T + gamma * lapn(lapn(x))
+
+    b = interp3_T(grid3, r, v, s) / T
+    x, hist, _ = cg(apply, b, np.zeros((nc, nz, ny, nx)), max_iter, rel_tol=rel_tol)
+    if channel is None:
+        return x, x[0] + x[4] + x[8], hist
+    return x, x[int(channel)], hist
 
 
 # ---------------------------------------------------------------------------
