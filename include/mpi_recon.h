@@ -313,6 +313,36 @@ int mpi_pnp_solve3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mp
                    mpi_dtype dtype, const void *data, const mpi_pnp_opts *opts, mpi_denoise3_fn denoise,
                    void *user, void *rho_out, mpi_pnp_iter_info *info, void *stream);
 
+/* Core Stage in three dimensions (Eq. first:step with n = 3).  The core
+ * operator at a point is the 3 x 3 matrix Ahat_km (receive channel k along
+ * the coordinate axis k, velocity component m), stored [9][nz][ny][nx] with
+ * component index 3k + m; I is the tensor product of the cosine interpolation
+ * of mpi_interp along x, y and z (nodes at the voxel centres, positions
+ * clamped to the node hull).  traj->r and traj->v are [T][3], s is [3][T]
+ * (channel k, sample t):
+ *   s[k][t] = sum_m I[Ahat_km](r_t) v_m(t).
+ * Same conventions as mpi_interp: device pointers, dtype of the call, T < 2^31,
+ * grids of fewer than 2^27 nodes; T == 0 writes nothing. */
+int mpi_interp3(const mpi_grid3_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
+                const void *Ahat, void *s, void *stream);
+
+/* Exact transpose of mpi_interp3: Ahat[3k+m] = sum_t w(r_t) v_m(t) s[k][t]
+ * ([3][T] -> [9][nz][ny][nx]), summed in a fixed order (no atomics). */
+int mpi_interp3_adjoint(const mpi_grid3_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
+                        const void *s, void *Ahat, void *stream);
+
+/* Solves ((1/T) M^T M + gamma Lap^T Lap) Ahat = (1/T) M^T s by CG from
+ * Ahat = 0 with M = mpi_interp3 and Lap the 7-point Laplacian with replicated
+ * boundary on each of the 9 components.  opts as for mpi_grid, with channel 0
+ * (all three channels: s [3][T], Ahat [9][nz][ny][nx], trace [nz][ny][nx] =
+ * A_00 + A_11 + A_22) or k + 1 (only channel k = 0, 1, 2 measured: s [1][T],
+ * Ahat holds the row (A_k0, A_k1, A_k2) as [3][nz][ny][nx], trace = A_kk).
+ * Operator in the call's dtype, CG vectors and inner products FP64; the stop
+ * test, polling and n_iter_out behave as in mpi_grid. */
+int mpi_grid3(const mpi_grid3_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
+              const void *s, const mpi_grid_opts *opts, void *Ahat, void *trace,
+              int *n_iter_out, void *stream);
+
 /* ---- Batched reconstructions --------------------------------------------- */
 
 /* A plan runs Algorithm 1 with the forward operator (FP32 operator, FP64 CG

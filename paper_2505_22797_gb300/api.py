@@ -118,6 +118,9 @@ _SIGS = {
     "mpi_forward3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_adjoint3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_conv3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_interp3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_interp3_adjoint": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_grid3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 6,
     "mpi_denoise_gaussian5_3d": [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 4
                                 + [ctypes.c_void_p] * 3,
     "mpi_pnp_solve3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
@@ -537,6 +540,57 @@ def mpi_conv3(model3, grid3, x, out=None, stream=None):
     _check(load().mpi_conv3(ctypes.byref(m), ctypes.byref(g), _dtype(x), _dev(x, dt, "in"),
                             _dev(out, dt, "out"), _stream(stream)))
     return out
+
+
+def mpi_interp3(grid3, r, v, Ahat, s=None, stream=None):
+    """Core Stage measurement in three dimensions: Ahat [9, nz, ny, nx] ->
+    s [3, T]."""
+    dt = Ahat.dtype
+    if s is None:
+        s = torch.empty((3, r.shape[0]), dtype=dt, device=Ahat.device)
+    tr = _traj(r, v, dt, 3)
+    g = make_grid3(grid3)
+    _check(load().mpi_interp3(ctypes.byref(g), ctypes.byref(tr), _dtype(Ahat), _dev(Ahat, dt, "Ahat"),
+                              _dev(s, dt, "s") if s.numel() else None, _stream(stream)))
+    return s
+
+
+def mpi_interp3_adjoint(grid3, r, v, s, Ahat=None, stream=None):
+    dt = s.dtype
+    g = make_grid3(grid3)
+    if Ahat is None:
+        Ahat = torch.empty((9, g.nz, g.ny, g.nx), dtype=dt, device=s.device)
+    tr = _traj(r, v, dt, 3)
+    _check(load().mpi_interp3_adjoint(ctypes.byref(g), ctypes.byref(tr), _dtype(s),
+                                      _dev(s, dt, "s") if s.numel() else None,
+                                      _dev(Ahat, dt, "Ahat"), _stream(stream)))
+    return Ahat
+
+
+def mpi_grid3(grid3, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=None, trace=None,
+              return_iters=False, channel=None, stream=None):
+    """Core Stage in three dimensions.  ``channel`` None: s is [3][T] and
+    Ahat [9][nz][ny][nx], trace = A_00 + A_11 + A_22; channel k (0, 1 or 2):
+    only that channel was measured, s is [T] (or [1][T]), Ahat holds the row
+    (A_k0, A_k1, A_k2) and trace = A_kk."""
+    dt = s.dtype
+    g = make_grid3(grid3)
+    nc = 9 if channel is None else 3
+    if Ahat is None:
+        Ahat = torch.empty((nc, g.nz, g.ny, g.nx), dtype=dt, device=s.device)
+    if trace is None:
+        trace = torch.empty((g.nz, g.ny, g.nx), dtype=dt, device=s.device)
+    tr = _traj(r, v, dt, 3)
+    opts = GridOpts(float(gamma), int(max_iter), float(rel_tol),
+                    0 if channel is None else int(channel) + 1)
+    n_it = ctypes.c_int(-1)
+    _check(load().mpi_grid3(ctypes.byref(g), ctypes.byref(tr), _dtype(s),
+                            _dev(s, dt, "s") if s.numel() else None, ctypes.byref(opts),
+                            _dev(Ahat, dt, "Ahat"), _dev(trace, dt, "trace"),
+                            ctypes.byref(n_it) if return_iters else None, _stream(stream)))
+    if return_iters:
+        return Ahat, trace, n_it.value
+    return Ahat, trace
 
 
 def mpi_denoise_gaussian5_3d(x, out=None, stream=None):

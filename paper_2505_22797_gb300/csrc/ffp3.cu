@@ -920,7 +920,7 @@ static int check_model3(const mpi_model3 *m)
     return MPI_OK;
 }
 
-static int check_grid3(const mpi_grid3_desc *g)
+int check_grid3(const mpi_grid3_desc *g)
 {
     if (!g) { set_error("grid is NULL"); return MPI_ERR_INVALID; }
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) {

@@ -1,0 +1,130 @@
+// Pieces of the Core Stage (Eq. first:step) shared by the two- and the
+// three-dimensional solves: the one-dimensional cosine weights of the
+// interpolation, the binning of samples by interpolation cell (count, scan,
+// fill, per-cell sort), the work units of the transpose and their ordered
+// combine, and the epilogue of the CG operator.  The non-template kernels
+// live in grid_ops.cu behind the launchers declared here.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+
+#include "pnp_ops.cuh"
+
+namespace mpi {
+
+struct AxisMap {
+    double inv_h;   // 1/h
+    double off;     // -p0/h - 1/2: continuous node index = p inv_h + off
+    int n;
+};
+
+// Node interval and cosine weights of a position along one axis: between
+// nodes k and k+1 at fraction f, node k+1 weighs (1 - cos(pi f))/2.  Outside
+// the node hull the position clamps to the edge node.
+template <typename R>
+__device__ __forceinline__ void axis_weights(R pos, const AxisMap &a, int &k0, R &w0, R &w1)
+{
+    if (a.n == 1) { k0 = 0; w0 = R(1); w1 = R(0); return; }
+    // The node index is formed in FP64: in FP32 its rounding (~1e-5 of a cell
+    // on 100+ node grids) would already be visible in the weights.
+    const double fi = double(pos) * a.inv_h + a.off;
+    if (!(fi > 0.0)) { k0 = 0; w0 = R(1); w1 = R(0); return; }
+    if (fi >= double(a.n - 1)) { k0 = a.n - 2; w0 = R(0); w1 = R(1); return; }
+    int k = (int)floor(fi);
+    k = min(k, a.n - 2);
+    const R f = R(fi - double(k));
+    k0 = k;
+    if constexpr (sizeof(R) == 4) w1 = 0.5f * (1.0f - cospif(f));
+    else w1 = 0.5 * (1.0 - cospi(f));
+    w0 = R(1) - w1;
+}
+
+inline AxisMap make_axis(double p0, double h, int n)
+{
+    return AxisMap{1.0 / h, -p0 / h - 0.5, n};
+}
+
+constexpr int kInterpSPT = 4;     // samples per thread of the interpolation (gathers in flight)
+// The transpose is organised in work units of at most kUnitLen consecutive
+// entries of a node's samples (its adjacent cells' runs, in cell order), so a
+// node next to cells where the trajectory dwells (thousands of samples)
+// spreads over many units instead of keeping one group of lanes busy alone.
+// Unit sums are combined per node in unit order (deterministic).
+constexpr int kUnitLen = 128;
+constexpr int kUnitLanes = 8;     // lanes per unit
+constexpr int kUnitThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kEpiThreads = 256, kEpiPer = 2048;
+
+inline int grid_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
+
+// Exclusive scan of count[0..n) into offset[0..n] (one block, deterministic);
+// also copies the offsets to cursor.
+int cell_scan_launch(const int *count, int n, int *offset, int *cursor, cudaStream_t st);
+// list[cursor[cell_of[t]]++] = t for every sample.
+int cell_fill_launch(int64_t T, const int *cell_of, int *cursor, int *list, cudaStream_t st);
+// Sorts each cell's run of list ascending.
+int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st);
+// unit_node[w] = node for the units unit_off[node] .. unit_off[node + 1].
+int unit_fill_launch(int N, const int *unit_off, int *unit_node, cudaStream_t st);
+// q = y + gamma lap2 and nblk partial sums of <p, q> (kEpiPer elements each).
+int grid_epilogue_launch(int64_t n, int nblk, const double *y, const double *lap2, double gamma,
+                         const double *p, double *q, double *dot_part, cudaStream_t st);
+// out[0] = sqrt(sum of the n partials), out[1] = tol out[0] (or -1 if tol <= 0).
+int norm_thresh_launch(const double *part, int n, double tol, double *out, cudaStream_t st);
+
+// rec[q] = rec_t[list[q]] and vs[q] = v[list[q]] (D velocity components):
+// the records and velocities of the samples in list (cell) order.
+template <typename Rec, typename R, int D>
+__global__ void k_sort_records(int64_t T, const int *__restrict__ list, const Rec *__restrict__ rec_t,
+                               const R *__restrict__ v, Rec *__restrict__ rec, R *__restrict__ vs)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = list[q];
+        rec[q] = rec_t[t];
+#pragma unroll
+        for (int m = 0; m < D; ++m) vs[D * q + m] = v[D * t + m];
+    }
+}
+
+// out[k][q] = in[k][list[q]] for the n_rows rows of a [n_rows][T] array.
+template <typename R>
+__global__ void k_gather_rows(int64_t T, int n_rows, const int *__restrict__ list, const R *__restrict__ in,
+                              R *__restrict__ out)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = list[q];
+        for (int k = 0; k < n_rows; ++k) out[(int64_t)k * T + q] = in[(int64_t)k * T + t];
+    }
+}
+
+template <typename R>
+int gather_rows(int64_t T, int n_rows, const int *list, const R *in, R *out, cudaStream_t st)
+{
+    if (T == 0) return MPI_OK;
+    k_gather_rows<R><<<grid_blocks(T), 256, 0, st>>>(T, n_rows, list, in, out);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// Ahat_m(node) = scale * sum of the node's NC unit partials, in unit order.
+template <typename R, typename OUT, int NC>
+__global__ void k_interp_T_combine(int N, const int *__restrict__ unit_off, const R *__restrict__ unit_part,
+                                   OUT *__restrict__ A, double scale)
+{
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
+        double acc[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) acc[m] = 0.0;
+        for (int w = unit_off[node]; w < unit_off[node + 1]; ++w)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) acc[m] += double(unit_part[(int64_t)w * NC + m]);
+#pragma unroll
+        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(acc[m] * scale);
+    }
+}
+
+}  // namespace mpi

@@ -8,10 +8,7 @@
 // per-cell sort by sample index give every cell a fixed sample order), and
 // each node gathers from its (up to) four adjacent cells.  All of it is
 // memory/latency bound.
-#include <algorithm>
-#include <cmath>
-
-#include "pnp_ops.cuh"
+#include "grid_common.cuh"
 
 namespace mpi {
 
@@ -19,38 +16,6 @@ int check_grid(const mpi_grid_desc *g);
 int check_traj(const mpi_traj *t);
 int check_dtype(mpi_dtype d);
 GridH to_host(const mpi_grid_desc *g);
-
-struct AxisMap {
-    double inv_h;   // 1/h
-    double off;     // -p0/h - 1/2: continuous node index = p inv_h + off
-    int n;
-};
-
-// Node interval and cosine weights of a position along one axis: between
-// nodes k and k+1 at fraction f, node k+1 weighs (1 - cos(pi f))/2.  Outside
-// the node hull the position clamps to the edge node.
-template <typename R>
-__device__ __forceinline__ void axis_weights(R pos, const AxisMap &a, int &k0, R &w0, R &w1)
-{
-    if (a.n == 1) { k0 = 0; w0 = R(1); w1 = R(0); return; }
-    // The node index is formed in FP64: in FP32 its rounding (~1e-5 of a cell
-    // on 100+ node grids) would already be visible in the weights.
-    const double fi = double(pos) * a.inv_h + a.off;
-    if (!(fi > 0.0)) { k0 = 0; w0 = R(1); w1 = R(0); return; }
-    if (fi >= double(a.n - 1)) { k0 = a.n - 2; w0 = R(0); w1 = R(1); return; }
-    int k = (int)floor(fi);
-    k = min(k, a.n - 2);
-    const R f = R(fi - double(k));
-    k0 = k;
-    if constexpr (sizeof(R) == 4) w1 = 0.5f * (1.0f - cospif(f));
-    else w1 = 0.5 * (1.0 - cospi(f));
-    w0 = R(1) - w1;
-}
-
-static AxisMap make_axis(double p0, double h, int n)
-{
-    return AxisMap{1.0 / h, -p0 / h - 0.5, n};
-}
 
 // Interpolation record of one sample: its cell (i0, j0) and the upper-node
 // cosine weights along x and y (the lower ones are 1 - w).  Fixed for a
@@ -70,8 +35,6 @@ __device__ __forceinline__ InterpRec<R> make_rec(R px, R py, const AxisMap &ax, 
     axis_weights<R>(py, ay, q.j0, w0, q.wy1);
     return q;
 }
-
-constexpr int kInterpSPT = 4;  // samples per thread (independent gathers in flight)
 
 // s[k][t] = sum_m I[Ahat_{2k+m}](r_t) v_m(t)   (Ahat of type AT, s of type R).
 // CH < 0: both channels, Ahat has 4 components, s 2 rows.  CH = k: only
@@ -138,7 +101,6 @@ __global__ void k_cell_count(int64_t T, const R *__restrict__ r, AxisMap ax, Axi
 
 // Exclusive scan of n ints by one block (deterministic); also copies the
 // offsets to `cursor`.
-constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(const int *__restrict__ count, int n, int *__restrict__ offset, int *__restrict__ cursor)
 {
@@ -211,15 +173,6 @@ __global__ void k_cell_sort(int n_cells, const int *__restrict__ offset, int *__
 // samples of the node's (up to) four cells, then a fixed butterfly sums the
 // lanes, so a node whose cells hold many samples (a trajectory that dwells)
 // costs one warp a longer loop instead of stalling 31 other nodes.
-// The transpose is organised in work units of at most kUnitLen consecutive
-// entries of a node's samples (its four cells' runs, in cell order), so a
-// node next to cells where the trajectory dwells (thousands of samples)
-// spreads over many units instead of keeping one group of lanes busy alone.
-// Unit sums are combined per node in unit order (deterministic).
-constexpr int kUnitLen = 128;
-constexpr int kUnitLanes = 8;     // lanes per unit
-constexpr int kUnitThreads = 256;
-
 // Samples in the (up to) four cells around node (i, j), in cell order.
 __device__ __forceinline__ int node_cells(int i, int j, int ncx, int ncy, int c[4])
 {
@@ -319,23 +272,6 @@ k_interp_T_units(const InterpRec<R> *__restrict__ rec, const R *__restrict__ vs,
     }
 }
 
-// Ahat_m(node) = scale * sum of the node's unit partials, in unit order.
-template <typename R, typename OUT, int NC>
-__global__ void k_interp_T_combine(int N, const int *__restrict__ unit_off, const R *__restrict__ unit_part,
-                                   OUT *__restrict__ A, double scale)
-{
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
-        double acc[NC];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) acc[m] = 0.0;
-        for (int w = unit_off[node]; w < unit_off[node + 1]; ++w)
-#pragma unroll
-            for (int m = 0; m < NC; ++m) acc[m] += double(unit_part[(int64_t)w * NC + m]);
-#pragma unroll
-        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(acc[m] * scale);
-    }
-}
-
 // Binning scratch for a trajectory on a grid.
 // Samples binned by interpolation cell.  list: sample indices sorted by cell
 // (ascending index within a cell); offset: start of each cell's run.  rec /
@@ -398,32 +334,6 @@ static Bins bins_carve(char *p, int64_t T, int nx, int ny)
     return b;
 }
 
-static int grid_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
-
-template <typename R>
-__global__ void k_sort_records(int64_t T, const int *__restrict__ list, const InterpRec<R> *__restrict__ rec_t,
-                               const R *__restrict__ v, InterpRec<R> *__restrict__ rec, R *__restrict__ vs)
-{
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = list[q];
-        rec[q] = rec_t[t];
-        vs[2 * q] = v[2 * t];
-        vs[2 * q + 1] = v[2 * t + 1];
-    }
-}
-
-template <typename R>
-__global__ void k_gather_rows(int64_t T, int n_rows, const int *__restrict__ list, const R *__restrict__ in,
-                              R *__restrict__ out)
-{
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = list[q];
-        for (int k = 0; k < n_rows; ++k) out[(int64_t)k * T + q] = in[(int64_t)k * T + t];
-    }
-}
-
 // Bins the samples, orders their records and velocities by cell and builds
 // the transpose's work units.
 template <typename R>
@@ -444,7 +354,7 @@ static int build_bins(const GridH &g, int64_t T, const R *r, const R *v, const B
         MPI_CHECK_LAUNCH();
         k_cell_sort<<<(nc + 127) / 128, 128, 0, st>>>(nc, b.offset, b.list);
         MPI_CHECK_LAUNCH();
-        k_sort_records<R><<<grid_blocks(T), 256, 0, st>>>(T, b.list, static_cast<const InterpRec<R> *>(b.rec_t),
+        k_sort_records<InterpRec<R>, R, 2><<<grid_blocks(T), 256, 0, st>>>(T, b.list, static_cast<const InterpRec<R> *>(b.rec_t),
                                                           v, static_cast<InterpRec<R> *>(b.rec),
                                                           static_cast<R *>(b.vs));
         MPI_CHECK_LAUNCH();
@@ -456,16 +366,6 @@ static int build_bins(const GridH &g, int64_t T, const R *r, const R *v, const B
     k_scan<<<1, kScanThreads, 0, st>>>(b.unit_cnt, N, b.unit_off, b.unit_cursor);
     MPI_CHECK_LAUNCH();
     k_unit_fill<<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, b.unit_node);
-    MPI_CHECK_LAUNCH();
-    return MPI_OK;
-}
-
-// out[k][q] = in[k][list[q]] for the n_rows rows of a [n_rows][T] array.
-template <typename R>
-static int gather_rows(int64_t T, int n_rows, const int *list, const R *in, R *out, cudaStream_t st)
-{
-    if (T == 0) return MPI_OK;
-    k_gather_rows<R><<<grid_blocks(T), 256, 0, st>>>(T, n_rows, list, in, out);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
@@ -491,7 +391,6 @@ static int launch_interp(const GridH &g, int64_t T, const R *r, const R *v, cons
     return MPI_OK;
 }
 
-// s_sorted: the samples' values in list order ([rows][T]).
 // s_sorted: the samples' values in list order ([rows][T]).
 template <typename R, typename OUT>
 static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const Bins &b, OUT *A, double scale,
@@ -536,7 +435,6 @@ __global__ void k_lap(int nx, int ny, int nc, const double *__restrict__ x, doub
 }
 
 // q = y + gamma lap2, partial sums of <p, q> (blocks of 2048 elements).
-constexpr int kEpiThreads = 256, kEpiPer = 2048;
 __global__ void __launch_bounds__(kEpiThreads)
 k_grid_epilogue(int64_t n, const double *__restrict__ y, const double *__restrict__ lap2, double gamma,
                 const double *__restrict__ p, double *__restrict__ q, double *__restrict__ dot_part)
@@ -697,6 +595,51 @@ static int check_interp_args(const mpi_grid_desc *grid, const mpi_traj *traj, mp
         set_error("interpolation supports T < 2^31");
         return MPI_ERR_UNSUPPORTED;
     }
+    return MPI_OK;
+}
+
+// Launchers of the binning and epilogue kernels for the 3-D Core Stage.
+int cell_scan_launch(const int *count, int n, int *offset, int *cursor, cudaStream_t st)
+{
+    k_scan<<<1, kScanThreads, 0, st>>>(count, n, offset, cursor);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+int cell_fill_launch(int64_t T, const int *cell_of, int *cursor, int *list, cudaStream_t st)
+{
+    if (T == 0) return MPI_OK;
+    k_cell_fill<<<grid_blocks(T), 256, 0, st>>>(T, cell_of, cursor, list);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st)
+{
+    k_cell_sort<<<(n_cells + 127) / 128, 128, 0, st>>>(n_cells, offset, list);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+int unit_fill_launch(int N, const int *unit_off, int *unit_node, cudaStream_t st)
+{
+    k_unit_fill<<<grid_blocks(N), 256, 0, st>>>(N, unit_off, unit_node);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+int grid_epilogue_launch(int64_t n, int nblk, const double *y, const double *lap2, double gamma,
+                         const double *p, double *q, double *dot_part, cudaStream_t st)
+{
+    k_grid_epilogue<<<nblk, kEpiThreads, 0, st>>>(n, y, lap2, gamma, p, q, dot_part);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+int norm_thresh_launch(const double *part, int n, double tol, double *out, cudaStream_t st)
+{
+    k_norm_thresh<<<1, 32, 0, st>>>(part, n, tol, out);
+    MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
 
