@@ -4,7 +4,8 @@
 
 Builds the inputs of the workload (seeded synthetic), runs `--warmup`
 untimed applications and then `--reps` applications of the chosen operator
-(forward A, adjoint A^T, dbeta, conv) in the chosen precision, timing each
+(forward A, adjoint A^T, dbeta, conv, the Core Stage interpolation,
+its transpose and two Core Stage CG steps) in the chosen precision, timing each
 with CUDA events on the current stream, and prints one line per operator.
 It is the small, self-contained command to put under a profiler.
 """
@@ -47,10 +48,15 @@ def main(argv=None):
     out = torch.empty_like(c)
     if three:
         s = api.mpi_forward3(m, g, r, v, c)
+        field = torch.stack([c * (1.0 - 0.1 * q) for q in range(9)]).contiguous()
+        s3 = torch.empty_like(s)
         ops = {
             "forward": lambda: api.mpi_forward3(m, g, r, v, c, s=s),
             "adjoint": lambda: api.mpi_adjoint3(m, g, r, v, s, c_out=out),
             "conv": lambda: api.mpi_conv3(m, g, c, out=out),
+            "interp": lambda: api.mpi_interp3(g, r, v, field, s=s3),
+            "interp_T": lambda: api.mpi_interp3_adjoint(g, r, v, s, Ahat=field),
+            "grid": lambda: api.mpi_grid3(g, r, v, s, gamma=1e-7, max_iter=2, rel_tol=0.0),
         }
     else:
         s = api.mpi_forward(m, g, r, v, c)
