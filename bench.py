@@ -38,11 +38,13 @@ sys.path.insert(0, ROOT)
 #          accumulation).
 #   "vfar" (u >= 144): exp(-2z) is below FP32 resolution and a, d take their
 #          asymptotic form (rsqrt and 4 FP32 operations instead of 10 + 3 XU).
+#          The adjoint evaluates a uW + d P there as a polynomial in 1/z in
+#          nested form: 2 (distance) + 2 (quadratic form) + 5, one rsqrt.
 # Pairs near the FFP (u < 1, the Taylor series) are a ~1e-4 fraction and are
 # counted as "far".  The algorithmic count of a launch is the pair-weighted
 # mix, with the vfar fraction measured on the workload's geometry.
 ALG_OPS = {"k_forward": {"far": (18, 3), "vfar": (12, 1)},
-           "k_adjoint": {"far": (17, 3), "vfar": (11, 1)}}
+           "k_adjoint": {"far": (17, 3), "vfar": (9, 1)}}
 VFAR_U32 = 144.0
 
 
@@ -379,9 +381,10 @@ def measure_transfer(api, syn, dev, stream, s_model):
 
 # 3-D pairs: "far" 25 FP32 + 3 XU (3 differences, 3 for |y|^2, 10 for a, d,
 # 9 for the dot products and accumulation); "vfar" replaces the 10 + 3 XU of
-# a, d by 4 + 1 XU.
+# a, d by 4 + 1 XU; the adjoint's vfar pair term is nested in 1/z (one
+# operation fewer).
 ALG_OPS_3D = {"k_forward3": {"far": (25, 3), "vfar": (19, 1)},
-              "k_adjoint3": {"far": (25, 3), "vfar": (19, 1)}}
+              "k_adjoint3": {"far": (25, 3), "vfar": (18, 1)}}
 
 
 def vfar_fraction3(model3, grid3, r, stride=64):

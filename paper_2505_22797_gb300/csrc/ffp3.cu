@@ -58,6 +58,14 @@ struct Mat3 {
 };
 
 constexpr int k3Threads = 128;
+// Minimum resident blocks per SM requested for the FP32 pair kernels
+// (compile-time tuning knobs; the FP64 kernels request 2).
+#ifndef MPI_FWD3_MINB
+#define MPI_FWD3_MINB 4
+#endif
+#ifndef MPI_ADJ3_MINB
+#define MPI_ADJ3_MINB 4
+#endif
 constexpr int k3FwdS = 4;                        // samples per thread (forward)
 constexpr int k3FwdTile = k3Threads * k3FwdS;    // samples per forward work item
 constexpr int k3Piece = 512;                     // voxels per staged pass / per voxel box
@@ -239,7 +247,7 @@ __device__ __forceinline__ void fwd3_pass(const V4<R> *sv, int cnt, const R (&Rx
 }
 
 template <typename R, typename CIN>
-__global__ void __launch_bounds__(k3Threads, sizeof(R) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(k3Threads, sizeof(R) == 4 ? MPI_FWD3_MINB : 2)
 k_forward3(const __grid_constant__ Fwd3Args<R, CIN> a)
 {
     __shared__ V4<R> sv[k3Piece];
@@ -318,18 +326,22 @@ __device__ __forceinline__ void adj3_pass(const V4<R> *sR, const V4<R> *sW, cons
         for (int m = 0; m < k3AdjV; ++m) {
             const R yx = Px[m] - Q.x, yy = Py[m] - Q.y, yz = Pz[m] - Q.z;
             const R u = fmx(yz, yz, fmx(yy, yy, yx * yx));
-            R a, d;
-            lang3<R, false, MODE>(u, a, d);
             const R yU = fmx(yz, U.z, fmx(yy, U.y, yx * U.x));
             const R yW = fmx(yz, W.z, fmx(yy, W.y, yx * W.x));
             // U^T K W = a (U.W) + d (y.U)(y.W)
-            acc[m] = fmx(d * yU, yW, fmx(a, W.w, acc[m]));
+            if constexpr (MODE == 2) {
+                acc[m] = pair_acc_vfar<R, false>(u, W.w, yU * yW, acc[m]);
+            } else {
+                R a, d;
+                lang3<R, false, MODE>(u, a, d);
+                acc[m] = fmx(d * yU, yW, fmx(a, W.w, acc[m]));
+            }
         }
     }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(k3Threads, sizeof(R) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(k3Threads, sizeof(R) == 4 ? MPI_ADJ3_MINB : 2)
 k_adjoint3(const __grid_constant__ Adj3Args<R> a)
 {
     __shared__ V4<R> sR[k3Batch], sW[k3Batch], sU[k3Batch];

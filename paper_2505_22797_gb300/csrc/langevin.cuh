@@ -65,6 +65,8 @@ template <> struct Lang<float> {
     static constexpr float near_u = kNearU32;
     static constexpr float vfar_u = kVfarU32, vfar_u_beta = kVfarU32Beta;
 
+    // 1/z for the asymptotic forms.
+    static __device__ __forceinline__ float iz_vfar(float u) { return rsqrt_approx(u); }
     // a, d for u >= vfar_u (asymptotic form, exact to FP32 there).
     static __device__ __forceinline__ void ad_vfar(float u, float &a, float &d)
     {
@@ -149,6 +151,7 @@ template <> struct Lang<double> {
     static constexpr double near_u = kNearU64;
     static constexpr double vfar_u = kVfarU64, vfar_u_beta = kVfarU64Beta;
 
+    static __device__ __forceinline__ double iz_vfar(double u) { return rsqrt_newton(u); }
     static __device__ __forceinline__ void ad_vfar(double u, double &a, double &d)
     {
         const double iz = rsqrt_newton(u), iz2 = iz * iz;
@@ -251,6 +254,25 @@ __device__ __forceinline__ void lang_vfar(R u, R &f1, R &f2)
     if constexpr (DBETA) Lang<R>::le_vfar(u, f1, f2);
     else Lang<R>::ad_vfar(u, f1, f2);
 }
+// acc + f1 uW + f2 P in the asymptotic range (the pair term of the adjoint
+// sums), as a polynomial in iz = 1/z evaluated in nested form:
+//   A^T:     (iz - iz^2) uW + iz^3 (2 iz - 1) P = iz (uW + iz (iz (2 iz - 1) P - uW)),
+//   d/dbeta: iz^2 uW - 2 iz^4 P                = iz^2 (uW - 2 iz^2 P).
+// Five (four) operations after P instead of the seven of forming f1 and f2
+// first and then the two products.
+template <typename R, bool DBETA>
+__device__ __forceinline__ R pair_acc_vfar(R u, R uW, R P, R acc)
+{
+    const R iz = Lang<R>::iz_vfar(u);
+    if constexpr (DBETA) {
+        const R iz2 = iz * iz;
+        return fmx(iz2, fmx(iz2 * P, R(-2), uW), acc);
+    } else {
+        const R w = fmx(iz, P * fmx(iz, R(2), R(-1)), -uW);
+        return fmx(iz, fmx(iz, w, uW), acc);
+    }
+}
+
 template <typename R, bool DBETA>
 __host__ __device__ constexpr R vfar_threshold()
 {

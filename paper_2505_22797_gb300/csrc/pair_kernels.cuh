@@ -28,14 +28,15 @@ constexpr int kAdjThreads = 128;  // 4 warps
 #endif
 // Tuning knobs (compile time), chosen by timing variants on GB300: minimum
 // resident blocks per SM requested from the register allocator for the FP32
-// kernels (fewer, fatter warps win: more registers let the compiler overlap
-// the three MUFU latencies of a pair), and the unroll depth of the forward
-// column loop.  The FP64 kernels request 2 blocks per SM (no spills).
+// kernels (6 x 128 threads for both: the forward's loop keeps 8 columns in
+// flight in 80 registers; the adjoint, whose asymptotic pair term is a short
+// dependent chain, is latency-bound below 6), and the unroll depth of the
+// forward column loop.  The FP64 kernels request 2 blocks per SM (no spills).
 #ifndef MPI_FWD_MINB
 #define MPI_FWD_MINB 6
 #endif
 #ifndef MPI_ADJ_MINB
-#define MPI_ADJ_MINB 4
+#define MPI_ADJ_MINB 6
 #endif
 #ifndef MPI_FWD_UNROLL
 #define MPI_FWD_UNROLL 8
@@ -237,6 +238,12 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
         wy_hi = max(wy_hi, __shfl_xor_sync(0xffffffffu, wy_hi, o));
     }
     constexpr R kUv = vfar_threshold<R, false>();
+    // Column origin and inverse pitch of the prescaled grid (for the per-row
+    // segment bounds below; read from global memory, the shared copy is not
+    // yet visible here).
+    const R x0c = F.xcol[0].x;
+    const R inv_h = R(1) / (nx > 1 ? F.xcol[1].x - x0c : R(1));
+    const R ax_lo = wx_lo - x0c, ax_hi = wx_hi - x0c;
 
     // Rows of the chunk are staged RB at a time.
 #pragma unroll 1
@@ -273,10 +280,12 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
                 const R gy = max(R(0), max(wy_lo - yr.y, yr.y - wy_hi));
                 const R gy2 = gy * gy;
                 if (gy2 < kUv) {
-                    const R w = sqrt(kUv - gy2) * R(1.0001);
-                    const R x0c = s_x[0].x;
-                    const R h = nx > 1 ? s_x[1].x - x0c : R(1);
-                    const R ia = (wx_lo - w - x0c) / h, ib = (wx_hi + w - x0c) / h;
+                    // sqrt(kUv - gy2) as x rsqrt(x) with an FP32 estimate (x >=
+                    // ulp(kUv) > 0); its error and that of the inverse pitch are
+                    // far inside the 1e-4 relative and one-column margins.
+                    const R x = kUv - gy2;
+                    const R w = x * R(rsqrt_approx(float(x))) * R(1.0001);
+                    const R ia = (ax_lo - w) * inv_h, ib = (ax_hi + w) * inv_h;
                     const R fl = min(max(floor(min(ia, ib)) - R(1), R(0)), R(nx));
                     const R fh = min(max(ceil(max(ia, ib)) + R(1), R(-1)), R(nx - 1));
                     lo = (int)fl;
@@ -377,9 +386,14 @@ __device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const 
         for (int v = 0; v < kAdjV; ++v) {
             const R yy = yrow_y[v] - rr.y;
             const R u = fmx(yy, yy, yx2);
-            R f1, f2;
-            lang_mode<R, DBETA, MODE>(u, f1, f2);
-            blk[v] += fmx(f1, q.x, f2 * fmx(yy, fmx(q.w, yy, Q1), Q0));
+            const R P = fmx(yy, fmx(q.w, yy, Q1), Q0);
+            if constexpr (MODE == 2) {
+                blk[v] = pair_acc_vfar<R, DBETA>(u, q.x, P, blk[v]);
+            } else {
+                R f1, f2;
+                lang_mode<R, DBETA, MODE>(u, f1, f2);
+                blk[v] += fmx(f1, q.x, f2 * P);
+            }
         }
     } else {
         const R ox = xc.x - rr.x, oy = xc.y - rr.y;
@@ -388,10 +402,14 @@ __device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const 
             const R yx = ox + yrow_x[v];
             const R yy = oy + yrow_y[v];
             const R u = fmx(yx, yx, yy * yy);
-            R f1, f2;
-            lang_mode<R, DBETA, MODE>(u, f1, f2);
             const R quad = fmx(yx, fmx(q.y, yx, q.z * yy), q.w * yy * yy);
-            blk[v] += fmx(f1, q.x, f2 * quad);
+            if constexpr (MODE == 2) {
+                blk[v] = pair_acc_vfar<R, DBETA>(u, q.x, quad, blk[v]);
+            } else {
+                R f1, f2;
+                lang_mode<R, DBETA, MODE>(u, f1, f2);
+                blk[v] += fmx(f1, q.x, f2 * quad);
+            }
         }
     }
 }
