@@ -137,7 +137,8 @@ template <> struct Lang<float> {
 // inverse-square-root iteration y <- y + y (1 - u y^2)/2), started from the
 // FP32 hardware estimate: each step squares the relative error (2^-22 ->
 // ~2^-43 -> below FP64 rounding), with FMAs only.  Valid for u in the FP32
-// normal range (the asymptotic forms use it for u >= 441).
+// normal range (the FP64 closed form uses it for u >= 1/4, the asymptotic
+// form for u >= 441).
 __device__ __forceinline__ double rsqrt_newton(double u)
 {
     double y = double(rsqrt_approx(float(u)));
@@ -165,14 +166,21 @@ template <> struct Lang<double> {
         e = -2.0 * lp * lp;
     }
 
+    // coth z and csch^2 z from q = exp(-2z) for u >= near_u: there z >= 1/2,
+    // so q <= 1/e and 1 - q >= 0.63 carries no cancellation (no expm1
+    // needed); one division, 1/(1 - q), serves both.
+    static __device__ __forceinline__ void coth_csch2(double z, double &coth, double &csch2)
+    {
+        const double q = exp(-2.0 * z);
+        const double r = 1.0 / (1.0 - q);
+        coth = (1.0 + q) * r;
+        csch2 = 4.0 * q * r * r;
+    }
     static __device__ __forceinline__ void ad_far(double u, double &a, double &d)
     {
-        const double z = sqrt(u);
-        const double iz = 1.0 / z, iz2 = iz * iz;
-        const double em = expm1(-2.0 * z);  // q - 1
-        const double q = exp(-2.0 * z);
-        const double coth = -(2.0 + em) / em;
-        const double csch2 = 4.0 * q / (em * em);
+        const double iz = rsqrt_newton(u), z = u * iz, iz2 = iz * iz;
+        double coth, csch2;
+        coth_csch2(z, coth, csch2);
         a = coth * iz - iz2;
         d = ((iz2 - csch2) - a) * iz2;
     }
@@ -188,12 +196,9 @@ template <> struct Lang<double> {
     }
     static __device__ __forceinline__ void le_far(double u, double &lp, double &e)
     {
-        const double z = sqrt(u);
-        const double iz = 1.0 / z, iz2 = iz * iz;
-        const double em = expm1(-2.0 * z);
-        const double q = exp(-2.0 * z);
-        const double coth = -(2.0 + em) / em;
-        const double csch2 = 4.0 * q / (em * em);
+        const double iz = rsqrt_newton(u), z = u * iz, iz2 = iz * iz;
+        double coth, csch2;
+        coth_csch2(z, coth, csch2);
         lp = iz2 - csch2;
         e = 2.0 * iz * (coth * csch2 - iz * iz2);
     }
