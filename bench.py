@@ -64,6 +64,14 @@ def vfar_fraction(model, grid, r, stride=64):
     return n_far / (P.shape[0] * Rb.shape[0])
 
 
+def issue_bound_gpair(sm_count, sm_mhz, n_fp32, n_xu):
+    """Pairs per second (1e9 units) the SMs can issue when a pair costs n_fp32
+    FP32 and n_xu XU operations: per SM and clock at most 128 thread
+    instructions in all, 128 on the FP32 pipe and 32 on the XU pipe."""
+    per_clk = min(128.0 / (n_fp32 + n_xu), 128.0 / n_fp32, 32.0 / n_xu)
+    return sm_count * sm_mhz * 1e6 * per_clk / 1e9
+
+
 def mixed_ops(kernel, f_vfar):
     (a32, axu), (b32, bxu) = ALG_OPS[kernel]["far"], ALG_OPS[kernel]["vfar"]
     return (1 - f_vfar) * a32 + f_vfar * b32, (1 - f_vfar) * axu + f_vfar * bxu
@@ -436,8 +444,7 @@ def measure_ffp3d(api, syn, dev, stream, sm_count, sm_max):
         ms = tot / max(n, 1)
         (a32, axu), (b32, bxu) = ALG_OPS_3D[name]["far"], ALG_OPS_3D[name]["vfar"]
         n_fp32, n_xu = (1 - f_vfar) * a32 + f_vfar * b32, (1 - f_vfar) * axu + f_vfar * bxu
-        per_clk = min(128.0 / (n_fp32 + n_xu), 128.0 / n_fp32, 32.0 / n_xu)
-        peak = sm_count * sm_max * 1e6 * per_clk / 1e9
+        peak = issue_bound_gpair(sm_count, sm_max, n_fp32, n_xu)
         rate = N * T / (ms * 1e-3) / 1e9
         out[name] = {"avg_launch_ms": ms, "gpair_per_s": rate, "peak": peak, "frac": rate / peak,
                      "peak_basis": (f"issue bound, {n_fp32:.2f} FP32 + {n_xu:.3f} XU algorithmic ops per "
@@ -628,8 +635,7 @@ def run_ours(args):
     # (32 results per SM per cycle on GB300, inferred from ncu's pct-of-peak).
     f_vfar = vfar_fraction(m, g, cfg["r"])
     n_fp32, n_xu = mixed_ops(dom, f_vfar)
-    per_clk = min(128.0 / (n_fp32 + n_xu), 128.0 / n_fp32, 32.0 / n_xu)
-    peak_gpair = sm_count * sm_max * 1e6 * per_clk / 1e9
+    peak_gpair = issue_bound_gpair(sm_count, sm_max, n_fp32, n_xu)
     achieved = (N * T) / (ms_l / n_l * 1e-3) / 1e9 if n_l else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gpair, "unit": "Gpair/s",
                 "frac": achieved / peak_gpair if achieved else None, "traffic": _traffic(dom),
