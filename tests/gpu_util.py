@@ -3,7 +3,7 @@ import numpy as np
 import torch
 
 # Tolerances on the relative L2 error against the FP64 oracle: FP32 paths
-# 1e-5, FP64 paths 1e-12 (the parity bar of the method's north star).
+# 1e-5, FP64 paths 1e-12.
 TOL32 = 1e-5
 TOL64 = 1e-12
 
