@@ -370,6 +370,33 @@ int launch_interp3_T(const G3 &g, int64_t T, const R *s_sorted, const Bins3 &b, 
     return MPI_OK;
 }
 
+// The 3-D Core Stage operator: (1/T) M^T M through the binned records and
+// the 7-point Laplacian of each component.
+template <typename R>
+struct GridOp3 final : CoreStageOp {
+    const G3 &g;
+    int64_t T;
+    int ch, nc;
+    const Bins3 &bins;
+    R *s_tmp;
+    double invT;
+    GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_)
+        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 9 : 3), bins(b_), s_tmp(s_tmp_),
+          invT(T_ > 0 ? 1.0 / double(T_) : 0.0) {}
+    int normal(const double *p, double *y, cudaStream_t st) override
+    {
+        MPI_TRY((launch_interp3<R, double>(g, T, nullptr, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
+                                           static_cast<const InterpRec3<R> *>(bins.rec))));
+        return launch_interp3_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch);
+    }
+    int lap(const double *x, double *out, cudaStream_t st) override
+    {
+        k_lap3<<<grid_blocks(nc * g.n()), 256, 0, st>>>(g.nx, g.ny, g.nz, nc, x, out);
+        MPI_CHECK_LAUNCH();
+        return MPI_OK;
+    }
+};
+
 template <typename R>
 int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid_opts &o, void *Ahat,
                void *trace, int *n_iter_out, cudaStream_t st)
@@ -378,7 +405,6 @@ int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid
     const int ch = o.channel - 1;  // -1: all channels; 0..2: that channel only
     const int nc = ch < 0 ? 9 : 3, rows = ch < 0 ? 3 : 1;
     const int64_t N = g.n(), nv = nc * N;
-    const int nblk = vec_blocks(nv);
     const R *r = static_cast<const R *>(tr->r), *v = static_cast<const R *>(tr->v);
     const R *s = static_cast<const R *>(s_in);
 
@@ -386,66 +412,19 @@ int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid
     const size_t o_bins = scr.reserve(bins3_bytes<R>(T, g));
     const size_t o_s = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_sd = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
-    const size_t vb = sizeof(double) * nv;
-    const size_t o_b = scr.reserve(vb), o_x = scr.reserve(vb), o_r = scr.reserve(vb), o_p = scr.reserve(vb),
-                 o_q = scr.reserve(vb), o_y = scr.reserve(vb), o_l1 = scr.reserve(vb), o_l2 = scr.reserve(vb);
-    const size_t o_parts = scr.reserve(sizeof(double) * 3 * nblk);
-    const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 8);
+    const size_t o_b = scr.reserve(sizeof(double) * nv), o_x = scr.reserve(sizeof(double) * nv);
     MPI_TRY(scr.allocate());
     const Bins3 bins = bins3_carve<R>(scr.at<char>(o_bins), T, g);
-    R *s_tmp = scr.at<R>(o_s), *s_data = scr.at<R>(o_sd);
-    double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x), *rr = scr.at<double>(o_r),
-           *p = scr.at<double>(o_p), *q = scr.at<double>(o_q), *y = scr.at<double>(o_y),
-           *l1 = scr.at<double>(o_l1), *l2 = scr.at<double>(o_l2);
-    double *pq_part = scr.at<double>(o_parts), *rr_part0 = pq_part + nblk, *rr_part1 = pq_part + 2 * nblk;
-    double *scal = scr.at<double>(o_sc);
-    int *done = reinterpret_cast<int *>(scal + 8), *iters = done + 1;
+    R *s_data = scr.at<R>(o_sd);
+    double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x);
 
     MPI_TRY(build_bins3<R>(g, T, r, v, bins, st));
-    const double invT = T > 0 ? 1.0 / double(T) : 0.0;
     MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
-    MPI_TRY((launch_interp3_T<R, double>(g, T, s_data, bins, b, invT, st, ch)));
-    MPI_TRY_CUDA(cudaMemsetAsync(x, 0, vb, st));
-    MPI_TRY_CUDA(cudaMemsetAsync(q, 0, vb, st));
-    MPI_TRY_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 + sizeof(int) * 8, st));
-    MPI_TRY(cg_init_launch(nv, b, x, q, scal, rr, p, rr_part0, done, st));
-    MPI_TRY(norm_thresh_launch(rr_part0, nblk, o.rel_tol, scal + kScalBnorm, st));
-    const double *thresh = o.rel_tol > 0.0 ? scal + kScalTol : nullptr;
-
-    int *h_done = nullptr;
-    MPI_TRY_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h_done), sizeof(int)));
-    struct PinnedFree {
-        int *p;
-        ~PinnedFree() { cudaFreeHost(p); }
-    } guard{h_done};
-
-    const int lap_grid = grid_blocks(nv);
-    const int poll = 16;
-    for (int it = 0; it < o.max_iter; ++it) {
-        // q = (1/T) M^T M p + gamma Lap Lap p
-        MPI_TRY((launch_interp3<R, double>(g, T, r, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
-                                           static_cast<const InterpRec3<R> *>(bins.rec))));
-        MPI_TRY((launch_interp3_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch)));
-        k_lap3<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, g.nz, nc, p, l1);
-        MPI_CHECK_LAUNCH();
-        k_lap3<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, g.nz, nc, l1, l2);
-        MPI_CHECK_LAUNCH();
-        MPI_TRY(grid_epilogue_launch(nv, nblk, y, l2, o.gamma, p, q, pq_part, st));
-        MPI_TRY(cg_step_launch(nv, x, rr, p, q, pq_part, nblk, (it & 1) ? rr_part1 : rr_part0,
-                               (it & 1) ? rr_part0 : rr_part1, done, thresh, iters, st));
-        if (thresh && (it + 1) % poll == 0 && it + 1 < o.max_iter) {
-            MPI_TRY_CUDA(cudaMemcpyAsync(h_done, done, sizeof(int), cudaMemcpyDeviceToHost, st));
-            MPI_TRY_CUDA(cudaStreamSynchronize(st));
-            if (*h_done) break;
-        }
-    }
+    GridOp3<R> op(g, T, ch, bins, scr.at<R>(o_s));
+    MPI_TRY((launch_interp3_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
+    MPI_TRY(core_stage_cg(op, nv, b, o, x, n_iter_out, st));
     k_grid3_output<R><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
     MPI_CHECK_LAUNCH();
-    if (n_iter_out) {
-        MPI_TRY_CUDA(cudaMemcpyAsync(h_done, iters, sizeof(int), cudaMemcpyDeviceToHost, st));
-        MPI_TRY_CUDA(cudaStreamSynchronize(st));
-        *n_iter_out = *h_done;
-    }
     return MPI_OK;
 }
 

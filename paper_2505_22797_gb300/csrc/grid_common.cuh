@@ -2,8 +2,8 @@
 // three-dimensional solves: the one-dimensional cosine weights of the
 // interpolation, the binning of samples by interpolation cell (count, scan,
 // fill, per-cell sort), the work units of the transpose and their ordered
-// combine, and the epilogue of the CG operator.  The non-template kernels
-// live in grid_ops.cu behind the launchers declared here.
+// combine, and the CG solve over a Core Stage operator.  The non-template
+// kernels live in grid_ops.cu behind the launchers declared here.
 #pragma once
 
 #include <algorithm>
@@ -55,7 +55,6 @@ constexpr int kUnitLen = 128;
 constexpr int kUnitLanes = 8;     // lanes per unit
 constexpr int kUnitThreads = 256;
 constexpr int kScanThreads = 1024;
-constexpr int kEpiThreads = 256, kEpiPer = 2048;
 
 inline int grid_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
 
@@ -68,11 +67,23 @@ int cell_fill_launch(int64_t T, const int *cell_of, int *cursor, int *list, cuda
 int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st);
 // unit_node[w] = node for the units unit_off[node] .. unit_off[node + 1].
 int unit_fill_launch(int N, const int *unit_off, int *unit_node, cudaStream_t st);
-// q = y + gamma lap2 and nblk partial sums of <p, q> (kEpiPer elements each).
-int grid_epilogue_launch(int64_t n, int nblk, const double *y, const double *lap2, double gamma,
-                         const double *p, double *q, double *dot_part, cudaStream_t st);
-// out[0] = sqrt(sum of the n partials), out[1] = tol out[0] (or -1 if tol <= 0).
-int norm_thresh_launch(const double *part, int n, double tol, double *out, cudaStream_t st);
+
+// The operator of one Core Stage solve on nv FP64 unknowns (all components
+// of all nodes): y = (1/T) M^T M p and the Laplacian of every component.
+// Both methods only enqueue on `st`.
+struct CoreStageOp {
+    virtual ~CoreStageOp() = default;
+    virtual int normal(const double *p, double *y, cudaStream_t st) = 0;
+    virtual int lap(const double *x, double *out, cudaStream_t st) = 0;
+};
+
+// CG from x = 0 on ((1/T) M^T M + gamma Lap Lap) x = b (Eq. first:step; Lap is
+// symmetric, so Lap^T Lap = Lap Lap) with opts' gamma, iteration limit and
+// relative tolerance; writes x (nv FP64 values).  With a tolerance the host
+// polls the device stop flag every 16 steps.  With n_iter_out (host) the
+// stream is synchronised and the number of CG updates stored.
+int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_opts &o, double *x,
+                  int *n_iter_out, cudaStream_t st);
 
 // rec[q] = rec_t[list[q]] and vs[q] = v[list[q]] (D velocity components):
 // the records and velocities of the samples in list (cell) order.

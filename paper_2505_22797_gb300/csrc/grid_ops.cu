@@ -435,6 +435,7 @@ __global__ void k_lap(int nx, int ny, int nc, const double *__restrict__ x, doub
 }
 
 // q = y + gamma lap2, partial sums of <p, q> (blocks of 2048 elements).
+constexpr int kEpiThreads = 256, kEpiPer = 2048;
 __global__ void __launch_bounds__(kEpiThreads)
 k_grid_epilogue(int64_t n, const double *__restrict__ y, const double *__restrict__ lap2, double gamma,
                 const double *__restrict__ p, double *__restrict__ q, double *__restrict__ dot_part)
@@ -475,92 +476,63 @@ __global__ void k_grid_output(int64_t N, int ch, const double *__restrict__ x, R
     }
 }
 
+// The 2-D Core Stage operator: (1/T) M^T M through the binned records and
+// the 5-point Laplacian of each component.
+template <typename R>
+struct GridOp2 final : CoreStageOp {
+    const GridH &g;
+    int64_t T;
+    int ch, nc;
+    const Bins &bins;
+    R *s_tmp;
+    double invT;
+    GridOp2(const GridH &g_, int64_t T_, int ch_, const Bins &b_, R *s_tmp_)
+        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 4 : 2), bins(b_), s_tmp(s_tmp_),
+          invT(T_ > 0 ? 1.0 / double(T_) : 0.0) {}
+    int normal(const double *p, double *y, cudaStream_t st) override
+    {
+        MPI_TRY((launch_interp<R, double>(g, T, nullptr, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
+                                          static_cast<const InterpRec<R> *>(bins.rec))));
+        return launch_interp_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch);
+    }
+    int lap(const double *x, double *out, cudaStream_t st) override
+    {
+        k_lap<<<grid_blocks(int64_t(nc) * g.nx * g.ny), 256, 0, st>>>(g.nx, g.ny, nc, x, out);
+        MPI_CHECK_LAUNCH();
+        return MPI_OK;
+    }
+};
+
 template <typename R>
 static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const mpi_grid_opts &o,
                      void *Ahat, void *trace, int *n_iter_out, cudaStream_t st)
 {
     const int64_t T = tr->T;
     const int ch = o.channel - 1;  // -1: both channels; 0 / 1: that channel only
-    const int nc = ch < 0 ? 4 : 2;
+    const int nc = ch < 0 ? 4 : 2, rows = ch < 0 ? 2 : 1;
     const int64_t N = (int64_t)g.nx * g.ny, n4 = nc * N;
-    const int nblk = vec_blocks(n4);
     const R *r = static_cast<const R *>(tr->r), *v = static_cast<const R *>(tr->v);
     const R *s = static_cast<const R *>(s_in);
 
     Scratch scr(st);
     const size_t o_bins = scr.reserve(bins_bytes<R>(T, g.nx, g.ny));
-    const size_t o_s = scr.reserve(sizeof(R) * (ch < 0 ? 2 : 1) * std::max<int64_t>(T, 1));
-    const size_t o_sd = scr.reserve(sizeof(R) * (ch < 0 ? 2 : 1) * std::max<int64_t>(T, 1));
-    const size_t vb = sizeof(double) * n4;
-    const size_t o_b = scr.reserve(vb), o_x = scr.reserve(vb), o_r = scr.reserve(vb),
-                 o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_y = scr.reserve(vb),
-                 o_l1 = scr.reserve(vb), o_l2 = scr.reserve(vb);
-    const size_t o_parts = scr.reserve(sizeof(double) * 3 * nblk);
-    const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 8);
+    const size_t o_s = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
+    const size_t o_sd = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
+    const size_t o_b = scr.reserve(sizeof(double) * n4), o_x = scr.reserve(sizeof(double) * n4);
     MPI_TRY(scr.allocate());
     const Bins bins = bins_carve<R>(scr.at<char>(o_bins), T, g.nx, g.ny);
-    R *s_tmp = scr.at<R>(o_s);
-    double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x), *rr = scr.at<double>(o_r),
-           *p = scr.at<double>(o_p), *q = scr.at<double>(o_q), *y = scr.at<double>(o_y),
-           *l1 = scr.at<double>(o_l1), *l2 = scr.at<double>(o_l2);
-    double *pq_part = scr.at<double>(o_parts), *rr_part0 = pq_part + nblk, *rr_part1 = pq_part + 2 * nblk;
-    double *scal = scr.at<double>(o_sc);
-    int *done = reinterpret_cast<int *>(scal + 8), *iters = done + 1;
+    R *s_data = scr.at<R>(o_sd);
+    double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x);
 
     MPI_TRY(build_bins<R>(g, T, r, v, bins, st));
-    const double invT = T > 0 ? 1.0 / double(T) : 0.0;
     // The sample vectors of the solve live in list (cell) order.
-    R *s_data = scr.at<R>(o_sd);
-    MPI_TRY(gather_rows<R>(T, ch < 0 ? 2 : 1, bins.list, s, s_data, st));
+    MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
+    GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_s));
     // b = (1/T) M^T s
-    MPI_TRY((launch_interp_T<R, double>(g, T, s_data, bins, b, invT, st, ch)));
-    MPI_TRY_CUDA(cudaMemsetAsync(x, 0, vb, st));
-    MPI_TRY_CUDA(cudaMemsetAsync(q, 0, vb, st));
-    MPI_TRY_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 + sizeof(int) * 8, st));
-    // r = b, p = b, rr partials (nu = 0 from the zeroed scalar block)
-    MPI_TRY(cg_init_launch(n4, b, x, q, scal, rr, p, rr_part0, done, st));
-    k_norm_thresh<<<1, 32, 0, st>>>(rr_part0, nblk, o.rel_tol, scal + kScalBnorm);
+    MPI_TRY((launch_interp_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
+    MPI_TRY(core_stage_cg(op, n4, b, o, x, n_iter_out, st));
+    k_grid_output<R><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
     MPI_CHECK_LAUNCH();
-    const double *thresh = o.rel_tol > 0.0 ? scal + kScalTol : nullptr;
-
-    int *h_done = nullptr;
-    MPI_TRY_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h_done), sizeof(int)));
-    struct PinnedFree {
-        int *p;
-        ~PinnedFree() { cudaFreeHost(p); }
-    } guard{h_done};
-
-    const int lap_grid = grid_blocks(n4);
-    const int poll = 16;
-    for (int it = 0; it < o.max_iter; ++it) {
-        // q = (1/T) M^T M p + gamma Lap Lap p
-        MPI_TRY((launch_interp<R, double>(g, T, r, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
-                                          static_cast<const InterpRec<R> *>(bins.rec))));
-        MPI_TRY((launch_interp_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch)));
-        k_lap<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, nc, p, l1);
-        MPI_CHECK_LAUNCH();
-        k_lap<<<lap_grid, 256, 0, st>>>(g.nx, g.ny, nc, l1, l2);
-        MPI_CHECK_LAUNCH();
-        k_grid_epilogue<<<nblk, kEpiThreads, 0, st>>>(n4, y, l2, o.gamma, p, q, pq_part);
-        MPI_CHECK_LAUNCH();
-        MPI_TRY(cg_step_launch(n4, x, rr, p, q, pq_part, nblk, (it & 1) ? rr_part1 : rr_part0,
-                               (it & 1) ? rr_part0 : rr_part1, done, thresh, iters, st));
-        if (thresh && (it + 1) % poll == 0 && it + 1 < o.max_iter) {
-            MPI_TRY_CUDA(cudaMemcpyAsync(h_done, done, sizeof(int), cudaMemcpyDeviceToHost, st));
-            MPI_TRY_CUDA(cudaStreamSynchronize(st));
-            if (*h_done) break;
-        }
-    }
-    const int vgrid = grid_blocks(N);
-    k_grid_output<R><<<vgrid, 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
-    MPI_CHECK_LAUNCH();
-    if (n_iter_out) {
-        int hi = 0;
-        MPI_TRY_CUDA(cudaMemcpyAsync(h_done, iters, sizeof(int), cudaMemcpyDeviceToHost, st));
-        MPI_TRY_CUDA(cudaStreamSynchronize(st));
-        hi = *h_done;
-        *n_iter_out = hi;
-    }
     return MPI_OK;
 }
 
@@ -598,7 +570,7 @@ static int check_interp_args(const mpi_grid_desc *grid, const mpi_traj *traj, mp
     return MPI_OK;
 }
 
-// Launchers of the binning and epilogue kernels for the 3-D Core Stage.
+// Launchers of the binning kernels for the 3-D Core Stage.
 int cell_scan_launch(const int *count, int n, int *offset, int *cursor, cudaStream_t st)
 {
     k_scan<<<1, kScanThreads, 0, st>>>(count, n, offset, cursor);
@@ -628,18 +600,61 @@ int unit_fill_launch(int N, const int *unit_off, int *unit_node, cudaStream_t st
     return MPI_OK;
 }
 
-int grid_epilogue_launch(int64_t n, int nblk, const double *y, const double *lap2, double gamma,
-                         const double *p, double *q, double *dot_part, cudaStream_t st)
+int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_opts &o, double *x,
+                  int *n_iter_out, cudaStream_t st)
 {
-    k_grid_epilogue<<<nblk, kEpiThreads, 0, st>>>(n, y, lap2, gamma, p, q, dot_part);
-    MPI_CHECK_LAUNCH();
-    return MPI_OK;
-}
+    const int nblk = vec_blocks(nv);
+    const int nepi = (int)std::max<int64_t>(1, (nv + kEpiPer - 1) / kEpiPer);
+    Scratch scr(st);
+    const size_t vb = sizeof(double) * nv;
+    const size_t o_r = scr.reserve(vb), o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_y = scr.reserve(vb),
+                 o_l1 = scr.reserve(vb), o_l2 = scr.reserve(vb);
+    const size_t o_pq = scr.reserve(sizeof(double) * nepi), o_rr = scr.reserve(sizeof(double) * 2 * nblk);
+    const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 8);
+    MPI_TRY(scr.allocate());
+    double *rr = scr.at<double>(o_r), *p = scr.at<double>(o_p), *q = scr.at<double>(o_q),
+           *y = scr.at<double>(o_y), *l1 = scr.at<double>(o_l1), *l2 = scr.at<double>(o_l2);
+    double *pq_part = scr.at<double>(o_pq), *rr_part0 = scr.at<double>(o_rr), *rr_part1 = rr_part0 + nblk;
+    double *scal = scr.at<double>(o_sc);
+    int *done = reinterpret_cast<int *>(scal + 8), *iters = done + 1;
 
-int norm_thresh_launch(const double *part, int n, double tol, double *out, cudaStream_t st)
-{
-    k_norm_thresh<<<1, 32, 0, st>>>(part, n, tol, out);
+    MPI_TRY_CUDA(cudaMemsetAsync(x, 0, vb, st));
+    MPI_TRY_CUDA(cudaMemsetAsync(q, 0, vb, st));
+    MPI_TRY_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 + sizeof(int) * 8, st));
+    // r = b, p = b, partial sums of r.r (nu = 0 from the zeroed scalar block)
+    MPI_TRY(cg_init_launch(nv, b, x, q, scal, rr, p, rr_part0, done, st));
+    k_norm_thresh<<<1, 32, 0, st>>>(rr_part0, nblk, o.rel_tol, scal + kScalBnorm);
     MPI_CHECK_LAUNCH();
+    const double *thresh = o.rel_tol > 0.0 ? scal + kScalTol : nullptr;
+
+    int *h_done = nullptr;
+    MPI_TRY_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h_done), sizeof(int)));
+    struct PinnedFree {
+        int *p;
+        ~PinnedFree() { cudaFreeHost(p); }
+    } guard{h_done};
+
+    const int poll = 16;
+    for (int it = 0; it < o.max_iter; ++it) {
+        // q = (1/T) M^T M p + gamma Lap Lap p, and <p, q>
+        MPI_TRY(op.normal(p, y, st));
+        MPI_TRY(op.lap(p, l1, st));
+        MPI_TRY(op.lap(l1, l2, st));
+        k_grid_epilogue<<<nepi, kEpiThreads, 0, st>>>(nv, y, l2, o.gamma, p, q, pq_part);
+        MPI_CHECK_LAUNCH();
+        MPI_TRY(cg_step_launch(nv, x, rr, p, q, pq_part, nepi, (it & 1) ? rr_part1 : rr_part0,
+                               (it & 1) ? rr_part0 : rr_part1, done, thresh, iters, st));
+        if (thresh && (it + 1) % poll == 0 && it + 1 < o.max_iter) {
+            MPI_TRY_CUDA(cudaMemcpyAsync(h_done, done, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MPI_TRY_CUDA(cudaStreamSynchronize(st));
+            if (*h_done) break;
+        }
+    }
+    if (n_iter_out) {
+        MPI_TRY_CUDA(cudaMemcpyAsync(h_done, iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPI_TRY_CUDA(cudaStreamSynchronize(st));
+        *n_iter_out = *h_done;
+    }
     return MPI_OK;
 }
 
