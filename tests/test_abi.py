@@ -140,3 +140,71 @@ def test_core_stage_argument_validation_without_gpu(lib):
     st = lib.mpi_grid(ctypes.byref(g2), ctypes.byref(tr0), 0, None,
                       ctypes.byref(_GridOpts(1e-7, 10, 1e-3, 3)), buf, buf, None, None)
     assert st == -1 and b"options" in lib.mpi_last_error_message()
+
+
+def test_other_entry_points_validate_without_gpu():
+    """3-D operators, the convolution entries, the transfer correction, the
+    PnP options and the batch plan reject bad arguments on the host with
+    MPI_ERR_INVALID (or MPI_ERR_UNSUPPORTED) and a message, before any CUDA
+    call."""
+    from paper_2505_22797_gb300 import api, build
+    build.build()
+    lib = api.load()
+    D9 = ctypes.c_double * 9
+    D4 = ctypes.c_double * 4
+    eye3 = D9(1, 0, 0, 0, 1, 0, 0, 0, 1)
+    G3 = D9(-1.25e-3, 0, 0, 0, -1.25e-3, 0, 0, 0, 2.5e-3)
+    m3 = api.Model3(2331.35, G3, 3, eye3)
+    g3 = api.Grid3Desc(4, 4, 2, -12, -12, -6, 6, 6, 6)
+    m2 = api.Model(2331.35, D4(2.5e-3, 0, 0, 2.5e-3), 2, D4(1, 0, 0, 1))
+    g2 = api.GridDesc(4, 4, -12, -12, 6, 6)
+    tr0 = api.Traj(0, None, None)
+    buf = ctypes.c_void_p(16)  # never dereferenced
+    pnp = api.PnPOpts(api.MPI_OP_FORWARD, 2, 3, 1e-3, 5.0, 0)
+    no_cb = api.DENOISE_FN(0)
+    no_cb3 = api.DENOISE3_FN(0)
+
+    def ref(x):
+        return ctypes.byref(x)
+
+    cases = [
+        ("singular G (3-D)", lambda: lib.mpi_forward3(ref(api.Model3(1.0, D9(), 3, eye3)), ref(g3), ref(tr0), 0,
+                                                     buf, buf, None), -1, b"singular"),
+        ("n_ch 4 (3-D)", lambda: lib.mpi_adjoint3(ref(api.Model3(1.0, G3, 4, eye3)), ref(g3), ref(tr0), 0,
+                                                 buf, buf, None), -1, b"n_ch"),
+        ("nz 0", lambda: lib.mpi_conv3(ref(m3), ref(api.Grid3Desc(4, 4, 0, 0, 0, 0, 1, 1, 1)), 0, buf, buf,
+                                       None), -1, b"nx, ny, nz"),
+        ("component 4", lambda: lib.mpi_conv_component(ref(m2), ref(g2), 0, 4, buf, buf, None), -1, b""),
+        ("conv dtype", lambda: lib.mpi_conv(ref(m2), ref(g2), 3, buf, buf, None), -1, b"dtype"),
+        ("transfer n_ch 0", lambda: lib.mpi_transfer_correct(0, 16, 0, buf, buf, None, None, buf, None),
+         -1, b""),
+        ("transfer n_ch 9", lambda: lib.mpi_transfer_correct(9, 16, 0, buf, buf, None, None, buf, None),
+         -1, b""),
+        ("transfer T < 0", lambda: lib.mpi_transfer_correct(2, -4, 0, buf, buf, None, None, buf, None),
+         -1, b""),
+        ("transfer a_hat NULL", lambda: lib.mpi_transfer_correct(2, 16, 0, buf, None, None, None, buf, None),
+         -1, b""),
+        ("pnp n_iter < 0", lambda: lib.mpi_pnp_solve(ref(m2), ref(g2), ref(tr0), 0, buf,
+                                                     ref(api.PnPOpts(0, -1, 3, 1e-3, 5.0, 0)), no_cb, None,
+                                                     buf, None, None), -1, b""),
+        ("pnp op 7", lambda: lib.mpi_pnp_solve(ref(m2), ref(g2), ref(tr0), 0, buf,
+                                               ref(api.PnPOpts(7, 2, 3, 1e-3, 5.0, 0)), no_cb, None,
+                                               buf, None, None), -1, b""),
+        ("pnp3 kernel entry", lambda: lib.mpi_pnp_solve3(ref(m3), ref(g3), ref(tr0), 0, buf,
+                                                        ref(api.PnPOpts(1, 2, 3, 1e-3, 5.0, 1)), no_cb3, None,
+                                                        buf, None, None), -1, b""),
+        ("pnp opts NULL", lambda: lib.mpi_pnp_solve(ref(m2), ref(g2), ref(tr0), 0, buf, None, no_cb, None,
+                                                    buf, None, None), -1, b""),
+        ("batch 0 frames", lambda: lib.mpi_batch_plan_create(0, ref(m2), ref(g2), None, None, ref(pnp), 0,
+                                                             ctypes.byref(ctypes.c_void_p())), -1, b""),
+        ("batch 65 frames", lambda: lib.mpi_batch_plan_create(65, ref(m2), ref(g2), None, None, ref(pnp), 0,
+                                                              ctypes.byref(ctypes.c_void_p())), None, b""),
+    ]
+    for what, call, want, why in cases:
+        st = call()
+        if want is None:
+            assert st in (-1, -6), (what, st)
+        else:
+            assert st == want, (what, st, lib.mpi_last_error_message())
+        msg = lib.mpi_last_error_message()
+        assert msg and why in msg, (what, msg)
