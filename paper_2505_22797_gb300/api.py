@@ -33,52 +33,64 @@ MPI_OP_FORWARD, MPI_OP_CONV = 0, 1
 
 
 class MPIError(RuntimeError):
+    """A non-zero status of a library call, with the library's message."""
+
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
         self.status = status
 
 
 class GridDesc(ctypes.Structure):
+    """mpi_grid_desc: nx x ny voxels, centres (x0 + (i + 1/2) dx, y0 + (j + 1/2) dy)."""
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x0", ctypes.c_double),
                 ("y0", ctypes.c_double), ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
 
 
 class Model(ctypes.Structure):
+    """mpi_model: beta = 1/(mu0 H_sat), G row-major 2x2, n_ch receive directions p."""
     _fields_ = [("beta", ctypes.c_double), ("G", ctypes.c_double * 4), ("n_ch", ctypes.c_int),
                 ("p", ctypes.c_double * 4)]
 
 
 class Traj(ctypes.Structure):
+    """mpi_traj: T samples, device pointers to r [T][dim] and v = dr/dt [T][dim]."""
     _fields_ = [("T", ctypes.c_int64), ("r", ctypes.c_void_p), ("v", ctypes.c_void_p)]
 
 
 class GridOpts(ctypes.Structure):
+    """mpi_grid_opts: gamma, CG iteration limit, relative tolerance, channel selector."""
     _fields_ = [("gamma", ctypes.c_double), ("max_iter", ctypes.c_int), ("rel_tol", ctypes.c_double),
                 ("channel", ctypes.c_int)]
 
 
 class PnPOpts(ctypes.Structure):
+    """mpi_pnp_opts: operator, outer iterations, CG steps, nu0, clip percentile,
+    kernel entry of the single-channel deconvolution."""
     _fields_ = [("op", ctypes.c_int), ("n_iter", ctypes.c_int), ("n_cg", ctypes.c_int),
                 ("nu0", ctypes.c_double), ("clip_pct", ctypes.c_double),
                 ("kernel_component", ctypes.c_int)]
 
 
 class Grid3Desc(ctypes.Structure):
+    """mpi_grid3_desc: nx x ny x nz voxels with origin and spacing per axis."""
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
 
 
 class Model3(ctypes.Structure):
+    """mpi_model3: beta, G row-major 3x3, n_ch (1..3) receive directions p."""
     _fields_ = [("beta", ctypes.c_double), ("G", ctypes.c_double * 9), ("n_ch", ctypes.c_int),
                 ("p", ctypes.c_double * 9)]
 
 
 class PnPIterInfo(ctypes.Structure):
+    """Per-iteration (sigma, nu, final CG residual) of Algorithm 1."""
     _fields_ = [("sigma", ctypes.c_double), ("nu", ctypes.c_double), ("cg_resid", ctypes.c_double)]
 
 
 class BatchInfo(ctypes.Structure):
+    """The tuned configuration of a batch plan (mpi_batch_plan_info)."""
     _fields_ = [("n_frames", ctypes.c_int), ("tuned", ctypes.c_int),
                 ("item_pairs_forward", ctypes.c_longlong), ("item_pairs_adjoint", ctypes.c_longlong),
                 ("persistent_forward", ctypes.c_int), ("persistent_adjoint", ctypes.c_int),
@@ -163,6 +175,7 @@ def load(path: str | None = None):
 
 
 def exported_symbols():
+    """Names of the entry points this binding declares that the library exports."""
     lib = load()
     return {name for name in _SIGS if hasattr(lib, name)}
 
@@ -171,10 +184,13 @@ PROF_FORWARD, PROF_ADJOINT, PROF_DBETA, PROF_CONV = 0, 1, 2, 3
 
 
 def mpi_kernel_launches() -> int:
+    """Number of library kernel launches since the library was loaded."""
     return int(load().mpi_kernel_launches())
 
 
 def mpi_profile_enable(enable: bool = True):
+    """Switch the per-kernel-class CUDA-event timing on or off (see
+    mpi_profile_read)."""
     _check(load().mpi_profile_enable(1 if enable else 0))
 
 
@@ -198,16 +214,19 @@ def _get(obj, key):
 
 
 def make_grid(grid) -> GridDesc:
+    """mpi_grid_desc from a mapping or object with nx, ny, x0, y0, dx, dy."""
     return GridDesc(int(_get(grid, "nx")), int(_get(grid, "ny")), float(_get(grid, "x0")),
                     float(_get(grid, "y0")), float(_get(grid, "dx")), float(_get(grid, "dy")))
 
 
 def make_grid3(grid) -> Grid3Desc:
+    """mpi_grid3_desc from a mapping or object with nx, ny, nz, x0, y0, z0, dx, dy, dz."""
     return Grid3Desc(*(int(_get(grid, k)) for k in ("nx", "ny", "nz")),
                      *(float(_get(grid, k)) for k in ("x0", "y0", "z0", "dx", "dy", "dz")))
 
 
 def make_model3(model) -> Model3:
+    """mpi_model3 from beta, G (3x3) and p (n_ch x 3, n_ch = 1..3)."""
     G = [float(x) for row in _get(model, "G") for x in row]
     P = [[float(x) for x in row] for row in _get(model, "p")]
     if len(G) != 9 or not 1 <= len(P) <= 3 or any(len(row) != 3 for row in P):
@@ -218,6 +237,7 @@ def make_model3(model) -> Model3:
 
 
 def make_model(model) -> Model:
+    """mpi_model from beta, G (2x2) and p (n_ch x 2, n_ch = 1 or 2)."""
     G = [float(x) for row in _get(model, "G") for x in row]
     P = [[float(x) for x in row] for row in _get(model, "p")]
     flat = [x for row in P for x in row] + [0.0] * (4 - 2 * len(P))
@@ -315,6 +335,9 @@ def mpi_dbeta(model, grid, r, v, c, g_s, out=None, stream=None):
 
 
 def mpi_conv(model, grid, x, out=None, stream=None):
+    """out = C x: linear (zero-padded) convolution of x [ny, nx] with the sampled
+    trace kernel beta tr(K(beta G y) G) (Eq. kernel:trace); direct sum on small
+    grids, FFT route above."""
     dt = x.dtype
     if out is None:
         out = torch.empty_like(x)
@@ -337,6 +360,8 @@ def mpi_conv_component(model, grid, component, x, out=None, stream=None):
 
 
 def mpi_interp(grid, r, v, Ahat, s=None, stream=None):
+    """Core Stage measurement (Eq. first:step): s[k][t] = sum_m I[Ahat_{2k+m}](r_t)
+    v_m(t) with the cosine interpolation I; Ahat [4, ny, nx] -> s [2, T]."""
     dt = Ahat.dtype
     if s is None:
         s = torch.empty((2, r.shape[0]), dtype=dt, device=Ahat.device)
@@ -348,6 +373,8 @@ def mpi_interp(grid, r, v, Ahat, s=None, stream=None):
 
 
 def mpi_interp_adjoint(grid, r, v, s, Ahat=None, stream=None):
+    """Exact transpose of mpi_interp: s [2, T] -> Ahat [4, ny, nx], summed in a
+    fixed order (no atomics)."""
     dt = s.dtype
     g = make_grid(grid)
     if Ahat is None:
@@ -385,6 +412,8 @@ def mpi_grid(grid, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=None,
 
 
 def mpi_denoise_gaussian5(x, out=None, stream=None):
+    """The built-in PnP denoiser: separable 5-tap Gaussian (sigma = 1 px), reflect
+    boundary, on x [ny, nx]."""
     dt = x.dtype
     if out is None:
         out = torch.empty_like(x)
@@ -507,6 +536,8 @@ class BatchPlan:
 # 3).  Volumes are [nz, ny, nx]; r and v are [T, 3].
 
 def mpi_forward3(model3, grid3, r, v, c, s=None, stream=None):
+    """Forward operator in three dimensions: c [nz, ny, nx] -> s [n_ch, T],
+    s[k][t] = sum c p_k^T beta K(beta G(x - r_t)) G v_t with the 3x3 kernel matrix."""
     dt = c.dtype
     n_ch = len(_get(model3, "p"))
     if s is None:
@@ -520,6 +551,7 @@ def mpi_forward3(model3, grid3, r, v, c, s=None, stream=None):
 
 
 def mpi_adjoint3(model3, grid3, r, v, s, c_out=None, stream=None):
+    """Adjoint of mpi_forward3: s [n_ch, T] -> c_out [nz, ny, nx]."""
     dt = s.dtype
     g = make_grid3(grid3)
     if c_out is None:
@@ -533,6 +565,8 @@ def mpi_adjoint3(model3, grid3, r, v, s, c_out=None, stream=None):
 
 
 def mpi_conv3(model3, grid3, x, out=None, stream=None):
+    """out = C x in three dimensions: convolution of x [nz, ny, nx] with the
+    sampled 3-D trace kernel (n - 1 = 2); direct sum or FFT route."""
     dt = x.dtype
     if out is None:
         out = torch.empty_like(x)
@@ -556,6 +590,8 @@ def mpi_interp3(grid3, r, v, Ahat, s=None, stream=None):
 
 
 def mpi_interp3_adjoint(grid3, r, v, s, Ahat=None, stream=None):
+    """Exact transpose of mpi_interp3: s [3, T] -> Ahat [9, nz, ny, nx], summed
+    in a fixed order (no atomics)."""
     dt = s.dtype
     g = make_grid3(grid3)
     if Ahat is None:
@@ -594,6 +630,8 @@ def mpi_grid3(grid3, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=Non
 
 
 def mpi_denoise_gaussian5_3d(x, out=None, stream=None):
+    """The built-in volume denoiser: the 5-tap Gaussian along x, y and z
+    (reflect boundary) on x [nz, ny, nx]."""
     dt = x.dtype
     if out is None:
         out = torch.empty_like(x)
