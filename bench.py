@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -204,10 +205,23 @@ class ClockSampler:
 KERNEL_SOURCES = ["common.cuh", "langevin.cuh", "pair_kernels.cuh", "pair_ops.cuh", "pair_ops.cu"]
 
 
-def kernel_digest():
+def code_only(text: str) -> str:
+    """C/CUDA source without comments and blank space: what a digest of the
+    kernel code should see (editing a comment changes no counter)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
+def kernel_digest(read=None):
+    """sha256 prefix of the code of the operator kernels' sources; `read(f)`
+    returns a source's text (default: the working tree)."""
+    if read is None:
+        def read(f):
+            return open(os.path.join(ROOT, "paper_2505_22797_gb300", "csrc", f)).read()
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2505_22797_gb300", "csrc", f), "rb").read())
+        h.update(code_only(read(f)).encode())
     return h.hexdigest()[:16]
 
 

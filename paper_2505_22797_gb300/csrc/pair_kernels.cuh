@@ -2,8 +2,14 @@
 //
 // Every (voxel, sample) pair evaluates the Langevin kernel once; there is no
 // contraction to hand to the tensor cores (one FMA per pair per channel), so
-// the kernels are bound by the FP32 and MUFU (XU) pipes: per pair 3 MUFU
-// operations (rsqrt, exp2, rcp) and ~18 FP32 operations.
+// the kernels are bound by instruction issue on the FP32 and MUFU (XU) pipes.
+// A pair costs the full closed form (3 MUFU: rsqrt, exp2, rcp, and ~18 FP32
+// operations) only near the samples; far from them (z >= 12, most pairs) the
+// asymptotic form needs one rsqrt and 12 (forward) or 9 (adjoint) FP32
+// operations, and within z < 1 the Taylor series replaces the closed form.
+// The regime is decided for warp-uniform segments (forward: column ranges of
+// a staged row; adjoint: groups of 32 staged samples, or single samples in
+// mixed groups); only the near-series check takes a per-pair warp vote.
 //
 // Both kernels take a frame table by value, so one launch can cover many
 // frames of different sizes: blockIdx.x enumerates work items of all frames

@@ -88,3 +88,14 @@ def test_traffic_is_dropped_for_other_sources(tmp_path, monkeypatch):
     assert bench._traffic("k_missing") is None
     (prof / "traffic.json").write_text("not json")
     assert bench._traffic("k_forward") is None
+
+
+def test_kernel_digest_sees_code_not_comments():
+    src = {f: "int a = 1;  // one\n/* block\n comment */\nint b = a + 2;\n" for f in bench.KERNEL_SOURCES}
+    base = bench.kernel_digest(lambda f: src[f])
+    edited = {f: "// a new comment\nint a = 1;\n\n\nint b = a + 2;   /* sum */\n" for f in bench.KERNEL_SOURCES}
+    assert bench.kernel_digest(lambda f: edited[f]) == base
+    changed = dict(src)
+    changed[bench.KERNEL_SOURCES[0]] = "int a = 1;\nint b = a + 3;\n"
+    assert bench.kernel_digest(lambda f: changed[f]) != base
+    assert bench.code_only("x = 1; // c\n/* d */ y = 2;") == "x = 1;\n y = 2;"
