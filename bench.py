@@ -109,6 +109,11 @@ def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
         return 0
+    if world > 1:
+        # torchrun gives every rank OMP_NUM_THREADS=1; the other ranks exit
+        # without work, so rank 0's oracle takes the host's cores as at N = 1
+        # (set before the oracle library, and with it OpenMP, is loaded).
+        os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     from oracle import oracle
     from paper_2505_22797_gb300 import synthetic as syn
     cfg = syn.config(WORKLOAD)

@@ -99,3 +99,25 @@ def test_kernel_digest_sees_code_not_comments():
     changed[bench.KERNEL_SOURCES[0]] = "int a = 1;\nint b = a + 3;\n"
     assert bench.kernel_digest(lambda f: changed[f]) != base
     assert bench.code_only("x = 1; // c\n/* d */ y = 2;") == "x = 1;\n y = 2;"
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as the benchmark contract launches N > 1 ranks, the reference
+    arm runs on rank 0 alone (one JSON line, n_gpus = N); the other rank
+    exits 0 without work."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    res = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                          "--master-addr", "127.0.0.1", "--master-port", str(port),
+                          os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "3"],
+                         capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert res.returncode == 0, res.stderr[-3000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1, res.stdout[-3000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    # rank 0 uses the host's cores although torchrun sets one thread per rank
+    assert d["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
