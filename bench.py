@@ -534,6 +534,12 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2505_22797_gb300 import api, build
     from paper_2505_22797_gb300 import synthetic as syn
+    if world > 1:
+        # one rank compiles (if the sources changed); the others then find the
+        # library built instead of compiling the same objects concurrently
+        if rank == 0:
+            build.build()
+        dist.barrier()
     build.build()
     api.load()
 
