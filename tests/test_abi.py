@@ -208,3 +208,32 @@ def test_other_entry_points_validate_without_gpu():
             assert st == want, (what, st, lib.mpi_last_error_message())
         msg = lib.mpi_last_error_message()
         assert msg and why in msg, (what, msg)
+
+
+def test_header_is_plain_c_and_links_from_c(tmp_path):
+    """include/mpi_recon.h is self-contained C99 (and C++17), and a plain C
+    program links against the library and calls it (no GPU needed for
+    mpi_version / mpi_status_string)."""
+    import shutil
+    import subprocess
+    cc, cxx = shutil.which("gcc"), shutil.which("g++")
+    if not cc or not cxx:
+        pytest.skip("gcc/g++ not available")
+    from paper_2505_22797_gb300 import build
+    lib = build.build()
+    hdr = os.path.join(ROOT, "include", "mpi_recon.h")
+    for comp, std, lang in ((cc, "-std=c99", "c"), (cxx, "-std=c++17", "c++")):
+        res = subprocess.run([comp, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                              "-x", lang, hdr], capture_output=True, text=True)
+        assert res.returncode == 0, res.stderr
+    src = tmp_path / "main.c"
+    src.write_text('#include <string.h>\n#include "mpi_recon.h"\n'
+                   'int main(void) { return (mpi_version() >= 100 && '
+                   'strcmp(mpi_status_string(MPI_ERR_INVALID), "invalid argument") == 0) ? 0 : 1; }\n')
+    exe = tmp_path / "main"
+    libdir = os.path.dirname(lib)
+    res = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir,
+                          "-l:" + os.path.basename(lib), "-Wl,-rpath," + libdir, "-o", str(exe)],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
