@@ -233,3 +233,27 @@ def test_gaussian5_3d_vs_scipy(orc, shape):
     x = np.random.default_rng(2).normal(size=shape)
     want = ndi.gaussian_filter(x, sigma=1.0, truncate=2.0, mode="reflect")
     assert np.allclose(orc.gaussian5_3d(x), want, rtol=1e-13, atol=1e-14)
+
+
+def test_trace_kernel_of_a_traceless_gradient_has_almost_no_mean(orc):
+    """tr(K(y) G) = a tr G + d y^T G y: for a scalar gradient the sampled trace
+    kernel is positive; for the physical, traceless FFP gradient
+    g diag(-1/2, -1/2, 1) only d y^T G y remains, which changes sign and sums
+    to almost nothing.  beta tr K(beta G y) (the kernel of the
+    gradient-weighted trace sum_k A_kk / G_kk) stays positive."""
+    grid = {"nx": 12, "ny": 12, "nz": 6, "x0": -6.0, "y0": -6.0, "z0": -3.0, "dx": 1.0, "dy": 1.0, "dz": 1.0}
+    g = 2.5e-3
+    iso = {"beta": 2331.35, "G": (g * np.eye(3)).tolist(), "p": np.eye(3).tolist()}
+    tl = {"beta": 2331.35, "G": np.diag([-g / 2, -g / 2, g]).tolist(), "p": np.eye(3).tolist()}
+    k_iso = orc.conv_kernel3(iso, grid)
+    k_tl = orc.conv_kernel3(tl, grid)
+    assert k_iso.min() > 0.0
+    assert k_tl.min() < 0.0 < k_tl.max()
+    assert abs(k_tl.sum()) < 0.05 * np.abs(k_tl).sum()
+    # beta tr K(beta G y) on the same offsets: positive
+    nz, ny, nx = 6, 12, 12
+    off = np.stack(np.meshgrid(np.arange(2 * nx - 1) - (nx - 1.0), np.arange(2 * ny - 1) - (ny - 1.0),
+                               np.arange(2 * nz - 1) - (nz - 1.0), indexing="xy"), -1).reshape(-1, 3)
+    y = tl["beta"] * off @ np.asarray(tl["G"]).T
+    K = orc.kernel_matrix3(y).reshape(-1, 3, 3)
+    assert np.trace(K, axis1=1, axis2=2).min() > 0.0
