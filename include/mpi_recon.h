@@ -203,7 +203,11 @@ typedef struct {
  * FP64.  With rel_tol > 0 the host polls the device-side stop flag every 16
  * CG steps (a stream synchronisation); the result is the same as stopping at
  * the first step that meets the tolerance.  If n_iter_out (HOST) is not NULL
- * the call synchronises the stream and stores the number of CG updates. */
+ * the call synchronises the stream and stores the number of CG updates.
+ * Lap is the bare stencil (no 1/h^2), so gamma is in stencil units: to
+ * regularise with the continuous Laplacian (stencil / h^2) on a grid of
+ * spacing h = dx = dy, pass gamma / h^4; that keeps one gamma valid across
+ * grid sizes. */
 int mpi_grid(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
              const void *s, const mpi_grid_opts *opts, void *Ahat, void *trace,
              int *n_iter_out, void *stream);
@@ -338,7 +342,8 @@ int mpi_interp3_adjoint(const mpi_grid3_desc *grid, const mpi_traj *traj, mpi_dt
  * A_00 + A_11 + A_22) or k + 1 (only channel k = 0, 1, 2 measured: s [1][T],
  * Ahat holds the row (A_k0, A_k1, A_k2) as [3][nz][ny][nx], trace = A_kk).
  * Operator in the call's dtype, CG vectors and inner products FP64; the stop
- * test, polling and n_iter_out behave as in mpi_grid. */
+ * test, polling, n_iter_out and the units of gamma (bare 7-point stencil)
+ * behave as in mpi_grid. */
 int mpi_grid3(const mpi_grid3_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
               const void *s, const mpi_grid_opts *opts, void *Ahat, void *trace,
               int *n_iter_out, void *stream);
