@@ -368,13 +368,26 @@ def measure_paper_pipeline(api, syn, dev, stream):
             return it, api.mpi_pnp_solve(m, g, None, None, a00.contiguous(), 10, 20, nu_c00,
                                          op=api.MPI_OP_CONV, kernel_component=0)
 
+        # the same pipeline with the continuous Laplacian (stencil / h^2, h in
+        # mm): the bare stencil's gamma becomes gamma / h^4
+        h = g["dx"]
+
+        def two_stage_scaled():
+            _, u, it = api.mpi_grid(g, r, v, s, gamma=1e-7 / h ** 4, max_iter=10000, rel_tol=1e-3,
+                                    return_iters=True)
+            return it, api.mpi_pnp_solve(m, g, None, None, u.contiguous(), 10, 20, nu_c,
+                                         op=api.MPI_OP_CONV)
+
         t2, (it2, rho2) = timed(two_stage)
         td, rhod = timed(direct)
         t1, (it1, rho1) = timed(single_x)
+        t3, (it3, rho3) = timed(two_stage_scaled)
         out[f"{n}x{n}"] = {
             "s": t2, "core_stage_cg_steps": it2, "rel_err_vs_phantom": err(rho2),
             "direct_A_pnp": {"s": td, "rel_err_vs_phantom": err(rhod)},
             "single_channel_x": {"s": t1, "core_stage_cg_steps": it1, "rel_err_vs_phantom": err(rho1)},
+            "two_stage_scaled_laplacian": {"s": t3, "gamma": 1e-7 / h ** 4, "core_stage_cg_steps": it3,
+                                           "rel_err_vs_phantom": err(rho3)},
             "paper_cpu_s": paper[n][0], "paper_rtx_a6000_s": paper[n][1]}
     return out
 
