@@ -735,3 +735,81 @@ void og_laplacian3(const og_grid3 *g, const double *f, double *out)
 #undef OG_AT
             }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Grid-scaled forms (the continuous reading of Eq. first:step's regulariser
+ * and of the deconvolution kernel).
+ *
+ * The Laplacian of a function sampled on the nodes, replicated boundary:
+ *   (f(i-1) - 2 f(i) + f(i+1)) / dx^2 + (f(j-1) - 2 f(j) + f(j+1)) / dy^2
+ * (and / dz^2 in three dimensions); with dx = dy = h it is the stencil of
+ * og_laplacian divided by h^2. */
+void og_laplacian_h(const og_grid *g, const double *f, double *out)
+{
+    int nx = g->nx, ny = g->ny;
+    double cx = 1.0 / (g->dx * g->dx), cy = 1.0 / (g->dy * g->dy);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int im = i > 0 ? i - 1 : 0, ip = i < nx - 1 ? i + 1 : nx - 1;
+            int jm = j > 0 ? j - 1 : 0, jp = j < ny - 1 ? j + 1 : ny - 1;
+            double c0 = f[(int64_t)j * nx + i];
+            out[(int64_t)j * nx + i] =
+                cx * (f[(int64_t)j * nx + im] - 2.0 * c0 + f[(int64_t)j * nx + ip]) +
+                cy * (f[(int64_t)jm * nx + i] - 2.0 * c0 + f[(int64_t)jp * nx + i]);
+        }
+}
+
+void og_laplacian3_h(const og_grid3 *g, const double *f, double *out)
+{
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    double cx = 1.0 / (g->dx * g->dx), cy = 1.0 / (g->dy * g->dy), cz = 1.0 / (g->dz * g->dz);
+    for (int l = 0; l < nz; ++l)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int im = i > 0 ? i - 1 : 0, ip = i < nx - 1 ? i + 1 : nx - 1;
+                int jm = j > 0 ? j - 1 : 0, jp = j < ny - 1 ? j + 1 : ny - 1;
+                int lm = l > 0 ? l - 1 : 0, lp = l < nz - 1 ? l + 1 : nz - 1;
+#define OG_AT(ll, jj, ii) f[((int64_t)(ll) * ny + (jj)) * nx + (ii)]
+                double c0 = OG_AT(l, j, i);
+                out[((int64_t)l * ny + j) * nx + i] = cx * (OG_AT(l, j, im) - 2.0 * c0 + OG_AT(l, j, ip)) +
+                                                      cy * (OG_AT(l, jm, i) - 2.0 * c0 + OG_AT(l, jp, i)) +
+                                                      cz * (OG_AT(lm, j, i) - 2.0 * c0 + OG_AT(lp, j, i));
+#undef OG_AT
+            }
+}
+
+/* The kernel of the gradient-weighted trace tr(Ahat G^-1): since
+ * Ahat = beta K(beta G .) G * c, tr(Ahat G^-1) = (beta tr K(beta G y)) * c,
+ * sampled on all voxel offsets like og_conv_kernel.  tr K = L' + (n-1) L/z
+ * is positive, whatever the signs of G. */
+void og_conv_kernel_trK(const og_model *m, const og_grid *g, double *kern)
+{
+    og_init_series();
+    int KX = 2 * g->nx - 1, KY = 2 * g->ny - 1;
+    for (int jj = 0; jj < KY; ++jj)
+        for (int ii = 0; ii < KX; ++ii) {
+            double off[2] = {(ii - (g->nx - 1)) * g->dx, (jj - (g->ny - 1)) * g->dy};
+            double y[2] = {m->beta * (m->G[0] * off[0] + m->G[1] * off[1]),
+                           m->beta * (m->G[2] * off[0] + m->G[3] * off[1])};
+            double K[4];
+            og_K(y, K);
+            kern[(int64_t)jj * KX + ii] = m->beta * (K[0] + K[3]);
+        }
+}
+
+void og_conv_kernel3_trK(const og_model3 *m, const og_grid3 *g, double *kern)
+{
+    og_init_series();
+    int KX = 2 * g->nx - 1, KY = 2 * g->ny - 1, KZ = 2 * g->nz - 1;
+    for (int ll = 0; ll < KZ; ++ll)
+        for (int jj = 0; jj < KY; ++jj)
+            for (int ii = 0; ii < KX; ++ii) {
+                double off[3] = {(ii - (g->nx - 1)) * g->dx, (jj - (g->ny - 1)) * g->dy,
+                                 (ll - (g->nz - 1)) * g->dz};
+                double H[3], K[9];
+                og_matvec3(m->G, off, H);
+                double y[3] = {m->beta * H[0], m->beta * H[1], m->beta * H[2]};
+                og_K3(y, K);
+                kern[((int64_t)ll * KY + jj) * KX + ii] = m->beta * (K[0] + K[4] + K[8]);
+            }
+}

@@ -19,6 +19,9 @@ Parity status per function (what pins each one lives in tests/test_oracle_*):
   kernel_matrix3, pair3, forward3, adjoint3, frob2_3, conv_kernel3, conv3,
   gaussian5_3d (three-dimensional FFP): pinned.
   interp3, interp3_T, laplacian3, core_stage3 (Core Stage with n = 3): pinned.
+  laplacian_h, laplacian3_h, conv_kernel_trK, conv_kernel3_trK,
+  weighted_trace, weighted_trace3 (grid-scaled regulariser, gradient-weighted
+  trace and its kernel): pinned.
   transfer_correct (DFT division by the transfer function, SNR
   thresholding): pinned.
   pnp: pinned step by step (identity-operator closed form, Algorithm 1
@@ -117,6 +120,10 @@ def _load():
             lib.og_interp3.argtypes = [P(_Grid3), ctypes.c_int, _I64, _D, _D, _D, _D]
             lib.og_interp3_T.argtypes = [P(_Grid3), ctypes.c_int, _I64, _D, _D, _D, _D]
             lib.og_laplacian3.argtypes = [P(_Grid3), _D, _D]
+            lib.og_laplacian_h.argtypes = [P(_Grid), _D, _D]
+            lib.og_laplacian3_h.argtypes = [P(_Grid3), _D, _D]
+            lib.og_conv_kernel_trK.argtypes = [P(_Model), P(_Grid), _D]
+            lib.og_conv_kernel3_trK.argtypes = [P(_Model3), P(_Grid3), _D]
             _lib = lib
     return _lib
 
@@ -279,6 +286,31 @@ def laplacian(grid, f) -> np.ndarray:
     return out
 
 
+def laplacian_h(grid, f) -> np.ndarray:
+    """The Laplacian of the function sampled on the nodes (replicated
+    boundary): the 5-point stencil with 1/dx^2 and 1/dy^2 (the continuous
+    reading of the Core Stage regulariser)."""
+    f = _f64(f)
+    out = np.empty_like(f)
+    _load().og_laplacian_h(ctypes.byref(_grid(grid)), _ptr(f), _ptr(out))
+    return out
+
+
+def conv_kernel_trK(model, grid) -> np.ndarray:
+    """beta tr K(beta G y) on all voxel offsets: the kernel of the
+    gradient-weighted trace tr(Ahat G^-1) (positive for any G)."""
+    out = np.empty((2 * int(grid["ny"]) - 1, 2 * int(grid["nx"]) - 1))
+    _load().og_conv_kernel_trK(ctypes.byref(_model(model)), ctypes.byref(_grid(grid)), _ptr(out))
+    return out
+
+
+def weighted_trace(model, Ahat) -> np.ndarray:
+    """tr(Ahat G^-1) per node from the 4 Core Stage components (index 2k+m)."""
+    Gi = np.linalg.inv(np.asarray(model["G"], dtype=np.float64).reshape(2, 2))
+    A = _f64(Ahat)
+    return sum(A[2 * k + m] * Gi[m, k] for k in range(2) for m in range(2))
+
+
 def conv_kernel(model, grid, component=None) -> np.ndarray:
     """kappa_G(y) = beta tr(K(beta G y) G) on all voxel offsets, or, with
     component = (a, b), the entry beta (K(beta G y) G)_ab (the single-channel
@@ -436,7 +468,15 @@ def pnp(op, opT, data, shape, n_it, n_cg, nu0, clip_pct=5.0, denoise=None,
     return rho2
 
 
-def core_stage_channel(grid, r, v, s_k, k, gamma, max_iter, rel_tol=None):
+def _lap_fn(kind, lap, lap_h):
+    if kind == "bare":
+        return lap
+    if kind == "scaled":
+        return lap_h
+    raise ValueError(f"unknown Laplacian {kind!r}")
+
+
+def core_stage_channel(grid, r, v, s_k, k, gamma, max_iter, rel_tol=None, lap="bare"):
     """Core Stage with only receive channel k measured (Sec. 3.6):
         s_k(t) = I[A_k0](r_t) v_x(t) + I[A_k1](r_t) v_y(t),
     the two components (A_k0, A_k1) solved as in Eq. first:step with the
@@ -460,8 +500,10 @@ def core_stage_channel(grid, r, v, s_k, k, gamma, max_iter, rel_tol=None):
         s2[k] = y
         return interp_T(grid, r, v, s2)[2 * k:2 * k + 2]
 
+    L = _lap_fn(lap, laplacian, laplacian_h)
+
     def lap2(x):
-        return np.stack([laplacian(grid, x[m]) for m in range(2)])
+        return np.stack([L(grid, x[m]) for m in range(2)])
 
     def apply(x):
         return MT(M(x)) / T + gamma * lap2(lap2(x))
@@ -471,18 +513,21 @@ def core_stage_channel(grid, r, v, s_k, k, gamma, max_iter, rel_tol=None):
     return x, x[k], hist
 
 
-def core_stage(grid, r, v, s, gamma, max_iter, rel_tol=None):
+def core_stage(grid, r, v, s, gamma, max_iter, rel_tol=None, lap="bare"):
     """Core Stage (Eq. first:step): CG on the Euler-Lagrange equations
         ((1/L) M^T M + gamma Lap^T Lap) Ahat = (1/L) M^T s,   L = T,
     with M the cosine-interpolation measurement operator and Lap the
     replicated-boundary 5-point Laplacian on each of the 4 components (it is
-    symmetric, so Lap^T Lap = Lap Lap).  Starts from 0.  Returns (Ahat
+    symmetric, so Lap^T Lap = Lap Lap; lap="scaled": with 1/dx^2, 1/dy^2).
+    Starts from 0.  Returns (Ahat
     [4, ny, nx], trace u = Ahat_00 + Ahat_11, residual history)."""
     T = r.shape[0]
     ny, nx = int(grid["ny"]), int(grid["nx"])
 
+    L = _lap_fn(lap, laplacian, laplacian_h)
+
     def lap4(x):
-        return np.stack([laplacian(grid, x[m]) for m in range(4)])
+        return np.stack([L(grid, x[m]) for m in range(4)])
 
     def apply(x):
         return interp_T(grid, r, v, interp(grid, r, v, x)) / T + gamma * lap4(lap4(x))
@@ -625,7 +670,32 @@ def laplacian3(grid3, f) -> np.ndarray:
     return out
 
 
-def core_stage3(grid3, r, v, s, gamma, max_iter, rel_tol=None, channel=None):
+def laplacian3_h(grid3, f) -> np.ndarray:
+    """The 7-point Laplacian with 1/dx^2, 1/dy^2, 1/dz^2 (replicated boundary)."""
+    f = _f64(f)
+    out = np.empty_like(f)
+    _load().og_laplacian3_h(ctypes.byref(_grid3(grid3)), _ptr(f), _ptr(out))
+    return out
+
+
+def conv_kernel3_trK(model3, grid3) -> np.ndarray:
+    """beta tr K(beta G y) on all voxel offsets in three dimensions: the kernel
+    of tr(Ahat G^-1), positive for any G (the trace kernel of a traceless G
+    is not)."""
+    shape = tuple(2 * int(grid3[k]) - 1 for k in ("nz", "ny", "nx"))
+    out = np.empty(shape)
+    _load().og_conv_kernel3_trK(ctypes.byref(_model3(model3)), ctypes.byref(_grid3(grid3)), _ptr(out))
+    return out
+
+
+def weighted_trace3(model3, Ahat) -> np.ndarray:
+    """tr(Ahat G^-1) per node from the 9 Core Stage components (index 3k+m)."""
+    Gi = np.linalg.inv(np.asarray(model3["G"], dtype=np.float64).reshape(3, 3))
+    A = _f64(Ahat)
+    return sum(A[3 * k + m] * Gi[m, k] for k in range(3) for m in range(3))
+
+
+def core_stage3(grid3, r, v, s, gamma, max_iter, rel_tol=None, channel=None, lap="bare"):
     """Core Stage in three dimensions (Eq. first:step with n = 3): CG from 0 on
         ((1/T) M^T M + gamma Lap Lap) Ahat = (1/T) M^T s
     for the 9 components Ahat_km (3 channels x 3 velocity components), Lap the
@@ -639,8 +709,10 @@ def core_stage3(grid3, r, v, s, gamma, max_iter, rel_tol=None, channel=None):
     s = _f64(s).reshape(-1, T)
     nc = 9 if channel is None else 3
 
+    L = _lap_fn(lap, laplacian3, laplacian3_h)
+
     def lapn(x):
-        return np.stack([laplacian3(grid3, x[m]) for m in range(nc)])
+        return np.stack([L(grid3, x[m]) for m in range(nc)])
 
     def apply(x):
         return interp3_T(grid3, r, v, interp3(grid3, r, v, x)) / T + gamma * lapn(lapn(x))
