@@ -189,6 +189,9 @@ typedef struct {
     double rel_tol;  /* stop when ||r|| <= rel_tol ||b|| (paper: 1e-3); <= 0: run max_iter */
     int channel;     /* 0: both channels measured; 1 or 2: only channel x (k = 0) or
                         y (k = 1) measured, the partial-data setting of Sec. 3.6 */
+    int lap_scaled;  /* 0: Lap is the bare stencil (gamma in stencil units); 1: the
+                        Laplacian with 1/dx^2, 1/dy^2 (and 1/dz^2 in mpi_grid3) per axis,
+                        which keeps one gamma valid across grid sizes */
 } mpi_grid_opts;
 
 /* Solves ((1/T) M^T M + gamma Lap^T Lap) Ahat = (1/T) M^T s by CG from
@@ -204,10 +207,9 @@ typedef struct {
  * CG steps (a stream synchronisation); the result is the same as stopping at
  * the first step that meets the tolerance.  If n_iter_out (HOST) is not NULL
  * the call synchronises the stream and stores the number of CG updates.
- * Lap is the bare stencil (no 1/h^2), so gamma is in stencil units: to
- * regularise with the continuous Laplacian (stencil / h^2) on a grid of
- * spacing h = dx = dy, pass gamma / h^4; that keeps one gamma valid across
- * grid sizes. */
+ * With opts->lap_scaled = 0, Lap is the bare stencil (no 1/h^2), so gamma is
+ * in stencil units (on a grid of spacing h = dx = dy, gamma / h^4 there equals
+ * gamma with lap_scaled = 1, up to rounding). */
 int mpi_grid(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
              const void *s, const mpi_grid_opts *opts, void *Ahat, void *trace,
              int *n_iter_out, void *stream);

@@ -60,7 +60,7 @@ class Traj(ctypes.Structure):
 class GridOpts(ctypes.Structure):
     """mpi_grid_opts: gamma, CG iteration limit, relative tolerance, channel selector."""
     _fields_ = [("gamma", ctypes.c_double), ("max_iter", ctypes.c_int), ("rel_tol", ctypes.c_double),
-                ("channel", ctypes.c_int)]
+                ("channel", ctypes.c_int), ("lap_scaled", ctypes.c_int)]
 
 
 class PnPOpts(ctypes.Structure):
@@ -387,10 +387,11 @@ def mpi_interp_adjoint(grid, r, v, s, Ahat=None, stream=None):
 
 
 def mpi_grid(grid, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=None, trace=None,
-             return_iters=False, channel=None, stream=None):
+             return_iters=False, channel=None, lap_scaled=False, stream=None):
     """Core Stage.  ``channel`` None: s is [2][T] and Ahat [4][ny][nx];
     channel k (0 or 1): only that channel was measured, s is [T] (or [1][T])
-    and Ahat holds (A_k0, A_k1), trace = A_kk."""
+    and Ahat holds (A_k0, A_k1), trace = A_kk.  ``lap_scaled``: regularise
+    with the Laplacian scaled by 1/dx^2, 1/dy^2 instead of the bare stencil."""
     dt = s.dtype
     g = make_grid(grid)
     nc = 4 if channel is None else 2
@@ -400,7 +401,7 @@ def mpi_grid(grid, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=None,
         trace = torch.empty((g.ny, g.nx), dtype=dt, device=s.device)
     tr = _traj(r, v, dt)
     opts = GridOpts(float(gamma), int(max_iter), float(rel_tol),
-                    0 if channel is None else int(channel) + 1)
+                    0 if channel is None else int(channel) + 1, 1 if lap_scaled else 0)
     n_it = ctypes.c_int(-1)
     _check(load().mpi_grid(ctypes.byref(g), ctypes.byref(tr), _dtype(s),
                            _dev(s, dt, "s") if s.numel() else None, ctypes.byref(opts),
@@ -604,11 +605,12 @@ def mpi_interp3_adjoint(grid3, r, v, s, Ahat=None, stream=None):
 
 
 def mpi_grid3(grid3, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=None, trace=None,
-              return_iters=False, channel=None, stream=None):
+              return_iters=False, channel=None, lap_scaled=False, stream=None):
     """Core Stage in three dimensions.  ``channel`` None: s is [3][T] and
     Ahat [9][nz][ny][nx], trace = A_00 + A_11 + A_22; channel k (0, 1 or 2):
     only that channel was measured, s is [T] (or [1][T]), Ahat holds the row
-    (A_k0, A_k1, A_k2) and trace = A_kk."""
+    (A_k0, A_k1, A_k2) and trace = A_kk.  ``lap_scaled``: the Laplacian with
+    1/dx^2, 1/dy^2, 1/dz^2 instead of the bare stencil."""
     dt = s.dtype
     g = make_grid3(grid3)
     nc = 9 if channel is None else 3
@@ -618,7 +620,7 @@ def mpi_grid3(grid3, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=Non
         trace = torch.empty((g.nz, g.ny, g.nx), dtype=dt, device=s.device)
     tr = _traj(r, v, dt, 3)
     opts = GridOpts(float(gamma), int(max_iter), float(rel_tol),
-                    0 if channel is None else int(channel) + 1)
+                    0 if channel is None else int(channel) + 1, 1 if lap_scaled else 0)
     n_it = ctypes.c_int(-1)
     _check(load().mpi_grid3(ctypes.byref(g), ctypes.byref(tr), _dtype(s),
                             _dev(s, dt, "s") if s.numel() else None, ctypes.byref(opts),

@@ -206,7 +206,9 @@ k_interp3_T_units(const InterpRec3<R> *__restrict__ rec, const R *__restrict__ v
 }
 
 // out_m = Lap x_m (7-point, replicated boundary) for the nc components, FP64.
-__global__ void k_lap3(int nx, int ny, int nz, int nc, const double *__restrict__ x, double *__restrict__ out)
+// scaled: per-axis second differences with 1/dx^2, 1/dy^2, 1/dz^2 (c).
+__global__ void k_lap3(int nx, int ny, int nz, int nc, bool scaled, double3 c, const double *__restrict__ x,
+                       double *__restrict__ out)
 {
     const int64_t N = (int64_t)nx * ny * nz;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * N;
@@ -218,7 +220,13 @@ __global__ void k_lap3(int nx, int ny, int nz, int nc, const double *__restrict_
         const int64_t xm = i > 0 ? -sx : 0, xp = i < nx - 1 ? sx : 0;
         const int64_t ym = j > 0 ? -sy : 0, yp = j < ny - 1 ? sy : 0;
         const int64_t zm = l > 0 ? -sz : 0, zp = l < nz - 1 ? sz : 0;
-        out[e] = f[k + xm] + f[k + xp] + f[k + ym] + f[k + yp] + f[k + zm] + f[k + zp] - 6.0 * f[k];
+        if (scaled) {
+            const double c0 = f[k];
+            out[e] = c.x * (f[k + xm] - 2.0 * c0 + f[k + xp]) + c.y * (f[k + ym] - 2.0 * c0 + f[k + yp]) +
+                     c.z * (f[k + zm] - 2.0 * c0 + f[k + zp]);
+        } else {
+            out[e] = f[k + xm] + f[k + xp] + f[k + ym] + f[k + yp] + f[k + zm] + f[k + zp] - 6.0 * f[k];
+        }
     }
 }
 
@@ -380,9 +388,10 @@ struct GridOp3 final : CoreStageOp {
     const Bins3 &bins;
     R *s_tmp;
     double invT;
-    GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_)
+    bool scaled;
+    GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_, bool scaled_)
         : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 9 : 3), bins(b_), s_tmp(s_tmp_),
-          invT(T_ > 0 ? 1.0 / double(T_) : 0.0) {}
+          invT(T_ > 0 ? 1.0 / double(T_) : 0.0), scaled(scaled_) {}
     int normal(const double *p, double *y, cudaStream_t st) override
     {
         MPI_TRY((launch_interp3<R, double>(g, T, nullptr, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
@@ -391,7 +400,8 @@ struct GridOp3 final : CoreStageOp {
     }
     int lap(const double *x, double *out, cudaStream_t st) override
     {
-        k_lap3<<<grid_blocks(nc * g.n()), 256, 0, st>>>(g.nx, g.ny, g.nz, nc, x, out);
+        const double3 c = make_double3(1.0 / (g.dx * g.dx), 1.0 / (g.dy * g.dy), 1.0 / (g.dz * g.dz));
+        k_lap3<<<grid_blocks(nc * g.n()), 256, 0, st>>>(g.nx, g.ny, g.nz, nc, scaled, c, x, out);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }
@@ -420,7 +430,7 @@ int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid
 
     MPI_TRY(build_bins3<R>(g, T, r, v, bins, st));
     MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
-    GridOp3<R> op(g, T, ch, bins, scr.at<R>(o_s));
+    GridOp3<R> op(g, T, ch, bins, scr.at<R>(o_s), o.lap_scaled != 0);
     MPI_TRY((launch_interp3_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
     MPI_TRY(core_stage_cg(op, nv, b, o, x, n_iter_out, st));
     k_grid3_output<R><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
@@ -503,7 +513,8 @@ int mpi_grid3(const mpi_grid3_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
 {
     MPI_TRY(check_interp3_args(grid, traj, dtype));
     if (!opts || !(opts->gamma >= 0.0) || !std::isfinite(opts->gamma) || opts->max_iter < 0 ||
-        std::isnan(opts->rel_tol) || opts->channel < 0 || opts->channel > 3) {
+        std::isnan(opts->rel_tol) || opts->channel < 0 || opts->channel > 3 || opts->lap_scaled < 0 ||
+        opts->lap_scaled > 1) {
         set_error("invalid Core Stage options");
         return MPI_ERR_INVALID;
     }

@@ -419,7 +419,9 @@ static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const B
 // --- Laplacian and the Core Stage operator ---------------------------------
 
 // out_m = Lap x_m for the nc components (replicated boundary), FP64.
-__global__ void k_lap(int nx, int ny, int nc, const double *__restrict__ x, double *__restrict__ out)
+// scaled: per-axis second differences with 1/dx^2 (cx) and 1/dy^2 (cy).
+__global__ void k_lap(int nx, int ny, int nc, bool scaled, double cx, double cy, const double *__restrict__ x,
+                      double *__restrict__ out)
 {
     const int64_t N = (int64_t)nx * ny;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * N;
@@ -429,8 +431,14 @@ __global__ void k_lap(int nx, int ny, int nc, const double *__restrict__ x, doub
         const double *f = x + m * N;
         const int im = i > 0 ? i - 1 : 0, ip = i < nx - 1 ? i + 1 : nx - 1;
         const int jm = j > 0 ? j - 1 : 0, jp = j < ny - 1 ? j + 1 : ny - 1;
-        out[e] = f[(int64_t)j * nx + im] + f[(int64_t)j * nx + ip] + f[(int64_t)jm * nx + i] +
-                 f[(int64_t)jp * nx + i] - 4.0 * f[k];
+        if (scaled) {
+            const double c0 = f[k];
+            out[e] = cx * (f[(int64_t)j * nx + im] - 2.0 * c0 + f[(int64_t)j * nx + ip]) +
+                     cy * (f[(int64_t)jm * nx + i] - 2.0 * c0 + f[(int64_t)jp * nx + i]);
+        } else {
+            out[e] = f[(int64_t)j * nx + im] + f[(int64_t)j * nx + ip] + f[(int64_t)jm * nx + i] +
+                     f[(int64_t)jp * nx + i] - 4.0 * f[k];
+        }
     }
 }
 
@@ -486,9 +494,10 @@ struct GridOp2 final : CoreStageOp {
     const Bins &bins;
     R *s_tmp;
     double invT;
-    GridOp2(const GridH &g_, int64_t T_, int ch_, const Bins &b_, R *s_tmp_)
+    bool scaled;
+    GridOp2(const GridH &g_, int64_t T_, int ch_, const Bins &b_, R *s_tmp_, bool scaled_)
         : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 4 : 2), bins(b_), s_tmp(s_tmp_),
-          invT(T_ > 0 ? 1.0 / double(T_) : 0.0) {}
+          invT(T_ > 0 ? 1.0 / double(T_) : 0.0), scaled(scaled_) {}
     int normal(const double *p, double *y, cudaStream_t st) override
     {
         MPI_TRY((launch_interp<R, double>(g, T, nullptr, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
@@ -497,7 +506,8 @@ struct GridOp2 final : CoreStageOp {
     }
     int lap(const double *x, double *out, cudaStream_t st) override
     {
-        k_lap<<<grid_blocks(int64_t(nc) * g.nx * g.ny), 256, 0, st>>>(g.nx, g.ny, nc, x, out);
+        k_lap<<<grid_blocks(int64_t(nc) * g.nx * g.ny), 256, 0, st>>>(g.nx, g.ny, nc, scaled, 1.0 / (g.dx * g.dx),
+                                                                       1.0 / (g.dy * g.dy), x, out);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }
@@ -527,7 +537,7 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     MPI_TRY(build_bins<R>(g, T, r, v, bins, st));
     // The sample vectors of the solve live in list (cell) order.
     MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
-    GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_s));
+    GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_s), o.lap_scaled != 0);
     // b = (1/T) M^T s
     MPI_TRY((launch_interp_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
     MPI_TRY(core_stage_cg(op, n4, b, o, x, n_iter_out, st));
@@ -689,7 +699,8 @@ int mpi_grid(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype, c
 {
     MPI_TRY(check_interp_args(grid, traj, dtype));
     if (!opts || !(opts->gamma >= 0.0) || !std::isfinite(opts->gamma) || opts->max_iter < 0 ||
-        std::isnan(opts->rel_tol) || opts->channel < 0 || opts->channel > 2) {
+        std::isnan(opts->rel_tol) || opts->channel < 0 || opts->channel > 2 || opts->lap_scaled < 0 ||
+        opts->lap_scaled > 1) {
         set_error("invalid Core Stage options");
         return MPI_ERR_INVALID;
     }

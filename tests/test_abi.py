@@ -92,7 +92,7 @@ class _Grid3(ctypes.Structure):
 
 class _GridOpts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("max_iter", ctypes.c_int), ("rel_tol", ctypes.c_double),
-                ("channel", ctypes.c_int)]
+                ("channel", ctypes.c_int), ("lap_scaled", ctypes.c_int)]
 
 
 def test_core_stage_argument_validation_without_gpu(lib):
@@ -127,6 +127,7 @@ def test_core_stage_argument_validation_without_gpu(lib):
         ("mpi_grid3", g3, tr0, 0, _GridOpts(1e-7, 10, 1e-3, 4), True, -1, b"options"),
         ("mpi_grid3", g3, tr0, 0, _GridOpts(-1.0, 10, 1e-3, 0), True, -1, b"options"),
         ("mpi_grid3", g3, tr0, 0, _GridOpts(1e-7, -1, 1e-3, 0), True, -1, b"options"),
+        ("mpi_grid3", g3, tr0, 0, _GridOpts(1e-7, 10, 1e-3, 0, 2), True, -1, b"options"),
         ("mpi_grid3", g3, tr0, 0, None, True, -1, b"options"),
         ("mpi_grid3", g3, tr0, 0, opts, False, -1, b"NULL"),
         ("mpi_interp3", g3, _Traj(8, None, None), 0, None, True, -1, b"NULL"),
@@ -139,6 +140,9 @@ def test_core_stage_argument_validation_without_gpu(lib):
     # the 2-D Core Stage: channel selector 0..2 only
     st = lib.mpi_grid(ctypes.byref(g2), ctypes.byref(tr0), 0, None,
                       ctypes.byref(_GridOpts(1e-7, 10, 1e-3, 3)), buf, buf, None, None)
+    assert st == -1 and b"options" in lib.mpi_last_error_message()
+    st = lib.mpi_grid(ctypes.byref(g2), ctypes.byref(tr0), 0, None,
+                      ctypes.byref(_GridOpts(1e-7, 10, 1e-3, 0, -1)), buf, buf, None, None)
     assert st == -1 and b"options" in lib.mpi_last_error_message()
 
 

@@ -130,3 +130,21 @@ def test_core_stage_channel_rejects_bad_selector():
     s = torch.zeros(3, dtype=torch.float64, device="cuda")
     with pytest.raises(api.MPIError):
         api.mpi_grid(g, r, r, s, max_iter=1, channel=2)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_core_stage_scaled_laplacian(orc, dt):
+    """lap_scaled: the regulariser is the Laplacian with 1/dx^2, 1/dy^2 (an
+    anisotropic grid here); fixed CG steps against the oracle's scaled Core
+    Stage."""
+    cfg = syn.small(20, 14, 2000, seed=6)
+    g, m = cfg["grid"], cfg["model"]
+    assert g["dx"] != g["dy"]
+    r, v, c = (rounded(cfg[k], dt) for k in ("r", "v", "c"))
+    s = rounded(orc.forward(m, g, r, v, c), dt)
+    want, want_u, hist = orc.core_stage(g, r, v, s, 1e-3, max_iter=30, lap="scaled")
+    A, u, n = api.mpi_grid(g, dev(r, dt), dev(v, dt), dev(s, dt), gamma=1e-3, max_iter=30, rel_tol=0.0,
+                           return_iters=True, lap_scaled=True)
+    assert n == len(hist) - 1
+    assert rel_l2(host(A), want) <= tol(dt)
+    assert rel_l2(host(u), want_u) <= tol(dt)

@@ -160,3 +160,19 @@ def test_core_stage3_rejects_bad_arguments():
         api.mpi_grid3(g, r, r, torch.zeros((3, 3), dtype=torch.float64, device="cuda"), gamma=-1.0)
     with pytest.raises(api.MPIError):
         api.mpi_interp3({**g, "dz": 0.0}, r, r, torch.zeros((9, 2, 4, 4), dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_core_stage3_scaled_laplacian(orc, dt):
+    """lap_scaled in three dimensions (1/dx^2, 1/dy^2, 1/dz^2 on a grid with
+    dy != dx): fixed CG steps against the oracle's scaled 3-D Core Stage."""
+    cfg = syn.small3(12, 10, 6, 2500, seed=7)
+    g = cfg["grid"]
+    assert g["dy"] != g["dx"]
+    g, r, v, s = _signal3(orc, cfg, dt)
+    want, want_u, hist = orc.core_stage3(g, r, v, s, 1e-3, max_iter=20, lap="scaled")
+    A, u, n = api.mpi_grid3(g, dev(r, dt), dev(v, dt), dev(s, dt), gamma=1e-3, max_iter=20, rel_tol=0.0,
+                            return_iters=True, lap_scaled=True)
+    assert n == len(hist) - 1
+    assert rel_l2(host(A), want) <= tol(dt)
+    assert rel_l2(host(u), want_u) <= tol(dt)
