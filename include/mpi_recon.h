@@ -302,6 +302,22 @@ int mpi_adjoint3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_
 int mpi_conv3(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, const void *in,
               void *out, void *stream);
 
+/* mpi_conv3 with a choice of kernel: 0 = the trace kernel above; 1 =
+ * beta tr K(beta G y), the kernel of the gradient-weighted trace
+ * tr(Ahat G^-1) (mpi_weighted_trace3).  For a traceless G (the physical 3-D
+ * FFP gradient, proportional to diag(-1, -1, 2)) the trace kernel reduces to
+ * beta d(z) y^T G y, which changes sign and has almost no mean; kernel 1 is
+ * positive for any G. */
+int mpi_conv3_kernel(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, int kernel,
+                     const void *in, void *out, void *stream);
+
+/* out[l][j][i] = tr(Ahat G^-1) = sum_{k,m} Ahat[3k+m][l][j][i] (G^-1)_mk for the 9
+ * components of mpi_grid3 (device, dtype of the call; summed in FP64).  Since
+ * Ahat = beta K(beta G .) G * c, this is (beta tr K(beta G y)) * c: the input
+ * of the deconvolution with mpi_conv3_kernel(kernel = 1). */
+int mpi_weighted_trace3(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype,
+                        const void *Ahat, void *out, void *stream);
+
 /* Volume denoiser callback: as mpi_denoise_fn on [nz][ny][nx]. */
 typedef int (*mpi_denoise3_fn)(const void *in, void *out, int nx, int ny, int nz, mpi_dtype dtype,
                                const double *sigma_dev, void *stream, void *user);
@@ -313,8 +329,9 @@ int mpi_denoise_gaussian5_3d(const void *in, void *out, int nx, int ny, int nz, 
 
 /* Algorithm 1 in three dimensions (the loop of mpi_pnp_solve) with the 3-D
  * forward operator (data s[n_ch][T]) or the 3-D convolution (data
- * u[nz][ny][nx]); opts->kernel_component must be 0.  denoise NULL selects
- * mpi_denoise_gaussian5_3d.  rho_out is [nz][ny][nx]. */
+ * u[nz][ny][nx]); opts->kernel_component selects the convolution's kernel as
+ * in mpi_conv3_kernel (0 or 1; 0 with the forward operator).  denoise NULL
+ * selects mpi_denoise_gaussian5_3d.  rho_out is [nz][ny][nx]. */
 int mpi_pnp_solve3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_traj *traj,
                    mpi_dtype dtype, const void *data, const mpi_pnp_opts *opts, mpi_denoise3_fn denoise,
                    void *user, void *rho_out, mpi_pnp_iter_info *info, void *stream);

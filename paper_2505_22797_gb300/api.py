@@ -130,6 +130,8 @@ _SIGS = {
     "mpi_forward3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_adjoint3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_conv3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_conv3_kernel": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 3,
+    "mpi_weighted_trace3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_interp3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_interp3_adjoint": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_grid3": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 6,
@@ -631,6 +633,30 @@ def mpi_grid3(grid3, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=Non
     return Ahat, trace
 
 
+def mpi_conv3_kernel(model3, grid3, kernel, x, out=None, stream=None):
+    """mpi_conv3 with kernel 0 (the trace kernel) or 1 (beta tr K(beta G y),
+    the kernel of the gradient-weighted trace)."""
+    dt = x.dtype
+    if out is None:
+        out = torch.empty_like(x)
+    m, g = make_model3(model3), make_grid3(grid3)
+    _check(load().mpi_conv3_kernel(ctypes.byref(m), ctypes.byref(g), _dtype(x), int(kernel),
+                                   _dev(x, dt, "in"), _dev(out, dt, "out"), _stream(stream)))
+    return out
+
+
+def mpi_weighted_trace3(model3, grid3, Ahat, out=None, stream=None):
+    """tr(Ahat G^-1) per node from the 9 Core Stage components [9, nz, ny, nx]."""
+    dt = Ahat.dtype
+    g = make_grid3(grid3)
+    if out is None:
+        out = torch.empty((g.nz, g.ny, g.nx), dtype=dt, device=Ahat.device)
+    m = make_model3(model3)
+    _check(load().mpi_weighted_trace3(ctypes.byref(m), ctypes.byref(g), _dtype(Ahat), _dev(Ahat, dt, "Ahat"),
+                                      _dev(out, dt, "out"), _stream(stream)))
+    return out
+
+
 def mpi_denoise_gaussian5_3d(x, out=None, stream=None):
     """The built-in volume denoiser: the 5-tap Gaussian along x, y and z
     (reflect boundary) on x [nz, ny, nx]."""
@@ -644,10 +670,11 @@ def mpi_denoise_gaussian5_3d(x, out=None, stream=None):
 
 
 def mpi_pnp_solve3(model3, grid3, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, op=MPI_OP_FORWARD,
-                   denoise=None, rho_out=None, with_info=False, stream=None):
+                   denoise=None, rho_out=None, with_info=False, kernel=0, stream=None):
     """Algorithm 1 in three dimensions.  ``denoise`` is None (built-in volume
     Gaussian) or a callable (in_tensor, out_tensor, sigma_dev_tensor) -> None
-    on [nz, ny, nx] volumes that enqueues on the current stream."""
+    on [nz, ny, nx] volumes that enqueues on the current stream.  ``kernel``
+    (with MPI_OP_CONV): 0 the trace kernel, 1 beta tr K(beta G y)."""
     dt = data.dtype
     g = make_grid3(grid3)
     if rho_out is None:
@@ -657,7 +684,7 @@ def mpi_pnp_solve3(model3, grid3, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, o
     else:
         tr = Traj(0, None, None) if r is None else _traj(r, v, dt, 3)
     m = make_model3(model3)
-    opts = PnPOpts(int(op), int(n_iter), int(n_cg), float(nu0), float(clip_pct), 0)
+    opts = PnPOpts(int(op), int(n_iter), int(n_cg), float(nu0), float(clip_pct), int(kernel))
     info = (PnPIterInfo * max(1, n_iter))() if with_info else None
     cb = DENOISE3_FN(0)
     keep = None

@@ -525,8 +525,11 @@ struct Op3 {
 constexpr int kC3x = 8, kC3y = 8, kC3z = 4;  // output / input tile
 constexpr int kC3Kx = 2 * kC3x - 1, kC3Ky = 2 * kC3y - 1, kC3Kz = 2 * kC3z - 1;
 
-// kappa_G(o) = beta tr(K(beta G o) G) = beta (a tr G + d y^T G y), y = beta G o.
-__global__ void k_conv3_kernel_sample(Grid3H g, double beta, Mat3 G, double *__restrict__ K)
+// kernel 0: kappa_G(o) = beta tr(K(beta G o) G) = beta (a tr G + d y^T G y),
+// y = beta G o (the trace kernel); kernel 1: beta tr K(beta G o) =
+// beta (3 a + d |y|^2), the kernel of the gradient-weighted trace
+// tr(Ahat G^-1) (positive for any G; the trace kernel of a traceless G is not).
+__global__ void k_conv3_kernel_sample(Grid3H g, double beta, Mat3 G, int kernel, double *__restrict__ K)
 {
     const int KX = 2 * g.nx - 1, KY = 2 * g.ny - 1, KZ = 2 * g.nz - 1;
     const int64_t n = (int64_t)KX * KY * KZ;
@@ -539,10 +542,14 @@ __global__ void k_conv3_kernel_sample(Grid3H g, double beta, Mat3 G, double *__r
         for (int q = 0; q < 3; ++q) y[q] = beta * (G.a[3 * q] * o[0] + G.a[3 * q + 1] * o[1] + G.a[3 * q + 2] * o[2]);
         double a, d;
         lang_checked<double, false>(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], a, d);
-        double yGy = 0.0;
-        for (int q = 0; q < 3; ++q)
-            yGy += y[q] * (G.a[3 * q] * y[0] + G.a[3 * q + 1] * y[1] + G.a[3 * q + 2] * y[2]);
-        K[e] = beta * (a * trG + d * yGy);
+        if (kernel == 1) {
+            K[e] = beta * (3.0 * a + d * (y[0] * y[0] + y[1] * y[1] + y[2] * y[2]));
+        } else {
+            double yGy = 0.0;
+            for (int q = 0; q < 3; ++q)
+                yGy += y[q] * (G.a[3 * q] * y[0] + G.a[3 * q + 1] * y[1] + G.a[3 * q + 2] * y[2]);
+            K[e] = beta * (a * trG + d * yGy);
+        }
     }
 }
 
@@ -560,14 +567,15 @@ static size_t conv3_kernel_bytes(const Grid3H &g, int elem)
 }
 
 template <typename R>
-static int conv3_prepare(const Model3H &m, const Grid3H &g, void *scratch, R **K_out, cudaStream_t st)
+static int conv3_prepare(const Model3H &m, const Grid3H &g, int kernel, void *scratch, R **K_out,
+                         cudaStream_t st)
 {
     const int64_t n = (int64_t)(2 * g.nx - 1) * (2 * g.ny - 1) * (2 * g.nz - 1);
     double *K64 = static_cast<double *>(scratch);
     Mat3 G;
     for (int q = 0; q < 9; ++q) G.a[q] = m.G[q];
     const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
-    k_conv3_kernel_sample<<<blocks, 256, 0, st>>>(g, m.beta, G, K64);
+    k_conv3_kernel_sample<<<blocks, 256, 0, st>>>(g, m.beta, G, kernel, K64);
     MPI_CHECK_LAUNCH();
     if constexpr (sizeof(R) == sizeof(double)) {
         *K_out = reinterpret_cast<R *>(K64);
@@ -733,13 +741,14 @@ static int dft3(const Conv3Plan<R> &P, typename Conv3Plan<R>::C2 *a, typename Co
 }
 
 template <typename R>
-static int conv3_plan_prepare(const Model3H &m, const Grid3H &g, void *scratch, Conv3Plan<R> &P, cudaStream_t st)
+static int conv3_plan_prepare(const Model3H &m, const Grid3H &g, int kernel, void *scratch, Conv3Plan<R> &P,
+                              cudaStream_t st)
 {
     using C2 = typename Conv3Plan<R>::C2;
     P.g = g;
     P.fft = conv3_uses_fft(g, sizeof(R));
     R *K = nullptr;
-    MPI_TRY(conv3_prepare<R>(m, g, scratch, &K, st));
+    MPI_TRY(conv3_prepare<R>(m, g, kernel, scratch, &K, st));
     P.K = K;
     if (!P.fft) return MPI_OK;
     P.NX = pow2_at_least(2 * g.nx - 1);
@@ -900,7 +909,7 @@ static int pnp3_impl(const Model3H &m, const Grid3H &g, const mpi_traj *tr, cons
         S.sA = scr.at<R>(o_sA);
         MPI_TRY(S.A.prepare(static_cast<const R *>(tr->r), static_cast<const R *>(tr->v), st));
     } else {
-        MPI_TRY(conv3_plan_prepare<R>(m, g, scr.at<char>(o_K), S.C, st));
+        MPI_TRY(conv3_plan_prepare<R>(m, g, o.kernel_component, scr.at<char>(o_K), S.C, st));
         S.tmp1 = scr.at<R>(o_t1);
         S.tmp2 = scr.at<R>(o_t2);
     }
@@ -998,14 +1007,56 @@ static int adjoint3_impl(const Model3H &m, const Grid3H &g, const mpi_traj *tr, 
 }
 
 template <typename R>
-static int conv3_impl(const Model3H &m, const Grid3H &g, const void *in, void *out, cudaStream_t st)
+static int conv3_impl(const Model3H &m, const Grid3H &g, int kernel, const void *in, void *out, cudaStream_t st)
 {
     Scratch scr(st);
     const size_t o_K = scr.reserve(conv3_plan_bytes(g, sizeof(R)));
     MPI_TRY(scr.allocate());
     Conv3Plan<R> C;
-    MPI_TRY(conv3_plan_prepare<R>(m, g, scr.at<char>(o_K), C, st));
+    MPI_TRY(conv3_plan_prepare<R>(m, g, kernel, scr.at<char>(o_K), C, st));
     return conv3_apply<R, R, R>(C, static_cast<const R *>(in), static_cast<R *>(out), st);
+}
+
+// out = tr(Ahat G^-1) per node: sum_{k,m} Ahat[3k+m] (G^-1)_mk, in FP64.
+template <typename R>
+__global__ void k_weighted_trace3(int64_t N, Mat3 Gi, const R *__restrict__ A, R *__restrict__ out)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc += double(A[(3 * k + q) * N + e]) * Gi.a[3 * q + k];
+        out[e] = R(acc);
+    }
+}
+
+static Mat3 inverse3(const double *G)
+{
+    const double det = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                       G[2] * (G[3] * G[7] - G[4] * G[6]);
+    Mat3 I;
+    I.a[0] = (G[4] * G[8] - G[5] * G[7]) / det;
+    I.a[1] = (G[2] * G[7] - G[1] * G[8]) / det;
+    I.a[2] = (G[1] * G[5] - G[2] * G[4]) / det;
+    I.a[3] = (G[5] * G[6] - G[3] * G[8]) / det;
+    I.a[4] = (G[0] * G[8] - G[2] * G[6]) / det;
+    I.a[5] = (G[2] * G[3] - G[0] * G[5]) / det;
+    I.a[6] = (G[3] * G[7] - G[4] * G[6]) / det;
+    I.a[7] = (G[1] * G[6] - G[0] * G[7]) / det;
+    I.a[8] = (G[0] * G[4] - G[1] * G[3]) / det;
+    return I;
+}
+
+template <typename R>
+static int weighted_trace3_impl(const Model3H &m, const Grid3H &g, const void *A, void *out, cudaStream_t st)
+{
+    const int64_t N = g.n();
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 8192));
+    k_weighted_trace3<R><<<blocks, 256, 0, st>>>(N, inverse3(m.G), static_cast<const R *>(A), static_cast<R *>(out));
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
 }
 
 template <typename R>
@@ -1051,17 +1102,37 @@ int mpi_adjoint3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mpi_
                             : adjoint3_impl<double>(m, g, traj, s, c_out, as_stream(stream));
 }
 
-int mpi_conv3(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, const void *in,
-              void *out, void *stream)
+int mpi_conv3_kernel(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, int kernel,
+                     const void *in, void *out, void *stream)
 {
     MPI_TRY(check_model3(model));
     MPI_TRY(check_grid3(grid));
     MPI_TRY(check_dtype(dtype));
+    if (kernel != 0 && kernel != 1) { set_error("kernel must be 0 or 1 (got %d)", kernel); return MPI_ERR_INVALID; }
     if (!in || !out || in == out) { set_error("in/out NULL or aliased"); return MPI_ERR_INVALID; }
     const Model3H m = to_host3(model);
     const Grid3H g = to_host3(grid);
-    return dtype == MPI_F32 ? conv3_impl<float>(m, g, in, out, as_stream(stream))
-                            : conv3_impl<double>(m, g, in, out, as_stream(stream));
+    return dtype == MPI_F32 ? conv3_impl<float>(m, g, kernel, in, out, as_stream(stream))
+                            : conv3_impl<double>(m, g, kernel, in, out, as_stream(stream));
+}
+
+int mpi_conv3(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, const void *in,
+              void *out, void *stream)
+{
+    return mpi_conv3_kernel(model, grid, dtype, 0, in, out, stream);
+}
+
+int mpi_weighted_trace3(const mpi_model3 *model, const mpi_grid3_desc *grid, mpi_dtype dtype, const void *Ahat,
+                        void *out, void *stream)
+{
+    MPI_TRY(check_model3(model));
+    MPI_TRY(check_grid3(grid));
+    MPI_TRY(check_dtype(dtype));
+    if (!Ahat || !out) { set_error("Ahat or out is NULL"); return MPI_ERR_INVALID; }
+    const Model3H m = to_host3(model);
+    const Grid3H g = to_host3(grid);
+    return dtype == MPI_F32 ? weighted_trace3_impl<float>(m, g, Ahat, out, as_stream(stream))
+                            : weighted_trace3_impl<double>(m, g, Ahat, out, as_stream(stream));
 }
 
 int mpi_denoise_gaussian5_3d(const void *in, void *out, int nx, int ny, int nz, mpi_dtype dtype,
@@ -1092,7 +1163,8 @@ int mpi_pnp_solve3(const mpi_model3 *model, const mpi_grid3_desc *grid, const mp
     }
     if (opts->op == MPI_OP_FORWARD) MPI_TRY(check_traj(traj));
     if (opts->n_iter < 0 || opts->n_cg < 0 || !(opts->nu0 >= 0.0) || !std::isfinite(opts->nu0) ||
-        !(opts->clip_pct <= 100.0) || std::isnan(opts->clip_pct) || opts->kernel_component != 0) {
+        !(opts->clip_pct <= 100.0) || std::isnan(opts->clip_pct) || opts->kernel_component < 0 ||
+        opts->kernel_component > (opts->op == MPI_OP_CONV ? 1 : 0)) {
         set_error("invalid PnP options (n_iter %d, n_cg %d, nu0 %g, clip_pct %g, kernel_component %d)",
                   opts->n_iter, opts->n_cg, opts->nu0, opts->clip_pct, opts->kernel_component);
         return MPI_ERR_INVALID;

@@ -195,8 +195,15 @@ def test_other_entry_points_validate_without_gpu():
                                                ref(api.PnPOpts(7, 2, 3, 1e-3, 5.0, 0)), no_cb, None,
                                                buf, None, None), -1, b""),
         ("pnp3 kernel entry", lambda: lib.mpi_pnp_solve3(ref(m3), ref(g3), ref(tr0), 0, buf,
-                                                        ref(api.PnPOpts(1, 2, 3, 1e-3, 5.0, 1)), no_cb3, None,
+                                                        ref(api.PnPOpts(1, 2, 3, 1e-3, 5.0, 2)), no_cb3, None,
                                                         buf, None, None), -1, b""),
+        ("pnp3 kernel with A", lambda: lib.mpi_pnp_solve3(ref(m3), ref(g3), ref(tr0), 0, buf,
+                                                         ref(api.PnPOpts(0, 2, 3, 1e-3, 5.0, 1)), no_cb3, None,
+                                                         buf, None, None), -1, b""),
+        ("conv3 kernel 2", lambda: lib.mpi_conv3_kernel(ref(m3), ref(g3), 0, 2, buf, ctypes.c_void_p(32), None),
+         -1, b"kernel"),
+        ("weighted trace NULL", lambda: lib.mpi_weighted_trace3(ref(m3), ref(g3), 0, None, buf, None), -1,
+         b"NULL"),
         ("pnp opts NULL", lambda: lib.mpi_pnp_solve(ref(m2), ref(g2), ref(tr0), 0, buf, None, no_cb, None,
                                                     buf, None, None), -1, b""),
         ("batch 0 frames", lambda: lib.mpi_batch_plan_create(0, ref(m2), ref(g2), None, None, ref(pnp), 0,

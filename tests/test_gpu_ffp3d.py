@@ -193,3 +193,45 @@ def test_pnp3_conv_fft_route(orc):
     want = orc.pnp(op, op, u, (18, 20, 24), 2, 3, 0.05, denoise=lambda x, sig: orc.gaussian5_3d(x))
     got = api.mpi_pnp_solve3(m, g, None, None, dev(u, dt), 2, 3, 0.05, op=api.MPI_OP_CONV)
     assert rel_l2(host(got), want) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("shape", [(9, 7, 5), (24, 20, 18)])
+def test_conv3_weighted_trace_kernel(orc, dt, shape):
+    """mpi_conv3_kernel(kernel = 1): the convolution with beta tr K(beta G y)
+    on the direct and the FFT route, for the traceless default gradient and a
+    general one."""
+    nx, ny, nz = shape
+    g = syn.box_grid3(nx, ny, nz)
+    for m in (syn.default_model3(), dict(syn.default_model3(), G=G_GEN)):
+        x = rounded(np.random.default_rng(nx + 1).normal(size=(nz, ny, nx)), dt)
+        want = orc.conv3(g, orc.conv_kernel3_trK(m, g), x)
+        assert rel_l2(host(api.mpi_conv3_kernel(m, g, 1, dev(x, dt))), want) <= tol(dt)
+        want0 = orc.conv3(g, orc.conv_kernel3(m, g), x)
+        assert rel_l2(host(api.mpi_conv3_kernel(m, g, 0, dev(x, dt))), want0) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_weighted_trace3(orc, dt):
+    g = syn.box_grid3(7, 6, 5)
+    for m in (syn.default_model3(), dict(syn.default_model3(), G=G_GEN)):
+        A = rounded(np.random.default_rng(3).normal(size=(9, 5, 6, 7)), dt)
+        want = orc.weighted_trace3(m, A)
+        assert rel_l2(host(api.mpi_weighted_trace3(m, g, dev(A, dt))), want) <= tol(dt)
+
+
+def test_pnp3_conv_weighted_trace_kernel(orc):
+    """PnP with kernel = 1 convolves with beta tr K(beta G y).  That kernel is
+    ~1e3 times the traceless trace kernel, so nu0 = 0.05 leaves C^T C + nu I
+    badly conditioned: at 3 x 4 steps the oracle's own one-ulp spread is
+    6.5e-13 and a GB300 run differed by 4.8e-12.  At 2 x 2 steps the spread is
+    1e-15, and the strict FP64 bar applies."""
+    dt = torch.float64
+    g = syn.box_grid3(9, 8, 5)
+    m = syn.default_model3()
+    u = np.random.default_rng(7).normal(size=(5, 8, 9)) + 1.0
+    kern = orc.conv_kernel3_trK(m, g)
+    op = lambda x: orc.conv3(g, kern, x)  # noqa: E731
+    want = orc.pnp(op, op, u, (5, 8, 9), 2, 2, 0.05, denoise=lambda x, sig: orc.gaussian5_3d(x))
+    got = api.mpi_pnp_solve3(m, g, None, None, dev(u, dt), 2, 2, 0.05, op=api.MPI_OP_CONV, kernel=1)
+    assert rel_l2(host(got), want) <= tol(dt)
