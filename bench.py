@@ -368,26 +368,32 @@ def measure_paper_pipeline(api, syn, dev, stream):
             return it, api.mpi_pnp_solve(m, g, None, None, a00.contiguous(), 10, 20, nu_c00,
                                          op=api.MPI_OP_CONV, kernel_component=0)
 
-        # the same pipeline with the continuous Laplacian (stencil / h^2, h in
-        # mm): the bare stencil's gamma becomes gamma / h^4
-        h = g["dx"]
-
+        # the same pipelines with the continuous Laplacian as the regulariser
+        # (the stencil with 1/dx^2, 1/dy^2; lengths in mm) at the paper's gamma
         def two_stage_scaled():
-            _, u, it = api.mpi_grid(g, r, v, s, gamma=1e-7 / h ** 4, max_iter=10000, rel_tol=1e-3,
-                                    return_iters=True)
+            _, u, it = api.mpi_grid(g, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3,
+                                    return_iters=True, lap_scaled=True)
             return it, api.mpi_pnp_solve(m, g, None, None, u.contiguous(), 10, 20, nu_c,
                                          op=api.MPI_OP_CONV)
+
+        def single_x_scaled():
+            _, a00, it = api.mpi_grid(g, r, v, s_x, gamma=1e-7, max_iter=10000, rel_tol=1e-3,
+                                      return_iters=True, channel=0, lap_scaled=True)
+            return it, api.mpi_pnp_solve(m, g, None, None, a00.contiguous(), 10, 20, nu_c00,
+                                         op=api.MPI_OP_CONV, kernel_component=0)
 
         t2, (it2, rho2) = timed(two_stage)
         td, rhod = timed(direct)
         t1, (it1, rho1) = timed(single_x)
         t3, (it3, rho3) = timed(two_stage_scaled)
+        t4, (it4, rho4) = timed(single_x_scaled)
         out[f"{n}x{n}"] = {
             "s": t2, "core_stage_cg_steps": it2, "rel_err_vs_phantom": err(rho2),
             "direct_A_pnp": {"s": td, "rel_err_vs_phantom": err(rhod)},
             "single_channel_x": {"s": t1, "core_stage_cg_steps": it1, "rel_err_vs_phantom": err(rho1)},
-            "two_stage_scaled_laplacian": {"s": t3, "gamma": 1e-7 / h ** 4, "core_stage_cg_steps": it3,
-                                           "rel_err_vs_phantom": err(rho3)},
+            "two_stage_scaled_laplacian": {"s": t3, "core_stage_cg_steps": it3, "rel_err_vs_phantom": err(rho3)},
+            "single_channel_x_scaled_laplacian": {"s": t4, "core_stage_cg_steps": it4,
+                                                  "rel_err_vs_phantom": err(rho4)},
             "paper_cpu_s": paper[n][0], "paper_rtx_a6000_s": paper[n][1]}
     return out
 

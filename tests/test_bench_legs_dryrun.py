@@ -57,13 +57,15 @@ def _fake_api(orc):
     def mpi_conv_component(m, g, comp, z, out=None, stream=None):
         return T(conv_fft(kernel(m, g, comp), N(z)))
 
-    def mpi_grid(g, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, return_iters=False, channel=None, **kw):
-        api.calls.append(("grid", g["nx"], gamma, channel))
+    def mpi_grid(g, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, return_iters=False, channel=None,
+                 lap_scaled=False, **kw):
+        api.calls.append(("grid", g["nx"], gamma, channel, lap_scaled))
+        lap = "scaled" if lap_scaled else "bare"
         if channel is None:
-            A, u, h = orc.core_stage(g, N(r), N(v), N(s), gamma, max_iter, rel_tol=rel_tol)
+            A, u, h = orc.core_stage(g, N(r), N(v), N(s), gamma, max_iter, rel_tol=rel_tol, lap=lap)
         else:
             A, u, h = orc.core_stage_channel(g, N(r), N(v), N(s).reshape(-1), channel, gamma, max_iter,
-                                             rel_tol=rel_tol)
+                                             rel_tol=rel_tol, lap=lap)
         return (T(A), T(u), len(h) - 1) if return_iters else (T(A), T(u))
 
     def mpi_pnp_solve(m, g, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, op=0, kernel_component=None, **kw):
@@ -92,14 +94,17 @@ def test_paper_pipeline_leg_logic(orc, monkeypatch):
     assert set(out) == {"21x21", "100x100"}
     for n, rec in ((21, out["21x21"]), (100, out["100x100"])):
         for key in ("s", "core_stage_cg_steps", "rel_err_vs_phantom", "direct_A_pnp", "single_channel_x",
-                    "two_stage_scaled_laplacian", "paper_cpu_s", "paper_rtx_a6000_s"):
+                    "two_stage_scaled_laplacian", "single_channel_x_scaled_laplacian", "paper_cpu_s",
+                    "paper_rtx_a6000_s"):
             assert key in rec, key
-        sc = rec["two_stage_scaled_laplacian"]
-        assert sc["gamma"] == pytest.approx(1e-7 / (24.0 / n) ** 4)
-        assert sc["core_stage_cg_steps"] > 0 and np.isfinite(sc["rel_err_vs_phantom"])
+        for k in ("two_stage_scaled_laplacian", "single_channel_x_scaled_laplacian"):
+            assert rec[k]["core_stage_cg_steps"] > 0 and np.isfinite(rec[k]["rel_err_vs_phantom"])
     # the scaled regulariser keeps the fine grid near the coarse one (reading of the regulariser)
     assert out["100x100"]["two_stage_scaled_laplacian"]["rel_err_vs_phantom"] < 0.45
+    assert out["100x100"]["single_channel_x_scaled_laplacian"]["rel_err_vs_phantom"] < 0.6
     grids = [c for c in api.calls if c[0] == "grid"]
-    assert {(c[1], c[3]) for c in grids} == {(21, None), (21, 0), (100, None), (100, 0)}
+    assert {(c[1], c[3], c[4]) for c in grids} == {(n, ch, sc) for n in (21, 100) for ch in (None, 0)
+                                                   for sc in (False, True)}
+    assert all(c[2] == 1e-7 for c in grids)
     pnps = [c for c in api.calls if c[0] == "pnp"]
     assert ("pnp", 100, 1, 0) in pnps and ("pnp", 100, 0, None) in pnps

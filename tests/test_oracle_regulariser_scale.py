@@ -49,3 +49,28 @@ def test_unscaled_stencil_fails_on_the_fine_grid_and_scaled_one_does_not(orc):
     assert coarse < 0.45 and abs(coarse_scaled - coarse) < 0.02
     assert fine > 1.5
     assert fine_scaled < 0.4
+
+
+def test_single_channel_pipeline_on_the_fine_grid(orc):
+    """The single-channel form (channel x only, Sec. 3.6: Core Stage on one
+    channel, PnP with the (0, 0) kernel entry) shows the same: at 100x100 the
+    bare stencil fails and the scaled Laplacian reconstructs."""
+    m = syn.default_model()
+    r, v = syn.lissajous(1632, 17, 16)
+    n = 100
+    g = syn.square_grid(n)
+    c = syn.ellipses(g, np.random.default_rng(101))
+    s = syn.add_noise(orc.forward(m, g, r, v, c), 0.01, 201)
+    kern = orc.conv_kernel(m, g, component=(0, 0))
+
+    def C(x):
+        return orc.conv(g, kern, x.reshape(n, n))
+
+    rng = np.random.default_rng(5)
+    nu0 = 1e-3 * np.mean([np.sum(C(rng.integers(0, 2, (n, n)) * 2.0 - 1.0) ** 2) for _ in range(4)]) / (n * n)
+    errs = {}
+    for lap in ("bare", "scaled"):
+        _, a00, _ = orc.core_stage_channel(g, r, v, s[0], 0, 1e-7, 10000, rel_tol=1e-3, lap=lap)
+        rho = orc.pnp(C, C, a00, (n, n), 10, 20, nu0)
+        errs[lap] = float(np.linalg.norm(rho - c) / np.linalg.norm(c))
+    assert errs["bare"] > 1.5 and errs["scaled"] < 0.6
