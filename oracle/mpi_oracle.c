@@ -442,6 +442,18 @@ void og_conv(const og_grid *g, const double *kern, const double *in, double *out
         }
 }
 
+/* Host threads of the parallel loops (all outputs are independent, so the
+   count changes no result, only the wall-clock time of a timing run). */
+void og_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 int og_num_threads(void)
 {
 #ifdef _OPENMP

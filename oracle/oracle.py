@@ -108,6 +108,8 @@ def _load():
             lib.og_conv_kernel_component.argtypes = [P(_Model), P(_Grid), ctypes.c_int, _D]
             lib.og_conv.argtypes = [P(_Grid), _D, _D, _D]
             lib.og_num_threads.restype = ctypes.c_int
+            lib.og_set_num_threads.argtypes = [ctypes.c_int]
+            lib.og_set_num_threads.restype = None
             lib.og_kernel_matrix3.argtypes = [_I64, _D, _D]
             lib.og_pair3_export.argtypes = [P(_Model3), _D, _D, _D, _D]
             lib.og_forward3.argtypes = [P(_Model3), P(_Grid3), _I64, _D, _D, _D, _D]
@@ -171,6 +173,12 @@ def _model3(m) -> _Model3:
 
 def num_threads() -> int:
     return int(_load().og_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Host threads of the oracle's parallel loops (timing only: the loops
+    are over independent outputs, so results do not depend on it)."""
+    _load().og_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------------------
@@ -454,7 +462,9 @@ def pnp(op, opT, data, shape, n_it, n_cg, nu0, clip_pct=5.0, denoise=None,
         rhs = b0 + nu_k * rho2
         apply = lambda x, nu_k=nu_k: _f64(opT(op(x))).reshape(shape) + nu_k * x
         rho1, hist, _ = cg(apply, rhs, rho2, n_cg)
+        clip = float("-inf")
         if clip_pct is not None and clip_pct >= 0:
+            clip = percentile_value(rho1, clip_pct)
             rho1 = percentile_clamp(rho1, clip_pct)
         sigma = float(np.sqrt(variance(rho1)))
         if k == 0:
@@ -464,7 +474,7 @@ def pnp(op, opT, data, shape, n_it, n_cg, nu0, clip_pct=5.0, denoise=None,
             nu = lam / (sigma * sigma)
         if record is not None:
             record.append({"sigma": sigma, "nu": nu, "cg_resid": float(hist[-1]),
-                           "nu_used": nu_k})
+                           "nu_used": nu_k, "clip": clip})
     return rho2
 
 
