@@ -105,7 +105,10 @@ int mpi_forward(const mpi_model *model, const mpi_grid_desc *grid,
  * 32 MiB / (16 + 4 n_ch) bytes per sample in FP32 (1.39 million samples with
  * two channels) and half that in FP64.  The first call on a device looks up
  * the array's device address once (with that device current); make that
- * first call before any stream capture.  All calls share the array and keep
+ * first call before any stream capture.  The address is kept for the life of
+ * the process: after cudaDeviceReset on a device it no longer names the array
+ * (the reset unloads the library's device image), so do not call this entry
+ * point on a device that has been reset.  All calls share the array and keep
  * nothing across calls that a later call relies on; calls that overlap on the
  * GPU (other streams or host threads at the same time) race on it. */
 int mpi_forward_noalloc(const mpi_model *model, const mpi_grid_desc *grid,
@@ -245,6 +248,7 @@ typedef struct {
     double sigma;     /* noise estimate sqrt(Var(rho1)) of this iteration */
     double nu;        /* nu_{k+1} = lambda / sigma^2 */
     double cg_resid;  /* ||r|| after the last CG step */
+    double clip;      /* the percentile value rho1 was clamped to (-inf when trimming is off) */
 } mpi_pnp_iter_info;
 
 /* Algorithm 1: rho2 <- 0; for k < n_iter: rho1 <- CG(O^T O + nu_k I,
@@ -259,6 +263,36 @@ int mpi_pnp_solve(const mpi_model *model, const mpi_grid_desc *grid,
                   const mpi_traj *traj, mpi_dtype dtype, const void *data,
                   const mpi_pnp_opts *opts, mpi_denoise_fn denoise, void *user,
                   void *rho_out, mpi_pnp_iter_info *info, void *stream);
+
+/* Sum across the processes of a sample-sharded solve: replace the `count`
+ * FP64 values of the DEVICE buffer `buf` on every process by their
+ * elementwise sum over all processes, ordered on `stream` (enqueue the
+ * reduction on it, or complete it before returning).  Every process must
+ * receive the identical sum (an NCCL all-reduce does; so does a fixed-order
+ * host sum).  Returns 0 on success; nonzero aborts the solve. */
+typedef int (*mpi_allreduce_fn)(double *buf, int64_t count, void *stream, void *user);
+
+/* Algorithm 1 with O = A for ONE problem whose trajectory samples are split
+ * across processes (one GPU each).  A and A^T are sums over the samples
+ * (Eq. core:formula), so the samples partition the work: each process passes
+ * its own contiguous slice -- traj (r, v: [T_p][2], T_p >= 0) and data
+ * (s: [n_ch][T_p]) -- while model, grid, opts and the built-in or callback
+ * denoiser are the same on every process.  A of an image gives this process's
+ * samples with no exchange; A^T gives a partial image, which the library sums
+ * across processes with `allreduce` (N = nx*ny values): once for A^T data and
+ * once per CG step.  Every other step (CG vectors, inner products, trimming,
+ * noise estimate, denoiser) runs replicated on the identical reduced vectors,
+ * so all processes finish with the same rho_out.  One process with an
+ * allreduce that does nothing computes what mpi_pnp_solve computes, up to the
+ * rounding order of the CG inner products.  opts->op must be MPI_OP_FORWARD;
+ * allreduce must not be NULL.  A nonzero return of allreduce (or denoise) ends
+ * the call with MPI_ERR_CALLBACK.  Allocates scratch like mpi_pnp_solve plus
+ * one FP64 image. */
+int mpi_pnp_solve_sharded(const mpi_model *model, const mpi_grid_desc *grid,
+                          const mpi_traj *traj, mpi_dtype dtype, const void *data,
+                          const mpi_pnp_opts *opts, mpi_denoise_fn denoise, void *user,
+                          mpi_allreduce_fn allreduce, void *comm_user, void *rho_out,
+                          mpi_pnp_iter_info *info, void *stream);
 
 /* ---- Three-dimensional field-free point (Sec. 2 with n = 3) -------------- */
 
@@ -434,6 +468,25 @@ long long mpi_kernel_launches(void);
  * one class. */
 int mpi_profile_enable(int enable);
 int mpi_profile_read(int kernel_class, long long *launches, double *total_ms);
+
+/* Measured instruction throughput of the GPU (no counterpart in the paper:
+ * it supplies the denominator of the pair kernels' roofline, which are bound
+ * by instruction issue on the FP32 and MUFU/XU pipes, not by memory).
+ * Launches blocks_per_sm (1..8) blocks of 256 threads per SM on the current
+ * device; every thread runs 8 independent chains of `iters` (1..2^20)
+ * operations of kind `op`.  *ops_per_clk_sm receives the median over SMs of
+ * the thread-operations completed per SM clock cycle (clock64 spans of the
+ * SM's blocks, so independent of the clock frequency); *ms (nullable) the
+ * CUDA-event time of the launch.  Allocates ~2 MB of scratch
+ * (stream-ordered) and synchronises `stream`.  MPI_ERR_INVALID on arguments
+ * out of range. */
+#define MPI_PROBE_FMA 0   /* FP32 fma.rn */
+#define MPI_PROBE_RSQRT 1 /* rsqrt.approx.ftz.f32 */
+#define MPI_PROBE_EX2 2   /* ex2.approx.ftz.f32 */
+#define MPI_PROBE_RCP 3   /* rcp.approx.ftz.f32 */
+#define MPI_PROBE_DFMA 4  /* FP64 fma.rn */
+int mpi_probe_pipe_rate(int op, int blocks_per_sm, int iters, double *ops_per_clk_sm, double *ms,
+                        void *stream);
 
 #ifdef __cplusplus
 }

@@ -86,7 +86,8 @@ class Model3(ctypes.Structure):
 
 class PnPIterInfo(ctypes.Structure):
     """Per-iteration (sigma, nu, final CG residual) of Algorithm 1."""
-    _fields_ = [("sigma", ctypes.c_double), ("nu", ctypes.c_double), ("cg_resid", ctypes.c_double)]
+    _fields_ = [("sigma", ctypes.c_double), ("nu", ctypes.c_double), ("cg_resid", ctypes.c_double),
+                ("clip", ctypes.c_double)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -105,6 +106,8 @@ MPI_BATCH_MATCH_SINGLE = 2
 DENOISE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                ctypes.c_void_p)
 DENOISE3_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p)
@@ -126,6 +129,8 @@ _SIGS = {
                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "mpi_pnp_solve": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
                      + [DENOISE_FN] + [ctypes.c_void_p] * 4,
+    "mpi_pnp_solve_sharded": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
+                             + [DENOISE_FN, ctypes.c_void_p, ALLREDUCE_FN] + [ctypes.c_void_p] * 4,
     "mpi_transfer_correct": [ctypes.c_int, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 6,
     "mpi_forward3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_adjoint3": [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
@@ -150,6 +155,8 @@ _SIGS = {
     "mpi_status_string": [ctypes.c_int],
     "mpi_last_error_message": [],
     "mpi_version": [],
+    "mpi_probe_pipe_rate": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p],
 }
 
 
@@ -183,6 +190,18 @@ def exported_symbols():
 
 
 PROF_FORWARD, PROF_ADJOINT, PROF_DBETA, PROF_CONV = 0, 1, 2, 3
+PROBE_FMA, PROBE_RSQRT, PROBE_EX2, PROBE_RCP, PROBE_DFMA = 0, 1, 2, 3, 4
+
+
+def mpi_probe_pipe_rate(op: int, blocks_per_sm: int = 8, iters: int = 4096, stream=None):
+    """(thread-operations per SM per clock, launch ms) of one instruction
+    kind (PROBE_FMA, PROBE_RSQRT, PROBE_EX2, PROBE_RCP, PROBE_DFMA) measured on the
+    current GPU; the median over SMs of operations per SM clock cycle."""
+    rate = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(load().mpi_probe_pipe_rate(int(op), int(blocks_per_sm), int(iters), ctypes.byref(rate),
+                                      ctypes.byref(ms), _stream(stream)))
+    return float(rate.value), float(ms.value)
 
 
 def mpi_kernel_launches() -> int:
@@ -466,7 +485,48 @@ def mpi_pnp_solve(model, grid, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, op=M
                                 _dev(rho_out, dt, "rho_out"), info, _stream(stream)))
     del keep
     if with_info:
-        return rho_out, [(i.sigma, i.nu, i.cg_resid) for i in info[:n_iter]]
+        return rho_out, [(i.sigma, i.nu, i.cg_resid, i.clip) for i in info[:n_iter]]
+    return rho_out
+
+
+def mpi_pnp_solve_sharded(model, grid, r, v, data, n_iter, n_cg, nu0, allreduce, clip_pct=5.0,
+                          rho_out=None, with_info=False, stream=None):
+    """Algorithm 1 with A for one problem whose samples are split across
+    processes: ``r``, ``v`` ([T_p, 2]) and ``data`` ([n_ch, T_p]) are this
+    process's slice.  ``allreduce`` is a callable (tensor) -> None that
+    replaces a CUDA float64 tensor by its elementwise sum over all processes
+    (identical on every process), ordered on the current stream -- e.g.
+    ``torch.distributed.all_reduce`` with NCCL.  The library calls it on a
+    view of its own buffer with the library's stream made current."""
+    dt = data.dtype
+    g = make_grid(grid)
+    if rho_out is None:
+        rho_out = torch.empty((g.ny, g.nx), dtype=dt, device=data.device)
+    tr = _traj(r, v, dt)
+    m = make_model(model)
+    opts = PnPOpts(MPI_OP_FORWARD, int(n_iter), int(n_cg), float(nu0), float(clip_pct), 0)
+    info = (PnPIterInfo * max(1, n_iter))() if with_info else None
+    dev = data.device
+
+    def _ar(buf, count, strm, user):
+        try:
+            t = _wrap(buf, (int(count),), torch.float64, dev)
+            if int(strm or 0) == torch.cuda.current_stream(dev).cuda_stream:
+                allreduce(t)
+            else:
+                with torch.cuda.stream(torch.cuda.ExternalStream(int(strm), device=dev)):
+                    allreduce(t)
+            return 0
+        except Exception:  # noqa: BLE001 - reported as MPI_ERR_CALLBACK
+            return 1
+    cb = ALLREDUCE_FN(_ar)
+    data_ptr = _dev(data, dt, "data") if data.numel() else None
+    _check(load().mpi_pnp_solve_sharded(ctypes.byref(m), ctypes.byref(g), ctypes.byref(tr), _dtype(data),
+                                        data_ptr, ctypes.byref(opts), DENOISE_FN(0), None, cb, None,
+                                        _dev(rho_out, dt, "rho_out"), info, _stream(stream)))
+    del cb
+    if with_info:
+        return rho_out, [(i.sigma, i.nu, i.cg_resid, i.clip) for i in info[:n_iter]]
     return rho_out
 
 
@@ -706,7 +766,7 @@ def mpi_pnp_solve3(model3, grid3, r, v, data, n_iter, n_cg, nu0, clip_pct=5.0, o
                                  _dev(rho_out, dt, "rho_out"), info, _stream(stream)))
     del keep
     if with_info:
-        return rho_out, [(i.sigma, i.nu, i.cg_resid) for i in info[:n_iter]]
+        return rho_out, [(i.sigma, i.nu, i.cg_resid, i.clip) for i in info[:n_iter]]
     return rho_out
 
 

@@ -69,22 +69,23 @@ __device__ __forceinline__ int frame_of(const T (&f)[MAXN], int n, int64_t b)
 template <typename OUT, bool CG>
 __global__ void __launch_bounds__(256) k_reduce_batch(const __grid_constant__ RedTab B)
 {
-    __shared__ double sh[8][33];
+    __shared__ SumAcc<float> sh[8][33];
     const RedFrame &F = B.f[frame_of(B.f, B.n, blockIdx.x)];
     const int64_t b = blockIdx.x - F.blk0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = b * 32 + lane;
-    double acc = 0.0;
+    SumAcc<float> acc{};
     if (e < F.len) {
 #pragma unroll 8
-        for (int c = w; c < F.n_chunks; c += 8) acc += double(F.part[(int64_t)c * F.len + e]);
+        for (int c = w; c < F.n_chunks; c += 8) acc.add(F.part[(int64_t)c * F.len + e]);
     }
     sh[w][lane] = acc;
     __syncthreads();
     if (w == 0) {
-        double tot = 0.0;
+        SumAcc<float> all{};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) tot += sh[k][lane];
+        for (int k = 0; k < 8; ++k) all.add(sh[k][lane]);
+        double tot = all.value();
         OUT *out = reinterpret_cast<OUT *>(F.out);
         if constexpr (CG) {
             const double pe = e < F.len ? F.p[e] : 0.0;
@@ -252,7 +253,7 @@ static FwdSplit fwd_split_budget(int64_t T, int nx, int ny, int64_t budget)
     rows = std::max<int64_t>(1, std::min<int64_t>(rows, ny));
     sp.chunk_rows = (int)rows;
     sp.n_chunks = (int)((ny + rows - 1) / rows);
-    sp.rows_staged = (int)std::max<int64_t>(1, std::min<int64_t>(rows, (16 * 1024) / (8 * (int64_t)nx)));
+    sp.rows_staged = fwd_rows_staged((int)rows, nx, sizeof(float));
     return sp;
 }
 
@@ -342,7 +343,7 @@ static void configure(mpi_batch_plan &P, int64_t fb, int64_t ab, bool fpers, boo
     for (int f = 0; f < P.n; ++f) {
         P.fs[f] = single ? forward_split(P.T[f], P.g[f].nx, P.g[f].ny, 4, default_target_items())
                          : fwd_split_budget(P.T[f], P.g[f].nx, P.g[f].ny, fb);
-        P.as[f] = single ? adjoint_split(P.T[f], P.g[f].nx, P.g[f].ny, default_target_items())
+        P.as[f] = single ? adjoint_split(P.T[f], P.g[f].nx, P.g[f].ny, default_target_items(), 4)
                          : adj_split_budget(P.T[f], P.g[f].nx, P.g[f].ny, ab);
     }
     int64_t fi = 0, ai = 0;
@@ -372,8 +373,7 @@ static void configure(mpi_batch_plan &P, int64_t fb, int64_t ab, bool fpers, boo
         P.fwd_tab[1].f[f] = fw;
         P.fwd_tab[1].f[f].in = P.p + P.voff[f];
         fi += frame_items_fwd(P.fs[f]);
-        smem = std::max(smem, sizeof(V2<float>) * (P.g[f].nx + P.fs[f].rows_staged +
-                                                   size_t(P.fs[f].rows_staged) * P.g[f].nx));
+        smem = std::max(smem, fwd_smem_bytes(P.g[f].nx, P.fs[f].rows_staged, sizeof(float)));
         PairFrame<float> ad = base;
         ad.item0 = ai;
         ad.in = P.sA[f];
@@ -741,7 +741,7 @@ int mpi_batch_plan_create(int n_frames, const mpi_model *models, const mpi_grid_
         const FwdSplit fs_min = fwd_split_budget(P->T[f], P->g[f].nx, P->g[f].ny, bmin);
         const FwdSplit fs_single = forward_split(P->T[f], P->g[f].nx, P->g[f].ny, 4, default_target_items());
         const AdjSplit as_min = adj_split_budget(P->T[f], P->g[f].nx, P->g[f].ny, bmin);
-        const AdjSplit as_single = adjoint_split(P->T[f], P->g[f].nx, P->g[f].ny, default_target_items());
+        const AdjSplit as_single = adjoint_split(P->T[f], P->g[f].nx, P->g[f].ny, default_target_items(), 4);
         const int fch = std::max(fs_min.n_chunks, fs_single.n_chunks);
         const int ach = std::max(as_min.n_chunks, as_single.n_chunks);
         o_geo.push_back(take(geometry_bytes<float>(P->T[f], P->g[f].nx, P->g[f].ny)));

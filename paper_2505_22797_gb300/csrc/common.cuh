@@ -137,6 +137,50 @@ __device__ __forceinline__ void kahan_add(R &sum, R &comp, R x)
     sum = t;
 }
 
+// Sum of FP32 values carried as the unevaluated pair hi + lo.  Every addition
+// is Knuth's error-free TwoSum (six FP32 operations: hi + x = t + err
+// exactly), the rounding errors collect in lo, so the pair holds the sum to
+// about 2^-48 relative -- the accuracy of an FP64 accumulator -- while all
+// the work stays on the FP32 pipe.  (GB300 executes FP64 arithmetic and the
+// FP32 -> FP64 conversion at a small fraction of the FP32 rate, so summing
+// millions of FP32 partials in FP64 is bound by the FP64 pipe.)  The
+// explicit _rn intrinsics keep the compiler from contracting or reordering
+// the transformation.
+struct F2Sum {
+    float hi, lo;  // value-initialise (F2Sum{}) to start at zero
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(hi, x);
+        const float bp = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        hi = t;
+        lo = __fadd_rn(lo, err);
+    }
+    __device__ __forceinline__ void add(const F2Sum &o)
+    {
+        add(o.hi);
+        lo = __fadd_rn(lo, o.lo);
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+// Accumulator of a fixed-order sum of R values: the pair above for FP32
+// inputs, a plain FP64 sum for FP64 inputs.  Aggregates (usable in shared
+// memory): value-initialise, SumAcc<R>{}, to start at zero.
+template <typename R> struct SumAcc;
+template <> struct SumAcc<float> {
+    F2Sum s;
+    __device__ __forceinline__ void add(float x) { s.add(x); }
+    __device__ __forceinline__ void add(const SumAcc &o) { s.add(o.s); }
+    __device__ __forceinline__ double value() const { return s.value(); }
+};
+template <> struct SumAcc<double> {
+    double s;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void add(const SumAcc &o) { s += o.s; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v)
 {

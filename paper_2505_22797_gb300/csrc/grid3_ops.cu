@@ -387,15 +387,24 @@ struct GridOp3 final : CoreStageOp {
     int ch, nc;
     const Bins3 &bins;
     R *s_tmp;
+    R *p_r;  // FP32 path: the field rounded to R (nc N values); FP64: unused
     double invT;
     bool scaled;
-    GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_, bool scaled_)
-        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 9 : 3), bins(b_), s_tmp(s_tmp_),
+    GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_, R *p_r_, bool scaled_)
+        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 9 : 3), bins(b_), s_tmp(s_tmp_), p_r(p_r_),
           invT(T_ > 0 ? 1.0 / double(T_) : 0.0), scaled(scaled_) {}
     int normal(const double *p, double *y, cudaStream_t st) override
     {
-        MPI_TRY((launch_interp3<R, double>(g, T, nullptr, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
-                                           static_cast<const InterpRec3<R> *>(bins.rec))));
+        const InterpRec3<R> *rec = static_cast<const InterpRec3<R> *>(bins.rec);
+        const R *vs = static_cast<const R *>(bins.vs);
+        if constexpr (sizeof(R) == 4) {
+            const int64_t n = int64_t(nc) * g.n();
+            k_round_field<R><<<grid_blocks(n), 256, 0, st>>>(n, p, p_r);
+            MPI_CHECK_LAUNCH();
+            MPI_TRY((launch_interp3<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec)));
+        } else {
+            MPI_TRY((launch_interp3<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
+        }
         return launch_interp3_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch);
     }
     int lap(const double *x, double *out, cudaStream_t st) override
@@ -423,6 +432,7 @@ int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid
     const size_t o_s = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_sd = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_b = scr.reserve(sizeof(double) * nv), o_x = scr.reserve(sizeof(double) * nv);
+    const size_t o_pr = scr.reserve(sizeof(R) == 4 ? sizeof(R) * nv : 0);
     MPI_TRY(scr.allocate());
     const Bins3 bins = bins3_carve<R>(scr.at<char>(o_bins), T, g);
     R *s_data = scr.at<R>(o_sd);
@@ -430,7 +440,7 @@ int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid
 
     MPI_TRY(build_bins3<R>(g, T, r, v, bins, st));
     MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
-    GridOp3<R> op(g, T, ch, bins, scr.at<R>(o_s), o.lap_scaled != 0);
+    GridOp3<R> op(g, T, ch, bins, scr.at<R>(o_s), scr.at<R>(o_pr), o.lap_scaled != 0);
     MPI_TRY((launch_interp3_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
     MPI_TRY(core_stage_cg(op, nv, b, o, x, n_iter_out, st));
     k_grid3_output<R><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));

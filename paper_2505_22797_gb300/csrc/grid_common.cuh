@@ -121,20 +121,30 @@ int gather_rows(int64_t T, int n_rows, const int *list, const R *in, R *out, cud
     return MPI_OK;
 }
 
-// Ahat_m(node) = scale * sum of the node's NC unit partials, in unit order.
+// out[e] = R(in[e]) for e < n: the FP32 Core Stage rounds the FP64 field once
+// per CG step, so its interpolation gathers FP32 values (GB300 converts FP64
+// at a small fraction of the FP32 rate; a gather converting 16 or 72 values
+// per sample was bound by that conversion).
+template <typename R>
+__global__ void k_round_field(int64_t n, const double *__restrict__ in, R *__restrict__ out)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = R(in[e]);
+}
+
+// Ahat_m(node) = scale * sum of the node's NC unit partials, in unit order
+// (FP32 partials summed as error-free double-float pairs).
 template <typename R, typename OUT, int NC>
 __global__ void k_interp_T_combine(int N, const int *__restrict__ unit_off, const R *__restrict__ unit_part,
                                    OUT *__restrict__ A, double scale)
 {
     for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
-        double acc[NC];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) acc[m] = 0.0;
+        SumAcc<R> acc[NC] = {};
         for (int w = unit_off[node]; w < unit_off[node + 1]; ++w)
 #pragma unroll
-            for (int m = 0; m < NC; ++m) acc[m] += double(unit_part[(int64_t)w * NC + m]);
+            for (int m = 0; m < NC; ++m) acc[m].add(unit_part[(int64_t)w * NC + m]);
 #pragma unroll
-        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(acc[m] * scale);
+        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(acc[m].value() * scale);
     }
 }
 

@@ -493,15 +493,24 @@ struct GridOp2 final : CoreStageOp {
     int ch, nc;
     const Bins &bins;
     R *s_tmp;
+    R *p_r;  // FP32 path: the field rounded to R (nc N values); FP64: unused
     double invT;
     bool scaled;
-    GridOp2(const GridH &g_, int64_t T_, int ch_, const Bins &b_, R *s_tmp_, bool scaled_)
-        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 4 : 2), bins(b_), s_tmp(s_tmp_),
+    GridOp2(const GridH &g_, int64_t T_, int ch_, const Bins &b_, R *s_tmp_, R *p_r_, bool scaled_)
+        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 4 : 2), bins(b_), s_tmp(s_tmp_), p_r(p_r_),
           invT(T_ > 0 ? 1.0 / double(T_) : 0.0), scaled(scaled_) {}
     int normal(const double *p, double *y, cudaStream_t st) override
     {
-        MPI_TRY((launch_interp<R, double>(g, T, nullptr, static_cast<const R *>(bins.vs), p, s_tmp, st, ch,
-                                          static_cast<const InterpRec<R> *>(bins.rec))));
+        const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(bins.rec);
+        const R *vs = static_cast<const R *>(bins.vs);
+        if constexpr (sizeof(R) == 4) {
+            const int64_t n = int64_t(nc) * g.nx * g.ny;
+            k_round_field<R><<<grid_blocks(n), 256, 0, st>>>(n, p, p_r);
+            MPI_CHECK_LAUNCH();
+            MPI_TRY((launch_interp<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec)));
+        } else {
+            MPI_TRY((launch_interp<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
+        }
         return launch_interp_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch);
     }
     int lap(const double *x, double *out, cudaStream_t st) override
@@ -529,6 +538,7 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     const size_t o_s = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_sd = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_b = scr.reserve(sizeof(double) * n4), o_x = scr.reserve(sizeof(double) * n4);
+    const size_t o_pr = scr.reserve(sizeof(R) == 4 ? sizeof(R) * n4 : 0);
     MPI_TRY(scr.allocate());
     const Bins bins = bins_carve<R>(scr.at<char>(o_bins), T, g.nx, g.ny);
     R *s_data = scr.at<R>(o_sd);
@@ -537,7 +547,7 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     MPI_TRY(build_bins<R>(g, T, r, v, bins, st));
     // The sample vectors of the solve live in list (cell) order.
     MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
-    GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_s), o.lap_scaled != 0);
+    GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_s), scr.at<R>(o_pr), o.lap_scaled != 0);
     // b = (1/T) M^T s
     MPI_TRY((launch_interp_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
     MPI_TRY(core_stage_cg(op, n4, b, o, x, n_iter_out, st));

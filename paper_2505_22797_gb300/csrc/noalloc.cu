@@ -44,7 +44,10 @@ std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array for the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached for the life of the
+// process.  cudaDeviceReset unloads the device image the address points into,
+// so after a reset of a device the cached address is stale: this entry point
+// must not be called on a device that has been reset.
 int noalloc_scratch(void **out)
 {
     int dev = 0;

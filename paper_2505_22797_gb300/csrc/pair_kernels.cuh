@@ -16,6 +16,8 @@
 // (frame f owns items [item0_f, item0_f + n_items_f)).
 #pragma once
 
+#include <algorithm>
+
 #include "langevin.cuh"
 #include "pair_ops.cuh"
 
@@ -27,8 +29,43 @@ constexpr int kFwdThreads = 128;
 #endif
 constexpr int kFwdS = MPI_FWD_S;  // samples per thread
 constexpr int kFwdTile = kFwdThreads * kFwdS;
+// Staging of the forward's concentration rows: one copy per block, or (with
+// MPI_FWD_WSTAGE) one per warp, so that the warps of a block never wait for
+// one another at a barrier (their samples lie in different regimes and
+// finish their rows at different times).  A block's row buffers share one
+// byte budget.
+#ifndef MPI_FWD_WSTAGE
+#define MPI_FWD_WSTAGE 0
+#endif
+constexpr int kFwdStageCopies = MPI_FWD_WSTAGE ? kFwdThreads / 32 : 1;
+constexpr size_t kFwdRowBudget = 16 * 1024;
+// Rows staged at a time for rows of nx values of elem bytes.
+inline int fwd_rows_staged(int chunk_rows, int nx, int elem)
+{
+    const size_t per = kFwdRowBudget / kFwdStageCopies / (2 * size_t(elem) * size_t(nx));
+    return (int)std::max<size_t>(1, std::min<size_t>(size_t(chunk_rows), per));
+}
+// Dynamic shared memory of a forward block: xcol [nx] and, per copy, yrow [RB]
+// and RB rows of (x_i, c_i) pairs.
+inline size_t fwd_smem_bytes(int nx, int RB, int elem)
+{
+    return 2 * size_t(elem) * (size_t(nx) + kFwdStageCopies * (size_t(RB) + size_t(RB) * size_t(nx)));
+}
 
-constexpr int kAdjThreads = 128;  // 4 warps
+// Warps per adjoint block, and how the staged samples are shared: one copy
+// per block (MPI_ADJ_WSTAGE 0, block barriers around the staging) or one per
+// warp (1: the warps never wait for one another).  Timed on GB300 at
+// 128 x 128 / 65 536 samples: 4 warps with one copy per block 0.453 ms, one
+// copy per warp 0.466 ms, 2 warps 0.457 ms, 1 warp 0.537 ms.
+#ifndef MPI_ADJ_WARPS
+#define MPI_ADJ_WARPS 4
+#endif
+#ifndef MPI_ADJ_WSTAGE
+#define MPI_ADJ_WSTAGE 0
+#endif
+constexpr int kAdjStageCopies = MPI_ADJ_WSTAGE ? MPI_ADJ_WARPS : 1;
+constexpr int kAdjWarps = MPI_ADJ_WARPS;
+constexpr int kAdjThreads = 32 * kAdjWarps;
 #ifndef MPI_ADJ_V
 #define MPI_ADJ_V 8
 #endif
@@ -42,7 +79,7 @@ constexpr int kAdjThreads = 128;  // 4 warps
 #define MPI_FWD_MINB 6
 #endif
 #ifndef MPI_ADJ_MINB
-#define MPI_ADJ_MINB 6
+#define MPI_ADJ_MINB (24 / MPI_ADJ_WARPS)
 #endif
 #ifndef MPI_FWD_UNROLL
 #define MPI_FWD_UNROLL 8
@@ -56,10 +93,17 @@ constexpr int kFwdUnroll = MPI_FWD_UNROLL;
 constexpr int kFwdUnrollFar = MPI_FWD_UNROLL_FAR;
 constexpr int kAdjV = MPI_ADJ_V;  // voxels (rows) per thread
 constexpr int kAdjTileX = 32;
-constexpr int kAdjTileY = 4 * kAdjV;
+constexpr int kAdjTileY = kAdjWarps * kAdjV;
 #ifndef MPI_ADJ_BLOCK
 #define MPI_ADJ_BLOCK 256
 #endif
+// Unroll depth of the adjoint's asymptotic 32-sample loop (32 = the whole
+// group: staged-sample addresses become constant offsets).
+#ifndef MPI_ADJ_UNROLL_VFAR
+#define MPI_ADJ_UNROLL_VFAR 4
+#endif
+constexpr int kAdjUnrollVfar = MPI_ADJ_UNROLL_VFAR;
+
 constexpr int kAdjBlock = MPI_ADJ_BLOCK;  // samples staged per shared-memory block
 
 template <typename R>
@@ -211,12 +255,15 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
     const int RB = F.rows_staged;
     R A1, D1;  // the closed form at u = near_u (what clamped pairs received)
     Lang<R>::ad_far(Lang<R>::near_u, A1, D1);
-    // Shared memory: xcol [nx], yrow [RB], and RB rows of (x_i, c_ji) pairs.
+    // Shared memory: xcol [nx], then per staging copy yrow [RB] and RB rows
+    // of (x_i, c_ji) pairs.
+    const int lane_id = threadIdx.x & 31;
     V2<R> *s_x = reinterpret_cast<V2<R> *>(smem_raw);
-    V2<R> *s_y = s_x + nx;
+    V2<R> *s_y = s_x + nx + (MPI_FWD_WSTAGE ? (threadIdx.x >> 5) * (RB + RB * nx) : 0);
     V2<R> *s_xc = s_y + RB;
     const CIN *cin = reinterpret_cast<const CIN *>(F.in);
     for (int k = threadIdx.x; k < nx; k += kFwdThreads) s_x[k] = F.xcol[k];
+    if (MPI_FWD_WSTAGE) __syncthreads();  // xcol is read by every warp's staging
 
     R Rx[kFwdS], Ry[kFwdS], Wx[kFwdS], Wy[kFwdS];
     int64_t t[kFwdS];
@@ -255,11 +302,19 @@ __device__ __forceinline__ void forward_item(const PairBatch<R, MAXF> &B, int64_
 #pragma unroll 1
     for (int jb = j0; jb < j0 + nr; jb += RB) {
         const int nrb = min(RB, j0 + nr - jb);
-        __syncthreads();
-        for (int k = threadIdx.x; k < nrb * nx; k += kFwdThreads)
-            s_xc[k] = V2<R>{s_x[k % nx].x, R(cin[(int64_t)jb * nx + k])};
-        for (int k = threadIdx.x; k < nrb; k += kFwdThreads) s_y[k] = F.yrow[jb + k];
-        __syncthreads();
+        if (MPI_FWD_WSTAGE) {
+            __syncwarp();  // this warp's previous rows are consumed
+            for (int k = lane_id; k < nrb * nx; k += 32)
+                s_xc[k] = V2<R>{s_x[k % nx].x, R(cin[(int64_t)jb * nx + k])};
+            for (int k = lane_id; k < nrb; k += 32) s_y[k] = F.yrow[jb + k];
+            __syncwarp();
+        } else {
+            __syncthreads();
+            for (int k = threadIdx.x; k < nrb * nx; k += kFwdThreads)
+                s_xc[k] = V2<R>{s_x[k % nx].x, R(cin[(int64_t)jb * nx + k])};
+            for (int k = threadIdx.x; k < nrb; k += kFwdThreads) s_y[k] = F.yrow[jb + k];
+            __syncthreads();
+        }
 
 #pragma unroll 1
     for (int r = 0; r < nrb; ++r) {
@@ -422,22 +477,25 @@ __device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const 
 
 // ---------------------------------------------------------------------------
 // Adjoint A^T (DBETA = false) and the beta-derivative (DBETA = true).
-// Work item = (tile of 32 x 32 voxels, chunk of samples).  Lane = column, each
-// thread owns kAdjV consecutive rows of its column.  Samples are staged in
-// shared memory kAdjBlock at a time as
+// Work item = (tile of 32 x kAdjTileY voxels, chunk of samples).  Lane =
+// column; each thread owns kAdjV consecutive rows of its column, each warp a
+// 32 x kAdjV box.  Samples are staged in shared memory (kAdjStageCopies
+// copies), kAdjBlock at a time, as
 //   (B r_t) and (u.W, W_x u_x, W_x u_y + W_y u_x, W_y u_y),  u = sum_k s_k p_k,
 // so that the pair term u^T J w = a (u.W) + d (y.W)(y.u) is
 //   f1 uW + f2 (yx^2 Sxx + yx yy S2xy + yy^2 Syy)
 // with (f1, f2) = (a, d) for A^T and (L', L''/z) for d/dbeta.  Per warp and
 // staged block a ballot marks the samples whose distance to the warp's voxel
-// box keeps every pair in the closed-form range.
-template <typename R, bool DIAG, bool DBETA, int MAXF>
+// box keeps every pair in the closed-form range.  ONEBLK: every chunk is at
+// most one staged block (the chunk sum is that block's sum: no compensation
+// needed, the same result as the compensated sum).
+template <typename R, bool DIAG, bool DBETA, int MAXF, bool ONEBLK>
 __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_t item)
 {
-    __shared__ V2<R> s_r[kAdjBlock];
-    __shared__ V4<R> s_q[kAdjBlock];
-    __shared__ uint32_t s_far[4][kAdjBlock / 32];
-    __shared__ uint32_t s_vfar[4][kAdjBlock / 32];
+    __shared__ V2<R> s_rw[kAdjStageCopies][kAdjBlock];
+    __shared__ V4<R> s_qw[kAdjStageCopies][kAdjBlock];
+    __shared__ uint32_t s_far[kAdjWarps][kAdjBlock / 32];
+    __shared__ uint32_t s_vfar[kAdjWarps][kAdjBlock / 32];
     __shared__ double s_red[kAdjThreads / 32];
 
     const PairFrame<R> &F = B.f[find_frame(B, item)];
@@ -447,6 +505,11 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = (tile % F.tiles_x) * kAdjTileX + lane;
     const int jb = (tile / F.tiles_x) * kAdjTileY + warp * kAdjV;
+    V2<R> *s_r = s_rw[MPI_ADJ_WSTAGE ? warp : 0];
+    V4<R> *s_q = s_qw[MPI_ADJ_WSTAGE ? warp : 0];
+    // stager: this warp's lanes (one copy per warp) or the block's threads
+    const int st_id = MPI_ADJ_WSTAGE ? lane : (int)threadIdx.x;
+    constexpr int st_n = MPI_ADJ_WSTAGE ? 32 : kAdjThreads;
     const int ic = min(i, F.nx - 1);
 
     const V2<R> xc = F.xcol[ic];
@@ -487,8 +550,10 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
 #pragma unroll 1
     for (int64_t tb = t0; tb < t1; tb += kAdjBlock) {
         const int nb = (int)min((int64_t)kAdjBlock, t1 - tb);
-        __syncthreads();
-        for (int k = threadIdx.x; k < nb; k += kAdjThreads) {
+        // the previous block of staged samples is consumed
+        if (MPI_ADJ_WSTAGE) __syncwarp();
+        else __syncthreads();
+        for (int k = st_id; k < nb; k += st_n) {
             const int64_t t = tb + k;
             const V4<R> q = F.rw[t];
             R ux = R(0), uy = R(0);
@@ -500,7 +565,8 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
             s_r[k] = V2<R>{q.x, q.y};
             s_q[k] = V4<R>{ux * q.z + uy * q.w, q.z * ux, q.z * uy + q.w * ux, q.w * uy};
         }
-        __syncthreads();
+        if (MPI_ADJ_WSTAGE) __syncwarp();
+        else __syncthreads();
         // Far / very-far flags of this warp for the staged samples.
         for (int m = 0; m < kAdjBlock / 32; ++m) {
             const int k = m * 32 + lane;
@@ -533,7 +599,7 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
             const uint32_t vmask = s_vfar[warp][k0 >> 5];
             const int kn = min(32, nb - k0);
             if (kn == 32 && vmask == 0xffffffffu) {
-#pragma unroll 2
+#pragma unroll kAdjUnrollVfar
                 for (int k = k0; k < k0 + 32; ++k)
                     adj_sample<R, DIAG, DBETA, 2>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
             } else if (kn == 32 && mask == 0xffffffffu) {
@@ -553,7 +619,10 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
             }
         }
 #pragma unroll
-        for (int v = 0; v < kAdjV; ++v) kahan_add(acc[v], comp[v], blk[v]);
+        for (int v = 0; v < kAdjV; ++v) {
+            if (ONEBLK) acc[v] += blk[v];
+            else kahan_add(acc[v], comp[v], blk[v]);
+        }
     }
 
     if constexpr (!DBETA) {
@@ -621,14 +690,14 @@ __device__ __forceinline__ void forward_dispatch(const PairBatch<R, MAXF> &B, in
     }
 }
 
-template <typename R, int DM, bool DBETA, int MAXF>
+template <typename R, int DM, bool DBETA, int MAXF, bool ONEBLK>
 __device__ __forceinline__ void adjoint_dispatch(const PairBatch<R, MAXF> &B, int64_t item)
 {
     if constexpr (DM == 2) {
-        if (B.f[find_frame(B, item)].diag) adjoint_item<R, true, DBETA, MAXF>(B, item);
-        else adjoint_item<R, false, DBETA, MAXF>(B, item);
+        if (B.f[find_frame(B, item)].diag) adjoint_item<R, true, DBETA, MAXF, ONEBLK>(B, item);
+        else adjoint_item<R, false, DBETA, MAXF, ONEBLK>(B, item);
     } else {
-        adjoint_item<R, DM == 1, DBETA, MAXF>(B, item);
+        adjoint_item<R, DM == 1, DBETA, MAXF, ONEBLK>(B, item);
     }
 }
 
@@ -655,22 +724,22 @@ k_forward_persistent(const __grid_constant__ PairBatch<R, MAXF> B, int64_t n_ite
     queue_leave(queue);
 }
 
-template <typename R, int DM, bool DBETA, int MAXF>
-__global__ void __launch_bounds__(kAdjThreads, sizeof(R) == 4 ? MPI_ADJ_MINB : 2)
+template <typename R, int DM, bool DBETA, int MAXF, bool ONEBLK = false>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(R) == 4 ? MPI_ADJ_MINB : 8 / MPI_ADJ_WARPS)
 k_adjoint(const __grid_constant__ PairBatch<R, MAXF> B)
 {
-    adjoint_dispatch<R, DM, DBETA, MAXF>(B, blockIdx.x);
+    adjoint_dispatch<R, DM, DBETA, MAXF, ONEBLK>(B, blockIdx.x);
 }
 
-template <typename R, int DM, bool DBETA, int MAXF>
-__global__ void __launch_bounds__(kAdjThreads, sizeof(R) == 4 ? MPI_ADJ_MINB : 2)
+template <typename R, int DM, bool DBETA, int MAXF, bool ONEBLK = false>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(R) == 4 ? MPI_ADJ_MINB : 8 / MPI_ADJ_WARPS)
 k_adjoint_persistent(const __grid_constant__ PairBatch<R, MAXF> B, int64_t n_items,
                      unsigned long long *queue)
 {
     __shared__ long long s_item;
     int64_t item;
     while (queue_next(queue, n_items, &s_item, item)) {
-        adjoint_dispatch<R, DM, DBETA, MAXF>(B, item);
+        adjoint_dispatch<R, DM, DBETA, MAXF, ONEBLK>(B, item);
         __syncthreads();
     }
     queue_leave(queue);

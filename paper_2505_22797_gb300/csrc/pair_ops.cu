@@ -93,11 +93,6 @@ int prepare_geometry(const ModelH &m, const GridH &g, int64_t T, const void *r, 
 #endif
 int default_target_items() { return MPI_TARGET_MULT * device_sm_count(); }
 
-// Bytes of concentration rows staged in shared memory at a time: small enough
-// that the block's shared memory never limits occupancy below the register
-// limit (~10 blocks of 128 threads per SM).
-static constexpr size_t kFwdRowBytes = 16 * 1024;
-
 FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_items)
 {
     FwdSplit sp;
@@ -106,11 +101,13 @@ FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_ite
     want = std::max(1, std::min(want, ny));
     sp.chunk_rows = (ny + want - 1) / want;
     sp.n_chunks = (ny + sp.chunk_rows - 1) / sp.chunk_rows;
-    sp.rows_staged = (int)std::max<size_t>(1, std::min<size_t>(sp.chunk_rows, kFwdRowBytes / (2 * size_t(elem_bytes) * nx)));
+    // rows staged at a time: small enough that the block's shared memory never
+    // limits occupancy below the register limit
+    sp.rows_staged = fwd_rows_staged(sp.chunk_rows, nx, elem_bytes);
     return sp;
 }
 
-AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items)
+AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items, int elem_bytes)
 {
     AdjSplit sp;
     sp.tiles_x = (nx + kAdjTileX - 1) / kAdjTileX;
@@ -121,6 +118,18 @@ AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items)
     want = std::max<int64_t>(1, std::min(want, blocks));
     const int64_t per = (blocks + want - 1) / want;  // staged blocks per chunk
     sp.chunk_len = (int)(per * kAdjBlock);
+    // Small problems (a few tiles, a few staged blocks) would leave most SMs
+    // idle with whole-block chunks: split the samples finer, down to 32 per
+    // chunk in FP32 and 8 in FP64 (whose pair is ~10x dearer), so that there
+    // are about four items per SM.
+    const int64_t min_items = std::max(1, target_items / 16);
+    if ((int64_t)n_tiles * blocks < min_items && T > 0) {
+        const int64_t floor_len = elem_bytes == 8 ? 8 : 32;
+        const int64_t chunks = (min_items + n_tiles - 1) / n_tiles;
+        int64_t len = (T + chunks - 1) / chunks;
+        len = (len + floor_len - 1) / floor_len * floor_len;
+        sp.chunk_len = (int)std::min<int64_t>(kAdjBlock, std::max(floor_len, len));
+    }
     sp.n_chunks = (int)std::max<int64_t>(1, (T + sp.chunk_len - 1) / sp.chunk_len);
     return sp;
 }
@@ -306,9 +315,10 @@ size_t dbeta_partial_bytes(const AdjSplit &sp)
 
 // Sum over chunks of the partial slices part[c][e], e < len.  A block owns 32
 // consecutive elements; warp w sums chunks w, w+8, ... (coalesced rows of
-// 128 B), and warp 0 adds the eight warp sums in order.  With CG set the
-// epilogue writes out = sum + nu * p (FP64) and the block's partial sum of
-// <p, out> to dot_part[blockIdx.x].
+// 128 B), and warp 0 adds the eight warp sums in order.  FP32 partials are
+// summed as error-free double-float pairs (SumAcc), FP64 ones in FP64.  With
+// CG set the epilogue writes out = sum + nu * p (FP64) and the block's partial
+// sum of <p, out> to dot_part[blockIdx.x].
 constexpr int kRedThreads = 256;
 constexpr int kRedWarps = kRedThreads / 32;
 
@@ -318,22 +328,23 @@ k_reduce_chunks(const R *__restrict__ part, int n_chunks, int64_t len, OUT *__re
                 const double *__restrict__ p, const double *__restrict__ nu_dev,
                 double *__restrict__ dot_part)
 {
-    __shared__ double sh[kRedWarps][33];
+    __shared__ SumAcc<R> sh[kRedWarps][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * 32 + lane;
-    double acc = 0.0;
+    SumAcc<R> acc{};
     if (e < len) {
         // Sequential sum over this warp's chunks; the unroll only lets the
         // loads run ahead (the additions keep their order).
 #pragma unroll 8
-        for (int c = w; c < n_chunks; c += kRedWarps) acc += double(part[(int64_t)c * len + e]);
+        for (int c = w; c < n_chunks; c += kRedWarps) acc.add(part[(int64_t)c * len + e]);
     }
     sh[w][lane] = acc;
     __syncthreads();
     if (w == 0) {
-        double tot = 0.0;
+        SumAcc<R> all{};
 #pragma unroll
-        for (int k = 0; k < kRedWarps; ++k) tot += sh[k][lane];
+        for (int k = 0; k < kRedWarps; ++k) all.add(sh[k][lane]);
+        double tot = all.value();
         if constexpr (CG) {
             const double pe = e < len ? p[e] : 0.0;
             tot += *nu_dev * pe;
@@ -444,7 +455,7 @@ int launch_forward(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
     B.f[0].rows_staged = sp.rows_staged;
     B.f[0].near_cols = near_columns<R>(m, g);
     B.f[0].order = sp.order;
-    const size_t smem = sizeof(V2<R>) * (g.nx + sp.rows_staged + size_t(sp.rows_staged) * g.nx);
+    const size_t smem = fwd_smem_bytes(g.nx, sp.rows_staged, sizeof(R));
     const int64_t items = (int64_t)sp.n_tiles * sp.n_chunks;
     {
         ProfScope prof(kProfForward, st);
@@ -481,11 +492,15 @@ int launch_adjoint(const ModelH &m, const GridH &g, int64_t T, const Geometry<R>
         B.f[0].chunk = sp.chunk_len;
         B.f[0].order = sp.order;
         const int64_t items = (int64_t)sp.tiles_x * sp.tiles_y * sp.n_chunks;
+        const bool one = sp.chunk_len <= kAdjBlock;  // one staged block per chunk
         ProfScope prof(kProfAdjoint, st);
-        if (is_diag(m))
-            k_adjoint<R, 1, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
-        else
-            k_adjoint<R, 0, false, 1><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+        if (is_diag(m)) {
+            if (one) k_adjoint<R, 1, false, 1, true><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+            else k_adjoint<R, 1, false, 1, false><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+        } else {
+            if (one) k_adjoint<R, 0, false, 1, true><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+            else k_adjoint<R, 0, false, 1, false><<<(unsigned)items, kAdjThreads, 0, st>>>(B);
+        }
         MPI_CHECK_LAUNCH();
     } else {
         MPI_TRY_CUDA(cudaMemsetAsync(part, 0, sizeof(R) * N, st));

@@ -50,7 +50,7 @@ struct AdjSplit {
     const int *order = nullptr;
 };
 FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_items);
-AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items);
+AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items, int elem_bytes);
 int default_target_items();
 // Column half-width around a sample that can hold a near-FFP pair (forward).
 template <typename R>

@@ -214,7 +214,7 @@ int pnp_run(PnPOperator<R> &op, int64_t N, const void *data, const mpi_pnp_opts 
     const size_t o_pq = scr.reserve(sizeof(double) * std::max(nblk, n_pq));
     const size_t o_rr0 = scr.reserve(sizeof(double) * nblk), o_rr1 = scr.reserve(sizeof(double) * nblk);
     const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 4);
-    const size_t o_info = scr.reserve(sizeof(double) * 3 * std::max(o.n_iter, 1));
+    const size_t o_info = scr.reserve(sizeof(double) * kInfoCols * std::max(o.n_iter, 1));
     const size_t o_r1 = scr.reserve(sizeof(R) * N), o_r2 = scr.reserve(sizeof(R) * N);
     MPI_TRY(scr.allocate());
     double *b0 = scr.at<double>(o_b0), *x = scr.at<double>(o_x), *r = scr.at<double>(o_r),
@@ -245,7 +245,7 @@ int pnp_run(PnPOperator<R> &op, int64_t N, const void *data, const mpi_pnp_opts 
         // trimming, sigma, lambda (k = 0), nu
         k_outer_stats<R><<<1, kStatThreads, 0, st>>>(N, x, o.clip_pct >= 0.0 ? 1 : 0, o.clip_pct, k,
                                                     o.nu0, scal, rr_part[o.n_cg & 1], nblk,
-                                                    inf + 3 * k, rho1);
+                                                    inf + kInfoCols * k, rho1);
         MPI_CHECK_LAUNCH();
         R *dst = (k == o.n_iter - 1) ? static_cast<R *>(rho_out) : rho2;
         const int rc = fault_cb ? 1 : op.denoise(rho1, dst, scal + kScalSigma, st);
@@ -259,14 +259,15 @@ int pnp_run(PnPOperator<R> &op, int64_t N, const void *data, const mpi_pnp_opts 
     }
     if (o.n_iter == 0) MPI_TRY_CUDA(cudaMemsetAsync(rho_out, 0, sizeof(R) * N, st));
     if (info) {
-        std::vector<double> h(3 * std::max(o.n_iter, 1));
-        MPI_TRY_CUDA(cudaMemcpyAsync(h.data(), inf, sizeof(double) * 3 * o.n_iter,
+        std::vector<double> h(kInfoCols * std::max(o.n_iter, 1));
+        MPI_TRY_CUDA(cudaMemcpyAsync(h.data(), inf, sizeof(double) * kInfoCols * o.n_iter,
                                      cudaMemcpyDeviceToHost, st));
         MPI_TRY_CUDA(cudaStreamSynchronize(st));
         for (int k = 0; k < o.n_iter; ++k) {
-            info[k].sigma = h[3 * k];
-            info[k].nu = h[3 * k + 1];
-            info[k].cg_resid = h[3 * k + 2];
+            info[k].sigma = h[kInfoCols * k];
+            info[k].nu = h[kInfoCols * k + 1];
+            info[k].cg_resid = h[kInfoCols * k + 2];
+            info[k].clip = h[kInfoCols * k + 3];
         }
     }
     return MPI_OK;
@@ -289,12 +290,28 @@ struct PnPOp2D final : PnPOperator<R> {
     int64_t N = 0;
     mpi_denoise_fn den = nullptr;
     void *user = nullptr;
+    // Sample-sharded solve: this process's samples only; partial A^T images
+    // are summed across processes by `ar` into `red` (FP64, N values).
+    mpi_allreduce_fn ar = nullptr;
+    void *ar_user = nullptr;
+    double *red = nullptr;
 
+    int reduce(double *buf, cudaStream_t st)
+    {
+        const int rc = ar(buf, N, st, ar_user);
+        if (rc != 0) {
+            set_error("allreduce callback returned %d", rc);
+            return MPI_ERR_CALLBACK;
+        }
+        return MPI_OK;
+    }
     int rhs(const R *data, double *b0, cudaStream_t st) override
     {
-        if (op == MPI_OP_FORWARD)
-            return launch_adjoint<R, double>(m, g, T, geo, as, data, adj_part, b0, nullptr, nullptr,
-                                             nullptr, st);
+        if (op == MPI_OP_FORWARD) {
+            MPI_TRY((launch_adjoint<R, double>(m, g, T, geo, as, data, adj_part, b0, nullptr, nullptr,
+                                               nullptr, st)));
+            return ar ? reduce(b0, st) : MPI_OK;
+        }
         return conv_apply<R, R, double>(C, data, b0, st);
     }
     int apply_normal(const double *v, double *q, const double *nu_dev, double *pq_part,
@@ -302,13 +319,23 @@ struct PnPOp2D final : PnPOperator<R> {
     {
         if (op == MPI_OP_FORWARD) {
             MPI_TRY((launch_forward<R, double, R>(m, g, T, geo, fs, v, fwd_part, sA, st)));
-            return launch_adjoint<R, double>(m, g, T, geo, as, sA, adj_part, q, v, nu_dev, pq_part, st);
+            if (!ar)
+                return launch_adjoint<R, double>(m, g, T, geo, as, sA, adj_part, q, v, nu_dev, pq_part, st);
+            // partial A^T A v of this process's samples, summed across
+            // processes, then q = sum + nu v with the <v, q> partials
+            MPI_TRY((launch_adjoint<R, double>(m, g, T, geo, as, sA, adj_part, red, nullptr, nullptr,
+                                               nullptr, st)));
+            MPI_TRY(reduce(red, st));
+            return axpy_dot_launch<double>(N, red, v, nu_dev, q, pq_part, st);
         }
         MPI_TRY((conv_apply<R, double, R>(C, v, tmp1, st)));
         MPI_TRY((conv_apply<R, R, R>(C, tmp1, tmp2, st)));
         return axpy_dot_launch<R>(N, tmp2, v, nu_dev, q, pq_part, st);
     }
-    int n_pq() const override { return op == MPI_OP_FORWARD ? adjoint_dot_blocks(g.nx, g.ny) : vec_blocks(N); }
+    int n_pq() const override
+    {
+        return (op == MPI_OP_FORWARD && !ar) ? adjoint_dot_blocks(g.nx, g.ny) : vec_blocks(N);
+    }
     int denoise(const R *in, R *out, const double *sigma_dev, cudaStream_t st) override
     {
         if (den) return den(in, out, g.nx, g.ny, sizeof(R) == 4 ? MPI_F32 : MPI_F64, sigma_dev, st, user);
@@ -320,7 +347,8 @@ struct PnPOp2D final : PnPOperator<R> {
 template <typename R>
 static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const void *data,
                     const mpi_pnp_opts &o, mpi_denoise_fn den, void *user, void *rho_out,
-                    mpi_pnp_iter_info *info, cudaStream_t st)
+                    mpi_pnp_iter_info *info, cudaStream_t st, mpi_allreduce_fn ar = nullptr,
+                    void *ar_user = nullptr)
 {
     PnPOp2D<R> S;
     S.op = o.op;
@@ -330,13 +358,16 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
     S.N = (int64_t)g.nx * g.ny;
     S.den = den;
     S.user = user;
+    S.ar = ar;
+    S.ar_user = ar_user;
     const int target = default_target_items();
 
     Scratch scr(st);
-    size_t o_geo = 0, o_fp = 0, o_ap = 0, o_sA = 0, o_K = 0, o_t1 = 0, o_t2 = 0, o_ord = 0;
+    size_t o_geo = 0, o_fp = 0, o_ap = 0, o_sA = 0, o_K = 0, o_t1 = 0, o_t2 = 0, o_ord = 0, o_red = 0;
+    if (ar) o_red = scr.reserve(sizeof(double) * size_t(S.N));
     if (S.op == MPI_OP_FORWARD) {
         S.fs = forward_split(S.T, g.nx, g.ny, sizeof(R), target);
-        S.as = adjoint_split(S.T, g.nx, g.ny, target);
+        S.as = adjoint_split(S.T, g.nx, g.ny, target, sizeof(R));
         o_geo = scr.reserve(geometry_bytes<R>(S.T, g.nx, g.ny));
         o_ord = scr.reserve(item_order_bytes<R>(&S.fs, &S.as));
         o_fp = scr.reserve(forward_partial_bytes<R>(S.fs, m.n_ch, S.T));
@@ -348,6 +379,7 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
         o_t2 = scr.reserve(sizeof(R) * S.N);
     }
     MPI_TRY(scr.allocate());
+    if (ar) S.red = scr.at<double>(o_red);
     if (S.op == MPI_OP_FORWARD) {
         S.geo = geometry_carve<R>(scr.at<char>(o_geo), S.T, g.nx, g.ny);
         S.fwd_part = scr.at<R>(o_fp);
@@ -418,6 +450,39 @@ int mpi_pnp_solve(const mpi_model *model, const mpi_grid_desc *grid, const mpi_t
     return dtype == MPI_F32
                ? pnp_impl<float>(m, g, traj, data, *opts, denoise, user, rho_out, info, as_stream(stream))
                : pnp_impl<double>(m, g, traj, data, *opts, denoise, user, rho_out, info, as_stream(stream));
+}
+
+int mpi_pnp_solve_sharded(const mpi_model *model, const mpi_grid_desc *grid, const mpi_traj *traj,
+                          mpi_dtype dtype, const void *data, const mpi_pnp_opts *opts,
+                          mpi_denoise_fn denoise, void *user, mpi_allreduce_fn allreduce,
+                          void *comm_user, void *rho_out, mpi_pnp_iter_info *info, void *stream)
+{
+    if (!allreduce) { set_error("allreduce is NULL"); return MPI_ERR_INVALID; }
+    if (!opts) { set_error("opts is NULL"); return MPI_ERR_INVALID; }
+    if (opts->op != MPI_OP_FORWARD) {
+        set_error("the sample-sharded solve needs opts->op = MPI_OP_FORWARD");
+        return MPI_ERR_INVALID;
+    }
+    MPI_TRY(check_model(model));
+    MPI_TRY(check_grid(grid));
+    MPI_TRY(check_dtype(dtype));
+    MPI_TRY(check_traj(traj));
+    if (opts->n_iter < 0 || opts->n_cg < 0 || !(opts->nu0 >= 0.0) || !std::isfinite(opts->nu0) ||
+        !(opts->clip_pct <= 100.0) || std::isnan(opts->clip_pct)) {
+        set_error("invalid PnP options (n_iter %d, n_cg %d, nu0 %g, clip_pct %g)", opts->n_iter,
+                  opts->n_cg, opts->nu0, opts->clip_pct);
+        return MPI_ERR_INVALID;
+    }
+    if (!rho_out || (!data && traj->T > 0)) {
+        set_error("data or rho_out is NULL");
+        return MPI_ERR_INVALID;
+    }
+    const ModelH m = to_host(model);
+    const GridH g = to_host(grid);
+    const cudaStream_t st = as_stream(stream);
+    return dtype == MPI_F32
+               ? pnp_impl<float>(m, g, traj, data, *opts, denoise, user, rho_out, info, st, allreduce, comm_user)
+               : pnp_impl<double>(m, g, traj, data, *opts, denoise, user, rho_out, info, st, allreduce, comm_user);
 }
 
 int mpi_conv(const mpi_model *model, const mpi_grid_desc *grid, mpi_dtype dtype, const void *in,

@@ -14,6 +14,8 @@ constexpr int kVecThreads = 256;
 // sums of r.r): small enough that a 128 x 128 problem spreads over 32 blocks.
 constexpr int kVecPerBlock = 512;
 constexpr int kStatThreads = 1024;
+// Values per iteration in a solve's device record (mpi_pnp_iter_info).
+constexpr int kInfoCols = 4;
 
 // Sum of `n` partials in a fixed order, computed by the whole block and
 // returned to every thread (deterministic: fixed strides, fixed tree).
@@ -92,7 +94,8 @@ __device__ double block_select(const double *__restrict__ x, int64_t N, int64_t 
 // do_clip is 0), rho1 = max(x, P) rounded to R, the population variance of
 // rho1 in two FP64 passes, and updates the PnP scalars: sigma, lambda = nu0
 // sigma^2 on the first iteration, nu = lambda / sigma^2 (kept if sigma = 0).
-// rr_part/nblk: partial sums of the final CG residual for info_row.
+// rr_part/nblk: partial sums of the final CG residual for info_row (sigma,
+// nu, residual norm, clip value: kInfoCols values).
 template <typename R>
 __device__ void outer_stats_block(int64_t N, const double *__restrict__ x, int do_clip, double pct,
                                   bool first, double nu0, double *__restrict__ scal,
@@ -140,6 +143,7 @@ __device__ void outer_stats_block(int64_t N, const double *__restrict__ x, int d
             info_row[0] = sigma;
             info_row[1] = scal[kScalNu];
             info_row[2] = sqrt(rr);
+            info_row[3] = P;
         }
     }
     __syncthreads();

@@ -5,7 +5,7 @@
 Builds the inputs of the workload (seeded synthetic), runs `--warmup`
 untimed applications and then `--reps` applications of the chosen operator
 (forward A, adjoint A^T, dbeta, conv, the Core Stage interpolation,
-its transpose and two Core Stage CG steps) in the chosen precision, timing each
+its transpose, two Core Stage CG steps, or one whole PnP reconstruction) in the chosen precision, timing each
 with CUDA events on the current stream, and prints one line per operator.
 It is the small, self-contained command to put under a profiler.
 """
@@ -27,7 +27,7 @@ from paper_2505_22797_gb300 import synthetic as syn  # noqa: E402
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--op", choices=["forward", "adjoint", "dbeta", "conv", "interp", "interp_T", "grid",
-                                     "all"], default="all")
+                                     "pnp", "all"], default="all")
     ap.add_argument("--workload", default="c2", help="c1, c2, c2_partial, c4, c5 or 3d")
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--warmup", type=int, default=2)
@@ -70,8 +70,18 @@ def main(argv=None):
             "interp": lambda: api.mpi_interp(g, r, v, field, s=s2),
             "interp_T": lambda: api.mpi_interp_adjoint(g, r, v, s, Ahat=field),
             "grid": lambda: api.mpi_grid(g, r, v, s, gamma=1e-7, max_iter=2, rel_tol=0.0),
+            # one whole reconstruction of the workload (its PnP iterations and CG
+            # steps); nu0 = 1e-3 of the mean diagonal of A^T A from 4 probes
+            "pnp": lambda: api.mpi_pnp_solve(m, g, r, v, s, cfg["n_it"], cfg["n_cg"], nu0,
+                                             clip_pct=cfg["clip_pct"], rho_out=out),
         }
-    names = list(ops) if args.op == "all" else [args.op]
+        gen = torch.Generator(device="cpu").manual_seed(7)
+        fro = 0.0
+        for _ in range(4):
+            z = (torch.randint(0, 2, tuple(c.shape), generator=gen) * 2 - 1).to("cuda", dt)
+            fro += float(torch.sum(api.mpi_forward(m, g, r, v, z).double() ** 2)) / 4
+        nu0 = 1e-3 * fro / c.numel()
+    names = [n for n in ops if n != "pnp"] if args.op == "all" else [args.op]
     pairs = c.numel() * r.shape[0]
     stream = torch.cuda.current_stream()
     for name in names:
@@ -80,6 +90,9 @@ def main(argv=None):
             fn()
         torch.cuda.synchronize()
         ms = []
+        # the timed repetitions run inside an NVTX range named after the op,
+        # for a profiler's range filter (ncu --nvtx --nvtx-include "<op>/")
+        torch.cuda.nvtx.range_push(name)
         for _ in range(args.reps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -88,8 +101,10 @@ def main(argv=None):
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+        torch.cuda.nvtx.range_pop()
         best = min(ms)
-        rate = "" if name in ("conv", "interp", "interp_T", "grid") else f"  {pairs / best / 1e6:.1f} Gpair/s"
+        apps = 2 * cfg["n_it"] * (cfg["n_cg"] + 1) + 1 if name == "pnp" else 1
+        rate = "" if name in ("conv", "interp", "interp_T", "grid") else f"  {apps * pairs / best / 1e6:.1f} Gpair/s"
         line = f"{args.workload} {args.dtype} {name}: best {best:.3f} ms of {args.reps}{rate}"
         if args.kernel and name in ("forward", "adjoint", "dbeta", "conv"):
             cls = {"forward": api.PROF_FORWARD, "adjoint": api.PROF_ADJOINT,
