@@ -248,3 +248,17 @@ def test_header_is_plain_c_and_links_from_c(tmp_path):
                          capture_output=True, text=True)
     assert res.returncode == 0, res.stderr
     assert subprocess.run([str(exe)]).returncode == 0
+
+
+def test_pipe_probe_validates_without_gpu():
+    """The pipe-rate probe rejects an unknown instruction kind, an occupancy
+    outside 1..8 blocks per SM and a zero iteration count on the host."""
+    from paper_2505_22797_gb300 import api, build
+    build.build()
+    lib = api.load()
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    for op, bps, it in ((7, 4, 16), (api.PROBE_RSQRT, 0, 16), (api.PROBE_RSQRT, 9, 16),
+                        (api.PROBE_FMA, 4, 0)):
+        st = lib.mpi_probe_pipe_rate(op, bps, it, ctypes.byref(rate), ctypes.byref(ms), None)
+        assert st == api.MPI_ERR_INVALID
+        assert b"probe" in lib.mpi_last_error_message()

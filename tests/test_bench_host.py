@@ -19,7 +19,7 @@ def test_reference_arm_prints_one_contract_line():
     """`--impl reference` times the FP64 oracle on the host cores and prints
     one JSON line with the keys of the benchmark contract."""
     res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
+                          "--steps", "1", "--warmup", "3", "--ref-samples", "2048"], capture_output=True, text=True,
                          timeout=600, cwd=ROOT)
     assert res.returncode == 0, res.stderr[-2000:]
     lines = [ln for ln in res.stdout.splitlines() if ln.strip()]
@@ -37,6 +37,9 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"] and "model" not in d["config"]
+    # both arms describe the workload with the same config
+    from paper_2505_22797_gb300 import synthetic as syn
+    assert d["config"] == json.loads(json.dumps(bench._config_desc(syn.config(bench.WORKLOAD))))
 
 
 def test_issue_bound_arithmetic():
@@ -112,7 +115,7 @@ def test_reference_arm_under_torchrun_prints_once():
     res = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
                           "--master-addr", "127.0.0.1", "--master-port", str(port),
                           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
-                          "--steps", "1", "--warmup", "3"],
+                          "--steps", "1", "--warmup", "3", "--ref-samples", "2048"],
                          capture_output=True, text=True, timeout=900, cwd=ROOT)
     assert res.returncode == 0, res.stderr[-3000:]
     lines = [ln for ln in res.stdout.splitlines() if ln.strip().startswith("{")]
@@ -121,3 +124,22 @@ def test_reference_arm_under_torchrun_prints_once():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     # rank 0 uses the host's cores although torchrun sets one thread per rank
     assert d["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
+
+
+def test_roofline_bases():
+    """Three bases of the pair kernels' roofline: the tier-weighted
+    algorithmic count with measured pipe rates, the plain closed-form count
+    (25 FP32 + 3 XU at 128 / 16 per SM per clock) and the executed
+    instruction count at the issue rate."""
+    rates = {"fma": 128.0, "rsqrt": 16.0, "ex2": 16.0, "rcp": 16.0}
+    b = bench.roofline_bases("k_adjoint", 1.0, 152, 2070.0, rates, 2000.0, executed=12.5)
+    # all pairs asymptotic: 9 FP32 + 1 XU -> issue bound 128 / 10 per SM per clock
+    assert b["tier_weighted"]["peak"] == pytest.approx(152 * 2070e6 * 12.8 / 1e9)
+    assert b["plain_closed_form"]["peak"] == pytest.approx(152 * 2070e6 * 5.12 / 1e9)
+    assert b["executed"]["peak"] == pytest.approx(152 * 2070e6 * 128 / 12.5 / 1e9)
+    assert b["tier_weighted"]["frac"] == pytest.approx(2000.0 / b["tier_weighted"]["peak"])
+    # all pairs in the closed form: 3 XU at 16 per clock bind before issue (20 / 128)
+    far = bench.roofline_bases("k_adjoint", 0.0, 1, 1000.0, rates, None)
+    assert far["tier_weighted"]["peak"] == pytest.approx(1000e6 / (3 / 16) / 1e9)
+    assert far["tier_weighted"]["frac"] is None and "executed" not in far
+    assert bench.xu_cycles_mixed(0.5, rates) == pytest.approx(0.5 * 3 / 16 + 0.5 / 16)

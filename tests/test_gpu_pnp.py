@@ -42,6 +42,7 @@ def test_pnp_forward_small(orc, dt, shape):
     for k in range(4):
         assert abs(info[k][0] - rec[k]["sigma"]) <= 10 * tol(dt) * rec[k]["sigma"]
         assert abs(info[k][1] - rec[k]["nu"]) <= 10 * tol(dt) * rec[k]["nu"]
+        assert abs(info[k][3] - rec[k]["clip"]) <= 10 * tol(dt) * (abs(rec[k]["clip"]) + rec[k]["sigma"])
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -72,6 +73,45 @@ def test_pnp_c1_full(orc, dt):
     spread = roundoff_spread(orc, m, g, r, v, s, cfg["n_it"], cfg["n_cg"], nu0, dt)
     print(f"c1 PnP 50x20 {dt}: rel-L2 vs oracle {err:.3e}, oracle round-off spread {spread:.3e}")
     assert err <= max(tol(dt), 10 * spread)
+
+
+@pytest.fixture(scope="module")
+def c2_well_posed(orc):
+    """The 128 x 128 spiral workload (every 8th sample of the 32-turn spiral,
+    8192 samples, velocities per sample of the subsampled trajectory) with the
+    oracle's Algorithm 1 at 3 PnP iterations of 5 CG steps.  Inputs are
+    rounded to FP32 once, so the one oracle run (and its per-iteration record)
+    serves both precisions of the GPU path."""
+    cfg = syn.config("c2")
+    m, g = cfg["model"], cfg["grid"]
+    f32 = torch.float32
+    r = rounded(cfg["r"][::8], f32)
+    v = rounded(cfg["v"][::8] * 8.0, f32)
+    c = rounded(cfg["c"], f32)
+    s = rounded(syn.add_noise(orc.forward(m, g, r, v, c), cfg["noise_frac"], cfg["noise_seed"]), f32)
+    nu0 = orc.nu0_from_frob2(orc.frob2(m, g, r, v), g["nx"] * g["ny"])
+    rec = []
+    want = _oracle_pnp(orc, m, g, r, v, s, 3, 5, nu0, clip=cfg["clip_pct"], record=rec)
+    return m, g, r, v, s, nu0, want, rec, cfg["clip_pct"]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_pnp_c2_grid_well_posed(c2_well_posed, dt):
+    """Algorithm 1 on the 128 x 128 grid (the percentile select and the
+    variance run over 16 384 values in one block) at the strict bar: the
+    reconstruction within 1e-5 (FP32) / 1e-12 (FP64) of the oracle, and per
+    iteration sigma, nu and the 5th-percentile clip value."""
+    m, g, r, v, s, nu0, want, rec, clip = c2_well_posed
+    got, info = api.mpi_pnp_solve(m, g, dev(r, dt), dev(v, dt), dev(s, dt), 3, 5, nu0, clip_pct=clip,
+                                  with_info=True)
+    err = rel_l2(host(got), want)
+    print(f"128x128 PnP 3x5 {dt}: rel-L2 vs oracle {err:.3e}")
+    assert err <= tol(dt)
+    for k in range(3):
+        sig, nu, _, pclip = info[k]
+        assert abs(sig - rec[k]["sigma"]) <= 10 * tol(dt) * rec[k]["sigma"]
+        assert abs(nu - rec[k]["nu"]) <= 10 * tol(dt) * rec[k]["nu"]
+        assert abs(pclip - rec[k]["clip"]) <= 10 * tol(dt) * (abs(rec[k]["clip"]) + rec[k]["sigma"])
 
 
 def test_pnp_no_clip_zero_iters_and_deterministic(orc):

@@ -65,3 +65,32 @@ def test_noalloc_rejects_oversize_before_launch():
     assert e.value.status == api.MPI_ERR_UNSUPPORTED
     assert "scratch" in str(e.value)
     assert float(s[0, 0]) == 5.0  # nothing was enqueued
+
+
+def test_noalloc_needs_no_allocation(monkeypatch):
+    """With every library allocation made to fail (the host-side injector
+    MPI_FAULT=alloc), mpi_forward reports MPI_ERR_NOMEM while
+    mpi_forward_noalloc still computes the same result: it never allocates."""
+    dt = torch.float32
+    cfg = syn.small(24, 20, 900, "lissajous", seed=5)
+    m, g = cfg["model"], cfg["grid"]
+    r, v, c = _inputs(cfg, dt, 6)
+    want = host(api.mpi_forward(m, g, r, v, c))
+    monkeypatch.setenv("MPI_FAULT", "alloc")
+    with pytest.raises(api.MPIError) as e:
+        api.mpi_forward(m, g, r, v, c)
+    assert e.value.status == api.MPI_ERR_NOMEM
+    got = host(api.mpi_forward_noalloc(m, g, r, v, c))
+    monkeypatch.delenv("MPI_FAULT")
+    assert rel_l2(got, want) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+def test_noalloc_against_oracle(orc, dt):
+    """One small case compared with the FP64 oracle's forward directly."""
+    cfg = syn.small(24, 20, 900, "spiral", seed=7)
+    m, g = cfg["model"], cfg["grid"]
+    r, v, c = _inputs(cfg, dt, 8)
+    want = orc.forward(m, g, *(host(t) for t in (r, v, c)))
+    got = host(api.mpi_forward_noalloc(m, g, r, v, c))
+    assert rel_l2(got, want) <= tol(dt)
