@@ -7,12 +7,22 @@ forward operator A in FP32 and FP64 CG vectors/inner products.  Every step
 applies A and A^T 4201 times; the metric counts (voxel, sample) pairs per
 second over the whole reconstruction.
 
+Beside the headline the line carries, each measured (not extrapolated): the
+accuracy of every result (FP32 against the FP64 GPU form, the FP64 form's
+own one-ulp spread, the oracle on the 32 x 32 workload, the distance to the
+phantom), whole FP64 reconstructions (32 x 32; a subset of the 64 frames),
+the full 64-frame batch at 50 iterations, forward+backward of the 256 x 256
+gradient workload, the 512 x 512 operators and a 10-iteration window of its
+reconstruction, the roofline of the operator kernels on three bases with the
+pipe rates measured on the GPU, and the oracle timed on the host's cores.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun every rank reconstructs its own copy of the workload on its
-own GPU (independent problems: weak scaling, no data-path collective); rank 0
-prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
-bounded sample of the same workload instead.
+Under torchrun the ranks share each reconstruction: the trajectory samples
+are split across them (one GPU each) and the partial adjoint images are summed
+with an NCCL all-reduce once per CG step (strong scaling: the work per step is
+fixed); rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead.
 """
 from __future__ import annotations
 
@@ -24,6 +34,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -47,6 +58,13 @@ sys.path.insert(0, ROOT)
 ALG_OPS = {"k_forward": {"far": (18, 3), "vfar": (12, 1)},
            "k_adjoint": {"far": (17, 3), "vfar": (9, 1)}}
 VFAR_U32 = 144.0
+# The plain closed-form count of a pair, every pair in the full form (no
+# asymptotic tier): ~25 FP32 operations and 3 XU operations (a square root or
+# rsqrt, one exp, one reciprocal), with the FP32 pipe at 128 and the XU pipe
+# at 16 results per SM per clock.
+PLAIN_OPS = (25, 3)
+PLAIN_RATES = {"fma": 128.0, "xu": 16.0}
+ISSUE_PER_CLK = 128.0  # 4 schedulers x one 32-lane warp instruction per clock
 
 
 def vfar_fraction(model, grid, r, stride=64):
@@ -65,17 +83,58 @@ def vfar_fraction(model, grid, r, stride=64):
     return n_far / (P.shape[0] * Rb.shape[0])
 
 
-def issue_bound_gpair(sm_count, sm_mhz, n_fp32, n_xu):
-    """Pairs per second (1e9 units) the SMs can issue when a pair costs n_fp32
-    FP32 and n_xu XU operations: per SM and clock at most 128 thread
-    instructions in all, 128 on the FP32 pipe and 32 on the XU pipe."""
-    per_clk = min(128.0 / (n_fp32 + n_xu), 128.0 / n_fp32, 32.0 / n_xu)
+def pipe_bound_gpair(sm_count, sm_mhz, n_fp32, xu_cycles, n_xu, fma_rate=128.0,
+                     issue=ISSUE_PER_CLK):
+    """Pairs per second (1e9 units) the SMs can sustain when a pair costs
+    n_fp32 FP32 and n_xu XU operations that keep the XU pipe busy xu_cycles
+    SM clocks per pair: the slowest of instruction issue (128 thread
+    instructions per SM per clock), the FP32 pipe (fma_rate lanes) and the XU
+    pipe."""
+    per_clk = 1.0 / max((n_fp32 + n_xu) / issue, n_fp32 / fma_rate, xu_cycles)
     return sm_count * sm_mhz * 1e6 * per_clk / 1e9
+
+
+def issue_bound_gpair(sm_count, sm_mhz, n_fp32, n_xu, xu_rate=32.0):
+    """pipe_bound_gpair with one XU rate for every XU operation."""
+    return pipe_bound_gpair(sm_count, sm_mhz, n_fp32, n_xu / xu_rate, n_xu)
 
 
 def mixed_ops(kernel, f_vfar):
     (a32, axu), (b32, bxu) = ALG_OPS[kernel]["far"], ALG_OPS[kernel]["vfar"]
     return (1 - f_vfar) * a32 + f_vfar * b32, (1 - f_vfar) * axu + f_vfar * bxu
+
+
+def xu_cycles_mixed(f_vfar, rates):
+    """XU clocks per pair of the tier mix: a far pair runs rsqrt, ex2 and rcp,
+    an asymptotic one rsqrt alone, each at its measured rate (results per SM
+    per clock)."""
+    far = 1.0 / rates["rsqrt"] + 1.0 / rates["ex2"] + 1.0 / rates["rcp"]
+    return (1.0 - f_vfar) * far + f_vfar / rates["rsqrt"]
+
+
+def roofline_bases(kernel, f_vfar, sm_count, sm_mhz, rates, achieved, executed=None):
+    """The roofline of one pair kernel on three bases (pairs/s, 1e9):
+    tier_weighted -- the algorithmic count of the asymptotic/closed-form mix
+    with the measured pipe rates (the headline fraction); plain_closed_form --
+    every pair in the full closed form, 25 FP32 + 3 XU, FP32 at 128 and XU at
+    16 per SM per clock (above 1 when most pairs take the asymptotic form);
+    executed -- the instructions per pair the kernel actually executes (ncu),
+    at the issue rate."""
+    n32, nxu = mixed_ops(kernel, f_vfar)
+    peak = pipe_bound_gpair(sm_count, sm_mhz, n32, xu_cycles_mixed(f_vfar, rates), nxu,
+                            fma_rate=rates["fma"])
+    plain = sm_count * sm_mhz * 1e6 * min(PLAIN_RATES["fma"] / PLAIN_OPS[0],
+                                          PLAIN_RATES["xu"] / PLAIN_OPS[1]) / 1e9
+    out = {"tier_weighted": {"ops_per_pair": [round(n32, 3), round(nxu, 4)], "peak": peak,
+                             "frac": achieved / peak if achieved else None},
+           "plain_closed_form": {"ops_per_pair": list(PLAIN_OPS), "peak": plain,
+                                 "frac": achieved / plain if achieved else None}}
+    if executed:
+        ex = sm_count * sm_mhz * 1e6 * ISSUE_PER_CLK / executed / 1e9
+        out["executed"] = {"instructions_per_pair": executed, "peak": ex,
+                           "frac": achieved / ex if achieved else None}
+    return out
+
 
 METRIC = "A/Aᵀ Gvoxel·samples/s and PnP recon/s, FP32 batched vs FP64 plain, ≤1e-5 err"
 UNIT = "Gvoxel·samples/s"
@@ -89,21 +148,48 @@ def _dist():
     return rank, world, local
 
 
-def _config_desc(cfg, extra=None):
+def _config_desc(cfg):
+    """The workload, identical on both arms."""
     g = cfg["grid"]
-    d = {"workload": f"{g['nx']}x{g['ny']} voxels, 24x24 mm, Archimedean spiral (32 turns), "
-                     f"T={cfg['r'].shape[0]} samples, 2 channels, {cfg['n_it']} PnP iterations x "
-                     f"{cfg['n_cg']} CG steps, 5x5 Gaussian denoiser, 5th-percentile trimming",
-         "grid": [g["nx"], g["ny"]], "samples": int(cfg["r"].shape[0]), "pnp_iterations": cfg["n_it"],
-         "cg_steps": cfg["n_cg"], "operator_applications_per_step": 2 * cfg["n_it"] * (cfg["n_cg"] + 1) + 1,
-         "l2": "256 MiB buffer written between timed steps (inputs ~1.5 MB fit in L2)"}
-    if extra:
-        d.update(extra)
-    return d
+    return {"workload": f"{g['nx']}x{g['ny']} voxels, 24x24 mm, Archimedean spiral (32 turns), "
+                        f"T={cfg['r'].shape[0]} samples, 2 channels, {cfg['n_it']} PnP iterations x "
+                        f"{cfg['n_cg']} CG steps, 5x5 Gaussian denoiser, 5th-percentile trimming",
+            "grid": [g["nx"], g["ny"]], "samples": int(cfg["r"].shape[0]), "pnp_iterations": cfg["n_it"],
+            "cg_steps": cfg["n_cg"], "operator_applications_per_step": 2 * cfg["n_it"] * (cfg["n_cg"] + 1) + 1,
+            "l2": "256 MiB buffer written between timed steps (inputs ~1.5 MB fit in L2)"}
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = np.linalg.norm(b.ravel())
+    return float(np.linalg.norm((a - b).ravel()) / d) if d > 0 else float(np.linalg.norm(a.ravel()))
+
+
+def ulp_perturbed(s, seed=1):
+    """s moved by one unit in the last place (FP64), in seeded directions."""
+    s = np.asarray(s, dtype=np.float64)
+    return s + np.random.default_rng(seed).choice([-1.0, 1.0], size=s.shape) * np.spacing(np.abs(s))
 
 
 # ---------------------------------------------------------------------------
-# Reference arm: the FP64 CPU oracle.
+# The FP64 oracle on the host cores.
+
+def oracle_ops_rate(oracle, m, g, r, v, c, s, threads=None, reps=3):
+    """Best of `reps` wall-clock runs of one oracle A and one A^T application
+    (pairs/s, 1e9), with `threads` host threads (None: all)."""
+    if threads is not None:
+        oracle.set_num_threads(threads)
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.forward(m, g, r, v, c)
+        oracle.adjoint(m, g, r, v, s)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    pairs = 2 * g["nx"] * g["ny"] * r.shape[0]
+    return pairs / best / 1e9, best, oracle.num_threads()
+
 
 def run_reference(args):
     rank, world, _ = _dist()
@@ -118,7 +204,8 @@ def run_reference(args):
     from paper_2505_22797_gb300 import synthetic as syn
     cfg = syn.config(WORKLOAD)
     m, g = cfg["model"], cfg["grid"]
-    T_sub = 32768
+    T = cfg["r"].shape[0]
+    T_sub = min(T, args.ref_samples) if args.ref_samples else T
     r, v = cfg["r"][:T_sub], cfg["v"][:T_sub]
     c = cfg["c"]
     s = np.random.default_rng(1).normal(size=(2, T_sub))
@@ -134,12 +221,14 @@ def run_reference(args):
             times.append(dt)
     tot = sum(times)
     value = pairs * len(times) / tot / 1e9
-    sample = (f"one A and one A^T application of the 128x128 workload on its first {T_sub} "
-              f"samples ({pairs:.3e} pairs) per step")
+    what = "all" if T_sub == T else f"the first {T_sub} of the"
+    sample = (f"one A and one A^T application of the 128x128 workload on {what} {T} samples "
+              f"({pairs:.3e} pairs) per step; a reconstruction applies them {2 * cfg['n_it'] * (cfg['n_cg'] + 1) + 1} "
+              "times")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config_desc(cfg, {"sample": sample}),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config_desc(cfg),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -230,6 +319,27 @@ def kernel_digest(read=None):
     return h.hexdigest()[:16]
 
 
+def _profile_entry(kernel):
+    """The committed ncu summary of `kernel` (profiles/traffic.json) if it
+    was captured on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    ent = d.get(kernel)
+    if not ent or ent.get("source_digest") != kernel_digest():
+        return None
+    return ent
+
+
+def _inst_per_pair(kernel):
+    """Thread instructions executed per pair (ncu smsp__inst_executed x 32 /
+    pairs) from the committed summary, if current."""
+    ent = _profile_entry(kernel)
+    return ent.get("inst_per_pair") if ent else None
+
+
 def _traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was captured on the current kernel sources; else None."""
@@ -244,18 +354,143 @@ def _traffic(kernel):
     return ent.get("dram_bytes_per_launch")
 
 
-def measure_batched(api, syn, dev, stream, n_it_timed=1):
-    """The 64-frame workload (grids 64^2..256^2, T in [8192, 131072], FP32,
-    20 CG steps per PnP iteration) through one batch plan: one untimed run
-    that autotunes and captures the graph, then one timed run of
-    `n_it_timed` PnP iterations (after A^T of the data).  The full 50-iteration
-    reconstruction rate is extrapolated from the per-iteration time."""
+def _event_ms(stream, fn):
+    """Device time (ms) of what fn enqueues on `stream`, and fn's result."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), res
+
+
+def _nu0(apply, shape, dev, dtype, seed, probes=4):
+    """nu0 = 1e-3 ||O||_F^2 / N, ||O||_F^2 from Rademacher probes E ||O z||^2."""
+    import torch
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    fro = 0.0
+    for _ in range(probes):
+        z = (torch.randint(0, 2, shape, generator=gen) * 2 - 1).to(dev, dtype)
+        fro += float(torch.sum(apply(z).double() ** 2)) / probes
+    return 1e-3 * fro / int(np.prod(shape))
+
+
+def pipe_rates(api):
+    """Measured FP32-FMA, MUFU (rsqrt, ex2, rcp) and FP64-FMA rates, thread
+    operations per SM per clock (median over SMs, SM clock cycles)."""
+    out = {}
+    for name, op, it in (("fma", api.PROBE_FMA, 8192), ("rsqrt", api.PROBE_RSQRT, 4096),
+                         ("ex2", api.PROBE_EX2, 4096), ("rcp", api.PROBE_RCP, 4096),
+                         ("dfma", api.PROBE_DFMA, 512)):
+        api.mpi_probe_pipe_rate(op, 8, 64)
+        out[name], _ = api.mpi_probe_pipe_rate(op, 8, it)
+    return out
+
+
+def measure_c2_accuracy(api, syn, cfg, dev, stream, rho_headline, nu0):
+    """Accuracy of the headline workload's reconstruction.  The FP32 path
+    against the FP64 GPU form on the same (FP32-rounded) inputs, over the
+    first 5 PnP iterations of the configured 20-CG-step loop, beside the FP64
+    form's own spread when only the data's rounding to FP32 changes (the
+    iteration is chaotic at round-off level at this setting: a change of that
+    size moves the result as far as the FP32 operator does); the same
+    comparison in the well-posed 5 x 5 setting; and every result's distance
+    to the phantom."""
+    import torch
+    f32, f64 = torch.float32, torch.float64
+    m, g = cfg["model"], cfg["grid"]
+    c64 = np.asarray(cfg["c"], dtype=np.float64)
+    r = torch.as_tensor(cfg["r"], dtype=f32, device=dev)
+    v = torch.as_tensor(cfg["v"], dtype=f32, device=dev)
+    c = torch.as_tensor(cfg["c"], dtype=f32, device=dev)
+    s_clean = api.mpi_forward(m, g, r, v, c)
+    s_np = syn.add_noise(s_clean.cpu().numpy().astype(np.float64), cfg["noise_frac"], cfg["noise_seed"])
+    s32 = torch.as_tensor(s_np, dtype=f32, device=dev)
+    r64, v64, s64 = r.double(), v.double(), s32.double()
+    clip = cfg["clip_pct"]
+    out = {"nu0": nu0}
+    for label, n_it, n_cg in (("configured_first_5_iterations", 5, cfg["n_cg"]), ("well_posed_5x5", 5, 5)):
+        ms64, rho64 = _event_ms(stream, lambda: api.mpi_pnp_solve(m, g, r64, v64, s64, n_it, n_cg, nu0,
+                                                                  clip_pct=clip))
+        ms32, rho32 = _event_ms(stream, lambda: api.mpi_pnp_solve(m, g, r, v, s32, n_it, n_cg, nu0,
+                                                                  clip_pct=clip))
+        h64, h32 = rho64.cpu().numpy(), rho32.cpu().numpy()
+        ent = {"pnp_iterations": n_it, "cg_steps": n_cg,
+               "fp32_vs_fp64_rel_l2": rel_l2(h32, h64),
+               "fp64_s": ms64 * 1e-3, "fp32_s": ms32 * 1e-3,
+               "fp64_rel_l2_vs_phantom": rel_l2(h64, c64), "fp32_rel_l2_vs_phantom": rel_l2(h32, c64)}
+        if n_cg == cfg["n_cg"]:
+            # the FP64 form on the data before its rounding to FP32: how far an
+            # input change of FP32-rounding size alone moves the reconstruction
+            su = torch.as_tensor(s_np, dtype=f64, device=dev)
+            rho64u = api.mpi_pnp_solve(m, g, r64, v64, su, n_it, n_cg, nu0, clip_pct=clip)
+            ent["fp64_spread_from_fp32_rounding_of_s_rel_l2"] = rel_l2(rho64u.cpu().numpy(), h64)
+        out[label] = ent
+    out["headline_fp32_rel_l2_vs_phantom"] = rel_l2(rho_headline, c64)
+    out["note"] = ("FP32 operator with FP64 CG vectors against the all-FP64 GPU form on identical inputs; "
+                   "the configured 20-step CG is not continuous at round-off level (condition number "
+                   "~1e5), so the FP64 form's own spread under the FP32 rounding of its input is the floor "
+                   "of that comparison; the well-posed setting shows the operator's own accuracy")
+    return out
+
+
+def measure_c1(api, syn, dev, stream):
+    """The 32 x 32 plain-method workload (Lissajous 17/16, T = 1632, 50 PnP
+    iterations x 20 CG steps), whole reconstructions measured in FP64 (the
+    plain form) and FP32, best of 3 each; errors between them and to the
+    phantom.  Returns the record and the inputs for the oracle comparison."""
+    import torch
+    f32, f64 = torch.float32, torch.float64
+    cfg = syn.config("c1")
+    m, g = cfg["model"], cfg["grid"]
+    r = torch.as_tensor(cfg["r"], dtype=f32, device=dev)
+    v = torch.as_tensor(cfg["v"], dtype=f32, device=dev)
+    r64, v64 = r.double(), v.double()
+    c64 = torch.as_tensor(np.asarray(cfg["c"], np.float32), dtype=f64, device=dev)
+    s_clean = api.mpi_forward(m, g, r64, v64, c64).cpu().numpy()
+    s_np = np.asarray(syn.add_noise(s_clean, cfg["noise_frac"], cfg["noise_seed"]), np.float32).astype(np.float64)
+    s64 = torch.as_tensor(s_np, dtype=f64, device=dev)
+    s32 = s64.float()
+    nu0 = _nu0(lambda z: api.mpi_forward(m, g, r64, v64, z), (g["ny"], g["nx"]), dev, f64, 7)
+    n_it, n_cg, clip = cfg["n_it"], cfg["n_cg"], cfg["clip_pct"]
+    apps = 2 * n_it * (n_cg + 1) + 1
+    pairs = apps * g["nx"] * g["ny"] * cfg["r"].shape[0]
+    res = {}
+    for name, args in (("fp64", (r64, v64, s64)), ("fp32", (r, v, s32))):
+        best, rho = None, None
+        for _ in range(3):
+            ms, rho = _event_ms(stream, lambda: api.mpi_pnp_solve(m, g, *args, n_it, n_cg, nu0, clip_pct=clip))
+            best = ms if best is None else min(best, ms)
+        res[name] = (best, rho.double().cpu().numpy())
+    phantom = np.asarray(cfg["c"], dtype=np.float64)
+    out = {"workload": "32x32, 24 mm, Lissajous 17/16, T=1632, 2 channels, 50 PnP x 20 CG, measured whole "
+                       "reconstructions", "pairs_per_recon": pairs, "nu0": nu0}
+    for name in ("fp64", "fp32"):
+        ms, rho = res[name]
+        out[name] = {"recon_s": ms * 1e-3, "recon_per_s": 1e3 / ms, "gpair_per_s": pairs / (ms * 1e-3) / 1e9,
+                     "rel_l2_vs_phantom": rel_l2(rho, phantom)}
+    out["fp32_vs_fp64_rel_l2"] = rel_l2(res["fp32"][1], res["fp64"][1])
+    inputs = {"model": m, "grid": g, "r": r64.cpu().numpy(), "v": v64.cpu().numpy(), "s": s_np, "nu0": nu0,
+              "n_it": n_it, "n_cg": n_cg, "clip": clip, "rho64": res["fp64"][1], "rho32": res["fp32"][1]}
+    return out, inputs
+
+
+def measure_batched(api, syn, dev, stream, n_fp64_frames=2):
+    """The 64-frame workload (grids 64^2..256^2, T in [8192, 131072], 50 PnP
+    iterations x 20 CG steps per frame, FP32 operator, FP64 CG) through one
+    batch plan, measured whole: a 1-iteration plan tunes the work split (kept
+    in a cache file), then the 50-iteration plan runs once, timed (its run
+    includes the one-time graph capture).  Beside it, the plain FP64 form
+    (single-frame solves) on the n_fp64_frames frames of fewest pairs, each a
+    whole 50 x 20 reconstruction, timed; the FP32 batched result of those
+    frames against them, and every result's distance to its phantom."""
     import torch
     frames = syn.batch_frames(64)
-    f32 = torch.float32
-    r, v, s_list, specs, nu0 = [], [], [], [], []
-    pairs_app = 0
-    gen = torch.Generator(device="cpu").manual_seed(11)
+    f32, f64 = torch.float32, torch.float64
+    r, v, s_list, specs, nu0, pairs_app = [], [], [], [], [], []
     for fr in frames:
         m, g = fr["model"], fr["grid"]
         rr = torch.as_tensor(fr["r"], dtype=f32, device=dev)
@@ -263,37 +498,190 @@ def measure_batched(api, syn, dev, stream, n_it_timed=1):
         cc = torch.as_tensor(fr["c"], dtype=f32, device=dev)
         sc = api.mpi_forward(m, g, rr, vv, cc)
         sn = syn.add_noise(sc.cpu().numpy().astype(np.float64), fr["noise_frac"], fr["noise_seed"])
-        z = (torch.randint(0, 2, (g["ny"], g["nx"]), generator=gen) * 2 - 1).to(dev, f32)
-        fro = float(torch.sum(api.mpi_forward(m, g, rr, vv, z).double() ** 2))
-        N = g["nx"] * g["ny"]
-        nu0.append(1e-3 * fro / N)
+        nu0.append(_nu0(lambda z: api.mpi_forward(m, g, rr, vv, z), (g["ny"], g["nx"]), dev, f32, 11))
         r.append(rr)
         v.append(vv)
         s_list.append(torch.as_tensor(sn, dtype=f32, device=dev))
         specs.append((m, g, rr.shape[0]))
-        pairs_app += N * rr.shape[0]
-    n_cg = frames[0]["n_cg"]
-    plan = api.BatchPlan(specs, nu0, n_it_timed, n_cg, flags=api.MPI_BATCH_AUTOTUNE)
-    rho = plan.run(r, v, s_list)  # tunes, captures
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    plan.run(r, v, s_list, rho_out=rho)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    info = plan.info()
-    plan.close()
-    apps = 2 * n_it_timed * (n_cg + 1) + 1
-    rate = pairs_app * apps / (ms * 1e-3)
-    n_it_full = frames[0]["n_it"]
-    recon_s = pairs_app * (2 * n_it_full * (n_cg + 1) + 1) / rate
-    return {"frames": len(frames), "pairs_per_application": pairs_app,
-            "timed": f"{n_it_timed} PnP iteration(s) x {n_cg} CG steps + A^T of the data, all frames",
-            "ms": ms, "gpair_per_s": rate / 1e9,
-            "recon_per_s_extrapolated": len(frames) / recon_s,
-            "batch_s_extrapolated": recon_s, "plan": info}
+        pairs_app.append(g["nx"] * g["ny"] * rr.shape[0])
+    n_it, n_cg = frames[0]["n_it"], frames[0]["n_cg"]
+    apps = 2 * n_it * (n_cg + 1) + 1
+    cache = os.path.join(tempfile.gettempdir(), f"mpi_bench_tune_{os.getpid()}.txt")
+    old = os.environ.get("MPI_AUTOTUNE_CACHE")
+    os.environ["MPI_AUTOTUNE_CACHE"] = cache
+    try:
+        tune = api.BatchPlan(specs, nu0, 1, n_cg, flags=api.MPI_BATCH_AUTOTUNE)
+        tune.run(r, v, s_list)
+        torch.cuda.synchronize()
+        tune.close()
+        plan = api.BatchPlan(specs, nu0, n_it, n_cg, flags=api.MPI_BATCH_AUTOTUNE)
+        ms, rho = _event_ms(stream, lambda: plan.run(r, v, s_list))
+        info = plan.info()
+        plan.close()
+    finally:
+        if old is None:
+            os.environ.pop("MPI_AUTOTUNE_CACHE", None)
+        else:
+            os.environ["MPI_AUTOTUNE_CACHE"] = old
+        try:
+            os.remove(cache)
+        except OSError:
+            pass
+    total_pairs = sum(pairs_app) * apps
+    phantoms = [np.asarray(fr["c"], np.float64) for fr in frames]
+    dist32 = [rel_l2(rho[f].cpu().numpy(), phantoms[f]) for f in range(len(frames))]
+    out = {"frames": len(frames), "pnp_iterations": n_it, "cg_steps": n_cg,
+           "timed": "whole 64-frame reconstruction (A^T of the data, 50 PnP iterations x 20 CG steps), one run",
+           "batch_s": ms * 1e-3, "recon_per_s": len(frames) / (ms * 1e-3),
+           "gpair_per_s": total_pairs / (ms * 1e-3) / 1e9, "pairs": total_pairs,
+           "rel_l2_vs_phantom_median": float(np.median(dist32)), "plan": info}
+    # the plain FP64 form on the frames of fewest pairs
+    pick = sorted(range(len(frames)), key=lambda f: pairs_app[f])[:n_fp64_frames]
+    sub, t64, p64 = [], 0.0, 0
+    for f in pick:
+        m, g = frames[f]["model"], frames[f]["grid"]
+        ms64, rho64 = _event_ms(stream, lambda: api.mpi_pnp_solve(m, g, r[f].double(), v[f].double(),
+                                                                  s_list[f].double(), n_it, n_cg, nu0[f]))
+        h64 = rho64.cpu().numpy()
+        t64 += ms64 * 1e-3
+        p64 += pairs_app[f] * apps
+        sub.append({"frame": f, "grid": [g["nx"], g["ny"]], "samples": int(r[f].shape[0]),
+                    "fp64_recon_s": ms64 * 1e-3,
+                    "fp32_batched_vs_fp64_rel_l2": rel_l2(rho[f].cpu().numpy(), h64),
+                    "fp64_rel_l2_vs_phantom": rel_l2(h64, phantoms[f]),
+                    "fp32_batched_rel_l2_vs_phantom": dist32[f]})
+    out["fp64_plain_subset"] = {
+        "frames": sub, "recon_per_s": len(pick) / t64, "gpair_per_s": p64 / t64 / 1e9,
+        "note": ("all-FP64 single-frame solves (the plain form), whole 50 x 20 reconstructions of the "
+                 f"{len(pick)} frames of fewest pairs; the 64 frames take "
+                 f"{total_pairs / (p64 / t64):.0f} s at this measured FP64 pair rate")}
+    return out
+
+
+def measure_c4(api, syn, dev, stream):
+    """Gradients on the 256 x 256 / 262 144-sample workload: forward plus
+    backward (dL/dc through A^T, dL/dbeta through the beta-derivative kernel)
+    of L = 1/2 ||A(c; beta) - s||^2 through torch.autograd, FP32 timed (mean
+    of 3 after one warm-up), FP64 once; the FP32 gradients against FP64."""
+    import torch
+    from paper_2505_22797_gb300.autograd import mpi_forward_autograd
+    cfg = syn.config("c4")
+    m, g = cfg["model"], cfg["grid"]
+    res = {}
+    for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        r = torch.as_tensor(np.asarray(cfg["r"], np.float32), dtype=dt, device=dev)
+        v = torch.as_tensor(np.asarray(cfg["v"], np.float32), dtype=dt, device=dev)
+        c0 = torch.as_tensor(np.asarray(cfg["c"], np.float32), dtype=dt, device=dev)
+        s = torch.as_tensor(np.asarray(np.random.default_rng(204).normal(size=(2, r.shape[0])) * 0.1,
+                                       np.float32), dtype=dt, device=dev)
+
+        def step():
+            C = c0.clone().requires_grad_(True)
+            beta = torch.tensor(m["beta"], dtype=dt, device=dev, requires_grad=True)
+            L = 0.5 * torch.sum((mpi_forward_autograd(C, beta, m, g, r, v) - s) ** 2)
+            L.backward()
+            return C.grad, beta.grad
+        reps = 3 if name == "fp32" else 1
+        step()
+        torch.cuda.synchronize()
+        ms, gr = 0.0, None
+        for _ in range(reps):
+            t, gr = _event_ms(stream, step)
+            ms += t / reps
+        res[name] = (ms, gr[0].double().cpu().numpy(), float(gr[1]))
+    pairs = 3 * g["nx"] * g["ny"] * cfg["r"].shape[0]
+    return {"workload": "256x256, 24 mm, Lissajous 17/16, T=262144, 2 channels; loss 1/2||A(c;beta)-s||^2",
+            "fp32_fwd_bwd_ms": res["fp32"][0], "fp64_fwd_bwd_ms": res["fp64"][0],
+            "fp32_gpair_per_s": pairs / (res["fp32"][0] * 1e-3) / 1e9,
+            "pairs_per_step": pairs,
+            "dL_dc_fp32_vs_fp64_rel_l2": rel_l2(res["fp32"][1], res["fp64"][1]),
+            "dL_dbeta_fp32_vs_fp64_rel": abs(res["fp32"][2] - res["fp64"][2]) / abs(res["fp64"][2])}
+
+
+def measure_c5(api, syn, dev, stream, n_it_window=10):
+    """The 512 x 512 / 2^20-sample workload: kernel-only rates of A and A^T
+    (library event timing, mean of 2) and a measured window of the first
+    n_it_window PnP iterations (20 CG steps each) of its reconstruction, FP32;
+    the whole 200-iteration reconstruction time follows from the window's
+    measured rate (stated as such)."""
+    import torch
+    f32 = torch.float32
+    cfg = syn.config("c5")
+    m, g = cfg["model"], cfg["grid"]
+    r = torch.as_tensor(cfg["r"], dtype=f32, device=dev)
+    v = torch.as_tensor(cfg["v"], dtype=f32, device=dev)
+    c = torch.as_tensor(cfg["c"], dtype=f32, device=dev)
+    N, T = g["nx"] * g["ny"], cfg["r"].shape[0]
+    s_clean = api.mpi_forward(m, g, r, v, c)
+    s = torch.as_tensor(syn.add_noise(s_clean.cpu().numpy().astype(np.float64), cfg["noise_frac"],
+                                      cfg["noise_seed"]), dtype=f32, device=dev)
+    out = {"workload": "512x512, 48 mm, Lissajous + 1.5 mm at 25x, T=1048576, 2 channels"}
+    cout = torch.empty_like(c)
+    for name, cls, fn in (("k_forward", api.PROF_FORWARD, lambda: api.mpi_forward(m, g, r, v, c, s=s_clean)),
+                          ("k_adjoint", api.PROF_ADJOINT, lambda: api.mpi_adjoint(m, g, r, v, s, c_out=cout))):
+        fn()
+        torch.cuda.synchronize()
+        api.mpi_profile_enable(True)
+        for _ in range(2):
+            fn()
+        n, tot = api.mpi_profile_read(cls)
+        api.mpi_profile_enable(False)
+        out[name] = {"avg_launch_ms": tot / n, "gpair_per_s": N * T / (tot / n * 1e-3) / 1e9}
+    nu0 = _nu0(lambda z: api.mpi_forward(m, g, r, v, z), (g["ny"], g["nx"]), dev, f32, 7, probes=2)
+    n_cg = cfg["n_cg"]
+    ms, rho = _event_ms(stream, lambda: api.mpi_pnp_solve(m, g, r, v, s, n_it_window, n_cg, nu0,
+                                                           clip_pct=cfg["clip_pct"]))
+    apps = 2 * n_it_window * (n_cg + 1) + 1
+    rate = apps * N * T / (ms * 1e-3)
+    full_apps = 2 * cfg["n_it"] * (n_cg + 1) + 1
+    out["pnp_window"] = {"pnp_iterations": n_it_window, "cg_steps": n_cg, "s": ms * 1e-3,
+                         "gpair_per_s": rate / 1e9,
+                         "recon_s_at_window_rate": full_apps * N * T / rate,
+                         "note": f"whole reconstruction = {cfg['n_it']} iterations; its time is the "
+                                 "measured window's pair rate applied to its pair count"}
+    return out
+
+
+def cpu_baseline_leg(cfg, c1_inputs):
+    """The FP64 oracle on the host cores: one A and one A^T application of the
+    headline workload (all cores, best of 3), the same on one core (best of 3,
+    on every 32nd sample), and whole oracle reconstructions of the 32 x 32
+    workload (the configured 50 x 20 run, and again with the data moved by
+    one ulp) with the GPU results' errors against them."""
+    from oracle import oracle
+    oracle.build()
+    m, g = cfg["model"], cfg["grid"]
+    T = cfg["r"].shape[0]
+    s = np.random.default_rng(1).normal(size=(2, T))
+    all_cores = os.cpu_count() or 1
+    v_all, dt_all, n_all = oracle_ops_rate(oracle, m, g, cfg["r"], cfg["v"], cfg["c"], s, threads=all_cores)
+    sub = slice(0, T, 32)
+    v_one, dt_one, _ = oracle_ops_rate(oracle, m, g, cfg["r"][sub], cfg["v"][sub], cfg["c"], s[:, sub], threads=1)
+    oracle.set_num_threads(all_cores)
+    out = {"value": v_all, "unit": UNIT, "cores": n_all, "kind": "oracle",
+           "sample": (f"one A and one A^T application of the workload ({T} samples, "
+                      f"{2 * g['nx'] * g['ny'] * T:.3e} pairs), best of 3: {dt_all:.2f} s"),
+           "single_core": {"value": v_one, "unit": UNIT, "cores": 1,
+                           "sample": f"the same on every 32nd sample ({T // 32} samples), best of 3: {dt_one:.2f} s"}}
+    if c1_inputs:
+        d = c1_inputs
+        mm, gg = d["model"], d["grid"]
+
+        def recon(sdata):
+            return oracle.pnp(lambda x: oracle.forward(mm, gg, d["r"], d["v"], x),
+                              lambda y: oracle.adjoint(mm, gg, d["r"], d["v"], y), sdata,
+                              (gg["ny"], gg["nx"]), d["n_it"], d["n_cg"], d["nu0"], clip_pct=d["clip"])
+        t0 = time.perf_counter()
+        want = recon(d["s"])
+        t_rec = time.perf_counter() - t0
+        pert = recon(ulp_perturbed(d["s"]))
+        out["c1_oracle"] = {"recon_s": t_rec, "cores": oracle.num_threads(),
+                            "gpu_fp64_vs_oracle_rel_l2": rel_l2(d["rho64"], want),
+                            "gpu_fp32_vs_oracle_rel_l2": rel_l2(d["rho32"], want),
+                            "oracle_one_ulp_spread_rel_l2": rel_l2(pert, want),
+                            "note": "whole 50 x 20 reconstructions of the 32x32 workload by the oracle "
+                                    "on the same inputs as the GPU forms"}
+    return out
 
 
 def measure_paper_pipeline(api, syn, dev, stream):
@@ -574,22 +962,34 @@ def run_ours(args):
     s_clean = api.mpi_forward(m, g, r, v, c)
     s_np = syn.add_noise(s_clean.cpu().numpy().astype(np.float64), cfg["noise_frac"], cfg["noise_seed"])
     s = torch.as_tensor(s_np, dtype=f32, device=dev)
-    # nu0 = 1e-3 ||A||_F^2 / N with ||A||_F^2 from 4 Rademacher probes (E ||A z||^2).
-    gen = torch.Generator(device="cpu").manual_seed(7)
-    fro = 0.0
-    for _ in range(4):
-        z = (torch.randint(0, 2, (g["ny"], g["nx"]), generator=gen) * 2 - 1).to(dev, f32)
-        fro += float(torch.sum(api.mpi_forward(m, g, r, v, z).double() ** 2)) / 4
-    nu0 = 1e-3 * fro / N
+    nu0 = _nu0(lambda z: api.mpi_forward(m, g, r, v, z), (g["ny"], g["nx"]), dev, f32, 7)
     rho = torch.empty((g["ny"], g["nx"]), dtype=f32, device=dev)
     apps = 2 * n_it * (n_cg + 1) + 1
     pairs_step = apps * N * T
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    from paper_2505_22797_gb300 import multirank, sharded
+
+    if world > 1:
+        # One reconstruction split across the ranks by trajectory samples: each
+        # rank holds a contiguous slice; the partial adjoint images are summed
+        # with an NCCL all-reduce (once for A^T s, once per CG step).
+        nu0_t = torch.tensor([nu0], dtype=torch.float64, device=dev)
+        dist.broadcast(nu0_t, 0)
+        nu0 = float(nu0_t.item())
+        allreduce = sharded.dist_allreduce()
+        r_p, v_p, s_p = sharded.shard_inputs(r, v, s, rank, world)
+
+        def solve(rr, vv, ss):
+            api.mpi_pnp_solve_sharded(m, g, rr, vv, ss, n_it, n_cg, nu0, allreduce,
+                                      clip_pct=cfg["clip_pct"], rho_out=rho)
+    else:
+        r_p, v_p, s_p = r, v, s
+
+        def solve(rr, vv, ss):
+            api.mpi_pnp_solve(m, g, rr, vv, ss, n_it, n_cg, nu0, clip_pct=cfg["clip_pct"], rho_out=rho)
 
     def step():
-        api.mpi_pnp_solve(m, g, r, v, s, n_it, n_cg, nu0, clip_pct=cfg["clip_pct"], rho_out=rho)
-
-    from paper_2505_22797_gb300 import multirank
+        solve(r_p, v_p, s_p)
 
     def barrier():
         multirank.barrier()
@@ -604,7 +1004,6 @@ def run_ours(args):
     uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
     gpu_id = f"GPU-{uuid}" if uuid is not None else str(local)
     launches0 = api.mpi_kernel_launches()
-    api.mpi_profile_enable(True)
     step_ms = []
     with ClockSampler(gpu_id) as clocks:
         barrier()
@@ -619,40 +1018,47 @@ def run_ours(args):
             step_ms.append(e0.elapsed_time(e1))
         barrier()
     launches = api.mpi_kernel_launches() - launches0
-    prof = {k: api.mpi_profile_read(k) for k in (api.PROF_FORWARD, api.PROF_ADJOINT)}
-    api.mpi_profile_enable(False)
-    # every rank reconstructs its own problem: all ranks' units over the
-    # slowest rank's time
+    rho_headline = rho.double().cpu().numpy()
+    # the ranks share one reconstruction per step: its pairs over the slowest
+    # rank's time
     local_s = sum(step_ms) * 1e-3
     total_ms = multirank.max_over_ranks(local_s) * 1e3
-    value = multirank.job_rate(pairs_step * args.steps, local_s) / 1e9
-    recon_per_s = multirank.job_rate(args.steps, local_s)
+    value = pairs_step * args.steps / (total_ms * 1e-3) / 1e9
+    recon_per_s = args.steps / (total_ms * 1e-3)
 
-    # --- end to end through the public API, host buffers ------------------------
-    h_r = torch.as_tensor(cfg["r"], dtype=f32).pin_memory()
-    h_v = torch.as_tensor(cfg["v"], dtype=f32).pin_memory()
-    h_s = s.cpu().pin_memory()
+    # --- per-kernel timing: one more step with the library's event timing ---
+    flush.fill_(1)
+    api.mpi_profile_enable(True)
+    prof_ms, _ = _event_ms(stream, step)
+    prof = {k: api.mpi_profile_read(k) for k in (api.PROF_FORWARD, api.PROF_ADJOINT)}
+    api.mpi_profile_enable(False)
+
+    # --- end to end through the public API, host buffers, same step count --------
+    h_r = r_p.cpu().pin_memory()
+    h_v = v_p.cpu().pin_memory()
+    h_s = s_p.cpu().pin_memory()
     h_rho = torch.empty((g["ny"], g["nx"]), dtype=f32).pin_memory()
-    d_r, d_v, d_s = torch.empty_like(r), torch.empty_like(v), torch.empty_like(s)
+    d_r, d_v, d_s = torch.empty_like(r_p), torch.empty_like(v_p), torch.empty_like(s_p)
     e2e_ms = []
-    barrier()
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        d_r.copy_(h_r, non_blocking=True)
-        d_v.copy_(h_v, non_blocking=True)
-        d_s.copy_(h_s, non_blocking=True)
-        api.mpi_pnp_solve(m, g, d_r, d_v, d_s, n_it, n_cg, nu0, clip_pct=cfg["clip_pct"], rho_out=rho)
-        h_rho.copy_(rho, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    barrier()
+    with ClockSampler(gpu_id) as clocks_e2e:
+        barrier()
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d_r.copy_(h_r, non_blocking=True)
+            d_v.copy_(h_v, non_blocking=True)
+            d_s.copy_(h_s, non_blocking=True)
+            solve(d_r, d_v, d_s)
+            h_rho.copy_(rho, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        barrier()
     e2e_local_s = sum(e2e_ms) * 1e-3
     e2e_tot = multirank.max_over_ranks(e2e_local_s) * 1e3
-    e2e_value = multirank.job_rate(pairs_step * len(e2e_ms), e2e_local_s) / 1e9
+    e2e_value = pairs_step * len(e2e_ms) / (e2e_tot * 1e-3) / 1e9
     h2d = (h_r.numel() + h_v.numel() + h_s.numel()) * 4
     d2h = h_rho.numel() * 4
 
@@ -671,95 +1077,77 @@ def run_ours(args):
         pass
     clk = clocks.summary()
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    sm_run = clk.get("sm_mhz") or sm_max
+    rates = pipe_rates(api)
     (nf, fms), (na, ams) = prof[api.PROF_FORWARD], prof[api.PROF_ADJOINT]
-    dom, n_l, ms_l = ("k_forward", nf, fms) if fms >= ams else ("k_adjoint", na, ams)
-    # Algorithmic instructions per pair of the closed-form branch (FP32 ops,
-    # XU ops): every one occupies an issue slot (128 thread-instructions per
-    # SM per cycle), FP32 ops the FP32 pipe (128 lanes), XU ops the XU pipe
-    # (32 results per SM per cycle on GB300, inferred from ncu's pct-of-peak).
     f_vfar = vfar_fraction(m, g, cfg["r"])
-    n_fp32, n_xu = mixed_ops(dom, f_vfar)
-    peak_gpair = issue_bound_gpair(sm_count, sm_max, n_fp32, n_xu)
-    achieved = (N * T) / (ms_l / n_l * 1e-3) / 1e9 if n_l else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gpair, "unit": "Gpair/s",
-                "frac": achieved / peak_gpair if achieved else None, "traffic": _traffic(dom),
-                "kernel": dom, "launches": n_l, "avg_launch_ms": ms_l / n_l if n_l else None,
-                "peak_basis": (f"issue bound: {sm_count} SMs x {sm_max:.0f} MHz x 128 thread-instructions"
-                               f"/clk / ({n_fp32:.2f} FP32 + {n_xu:.3f} XU algorithmic ops per pair: "
-                               f"{f_vfar:.4f} of the pairs in the asymptotic regime u >= 144)"),
-                "other": {"k_forward_avg_ms": fms / nf if nf else None,
-                          "k_adjoint_avg_ms": ams / na if na else None,
-                          "share_of_step": (fms + ams) / total_ms if total_ms else None}}
+    kern = {}
+    for name, n_l, ms_l in (("k_forward", nf, fms), ("k_adjoint", na, ams)):
+        ach = (N * T) / (ms_l / n_l * 1e-3) / 1e9 if n_l else None
+        kern[name] = {"avg_launch_ms": ms_l / n_l if n_l else None, "launches": n_l, "achieved": ach,
+                      "bases": roofline_bases(name, f_vfar, sm_count, sm_run, rates, ach,
+                                              _inst_per_pair(name))}
+    dom = "k_forward" if fms >= ams else "k_adjoint"
+    kd = kern[dom]
+    tw = kd["bases"]["tier_weighted"]
+    roofline = {"bound": "alu", "achieved": kd["achieved"], "peak": tw["peak"], "unit": "Gpair/s",
+                "frac": tw["frac"], "traffic": _traffic(dom), "kernel": dom, "launches": kd["launches"],
+                "avg_launch_ms": kd["avg_launch_ms"],
+                "peak_basis": (f"pipe bound at the sampled clock: {sm_count} SMs x {sm_run:.0f} MHz x "
+                               f"1/max(issue 128/clk, FP32 {rates['fma']:.1f}/clk, XU rsqrt {rates['rsqrt']:.1f} "
+                               f"ex2 {rates['ex2']:.1f} rcp {rates['rcp']:.1f}/clk per SM, measured) over "
+                               f"{tw['ops_per_pair'][0]:.2f} FP32 + {tw['ops_per_pair'][1]:.3f} XU algorithmic "
+                               f"ops per pair ({f_vfar:.4f} of the pairs in the asymptotic regime u >= 144)"),
+                "bases": kd["bases"], "pipe_rates_per_sm_clk": rates, "kernels": kern,
+                "share_of_step": (fms + ams) / prof_ms if prof_ms else None,
+                "profiled_step_ms": prof_ms}
 
-    # --- FP64 plain form (one A and one A^T application) -----------------------
-    f64 = torch.float64
-    r64, v64, c64 = r.double(), v.double(), c.double()
-    s64 = api.mpi_forward(m, g, r64, v64, c64)
-    api.mpi_adjoint(m, g, r64, v64, s64)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    api.mpi_forward(m, g, r64, v64, c64, s=s64)
-    api.mpi_adjoint(m, g, r64, v64, s64)
-    e1.record(stream)
-    e1.synchronize()
-    f64_ms = e0.elapsed_time(e1)
-    f64_rate = 2 * N * T / (f64_ms * 1e-3) / 1e9
-    fp64_plain = {"gpair_per_s": f64_rate, "recon_s_extrapolated": pairs_step / (f64_rate * 1e9),
-                  "note": "one FP64 A and one FP64 A^T application, extrapolated to the "
-                          f"{apps} applications of a reconstruction"}
+    # --- further legs (rank 0, N = 1) -----------------------------------------
+    extra = {}
+    c1_inputs = None
 
-    # --- batched form: 64 frames of uneven size in one plan ----------------------
-    batched = None
+    def leg(name, fn):
+        """Run one secondary measurement with its own clock record."""
+        with ClockSampler(gpu_id) as ck:
+            res = fn()
+        out = res[0] if isinstance(res, tuple) else res
+        if isinstance(out, dict):
+            out["clocks"] = ck.summary()
+        extra[name] = out
+        return res
+
     if world == 1 and not args.no_batch:
-        batched = measure_batched(api, syn, dev, stream)
+        leg("accuracy_c2", lambda: measure_c2_accuracy(api, syn, cfg, dev, stream, rho_headline, nu0))
+        _, c1_inputs = leg("plain_fp64_c1", lambda: measure_c1(api, syn, dev, stream))
+        leg("batched", lambda: measure_batched(api, syn, dev, stream))
+        leg("gradients_c4", lambda: measure_c4(api, syn, dev, stream))
+        leg("large_c5", lambda: measure_c5(api, syn, dev, stream))
+        leg("paper_pipeline", lambda: measure_paper_pipeline(api, syn, dev, stream))
+        leg("transfer_correction", lambda: measure_transfer(api, syn, dev, stream, s))
+        leg("ffp3d", lambda: measure_ffp3d(api, syn, dev, stream, sm_count, sm_max))
 
-    # --- the paper's own two-stage pipeline, for context ------------------------
-    paper_pipeline = None
-    if world == 1 and not args.no_batch:
-        paper_pipeline = measure_paper_pipeline(api, syn, dev, stream)
-
-    # --- preprocessing: transfer-function correction --------------------------
-    transfer = None
-    if world == 1 and not args.no_batch:
-        transfer = measure_transfer(api, syn, dev, stream, s)
-
-    # --- the three-dimensional FFP --------------------------------------------
-    ffp3d = None
-    if world == 1 and not args.no_batch:
-        ffp3d = measure_ffp3d(api, syn, dev, stream, sm_count, sm_max)
-
-    # --- CPU baseline: the oracle on a bounded sample -----------------------
+    # --- CPU baseline: the oracle on the host's cores -------------------------
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        from oracle import oracle
-        oracle.build()
-        T_sub = T
-        rr_, vv_ = cfg["r"][:T_sub], cfg["v"][:T_sub]
-        ss_ = np.random.default_rng(1).normal(size=(2, T_sub))
-        t0 = time.perf_counter()
-        oracle.forward(m, g, rr_, vv_, cfg["c"])
-        oracle.adjoint(m, g, rr_, vv_, ss_)
-        dt = time.perf_counter() - t0
-        cpu = {"value": 2 * N * T_sub / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
-               "kind": "oracle",
-               "sample": f"one A and one A^T application of the workload ({T_sub} samples, "
-                         f"{2 * N * T_sub:.3e} pairs, {dt:.1f} s)"}
+        cpu = cpu_baseline_leg(cfg, c1_inputs)
 
+    med = statistics.median(step_ms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config_desc(cfg, {"precision": "FP32 operator, FP64 CG vectors and inner products",
-                                         "nu0": nu0}),
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config_desc(cfg),
+            "parallelism": (f"samples split across {world} GPUs, NCCL all-reduce of the partial adjoint "
+                            "image (N FP64 values) once per CG step" if world > 1 else "1 GPU"),
+            "precision": "FP32 operator, FP64 CG vectors and inner products", "nu0": nu0,
             "recon_per_s": recon_per_s,
+            "step_ms": {"median": med, "min": min(step_ms), "max": max(step_ms)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": len(e2e_ms),
-                    "recon_per_s": len(e2e_ms) * world / (e2e_tot * 1e-3)},
+                    "recon_per_s": len(e2e_ms) / (e2e_tot * 1e-3),
+                    "step_ms": {"median": statistics.median(e2e_ms), "min": min(e2e_ms), "max": max(e2e_ms)},
+                    "clocks": clocks_e2e.summary()},
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-            "fp64_plain": fp64_plain, "batched": batched, "paper_pipeline": paper_pipeline,
-            "ffp3d": ffp3d, "transfer_correction": transfer,
-            "clocks": clk, "impl": "ours"}
+            **extra, "clocks": clk, "impl": "ours"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -774,7 +1162,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
-                    help="skip the secondary measurements (64-frame batch, paper pipeline, 3-D FFP)")
+                    help="skip the secondary measurements (accuracy, 32x32 FP64, 64-frame batch, "
+                         "gradients, 512x512, paper pipeline, 3-D FFP)")
+    ap.add_argument("--ref-samples", type=int, default=0,
+                    help="reference arm: time the oracle on the first N samples (default: all)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
