@@ -418,8 +418,15 @@ def measure_c2_accuracy(api, syn, cfg, dev, stream, rho_headline, nu0):
         ms32, rho32 = _event_ms(stream, lambda: api.mpi_pnp_solve(m, g, r, v, s32, n_it, n_cg, nu0,
                                                                   clip_pct=clip))
         h64, h32 = rho64.cpu().numpy(), rho32.cpu().numpy()
+        # the FP32 path's own spread: the same run with the data moved by one
+        # FP32 ulp (its Krylov iteration amplifies any perturbation alike)
+        s32p = torch.as_tensor(np.asarray(s32.cpu().numpy(), np.float32) +
+                               np.random.default_rng(3).choice([-1.0, 1.0], size=s_np.shape).astype(np.float32) *
+                               np.spacing(np.abs(s32.cpu().numpy())), dtype=f32, device=dev)
+        rho32p = api.mpi_pnp_solve(m, g, r, v, s32p, n_it, n_cg, nu0, clip_pct=clip)
         ent = {"pnp_iterations": n_it, "cg_steps": n_cg,
                "fp32_vs_fp64_rel_l2": rel_l2(h32, h64),
+               "fp32_one_ulp_spread_rel_l2": rel_l2(rho32p.cpu().numpy(), h32),
                "fp64_s": ms64 * 1e-3, "fp32_s": ms32 * 1e-3,
                "fp64_rel_l2_vs_phantom": rel_l2(h64, c64), "fp32_rel_l2_vs_phantom": rel_l2(h32, c64)}
         if n_cg == cfg["n_cg"]:

@@ -217,7 +217,7 @@ static int adjoint_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, con
                         cudaStream_t st)
 {
     const int64_t T = tr->T;
-    AdjSplit sp = adjoint_split(T, g.nx, g.ny, default_target_items());
+    AdjSplit sp = adjoint_split(T, g.nx, g.ny, default_target_items(), sizeof(R));
     Scratch scr(st);
     const size_t o_geo = scr.reserve(geometry_bytes<R>(T, g.nx, g.ny));
     const size_t o_part = scr.reserve(adjoint_partial_bytes<R>(sp, g.nx, g.ny));
@@ -235,7 +235,7 @@ static int dbeta_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const
                       const void *gs, double *out, cudaStream_t st)
 {
     const int64_t T = tr->T;
-    AdjSplit sp = adjoint_split(T, g.nx, g.ny, default_target_items());
+    AdjSplit sp = adjoint_split(T, g.nx, g.ny, default_target_items(), sizeof(R));
     Scratch scr(st);
     const size_t o_geo = scr.reserve(geometry_bytes<R>(T, g.nx, g.ny));
     const size_t o_part = scr.reserve(dbeta_partial_bytes(sp));

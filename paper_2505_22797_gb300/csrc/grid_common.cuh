@@ -132,6 +132,15 @@ __global__ void k_round_field(int64_t n, const double *__restrict__ in, R *__res
         out[e] = R(in[e]);
 }
 
+// out[node * nc + m] = R(in[m * N + node]): the rounded field, node-interleaved
+// (the 2-D FP32 Core Stage gathers a corner's components in one vector load).
+template <typename R>
+__global__ void k_round_field_il(int64_t N, int nc, const double *__restrict__ in, R *__restrict__ out)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+        for (int m = 0; m < nc; ++m) out[e * nc + m] = R(in[m * N + e]);
+}
+
 // Ahat_m(node) = scale * sum of the node's NC unit partials, in unit order
 // (FP32 partials summed as error-free double-float pairs).
 template <typename R, typename OUT, int NC>

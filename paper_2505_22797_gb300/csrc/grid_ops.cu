@@ -41,7 +41,23 @@ __device__ __forceinline__ InterpRec<R> make_rec(R px, R py, const AxisMap &ax, 
 // channel k, Ahat holds (A_k0, A_k1) and s one row.  PRE: the records come
 // precomputed (rec), else they are formed from r.  Each thread handles
 // kInterpSPT samples a block apart, so its gathers are independent.
-template <typename R, typename AT, int CH, bool PRE>
+// IL: the field is node-interleaved (A[node * NCOMP + comp], NCOMP = 4 or 2
+// components of one node contiguous, 16- or 8-byte aligned), so a corner is
+// one vector load; otherwise component-major (A[comp * N + node]).  The
+// arithmetic is the same either way.
+template <typename R, int NCOMP> struct NodeVec;
+template <> struct NodeVec<float, 4> { using T = float4; };
+template <> struct NodeVec<float, 2> { using T = float2; };
+
+template <typename R, int NCOMP>
+__device__ __forceinline__ void load_node(const R *__restrict__ A, int64_t node, R (&out)[NCOMP])
+{
+    const typename NodeVec<R, NCOMP>::T q = reinterpret_cast<const typename NodeVec<R, NCOMP>::T *>(A)[node];
+    if constexpr (NCOMP == 4) { out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w; }
+    else { out[0] = q.x; out[1] = q.y; }
+}
+
+template <typename R, typename AT, int CH, bool PRE, bool IL = false>
 __global__ void __launch_bounds__(256)
 k_interp(int64_t T, const R *__restrict__ r, const InterpRec<R> *__restrict__ rec,
          const R *__restrict__ v, const AT *__restrict__ A, AxisMap ax, AxisMap ay, R *__restrict__ s)
@@ -66,6 +82,25 @@ k_interp(int64_t T, const R *__restrict__ r, const InterpRec<R> *__restrict__ re
             const int i0 = q[u].i0, j0 = q[u].j0;
             const int i1 = ax.n > 1 ? i0 + 1 : i0, j1 = ay.n > 1 ? j0 + 1 : j0;
             const R wx1 = q[u].wx1, wy1 = q[u].wy1, wx0 = R(1) - wx1, wy0 = R(1) - wy1;
+            if constexpr (IL) {
+                constexpr int NCOMP = 2 * K;
+                R f00[NCOMP], f01[NCOMP], f10[NCOMP], f11[NCOMP];  // f<row><col>
+                load_node<R, NCOMP>(reinterpret_cast<const R *>(A), (int64_t)j0 * nx + i0, f00);
+                load_node<R, NCOMP>(reinterpret_cast<const R *>(A), (int64_t)j0 * nx + i1, f01);
+                load_node<R, NCOMP>(reinterpret_cast<const R *>(A), (int64_t)j1 * nx + i0, f10);
+                load_node<R, NCOMP>(reinterpret_cast<const R *>(A), (int64_t)j1 * nx + i1, f11);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    R acc = R(0);
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        const int e = 2 * k + m;
+                        const R val = wy0 * (wx0 * f00[e] + wx1 * f01[e]) + wy1 * (wx0 * f10[e] + wx1 * f11[e]);
+                        acc += val * (m == 0 ? vv[u].x : vv[u].y);
+                    }
+                    if (t < T) s[(int64_t)k * T + t] = acc;
+                }
+            } else {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 R acc = R(0);
@@ -77,6 +112,7 @@ k_interp(int64_t T, const R *__restrict__ r, const InterpRec<R> *__restrict__ re
                     acc += val * (m == 0 ? vv[u].x : vv[u].y);
                 }
                 if (t < T) s[(int64_t)k * T + t] = acc;
+            }
             }
         }
     }
@@ -167,108 +203,124 @@ __global__ void k_cell_sort(int n_cells, const int *__restrict__ offset, int *__
     }
 }
 
-// Ahat_{2k+m}(node) = sum over samples t of the adjacent cells of
-// w_node(t) v_m(t) s_k(t), with rec, vs and s in list (cell) order.  CH = k:
-// only channel k (s one row), output the two components (A_k0, A_k1).  One warp per node: the lanes stride over the
-// samples of the node's (up to) four cells, then a fixed butterfly sums the
-// lanes, so a node whose cells hold many samples (a trajectory that dwells)
-// costs one warp a longer loop instead of stalling 31 other nodes.
-// Samples in the (up to) four cells around node (i, j), in cell order.
-__device__ __forceinline__ int node_cells(int i, int j, int ncx, int ncy, int c[4])
-{
-    int n = 0;
-    for (int cj = j - 1; cj <= j; ++cj) {
-        if (cj < 0 || cj >= ncy) continue;
-        for (int ci = i - 1; ci <= i; ++ci) {
-            if (ci < 0 || ci >= ncx) continue;
-            c[n++] = cj * ncx + ci;
-        }
-    }
-    return n;
-}
+// The transpose (Ahat_{2k+m}(node) = sum over the samples t of the node's
+// adjacent cells of w_node(t) v_m(t) s_k(t)) runs by cell: each cell's run of
+// samples (list order) is split into work units of at most kUnitLen entries;
+// a unit reads each of its samples once and forms, for the cell's four
+// corner nodes and every component, the sum of w_corner(t) v_m(t) s_k(t)
+// (kUnitLanes lanes per unit, then a fixed butterfly).  A node then adds the
+// unit sums of its (up to) four adjacent cells in a fixed order.  A sample is
+// read once instead of once per corner node, and a cell where the trajectory
+// dwells (thousands of samples) spreads over many units.
 
-__global__ void k_unit_count(int nx, int ny, int ncx, int ncy, const int *__restrict__ offset,
-                             int *__restrict__ unit_cnt)
-{
-    const int N = nx * ny;
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
-        int c[4];
-        const int nc = node_cells(node % nx, node / nx, ncx, ncy, c);
-        int tot = 0;
-        for (int k = 0; k < nc; ++k) tot += offset[c[k] + 1] - offset[c[k]];
-        unit_cnt[node] = max(1, (tot + kUnitLen - 1) / kUnitLen);
-    }
-}
-
+// unit_node[w] = node for the units unit_off[node] .. unit_off[node + 1]
+// (the node-unit transpose of the 3-D Core Stage).
 __global__ void k_unit_fill(int N, const int *__restrict__ unit_off, int *__restrict__ unit_node)
 {
     for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x)
         for (int w = unit_off[node]; w < unit_off[node + 1]; ++w) unit_node[w] = node;
 }
 
-// Partial sums of one unit: sum over its entries of w_node(t) v_m(t) s_k(t),
-// with rec, vs and s in list (cell) order.  CH = k: only channel k (s one row,
-// two components).  n_iter: the unit bound rounded up to whole blocks, so
-// every warp runs the same iterations and its shuffles see full warps.
+__global__ void k_cunit_count(int n_cells, const int *__restrict__ offset, int *__restrict__ cunit_cnt)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x)
+        cunit_cnt[c] = (offset[c + 1] - offset[c] + kUnitLen - 1) / kUnitLen;
+}
+
+__global__ void k_cunit_fill(int n_cells, const int *__restrict__ cunit_off, int *__restrict__ unit_cell)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x)
+        for (int w = cunit_off[c]; w < cunit_off[c + 1]; ++w) unit_cell[w] = c;
+}
+
+// Corner sums of one unit: for the corners (dx, dy) of the unit's cell
+// (corner index dx + 2 dy) and the NC components, the sum over the unit's
+// entries of w_dx w_dy v_m s_k, with rec, vs and s in list (cell) order.
+// CH = k: only channel k (s one row, two components).  n_iter: the unit
+// bound rounded up to whole blocks, so every warp runs the same iterations
+// and its shuffles see full warps.
 template <typename R, int CH>
 __global__ void __launch_bounds__(kUnitThreads)
-k_interp_T_units(const InterpRec<R> *__restrict__ rec, const R *__restrict__ vs, const R *__restrict__ s,
-                 int64_t T, int nx, int ncx, int ncy, const int *__restrict__ offset,
-                 const int *__restrict__ unit_off, const int *__restrict__ unit_node, int N, int n_iter,
+k_interp_T_cells(const InterpRec<R> *__restrict__ rec, const R *__restrict__ vs, const R *__restrict__ s,
+                 int64_t T, const int *__restrict__ offset, const int *__restrict__ cunit_off,
+                 const int *__restrict__ unit_cell, const int *__restrict__ n_units_dev, int n_iter,
                  R *__restrict__ unit_part)
 {
     constexpr int NC = CH < 0 ? 4 : 2;
     constexpr int G = kUnitLanes;
     constexpr int per_block = kUnitThreads / G;
     const int sub = threadIdx.x % G;
-    const int n_units = unit_off[N];
+    const int n_units = *n_units_dev;
     for (int base = blockIdx.x * per_block; base < n_iter; base += gridDim.x * per_block) {
         const int w = base + (int)threadIdx.x / G;
-        R acc[NC];
+        R acc[4][NC];
 #pragma unroll
-        for (int m = 0; m < NC; ++m) acc[m] = R(0);
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) acc[k][m] = R(0);
         if (w < n_units) {
-            const int node = unit_node[w];
-            const int i = node % nx, j = node / nx;
-            const int p0 = (w - unit_off[node]) * kUnitLen, p1 = p0 + kUnitLen;
-            int c[4];
-            const int nc = node_cells(i, j, ncx, ncy, c);
-            int pos = 0;
-            for (int k = 0; k < nc; ++k) {
-                const int q_base = offset[c[k]], cnt = offset[c[k] + 1] - q_base;
-                const int lo = max(p0, pos), hi = min(p1, pos + cnt);
+            const int c = unit_cell[w];
+            const int q0 = offset[c] + (w - cunit_off[c]) * kUnitLen;
+            const int q1 = min(offset[c + 1], q0 + kUnitLen);
 #pragma unroll 4
-                for (int pp = lo + sub; pp < hi; pp += G) {
-                    const int q = q_base + (pp - pos);
-                    const InterpRec<R> rc = rec[q];
-                    const R wx = (i == rc.i0) ? R(1) - rc.wx1 : rc.wx1;
-                    const R wy = (j == rc.j0) ? R(1) - rc.wy1 : rc.wy1;
-                    const R wt = wy * wx;
-                    const R vx = vs[2 * q], vy = vs[2 * q + 1];
-                    if constexpr (CH < 0) {
-                        const R s0 = s[q], s1 = s[T + q];
-                        acc[0] += wt * (vx * s0);
-                        acc[1] += wt * (vy * s0);
-                        acc[2] += wt * (vx * s1);
-                        acc[3] += wt * (vy * s1);
-                    } else {
-                        const R sk = s[q];
-                        acc[0] += wt * (vx * sk);
-                        acc[1] += wt * (vy * sk);
-                    }
+            for (int q = q0 + sub; q < q1; q += G) {
+                const InterpRec<R> rc = rec[q];
+                const R wx1 = rc.wx1, wy1 = rc.wy1, wx0 = R(1) - wx1, wy0 = R(1) - wy1;
+                const R wt[4] = {wy0 * wx0, wy0 * wx1, wy1 * wx0, wy1 * wx1};
+                const R vx = vs[2 * q], vy = vs[2 * q + 1];
+                R pr[NC];
+                if constexpr (CH < 0) {
+                    const R s0 = s[q], s1 = s[T + q];
+                    pr[0] = vx * s0; pr[1] = vy * s0; pr[2] = vx * s1; pr[3] = vy * s1;
+                } else {
+                    const R sk = s[q];
+                    pr[0] = vx * sk; pr[1] = vy * sk;
                 }
-                pos += cnt;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) acc[k][m] += wt[k] * pr[m];
             }
         }
 #pragma unroll
-        for (int m = 0; m < NC; ++m) {
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
-        }
+            for (int m = 0; m < NC; ++m)
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) acc[k][m] += __shfl_xor_sync(0xffffffffu, acc[k][m], o);
         if (sub == 0 && w < n_units) {
 #pragma unroll
-            for (int m = 0; m < NC; ++m) unit_part[(int64_t)w * NC + m] = acc[m];
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int m = 0; m < NC; ++m) unit_part[((int64_t)w * 4 + k) * NC + m] = acc[k][m];
         }
+    }
+}
+
+// Ahat_m(node) = scale * the sum, over the node's adjacent cells (row-major
+// cell order) and their units in order, of the unit sums of the corner the
+// node is in that cell (FP32 unit sums as error-free double-float pairs).
+template <typename R, typename OUT, int NC>
+__global__ void k_interp_T_cell_combine(int nx, int ny, int ncx, int ncy, const int *__restrict__ cunit_off,
+                                        const R *__restrict__ unit_part, OUT *__restrict__ A, double scale)
+{
+    const int N = nx * ny;
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
+        const int i = node % nx, j = node / nx;
+        SumAcc<R> acc[NC] = {};
+        for (int cj = j - 1; cj <= j; ++cj) {
+            if (cj < 0 || cj >= ncy) continue;
+            for (int ci = i - 1; ci <= i; ++ci) {
+                if (ci < 0 || ci >= ncx) continue;
+                const int c = cj * ncx + ci;
+                const int corner = (i - ci) + 2 * (j - cj);
+                for (int w = cunit_off[c]; w < cunit_off[c + 1]; ++w)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) acc[m].add(unit_part[((int64_t)w * 4 + corner) * NC + m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(acc[m].value() * scale);
     }
 }
 
@@ -283,17 +335,21 @@ struct Bins {
     void *rec_t;  // InterpRec<R>[T], sample order (scratch of the binning)
     void *rec;    // InterpRec<R>[T], list order
     void *vs;     // R[T][2], list order
-    // Work units of the transpose (see kUnitLen): per node unit_off[node] ..
-    // unit_off[node + 1]; the node of each unit; 4 partial sums per unit.
-    int *unit_cnt, *unit_off, *unit_cursor, *unit_node;
+    // Work units of the transpose (see kUnitLen): per cell cunit_off[c] ..
+    // cunit_off[c + 1] (cunit_off[n_cells] = the number of units); the cell
+    // of each unit; 4 corners x 4 partial sums per unit.
+    int *cunit_cnt, *cunit_off, *cunit_cursor, *unit_cell;
     void *unit_part;
     int n_units_max;
     int ncx, ncy;
 };
 
+// Units of the cell runs: at most one per kUnitLen samples plus one per
+// non-empty cell.
 static int units_bound(int64_t T, int nx, int ny)
 {
-    return (int)std::min<int64_t>(INT32_MAX, (int64_t)nx * ny + (4 * T + kUnitLen - 1) / kUnitLen + 1);
+    const int64_t nc = int64_t(std::max(nx - 1, 1)) * std::max(ny - 1, 1);
+    return (int)std::min<int64_t>(INT32_MAX, (T + kUnitLen - 1) / kUnitLen + std::min<int64_t>(T, nc) + 1);
 }
 
 template <typename R>
@@ -301,11 +357,11 @@ static size_t bins_bytes(int64_t T, int nx, int ny)
 {
     const size_t nc = size_t(std::max(nx - 1, 1)) * std::max(ny - 1, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t N = size_t(nx) * ny, U = size_t(units_bound(T, nx, ny));
+    const size_t U = size_t(units_bound(T, nx, ny));
     return up(sizeof(int) * std::max<int64_t>(T, 1)) * 2 + up(sizeof(int) * nc) * 2 +
            up(sizeof(int) * (nc + 1)) + 2 * up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1)) +
-           up(2 * sizeof(R) * std::max<int64_t>(T, 1)) + up(sizeof(int) * N) * 2 + up(sizeof(int) * (N + 1)) +
-           up(sizeof(int) * U) + up(4 * sizeof(R) * U);
+           up(2 * sizeof(R) * std::max<int64_t>(T, 1)) + up(sizeof(int) * nc) * 2 + up(sizeof(int) * (nc + 1)) +
+           up(sizeof(int) * U) + up(16 * sizeof(R) * U);
 }
 
 template <typename R>
@@ -324,12 +380,11 @@ static Bins bins_carve(char *p, int64_t T, int nx, int ny)
     b.rec_t = p; p += up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1));
     b.rec = p; p += up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1));
     b.vs = p; p += up(2 * sizeof(R) * std::max<int64_t>(T, 1));
-    const size_t N = size_t(nx) * ny;
     b.n_units_max = units_bound(T, nx, ny);
-    b.unit_cnt = reinterpret_cast<int *>(p); p += up(sizeof(int) * N);
-    b.unit_cursor = reinterpret_cast<int *>(p); p += up(sizeof(int) * N);
-    b.unit_off = reinterpret_cast<int *>(p); p += up(sizeof(int) * (N + 1));
-    b.unit_node = reinterpret_cast<int *>(p); p += up(sizeof(int) * size_t(b.n_units_max));
+    b.cunit_cnt = reinterpret_cast<int *>(p); p += up(sizeof(int) * nc);
+    b.cunit_cursor = reinterpret_cast<int *>(p); p += up(sizeof(int) * nc);
+    b.cunit_off = reinterpret_cast<int *>(p); p += up(sizeof(int) * (nc + 1));
+    b.unit_cell = reinterpret_cast<int *>(p); p += up(sizeof(int) * size_t(b.n_units_max));
     b.unit_part = p;
     return b;
 }
@@ -360,12 +415,11 @@ static int build_bins(const GridH &g, int64_t T, const R *r, const R *v, const B
         MPI_CHECK_LAUNCH();
     }
     // Work units of the transpose.
-    const int N = g.nx * g.ny;
-    k_unit_count<<<grid_blocks(N), 256, 0, st>>>(g.nx, g.ny, b.ncx, b.ncy, b.offset, b.unit_cnt);
+    k_cunit_count<<<grid_blocks(nc), 256, 0, st>>>(nc, b.offset, b.cunit_cnt);
     MPI_CHECK_LAUNCH();
-    k_scan<<<1, kScanThreads, 0, st>>>(b.unit_cnt, N, b.unit_off, b.unit_cursor);
+    k_scan<<<1, kScanThreads, 0, st>>>(b.cunit_cnt, nc, b.cunit_off, b.cunit_cursor);
     MPI_CHECK_LAUNCH();
-    k_unit_fill<<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, b.unit_node);
+    k_cunit_fill<<<grid_blocks(nc), 256, 0, st>>>(nc, b.cunit_off, b.unit_cell);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
@@ -373,11 +427,20 @@ static int build_bins(const GridH &g, int64_t T, const R *r, const R *v, const B
 // rec (nullable): precomputed records of the samples (Core Stage).
 template <typename R, typename AT>
 static int launch_interp(const GridH &g, int64_t T, const R *r, const R *v, const AT *A, R *s,
-                         cudaStream_t st, int ch = -1, const InterpRec<R> *rec = nullptr)
+                         cudaStream_t st, int ch = -1, const InterpRec<R> *rec = nullptr, bool il = false)
 {
     if (T == 0) return MPI_OK;
     const AxisMap ax = make_axis(g.x0, g.dx, g.nx), ay = make_axis(g.y0, g.dy, g.ny);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((T + 256 * kInterpSPT - 1) / (256 * kInterpSPT), 8192));
+    if constexpr (sizeof(AT) == 4) {
+        if (il) {  // node-interleaved FP32 field, records precomputed
+            if (ch < 0) k_interp<R, AT, -1, true, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+            else if (ch == 0) k_interp<R, AT, 0, true, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+            else k_interp<R, AT, 1, true, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
+            MPI_CHECK_LAUNCH();
+            return MPI_OK;
+        }
+    }
     if (rec) {
         if (ch < 0) k_interp<R, AT, -1, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
         else if (ch == 0) k_interp<R, AT, 0, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, ay, s);
@@ -397,21 +460,27 @@ static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const B
                            cudaStream_t st, int ch = -1)
 {
     const int N = g.nx * g.ny;
+    const int nc = b.ncx * b.ncy;
     constexpr int per_block = kUnitThreads / kUnitLanes;
     const int n_iter = (b.n_units_max + per_block - 1) / per_block * per_block;
     const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, 65535));
     const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(b.rec);
     const R *vs = static_cast<const R *>(b.vs);
     R *part = static_cast<R *>(b.unit_part);
+    const int *n_units = b.cunit_off + nc;
     if (ch < 0)
-        k_interp_T_units<R, -1><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, g.nx, b.ncx, b.ncy, b.offset,
-                                                                 b.unit_off, b.unit_node, N, n_iter, part);
+        k_interp_T_cells<R, -1><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, b.offset, b.cunit_off,
+                                                                 b.unit_cell, n_units, n_iter, part);
     else
-        k_interp_T_units<R, 0><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, g.nx, b.ncx, b.ncy, b.offset,
-                                                                b.unit_off, b.unit_node, N, n_iter, part);
+        k_interp_T_cells<R, 0><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, b.offset, b.cunit_off,
+                                                                b.unit_cell, n_units, n_iter, part);
     MPI_CHECK_LAUNCH();
-    if (ch < 0) k_interp_T_combine<R, OUT, 4><<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, part, A, scale);
-    else k_interp_T_combine<R, OUT, 2><<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, part, A, scale);
+    if (ch < 0)
+        k_interp_T_cell_combine<R, OUT, 4><<<grid_blocks(N), 256, 0, st>>>(g.nx, g.ny, b.ncx, b.ncy, b.cunit_off,
+                                                                          part, A, scale);
+    else
+        k_interp_T_cell_combine<R, OUT, 2><<<grid_blocks(N), 256, 0, st>>>(g.nx, g.ny, b.ncx, b.ncy, b.cunit_off,
+                                                                          part, A, scale);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
@@ -504,10 +573,10 @@ struct GridOp2 final : CoreStageOp {
         const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(bins.rec);
         const R *vs = static_cast<const R *>(bins.vs);
         if constexpr (sizeof(R) == 4) {
-            const int64_t n = int64_t(nc) * g.nx * g.ny;
-            k_round_field<R><<<grid_blocks(n), 256, 0, st>>>(n, p, p_r);
+            const int64_t N = int64_t(g.nx) * g.ny;
+            k_round_field_il<R><<<grid_blocks(N), 256, 0, st>>>(N, nc, p, p_r);
             MPI_CHECK_LAUNCH();
-            MPI_TRY((launch_interp<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec)));
+            MPI_TRY((launch_interp<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec, true)));
         } else {
             MPI_TRY((launch_interp<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
         }

@@ -56,7 +56,8 @@ inline size_t fwd_smem_bytes(int nx, int RB, int elem)
 // per block (MPI_ADJ_WSTAGE 0, block barriers around the staging) or one per
 // warp (1: the warps never wait for one another).  Timed on GB300 at
 // 128 x 128 / 65 536 samples: 4 warps with one copy per block 0.453 ms, one
-// copy per warp 0.466 ms, 2 warps 0.457 ms, 1 warp 0.537 ms.
+// copy per warp 0.466 ms, 2 warps 0.457 ms, 1 warp 0.537 ms (512 x 512 /
+// 2^20 samples: one copy per block 101 ms, per warp 108 ms).
 #ifndef MPI_ADJ_WARPS
 #define MPI_ADJ_WARPS 4
 #endif
@@ -71,10 +72,11 @@ constexpr int kAdjThreads = 32 * kAdjWarps;
 #endif
 // Tuning knobs (compile time), chosen by timing variants on GB300: minimum
 // resident blocks per SM requested from the register allocator for the FP32
-// kernels (6 x 128 threads for both: the forward's loop keeps 8 columns in
-// flight in 80 registers; the adjoint, whose asymptotic pair term is a short
-// dependent chain, is latency-bound below 6), and the unroll depth of the
-// forward column loop.  The FP64 kernels request 2 blocks per SM (no spills).
+// kernels (6 x 128 threads for both, 80 registers; the adjoint, whose
+// asymptotic pair term is a short dependent chain, is latency-bound below 6),
+// and the unroll depth of the forward column loop (4 columns in flight: 2 %
+// faster than 8 at 128 x 128 / 65 536 samples).  The FP64 kernels request 2
+// blocks per SM (no spills).
 #ifndef MPI_FWD_MINB
 #define MPI_FWD_MINB 6
 #endif
@@ -82,7 +84,7 @@ constexpr int kAdjThreads = 32 * kAdjWarps;
 #define MPI_ADJ_MINB (24 / MPI_ADJ_WARPS)
 #endif
 #ifndef MPI_FWD_UNROLL
-#define MPI_FWD_UNROLL 8
+#define MPI_FWD_UNROLL 4
 #endif
 constexpr int kFwdUnroll = MPI_FWD_UNROLL;
 // Unroll depth of the full closed-form column loops (a few percent of the
@@ -100,7 +102,7 @@ constexpr int kAdjTileY = kAdjWarps * kAdjV;
 // Unroll depth of the adjoint's asymptotic 32-sample loop (32 = the whole
 // group: staged-sample addresses become constant offsets).
 #ifndef MPI_ADJ_UNROLL_VFAR
-#define MPI_ADJ_UNROLL_VFAR 4
+#define MPI_ADJ_UNROLL_VFAR 2
 #endif
 constexpr int kAdjUnrollVfar = MPI_ADJ_UNROLL_VFAR;
 

@@ -40,8 +40,9 @@ __device__ __forceinline__ typename ProbeType<OP>::T probe_op(typename ProbeType
         asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     else if constexpr (OP == MPI_PROBE_EX2)
         asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));  // stays in (0, 1]
-    else
-        asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    else  // x <- 1/(x + 1): an add keeps the assembler from folding rcp(rcp(x))
+        asm volatile("{ .reg .f32 t; add.ftz.f32 t, %1, 0f3F800000; rcp.approx.ftz.f32 %0, t; }"
+                     : "=f"(y) : "f"(x));
     return y;
 }
 

@@ -13,7 +13,8 @@ DTYPES = [torch.float32, torch.float64]
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("shape", [(1, 1, 7), (2, 3, 40), (17, 13, 700), (64, 64, 8192)])
+@pytest.mark.parametrize("shape", [(1, 1, 7), (1, 9, 300), (11, 1, 300), (2, 3, 40), (17, 13, 700),
+                                   (64, 64, 8192)])
 def test_interp_and_transpose(orc, dt, shape):
     nx, ny, T = shape
     g = syn.square_grid(nx, 24.0, ny)
@@ -28,16 +29,17 @@ def test_interp_and_transpose(orc, dt, shape):
                   orc.interp_T(g, r, v, s)) <= tol(dt)
 
 
-def test_interp_T_dense_cell():
+@pytest.mark.parametrize("dt", DTYPES)
+def test_interp_T_dense_cell(dt):
     """Thousands of samples in one cell (a trajectory that dwells): the
-    per-cell ordering takes the long-list path; result matches FP64 sums."""
-    dt = torch.float64
+    per-cell ordering takes the long-list path and the cell's run spans many
+    work units; result matches FP64 sums."""
     g = syn.square_grid(8, 8.0)
     T = 5000
     rng = np.random.default_rng(0)
-    r = 0.3 + 0.1 * rng.uniform(size=(T, 2))
-    v = rng.normal(size=(T, 2))
-    s = rng.normal(size=(2, T))
+    r = rounded(0.3 + 0.1 * rng.uniform(size=(T, 2)), dt)
+    v = rounded(rng.normal(size=(T, 2)), dt)
+    s = rounded(rng.normal(size=(2, T)), dt)
     from oracle import oracle as orc
     assert rel_l2(host(api.mpi_interp_adjoint(g, dev(r, dt), dev(v, dt), dev(s, dt))),
                   orc.interp_T(g, r, v, s)) <= tol(dt)
