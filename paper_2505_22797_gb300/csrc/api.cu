@@ -199,7 +199,7 @@ static int forward_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, con
 {
     const int64_t T = tr->T;
     if (T == 0) return MPI_OK;
-    FwdSplit sp = forward_split(T, g.nx, g.ny, sizeof(R), default_target_items());
+    FwdSplit sp = forward_split(T, g.nx, g.ny, sizeof(R), forward_target_items());
     Scratch scr(st);
     const size_t o_geo = scr.reserve(geometry_bytes<R>(T, g.nx, g.ny));
     const size_t o_part = scr.reserve(forward_partial_bytes<R>(sp, m.n_ch, T));

@@ -341,7 +341,7 @@ static void configure(mpi_batch_plan &P, int64_t fb, int64_t ab, bool fpers, boo
     P.as.resize(P.n);
     const bool single = (P.flags & MPI_BATCH_MATCH_SINGLE) != 0;
     for (int f = 0; f < P.n; ++f) {
-        P.fs[f] = single ? forward_split(P.T[f], P.g[f].nx, P.g[f].ny, 4, default_target_items())
+        P.fs[f] = single ? forward_split(P.T[f], P.g[f].nx, P.g[f].ny, 4, forward_target_items())
                          : fwd_split_budget(P.T[f], P.g[f].nx, P.g[f].ny, fb);
         P.as[f] = single ? adjoint_split(P.T[f], P.g[f].nx, P.g[f].ny, default_target_items(), 4)
                          : adj_split_budget(P.T[f], P.g[f].nx, P.g[f].ny, ab);
@@ -739,7 +739,7 @@ int mpi_batch_plan_create(int n_frames, const mpi_model *models, const mpi_grid_
     auto take = [&](size_t b) { size_t o = tot; tot += (b + 255) & ~size_t(255); return o; };
     for (int f = 0; f < n_frames; ++f) {
         const FwdSplit fs_min = fwd_split_budget(P->T[f], P->g[f].nx, P->g[f].ny, bmin);
-        const FwdSplit fs_single = forward_split(P->T[f], P->g[f].nx, P->g[f].ny, 4, default_target_items());
+        const FwdSplit fs_single = forward_split(P->T[f], P->g[f].nx, P->g[f].ny, 4, forward_target_items());
         const AdjSplit as_min = adj_split_budget(P->T[f], P->g[f].nx, P->g[f].ny, bmin);
         const AdjSplit as_single = adjoint_split(P->T[f], P->g[f].nx, P->g[f].ny, default_target_items(), 4);
         const int fch = std::max(fs_min.n_chunks, fs_single.n_chunks);

@@ -463,7 +463,10 @@ static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const B
     const int nc = b.ncx * b.ncy;
     constexpr int per_block = kUnitThreads / kUnitLanes;
     const int n_iter = (b.n_units_max + per_block - 1) / per_block * per_block;
-    const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, 65535));
+    // One wave of blocks striding over the units: the bound on the units is
+    // loose (every cell counted non-empty), the real count is on the device.
+    const int wave = device_sm_count() * (2048 / kUnitThreads);
+    const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, wave));
     const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(b.rec);
     const R *vs = static_cast<const R *>(b.vs);
     R *part = static_cast<R *>(b.unit_part);

@@ -84,7 +84,7 @@ int forward_noalloc_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, co
         return MPI_ERR_UNSUPPORTED;
     }
     // As many row chunks as the default split wants, capped by what fits.
-    FwdSplit sp = forward_split(T, g.nx, g.ny, sizeof(R), default_target_items());
+    FwdSplit sp = forward_split(T, g.nx, g.ny, sizeof(R), forward_target_items());
     const int max_chunks = (int)std::min<size_t>(
         (kNoAllocScratchBytes - geo_bytes) / up(per_chunk), (size_t)g.ny);
     if (sp.n_chunks > max_chunks)

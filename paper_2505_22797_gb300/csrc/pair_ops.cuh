@@ -51,7 +51,8 @@ struct AdjSplit {
 };
 FwdSplit forward_split(int64_t T, int nx, int ny, int elem_bytes, int target_items);
 AdjSplit adjoint_split(int64_t T, int nx, int ny, int target_items, int elem_bytes);
-int default_target_items();
+int default_target_items();  // adjoint and d/dbeta work items per launch
+int forward_target_items();  // forward work items per launch
 // Column half-width around a sample that can hold a near-FFP pair (forward).
 template <typename R>
 int near_columns(const ModelH &m, const GridH &g);

@@ -366,7 +366,7 @@ static int pnp_impl(const ModelH &m, const GridH &g, const mpi_traj *tr, const v
     size_t o_geo = 0, o_fp = 0, o_ap = 0, o_sA = 0, o_K = 0, o_t1 = 0, o_t2 = 0, o_ord = 0, o_red = 0;
     if (ar) o_red = scr.reserve(sizeof(double) * size_t(S.N));
     if (S.op == MPI_OP_FORWARD) {
-        S.fs = forward_split(S.T, g.nx, g.ny, sizeof(R), target);
+        S.fs = forward_split(S.T, g.nx, g.ny, sizeof(R), forward_target_items());
         S.as = adjoint_split(S.T, g.nx, g.ny, target, sizeof(R));
         o_geo = scr.reserve(geometry_bytes<R>(S.T, g.nx, g.ny));
         o_ord = scr.reserve(item_order_bytes<R>(&S.fs, &S.as));
