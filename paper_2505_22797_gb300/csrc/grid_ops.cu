@@ -463,10 +463,10 @@ static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const B
     const int nc = b.ncx * b.ncy;
     constexpr int per_block = kUnitThreads / kUnitLanes;
     const int n_iter = (b.n_units_max + per_block - 1) / per_block * per_block;
-    // One wave of blocks striding over the units: the bound on the units is
-    // loose (every cell counted non-empty), the real count is on the device.
-    const int wave = device_sm_count() * (2048 / kUnitThreads);
-    const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, wave));
+    // Blocks for the bound on the units (every cell counted non-empty); the
+    // real count is on the device and the surplus blocks exit at once (a
+    // one-wave striding grid was slower at 512 x 512 / 2^20 samples).
+    const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, 65535));
     const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(b.rec);
     const R *vs = static_cast<const R *>(b.vs);
     R *part = static_cast<R *>(b.unit_part);
@@ -726,21 +726,66 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
         ~PinnedFree() { cudaFreeHost(p); }
     } guard{h_done};
 
-    const int poll = 16;
-    for (int it = 0; it < o.max_iter; ++it) {
-        // q = (1/T) M^T M p + gamma Lap Lap p, and <p, q>
-        MPI_TRY(op.normal(p, y, st));
-        MPI_TRY(op.lap(p, l1, st));
-        MPI_TRY(op.lap(l1, l2, st));
-        k_grid_epilogue<<<nepi, kEpiThreads, 0, st>>>(nv, y, l2, o.gamma, p, q, pq_part);
+    // One CG step: q = (1/T) M^T M p + gamma Lap Lap p, <p, q>, and the update.
+    auto enqueue_step = [&](int it, cudaStream_t s) -> int {
+        MPI_TRY(op.normal(p, y, s));
+        MPI_TRY(op.lap(p, l1, s));
+        MPI_TRY(op.lap(l1, l2, s));
+        k_grid_epilogue<<<nepi, kEpiThreads, 0, s>>>(nv, y, l2, o.gamma, p, q, pq_part);
         MPI_CHECK_LAUNCH();
-        MPI_TRY(cg_step_launch(nv, x, rr, p, q, pq_part, nepi, (it & 1) ? rr_part1 : rr_part0,
-                               (it & 1) ? rr_part0 : rr_part1, done, thresh, iters, st));
-        if (thresh && (it + 1) % poll == 0 && it + 1 < o.max_iter) {
-            MPI_TRY_CUDA(cudaMemcpyAsync(h_done, done, sizeof(int), cudaMemcpyDeviceToHost, st));
-            MPI_TRY_CUDA(cudaStreamSynchronize(st));
-            if (*h_done) break;
+        return cg_step_launch(nv, x, rr, p, q, pq_part, nepi, (it & 1) ? rr_part1 : rr_part0,
+                              (it & 1) ? rr_part0 : rr_part1, done, thresh, iters, s);
+    };
+    auto poll_done = [&](bool &stop) -> int {
+        MPI_TRY_CUDA(cudaMemcpyAsync(h_done, done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPI_TRY_CUDA(cudaStreamSynchronize(st));
+        stop = *h_done != 0;
+        return MPI_OK;
+    };
+
+    // The steps are short dependent launches (latency-bound), so a run of
+    // `poll` steps -- the span between two host polls of the stop flag -- is
+    // captured once as a CUDA graph and replayed: the same kernels with the
+    // same arguments in the same order (poll is even, so the alternation of the
+    // residual partials repeats), hence the same result.  The capture uses a
+    // private stream (the caller's may be the legacy default stream, which
+    // cannot be captured); the graph runs on the caller's stream.
+    const int poll = 16;
+    int it = 0;
+    bool stop = false;
+    if (o.max_iter >= 2 * poll) {
+        struct GraphRes {
+            cudaStream_t cap = nullptr;
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            ~GraphRes()
+            {
+                if (exec) cudaGraphExecDestroy(exec);  // freed once a launch in flight completes
+                if (graph) cudaGraphDestroy(graph);
+                if (cap) cudaStreamDestroy(cap);
+            }
+        } g;
+        MPI_TRY_CUDA(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
+        MPI_TRY_CUDA(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
+        const long long before = mpi_kernel_launches();
+        int rc = MPI_OK;
+        for (int k = 0; k < poll && rc == MPI_OK; ++k) rc = enqueue_step(k, g.cap);
+        note_launches(before - mpi_kernel_launches());  // captured, not launched
+        const cudaError_t ec = cudaStreamEndCapture(g.cap, &g.graph);
+        MPI_TRY(rc);
+        MPI_TRY_CUDA(ec);
+        size_t nodes = 0;
+        MPI_TRY_CUDA(cudaGraphGetNodes(g.graph, nullptr, &nodes));
+        MPI_TRY_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+        for (; it + poll <= o.max_iter && !stop; it += poll) {
+            MPI_TRY_CUDA(cudaGraphLaunch(g.exec, st));
+            note_launches((long long)nodes);
+            if (thresh && it + poll < o.max_iter) MPI_TRY(poll_done(stop));
         }
+    }
+    for (; it < o.max_iter && !stop; ++it) {
+        MPI_TRY(enqueue_step(it, st));
+        if (thresh && (it + 1) % poll == 0 && it + 1 < o.max_iter) MPI_TRY(poll_done(stop));
     }
     if (n_iter_out) {
         MPI_TRY_CUDA(cudaMemcpyAsync(h_done, iters, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -46,14 +46,17 @@ def test_interp_T_dense_cell(dt):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-def test_core_stage_fixed_iterations(orc, dt):
+@pytest.mark.parametrize("steps", [30, 37])
+def test_core_stage_fixed_iterations(orc, dt, steps):
+    """Fixed CG step counts: 30 steps run step by step; 37 run as two
+    replays of the 16-step graph and 5 more steps."""
     cfg = syn.small(20, 18, 2000, seed=5)
     g, m = cfg["grid"], cfg["model"]
     r, v, c = (rounded(cfg[k], dt) for k in ("r", "v", "c"))
     s = rounded(orc.forward(m, g, r, v, c), dt)
     gamma = 1e-4
-    want, want_u, hist = orc.core_stage(g, r, v, s, gamma, max_iter=30)
-    A, u, n = api.mpi_grid(g, dev(r, dt), dev(v, dt), dev(s, dt), gamma=gamma, max_iter=30,
+    want, want_u, hist = orc.core_stage(g, r, v, s, gamma, max_iter=steps)
+    A, u, n = api.mpi_grid(g, dev(r, dt), dev(v, dt), dev(s, dt), gamma=gamma, max_iter=steps,
                            rel_tol=0.0, return_iters=True)
     assert n == len(hist) - 1
     assert rel_l2(host(A), want) <= tol(dt)
