@@ -7,6 +7,7 @@
 #include <mutex>
 #include <vector>
 
+#include "graph.cuh"
 #include "pair_ops.cuh"
 
 namespace mpi {
@@ -114,6 +115,39 @@ ProfScope::~ProfScope()
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (cudaEventRecord(ev_[1], st_) == cudaSuccess) g_prof_pending.push_back({cls_, {ev_[0], ev_[1]}});
 }
+
+bool profile_enabled()
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return g_prof_on;
+}
+
+CapturedGraph::~CapturedGraph()
+{
+    if (exec_) cudaGraphExecDestroy(exec_);  // freed once a replay in flight completes
+    if (graph_) cudaGraphDestroy(graph_);
+    if (cap_) cudaStreamDestroy(cap_);
+}
+
+int CapturedGraph::fail()
+{
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+    (void)cudaGetLastError();  // a refused capture leaves no error for the direct path
+    return MPI_ERR_UNSUPPORTED;
+}
+
+int CapturedGraph::launch(cudaStream_t st)
+{
+    MPI_TRY_CUDA(cudaGraphLaunch(exec_, st));
+    note_launches((long long)nodes_);
+    return MPI_OK;
+}
+
+long long CapturedGraph::counted_launches() { return mpi_kernel_launches(); }
+void CapturedGraph::uncount_launches(long long n) { note_launches(-n); }
 
 int device_sm_count()
 {

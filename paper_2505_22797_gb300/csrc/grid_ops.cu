@@ -8,6 +8,7 @@
 // per-cell sort by sample index give every cell a fixed sample order), and
 // each node gathers from its (up to) four adjacent cells.  All of it is
 // memory/latency bound.
+#include "graph.cuh"
 #include "grid_common.cuh"
 
 namespace mpi {
@@ -754,33 +755,15 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
     int it = 0;
     bool stop = false;
     if (o.max_iter >= 2 * poll) {
-        struct GraphRes {
-            cudaStream_t cap = nullptr;
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            ~GraphRes()
-            {
-                if (exec) cudaGraphExecDestroy(exec);  // freed once a launch in flight completes
-                if (graph) cudaGraphDestroy(graph);
-                if (cap) cudaStreamDestroy(cap);
+        CapturedGraph g;
+        if (g.capture([&](cudaStream_t s) -> int {
+                for (int k = 0; k < poll; ++k) MPI_TRY(enqueue_step(k, s));
+                return MPI_OK;
+            }) == MPI_OK) {
+            for (; it + poll <= o.max_iter && !stop; it += poll) {
+                MPI_TRY(g.launch(st));
+                if (thresh && it + poll < o.max_iter) MPI_TRY(poll_done(stop));
             }
-        } g;
-        MPI_TRY_CUDA(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
-        MPI_TRY_CUDA(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
-        const long long before = mpi_kernel_launches();
-        int rc = MPI_OK;
-        for (int k = 0; k < poll && rc == MPI_OK; ++k) rc = enqueue_step(k, g.cap);
-        note_launches(before - mpi_kernel_launches());  // captured, not launched
-        const cudaError_t ec = cudaStreamEndCapture(g.cap, &g.graph);
-        MPI_TRY(rc);
-        MPI_TRY_CUDA(ec);
-        size_t nodes = 0;
-        MPI_TRY_CUDA(cudaGraphGetNodes(g.graph, nullptr, &nodes));
-        MPI_TRY_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
-        for (; it + poll <= o.max_iter && !stop; it += poll) {
-            MPI_TRY_CUDA(cudaGraphLaunch(g.exec, st));
-            note_launches((long long)nodes);
-            if (thresh && it + poll < o.max_iter) MPI_TRY(poll_done(stop));
         }
     }
     for (; it < o.max_iter && !stop; ++it) {

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <vector>
 
+#include "graph.cuh"
 #include "conv_ops.cuh"
 #include "pnp_device.cuh"
 
@@ -231,17 +232,30 @@ int pnp_run(PnPOperator<R> &op, int64_t N, const void *data, const mpi_pnp_opts 
 
     const bool fault_cb = getenv("MPI_FAULT") && strcmp(getenv("MPI_FAULT"), "callback") == 0;
     const int vgrid = (int)std::min<int64_t>((N + 255) / 256, 4096);
+    // The CG of one iteration (from x = rho2): q = (O^T O + nu I) x, the
+    // initial residual and n_cg steps -- the same launches with the same
+    // arguments every iteration (nu is read on the device).
+    auto enqueue_cg = [&](cudaStream_t s) -> int {
+        MPI_TRY(op.apply_normal(x, q, scal + kScalNu, pq_part, s));
+        MPI_TRY(cg_init_launch(N, b0, x, q, scal + kScalNu, r, p, rr_part[0], done, s));
+        for (int i = 0; i < o.n_cg; ++i) {
+            MPI_TRY(op.apply_normal(p, q, scal + kScalNu, pq_part, s));
+            MPI_TRY(cg_step_launch(N, x, r, p, q, pq_part, n_pq, rr_part[i & 1], rr_part[(i + 1) & 1],
+                                   done, nullptr, nullptr, s));
+        }
+        return MPI_OK;
+    };
+    // Captured once as a CUDA graph and replayed every iteration (the launches
+    // are short at small sizes, where issuing them one by one is the cost);
+    // not with the per-launch profiler on or an operator that calls back.
+    CapturedGraph cg_graph;
+    if (o.n_iter >= 2 && op.capturable() && !profile_enabled()) (void)cg_graph.capture(enqueue_cg);
     for (int k = 0; k < o.n_iter; ++k) {
         // rho1 <- CG(O^T O + nu I, O^T data + nu rho2, x0 = rho2), n_cg steps
         k_set_x<R><<<vgrid, 256, 0, st>>>(N, k == 0 ? nullptr : rho2, x);
         MPI_CHECK_LAUNCH();
-        MPI_TRY(op.apply_normal(x, q, scal + kScalNu, pq_part, st));
-        MPI_TRY(cg_init_launch(N, b0, x, q, scal + kScalNu, r, p, rr_part[0], done, st));
-        for (int i = 0; i < o.n_cg; ++i) {
-            MPI_TRY(op.apply_normal(p, q, scal + kScalNu, pq_part, st));
-            MPI_TRY(cg_step_launch(N, x, r, p, q, pq_part, n_pq, rr_part[i & 1], rr_part[(i + 1) & 1],
-                                   done, nullptr, nullptr, st));
-        }
+        if (cg_graph.ready()) MPI_TRY(cg_graph.launch(st));
+        else MPI_TRY(enqueue_cg(st));
         // trimming, sigma, lambda (k = 0), nu
         k_outer_stats<R><<<1, kStatThreads, 0, st>>>(N, x, o.clip_pct >= 0.0 ? 1 : 0, o.clip_pct, k,
                                                     o.nu0, scal, rr_part[o.n_cg & 1], nblk,
@@ -342,6 +356,7 @@ struct PnPOp2D final : PnPOperator<R> {
         return launch_gauss5<R>(in, out, g.nx, g.ny, st);
     }
     bool has_callback() const override { return den != nullptr; }
+    bool capturable() const override { return ar == nullptr; }
 };
 
 template <typename R>

@@ -55,6 +55,9 @@ struct PnPOperator {
     // user callback; returns the callback's status (nonzero = failure).
     virtual int denoise(const R *in, R *out, const double *sigma_dev, cudaStream_t st) = 0;
     virtual bool has_callback() const = 0;
+    // Whether apply_normal only enqueues device work (no host wait or
+    // callback), so the CG of an iteration may be captured as a CUDA graph.
+    virtual bool capturable() const { return true; }
 };
 
 // Algorithm 1 with operator O on N unknowns and the data of O's range (type
