@@ -92,10 +92,14 @@ k_fft_pass(const C *__restrict__ x, C *__restrict__ y, int64_t n, int R, int64_t
         butterfly<C, int64_t>(xc, yc, n, R, Ns, W, j);
 }
 
-// Every pass of one sequence in shared memory: block b loads sequence b,
-// runs the same butterflies pass by pass between two shared buffers and
-// writes the result back in place (one global read and write per transform
-// instead of one per pass).
+// Every pass of a sequence in shared memory: one global read and one global
+// write per 1-D transform instead of one per pass.  The first pass reads the
+// sequence from global memory and the last one writes it back (a single-pass
+// transform is staged through shared memory, since reading and writing the
+// same global row in one pass would race); the passes between run from one
+// shared buffer to the other.  A block holds `rpb` sequences of `tpr` threads
+// each, so short sequences (few butterflies per pass) still keep the block's
+// threads busy.
 constexpr int kSmemFftMaxPasses = 24;
 struct RadixList {
     int n_pass;
@@ -104,26 +108,38 @@ struct RadixList {
 
 template <typename C>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_smem(C *__restrict__ x, int n, RadixList rl, const C *__restrict__ W, int64_t dist)
+k_fft_smem(C *__restrict__ x, int n, RadixList rl, const C *__restrict__ W, int64_t dist, int n_seq, int rpb)
 {
     extern __shared__ __align__(16) unsigned char fft_smem[];
-    C *A = reinterpret_cast<C *>(fft_smem);
+    const int tpr = blockDim.x / rpb;
+    const int row = threadIdx.x / tpr, tid = threadIdx.x % tpr;
+    const int seq = blockIdx.x * rpb + row;
+    const bool active = row < rpb && seq < n_seq;
+    C *A = reinterpret_cast<C *>(fft_smem) + (size_t)2 * n * min(row, rpb - 1);
     C *B = A + n;
-    C *xc = x + blockIdx.x * dist;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) A[e] = xc[e];
-    __syncthreads();
-    C *src = A, *dst = B;
-    int Ns = 1;
-    for (int p = 0; p < rl.n_pass; ++p) {
-        const int R = rl.r[p];
-        for (int j = threadIdx.x; j < n / R; j += blockDim.x) butterfly<C, int>(src, dst, n, R, Ns, W, j);
+    C *xc = x + (int64_t)min(seq, n_seq - 1) * dist;
+    const int last = rl.n_pass - 1;
+    if (last == 0) {  // one pass: stage through shared memory
+        if (active)
+            for (int e = tid; e < n; e += tpr) A[e] = xc[e];
         __syncthreads();
-        C *tmp = src;
+        if (active)
+            for (int j = tid; j < n / rl.r[0]; j += tpr) butterfly<C, int>(A, xc, n, rl.r[0], 1, W, j);
+        return;
+    }
+    const C *src = xc;
+    C *dst = A;
+    int Ns = 1;
+    for (int p = 0; p <= last; ++p) {
+        const int R = rl.r[p];
+        C *out = (p == last) ? xc : dst;
+        if (active)
+            for (int j = tid; j < n / R; j += tpr) butterfly<C, int>(src, out, n, R, Ns, W, j);
+        __syncthreads();
         src = dst;
-        dst = tmp;
+        dst = (dst == A) ? B : A;
         Ns *= R;
     }
-    for (int e = threadIdx.x; e < n; e += blockDim.x) xc[e] = src[e];
 }
 
 unsigned fft_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + kFftThreads - 1) / kFftThreads, 4096)); }
@@ -138,12 +154,22 @@ static int fft_run_t(const FftPlan &p, C *a, C *b, int n_ch, int64_t dist, const
     if (p.radix.empty()) return MPI_OK;
     const size_t smem = 2 * sizeof(C) * size_t(p.n);
     if (smem <= 64 * 1024 && (int)p.radix.size() <= kSmemFftMaxPasses) {
-        if (smem > 48 * 1024)  // opt in above the default limit (set on the current device)
-            MPI_TRY_CUDA(cudaFuncSetAttribute(k_fft_smem<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RadixList rl{};
         rl.n_pass = (int)p.radix.size();
-        for (int q = 0; q < rl.n_pass; ++q) rl.r[q] = p.radix[q];
-        k_fft_smem<C><<<(unsigned)n_ch, kFftThreads, smem, st>>>(a, (int)p.n, rl, W, dist);
+        int most = 1;  // the most butterflies of any pass
+        for (int q = 0; q < rl.n_pass; ++q) {
+            rl.r[q] = p.radix[q];
+            most = std::max(most, (int)(p.n / p.radix[q]));
+        }
+        // sequences per block: as many as leave every thread a butterfly in
+        // the widest pass, within the block's shared memory
+        int rpb = 1;
+        while (rpb * 2 * most <= kFftThreads && size_t(rpb) * 2 * smem <= 48 * 1024 && rpb * 2 <= n_ch) rpb *= 2;
+        const size_t smem_blk = smem * size_t(rpb);
+        if (smem_blk > 48 * 1024)  // opt in above the default limit (set on the current device)
+            MPI_TRY_CUDA(cudaFuncSetAttribute(k_fft_smem<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_blk));
+        const unsigned blocks = (unsigned)((n_ch + rpb - 1) / rpb);
+        k_fft_smem<C><<<blocks, kFftThreads, smem_blk, st>>>(a, (int)p.n, rl, W, dist, n_ch, rpb);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }

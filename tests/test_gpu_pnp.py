@@ -239,7 +239,7 @@ def test_pnp_forward_single_channel(orc, dt):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("shape", [(80, 80), (128, 128), (97, 113), (181, 64)])
+@pytest.mark.parametrize("shape", [(80, 80), (128, 128), (97, 113), (181, 64), (300, 20)])
 def test_conv_fft_route(orc, dt, shape):
     """Grids of 4096 voxels and more (FP32; 1024 in FP64) take the FFT route (circular convolution
     on a padded grid): same linear convolution as the oracle's direct sum."""
