@@ -7,9 +7,10 @@
 //
 // Same organisation as the 2-D solve: interpolation records computed once per
 // trajectory, samples binned by interpolation cell (a cell now has 8 corner
-// nodes, a node up to 8 adjacent cells), the transpose gathered per node in
-// work units of at most kUnitLen samples with an ordered combine (no float
-// atomics, run-to-run identical), CG vectors and inner products in FP64.
+// nodes, a node up to 8 adjacent cells), the transpose summed per cell in
+// work units of at most kUnitLen samples and combined per node in a fixed
+// order (no float atomics, run-to-run identical), CG vectors and inner
+// products in FP64.
 #include "grid_common.cuh"
 
 namespace mpi {
@@ -52,8 +53,12 @@ __device__ __forceinline__ InterpRec3<R> make_rec3(R px, R py, R pz, const Axes3
 // s[k][t] = sum_m I[Ahat_{3k+m}](r_t) v_m(t).  CH < 0: all three channels
 // (Ahat 9 components, s 3 rows); CH = k: channel k only (Ahat holds
 // (A_k0, A_k1, A_k2), s one row).  PRE: records precomputed (rec), else formed
-// from r.  kInterpSPT samples per thread, a block apart.
-template <typename R, typename AT, int CH, bool PRE>
+// from r.  One thread per output s[k][t] (element e = k T + t): a Core Stage
+// trajectory of ~10^5 samples then still fills the GPU.  IL (FP32 field,
+// records precomputed): the field is node-interleaved, A4[node K + k] =
+// (A_{3k}, A_{3k+1}, A_{3k+2}, 0) with K rows, so a corner's three
+// components are one 16-byte load.
+template <typename R, typename AT, int CH, bool PRE, bool IL = false>
 __global__ void __launch_bounds__(256)
 k_interp3(int64_t T, const R *__restrict__ r, const InterpRec3<R> *__restrict__ rec,
           const R *__restrict__ v, const AT *__restrict__ A, Axes3 ax, R *__restrict__ s)
@@ -61,43 +66,59 @@ k_interp3(int64_t T, const R *__restrict__ r, const InterpRec3<R> *__restrict__ 
     const int nx = ax.x.n, ny = ax.y.n;
     const int64_t N = (int64_t)nx * ny * ax.z.n;
     constexpr int K = CH < 0 ? 3 : 1;
-    const int64_t span = (int64_t)blockDim.x * kInterpSPT;
-    for (int64_t base = blockIdx.x * span + threadIdx.x; base < T; base += (int64_t)gridDim.x * span) {
-        InterpRec3<R> q[kInterpSPT];
-        R vv[kInterpSPT][3];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < K * T;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = K == 1 ? 0 : int(e >= T) + int(e >= 2 * T);
+        const int64_t t = e - k * T;
+        InterpRec3<R> q;
+        if constexpr (PRE) q = rec[t];
+        else q = make_rec3<R>(r[3 * t], r[3 * t + 1], r[3 * t + 2], ax);
+        const R vv[3] = {v[3 * t], v[3 * t + 1], v[3 * t + 2]};
+        const int i0 = q.i0, j0 = q.j0, l0 = q.l0;
+        const int i1 = nx > 1 ? i0 + 1 : i0, j1 = ny > 1 ? j0 + 1 : j0, l1 = ax.z.n > 1 ? l0 + 1 : l0;
+        const R wx1 = q.wx1, wy1 = q.wy1, wz1 = q.wz1;
+        const R wx0 = R(1) - wx1, wy0 = R(1) - wy1, wz0 = R(1) - wz1;
+        const int64_t r00 = ((int64_t)l0 * ny + j0) * nx, r01 = ((int64_t)l0 * ny + j1) * nx;
+        const int64_t r10 = ((int64_t)l1 * ny + j0) * nx, r11 = ((int64_t)l1 * ny + j1) * nx;
+        R acc = R(0);
+        if constexpr (IL) {
+            const float4 *A4 = reinterpret_cast<const float4 *>(A);
+            const float4 a000 = A4[(r00 + i0) * K + k], a100 = A4[(r00 + i1) * K + k];
+            const float4 a010 = A4[(r01 + i0) * K + k], a110 = A4[(r01 + i1) * K + k];
+            const float4 a001 = A4[(r10 + i0) * K + k], a101 = A4[(r10 + i1) * K + k];
+            const float4 a011 = A4[(r11 + i0) * K + k], a111 = A4[(r11 + i1) * K + k];
+            auto tri = [&](float c000, float c100, float c010, float c110, float c001, float c101, float c011,
+                           float c111) {
+                const R lo = wy0 * (wx0 * c000 + wx1 * c100) + wy1 * (wx0 * c010 + wx1 * c110);
+                const R hi = wy0 * (wx0 * c001 + wx1 * c101) + wy1 * (wx0 * c011 + wx1 * c111);
+                return wz0 * lo + wz1 * hi;
+            };
+            acc += tri(a000.x, a100.x, a010.x, a110.x, a001.x, a101.x, a011.x, a111.x) * vv[0];
+            acc += tri(a000.y, a100.y, a010.y, a110.y, a001.y, a101.y, a011.y, a111.y) * vv[1];
+            acc += tri(a000.z, a100.z, a010.z, a110.z, a001.z, a101.z, a011.z, a111.z) * vv[2];
+        } else {
 #pragma unroll
-        for (int u = 0; u < kInterpSPT; ++u) {
-            const int64_t t = min(base + u * (int64_t)blockDim.x, T - 1);
-            if constexpr (PRE) q[u] = rec[t];
-            else q[u] = make_rec3<R>(r[3 * t], r[3 * t + 1], r[3 * t + 2], ax);
-#pragma unroll
-            for (int m = 0; m < 3; ++m) vv[u][m] = v[3 * t + m];
-        }
-#pragma unroll
-        for (int u = 0; u < kInterpSPT; ++u) {
-            const int64_t t = base + u * (int64_t)blockDim.x;
-            const int i0 = q[u].i0, j0 = q[u].j0, l0 = q[u].l0;
-            const int i1 = nx > 1 ? i0 + 1 : i0, j1 = ny > 1 ? j0 + 1 : j0, l1 = ax.z.n > 1 ? l0 + 1 : l0;
-            const R wx1 = q[u].wx1, wy1 = q[u].wy1, wz1 = q[u].wz1;
-            const R wx0 = R(1) - wx1, wy0 = R(1) - wy1, wz0 = R(1) - wz1;
-            const int64_t r00 = ((int64_t)l0 * ny + j0) * nx, r01 = ((int64_t)l0 * ny + j1) * nx;
-            const int64_t r10 = ((int64_t)l1 * ny + j0) * nx, r11 = ((int64_t)l1 * ny + j1) * nx;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                R acc = R(0);
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const AT *F = A + (CH < 0 ? 3 * k + m : m) * N;
-                    const R lo = wy0 * (wx0 * R(F[r00 + i0]) + wx1 * R(F[r00 + i1])) +
-                                 wy1 * (wx0 * R(F[r01 + i0]) + wx1 * R(F[r01 + i1]));
-                    const R hi = wy0 * (wx0 * R(F[r10 + i0]) + wx1 * R(F[r10 + i1])) +
-                                 wy1 * (wx0 * R(F[r11 + i0]) + wx1 * R(F[r11 + i1]));
-                    acc += (wz0 * lo + wz1 * hi) * vv[u][m];
-                }
-                if (t < T) s[(int64_t)k * T + t] = acc;
+            for (int m = 0; m < 3; ++m) {
+                const AT *F = A + (CH < 0 ? 3 * k + m : m) * N;
+                const R lo = wy0 * (wx0 * R(F[r00 + i0]) + wx1 * R(F[r00 + i1])) +
+                             wy1 * (wx0 * R(F[r01 + i0]) + wx1 * R(F[r01 + i1]));
+                const R hi = wy0 * (wx0 * R(F[r10 + i0]) + wx1 * R(F[r10 + i1])) +
+                             wy1 * (wx0 * R(F[r11 + i0]) + wx1 * R(F[r11 + i1]));
+                acc += (wz0 * lo + wz1 * hi) * vv[m];
             }
         }
+        s[e] = acc;
     }
+}
+
+// A4[node K + k] = (A_{3k}, A_{3k+1}, A_{3k+2}, 0) rounded to FP32 from the
+// component-major FP64 field x (K = 3: nine components; K = 1: three).
+__global__ void k_round_field3_il(int64_t N, int K, const double *__restrict__ x, float4 *__restrict__ A4)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < K; ++k)
+            A4[e * K + k] = make_float4(float(x[(3 * k) * N + e]), float(x[(3 * k + 1) * N + e]),
+                                        float(x[(3 * k + 2) * N + e]), 0.0f);
 }
 
 template <typename R>
@@ -114,120 +135,228 @@ __global__ void k_cell_count3(int64_t T, const R *__restrict__ r, Axes3 ax, int 
     }
 }
 
-// Calls f(cell) for the (up to) eight cells around node (i, j, l), in
-// ascending cell order.
-template <typename F>
-__device__ __forceinline__ void for_node_cells3(int i, int j, int l, int ncx, int ncy, int ncz, F &&f)
+// The transpose (Ahat_{3k+m}(node) = sum over the samples t of the node's
+// adjacent cells of w_node(t) v_m(t) s_k(t)) runs by cell: each cell's run of
+// samples (list order) is split into work units of at most kUnitLen3
+// entries, one warp per unit.  Lane = 8 g + corner: the lane takes corner
+// node `corner` = dx + 2 dy + 4 dz of the cell and every 4th entry from g
+// (the eight corner lanes of a group read the same sample: one request per
+// entry for all corners), and a fixed two-level butterfly adds the four
+// groups.  The unit that completes its cell last (a per-cell arrival counter)
+// adds the cell's units in order into one sum per corner and component, so a
+// node combines exactly one value per adjacent cell, however many samples
+// the trajectory leaves in it (a 3-D trajectory leaves most cells empty and
+// piles hundreds of samples into a few).  A sample is read once instead of
+// once per corner node.
+#ifndef MPI_UNIT_LEN3
+#define MPI_UNIT_LEN3 64
+#endif
+constexpr int kUnitLen3 = MPI_UNIT_LEN3;
+constexpr int kT3Groups = 4;                      // entry groups per unit (lanes = 8 corners x 4)
+constexpr int kT3UnitsPerBlock = kUnitThreads / 32;
+
+__global__ void k_cunit_count3(int n_cells, const int *__restrict__ offset, int *__restrict__ cunit_cnt)
 {
-    for (int cl = max(l - 1, 0); cl <= min(l, ncz - 1); ++cl)
-        for (int cj = max(j - 1, 0); cj <= min(j, ncy - 1); ++cj)
-            for (int ci = max(i - 1, 0); ci <= min(i, ncx - 1); ++ci) f((cl * ncy + cj) * ncx + ci);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x)
+        cunit_cnt[c] = (offset[c + 1] - offset[c] + kUnitLen3 - 1) / kUnitLen3;
 }
 
-__global__ void k_unit_count3(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restrict__ offset,
-                              int *__restrict__ unit_cnt)
+__global__ void k_cunit_fill3(int n_cells, const int *__restrict__ cunit_off, int *__restrict__ unit_cell)
 {
-    const int N = nx * ny * nz;
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
-        const int i = node % nx, j = (node / nx) % ny, l = node / (nx * ny);
-        int tot = 0;
-        for_node_cells3(i, j, l, ncx, ncy, ncz, [&](int c) { tot += offset[c + 1] - offset[c]; });
-        unit_cnt[node] = max(1, (tot + kUnitLen - 1) / kUnitLen);
-    }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x)
+        for (int w = cunit_off[c]; w < cunit_off[c + 1]; ++w) unit_cell[w] = c;
 }
 
-// Partial sums of one work unit: sum over its entries of w_node(t) v_m(t)
-// s_k(t) (records, velocities and s in list order).  CH < 0: 9 sums; CH = k:
-// channel k only (s one row), 3 sums.  n_iter: the unit bound rounded up to
-// whole blocks, so every warp runs the same iterations and its shuffles see
-// full warps.
+// A cell's corner sums as an unevaluated pair hi + lo (FP32: the error-free
+// double-float sum of its unit sums; FP64: lo = 0).
+__device__ __forceinline__ void cell_add(SumAcc<float> &a, V2<float> v) { a.s.add(F2Sum{v.x, v.y}); }
+__device__ __forceinline__ void cell_add(SumAcc<double> &a, V2<double> v) { a.add(v.x); }
+__device__ __forceinline__ V2<float> cell_pair(const SumAcc<float> &a) { return V2<float>{a.s.hi, a.s.lo}; }
+__device__ __forceinline__ V2<double> cell_pair(const SumAcc<double> &a) { return V2<double>{a.s, 0.0}; }
+
+// Unit sums and cell sums of the transpose: unit_part[(w 8 + corner) NC + m]
+// and, at the cell's first unit u0, cell_part[(u0 8 + corner) NC + m] =
+// the cell's corner-`corner` sum of w_dx w_dy w_dz v_m s_k (CH < 0: 9 sums,
+// component 3k + m; CH = k: channel k only, 3 sums).  cell_cnt: zero on entry
+// and on exit.
 template <typename R, int CH>
 __global__ void __launch_bounds__(kUnitThreads)
-k_interp3_T_units(const InterpRec3<R> *__restrict__ rec, const R *__restrict__ vs, const R *__restrict__ s,
-                  int64_t T, int nx, int ny, int ncx, int ncy, int ncz, const int *__restrict__ offset,
-                  const int *__restrict__ unit_off, const int *__restrict__ unit_node, int N, int n_iter,
-                  R *__restrict__ unit_part)
+k_interp3_T_cells(const InterpRec3<R> *__restrict__ rec, const R *__restrict__ vs, const R *__restrict__ s,
+                  int64_t T, const int *__restrict__ offset, const int *__restrict__ cunit_off,
+                  const int *__restrict__ unit_cell, const int *__restrict__ n_units_dev, int n_iter,
+                  R *__restrict__ unit_part, V2<R> *__restrict__ cell_part, unsigned *__restrict__ cell_cnt)
 {
     constexpr int NC = CH < 0 ? 9 : 3;
-    constexpr int G = kUnitLanes;
-    constexpr int per_block = kUnitThreads / G;
-    const int sub = threadIdx.x % G;
-    const int n_units = unit_off[N];
-    for (int base = blockIdx.x * per_block; base < n_iter; base += gridDim.x * per_block) {
-        const int w = base + (int)threadIdx.x / G;
+    const int lane = threadIdx.x & 31, corner = lane & 7, g = lane >> 3;
+    const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+    const int n_units = *n_units_dev;
+    for (int base = blockIdx.x * kT3UnitsPerBlock; base < n_iter; base += gridDim.x * kT3UnitsPerBlock) {
+        const int w = base + (int)(threadIdx.x >> 5);  // warp-uniform
+        if (w >= n_units) continue;
         R acc[NC];
 #pragma unroll
         for (int m = 0; m < NC; ++m) acc[m] = R(0);
-        if (w < n_units) {
-            const int node = unit_node[w];
-            const int i = node % nx, j = (node / nx) % ny, l = node / (nx * ny);
-            const int p0 = (w - unit_off[node]) * kUnitLen, p1 = p0 + kUnitLen;
-            int pos = 0;
-            for_node_cells3(i, j, l, ncx, ncy, ncz, [&](int c) {
-                const int q_base = offset[c], cnt = offset[c + 1] - q_base;
-                const int lo = max(p0, pos), hi = min(p1, pos + cnt);
-#pragma unroll 2
-                for (int pp = lo + sub; pp < hi; pp += G) {
-                    const int q = q_base + (pp - pos);
-                    const InterpRec3<R> rc = rec[q];
-                    const R wx = (i == rc.i0) ? R(1) - rc.wx1 : rc.wx1;
-                    const R wy = (j == rc.j0) ? R(1) - rc.wy1 : rc.wy1;
-                    const R wz = (l == rc.l0) ? R(1) - rc.wz1 : rc.wz1;
-                    const R wt = wz * (wy * wx);
-                    const R v0 = vs[3 * q], v1 = vs[3 * q + 1], v2 = vs[3 * q + 2];
-                    if constexpr (CH < 0) {
+        const int c = unit_cell[w];
+        const int u0 = cunit_off[c], nu = cunit_off[c + 1] - u0;
+        const int q0 = offset[c] + (w - u0) * kUnitLen3;
+        const int q1 = min(offset[c + 1], q0 + kUnitLen3);
+#pragma unroll 4
+        for (int q = q0 + g; q < q1; q += kT3Groups) {
+            const InterpRec3<R> rc = rec[q];
+            const R wx = dx ? rc.wx1 : R(1) - rc.wx1;
+            const R wy = dy ? rc.wy1 : R(1) - rc.wy1;
+            const R wz = dz ? rc.wz1 : R(1) - rc.wz1;
+            const R wt = wz * (wy * wx);
+            const R v0 = vs[3 * q], v1 = vs[3 * q + 1], v2 = vs[3 * q + 2];
+            if constexpr (CH < 0) {
 #pragma unroll
-                        for (int kk = 0; kk < 3; ++kk) {
-                            const R sk = wt * s[(int64_t)kk * T + q];
-                            acc[3 * kk] += v0 * sk;
-                            acc[3 * kk + 1] += v1 * sk;
-                            acc[3 * kk + 2] += v2 * sk;
-                        }
-                    } else {
-                        const R sk = wt * s[q];
-                        acc[0] += v0 * sk;
-                        acc[1] += v1 * sk;
-                        acc[2] += v2 * sk;
-                    }
+                for (int kk = 0; kk < 3; ++kk) {
+                    const R sk = wt * s[(int64_t)kk * T + q];
+                    acc[3 * kk] += v0 * sk;
+                    acc[3 * kk + 1] += v1 * sk;
+                    acc[3 * kk + 2] += v2 * sk;
                 }
-                pos += cnt;
-            });
+            } else {
+                const R sk = wt * s[q];
+                acc[0] += v0 * sk;
+                acc[1] += v1 * sk;
+                acc[2] += v2 * sk;
+            }
         }
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+            acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], 8);
+            acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], 16);
         }
-        if (sub == 0 && w < n_units) {
+        if (nu == 1) {  // the cell's only unit: its sums are the cell's
+            if (g == 0) {
 #pragma unroll
-            for (int m = 0; m < NC; ++m) unit_part[(int64_t)w * NC + m] = acc[m];
+                for (int m = 0; m < NC; ++m) cell_part[((int64_t)u0 * 8 + corner) * NC + m] = V2<R>{acc[m], R(0)};
+            }
+            continue;
+        }
+        if (g == 0) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) unit_part[((int64_t)w * 8 + corner) * NC + m] = acc[m];
+        }
+        __threadfence();  // each lane's unit sums visible device-wide before the arrival
+        __syncwarp();
+        unsigned prev = 0;
+        if (lane == 0) prev = atomicAdd(&cell_cnt[c], 1u);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev != unsigned(nu - 1)) continue;  // another unit of the cell finishes it
+        if (lane == 0) cell_cnt[c] = 0u;
+        __threadfence();
+        if (g == 0) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                SumAcc<R> a = {};
+                for (int u = u0; u < u0 + nu; ++u) a.add(__ldcg(unit_part + ((int64_t)u * 8 + corner) * NC + m));
+                cell_part[((int64_t)u0 * 8 + corner) * NC + m] = cell_pair(a);
+            }
         }
     }
 }
 
-// out_m = Lap x_m (7-point, replicated boundary) for the nc components, FP64.
-// scaled: per-axis second differences with 1/dx^2, 1/dy^2, 1/dz^2 (c).
+// The combine of one unknown (component m of the node at i, j, l): the sum,
+// over the node's adjacent non-empty cells in ascending cell order, of the
+// cell sums of the corner the node is in that cell.
+template <typename R, int NC>
+__device__ __forceinline__ double node_combine3(int i, int j, int l, int m, int ncx, int ncy, int ncz,
+                                                const int *__restrict__ cunit_off,
+                                                const V2<R> *__restrict__ cell_part)
+{
+    SumAcc<R> sum = {};
+#pragma unroll
+    for (int dz = 1; dz >= 0; --dz)
+#pragma unroll
+        for (int dy = 1; dy >= 0; --dy)
+#pragma unroll
+            for (int dx = 1; dx >= 0; --dx) {
+                const int cl = l - dz, cj = j - dy, ci = i - dx;
+                if (cl < 0 || cl >= ncz || cj < 0 || cj >= ncy || ci < 0 || ci >= ncx) continue;
+                const int cc = (cl * ncy + cj) * ncx + ci;
+                const int u0 = cunit_off[cc];
+                if (cunit_off[cc + 1] == u0) continue;
+                cell_add(sum, cell_part[((int64_t)u0 * 8 + dx + 2 * dy + 4 * dz) * NC + m]);
+            }
+    return sum.value();
+}
+
+// Ahat_m(node) = scale * node_combine3 for all NC components.
+template <typename R, typename OUT, int NC>
+__global__ void k_interp3_T_cell_combine(int nx, int ny, int nz, int ncx, int ncy, int ncz,
+                                         const int *__restrict__ cunit_off, const V2<R> *__restrict__ cell_part,
+                                         OUT *__restrict__ A, double scale)
+{
+    const int N = nx * ny * nz;  // < 2^27
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NC * N; e += gridDim.x * blockDim.x) {
+        const int m = e / N, node = e - m * N;
+        const int i = node % nx, j = (node / nx) % ny, l = node / (nx * ny);
+        A[e] = OUT(node_combine3<R, NC>(i, j, l, m, ncx, ncy, ncz, cunit_off, cell_part) * scale);
+    }
+}
+
+// (Lap f)(node k at i, j, l): 7-point, replicated boundary (a missing
+// neighbour is the node itself), FP64.  scaled: per-axis second differences
+// with 1/dx^2, 1/dy^2, 1/dz^2 (c); else the plain stencil.
+__device__ __forceinline__ double lap3_at(const double *__restrict__ f, int64_t k, int i, int j, int l, int nx,
+                                          int ny, int nz, bool scaled, double3 c)
+{
+    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+    const int64_t xm = i > 0 ? -sx : 0, xp = i < nx - 1 ? sx : 0;
+    const int64_t ym = j > 0 ? -sy : 0, yp = j < ny - 1 ? sy : 0;
+    const int64_t zm = l > 0 ? -sz : 0, zp = l < nz - 1 ? sz : 0;
+    if (scaled) {
+        const double c0 = f[k];
+        return c.x * (f[k + xm] - 2.0 * c0 + f[k + xp]) + c.y * (f[k + ym] - 2.0 * c0 + f[k + yp]) +
+               c.z * (f[k + zm] - 2.0 * c0 + f[k + zp]);
+    }
+    return f[k + xm] + f[k + xp] + f[k + ym] + f[k + yp] + f[k + zm] + f[k + zp] - 6.0 * f[k];
+}
+
+// out_m = Lap x_m for the nc components.
 __global__ void k_lap3(int nx, int ny, int nz, int nc, bool scaled, double3 c, const double *__restrict__ x,
                        double *__restrict__ out)
 {
-    const int64_t N = (int64_t)nx * ny * nz;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * N;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = e / N, k = e % N;
-        const int i = (int)(k % nx), j = (int)((k / nx) % ny), l = (int)(k / ((int64_t)nx * ny));
-        const double *f = x + m * N;
-        const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
-        const int64_t xm = i > 0 ? -sx : 0, xp = i < nx - 1 ? sx : 0;
-        const int64_t ym = j > 0 ? -sy : 0, yp = j < ny - 1 ? sy : 0;
-        const int64_t zm = l > 0 ? -sz : 0, zp = l < nz - 1 ? sz : 0;
-        if (scaled) {
-            const double c0 = f[k];
-            out[e] = c.x * (f[k + xm] - 2.0 * c0 + f[k + xp]) + c.y * (f[k + ym] - 2.0 * c0 + f[k + yp]) +
-                     c.z * (f[k + zm] - 2.0 * c0 + f[k + zp]);
-        } else {
-            out[e] = f[k + xm] + f[k + xp] + f[k + ym] + f[k + yp] + f[k + zm] + f[k + zp] - 6.0 * f[k];
-        }
+    // nc N < 2^31 (grids of fewer than 2^27 nodes): 32-bit index arithmetic
+    const int N = nx * ny * nz;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * N; e += gridDim.x * blockDim.x) {
+        const int m = e / N, k = e - m * N;
+        const int i = k % nx, j = (k / nx) % ny, l = k / (nx * ny);
+        out[e] = lap3_at(x + (int64_t)m * N, k, i, j, l, nx, ny, nz, scaled, c);
     }
+}
+
+// One Core Stage step's operator after the transpose's cell sums, for every
+// unknown e = m N + node: y = scale * node_combine3, q = y + gamma (Lap l1)(e)
+// with l1 = Lap p, written to q, and the partial sums of <p, q> over blocks
+// of kQPer3 consecutive unknowns, finished into alpha by the last block.
+constexpr int kQThreads3 = 256, kQPer3 = 512;
+template <typename R, int NC>
+__global__ void __launch_bounds__(kQThreads3)
+k_grid3_q(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restrict__ cunit_off,
+          const V2<R> *__restrict__ cell_part, double scale, bool scaled, double3 c, double gamma,
+          const double *__restrict__ l1, const double *__restrict__ p, double *__restrict__ q,
+          double *__restrict__ pq_part, CsScal *sc)
+{
+    __shared__ double sh[kQThreads3 / 32];
+    __shared__ bool last;
+    // NC N < 2^31 (grids of fewer than 2^27 nodes): 32-bit index arithmetic
+    const int N = nx * ny * nz, nv = NC * N;
+    const int e0 = blockIdx.x * kQPer3, e1 = min(nv, e0 + kQPer3);
+    double acc = 0.0;
+    for (int e = e0 + threadIdx.x; e < e1; e += kQThreads3) {
+        const int m = e / N, node = e - m * N;
+        const int i = node % nx, j = (node / nx) % ny, l = node / (nx * ny);
+        const double y = node_combine3<R, NC>(i, j, l, m, ncx, ncy, ncz, cunit_off, cell_part) * scale;
+        const double qe = y + gamma * lap3_at(l1 + (int64_t)m * N, node, i, j, l, nx, ny, nz, scaled, c);
+        q[e] = qe;
+        acc += p[e] * qe;
+    }
+    acc = block_sum<double, kQThreads3>(acc, sh);
+    if (threadIdx.x == 0) pq_part[blockIdx.x] = acc;
+    cs_finish_pq<kQThreads3>(pq_part, gridDim.x, sc, sh, &last);
 }
 
 // Ahat and its trace (all channels: A_00 + A_11 + A_22; channel k: A_kk,
@@ -248,29 +377,34 @@ __global__ void k_grid3_output(int64_t N, int ch, const double *__restrict__ x, 
 struct Bins3 {
     int *cell_of, *count, *offset, *cursor, *list;
     void *rec_t, *rec, *vs;
-    int *unit_cnt, *unit_off, *unit_cursor, *unit_node;
-    void *unit_part;
-    int n_units_max;
+    int *cunit_cnt, *cunit_off, *cunit_cursor, *unit_cell;  // transpose work units per cell
+    void *unit_part;  // 8 corners x (9 or 3) sums per unit
+    void *cell_part;  // V2<R>: the cell's corner sums, at its first unit's slot
+    unsigned *cell_cnt;  // per-cell arrival counters of the units
+    int n_units_max;  // bound on the units (allocation)
+    int n_units = -1;  // the exact count when read back to the host, else -1
     int ncx, ncy, ncz;
 };
 
 inline size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
-int units_bound3(int64_t T, int64_t N)
+// Units of the cell runs: at most one per kUnitLen3 samples plus one per
+// non-empty cell.
+int units_bound3(int64_t T, int64_t nc)
 {
-    // Every sample lies in one cell and so in the runs of at most 8 nodes.
-    return (int)std::min<int64_t>(INT32_MAX, N + (8 * T + kUnitLen - 1) / kUnitLen + 1);
+    return (int)std::min<int64_t>(INT32_MAX, (T + kUnitLen3 - 1) / kUnitLen3 + std::min<int64_t>(T, nc) + 1);
 }
 
 template <typename R>
 size_t bins3_bytes(int64_t T, const G3 &g)
 {
     const size_t nc = size_t(std::max(g.nx - 1, 1)) * std::max(g.ny - 1, 1) * std::max(g.nz - 1, 1);
-    const size_t N = size_t(g.n()), U = size_t(units_bound3(T, g.n()));
+    const size_t U = size_t(units_bound3(T, int64_t(nc)));
     const size_t T1 = size_t(std::max<int64_t>(T, 1));
     return up256(sizeof(int) * T1) * 2 + up256(sizeof(int) * nc) * 2 + up256(sizeof(int) * (nc + 1)) +
-           2 * up256(sizeof(InterpRec3<R>) * T1) + up256(3 * sizeof(R) * T1) + up256(sizeof(int) * N) * 2 +
-           up256(sizeof(int) * (N + 1)) + up256(sizeof(int) * U) + up256(9 * sizeof(R) * U);
+           2 * up256(sizeof(InterpRec3<R>) * T1) + up256(3 * sizeof(R) * T1) + up256(sizeof(int) * nc) * 2 +
+           up256(sizeof(int) * (nc + 1)) + up256(sizeof(int) * U) + up256(8 * 9 * sizeof(R) * U) +
+           up256(8 * 9 * sizeof(V2<R>) * U) + up256(sizeof(unsigned) * nc);
 }
 
 template <typename R>
@@ -290,13 +424,14 @@ Bins3 bins3_carve(char *p, int64_t T, const G3 &g)
     b.rec_t = p; p += up256(sizeof(InterpRec3<R>) * T1);
     b.rec = p; p += up256(sizeof(InterpRec3<R>) * T1);
     b.vs = p; p += up256(3 * sizeof(R) * T1);
-    const size_t N = size_t(g.n());
-    b.n_units_max = units_bound3(T, g.n());
-    b.unit_cnt = reinterpret_cast<int *>(p); p += up256(sizeof(int) * N);
-    b.unit_cursor = reinterpret_cast<int *>(p); p += up256(sizeof(int) * N);
-    b.unit_off = reinterpret_cast<int *>(p); p += up256(sizeof(int) * (N + 1));
-    b.unit_node = reinterpret_cast<int *>(p); p += up256(sizeof(int) * size_t(b.n_units_max));
-    b.unit_part = p;
+    b.n_units_max = units_bound3(T, int64_t(nc));
+    b.cunit_cnt = reinterpret_cast<int *>(p); p += up256(sizeof(int) * nc);
+    b.cunit_cursor = reinterpret_cast<int *>(p); p += up256(sizeof(int) * nc);
+    b.cunit_off = reinterpret_cast<int *>(p); p += up256(sizeof(int) * (nc + 1));
+    b.unit_cell = reinterpret_cast<int *>(p); p += up256(sizeof(int) * size_t(b.n_units_max));
+    b.unit_part = p; p += up256(8 * 9 * sizeof(R) * size_t(b.n_units_max));
+    b.cell_part = p; p += up256(8 * 9 * sizeof(V2<R>) * size_t(b.n_units_max));
+    b.cell_cnt = reinterpret_cast<unsigned *>(p);
     return b;
 }
 
@@ -311,6 +446,7 @@ int build_bins3(const G3 &g, int64_t T, const R *r, const R *v, const Bins3 &b, 
     const Axes3 ax = axes_of(g);
     const int nc = b.ncx * b.ncy * b.ncz;
     MPI_TRY_CUDA(cudaMemsetAsync(b.count, 0, sizeof(int) * nc, st));
+    MPI_TRY_CUDA(cudaMemsetAsync(b.cell_cnt, 0, sizeof(unsigned) * nc, st));
     if (T > 0) {
         k_cell_count3<R><<<grid_blocks(T), 256, 0, st>>>(T, r, ax, b.ncx, b.ncy, b.cell_of, b.count,
                                                           static_cast<InterpRec3<R> *>(b.rec_t));
@@ -325,21 +461,33 @@ int build_bins3(const G3 &g, int64_t T, const R *r, const R *v, const Bins3 &b, 
             static_cast<R *>(b.vs));
         MPI_CHECK_LAUNCH();
     }
-    const int N = (int)g.n();
-    k_unit_count3<<<grid_blocks(N), 256, 0, st>>>(g.nx, g.ny, g.nz, b.ncx, b.ncy, b.ncz, b.offset, b.unit_cnt);
+    // Work units of the transpose.
+    k_cunit_count3<<<grid_blocks(nc), 256, 0, st>>>(nc, b.offset, b.cunit_cnt);
     MPI_CHECK_LAUNCH();
-    MPI_TRY(cell_scan_launch(b.unit_cnt, N, b.unit_off, b.unit_cursor, st));
-    return unit_fill_launch(N, b.unit_off, b.unit_node, st);
+    MPI_TRY(cell_scan_launch(b.cunit_cnt, nc, b.cunit_off, b.cunit_cursor, st));
+    k_cunit_fill3<<<grid_blocks(nc), 256, 0, st>>>(nc, b.cunit_off, b.unit_cell);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
 }
 
+// il: the FP32 field in the node-interleaved layout of k_round_field3_il
+// (records precomputed).
 template <typename R, typename AT>
 int launch_interp3(const G3 &g, int64_t T, const R *r, const R *v, const AT *A, R *s, cudaStream_t st,
-                   int ch = -1, const InterpRec3<R> *rec = nullptr)
+                   int ch = -1, const InterpRec3<R> *rec = nullptr, bool il = false)
 {
     if (T == 0) return MPI_OK;
     const Axes3 ax = axes_of(g);
-    const int blocks =
-        (int)std::max<int64_t>(1, std::min<int64_t>((T + 256 * kInterpSPT - 1) / (256 * kInterpSPT), 8192));
+    const int64_t outs = (ch < 0 ? 3 : 1) * T;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((outs + 255) / 256, 16384));
+    if constexpr (sizeof(AT) == 4) {
+        if (il) {
+            if (ch < 0) k_interp3<R, AT, -1, true, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, s);
+            else k_interp3<R, AT, 0, true, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, s);
+            MPI_CHECK_LAUNCH();
+            return MPI_OK;
+        }
+    }
     if (rec) {
         if (ch < 0) k_interp3<R, AT, -1, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, s);
         else k_interp3<R, AT, 0, true><<<blocks, 256, 0, st>>>(T, r, rec, v, A, ax, s);
@@ -351,35 +499,60 @@ int launch_interp3(const G3 &g, int64_t T, const R *r, const R *v, const AT *A, 
     return MPI_OK;
 }
 
+// The transpose's unit sums (k_interp3_T_cells) into b.unit_part.
 // s_sorted: the samples' values in list order ([rows][T]).
-template <typename R, typename OUT>
-int launch_interp3_T(const G3 &g, int64_t T, const R *s_sorted, const Bins3 &b, OUT *A, double scale,
-                     cudaStream_t st, int ch = -1)
+template <typename R>
+int launch_interp3_T_units(int64_t T, const R *s_sorted, const Bins3 &b, cudaStream_t st, int ch)
 {
-    const int N = (int)g.n();
-    constexpr int per_block = kUnitThreads / kUnitLanes;
-    const int n_iter = (b.n_units_max + per_block - 1) / per_block * per_block;
+    const int nc = b.ncx * b.ncy * b.ncz;
+    constexpr int per_block = kT3UnitsPerBlock;
+    // Blocks for the exact unit count where the host has it, else for the
+    // bound (the real count is on the device, cunit_off[nc], and surplus
+    // blocks exit at once).
+    const int units = b.n_units >= 0 ? b.n_units : b.n_units_max;
+    const int n_iter = (units + per_block - 1) / per_block * per_block;
     const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, 65535));
     const InterpRec3<R> *rec = static_cast<const InterpRec3<R> *>(b.rec);
     const R *vs = static_cast<const R *>(b.vs);
     R *part = static_cast<R *>(b.unit_part);
+    V2<R> *cpart = static_cast<V2<R> *>(b.cell_part);
+    const int *n_units = b.cunit_off + nc;
     if (ch < 0)
-        k_interp3_T_units<R, -1><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, g.nx, g.ny, b.ncx, b.ncy,
-                                                                  b.ncz, b.offset, b.unit_off, b.unit_node, N,
-                                                                  n_iter, part);
+        k_interp3_T_cells<R, -1><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, b.offset, b.cunit_off,
+                                                                  b.unit_cell, n_units, n_iter, part, cpart,
+                                                                  b.cell_cnt);
     else
-        k_interp3_T_units<R, 0><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, g.nx, g.ny, b.ncx, b.ncy,
-                                                                 b.ncz, b.offset, b.unit_off, b.unit_node, N,
-                                                                 n_iter, part);
+        k_interp3_T_cells<R, 0><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, b.offset, b.cunit_off,
+                                                                 b.unit_cell, n_units, n_iter, part, cpart,
+                                                                 b.cell_cnt);
     MPI_CHECK_LAUNCH();
-    if (ch < 0) k_interp_T_combine<R, OUT, 9><<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, part, A, scale);
-    else k_interp_T_combine<R, OUT, 3><<<grid_blocks(N), 256, 0, st>>>(N, b.unit_off, part, A, scale);
+    return MPI_OK;
+}
+
+// A = scale M^T s (all nine components, or channel ch's three).
+template <typename R, typename OUT>
+int launch_interp3_T(const G3 &g, int64_t T, const R *s_sorted, const Bins3 &b, OUT *A, double scale,
+                     cudaStream_t st, int ch = -1)
+{
+    MPI_TRY(launch_interp3_T_units<R>(T, s_sorted, b, st, ch));
+    const int64_t N = g.n();
+    const V2<R> *cpart = static_cast<const V2<R> *>(b.cell_part);
+    if (ch < 0)
+        k_interp3_T_cell_combine<R, OUT, 9><<<grid_blocks(9 * N), 256, 0, st>>>(
+            g.nx, g.ny, g.nz, b.ncx, b.ncy, b.ncz, b.cunit_off, cpart, A, scale);
+    else
+        k_interp3_T_cell_combine<R, OUT, 3><<<grid_blocks(3 * N), 256, 0, st>>>(
+            g.nx, g.ny, g.nz, b.ncx, b.ncy, b.ncz, b.cunit_off, cpart, A, scale);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
 
 // The 3-D Core Stage operator: (1/T) M^T M through the binned records and
-// the 7-point Laplacian of each component.
+// the 7-point Laplacian of each component.  A step runs fused (step_q): the
+// field rounded to FP32 in the interleaved layout (FP32 path), M p, the
+// transpose's unit and cell sums, l1 = Lap p, and one pass forming
+// q = (1/T) M^T M p + gamma Lap l1 with the partial sums of <p, q> and alpha
+// -- five launches where the composed form takes seven.
 template <typename R>
 struct GridOp3 final : CoreStageOp {
     const G3 &g;
@@ -387,30 +560,61 @@ struct GridOp3 final : CoreStageOp {
     int ch, nc;
     const Bins3 &bins;
     R *s_tmp;
-    R *p_r;  // FP32 path: the field rounded to R (nc N values); FP64: unused
+    float4 *p_il;  // FP32 path: the field rounded, interleaved (K N float4); FP64: unused
     double invT;
     bool scaled;
-    GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_, R *p_r_, bool scaled_)
-        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 9 : 3), bins(b_), s_tmp(s_tmp_), p_r(p_r_),
+    GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_, float4 *p_il_, bool scaled_)
+        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 9 : 3), bins(b_), s_tmp(s_tmp_), p_il(p_il_),
           invT(T_ > 0 ? 1.0 / double(T_) : 0.0), scaled(scaled_) {}
-    int normal(const double *p, double *y, cudaStream_t st) override
+    double3 lap_coef() const
+    {
+        return make_double3(1.0 / (g.dx * g.dx), 1.0 / (g.dy * g.dy), 1.0 / (g.dz * g.dz));
+    }
+    // s_tmp = M p (list order).
+    int forward(const double *p, cudaStream_t st)
     {
         const InterpRec3<R> *rec = static_cast<const InterpRec3<R> *>(bins.rec);
         const R *vs = static_cast<const R *>(bins.vs);
         if constexpr (sizeof(R) == 4) {
-            const int64_t n = int64_t(nc) * g.n();
-            k_round_field<R><<<grid_blocks(n), 256, 0, st>>>(n, p, p_r);
+            const int K = ch < 0 ? 3 : 1;
+            k_round_field3_il<<<grid_blocks(g.n()), 256, 0, st>>>(g.n(), K, p, p_il);
             MPI_CHECK_LAUNCH();
-            MPI_TRY((launch_interp3<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec)));
+            return launch_interp3<R, float>(g, T, nullptr, vs, reinterpret_cast<const float *>(p_il), s_tmp, st,
+                                            ch, rec, true);
         } else {
-            MPI_TRY((launch_interp3<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
+            return launch_interp3<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec);
         }
+    }
+    int normal(const double *p, double *y, cudaStream_t st) override
+    {
+        MPI_TRY(forward(p, st));
         return launch_interp3_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch);
     }
     int lap(const double *x, double *out, cudaStream_t st) override
     {
-        const double3 c = make_double3(1.0 / (g.dx * g.dx), 1.0 / (g.dy * g.dy), 1.0 / (g.dz * g.dz));
-        k_lap3<<<grid_blocks(nc * g.n()), 256, 0, st>>>(g.nx, g.ny, g.nz, nc, scaled, c, x, out);
+        k_lap3<<<grid_blocks(nc * g.n()), 256, 0, st>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), x, out);
+        MPI_CHECK_LAUNCH();
+        return MPI_OK;
+    }
+    bool fused() const override { return true; }
+    int pq_blocks(int64_t nv) const override { return (int)std::max<int64_t>(1, (nv + kQPer3 - 1) / kQPer3); }
+    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *, double *l1,
+               cudaStream_t st) override
+    {
+        MPI_TRY(forward(p, st));
+        MPI_TRY(launch_interp3_T_units<R>(T, s_tmp, bins, st, ch));
+        MPI_TRY(lap(p, l1, st));
+        const int64_t nv = int64_t(nc) * g.n();
+        const unsigned blocks = (unsigned)pq_blocks(nv);
+        const V2<R> *cpart = static_cast<const V2<R> *>(bins.cell_part);
+        if (ch < 0)
+            k_grid3_q<R, 9><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,
+                                                          bins.cunit_off, cpart, invT, scaled, lap_coef(), gamma,
+                                                          l1, p, q, pq_part, sc);
+        else
+            k_grid3_q<R, 3><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,
+                                                          bins.cunit_off, cpart, invT, scaled, lap_coef(), gamma,
+                                                          l1, p, q, pq_part, sc);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }
@@ -432,15 +636,28 @@ int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid
     const size_t o_s = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_sd = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_b = scr.reserve(sizeof(double) * nv), o_x = scr.reserve(sizeof(double) * nv);
-    const size_t o_pr = scr.reserve(sizeof(R) == 4 ? sizeof(R) * nv : 0);
+    const size_t o_pr = scr.reserve(sizeof(R) == 4 ? sizeof(float4) * rows * N : 0);
     MPI_TRY(scr.allocate());
-    const Bins3 bins = bins3_carve<R>(scr.at<char>(o_bins), T, g);
+    Bins3 bins = bins3_carve<R>(scr.at<char>(o_bins), T, g);
     R *s_data = scr.at<R>(o_sd);
     double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x);
 
     MPI_TRY(build_bins3<R>(g, T, r, v, bins, st));
     MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
-    GridOp3<R> op(g, T, ch, bins, scr.at<R>(o_s), scr.at<R>(o_pr), o.lap_scaled != 0);
+    // The transpose runs a few thousand times with the same units: read their
+    // count once, so every launch covers exactly them.
+    {
+        const int n_cells = bins.ncx * bins.ncy * bins.ncz;
+        int n_units = 0;
+        MPI_TRY_CUDA(cudaMemcpyAsync(&n_units, bins.cunit_off + n_cells, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPI_TRY_CUDA(cudaStreamSynchronize(st));
+        if (n_units < 0 || n_units > bins.n_units_max) {
+            set_error("3-D Core Stage: %d work units exceed the bound %d", n_units, bins.n_units_max);
+            return MPI_ERR_CUDA;
+        }
+        bins.n_units = n_units;
+    }
+    GridOp3<R> op(g, T, ch, bins, scr.at<R>(o_s), scr.at<float4>(o_pr), o.lap_scaled != 0);
     MPI_TRY((launch_interp3_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
     MPI_TRY(core_stage_cg(op, nv, b, o, x, n_iter_out, st));
     k_grid3_output<R><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));

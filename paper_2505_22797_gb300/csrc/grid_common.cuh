@@ -47,10 +47,10 @@ inline AxisMap make_axis(double p0, double h, int n)
 
 constexpr int kInterpSPT = 4;     // samples per thread of the interpolation (gathers in flight)
 // The transpose is organised in work units of at most kUnitLen consecutive
-// entries of a node's samples (its adjacent cells' runs, in cell order), so a
-// node next to cells where the trajectory dwells (thousands of samples)
-// spreads over many units instead of keeping one group of lanes busy alone.
-// Unit sums are combined per node in unit order (deterministic).
+// entries of a cell's run of samples, so a cell where the trajectory dwells
+// (thousands of samples) spreads over many units instead of keeping one
+// group of lanes busy alone.  A node combines the unit sums of its adjacent
+// cells in a fixed order (deterministic).
 constexpr int kUnitLen = 128;
 constexpr int kUnitLanes = 8;     // lanes per unit
 constexpr int kUnitThreads = 256;
@@ -65,16 +65,92 @@ int cell_scan_launch(const int *count, int n, int *offset, int *cursor, cudaStre
 int cell_fill_launch(int64_t T, const int *cell_of, int *cursor, int *list, cudaStream_t st);
 // Sorts each cell's run of list ascending.
 int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st);
-// unit_node[w] = node for the units unit_off[node] .. unit_off[node + 1].
-int unit_fill_launch(int N, const int *unit_off, int *unit_node, cudaStream_t st);
+
+// The step epilogue q = y + gamma Lap Lap p and the partial sums of <p, q>
+// run in blocks of kEpiThreads threads over kEpiPer consecutive elements.
+constexpr int kEpiThreads = 256, kEpiPer = 2048;
+
+// Device scalars of one Core Stage CG solve.  A reduction's partial sums are
+// added once per step, in a fixed order, by the block of the producing
+// kernel that arrives last at the reduction's counter (the next kernel reads
+// the finished scalar instead of every block re-adding the partials, which
+// costs FP64 work quadratic in the block count).  No block waits for another.
+struct CsScal {
+    double rr;            // r.r of the current residual
+    double alpha, beta;   // the step's coefficients
+    double bnorm, tol;    // ||b|| and the stop threshold on ||r|| (< 0: none)
+    unsigned cnt[4];      // arrival counters of the reductions (zero between launches)
+    int done;             // set once the solve has stopped
+    int iters;            // CG updates performed
+};
+enum { kCntPq = 0, kCntRr = 1, kCntInit = 2 };
+
+#ifdef __CUDACC__
+// Called by every thread after thread 0 wrote this block's partial: true in
+// the block that arrived last (which also re-arms the counter).  The partial
+// is made visible device-wide before the arrival is counted; the last block
+// reads the partials through L2 (cs_sum_parts).
+__device__ __forceinline__ bool cs_last_block(unsigned *cnt, bool *sh_last)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(cnt, 1u);
+        *sh_last = prev == gridDim.x - 1;
+        if (*sh_last) {
+            *cnt = 0u;
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return *sh_last;
+}
+
+// Sum of n partials in a fixed order (thread strides, then a fixed tree),
+// valid in thread 0.  The loads bypass L1: the partials come from other blocks.
+template <int NT>
+__device__ __forceinline__ double cs_sum_parts(const double *part, int n, double *sh /* >= NT/32 */)
+{
+    double a = 0.0;
+    for (int k = threadIdx.x; k < n; k += NT) a += __ldcg(part + k);
+    return block_sum<double, NT>(a, sh);
+}
+
+// After a step's <p, q> partials: pq, the stop test (stopped before, r.r or
+// p.q exactly zero -- converged to round-off -- or ||r|| at or below the
+// threshold) and alpha = r.r / p.q.  All threads call it.
+template <int NT>
+__device__ __forceinline__ void cs_finish_pq(const double *pq_part, int n, CsScal *sc, double *sh, bool *sh_last)
+{
+    if (!cs_last_block(&sc->cnt[kCntPq], sh_last)) return;
+    const double pq = cs_sum_parts<NT>(pq_part, n, sh);
+    if (threadIdx.x == 0) {
+        const double rr = sc->rr;
+        if (sc->done != 0 || rr == 0.0 || pq == 0.0 || (sc->tol >= 0.0 && sqrt(rr) <= sc->tol)) sc->done = 1;
+        else sc->alpha = rr / pq;
+    }
+}
+#endif
 
 // The operator of one Core Stage solve on nv FP64 unknowns (all components
 // of all nodes): y = (1/T) M^T M p and the Laplacian of every component.
-// Both methods only enqueue on `st`.
+// The methods only enqueue on `st`.
 struct CoreStageOp {
     virtual ~CoreStageOp() = default;
     virtual int normal(const double *p, double *y, cudaStream_t st) = 0;
     virtual int lap(const double *x, double *out, cudaStream_t st) = 0;
+    // An operator with a fused step (fused() true) forms q = (1/T) M^T M p +
+    // gamma Lap Lap p and the partial sums of <p, q> itself, in pq_blocks(nv)
+    // fixed blocks, with two FP64 work vectors of nv values; the solve then
+    // does not call normal() and lap().
+    virtual bool fused() const { return false; }
+    virtual int pq_blocks(int64_t nv) const { return (int)std::max<int64_t>(1, (nv + kEpiPer - 1) / kEpiPer); }
+    // pq_part: pq_blocks(nv) partials; the producing kernel finishes them
+    // with cs_finish_pq on sc.
+    virtual int step_q(const double *, double, double *, double *, CsScal *, double *, double *, cudaStream_t)
+    {
+        return MPI_ERR_UNSUPPORTED;
+    }
 };
 
 // CG from x = 0 on ((1/T) M^T M + gamma Lap Lap) x = b (Eq. first:step; Lap is
@@ -139,22 +215,6 @@ __global__ void k_round_field_il(int64_t N, int nc, const double *__restrict__ i
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
         for (int m = 0; m < nc; ++m) out[e * nc + m] = R(in[m * N + e]);
-}
-
-// Ahat_m(node) = scale * sum of the node's NC unit partials, in unit order
-// (FP32 partials summed as error-free double-float pairs).
-template <typename R, typename OUT, int NC>
-__global__ void k_interp_T_combine(int N, const int *__restrict__ unit_off, const R *__restrict__ unit_part,
-                                   OUT *__restrict__ A, double scale)
-{
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
-        SumAcc<R> acc[NC] = {};
-        for (int w = unit_off[node]; w < unit_off[node + 1]; ++w)
-#pragma unroll
-            for (int m = 0; m < NC; ++m) acc[m].add(unit_part[(int64_t)w * NC + m]);
-#pragma unroll
-        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(acc[m].value() * scale);
-    }
 }
 
 }  // namespace mpi

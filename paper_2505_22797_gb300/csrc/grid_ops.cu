@@ -214,14 +214,6 @@ __global__ void k_cell_sort(int n_cells, const int *__restrict__ offset, int *__
 // read once instead of once per corner node, and a cell where the trajectory
 // dwells (thousands of samples) spreads over many units.
 
-// unit_node[w] = node for the units unit_off[node] .. unit_off[node + 1]
-// (the node-unit transpose of the 3-D Core Stage).
-__global__ void k_unit_fill(int N, const int *__restrict__ unit_off, int *__restrict__ unit_node)
-{
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x)
-        for (int w = unit_off[node]; w < unit_off[node + 1]; ++w) unit_node[w] = node;
-}
-
 __global__ void k_cunit_count(int n_cells, const int *__restrict__ offset, int *__restrict__ cunit_cnt)
 {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x)
@@ -515,13 +507,14 @@ __global__ void k_lap(int nx, int ny, int nc, bool scaled, double cx, double cy,
     }
 }
 
-// q = y + gamma lap2, partial sums of <p, q> (blocks of 2048 elements).
-constexpr int kEpiThreads = 256, kEpiPer = 2048;
+// q = y + gamma lap2, partial sums of <p, q> (blocks of kEpiPer elements),
+// finished into the step's alpha by the last block.
 __global__ void __launch_bounds__(kEpiThreads)
 k_grid_epilogue(int64_t n, const double *__restrict__ y, const double *__restrict__ lap2, double gamma,
-                const double *__restrict__ p, double *__restrict__ q, double *__restrict__ dot_part)
+                const double *__restrict__ p, double *__restrict__ q, double *__restrict__ dot_part, CsScal *sc)
 {
     __shared__ double sh[kEpiThreads / 32];
+    __shared__ bool last;
     const int64_t e0 = (int64_t)blockIdx.x * kEpiPer, e1 = min(n, e0 + kEpiPer);
     double acc = 0.0;
     for (int64_t e = e0 + threadIdx.x; e < e1; e += kEpiThreads) {
@@ -531,15 +524,92 @@ k_grid_epilogue(int64_t n, const double *__restrict__ y, const double *__restric
     }
     acc = block_sum<double, kEpiThreads>(acc, sh);
     if (threadIdx.x == 0) dot_part[blockIdx.x] = acc;
+    cs_finish_pq<kEpiThreads>(dot_part, gridDim.x, sc, sh, &last);
 }
 
-__global__ void k_norm_thresh(const double *__restrict__ part, int n, double tol, double *out)
+// --- Core Stage CG vector kernels -----------------------------------------
+// Blocks of kCsThreads threads over kCsPer consecutive unknowns; each
+// reduction is finished by its last block (CsScal), so a kernel reads its
+// coefficient as one scalar.
+constexpr int kCsThreads = 256, kCsPer = 2048;
+inline int cs_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kCsPer - 1) / kCsPer); }
+
+// r = b, p = b (x = 0), r.r, ||b|| and the stop threshold rel_tol ||b||.
+__global__ void __launch_bounds__(kCsThreads)
+k_cs_init(int64_t n, const double *__restrict__ b, double *__restrict__ r, double *__restrict__ p,
+          double *__restrict__ rr_part, double rel_tol, CsScal *sc)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double a = 0.0;
-        for (int k = 0; k < n; ++k) a += part[k];
-        out[0] = sqrt(a);
-        out[1] = tol > 0.0 ? tol * sqrt(a) : -1.0;
+    __shared__ double sh[kCsThreads / 32];
+    __shared__ bool last;
+    const int64_t e0 = (int64_t)blockIdx.x * kCsPer;
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < kCsPer / kCsThreads; ++u) {
+        const int64_t e = e0 + u * kCsThreads + threadIdx.x;
+        if (e < n) {
+            const double be = b[e];
+            r[e] = be;
+            p[e] = be;
+            acc += be * be;
+        }
+    }
+    acc = block_sum<double, kCsThreads>(acc, sh);
+    if (threadIdx.x == 0) rr_part[blockIdx.x] = acc;
+    if (!cs_last_block(&sc->cnt[kCntInit], &last)) return;
+    const double rr = cs_sum_parts<kCsThreads>(rr_part, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        sc->rr = rr;
+        sc->bnorm = sqrt(rr);
+        sc->tol = rel_tol > 0.0 ? rel_tol * sqrt(rr) : -1.0;
+        sc->done = 0;
+        sc->iters = 0;
+    }
+}
+
+// x += alpha p, r -= alpha q, the new r.r and beta = r.r(new) / r.r(old);
+// counts the update.  Nothing once the solve has stopped.
+__global__ void __launch_bounds__(kCsThreads)
+k_cs_step1(int64_t n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+           const double *__restrict__ q, double *__restrict__ rr_part, CsScal *sc)
+{
+    __shared__ double sh[kCsThreads / 32];
+    __shared__ bool last;
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    const int64_t e0 = (int64_t)blockIdx.x * kCsPer;
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < kCsPer / kCsThreads; ++u) {
+        const int64_t e = e0 + u * kCsThreads + threadIdx.x;
+        if (e < n) {
+            x[e] = x[e] + alpha * p[e];
+            const double re = r[e] - alpha * q[e];
+            r[e] = re;
+            acc += re * re;
+        }
+    }
+    acc = block_sum<double, kCsThreads>(acc, sh);
+    if (threadIdx.x == 0) rr_part[blockIdx.x] = acc;
+    if (!cs_last_block(&sc->cnt[kCntRr], &last)) return;
+    const double rr = cs_sum_parts<kCsThreads>(rr_part, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        sc->beta = rr / sc->rr;
+        sc->rr = rr;
+        sc->iters += 1;
+    }
+}
+
+// p = r + beta p.
+__global__ void __launch_bounds__(kCsThreads)
+k_cs_step2(int64_t n, const double *__restrict__ r, double *__restrict__ p, const CsScal *sc)
+{
+    if (sc->done) return;
+    const double beta = sc->beta;
+    const int64_t e0 = (int64_t)blockIdx.x * kCsPer;
+#pragma unroll
+    for (int u = 0; u < kCsPer / kCsThreads; ++u) {
+        const int64_t e = e0 + u * kCsThreads + threadIdx.x;
+        if (e < n) p[e] = r[e] + beta * p[e];
     }
 }
 
@@ -686,39 +756,30 @@ int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st)
     return MPI_OK;
 }
 
-int unit_fill_launch(int N, const int *unit_off, int *unit_node, cudaStream_t st)
-{
-    k_unit_fill<<<grid_blocks(N), 256, 0, st>>>(N, unit_off, unit_node);
-    MPI_CHECK_LAUNCH();
-    return MPI_OK;
-}
 
 int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_opts &o, double *x,
                   int *n_iter_out, cudaStream_t st)
 {
-    const int nblk = vec_blocks(nv);
-    const int nepi = (int)std::max<int64_t>(1, (nv + kEpiPer - 1) / kEpiPer);
+    const int ncs = cs_blocks(nv);
+    const int nepi = op.pq_blocks(nv);
     Scratch scr(st);
     const size_t vb = sizeof(double) * nv;
-    const size_t o_r = scr.reserve(vb), o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_y = scr.reserve(vb),
-                 o_l1 = scr.reserve(vb), o_l2 = scr.reserve(vb);
-    const size_t o_pq = scr.reserve(sizeof(double) * nepi), o_rr = scr.reserve(sizeof(double) * 2 * nblk);
-    const size_t o_sc = scr.reserve(sizeof(double) * 8 + sizeof(int) * 8);
+    const size_t o_r = scr.reserve(vb), o_p = scr.reserve(vb), o_q = scr.reserve(vb),
+                 o_y = scr.reserve(op.fused() ? 0 : vb), o_l1 = scr.reserve(vb),
+                 o_l2 = scr.reserve(op.fused() ? 0 : vb);
+    const size_t o_pq = scr.reserve(sizeof(double) * nepi), o_rr = scr.reserve(sizeof(double) * ncs);
+    const size_t o_sc = scr.reserve(sizeof(CsScal));
     MPI_TRY(scr.allocate());
     double *rr = scr.at<double>(o_r), *p = scr.at<double>(o_p), *q = scr.at<double>(o_q),
            *y = scr.at<double>(o_y), *l1 = scr.at<double>(o_l1), *l2 = scr.at<double>(o_l2);
-    double *pq_part = scr.at<double>(o_pq), *rr_part0 = scr.at<double>(o_rr), *rr_part1 = rr_part0 + nblk;
-    double *scal = scr.at<double>(o_sc);
-    int *done = reinterpret_cast<int *>(scal + 8), *iters = done + 1;
+    double *pq_part = scr.at<double>(o_pq), *rr_part = scr.at<double>(o_rr);
+    CsScal *sc = scr.at<CsScal>(o_sc);
 
     MPI_TRY_CUDA(cudaMemsetAsync(x, 0, vb, st));
-    MPI_TRY_CUDA(cudaMemsetAsync(q, 0, vb, st));
-    MPI_TRY_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 + sizeof(int) * 8, st));
-    // r = b, p = b, partial sums of r.r (nu = 0 from the zeroed scalar block)
-    MPI_TRY(cg_init_launch(nv, b, x, q, scal, rr, p, rr_part0, done, st));
-    k_norm_thresh<<<1, 32, 0, st>>>(rr_part0, nblk, o.rel_tol, scal + kScalBnorm);
+    MPI_TRY_CUDA(cudaMemsetAsync(sc, 0, sizeof(CsScal), st));
+    // r = b, p = b, r.r, ||b|| and the threshold
+    k_cs_init<<<ncs, kCsThreads, 0, st>>>(nv, b, rr, p, rr_part, o.rel_tol, sc);
     MPI_CHECK_LAUNCH();
-    const double *thresh = o.rel_tol > 0.0 ? scal + kScalTol : nullptr;
 
     int *h_done = nullptr;
     MPI_TRY_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h_done), sizeof(int)));
@@ -726,16 +787,26 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
         int *p;
         ~PinnedFree() { cudaFreeHost(p); }
     } guard{h_done};
+    int *done = &sc->done, *iters = &sc->iters;
+    const bool thresh = o.rel_tol > 0.0;
 
-    // One CG step: q = (1/T) M^T M p + gamma Lap Lap p, <p, q>, and the update.
-    auto enqueue_step = [&](int it, cudaStream_t s) -> int {
-        MPI_TRY(op.normal(p, y, s));
-        MPI_TRY(op.lap(p, l1, s));
-        MPI_TRY(op.lap(l1, l2, s));
-        k_grid_epilogue<<<nepi, kEpiThreads, 0, s>>>(nv, y, l2, o.gamma, p, q, pq_part);
+    // One CG step: q = (1/T) M^T M p + gamma Lap Lap p, <p, q> and alpha (or
+    // the stop), then the update and beta, then the new direction.
+    auto enqueue_step = [&](int, cudaStream_t s) -> int {
+        if (op.fused()) {
+            MPI_TRY(op.step_q(p, o.gamma, q, pq_part, sc, y, l1, s));
+        } else {
+            MPI_TRY(op.normal(p, y, s));
+            MPI_TRY(op.lap(p, l1, s));
+            MPI_TRY(op.lap(l1, l2, s));
+            k_grid_epilogue<<<nepi, kEpiThreads, 0, s>>>(nv, y, l2, o.gamma, p, q, pq_part, sc);
+            MPI_CHECK_LAUNCH();
+        }
+        k_cs_step1<<<ncs, kCsThreads, 0, s>>>(nv, x, rr, p, q, rr_part, sc);
         MPI_CHECK_LAUNCH();
-        return cg_step_launch(nv, x, rr, p, q, pq_part, nepi, (it & 1) ? rr_part1 : rr_part0,
-                              (it & 1) ? rr_part0 : rr_part1, done, thresh, iters, s);
+        k_cs_step2<<<ncs, kCsThreads, 0, s>>>(nv, rr, p, sc);
+        MPI_CHECK_LAUNCH();
+        return MPI_OK;
     };
     auto poll_done = [&](bool &stop) -> int {
         MPI_TRY_CUDA(cudaMemcpyAsync(h_done, done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -747,8 +818,7 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
     // The steps are short dependent launches (latency-bound), so a run of
     // `poll` steps -- the span between two host polls of the stop flag -- is
     // captured once as a CUDA graph and replayed: the same kernels with the
-    // same arguments in the same order (poll is even, so the alternation of the
-    // residual partials repeats), hence the same result.  The capture uses a
+    // same arguments in the same order, hence the same result.  The capture uses a
     // private stream (the caller's may be the legacy default stream, which
     // cannot be captured); the graph runs on the caller's stream.
     const int poll = 16;

@@ -5,7 +5,8 @@
 Builds the inputs of the workload (seeded synthetic), runs `--warmup`
 untimed applications and then `--reps` applications of the chosen operator
 (forward A, adjoint A^T, dbeta, conv, the Core Stage interpolation,
-its transpose, two Core Stage CG steps, or one whole PnP reconstruction) in the chosen precision, timing each
+its transpose, a Core Stage solve of --grid-iters CG steps, or one whole
+PnP reconstruction) in the chosen precision, timing each
 with CUDA events on the current stream, and prints one line per operator.
 It is the small, self-contained command to put under a profiler.
 """
@@ -32,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--grid-iters", type=int, default=2,
+                    help="CG steps of the grid op (a fixed count: rel_tol 0)")
     ap.add_argument("--kernel", action="store_true",
                     help="report the operator kernel alone (library event timing, mean of reps)")
     args = ap.parse_args(argv)
@@ -56,7 +59,7 @@ def main(argv=None):
             "conv": lambda: api.mpi_conv3(m, g, c, out=out),
             "interp": lambda: api.mpi_interp3(g, r, v, field, s=s3),
             "interp_T": lambda: api.mpi_interp3_adjoint(g, r, v, s, Ahat=field),
-            "grid": lambda: api.mpi_grid3(g, r, v, s, gamma=1e-7, max_iter=2, rel_tol=0.0),
+            "grid": lambda: api.mpi_grid3(g, r, v, s, gamma=1e-7, max_iter=args.grid_iters, rel_tol=0.0),
         }
     else:
         s = api.mpi_forward(m, g, r, v, c)
@@ -69,7 +72,7 @@ def main(argv=None):
             "conv": lambda: api.mpi_conv(m, g, c, out=out),
             "interp": lambda: api.mpi_interp(g, r, v, field, s=s2),
             "interp_T": lambda: api.mpi_interp_adjoint(g, r, v, s, Ahat=field),
-            "grid": lambda: api.mpi_grid(g, r, v, s, gamma=1e-7, max_iter=2, rel_tol=0.0),
+            "grid": lambda: api.mpi_grid(g, r, v, s, gamma=1e-7, max_iter=args.grid_iters, rel_tol=0.0),
             # one whole reconstruction of the workload (its PnP iterations and CG
             # steps); nu0 = 1e-3 of the mean diagonal of A^T A from 4 probes
             "pnp": lambda: api.mpi_pnp_solve(m, g, r, v, s, cfg["n_it"], cfg["n_cg"], nu0,
