@@ -111,16 +111,6 @@ k_interp3(int64_t T, const R *__restrict__ r, const InterpRec3<R> *__restrict__ 
     }
 }
 
-// A4[node K + k] = (A_{3k}, A_{3k+1}, A_{3k+2}, 0) rounded to FP32 from the
-// component-major FP64 field x (K = 3: nine components; K = 1: three).
-__global__ void k_round_field3_il(int64_t N, int K, const double *__restrict__ x, float4 *__restrict__ A4)
-{
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-        for (int k = 0; k < K; ++k)
-            A4[e * K + k] = make_float4(float(x[(3 * k) * N + e]), float(x[(3 * k + 1) * N + e]),
-                                        float(x[(3 * k + 2) * N + e]), 0.0f);
-}
-
 template <typename R>
 __global__ void k_cell_count3(int64_t T, const R *__restrict__ r, Axes3 ax, int ncx, int ncy,
                               int *__restrict__ cell_of, int *__restrict__ count, InterpRec3<R> *__restrict__ rec)
@@ -247,26 +237,24 @@ k_interp3_T_cells(const InterpRec3<R> *__restrict__ rec, const R *__restrict__ v
         if (prev != unsigned(nu - 1)) continue;  // another unit of the cell finishes it
         if (lane == 0) cell_cnt[c] = 0u;
         __threadfence();
-        if (g == 0) {
-#pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                SumAcc<R> a = {};
-                for (int u = u0; u < u0 + nu; ++u) a.add(__ldcg(unit_part + ((int64_t)u * 8 + corner) * NC + m));
-                cell_part[((int64_t)u0 * 8 + corner) * NC + m] = cell_pair(a);
-            }
+        // the four groups share the components: group g adds m = g, g + 4, ...
+        for (int m = g; m < NC; m += kT3Groups) {
+            SumAcc<R> a = {};
+#pragma unroll 4
+            for (int u = u0; u < u0 + nu; ++u) a.add(__ldcg(unit_part + ((int64_t)u * 8 + corner) * NC + m));
+            cell_part[((int64_t)u0 * 8 + corner) * NC + m] = cell_pair(a);
         }
     }
 }
 
-// The combine of one unknown (component m of the node at i, j, l): the sum,
-// over the node's adjacent non-empty cells in ascending cell order, of the
-// cell sums of the corner the node is in that cell.
+// The combine of one node (at i, j, l), all NC components: the sums, over
+// the node's adjacent non-empty cells in ascending cell order, of the cell
+// sums of the corner the node is in that cell.
 template <typename R, int NC>
-__device__ __forceinline__ double node_combine3(int i, int j, int l, int m, int ncx, int ncy, int ncz,
-                                                const int *__restrict__ cunit_off,
-                                                const V2<R> *__restrict__ cell_part)
+__device__ __forceinline__ void node_combine3(int i, int j, int l, int ncx, int ncy, int ncz,
+                                              const int *__restrict__ cunit_off,
+                                              const V2<R> *__restrict__ cell_part, SumAcc<R> (&sum)[NC])
 {
-    SumAcc<R> sum = {};
 #pragma unroll
     for (int dz = 1; dz >= 0; --dz)
 #pragma unroll
@@ -278,9 +266,10 @@ __device__ __forceinline__ double node_combine3(int i, int j, int l, int m, int 
                 const int cc = (cl * ncy + cj) * ncx + ci;
                 const int u0 = cunit_off[cc];
                 if (cunit_off[cc + 1] == u0) continue;
-                cell_add(sum, cell_part[((int64_t)u0 * 8 + dx + 2 * dy + 4 * dz) * NC + m]);
+                const V2<R> *cp = cell_part + ((int64_t)u0 * 8 + dx + 2 * dy + 4 * dz) * NC;
+#pragma unroll
+                for (int m = 0; m < NC; ++m) cell_add(sum[m], cp[m]);
             }
-    return sum.value();
 }
 
 // Ahat_m(node) = scale * node_combine3 for all NC components.
@@ -290,10 +279,12 @@ __global__ void k_interp3_T_cell_combine(int nx, int ny, int nz, int ncx, int nc
                                          OUT *__restrict__ A, double scale)
 {
     const int N = nx * ny * nz;  // < 2^27
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NC * N; e += gridDim.x * blockDim.x) {
-        const int m = e / N, node = e - m * N;
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N; node += gridDim.x * blockDim.x) {
         const int i = node % nx, j = (node / nx) % ny, l = node / (nx * ny);
-        A[e] = OUT(node_combine3<R, NC>(i, j, l, m, ncx, ncy, ncz, cunit_off, cell_part) * scale);
+        SumAcc<R> sum[NC] = {};
+        node_combine3<R, NC>(i, j, l, ncx, ncy, ncz, cunit_off, cell_part, sum);
+#pragma unroll
+        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(sum[m].value() * scale);
     }
 }
 
@@ -328,11 +319,14 @@ __global__ void k_lap3(int nx, int ny, int nz, int nc, bool scaled, double3 c, c
     }
 }
 
-// One Core Stage step's operator after the transpose's cell sums, for every
-// unknown e = m N + node: y = scale * node_combine3, q = y + gamma (Lap l1)(e)
-// with l1 = Lap p, written to q, and the partial sums of <p, q> over blocks
-// of kQPer3 consecutive unknowns, finished into alpha by the last block.
-constexpr int kQThreads3 = 256, kQPer3 = 512;
+// One Core Stage step's operator after the transpose's cell sums, one
+// thread per node and all its components m: y = scale * node_combine3,
+// q = y + gamma (Lap l1) with l1 = Lap p, written to q, and the partial sums
+// of <p, q> over blocks of kQThreads3 consecutive nodes, finished into alpha
+// by the last block.  (Small blocks: a 48 x 48 x 24 grid still spreads over
+// about three blocks per SM, so the FP64 pipes that bound this kernel stay
+// evenly loaded.)
+constexpr int kQThreads3 = 128;
 template <typename R, int NC>
 __global__ void __launch_bounds__(kQThreads3)
 k_grid3_q(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restrict__ cunit_off,
@@ -342,17 +336,21 @@ k_grid3_q(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restri
 {
     __shared__ double sh[kQThreads3 / 32];
     __shared__ bool last;
-    // NC N < 2^31 (grids of fewer than 2^27 nodes): 32-bit index arithmetic
-    const int N = nx * ny * nz, nv = NC * N;
-    const int e0 = blockIdx.x * kQPer3, e1 = min(nv, e0 + kQPer3);
+    const int N = nx * ny * nz;  // < 2^27
+    const int node = blockIdx.x * kQThreads3 + threadIdx.x;
     double acc = 0.0;
-    for (int e = e0 + threadIdx.x; e < e1; e += kQThreads3) {
-        const int m = e / N, node = e - m * N;
+    if (node < N) {
         const int i = node % nx, j = (node / nx) % ny, l = node / (nx * ny);
-        const double y = node_combine3<R, NC>(i, j, l, m, ncx, ncy, ncz, cunit_off, cell_part) * scale;
-        const double qe = y + gamma * lap3_at(l1 + (int64_t)m * N, node, i, j, l, nx, ny, nz, scaled, c);
-        q[e] = qe;
-        acc += p[e] * qe;
+        SumAcc<R> sum[NC] = {};
+        node_combine3<R, NC>(i, j, l, ncx, ncy, ncz, cunit_off, cell_part, sum);
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const int64_t e = (int64_t)m * N + node;
+            const double y = sum[m].value() * scale;
+            const double qe = y + gamma * lap3_at(l1 + (int64_t)m * N, node, i, j, l, nx, ny, nz, scaled, c);
+            q[e] = qe;
+            acc += p[e] * qe;
+        }
     }
     acc = block_sum<double, kQThreads3>(acc, sh);
     if (threadIdx.x == 0) pq_part[blockIdx.x] = acc;
@@ -538,21 +536,20 @@ int launch_interp3_T(const G3 &g, int64_t T, const R *s_sorted, const Bins3 &b, 
     const int64_t N = g.n();
     const V2<R> *cpart = static_cast<const V2<R> *>(b.cell_part);
     if (ch < 0)
-        k_interp3_T_cell_combine<R, OUT, 9><<<grid_blocks(9 * N), 256, 0, st>>>(
+        k_interp3_T_cell_combine<R, OUT, 9><<<grid_blocks(N), 256, 0, st>>>(
             g.nx, g.ny, g.nz, b.ncx, b.ncy, b.ncz, b.cunit_off, cpart, A, scale);
     else
-        k_interp3_T_cell_combine<R, OUT, 3><<<grid_blocks(3 * N), 256, 0, st>>>(
+        k_interp3_T_cell_combine<R, OUT, 3><<<grid_blocks(N), 256, 0, st>>>(
             g.nx, g.ny, g.nz, b.ncx, b.ncy, b.ncz, b.cunit_off, cpart, A, scale);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
 
 // The 3-D Core Stage operator: (1/T) M^T M through the binned records and
-// the 7-point Laplacian of each component.  A step runs fused (step_q): the
-// field rounded to FP32 in the interleaved layout (FP32 path), M p, the
-// transpose's unit and cell sums, l1 = Lap p, and one pass forming
-// q = (1/T) M^T M p + gamma Lap l1 with the partial sums of <p, q> and alpha
-// -- five launches where the composed form takes seven.
+// the 7-point Laplacian of each component.  A step: l1 = Lap p on the side
+// stream while the main chain runs M p (through the FP32 copy of p on the
+// FP32 path) and the transpose's unit and cell sums; then one pass forms q
+// and the <p, q> partials (k_grid3_q).
 template <typename R>
 struct GridOp3 final : CoreStageOp {
     const G3 &g;
@@ -560,7 +557,7 @@ struct GridOp3 final : CoreStageOp {
     int ch, nc;
     const Bins3 &bins;
     R *s_tmp;
-    float4 *p_il;  // FP32 path: the field rounded, interleaved (K N float4); FP64: unused
+    float4 *p_il;  // FP32 path: the FP32 copy of p, K float4 rows per node; FP64: unused
     double invT;
     bool scaled;
     GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_, float4 *p_il_, bool scaled_)
@@ -570,42 +567,31 @@ struct GridOp3 final : CoreStageOp {
     {
         return make_double3(1.0 / (g.dx * g.dx), 1.0 / (g.dy * g.dy), 1.0 / (g.dz * g.dz));
     }
-    // s_tmp = M p (list order).
-    int forward(const double *p, cudaStream_t st)
+    P32 p32() const override
     {
+        if constexpr (sizeof(R) == 4)
+            return P32{reinterpret_cast<float *>(p_il), ch < 0 ? kP32Rows3x4 : kP32Rows1x4, g.n()};
+        return P32{};
+    }
+    int pq_blocks(int64_t) const override { return (int)((g.n() + kQThreads3 - 1) / kQThreads3); }
+    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1,
+               const StepFork &fk, cudaStream_t st) override
+    {
+        MPI_TRY_CUDA(cudaEventRecord(fk.fork, st));
+        MPI_TRY_CUDA(cudaStreamWaitEvent(fk.side, fk.fork, 0));
+        k_lap3<<<grid_blocks(nc * g.n()), 256, 0, fk.side>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), p, l1);
+        MPI_CHECK_LAUNCH();
+        MPI_TRY_CUDA(cudaEventRecord(fk.join, fk.side));
         const InterpRec3<R> *rec = static_cast<const InterpRec3<R> *>(bins.rec);
         const R *vs = static_cast<const R *>(bins.vs);
-        if constexpr (sizeof(R) == 4) {
-            const int K = ch < 0 ? 3 : 1;
-            k_round_field3_il<<<grid_blocks(g.n()), 256, 0, st>>>(g.n(), K, p, p_il);
-            MPI_CHECK_LAUNCH();
-            return launch_interp3<R, float>(g, T, nullptr, vs, reinterpret_cast<const float *>(p_il), s_tmp, st,
-                                            ch, rec, true);
-        } else {
-            return launch_interp3<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec);
-        }
-    }
-    int normal(const double *p, double *y, cudaStream_t st) override
-    {
-        MPI_TRY(forward(p, st));
-        return launch_interp3_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch);
-    }
-    int lap(const double *x, double *out, cudaStream_t st) override
-    {
-        k_lap3<<<grid_blocks(nc * g.n()), 256, 0, st>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), x, out);
-        MPI_CHECK_LAUNCH();
-        return MPI_OK;
-    }
-    bool fused() const override { return true; }
-    int pq_blocks(int64_t nv) const override { return (int)std::max<int64_t>(1, (nv + kQPer3 - 1) / kQPer3); }
-    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *, double *l1,
-               cudaStream_t st) override
-    {
-        MPI_TRY(forward(p, st));
+        if constexpr (sizeof(R) == 4)
+            MPI_TRY((launch_interp3<R, float>(g, T, nullptr, vs, reinterpret_cast<const float *>(p_il), s_tmp, st,
+                                              ch, rec, true)));
+        else
+            MPI_TRY((launch_interp3<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
         MPI_TRY(launch_interp3_T_units<R>(T, s_tmp, bins, st, ch));
-        MPI_TRY(lap(p, l1, st));
-        const int64_t nv = int64_t(nc) * g.n();
-        const unsigned blocks = (unsigned)pq_blocks(nv);
+        MPI_TRY_CUDA(cudaStreamWaitEvent(st, fk.join, 0));
+        const unsigned blocks = (unsigned)pq_blocks(0);
         const V2<R> *cpart = static_cast<const V2<R> *>(bins.cell_part);
         if (ch < 0)
             k_grid3_q<R, 9><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,

@@ -66,10 +66,6 @@ int cell_fill_launch(int64_t T, const int *cell_of, int *cursor, int *list, cuda
 // Sorts each cell's run of list ascending.
 int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st);
 
-// The step epilogue q = y + gamma Lap Lap p and the partial sums of <p, q>
-// run in blocks of kEpiThreads threads over kEpiPer consecutive elements.
-constexpr int kEpiThreads = 256, kEpiPer = 2048;
-
 // Device scalars of one Core Stage CG solve.  A reduction's partial sums are
 // added once per step, in a fixed order, by the block of the producing
 // kernel that arrives last at the reduction's counter (the next kernel reads
@@ -132,25 +128,40 @@ __device__ __forceinline__ void cs_finish_pq(const double *pq_part, int n, CsSca
 }
 #endif
 
+// Layouts of the FP32 copy of the CG direction an operator reads (FP32
+// path), for N nodes: kP32Node4 / kP32Node2: a node's 4 / 2 components as one
+// float4 / float2 (2-D); kP32Rows3x4 / kP32Rows1x4: three rows / one row of
+// three components per node, each a float4 (A_{3k}, A_{3k+1}, A_{3k+2}, 0)
+// (3-D).
+enum P32Layout { kP32None = 0, kP32Node4, kP32Node2, kP32Rows3x4, kP32Rows1x4 };
+struct P32 {
+    float *buf = nullptr;
+    int layout = kP32None;
+    int64_t N = 0;
+};
+
+// A side stream for work of a step that is independent of its main chain:
+// forked from and joined back into the step's stream with the two events
+// (inside a graph capture this makes parallel branches).
+struct StepFork {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
+
 // The operator of one Core Stage solve on nv FP64 unknowns (all components
-// of all nodes): y = (1/T) M^T M p and the Laplacian of every component.
-// The methods only enqueue on `st`.
+// of all nodes).  Its methods only enqueue.
 struct CoreStageOp {
     virtual ~CoreStageOp() = default;
-    virtual int normal(const double *p, double *y, cudaStream_t st) = 0;
-    virtual int lap(const double *x, double *out, cudaStream_t st) = 0;
-    // An operator with a fused step (fused() true) forms q = (1/T) M^T M p +
-    // gamma Lap Lap p and the partial sums of <p, q> itself, in pq_blocks(nv)
-    // fixed blocks, with two FP64 work vectors of nv values; the solve then
-    // does not call normal() and lap().
-    virtual bool fused() const { return false; }
-    virtual int pq_blocks(int64_t nv) const { return (int)std::max<int64_t>(1, (nv + kEpiPer - 1) / kEpiPer); }
-    // pq_part: pq_blocks(nv) partials; the producing kernel finishes them
-    // with cs_finish_pq on sc.
-    virtual int step_q(const double *, double, double *, double *, CsScal *, double *, double *, cudaStream_t)
-    {
-        return MPI_ERR_UNSUPPORTED;
-    }
+    // The FP32 copy of p the operator reads (buf null: it reads p in FP64).
+    // The solve keeps the copy equal to p rounded to FP32: it writes it after
+    // the first direction and with every direction update.
+    virtual P32 p32() const { return P32{}; }
+    // q = (1/T) M^T M p + gamma Lap Lap p and the partial sums of <p, q> in
+    // pq_blocks(nv) fixed blocks, finished by the producing kernel with
+    // cs_finish_pq on sc.  l1: an FP64 work vector of nv values.
+    virtual int pq_blocks(int64_t nv) const = 0;
+    virtual int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1,
+                       const StepFork &fk, cudaStream_t st) = 0;
 };
 
 // CG from x = 0 on ((1/T) M^T M + gamma Lap Lap) x = b (Eq. first:step; Lap is
@@ -195,26 +206,6 @@ int gather_rows(int64_t T, int n_rows, const int *list, const R *in, R *out, cud
     k_gather_rows<R><<<grid_blocks(T), 256, 0, st>>>(T, n_rows, list, in, out);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
-}
-
-// out[e] = R(in[e]) for e < n: the FP32 Core Stage rounds the FP64 field once
-// per CG step, so its interpolation gathers FP32 values (GB300 converts FP64
-// at a small fraction of the FP32 rate; a gather converting 16 or 72 values
-// per sample was bound by that conversion).
-template <typename R>
-__global__ void k_round_field(int64_t n, const double *__restrict__ in, R *__restrict__ out)
-{
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = R(in[e]);
-}
-
-// out[node * nc + m] = R(in[m * N + node]): the rounded field, node-interleaved
-// (the 2-D FP32 Core Stage gathers a corner's components in one vector load).
-template <typename R>
-__global__ void k_round_field_il(int64_t N, int nc, const double *__restrict__ in, R *__restrict__ out)
-{
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-        for (int m = 0; m < nc; ++m) out[e * nc + m] = R(in[m * N + e]);
 }
 
 }  // namespace mpi

@@ -333,7 +333,8 @@ struct Bins {
     // of each unit; 4 corners x 4 partial sums per unit.
     int *cunit_cnt, *cunit_off, *cunit_cursor, *unit_cell;
     void *unit_part;
-    int n_units_max;
+    int n_units_max;   // bound on the units (allocation)
+    int n_units = -1;  // the exact count when read back to the host, else -1
     int ncx, ncy;
 };
 
@@ -447,18 +448,18 @@ static int launch_interp(const GridH &g, int64_t T, const R *r, const R *v, cons
     return MPI_OK;
 }
 
+// The transpose's unit sums (k_interp_T_cells) into b.unit_part.
 // s_sorted: the samples' values in list order ([rows][T]).
-template <typename R, typename OUT>
-static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const Bins &b, OUT *A, double scale,
-                           cudaStream_t st, int ch = -1)
+template <typename R>
+static int launch_interp_T_units(int64_t T, const R *s_sorted, const Bins &b, cudaStream_t st, int ch)
 {
-    const int N = g.nx * g.ny;
     const int nc = b.ncx * b.ncy;
     constexpr int per_block = kUnitThreads / kUnitLanes;
-    const int n_iter = (b.n_units_max + per_block - 1) / per_block * per_block;
-    // Blocks for the bound on the units (every cell counted non-empty); the
-    // real count is on the device and the surplus blocks exit at once (a
-    // one-wave striding grid was slower at 512 x 512 / 2^20 samples).
+    // Blocks for the exact unit count where the host has it, else for the
+    // bound (every cell counted non-empty): the real count is on the device
+    // and the surplus blocks exit at once.
+    const int units = b.n_units >= 0 ? b.n_units : b.n_units_max;
+    const int n_iter = (units + per_block - 1) / per_block * per_block;
     const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, 65535));
     const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(b.rec);
     const R *vs = static_cast<const R *>(b.vs);
@@ -471,6 +472,17 @@ static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const B
         k_interp_T_cells<R, 0><<<blocks, kUnitThreads, 0, st>>>(rec, vs, s_sorted, T, b.offset, b.cunit_off,
                                                                 b.unit_cell, n_units, n_iter, part);
     MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// A = scale M^T s (all four components, or channel ch's two).
+template <typename R, typename OUT>
+static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const Bins &b, OUT *A, double scale,
+                           cudaStream_t st, int ch = -1)
+{
+    MPI_TRY(launch_interp_T_units<R>(T, s_sorted, b, st, ch));
+    const int N = g.nx * g.ny;
+    const R *part = static_cast<const R *>(b.unit_part);
     if (ch < 0)
         k_interp_T_cell_combine<R, OUT, 4><<<grid_blocks(N), 256, 0, st>>>(g.nx, g.ny, b.ncx, b.ncy, b.cunit_off,
                                                                           part, A, scale);
@@ -483,48 +495,75 @@ static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const B
 
 // --- Laplacian and the Core Stage operator ---------------------------------
 
-// out_m = Lap x_m for the nc components (replicated boundary), FP64.
-// scaled: per-axis second differences with 1/dx^2 (cx) and 1/dy^2 (cy).
+// (Lap f)(node k at i, j): 5-point, replicated boundary (a missing
+// neighbour is the node itself), FP64.  scaled: per-axis second differences
+// with 1/dx^2 (cx) and 1/dy^2 (cy); else the plain stencil.
+__device__ __forceinline__ double lap2_at(const double *__restrict__ f, int k, int i, int j, int nx, int ny,
+                                          bool scaled, double cx, double cy)
+{
+    const int im = i > 0 ? i - 1 : 0, ip = i < nx - 1 ? i + 1 : nx - 1;
+    const int jm = j > 0 ? j - 1 : 0, jp = j < ny - 1 ? j + 1 : ny - 1;
+    if (scaled) {
+        const double c0 = f[k];
+        return cx * (f[j * nx + im] - 2.0 * c0 + f[j * nx + ip]) + cy * (f[jm * nx + i] - 2.0 * c0 + f[jp * nx + i]);
+    }
+    return f[j * nx + im] + f[j * nx + ip] + f[jm * nx + i] + f[jp * nx + i] - 4.0 * f[k];
+}
+
+// out_m = Lap x_m for the nc components.
 __global__ void k_lap(int nx, int ny, int nc, bool scaled, double cx, double cy, const double *__restrict__ x,
                       double *__restrict__ out)
 {
-    const int64_t N = (int64_t)nx * ny;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc * N;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = e / N, k = e % N;
-        const int i = (int)(k % nx), j = (int)(k / nx);
-        const double *f = x + m * N;
-        const int im = i > 0 ? i - 1 : 0, ip = i < nx - 1 ? i + 1 : nx - 1;
-        const int jm = j > 0 ? j - 1 : 0, jp = j < ny - 1 ? j + 1 : ny - 1;
-        if (scaled) {
-            const double c0 = f[k];
-            out[e] = cx * (f[(int64_t)j * nx + im] - 2.0 * c0 + f[(int64_t)j * nx + ip]) +
-                     cy * (f[(int64_t)jm * nx + i] - 2.0 * c0 + f[(int64_t)jp * nx + i]);
-        } else {
-            out[e] = f[(int64_t)j * nx + im] + f[(int64_t)j * nx + ip] + f[(int64_t)jm * nx + i] +
-                     f[(int64_t)jp * nx + i] - 4.0 * f[k];
-        }
+    const int N = nx * ny;  // nc N < 2^31 (grids of at most 2^28 nodes)
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * N; e += gridDim.x * blockDim.x) {
+        const int m = e / N, k = e - m * N;
+        out[e] = lap2_at(x + (int64_t)m * N, k, k % nx, k / nx, nx, ny, scaled, cx, cy);
     }
 }
 
-// q = y + gamma lap2, partial sums of <p, q> (blocks of kEpiPer elements),
-// finished into the step's alpha by the last block.
-__global__ void __launch_bounds__(kEpiThreads)
-k_grid_epilogue(int64_t n, const double *__restrict__ y, const double *__restrict__ lap2, double gamma,
-                const double *__restrict__ p, double *__restrict__ q, double *__restrict__ dot_part, CsScal *sc)
+// One 2-D Core Stage step after the transpose's unit sums, one thread per
+// node and all its components m: y = scale * (the node's combine, as
+// k_interp_T_cell_combine forms it), q = y + gamma (Lap l1) with l1 = Lap p,
+// written to q, and the partial sums of <p, q> over blocks of kQThreads
+// consecutive nodes, finished into alpha by the last block.
+constexpr int kQThreads = 256;
+template <typename R, int NC>
+__global__ void __launch_bounds__(kQThreads)
+k_grid_q(int nx, int ny, int ncx, int ncy, const int *__restrict__ cunit_off, const R *__restrict__ unit_part,
+         double scale, bool scaled, double cx, double cy, double gamma, const double *__restrict__ l1,
+         const double *__restrict__ p, double *__restrict__ q, double *__restrict__ pq_part, CsScal *sc)
 {
-    __shared__ double sh[kEpiThreads / 32];
+    __shared__ double sh[kQThreads / 32];
     __shared__ bool last;
-    const int64_t e0 = (int64_t)blockIdx.x * kEpiPer, e1 = min(n, e0 + kEpiPer);
+    const int N = nx * ny;  // <= 2^28
+    const int node = blockIdx.x * kQThreads + threadIdx.x;
     double acc = 0.0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += kEpiThreads) {
-        const double qe = y[e] + gamma * lap2[e];
-        q[e] = qe;
-        acc += p[e] * qe;
+    if (node < N) {
+        const int i = node % nx, j = node / nx;
+        SumAcc<R> sum[NC] = {};
+        for (int cj = j - 1; cj <= j; ++cj) {
+            if (cj < 0 || cj >= ncy) continue;
+            for (int ci = i - 1; ci <= i; ++ci) {
+                if (ci < 0 || ci >= ncx) continue;
+                const int c = cj * ncx + ci;
+                const int corner = (i - ci) + 2 * (j - cj);
+                for (int w = cunit_off[c]; w < cunit_off[c + 1]; ++w)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) sum[m].add(unit_part[((int64_t)w * 4 + corner) * NC + m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const int64_t e = (int64_t)m * N + node;
+            const double y = sum[m].value() * scale;
+            const double qe = y + gamma * lap2_at(l1 + (int64_t)m * N, node, i, j, nx, ny, scaled, cx, cy);
+            q[e] = qe;
+            acc += p[e] * qe;
+        }
     }
-    acc = block_sum<double, kEpiThreads>(acc, sh);
-    if (threadIdx.x == 0) dot_part[blockIdx.x] = acc;
-    cs_finish_pq<kEpiThreads>(dot_part, gridDim.x, sc, sh, &last);
+    acc = block_sum<double, kQThreads>(acc, sh);
+    if (threadIdx.x == 0) pq_part[blockIdx.x] = acc;
+    cs_finish_pq<kQThreads>(pq_part, gridDim.x, sc, sh, &last);
 }
 
 // --- Core Stage CG vector kernels -----------------------------------------
@@ -574,16 +613,29 @@ k_cs_step1(int64_t n, double *__restrict__ x, double *__restrict__ r, const doub
 {
     __shared__ double sh[kCsThreads / 32];
     __shared__ bool last;
+    constexpr int U = kCsPer / kCsThreads;
+    const int64_t e0 = (int64_t)blockIdx.x * kCsPer + threadIdx.x;
+    // the vectors are loaded before the stop flag is read: the flag comes
+    // from the previous kernel and would otherwise add a round trip
+    double xv[U], pv[U], rv[U], qv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t e = e0 + u * kCsThreads;
+        const bool in = e < n;
+        xv[u] = in ? x[e] : 0.0;
+        pv[u] = in ? p[e] : 0.0;
+        rv[u] = in ? r[e] : 0.0;
+        qv[u] = in ? q[e] : 0.0;
+    }
     if (sc->done) return;
     const double alpha = sc->alpha;
-    const int64_t e0 = (int64_t)blockIdx.x * kCsPer;
     double acc = 0.0;
 #pragma unroll
-    for (int u = 0; u < kCsPer / kCsThreads; ++u) {
-        const int64_t e = e0 + u * kCsThreads + threadIdx.x;
+    for (int u = 0; u < U; ++u) {
+        const int64_t e = e0 + u * kCsThreads;
         if (e < n) {
-            x[e] = x[e] + alpha * p[e];
-            const double re = r[e] - alpha * q[e];
+            x[e] = xv[u] + alpha * pv[u];
+            const double re = rv[u] - alpha * qv[u];
             r[e] = re;
             acc += re * re;
         }
@@ -613,6 +665,105 @@ k_cs_step2(int64_t n, const double *__restrict__ r, double *__restrict__ p, cons
     }
 }
 
+// The FP32 copy of p in the operator's layout (P32Layout): the FP32 Core
+// Stage gathers FP32 values in its interpolation (GB300 converts FP64 at a
+// small fraction of the FP32 rate; a gather converting 16 or 72 values per
+// sample was bound by that conversion), and the direction update writes the
+// copy as it forms p.  Components per node:
+template <int L>
+constexpr int p32_nc()
+{
+    return L == kP32Node4 ? 4 : L == kP32Node2 ? 2 : L == kP32Rows3x4 ? 9 : 3;
+}
+template <int L>
+__device__ __forceinline__ void p32_store(float *buf, int64_t node, const float *v)
+{
+    if constexpr (L == kP32Node4) {
+        reinterpret_cast<float4 *>(buf)[node] = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (L == kP32Node2) {
+        reinterpret_cast<float2 *>(buf)[node] = make_float2(v[0], v[1]);
+    } else {
+        constexpr int K = p32_nc<L>() / 3;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            reinterpret_cast<float4 *>(buf)[node * K + k] = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], 0.0f);
+    }
+}
+
+// buf = p rounded to FP32 (one thread per node, all its components).
+template <int L>
+__global__ void __launch_bounds__(kCsThreads) k_cs_round(int64_t N, const double *__restrict__ p, float *buf)
+{
+    constexpr int NC = p32_nc<L>();
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < N;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        float v[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) v[m] = float(p[m * N + node]);
+        p32_store<L>(buf, node, v);
+    }
+}
+
+// p = r + beta p and its FP32 copy (one thread per node, all its components).
+template <int L>
+__global__ void __launch_bounds__(kCsThreads)
+k_cs_step2_p32(int64_t N, const double *__restrict__ r, double *__restrict__ p, const CsScal *sc, float *buf)
+{
+    constexpr int NC = p32_nc<L>();
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < N;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        double rv[NC], pv[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            rv[m] = r[m * N + node];
+            pv[m] = p[m * N + node];
+        }
+        if (sc->done) return;  // (read after the vector loads are issued)
+        const double beta = sc->beta;
+        float v[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const double pe = rv[m] + beta * pv[m];
+            p[m * N + node] = pe;
+            v[m] = float(pe);
+        }
+        p32_store<L>(buf, node, v);
+    }
+}
+
+static int cs_round_launch(const P32 &d, const double *p, cudaStream_t st)
+{
+    const int blocks = grid_blocks(d.N);
+    switch (d.layout) {
+        case kP32Node4: k_cs_round<kP32Node4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
+        case kP32Node2: k_cs_round<kP32Node2><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
+        case kP32Rows3x4: k_cs_round<kP32Rows3x4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
+        default: k_cs_round<kP32Rows1x4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
+    }
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+static int cs_step2_launch(const P32 &d, int64_t nv, const double *r, double *p, const CsScal *sc,
+                           cudaStream_t st)
+{
+    if (!d.buf) {
+        k_cs_step2<<<cs_blocks(nv), kCsThreads, 0, st>>>(nv, r, p, sc);
+    } else {
+        const int blocks = grid_blocks(d.N);
+        switch (d.layout) {
+            case kP32Node4: k_cs_step2_p32<kP32Node4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf); break;
+            case kP32Node2: k_cs_step2_p32<kP32Node2><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf); break;
+            case kP32Rows3x4:
+                k_cs_step2_p32<kP32Rows3x4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf);
+                break;
+            default: k_cs_step2_p32<kP32Rows1x4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf); break;
+        }
+    }
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
 // Ahat and its trace (both channels: A_00 + A_11; one channel k: A_kk,
 // which is component k of the stored pair (A_k0, A_k1)).
 template <typename R>
@@ -628,7 +779,10 @@ __global__ void k_grid_output(int64_t N, int ch, const double *__restrict__ x, R
 }
 
 // The 2-D Core Stage operator: (1/T) M^T M through the binned records and
-// the 5-point Laplacian of each component.
+// the 5-point Laplacian of each component.  A step: l1 = Lap p on the side
+// stream while the main chain runs M p (through the FP32 copy of p on the
+// FP32 path) and the transpose's unit sums; then one pass forms q and the
+// <p, q> partials (k_grid_q).
 template <typename R>
 struct GridOp2 final : CoreStageOp {
     const GridH &g;
@@ -636,30 +790,42 @@ struct GridOp2 final : CoreStageOp {
     int ch, nc;
     const Bins &bins;
     R *s_tmp;
-    R *p_r;  // FP32 path: the field rounded to R (nc N values); FP64: unused
+    R *p_r;  // FP32 path: the FP32 copy of p, node-interleaved (nc N values); FP64: unused
     double invT;
     bool scaled;
     GridOp2(const GridH &g_, int64_t T_, int ch_, const Bins &b_, R *s_tmp_, R *p_r_, bool scaled_)
         : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 4 : 2), bins(b_), s_tmp(s_tmp_), p_r(p_r_),
           invT(T_ > 0 ? 1.0 / double(T_) : 0.0), scaled(scaled_) {}
-    int normal(const double *p, double *y, cudaStream_t st) override
+    P32 p32() const override
     {
+        if constexpr (sizeof(R) == 4)
+            return P32{reinterpret_cast<float *>(p_r), nc == 4 ? kP32Node4 : kP32Node2, int64_t(g.nx) * g.ny};
+        return P32{};
+    }
+    int pq_blocks(int64_t) const override { return (int)((int64_t(g.nx) * g.ny + kQThreads - 1) / kQThreads); }
+    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1,
+               const StepFork &fk, cudaStream_t st) override
+    {
+        const double cx = 1.0 / (g.dx * g.dx), cy = 1.0 / (g.dy * g.dy);
+        MPI_TRY_CUDA(cudaEventRecord(fk.fork, st));
+        MPI_TRY_CUDA(cudaStreamWaitEvent(fk.side, fk.fork, 0));
+        k_lap<<<grid_blocks(int64_t(nc) * g.nx * g.ny), 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, p, l1);
+        MPI_CHECK_LAUNCH();
+        MPI_TRY_CUDA(cudaEventRecord(fk.join, fk.side));
         const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(bins.rec);
         const R *vs = static_cast<const R *>(bins.vs);
-        if constexpr (sizeof(R) == 4) {
-            const int64_t N = int64_t(g.nx) * g.ny;
-            k_round_field_il<R><<<grid_blocks(N), 256, 0, st>>>(N, nc, p, p_r);
-            MPI_CHECK_LAUNCH();
-            MPI_TRY((launch_interp<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec, true)));
-        } else {
-            MPI_TRY((launch_interp<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
-        }
-        return launch_interp_T<R, double>(g, T, s_tmp, bins, y, invT, st, ch);
-    }
-    int lap(const double *x, double *out, cudaStream_t st) override
-    {
-        k_lap<<<grid_blocks(int64_t(nc) * g.nx * g.ny), 256, 0, st>>>(g.nx, g.ny, nc, scaled, 1.0 / (g.dx * g.dx),
-                                                                       1.0 / (g.dy * g.dy), x, out);
+        if constexpr (sizeof(R) == 4) MPI_TRY((launch_interp<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec, true)));
+        else MPI_TRY((launch_interp<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
+        MPI_TRY(launch_interp_T_units<R>(T, s_tmp, bins, st, ch));
+        MPI_TRY_CUDA(cudaStreamWaitEvent(st, fk.join, 0));
+        const unsigned blocks = (unsigned)pq_blocks(0);
+        const R *part = static_cast<const R *>(bins.unit_part);
+        if (ch < 0)
+            k_grid_q<R, 4><<<blocks, kQThreads, 0, st>>>(g.nx, g.ny, bins.ncx, bins.ncy, bins.cunit_off, part, invT,
+                                                        scaled, cx, cy, gamma, l1, p, q, pq_part, sc);
+        else
+            k_grid_q<R, 2><<<blocks, kQThreads, 0, st>>>(g.nx, g.ny, bins.ncx, bins.ncy, bins.cunit_off, part, invT,
+                                                        scaled, cx, cy, gamma, l1, p, q, pq_part, sc);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }
@@ -683,13 +849,26 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     const size_t o_b = scr.reserve(sizeof(double) * n4), o_x = scr.reserve(sizeof(double) * n4);
     const size_t o_pr = scr.reserve(sizeof(R) == 4 ? sizeof(R) * n4 : 0);
     MPI_TRY(scr.allocate());
-    const Bins bins = bins_carve<R>(scr.at<char>(o_bins), T, g.nx, g.ny);
+    Bins bins = bins_carve<R>(scr.at<char>(o_bins), T, g.nx, g.ny);
     R *s_data = scr.at<R>(o_sd);
     double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x);
 
     MPI_TRY(build_bins<R>(g, T, r, v, bins, st));
     // The sample vectors of the solve live in list (cell) order.
     MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
+    // The transpose runs up to thousands of times with the same units: read
+    // their count once, so every launch covers exactly them.
+    {
+        int n_units = 0;
+        MPI_TRY_CUDA(cudaMemcpyAsync(&n_units, bins.cunit_off + bins.ncx * bins.ncy, sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+        MPI_TRY_CUDA(cudaStreamSynchronize(st));
+        if (n_units < 0 || n_units > bins.n_units_max) {
+            set_error("Core Stage: %d work units exceed the bound %d", n_units, bins.n_units_max);
+            return MPI_ERR_CUDA;
+        }
+        bins.n_units = n_units;
+    }
     GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_s), scr.at<R>(o_pr), o.lap_scaled != 0);
     // b = (1/T) M^T s
     MPI_TRY((launch_interp_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
@@ -761,25 +940,43 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
                   int *n_iter_out, cudaStream_t st)
 {
     const int ncs = cs_blocks(nv);
-    const int nepi = op.pq_blocks(nv);
+    const int npq = op.pq_blocks(nv);
+    const P32 p32 = op.p32();
     Scratch scr(st);
     const size_t vb = sizeof(double) * nv;
-    const size_t o_r = scr.reserve(vb), o_p = scr.reserve(vb), o_q = scr.reserve(vb),
-                 o_y = scr.reserve(op.fused() ? 0 : vb), o_l1 = scr.reserve(vb),
-                 o_l2 = scr.reserve(op.fused() ? 0 : vb);
-    const size_t o_pq = scr.reserve(sizeof(double) * nepi), o_rr = scr.reserve(sizeof(double) * ncs);
+    const size_t o_r = scr.reserve(vb), o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_l1 = scr.reserve(vb);
+    const size_t o_pq = scr.reserve(sizeof(double) * npq), o_rr = scr.reserve(sizeof(double) * ncs);
     const size_t o_sc = scr.reserve(sizeof(CsScal));
     MPI_TRY(scr.allocate());
     double *rr = scr.at<double>(o_r), *p = scr.at<double>(o_p), *q = scr.at<double>(o_q),
-           *y = scr.at<double>(o_y), *l1 = scr.at<double>(o_l1), *l2 = scr.at<double>(o_l2);
+           *l1 = scr.at<double>(o_l1);
     double *pq_part = scr.at<double>(o_pq), *rr_part = scr.at<double>(o_rr);
     CsScal *sc = scr.at<CsScal>(o_sc);
+
+    // The side stream and events of the step's fork-join (released when the
+    // solve returns; the stream's work is joined into st by then).
+    struct Fork {
+        StepFork f{nullptr, nullptr, nullptr};
+        ~Fork()
+        {
+            if (f.side) {
+                cudaStreamSynchronize(f.side);  // (an error path may have left a fork unjoined)
+                cudaStreamDestroy(f.side);
+            }
+            if (f.fork) cudaEventDestroy(f.fork);
+            if (f.join) cudaEventDestroy(f.join);
+        }
+    } fk;
+    MPI_TRY_CUDA(cudaStreamCreateWithFlags(&fk.f.side, cudaStreamNonBlocking));
+    MPI_TRY_CUDA(cudaEventCreateWithFlags(&fk.f.fork, cudaEventDisableTiming));
+    MPI_TRY_CUDA(cudaEventCreateWithFlags(&fk.f.join, cudaEventDisableTiming));
 
     MPI_TRY_CUDA(cudaMemsetAsync(x, 0, vb, st));
     MPI_TRY_CUDA(cudaMemsetAsync(sc, 0, sizeof(CsScal), st));
     // r = b, p = b, r.r, ||b|| and the threshold
     k_cs_init<<<ncs, kCsThreads, 0, st>>>(nv, b, rr, p, rr_part, o.rel_tol, sc);
     MPI_CHECK_LAUNCH();
+    if (p32.buf) MPI_TRY(cs_round_launch(p32, p, st));
 
     int *h_done = nullptr;
     MPI_TRY_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h_done), sizeof(int)));
@@ -791,22 +988,13 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
     const bool thresh = o.rel_tol > 0.0;
 
     // One CG step: q = (1/T) M^T M p + gamma Lap Lap p, <p, q> and alpha (or
-    // the stop), then the update and beta, then the new direction.
+    // the stop), then the update and beta, then the new direction (and its
+    // FP32 copy).
     auto enqueue_step = [&](int, cudaStream_t s) -> int {
-        if (op.fused()) {
-            MPI_TRY(op.step_q(p, o.gamma, q, pq_part, sc, y, l1, s));
-        } else {
-            MPI_TRY(op.normal(p, y, s));
-            MPI_TRY(op.lap(p, l1, s));
-            MPI_TRY(op.lap(l1, l2, s));
-            k_grid_epilogue<<<nepi, kEpiThreads, 0, s>>>(nv, y, l2, o.gamma, p, q, pq_part, sc);
-            MPI_CHECK_LAUNCH();
-        }
+        MPI_TRY(op.step_q(p, o.gamma, q, pq_part, sc, l1, fk.f, s));
         k_cs_step1<<<ncs, kCsThreads, 0, s>>>(nv, x, rr, p, q, rr_part, sc);
         MPI_CHECK_LAUNCH();
-        k_cs_step2<<<ncs, kCsThreads, 0, s>>>(nv, rr, p, sc);
-        MPI_CHECK_LAUNCH();
-        return MPI_OK;
+        return cs_step2_launch(p32, nv, rr, p, sc, s);
     };
     auto poll_done = [&](bool &stop) -> int {
         MPI_TRY_CUDA(cudaMemcpyAsync(h_done, done, sizeof(int), cudaMemcpyDeviceToHost, st));
