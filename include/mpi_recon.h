@@ -485,6 +485,7 @@ int mpi_profile_read(int kernel_class, long long *launches, double *total_ms);
 #define MPI_PROBE_EX2 2   /* ex2.approx.ftz.f32 */
 #define MPI_PROBE_RCP 3   /* rcp.approx.ftz.f32 (each after an FP32 add) */
 #define MPI_PROBE_DFMA 4  /* FP64 fma.rn */
+#define MPI_PROBE_FMA2 5  /* fma.rn.f32x2 (two packed FP32 lanes: counted as 2 operations) */
 int mpi_probe_pipe_rate(int op, int blocks_per_sm, int iters, double *ops_per_clk_sm, double *ms,
                         void *stream);
 

@@ -190,13 +190,14 @@ def exported_symbols():
 
 
 PROF_FORWARD, PROF_ADJOINT, PROF_DBETA, PROF_CONV = 0, 1, 2, 3
-PROBE_FMA, PROBE_RSQRT, PROBE_EX2, PROBE_RCP, PROBE_DFMA = 0, 1, 2, 3, 4
+PROBE_FMA, PROBE_RSQRT, PROBE_EX2, PROBE_RCP, PROBE_DFMA, PROBE_FMA2 = 0, 1, 2, 3, 4, 5
 
 
 def mpi_probe_pipe_rate(op: int, blocks_per_sm: int = 8, iters: int = 4096, stream=None):
     """(thread-operations per SM per clock, launch ms) of one instruction
-    kind (PROBE_FMA, PROBE_RSQRT, PROBE_EX2, PROBE_RCP, PROBE_DFMA) measured on the
-    current GPU; the median over SMs of operations per SM clock cycle."""
+    kind (PROBE_FMA, PROBE_RSQRT, PROBE_EX2, PROBE_RCP, PROBE_DFMA, PROBE_FMA2)
+    measured on the current GPU; the median over SMs of operations per SM
+    clock cycle (PROBE_FMA2: two per packed instruction)."""
     rate = ctypes.c_double(0.0)
     ms = ctypes.c_double(0.0)
     _check(load().mpi_probe_pipe_rate(int(op), int(blocks_per_sm), int(iters), ctypes.byref(rate),

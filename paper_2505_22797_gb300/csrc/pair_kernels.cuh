@@ -72,16 +72,17 @@ constexpr int kAdjThreads = 32 * kAdjWarps;
 #endif
 // Tuning knobs (compile time), chosen by timing variants on GB300: minimum
 // resident blocks per SM requested from the register allocator for the FP32
-// kernels (6 x 128 threads for both, 80 registers; the adjoint, whose
-// asymptotic pair term is a short dependent chain, is latency-bound below 6),
-// and the unroll depth of the forward column loop (4 columns in flight: 2 %
-// faster than 8 at 128 x 128 / 65 536 samples).  The FP64 kernels request 2
-// blocks per SM (no spills).
+// kernels (forward: 6 x 128 threads, 80 registers; adjoint: 5 x 128, 96
+// registers -- its packed asymptotic tier spills at 80; at 128 x 128 /
+// 65 536 samples 0.431 ms against 0.438 ms with 4 blocks and 0.441 ms with
+// 6), and the unroll depth of the forward column loop (4 columns in flight:
+// 2 % faster than 8 at 128 x 128 / 65 536 samples).  The FP64 kernels
+// request 2 blocks per SM (no spills).
 #ifndef MPI_FWD_MINB
 #define MPI_FWD_MINB 6
 #endif
 #ifndef MPI_ADJ_MINB
-#define MPI_ADJ_MINB (24 / MPI_ADJ_WARPS)
+#define MPI_ADJ_MINB (20 / MPI_ADJ_WARPS)
 #endif
 #ifndef MPI_FWD_UNROLL
 #define MPI_FWD_UNROLL 4
@@ -99,12 +100,24 @@ constexpr int kAdjTileY = kAdjWarps * kAdjV;
 #ifndef MPI_ADJ_BLOCK
 #define MPI_ADJ_BLOCK 256
 #endif
-// Unroll depth of the adjoint's asymptotic 32-sample loop (32 = the whole
-// group: staged-sample addresses become constant offsets).
+// Unroll depth of the adjoint's asymptotic loop over a group's 32 samples
+// (packed: 16 sample pairs; 4 pairs in flight timed fastest, 0.431 ms at
+// 128 x 128 / 65 536 samples against 0.432 ms with 1).
 #ifndef MPI_ADJ_UNROLL_VFAR
-#define MPI_ADJ_UNROLL_VFAR 2
+#define MPI_ADJ_UNROLL_VFAR 4
 #endif
 constexpr int kAdjUnrollVfar = MPI_ADJ_UNROLL_VFAR;
+// FP32 asymptotic tier of the adjoint in packed two-lane FP32 arithmetic
+// (fma.rn.f32x2 and its add/mul forms, sm_100 and later): the pair term is
+// issue-bound, and a packed instruction does two lanes' FP32 work in one
+// issue slot (measured on GB300: 126 FP32 FMAs per SM per clock either way,
+// from half the instructions).  The staged samples are then also kept as
+// even/odd pairs, and each voxel accumulates its even and odd samples in the
+// two lanes of a pair (added into the voxel's sum after each group of 32).
+#ifndef MPI_ADJ_PACK
+#define MPI_ADJ_PACK 1
+#endif
+constexpr bool kAdjPack = MPI_ADJ_PACK != 0;
 
 constexpr int kAdjBlock = MPI_ADJ_BLOCK;  // samples staged per shared-memory block
 
@@ -477,6 +490,43 @@ __device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const 
     }
 }
 
+#ifdef __CUDACC__
+// Two staged samples (2h, 2h + 1) against this thread's kAdjV voxels in the
+// asymptotic range, diagonal G, packed: a = (-x_e, -x_o, -y_e, -y_o) of B r,
+// b = (uW_e, uW_o, Sxx_e, Sxx_o), c = (S2xy_e, S2xy_o, Syy_e, Syy_o); xc2 =
+// (x_c, x_c) of the thread's column, yr2[v] = (y_v, y_v).  Lane-wise the
+// same operations, in the same order, as adj_sample's MODE 2 on each sample.
+template <bool DBETA>
+__device__ __forceinline__ void adj_pair2_vfar_diag(const float4 a, const float4 b, const float4 c,
+                                                    const float2 xc2, const float2 (&yr2)[kAdjV],
+                                                    float2 (&blk2)[kAdjV])
+{
+    const float2 nry = make_float2(a.z, a.w);
+    const float2 uW = make_float2(b.x, b.y), Sxx = make_float2(b.z, b.w);
+    const float2 S2xy = make_float2(c.x, c.y), Syy = make_float2(c.z, c.w);
+    const float2 yx = __fadd2_rn(xc2, make_float2(a.x, a.y));
+    const float2 yx2 = __fmul2_rn(yx, yx);
+    const float2 Q0 = __fmul2_rn(Sxx, yx2), Q1 = __fmul2_rn(S2xy, yx);
+    const float2 nuW = __fmul2_rn(uW, make_float2(-1.0f, -1.0f));
+#pragma unroll
+    for (int v = 0; v < kAdjV; ++v) {
+        const float2 yy = __fadd2_rn(yr2[v], nry);
+        const float2 u = __ffma2_rn(yy, yy, yx2);
+        const float2 P = __ffma2_rn(yy, __ffma2_rn(Syy, yy, Q1), Q0);
+        const float2 iz = make_float2(Lang<float>::iz_vfar(u.x), Lang<float>::iz_vfar(u.y));
+        if constexpr (DBETA) {
+            const float2 iz2 = __fmul2_rn(iz, iz);
+            const float2 t = __ffma2_rn(__fmul2_rn(iz2, P), make_float2(-2.0f, -2.0f), uW);
+            blk2[v] = __ffma2_rn(iz2, t, blk2[v]);
+        } else {
+            const float2 t = __fmul2_rn(P, __ffma2_rn(iz, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f)));
+            const float2 w = __ffma2_rn(iz, t, nuW);
+            blk2[v] = __ffma2_rn(iz, __ffma2_rn(iz, w, uW), blk2[v]);
+        }
+    }
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // Adjoint A^T (DBETA = false) and the beta-derivative (DBETA = true).
 // Work item = (tile of 32 x kAdjTileY voxels, chunk of samples).  Lane =
@@ -494,8 +544,12 @@ __device__ __forceinline__ void adj_sample(const V2<R> rr, const V4<R> q, const 
 template <typename R, bool DIAG, bool DBETA, int MAXF, bool ONEBLK>
 __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_t item)
 {
+    // PACK: the FP32 diagonal-G asymptotic tier runs packed (kAdjPack), from
+    // a second copy of the staged samples in pairs (three float4 per pair).
+    constexpr bool PACK = kAdjPack && sizeof(R) == 4 && DIAG;
     __shared__ V2<R> s_rw[kAdjStageCopies][kAdjBlock];
     __shared__ V4<R> s_qw[kAdjStageCopies][kAdjBlock];
+    __shared__ float4 s_pkw[PACK ? kAdjStageCopies : 1][PACK ? 3 * kAdjBlock / 2 : 1];
     __shared__ uint32_t s_far[kAdjWarps][kAdjBlock / 32];
     __shared__ uint32_t s_vfar[kAdjWarps][kAdjBlock / 32];
     __shared__ double s_red[kAdjThreads / 32];
@@ -509,6 +563,7 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
     const int jb = (tile / F.tiles_x) * kAdjTileY + warp * kAdjV;
     V2<R> *s_r = s_rw[MPI_ADJ_WSTAGE ? warp : 0];
     V4<R> *s_q = s_qw[MPI_ADJ_WSTAGE ? warp : 0];
+    float4 *s_pk = s_pkw[PACK && MPI_ADJ_WSTAGE ? warp : 0];
     // stager: this warp's lanes (one copy per warp) or the block's threads
     const int st_id = MPI_ADJ_WSTAGE ? lane : (int)threadIdx.x;
     constexpr int st_n = MPI_ADJ_WSTAGE ? 32 : kAdjThreads;
@@ -522,6 +577,10 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
         yrow_x[v] = q.x;
         yrow_y[v] = q.y;
     }
+    const float2 xc2 = make_float2(float(xc.x), float(xc.x));
+    float2 yr2[PACK ? kAdjV : 1];
+#pragma unroll
+    for (int v = 0; v < (PACK ? kAdjV : 1); ++v) yr2[v] = make_float2(float(yrow_y[v]), float(yrow_y[v]));
     // Voxel box of this warp in prescaled coordinates (conservative).
     R bx_lo = xc.x, bx_hi = xc.x, by_lo = xc.y, by_hi = xc.y;
 #pragma unroll
@@ -564,8 +623,18 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
                 ux += sv * F.p[2 * c];
                 uy += sv * F.p[2 * c + 1];
             }
+            const V4<R> sq = V4<R>{ux * q.z + uy * q.w, q.z * ux, q.z * uy + q.w * ux, q.w * uy};
             s_r[k] = V2<R>{q.x, q.y};
-            s_q[k] = V4<R>{ux * q.z + uy * q.w, q.z * ux, q.z * uy + q.w * ux, q.w * uy};
+            s_q[k] = sq;
+            if constexpr (PACK) {
+                float *pb = reinterpret_cast<float *>(s_pk + 3 * (k >> 1)) + (k & 1);
+                pb[0] = -float(q.x);
+                pb[2] = -float(q.y);
+                pb[4] = float(sq.x);
+                pb[6] = float(sq.y);
+                pb[8] = float(sq.z);
+                pb[10] = float(sq.w);
+            }
         }
         if (MPI_ADJ_WSTAGE) __syncwarp();
         else __syncthreads();
@@ -601,9 +670,22 @@ __device__ __forceinline__ void adjoint_item(const PairBatch<R, MAXF> &B, int64_
             const uint32_t vmask = s_vfar[warp][k0 >> 5];
             const int kn = min(32, nb - k0);
             if (kn == 32 && vmask == 0xffffffffu) {
+                if constexpr (PACK) {
+                    // the group's even and odd samples in the two lanes, then
+                    // added into the block sums
+                    float2 blk2[kAdjV];
+#pragma unroll
+                    for (int v = 0; v < kAdjV; ++v) blk2[v] = make_float2(0.0f, 0.0f);
 #pragma unroll kAdjUnrollVfar
-                for (int k = k0; k < k0 + 32; ++k)
-                    adj_sample<R, DIAG, DBETA, 2>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
+                    for (int h = k0 >> 1; h < (k0 >> 1) + 16; ++h)
+                        adj_pair2_vfar_diag<DBETA>(s_pk[3 * h], s_pk[3 * h + 1], s_pk[3 * h + 2], xc2, yr2, blk2);
+#pragma unroll
+                    for (int v = 0; v < kAdjV; ++v) blk[v] += blk2[v].x + blk2[v].y;
+                } else {
+#pragma unroll kAdjUnrollVfar
+                    for (int k = k0; k < k0 + 32; ++k)
+                        adj_sample<R, DIAG, DBETA, 2>(s_r[k], s_q[k], xc, yrow_x, yrow_y, blk);
+                }
             } else if (kn == 32 && mask == 0xffffffffu) {
 #pragma unroll 2
                 for (int k = k0; k < k0 + 32; ++k)

@@ -1,7 +1,8 @@
 // Pipe-rate probe: the measured throughput of the instruction kinds the pair
 // kernels are made of (FP32 FMA, and the MUFU/XU operations rsqrt.approx,
-// ex2.approx, rcp.approx; FP64 FMA for the all-FP64 form), in
-// thread-operations per SM per clock.  The pair
+// ex2.approx, rcp.approx; FP64 FMA for the all-FP64 form; the packed
+// two-lane FP32 FMA fma.rn.f32x2 of sm_100 and later, counted as two
+// operations), in thread-operations per SM per clock.  The pair
 // kernels' roofline is an issue/pipe bound, so its denominator is taken from
 // this measurement on the GPU that runs them rather than from a datasheet.
 //
@@ -24,6 +25,19 @@ constexpr int kProbeChains = 8;
 
 template <int OP> struct ProbeType { using T = float; };
 template <> struct ProbeType<MPI_PROBE_DFMA> { using T = double; };
+template <> struct ProbeType<MPI_PROBE_FMA2> { using T = unsigned long long; };  // two packed f32
+
+template <typename T> __device__ __forceinline__ T probe_init(float v) { return T(v); }
+template <> __device__ __forceinline__ unsigned long long probe_init<unsigned long long>(float v)
+{
+    const unsigned b = __float_as_uint(v);
+    return (unsigned long long)b | ((unsigned long long)b << 32);
+}
+template <typename T> __device__ __forceinline__ float probe_value(T v) { return float(v); }
+template <> __device__ __forceinline__ float probe_value<unsigned long long>(unsigned long long v)
+{
+    return __uint_as_float((unsigned)v) + __uint_as_float((unsigned)(v >> 32));
+}
 
 // Every timed operation is a volatile asm statement: the compiler keeps them
 // all, in program order relative to the (volatile) clock reads around the
@@ -34,6 +48,10 @@ __device__ __forceinline__ typename ProbeType<OP>::T probe_op(typename ProbeType
     typename ProbeType<OP>::T y;
     if constexpr (OP == MPI_PROBE_FMA)
         asm volatile("fma.rn.f32 %0, %1, 0f3F7FC000, 0f3A800000;" : "=f"(y) : "f"(x));
+    else if constexpr (OP == MPI_PROBE_FMA2)  // both lanes: x <- x 0.99902 + 2^-10
+        asm volatile("fma.rn.f32x2 %0, %1, %2, %3;"
+                     : "=l"(y)
+                     : "l"(x), "l"(0x3F7FC0003F7FC000ull), "l"(0x3A8000003A800000ull));
     else if constexpr (OP == MPI_PROBE_DFMA)
         asm volatile("fma.rn.f64 %0, %1, 0d3FEFF80000000000, 0d3F50000000000000;" : "=d"(y) : "d"(x));
     else if constexpr (OP == MPI_PROBE_RSQRT)
@@ -59,7 +77,7 @@ k_pipe_probe(int iters, float *__restrict__ sink, long long *__restrict__ rec)
     using T = typename ProbeType<OP>::T;
     T x[kProbeChains];
 #pragma unroll
-    for (int k = 0; k < kProbeChains; ++k) x[k] = T(0.5f + 0.001f * float((threadIdx.x + 37 * k) & 255));
+    for (int k = 0; k < kProbeChains; ++k) x[k] = probe_init<T>(0.5f + 0.001f * float((threadIdx.x + 37 * k) & 255));
     const unsigned long long t0 = (unsigned long long)clock64();
     // unrolled so that loop control is a few percent of the issued
     // instructions (FP32 FMA is issue-bound, and counts them)
@@ -71,7 +89,7 @@ k_pipe_probe(int iters, float *__restrict__ sink, long long *__restrict__ rec)
     const unsigned long long t1 = (unsigned long long)clock64();
     float acc = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kProbeChains; ++k) acc += float(x[k]);
+    for (int k = 0; k < kProbeChains; ++k) acc += probe_value<T>(x[k]);
     sink[(int64_t)blockIdx.x * kProbeThreads + threadIdx.x] = acc;
     atomicMin(&s_t0, t0);
     atomicMax(&s_t1, t1);
@@ -100,7 +118,7 @@ using namespace mpi;
 extern "C" int mpi_probe_pipe_rate(int op, int blocks_per_sm, int iters, double *ops_per_clk_sm,
                                    double *ms, void *stream)
 {
-    if (op < MPI_PROBE_FMA || op > MPI_PROBE_DFMA || blocks_per_sm < 1 || blocks_per_sm > 8 ||
+    if (op < MPI_PROBE_FMA || op > MPI_PROBE_FMA2 || blocks_per_sm < 1 || blocks_per_sm > 8 ||
         iters < 1 || iters > (1 << 20) || !ops_per_clk_sm) {
         set_error("invalid pipe probe arguments (op %d, blocks_per_sm %d, iters %d)", op,
                   blocks_per_sm, iters);
@@ -124,6 +142,7 @@ extern "C" int mpi_probe_pipe_rate(int op, int blocks_per_sm, int iters, double 
         case MPI_PROBE_RSQRT: rc = probe_launch<MPI_PROBE_RSQRT>(blocks, iters, sink, rec, st); break;
         case MPI_PROBE_EX2: rc = probe_launch<MPI_PROBE_EX2>(blocks, iters, sink, rec, st); break;
         case MPI_PROBE_DFMA: rc = probe_launch<MPI_PROBE_DFMA>(blocks, iters, sink, rec, st); break;
+        case MPI_PROBE_FMA2: rc = probe_launch<MPI_PROBE_FMA2>(blocks, iters, sink, rec, st); break;
         default: rc = probe_launch<MPI_PROBE_RCP>(blocks, iters, sink, rec, st); break;
     }
     MPI_TRY(rc);
@@ -148,7 +167,8 @@ extern "C" int mpi_probe_pipe_rate(int op, int blocks_per_sm, int iters, double 
         nb[s] += 1;
     }
     std::vector<double> rate;
-    const double ops_per_block = double(kProbeThreads) * kProbeChains * double(iters);
+    const double ops_per_block =
+        double(kProbeThreads) * kProbeChains * double(iters) * (op == MPI_PROBE_FMA2 ? 2.0 : 1.0);
     for (int s = 0; s <= max_sm; ++s)
         if (nb[s] > 0 && hi[s] > lo[s]) rate.push_back(ops_per_block * double(nb[s]) / double(hi[s] - lo[s]));
     if (rate.empty()) {
