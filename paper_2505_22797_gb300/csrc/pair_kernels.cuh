@@ -75,9 +75,10 @@ constexpr int kAdjThreads = 32 * kAdjWarps;
 // kernels (forward: 6 x 128 threads, 80 registers; adjoint: 5 x 128, 96
 // registers -- its packed asymptotic tier spills at 80; at 128 x 128 /
 // 65 536 samples 0.431 ms against 0.438 ms with 4 blocks and 0.441 ms with
-// 6), and the unroll depth of the forward column loop (4 columns in flight:
-// 2 % faster than 8 at 128 x 128 / 65 536 samples).  The FP64 kernels
-// request 2 blocks per SM (no spills).
+// 6), and the unroll depth of the forward column loop (packed asymptotic
+// loop: 8 columns in flight, 0.457 ms at 128 x 128 / 65 536 samples against
+// 0.461 ms with 4 and 0.471 ms with 2).  The FP64 kernels request 2 blocks
+// per SM (no spills).
 #ifndef MPI_FWD_MINB
 #define MPI_FWD_MINB 6
 #endif
@@ -85,9 +86,13 @@ constexpr int kAdjThreads = 32 * kAdjWarps;
 #define MPI_ADJ_MINB (20 / MPI_ADJ_WARPS)
 #endif
 #ifndef MPI_FWD_UNROLL
-#define MPI_FWD_UNROLL 4
+#define MPI_FWD_UNROLL 8
 #endif
 constexpr int kFwdUnroll = MPI_FWD_UNROLL;
+#ifndef MPI_FWD_PACK
+#define MPI_FWD_PACK 1
+#endif
+constexpr bool kFwdPack = MPI_FWD_PACK != 0;
 // Unroll depth of the full closed-form column loops (a few percent of the
 // pairs once the asymptotic tier takes the rest: kept short for code size).
 #ifndef MPI_FWD_UNROLL_FAR
@@ -192,13 +197,41 @@ __device__ __forceinline__ void fwd_row_far(int i0, int i1, const V2<R> *__restr
 }
 
 // The same sums over columns [i0, i1) whose pairs all have u >= vfar_u: the
-// asymptotic closed form (one rsqrt per pair).
+// asymptotic closed form (one rsqrt per pair).  FP32 with two samples per
+// thread and kFwdPack: the two samples are the two lanes of packed FP32
+// arithmetic (f32x2, sm_100 and later: the same FP32 work from half the
+// issue slots; the FMA pipe then bounds the loop).
 template <typename R>
 __device__ __forceinline__ void fwd_row_vfar(int i0, int i1, const V2<R> *__restrict__ xc,
                                              const R (&Rx)[kFwdS], const R (&yy2)[kFwdS],
                                              const R (&Wx)[kFwdS], const R (&yyW)[kFwdS],
                                              R (&sa)[kFwdS], R (&vx)[kFwdS], R (&fy)[kFwdS])
 {
+    if constexpr (kFwdPack && sizeof(R) == 4 && kFwdS == 2) {
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        const float2 nRx = make_float2(-Rx[0], -Rx[1]), yy2p = make_float2(yy2[0], yy2[1]);
+        const float2 Wxp = make_float2(Wx[0], Wx[1]), yyWp = make_float2(yyW[0], yyW[1]);
+        float2 sa2 = make_float2(0.0f, 0.0f), vx2 = sa2, fy2 = sa2;
+#pragma unroll kFwdUnroll
+        for (int i = i0; i < i1; ++i) {
+            const V2<R> q = xc[i];
+            const float2 cc = make_float2(q.y, q.y);
+            const float2 yx = __fadd2_rn(make_float2(q.x, q.x), nRx);
+            const float2 u = __ffma2_rn(yx, yx, yy2p);
+            const float2 iz = make_float2(Lang<float>::iz_vfar(u.x), Lang<float>::iz_vfar(u.y));
+            const float2 iz2 = __fmul2_rn(iz, iz);
+            const float2 a = __ffma2_rn(iz2, m1, iz);                       // iz - iz^2
+            const float2 d = __fmul2_rn(__ffma2_rn(a, m1, iz2), iz2);       // (2 iz^2 - iz) iz^2
+            sa2 = __ffma2_rn(cc, a, sa2);
+            const float2 f = __fmul2_rn(__fmul2_rn(cc, d), __ffma2_rn(yx, Wxp, yyWp));
+            vx2 = __ffma2_rn(f, yx, vx2);
+            fy2 = __fadd2_rn(fy2, f);
+        }
+        sa[0] += sa2.x; sa[1] += sa2.y;
+        vx[0] += vx2.x; vx[1] += vx2.y;
+        fy[0] += fy2.x; fy[1] += fy2.y;
+        return;
+    }
 #pragma unroll kFwdUnroll
     for (int i = i0; i < i1; ++i) {
         const V2<R> q = xc[i];
