@@ -54,7 +54,10 @@ sys.path.insert(0, ROOT)
 #          nested form: 2 (distance) + 2 (quadratic form) + 5, one rsqrt.
 # Pairs near the FFP (u < 1, the Taylor series) are a ~1e-4 fraction and are
 # counted as "far".  The algorithmic count of a launch is the pair-weighted
-# mix, with the vfar fraction measured on the workload's geometry.
+# mix, with the vfar fraction measured on the workload's geometry.  The FP32
+# kernels issue the vfar tier's FP32 operations as packed two-lane
+# instructions (f32x2: two operations per issue slot, the same FP32 lanes),
+# so that tier's issue count is half its FP32 operations plus its XU ones.
 ALG_OPS = {"k_forward": {"far": (18, 3), "vfar": (12, 1)},
            "k_adjoint": {"far": (17, 3), "vfar": (9, 1)}}
 VFAR_U32 = 144.0
@@ -112,17 +115,28 @@ def xu_cycles_mixed(f_vfar, rates):
     return (1.0 - f_vfar) * far + f_vfar / rates["rsqrt"]
 
 
+def packed_issue(kernel, f_vfar):
+    """Issue slots per pair of the tier mix when the vfar tier's FP32
+    operations are packed two per instruction."""
+    (a32, axu), (b32, bxu) = ALG_OPS[kernel]["far"], ALG_OPS[kernel]["vfar"]
+    return (1 - f_vfar) * (a32 + axu) + f_vfar * (b32 / 2.0 + bxu)
+
+
 def roofline_bases(kernel, f_vfar, sm_count, sm_mhz, rates, achieved, executed=None):
     """The roofline of one pair kernel on three bases (pairs/s, 1e9):
     tier_weighted -- the algorithmic count of the asymptotic/closed-form mix
-    with the measured pipe rates (the headline fraction); plain_closed_form --
+    with the measured pipe rates (FP32 lanes at the faster of the scalar and
+    packed FMA rates; issue of the packed instruction count; the headline
+    fraction); plain_closed_form --
     every pair in the full closed form, 25 FP32 + 3 XU, FP32 at 128 and XU at
     16 per SM per clock (above 1 when most pairs take the asymptotic form);
     executed -- the instructions per pair the kernel actually executes (ncu),
     at the issue rate."""
     n32, nxu = mixed_ops(kernel, f_vfar)
-    peak = pipe_bound_gpair(sm_count, sm_mhz, n32, xu_cycles_mixed(f_vfar, rates), nxu,
-                            fma_rate=rates["fma"])
+    lanes = max(rates["fma"], rates.get("fma2", 0.0))
+    per_clk = 1.0 / max(packed_issue(kernel, f_vfar) / ISSUE_PER_CLK, n32 / lanes,
+                        xu_cycles_mixed(f_vfar, rates))
+    peak = sm_count * sm_mhz * 1e6 * per_clk / 1e9
     plain = sm_count * sm_mhz * 1e6 * min(PLAIN_RATES["fma"] / PLAIN_OPS[0],
                                           PLAIN_RATES["xu"] / PLAIN_OPS[1]) / 1e9
     out = {"tier_weighted": {"ops_per_pair": [round(n32, 3), round(nxu, 4)], "peak": peak,
@@ -382,9 +396,9 @@ def pipe_rates(api):
     """Measured FP32-FMA, MUFU (rsqrt, ex2, rcp) and FP64-FMA rates, thread
     operations per SM per clock (median over SMs, SM clock cycles)."""
     out = {}
-    for name, op, it in (("fma", api.PROBE_FMA, 8192), ("rsqrt", api.PROBE_RSQRT, 4096),
-                         ("ex2", api.PROBE_EX2, 4096), ("rcp", api.PROBE_RCP, 4096),
-                         ("dfma", api.PROBE_DFMA, 512)):
+    for name, op, it in (("fma", api.PROBE_FMA, 8192), ("fma2", api.PROBE_FMA2, 8192),
+                         ("rsqrt", api.PROBE_RSQRT, 4096), ("ex2", api.PROBE_EX2, 4096),
+                         ("rcp", api.PROBE_RCP, 4096), ("dfma", api.PROBE_DFMA, 512)):
         api.mpi_probe_pipe_rate(op, 8, 64)
         out[name], _ = api.mpi_probe_pipe_rate(op, 8, it)
     return out
@@ -1161,10 +1175,13 @@ def run_ours(args):
                 "frac": tw["frac"], "traffic": _traffic(dom), "kernel": dom, "launches": kd["launches"],
                 "avg_launch_ms": kd["avg_launch_ms"],
                 "peak_basis": (f"pipe bound at the sampled clock: {sm_count} SMs x {sm_run:.0f} MHz x "
-                               f"1/max(issue 128/clk, FP32 {rates['fma']:.1f}/clk, XU rsqrt {rates['rsqrt']:.1f} "
-                               f"ex2 {rates['ex2']:.1f} rcp {rates['rcp']:.1f}/clk per SM, measured) over "
-                               f"{tw['ops_per_pair'][0]:.2f} FP32 + {tw['ops_per_pair'][1]:.3f} XU algorithmic "
-                               f"ops per pair ({f_vfar:.4f} of the pairs in the asymptotic regime u >= 144)"),
+                               f"1/max(issue 128/clk of {packed_issue(dom, f_vfar):.2f} instructions per pair "
+                               f"(asymptotic tier's FP32 packed two per instruction), FP32 lanes "
+                               f"{max(rates['fma'], rates.get('fma2', 0.0)):.1f}/clk, XU rsqrt "
+                               f"{rates['rsqrt']:.1f} ex2 {rates['ex2']:.1f} rcp {rates['rcp']:.1f}/clk per SM, "
+                               f"measured) over {tw['ops_per_pair'][0]:.2f} FP32 + {tw['ops_per_pair'][1]:.3f} "
+                               f"XU algorithmic ops per pair ({f_vfar:.4f} of the pairs in the asymptotic regime "
+                               f"u >= 144)"),
                 "bases": kd["bases"], "pipe_rates_per_sm_clk": rates, "kernels": kern,
                 "share_of_step": (fms + ams) / prof_ms if prof_ms else None,
                 "profiled_step_ms": prof_ms}

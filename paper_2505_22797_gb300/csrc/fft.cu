@@ -77,6 +77,43 @@ __device__ __forceinline__ void butterfly(const C *__restrict__ xc, C *__restric
     }
 }
 
+// The same butterfly for a power-of-two length with R = 2 or 4: the index
+// arithmetic by shifts and masks (lg_n = log2 n, lg_ns = log2 Ns) instead of
+// the divisions by runtime values above, which cost more instructions than
+// the butterfly itself.  The same loads, twiddles and operations: the
+// results are identical.
+template <typename C>
+__device__ __forceinline__ void butterfly_p2(const C *__restrict__ xc, C *__restrict__ yc, int lg_n, int R,
+                                             int lg_ns, const C *__restrict__ W, int j)
+{
+    const int Ns = 1 << lg_ns;
+    const int k = j & (Ns - 1);
+    if (R == 4) {
+        const int nb = 1 << (lg_n - 2);
+        const int tw = k << (lg_n - lg_ns - 2);  // k n / (4 Ns)
+        const int out0 = ((j >> lg_ns) << (lg_ns + 2)) + k;
+        const C a0 = xc[j];
+        const C a1 = cmul(xc[j + nb], W[tw]);
+        const C a2 = cmul(xc[j + 2 * nb], W[2 * tw]);
+        const C a3 = cmul(xc[j + 3 * nb], W[3 * tw]);
+        const C s02 = cxv(a0.x + a2.x, a0.y + a2.y);
+        const C d02 = cxv(a0.x - a2.x, a0.y - a2.y);
+        const C s13 = cxv(a1.x + a3.x, a1.y + a3.y);
+        const C d13 = cxv(a1.x - a3.x, a1.y - a3.y);
+        yc[out0] = cxv(s02.x + s13.x, s02.y + s13.y);
+        yc[out0 + Ns] = cxv(d02.x + d13.y, d02.y - d13.x);
+        yc[out0 + 2 * Ns] = cxv(s02.x - s13.x, s02.y - s13.y);
+        yc[out0 + 3 * Ns] = cxv(d02.x - d13.y, d02.y + d13.x);
+    } else {
+        const int nb = 1 << (lg_n - 1);
+        const int tw = k << (lg_n - lg_ns - 1);  // k n / (2 Ns)
+        const int out0 = ((j >> lg_ns) << (lg_ns + 1)) + k;
+        const C a = xc[j], b = cmul(xc[j + nb], W[tw]);
+        yc[out0] = cxv(a.x + b.x, a.y + b.y);
+        yc[out0 + Ns] = cxv(a.x - b.x, a.y - b.y);
+    }
+}
+
 // One Stockham pass over global memory; `dist` is the distance between
 // channels (blockIdx.y).
 template <typename C>
@@ -103,6 +140,7 @@ k_fft_pass(const C *__restrict__ x, C *__restrict__ y, int64_t n, int R, int64_t
 constexpr int kSmemFftMaxPasses = 24;
 struct RadixList {
     int n_pass;
+    int lg_n;  // log2 n when every radix is 2 or 4 (shift arithmetic), else -1
     int r[kSmemFftMaxPasses];
 };
 
@@ -129,6 +167,21 @@ k_fft_smem(C *__restrict__ x, int n, RadixList rl, const C *__restrict__ W, int6
     }
     const C *src = xc;
     C *dst = A;
+    if (rl.lg_n >= 0) {
+        int lg_ns = 0;
+        for (int p = 0; p <= last; ++p) {
+            const int R = rl.r[p];
+            C *out = (p == last) ? xc : dst;
+            if (active)
+                for (int j = tid; j < (n >> (R == 4 ? 2 : 1)); j += tpr)
+                    butterfly_p2<C>(src, out, rl.lg_n, R, lg_ns, W, j);
+            __syncthreads();
+            src = dst;
+            dst = (dst == A) ? B : A;
+            lg_ns += R == 4 ? 2 : 1;
+        }
+        return;
+    }
     int Ns = 1;
     for (int p = 0; p <= last; ++p) {
         const int R = rl.r[p];
@@ -157,10 +210,15 @@ static int fft_run_t(const FftPlan &p, C *a, C *b, int n_ch, int64_t dist, const
         RadixList rl{};
         rl.n_pass = (int)p.radix.size();
         int most = 1;  // the most butterflies of any pass
+        bool p2 = true;
         for (int q = 0; q < rl.n_pass; ++q) {
             rl.r[q] = p.radix[q];
             most = std::max(most, (int)(p.n / p.radix[q]));
+            p2 = p2 && (p.radix[q] == 2 || p.radix[q] == 4);
         }
+        int lg = 0;
+        while ((int64_t(1) << lg) < p.n) ++lg;
+        rl.lg_n = p2 ? lg : -1;
         // sequences per block: as many as leave every thread a butterfly in
         // the widest pass, within the block's shared memory
         int rpb = 1;

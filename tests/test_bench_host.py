@@ -48,7 +48,7 @@ def test_issue_bound_arithmetic():
         152 * 2070e6 * 128 / 13 / 1e9)
     # an XU-heavy pair is held by the 32-lane XU pipe, not by issue
     assert bench.issue_bound_gpair(1, 1000.0, 1.0, 10.0) == pytest.approx(1000e6 * 32 / 10 / 1e9)
-    # the roofline peak quoted for the forward operator on the spiral workload
+    # the scalar-issue bound of the forward operator's tier mix on the spiral workload
     f32, xu = bench.mixed_ops("k_forward", 0.9772)
     assert bench.issue_bound_gpair(152, 2070.0, f32, xu) == pytest.approx(3055.1, rel=1e-4)
 
@@ -133,8 +133,14 @@ def test_roofline_bases():
     instruction count at the issue rate."""
     rates = {"fma": 128.0, "rsqrt": 16.0, "ex2": 16.0, "rcp": 16.0}
     b = bench.roofline_bases("k_adjoint", 1.0, 152, 2070.0, rates, 2000.0, executed=12.5)
-    # all pairs asymptotic: 9 FP32 + 1 XU -> issue bound 128 / 10 per SM per clock
-    assert b["tier_weighted"]["peak"] == pytest.approx(152 * 2070e6 * 12.8 / 1e9)
+    # all pairs asymptotic: 9 FP32 + 1 XU, issued as 4.5 packed + 1 -> the
+    # FP32 lanes bind: 128 / 9 pairs per SM per clock
+    assert b["tier_weighted"]["peak"] == pytest.approx(152 * 2070e6 * 128 / 9 / 1e9)
+    assert bench.packed_issue("k_adjoint", 1.0) == pytest.approx(5.5)
+    assert bench.packed_issue("k_adjoint", 0.0) == pytest.approx(20.0)
+    # a faster packed-FMA rate raises the lane bound
+    b2 = bench.roofline_bases("k_adjoint", 1.0, 152, 2070.0, dict(rates, fma=120.0, fma2=126.0), None)
+    assert b2["tier_weighted"]["peak"] == pytest.approx(152 * 2070e6 * 126 / 9 / 1e9)
     assert b["plain_closed_form"]["peak"] == pytest.approx(152 * 2070e6 * 5.12 / 1e9)
     assert b["executed"]["peak"] == pytest.approx(152 * 2070e6 * 128 / 12.5 / 1e9)
     assert b["tier_weighted"]["frac"] == pytest.approx(2000.0 / b["tier_weighted"]["peak"])
