@@ -306,33 +306,33 @@ __device__ __forceinline__ double lap3_at(const double *__restrict__ f, int64_t 
     return f[k + xm] + f[k + xp] + f[k + ym] + f[k + yp] + f[k + zm] + f[k + zp] - 6.0 * f[k];
 }
 
-// out_m = Lap x_m for the nc components.
+// out_m = Lap x_m for the nc components (SCALE: w Lap x_m).
+template <bool SCALE>
 __global__ void k_lap3(int nx, int ny, int nz, int nc, bool scaled, double3 c, const double *__restrict__ x,
-                       double *__restrict__ out)
+                       double *__restrict__ out, double w)
 {
     // nc N < 2^31 (grids of fewer than 2^27 nodes): 32-bit index arithmetic
     const int N = nx * ny * nz;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * N; e += gridDim.x * blockDim.x) {
         const int m = e / N, k = e - m * N;
         const int i = k % nx, j = (k / nx) % ny, l = k / (nx * ny);
-        out[e] = lap3_at(x + (int64_t)m * N, k, i, j, l, nx, ny, nz, scaled, c);
+        const double L = lap3_at(x + (int64_t)m * N, k, i, j, l, nx, ny, nz, scaled, c);
+        out[e] = SCALE ? w * L : L;
     }
 }
 
 // One Core Stage step's operator after the transpose's cell sums, one
-// thread per node and all its components m: y = scale * node_combine3,
-// q = y + gamma (Lap l1) with l1 = Lap p, written to q, and the partial sums
-// of <p, q> over blocks of kQThreads3 consecutive nodes, finished into alpha
-// by the last block.  (Small blocks: a 48 x 48 x 24 grid still spreads over
-// about three blocks per SM, so the FP64 pipes that bound this kernel stay
-// evenly loaded.)
+// thread per node and all its components m: q = scale * node_combine3 + l2
+// with l2 = gamma Lap Lap p (formed on the side stream), written to q, and
+// the partial sums of <p, q> over blocks of kQThreads3 consecutive nodes,
+// finished into alpha by the last block.  (Small blocks: a 48 x 48 x 24
+// grid still spreads over about three blocks per SM.)
 constexpr int kQThreads3 = 128;
 template <typename R, int NC>
 __global__ void __launch_bounds__(kQThreads3)
 k_grid3_q(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restrict__ cunit_off,
-          const V2<R> *__restrict__ cell_part, double scale, bool scaled, double3 c, double gamma,
-          const double *__restrict__ l1, const double *__restrict__ p, double *__restrict__ q,
-          double *__restrict__ pq_part, CsScal *sc)
+          const V2<R> *__restrict__ cell_part, double scale, const double *__restrict__ l2,
+          const double *__restrict__ p, double *__restrict__ q, double *__restrict__ pq_part, CsScal *sc)
 {
     __shared__ double sh[kQThreads3 / 32];
     __shared__ bool last;
@@ -346,8 +346,7 @@ k_grid3_q(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restri
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
             const int64_t e = (int64_t)m * N + node;
-            const double y = sum[m].value() * scale;
-            const double qe = y + gamma * lap3_at(l1 + (int64_t)m * N, node, i, j, l, nx, ny, nz, scaled, c);
+            const double qe = fma(sum[m].value(), scale, l2[e]);
             q[e] = qe;
             acc += p[e] * qe;
         }
@@ -546,10 +545,10 @@ int launch_interp3_T(const G3 &g, int64_t T, const R *s_sorted, const Bins3 &b, 
 }
 
 // The 3-D Core Stage operator: (1/T) M^T M through the binned records and
-// the 7-point Laplacian of each component.  A step: l1 = Lap p on the side
-// stream while the main chain runs M p (through the FP32 copy of p on the
-// FP32 path) and the transpose's unit and cell sums; then one pass forms q
-// and the <p, q> partials (k_grid3_q).
+// the 7-point Laplacian of each component.  A step: l2 = gamma Lap Lap p on
+// the side stream (two FP64-bound passes) while the main chain runs M p
+// (through the FP32 copy of p on the FP32 path) and the transpose's unit
+// and cell sums; then one pass forms q and the <p, q> partials (k_grid3_q).
 template <typename R>
 struct GridOp3 final : CoreStageOp {
     const G3 &g;
@@ -574,12 +573,15 @@ struct GridOp3 final : CoreStageOp {
         return P32{};
     }
     int pq_blocks(int64_t) const override { return (int)((g.n() + kQThreads3 - 1) / kQThreads3); }
-    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1,
+    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1, double *l2,
                const StepFork &fk, cudaStream_t st) override
     {
+        const int lb = grid_blocks(nc * g.n());
         MPI_TRY_CUDA(cudaEventRecord(fk.fork, st));
         MPI_TRY_CUDA(cudaStreamWaitEvent(fk.side, fk.fork, 0));
-        k_lap3<<<grid_blocks(nc * g.n()), 256, 0, fk.side>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), p, l1);
+        k_lap3<false><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), p, l1, 1.0);
+        MPI_CHECK_LAUNCH();
+        k_lap3<true><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), l1, l2, gamma);
         MPI_CHECK_LAUNCH();
         MPI_TRY_CUDA(cudaEventRecord(fk.join, fk.side));
         const InterpRec3<R> *rec = static_cast<const InterpRec3<R> *>(bins.rec);
@@ -595,12 +597,10 @@ struct GridOp3 final : CoreStageOp {
         const V2<R> *cpart = static_cast<const V2<R> *>(bins.cell_part);
         if (ch < 0)
             k_grid3_q<R, 9><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,
-                                                          bins.cunit_off, cpart, invT, scaled, lap_coef(), gamma,
-                                                          l1, p, q, pq_part, sc);
+                                                          bins.cunit_off, cpart, invT, l2, p, q, pq_part, sc);
         else
             k_grid3_q<R, 3><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,
-                                                          bins.cunit_off, cpart, invT, scaled, lap_coef(), gamma,
-                                                          l1, p, q, pq_part, sc);
+                                                          bins.cunit_off, cpart, invT, l2, p, q, pq_part, sc);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }

@@ -158,10 +158,10 @@ struct CoreStageOp {
     virtual P32 p32() const { return P32{}; }
     // q = (1/T) M^T M p + gamma Lap Lap p and the partial sums of <p, q> in
     // pq_blocks(nv) fixed blocks, finished by the producing kernel with
-    // cs_finish_pq on sc.  l1: an FP64 work vector of nv values.
+    // cs_finish_pq on sc.  l1, l2: FP64 work vectors of nv values.
     virtual int pq_blocks(int64_t nv) const = 0;
     virtual int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1,
-                       const StepFork &fk, cudaStream_t st) = 0;
+                       double *l2, const StepFork &fk, cudaStream_t st) = 0;
 };
 
 // CG from x = 0 on ((1/T) M^T M + gamma Lap Lap) x = b (Eq. first:step; Lap is

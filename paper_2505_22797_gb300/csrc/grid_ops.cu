@@ -510,28 +510,31 @@ __device__ __forceinline__ double lap2_at(const double *__restrict__ f, int k, i
     return f[j * nx + im] + f[j * nx + ip] + f[jm * nx + i] + f[jp * nx + i] - 4.0 * f[k];
 }
 
-// out_m = Lap x_m for the nc components.
+// out_m = Lap x_m for the nc components (SCALE: w Lap x_m).
+template <bool SCALE>
 __global__ void k_lap(int nx, int ny, int nc, bool scaled, double cx, double cy, const double *__restrict__ x,
-                      double *__restrict__ out)
+                      double *__restrict__ out, double w)
 {
     const int N = nx * ny;  // nc N < 2^31 (grids of at most 2^28 nodes)
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * N; e += gridDim.x * blockDim.x) {
         const int m = e / N, k = e - m * N;
-        out[e] = lap2_at(x + (int64_t)m * N, k, k % nx, k / nx, nx, ny, scaled, cx, cy);
+        const double L = lap2_at(x + (int64_t)m * N, k, k % nx, k / nx, nx, ny, scaled, cx, cy);
+        out[e] = SCALE ? w * L : L;
     }
 }
 
 // One 2-D Core Stage step after the transpose's unit sums, one thread per
-// node and all its components m: y = scale * (the node's combine, as
-// k_interp_T_cell_combine forms it), q = y + gamma (Lap l1) with l1 = Lap p,
-// written to q, and the partial sums of <p, q> over blocks of kQThreads
-// consecutive nodes, finished into alpha by the last block.
+// node and all its components m: q = scale * (the node's combine, as
+// k_interp_T_cell_combine forms it) + l2 with l2 = gamma Lap Lap p (formed
+// on the side stream), written to q, and the partial sums of <p, q> over
+// blocks of kQThreads consecutive nodes, finished into alpha by the last
+// block.
 constexpr int kQThreads = 256;
 template <typename R, int NC>
 __global__ void __launch_bounds__(kQThreads)
 k_grid_q(int nx, int ny, int ncx, int ncy, const int *__restrict__ cunit_off, const R *__restrict__ unit_part,
-         double scale, bool scaled, double cx, double cy, double gamma, const double *__restrict__ l1,
-         const double *__restrict__ p, double *__restrict__ q, double *__restrict__ pq_part, CsScal *sc)
+         double scale, const double *__restrict__ l2, const double *__restrict__ p, double *__restrict__ q,
+         double *__restrict__ pq_part, CsScal *sc)
 {
     __shared__ double sh[kQThreads / 32];
     __shared__ bool last;
@@ -555,8 +558,7 @@ k_grid_q(int nx, int ny, int ncx, int ncy, const int *__restrict__ cunit_off, co
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
             const int64_t e = (int64_t)m * N + node;
-            const double y = sum[m].value() * scale;
-            const double qe = y + gamma * lap2_at(l1 + (int64_t)m * N, node, i, j, nx, ny, scaled, cx, cy);
+            const double qe = fma(sum[m].value(), scale, l2[e]);
             q[e] = qe;
             acc += p[e] * qe;
         }
@@ -779,10 +781,10 @@ __global__ void k_grid_output(int64_t N, int ch, const double *__restrict__ x, R
 }
 
 // The 2-D Core Stage operator: (1/T) M^T M through the binned records and
-// the 5-point Laplacian of each component.  A step: l1 = Lap p on the side
-// stream while the main chain runs M p (through the FP32 copy of p on the
-// FP32 path) and the transpose's unit sums; then one pass forms q and the
-// <p, q> partials (k_grid_q).
+// the 5-point Laplacian of each component.  A step: l2 = gamma Lap Lap p on
+// the side stream (two FP64-bound passes) while the main chain runs M p
+// (through the FP32 copy of p on the FP32 path) and the transpose's unit
+// sums; then one pass forms q and the <p, q> partials (k_grid_q).
 template <typename R>
 struct GridOp2 final : CoreStageOp {
     const GridH &g;
@@ -803,13 +805,16 @@ struct GridOp2 final : CoreStageOp {
         return P32{};
     }
     int pq_blocks(int64_t) const override { return (int)((int64_t(g.nx) * g.ny + kQThreads - 1) / kQThreads); }
-    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1,
+    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1, double *l2,
                const StepFork &fk, cudaStream_t st) override
     {
         const double cx = 1.0 / (g.dx * g.dx), cy = 1.0 / (g.dy * g.dy);
+        const int lb = grid_blocks(int64_t(nc) * g.nx * g.ny);
         MPI_TRY_CUDA(cudaEventRecord(fk.fork, st));
         MPI_TRY_CUDA(cudaStreamWaitEvent(fk.side, fk.fork, 0));
-        k_lap<<<grid_blocks(int64_t(nc) * g.nx * g.ny), 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, p, l1);
+        k_lap<false><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, p, l1, 1.0);
+        MPI_CHECK_LAUNCH();
+        k_lap<true><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, l1, l2, gamma);
         MPI_CHECK_LAUNCH();
         MPI_TRY_CUDA(cudaEventRecord(fk.join, fk.side));
         const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(bins.rec);
@@ -822,10 +827,10 @@ struct GridOp2 final : CoreStageOp {
         const R *part = static_cast<const R *>(bins.unit_part);
         if (ch < 0)
             k_grid_q<R, 4><<<blocks, kQThreads, 0, st>>>(g.nx, g.ny, bins.ncx, bins.ncy, bins.cunit_off, part, invT,
-                                                        scaled, cx, cy, gamma, l1, p, q, pq_part, sc);
+                                                        l2, p, q, pq_part, sc);
         else
             k_grid_q<R, 2><<<blocks, kQThreads, 0, st>>>(g.nx, g.ny, bins.ncx, bins.ncy, bins.cunit_off, part, invT,
-                                                        scaled, cx, cy, gamma, l1, p, q, pq_part, sc);
+                                                        l2, p, q, pq_part, sc);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }
@@ -944,12 +949,13 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
     const P32 p32 = op.p32();
     Scratch scr(st);
     const size_t vb = sizeof(double) * nv;
-    const size_t o_r = scr.reserve(vb), o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_l1 = scr.reserve(vb);
+    const size_t o_r = scr.reserve(vb), o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_l1 = scr.reserve(vb),
+                 o_l2 = scr.reserve(vb);
     const size_t o_pq = scr.reserve(sizeof(double) * npq), o_rr = scr.reserve(sizeof(double) * ncs);
     const size_t o_sc = scr.reserve(sizeof(CsScal));
     MPI_TRY(scr.allocate());
     double *rr = scr.at<double>(o_r), *p = scr.at<double>(o_p), *q = scr.at<double>(o_q),
-           *l1 = scr.at<double>(o_l1);
+           *l1 = scr.at<double>(o_l1), *l2 = scr.at<double>(o_l2);
     double *pq_part = scr.at<double>(o_pq), *rr_part = scr.at<double>(o_rr);
     CsScal *sc = scr.at<CsScal>(o_sc);
 
@@ -991,7 +997,7 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
     // the stop), then the update and beta, then the new direction (and its
     // FP32 copy).
     auto enqueue_step = [&](int, cudaStream_t s) -> int {
-        MPI_TRY(op.step_q(p, o.gamma, q, pq_part, sc, l1, fk.f, s));
+        MPI_TRY(op.step_q(p, o.gamma, q, pq_part, sc, l1, l2, fk.f, s));
         k_cs_step1<<<ncs, kCsThreads, 0, s>>>(nv, x, rr, p, q, rr_part, sc);
         MPI_CHECK_LAUNCH();
         return cs_step2_launch(p32, nv, rr, p, sc, s);
