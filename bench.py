@@ -893,7 +893,8 @@ def measure_transfer(api, syn, dev, stream, s_model):
 # 3-D pairs: "far" 25 FP32 + 3 XU (3 differences, 3 for |y|^2, 10 for a, d,
 # 9 for the dot products and accumulation); "vfar" replaces the 10 + 3 XU of
 # a, d by 4 + 1 XU; the adjoint's vfar pair term is nested in 1/z (one
-# operation fewer).
+# operation fewer).  As in 2-D, the FP32 kernels issue the vfar tier's FP32
+# operations packed two per instruction.
 ALG_OPS_3D = {"k_forward3": {"far": (25, 3), "vfar": (19, 1)},
               "k_adjoint3": {"far": (25, 3), "vfar": (18, 1)}}
 
@@ -947,11 +948,15 @@ def measure_ffp3d(api, syn, dev, stream, sm_count, sm_max):
         ms = tot / max(n, 1)
         (a32, axu), (b32, bxu) = ALG_OPS_3D[name]["far"], ALG_OPS_3D[name]["vfar"]
         n_fp32, n_xu = (1 - f_vfar) * a32 + f_vfar * b32, (1 - f_vfar) * axu + f_vfar * bxu
-        peak = issue_bound_gpair(sm_count, sm_max, n_fp32, n_xu)
+        issue = (1 - f_vfar) * (a32 + axu) + f_vfar * (b32 / 2.0 + bxu)
+        xu_clk = (1 - f_vfar) * (2.0 / 16 + 1.0 / 32) + f_vfar / 16
+        peak = sm_count * sm_max * 1e6 / max(issue / ISSUE_PER_CLK, n_fp32 / 126.0, xu_clk) / 1e9
         rate = N * T / (ms * 1e-3) / 1e9
         out[name] = {"avg_launch_ms": ms, "gpair_per_s": rate, "peak": peak, "frac": rate / peak,
-                     "peak_basis": (f"issue bound, {n_fp32:.2f} FP32 + {n_xu:.3f} XU algorithmic ops per "
-                                    f"pair ({f_vfar:.4f} of the pairs in the asymptotic regime)")}
+                     "peak_basis": (f"pipe bound: {n_fp32:.2f} FP32 + {n_xu:.3f} XU algorithmic ops per pair "
+                                    f"({f_vfar:.4f} of the pairs in the asymptotic regime, its FP32 issued "
+                                    f"packed: {issue:.2f} instructions per pair), FP32 lanes 126, rsqrt and rcp "
+                                    f"16, ex2 32 per SM per clock, issue 128")}
     gen = torch.Generator(device="cpu").manual_seed(5)
     fro = 0.0
     for _ in range(4):

@@ -220,6 +220,62 @@ __device__ __forceinline__ void lang3(R u, R &f1, R &f2)
     else lang_checked<R, DBETA>(u, f1, f2);
 }
 
+// The asymptotic pass in packed two-lane FP32 arithmetic (f32x2, sm_100 and
+// later), samples (2h, 2h + 1) of the thread in the two lanes: the same FP32
+// work from half the issue slots (the pass is issue-bound in scalar form).
+#ifndef MPI_FWD3_PACK
+#define MPI_FWD3_PACK 1
+#endif
+__device__ __forceinline__ void fwd3_pass_vfar_packed(const V4<float> *sv, int cnt, const float (&Rx)[k3FwdS],
+                                                      const float (&Ry)[k3FwdS], const float (&Rz)[k3FwdS],
+                                                      const float (&Wx)[k3FwdS], const float (&Wy)[k3FwdS],
+                                                      const float (&Wz)[k3FwdS], float (&sa)[k3FwdS],
+                                                      float (&Sx)[k3FwdS], float (&Sy)[k3FwdS],
+                                                      float (&Sz)[k3FwdS])
+{
+    constexpr int H = k3FwdS / 2;
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    float2 nRx[H], nRy[H], nRz[H], Wx2[H], Wy2[H], Wz2[H], sa2[H], Sx2[H], Sy2[H], Sz2[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        nRx[h] = make_float2(-Rx[2 * h], -Rx[2 * h + 1]);
+        nRy[h] = make_float2(-Ry[2 * h], -Ry[2 * h + 1]);
+        nRz[h] = make_float2(-Rz[2 * h], -Rz[2 * h + 1]);
+        Wx2[h] = make_float2(Wx[2 * h], Wx[2 * h + 1]);
+        Wy2[h] = make_float2(Wy[2 * h], Wy[2 * h + 1]);
+        Wz2[h] = make_float2(Wz[2 * h], Wz[2 * h + 1]);
+        sa2[h] = Sx2[h] = Sy2[h] = Sz2[h] = make_float2(0.0f, 0.0f);
+    }
+#pragma unroll 2
+    for (int e = 0; e < cnt; ++e) {
+        const V4<float> P = sv[e];
+        const float2 Px = make_float2(P.x, P.x), Py = make_float2(P.y, P.y), Pz = make_float2(P.z, P.z);
+        const float2 Pw = make_float2(P.w, P.w);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const float2 yx = __fadd2_rn(Px, nRx[h]), yy = __fadd2_rn(Py, nRy[h]), yz = __fadd2_rn(Pz, nRz[h]);
+            const float2 u = __ffma2_rn(yz, yz, __ffma2_rn(yy, yy, __fmul2_rn(yx, yx)));
+            const float2 iz = make_float2(Lang<float>::iz_vfar(u.x), Lang<float>::iz_vfar(u.y));
+            const float2 iz2 = __fmul2_rn(iz, iz);
+            const float2 a = __ffma2_rn(iz2, m1, iz);                  // iz - iz^2
+            const float2 d = __fmul2_rn(__ffma2_rn(a, m1, iz2), iz2);  // (2 iz^2 - iz) iz^2
+            const float2 yW = __ffma2_rn(yz, Wz2[h], __ffma2_rn(yy, Wy2[h], __fmul2_rn(yx, Wx2[h])));
+            const float2 t = __fmul2_rn(__fmul2_rn(Pw, d), yW);
+            Sx2[h] = __ffma2_rn(t, yx, Sx2[h]);
+            Sy2[h] = __ffma2_rn(t, yy, Sy2[h]);
+            Sz2[h] = __ffma2_rn(t, yz, Sz2[h]);
+            sa2[h] = __ffma2_rn(Pw, a, sa2[h]);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        sa[2 * h] += sa2[h].x; sa[2 * h + 1] += sa2[h].y;
+        Sx[2 * h] += Sx2[h].x; Sx[2 * h + 1] += Sx2[h].y;
+        Sy[2 * h] += Sy2[h].x; Sy[2 * h + 1] += Sy2[h].y;
+        Sz[2 * h] += Sz2[h].x; Sz[2 * h + 1] += Sz2[h].y;
+    }
+}
+
 template <typename R, int MODE>
 __device__ __forceinline__ void fwd3_pass(const V4<R> *sv, int cnt, const R (&Rx)[k3FwdS],
                                           const R (&Ry)[k3FwdS], const R (&Rz)[k3FwdS],
@@ -227,6 +283,10 @@ __device__ __forceinline__ void fwd3_pass(const V4<R> *sv, int cnt, const R (&Rx
                                           const R (&Wz)[k3FwdS], R (&sa)[k3FwdS], R (&Sx)[k3FwdS],
                                           R (&Sy)[k3FwdS], R (&Sz)[k3FwdS])
 {
+    if constexpr (MODE == 2 && sizeof(R) == 4 && MPI_FWD3_PACK && k3FwdS % 2 == 0) {
+        fwd3_pass_vfar_packed(sv, cnt, Rx, Ry, Rz, Wx, Wy, Wz, sa, Sx, Sy, Sz);
+        return;
+    }
 #pragma unroll 2
     for (int e = 0; e < cnt; ++e) {
         const V4<R> P = sv[e];
@@ -340,11 +400,55 @@ __device__ __forceinline__ void adj3_pass(const V4<R> *sR, const V4<R> *sW, cons
     }
 }
 
+// The asymptotic pass in packed two-lane FP32 arithmetic, staged samples
+// (2h, 2h + 1) in the two lanes (the pass is issue-bound in scalar form).
+// pk: the staged samples as pairs, five float4 per pair h:
+//   (-Qx, -Qy), (-Qz, Wx), (Wy, Wz), (uW, Ux), (Uy, Uz)   (each entry: even, odd sample).
+#ifndef MPI_ADJ3_PACK
+#define MPI_ADJ3_PACK 1
+#endif
+__device__ __forceinline__ void adj3_pass_vfar_packed(const float4 *pk, int npair, const float (&Px)[k3AdjV],
+                                                      const float (&Py)[k3AdjV], const float (&Pz)[k3AdjV],
+                                                      float (&acc)[k3AdjV])
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f), two = make_float2(2.0f, 2.0f);
+    float2 acc2[k3AdjV];
+#pragma unroll
+    for (int m = 0; m < k3AdjV; ++m) acc2[m] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int h = 0; h < npair; ++h) {
+        const float4 A = pk[5 * h], B = pk[5 * h + 1], C = pk[5 * h + 2], D = pk[5 * h + 3], E = pk[5 * h + 4];
+        const float2 nQx = make_float2(A.x, A.y), nQy = make_float2(A.z, A.w), nQz = make_float2(B.x, B.y);
+        const float2 Wx = make_float2(B.z, B.w), Wy = make_float2(C.x, C.y), Wz = make_float2(C.z, C.w);
+        const float2 uW = make_float2(D.x, D.y), Ux = make_float2(D.z, D.w);
+        const float2 Uy = make_float2(E.x, E.y), Uz = make_float2(E.z, E.w);
+        const float2 nuW = __fmul2_rn(uW, m1);
+#pragma unroll
+        for (int m = 0; m < k3AdjV; ++m) {
+            const float2 yx = __fadd2_rn(make_float2(Px[m], Px[m]), nQx);
+            const float2 yy = __fadd2_rn(make_float2(Py[m], Py[m]), nQy);
+            const float2 yz = __fadd2_rn(make_float2(Pz[m], Pz[m]), nQz);
+            const float2 u = __ffma2_rn(yz, yz, __ffma2_rn(yy, yy, __fmul2_rn(yx, yx)));
+            const float2 yU = __ffma2_rn(yz, Uz, __ffma2_rn(yy, Uy, __fmul2_rn(yx, Ux)));
+            const float2 yW = __ffma2_rn(yz, Wz, __ffma2_rn(yy, Wy, __fmul2_rn(yx, Wx)));
+            const float2 P = __fmul2_rn(yU, yW);
+            const float2 iz = make_float2(Lang<float>::iz_vfar(u.x), Lang<float>::iz_vfar(u.y));
+            // iz (uW + iz (iz (2 iz - 1) P - uW)), as pair_acc_vfar
+            const float2 w = __ffma2_rn(iz, __fmul2_rn(P, __ffma2_rn(iz, two, m1)), nuW);
+            acc2[m] = __ffma2_rn(iz, __ffma2_rn(iz, w, uW), acc2[m]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < k3AdjV; ++m) acc[m] += acc2[m].x + acc2[m].y;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(k3Threads, sizeof(R) == 4 ? MPI_ADJ3_MINB : 2)
 k_adjoint3(const __grid_constant__ Adj3Args<R> a)
 {
+    constexpr bool PACK = sizeof(R) == 4 && MPI_ADJ3_PACK;
     __shared__ V4<R> sR[k3Batch], sW[k3Batch], sU[k3Batch];
+    __shared__ float4 sPk[PACK ? 5 * (k3Batch / 2) : 1];
     const int vt = (int)(blockIdx.x % a.n_vt);
     const int64_t chunk = blockIdx.x / a.n_vt;
     const int64_t vbase = (int64_t)vt * k3AdjTile;
@@ -376,16 +480,31 @@ k_adjoint3(const __grid_constant__ Adj3Args<R> a)
                 uy = fmx(sk, a.p[3 * k + 1], uy);
                 uz = fmx(sk, a.p[3 * k + 2], uz);
             }
+            const R uW = fmx(uz, W.z, fmx(uy, W.y, ux * W.x));
             sR[e] = Q;
-            sW[e] = V4<R>{W.x, W.y, W.z, fmx(uz, W.z, fmx(uy, W.y, ux * W.x))};
+            sW[e] = V4<R>{W.x, W.y, W.z, uW};
             sU[e] = V4<R>{ux, uy, uz, R(0)};
+            if constexpr (PACK) {
+                float *pb = reinterpret_cast<float *>(sPk + 5 * (e >> 1)) + (e & 1);
+                const float v[10] = {-float(Q.x), -float(Q.y), -float(Q.z), float(W.x), float(W.y),
+                                     float(W.z), float(uW), float(ux), float(uy), float(uz)};
+#pragma unroll
+                for (int j = 0; j < 10; ++j) pb[2 * j] = v[j];
+                if ((e & 1) == 0 && e + 1 == cnt) {
+                    // odd count: the pair's second sample contributes nothing
+                    // (W and U zero) at the first one's position (u > 0)
+#pragma unroll
+                    for (int j = 0; j < 10; ++j) pb[2 * j + 1] = j < 3 ? v[j] : 0.0f;
+                }
+            }
         }
         __syncthreads();
         const int64_t sb = tb / k3Batch;
         const R gap2 = box_gap2(vlo, vhi, a.sbox[2 * sb], a.sbox[2 * sb + 1]);
-        if (gap2 >= vfar_threshold<R, false>())
-            adj3_pass<R, 2>(sR, sW, sU, cnt, Px, Py, Pz, acc);
-        else if (far_field(gap2))
+        if (gap2 >= vfar_threshold<R, false>()) {
+            if constexpr (PACK) adj3_pass_vfar_packed(sPk, (cnt + 1) / 2, Px, Py, Pz, acc);
+            else adj3_pass<R, 2>(sR, sW, sU, cnt, Px, Py, Pz, acc);
+        } else if (far_field(gap2))
             adj3_pass<R, 1>(sR, sW, sU, cnt, Px, Py, Pz, acc);
         else
             adj3_pass<R, 0>(sR, sW, sU, cnt, Px, Py, Pz, acc);
