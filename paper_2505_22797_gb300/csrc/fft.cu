@@ -220,9 +220,16 @@ static int fft_run_t(const FftPlan &p, C *a, C *b, int n_ch, int64_t dist, const
         while ((int64_t(1) << lg) < p.n) ++lg;
         rl.lg_n = p2 ? lg : -1;
         // sequences per block: as many as leave every thread a butterfly in
-        // the widest pass, within the block's shared memory
+        // the widest pass, within the block's shared memory -- and more (a
+        // thread then takes several butterflies per pass) while the blocks
+        // would not all be resident at once: a 1024 x 1024 transform's 1024
+        // one-row blocks exceeded the ~6 resident per SM by 112, which ran
+        // alone as a second wave for a third of the launch.
+        const int wave = device_sm_count() * 6;
         int rpb = 1;
-        while (rpb * 2 * most <= kFftThreads && size_t(rpb) * 2 * smem <= 48 * 1024 && rpb * 2 <= n_ch) rpb *= 2;
+        while (size_t(rpb) * 2 * smem <= 48 * 1024 && rpb * 2 <= n_ch && rpb * 2 <= kFftThreads / 32 &&
+               (rpb * 2 * most <= kFftThreads || (n_ch + rpb - 1) / rpb > wave))
+            rpb *= 2;
         const size_t smem_blk = smem * size_t(rpb);
         if (smem_blk > 48 * 1024)  // opt in above the default limit (set on the current device)
             MPI_TRY_CUDA(cudaFuncSetAttribute(k_fft_smem<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_blk));
