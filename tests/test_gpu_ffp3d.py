@@ -56,6 +56,21 @@ def test_forward3_far_trajectory(orc):
     assert rel_l2(host(got), orc.adjoint3(m, g, r, v, y)) <= tol(dt)
 
 
+@pytest.mark.parametrize("T", [257, 901])
+def test_adjoint3_asymptotic_odd_batches(orc, T):
+    """A trajectory far above the volume: every staged pass takes the packed
+    asymptotic form, and an odd sample count leaves the last staged pair with
+    one real sample (its partner carries zero weight)."""
+    dt = torch.float32
+    m, g, r, v, c = _case(dict(nx=12, ny=10, nz=6, T=T), dt)
+    r = r + np.array([0.0, 0.0, 400.0])
+    s = api.mpi_forward3(m, g, dev(r, dt), dev(v, dt), dev(c, dt))
+    assert rel_l2(host(s), orc.forward3(m, g, r, v, c)) <= tol(dt)
+    y = rounded(np.random.default_rng(5).normal(size=s.shape), dt)
+    got = api.mpi_adjoint3(m, g, dev(r, dt), dev(v, dt), dev(y, dt))
+    assert rel_l2(host(got), orc.adjoint3(m, g, r, v, y)) <= tol(dt)
+
+
 def test_empty_trajectory3():
     g = syn.box_grid3(4, 3, 2)
     m = syn.default_model3()

@@ -50,6 +50,26 @@ def test_forward_adjoint_small(orc, dt, case):
     assert rel_l2(got_g, want_g) <= tol(dt)
 
 
+@pytest.mark.parametrize("shift", [60.0, 0.6])
+def test_packed_asymptotic_tiers(orc, shift):
+    """FP32 on a ragged grid with the trajectory moved sideways: far (every
+    pair in the packed asymptotic tiers of the forward row loop and the
+    adjoint's sample groups, the last group partial) and near the grid's edge
+    (asymptotic, closed-form and mixed segments and groups side by side)."""
+    dt = torch.float32
+    cfg = _case(37, 29, 1001, "spiral", seed=11)
+    m, g = cfg["model"], cfg["grid"]
+    r = rounded(cfg["r"] + np.array([shift * 12.0, 0.0]), dt)
+    v, c = (rounded(cfg[k], dt) for k in ("v", "c"))
+    want = orc.forward(m, g, r, v, c)
+    got = host(api.mpi_forward(m, g, dev(r, dt), dev(v, dt), dev(c, dt)))
+    assert rel_l2(got, want) <= tol(dt)
+    s = rounded(np.random.default_rng(8).normal(size=want.shape), dt)
+    want_g = orc.adjoint(m, g, r, v, s)
+    got_g = host(api.mpi_adjoint(m, g, dev(r, dt), dev(v, dt), dev(s, dt)))
+    assert rel_l2(got_g, want_g) <= tol(dt)
+
+
 @pytest.mark.parametrize("dt", DTYPES)
 def test_dbeta_small(orc, dt):
     cfg = _case(41, 23, 1500, "spiral")
