@@ -354,6 +354,16 @@ def _inst_per_pair(kernel):
     return ent.get("inst_per_pair") if ent else None
 
 
+def _pipe_util(kernel):
+    """FP32 (FMA) and XU pipe utilisation of `kernel` (percent, ncu) from the
+    committed summary, if it was captured on the current kernel sources."""
+    ent = _profile_entry(kernel)
+    if not ent or "fma_pipe_active_pct" not in ent:
+        return None
+    return {"fma_pipe_active_pct": ent["fma_pipe_active_pct"], "xu_pipe_inst_pct": ent.get("xu_pipe_inst_pct"),
+            "source": "profiles/traffic.json (ncu --set full, one launch)"}
+
+
 def _traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was captured on the current kernel sources; else None."""
@@ -1172,7 +1182,8 @@ def run_ours(args):
         ach = (N * T) / (ms_l / n_l * 1e-3) / 1e9 if n_l else None
         kern[name] = {"avg_launch_ms": ms_l / n_l if n_l else None, "launches": n_l, "achieved": ach,
                       "bases": roofline_bases(name, f_vfar, sm_count, sm_run, rates, ach,
-                                              _inst_per_pair(name))}
+                                              _inst_per_pair(name)),
+                      "pipe_utilisation": _pipe_util(name)}
     dom = "k_forward" if fms >= ams else "k_adjoint"
     kd = kern[dom]
     tw = kd["bases"]["tier_weighted"]
