@@ -89,6 +89,27 @@ __device__ double block_select(const double *__restrict__ x, int64_t N, int64_t 
     return key_f64(prefix);
 }
 
+// Minimum over the block (order-independent), returned to every thread.
+template <int NT>
+__device__ __forceinline__ double block_min(double v, double *sh /* >= NT/32 + 1 */)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();  // sh may still be read by an earlier reduction
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = sh[0];
+        for (int w = 1; w < NT / 32; ++w) m = fmin(m, sh[w]);
+        sh[NT / 32] = m;
+    }
+    __syncthreads();
+    const double r = sh[NT / 32];
+    __syncthreads();
+    return r;
+}
+
 // One block computes, for the N values x: the clip value P (the pct-th
 // percentile, linear interpolation between order statistics; -inf when
 // do_clip is 0), rho1 = max(x, P) rounded to R, the population variance of
@@ -111,7 +132,26 @@ __device__ void outer_stats_block(int64_t N, const double *__restrict__ x, int d
         const int64_t lo = (int64_t)floor(h);
         const int64_t hi = min(lo + 1, N - 1);
         const double xlo = block_select<kStatThreads>(x, N, lo, hist, sh_u);
-        const double xhi = (hi == lo) ? xlo : block_select<kStatThreads>(x, N, hi, hist, sh_u);
+        // The next order statistic in one pass instead of a second select:
+        // x(lo + 1) is xlo itself when more than lo + 1 values are <= xlo,
+        // else the smallest value above xlo (exact, order-independent).
+        double xhi = xlo;
+        if (hi != lo) {
+            int64_t le = 0;
+            double gt = INFINITY;
+            for (int64_t i = threadIdx.x; i < N; i += kStatThreads) {
+                const double v = x[i];
+                if (v <= xlo) ++le;
+                else gt = fmin(gt, v);
+            }
+            le = block_sum<int64_t, kStatThreads>(le, reinterpret_cast<int64_t *>(sh));
+            if (threadIdx.x == 0) sh_u[0] = (unsigned long long)le;
+            __syncthreads();
+            le = (int64_t)sh_u[0];
+            __syncthreads();
+            gt = block_min<kStatThreads>(gt, sh);
+            xhi = le > hi ? xlo : gt;
+        }
         P = xlo + (h - double(lo)) * (xhi - xlo);
     }
     double s = 0.0;
