@@ -284,15 +284,17 @@ __global__ void k_interp3_T_cell_combine(int nx, int ny, int nz, int ncx, int nc
         SumAcc<R> sum[NC] = {};
         node_combine3<R, NC>(i, j, l, ncx, ncy, ncz, cunit_off, cell_part, sum);
 #pragma unroll
-        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(sum[m].value() * scale);
+        for (int m = 0; m < NC; ++m) cs_store(A[(int64_t)m * N + node], sum[m].value() * scale);
     }
 }
 
 // (Lap f)(node k at i, j, l): 7-point, replicated boundary (a missing
 // neighbour is the node itself), FP64.  scaled: per-axis second differences
 // with 1/dx^2, 1/dy^2, 1/dz^2 (c); else the plain stencil.
+template <typename E> struct Coef3 { E x, y, z; };
+
 __device__ __forceinline__ double lap3_at(const double *__restrict__ f, int64_t k, int i, int j, int l, int nx,
-                                          int ny, int nz, bool scaled, double3 c)
+                                          int ny, int nz, bool scaled, Coef3<double> c)
 {
     const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
     const int64_t xm = i > 0 ? -sx : 0, xp = i < nx - 1 ? sx : 0;
@@ -305,19 +307,37 @@ __device__ __forceinline__ double lap3_at(const double *__restrict__ f, int64_t 
     }
     return f[k + xm] + f[k + xp] + f[k + ym] + f[k + yp] + f[k + zm] + f[k + zp] - 6.0 * f[k];
 }
+// The same in double-float arithmetic (coefficients as double-float pairs).
+__device__ __forceinline__ df lap3_at(const df *__restrict__ f, int64_t k, int i, int j, int l, int nx, int ny,
+                                      int nz, bool scaled, Coef3<df> c)
+{
+    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+    const int64_t xm = i > 0 ? -sx : 0, xp = i < nx - 1 ? sx : 0;
+    const int64_t ym = j > 0 ? -sy : 0, yp = j < ny - 1 ? sy : 0;
+    const int64_t zm = l > 0 ? -sz : 0, zp = l < nz - 1 ? sz : 0;
+    const df c0 = f[k];
+    const df ax = df_add(f[k + xm], f[k + xp]), ay = df_add(f[k + ym], f[k + yp]), az = df_add(f[k + zm], f[k + zp]);
+    if (scaled) {
+        const df m2 = make_float2(-2.0f, 0.0f);
+        return df_add(df_add(df_mul(df_axpy(ax, m2, c0), c.x), df_mul(df_axpy(ay, m2, c0), c.y)),
+                      df_mul(df_axpy(az, m2, c0), c.z));
+    }
+    return df_axpy(df_add(df_add(ax, ay), az), make_float2(-6.0f, 0.0f), c0);
+}
 
-// out_m = Lap x_m for the nc components (SCALE: w Lap x_m).
-template <bool SCALE>
-__global__ void k_lap3(int nx, int ny, int nz, int nc, bool scaled, double3 c, const double *__restrict__ x,
-                       double *__restrict__ out, double w)
+// out_m = Lap x_m for the nc components (SCALE: w Lap x_m); E: FP64 or
+// double-float elements (and scalars).
+template <typename E, bool SCALE>
+__global__ void k_lap3(int nx, int ny, int nz, int nc, bool scaled, Coef3<E> c, const E *__restrict__ x,
+                       E *__restrict__ out, E w)
 {
     // nc N < 2^31 (grids of fewer than 2^27 nodes): 32-bit index arithmetic
     const int N = nx * ny * nz;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * N; e += gridDim.x * blockDim.x) {
         const int m = e / N, k = e - m * N;
         const int i = k % nx, j = (k / nx) % ny, l = k / (nx * ny);
-        const double L = lap3_at(x + (int64_t)m * N, k, i, j, l, nx, ny, nz, scaled, c);
-        out[e] = SCALE ? w * L : L;
+        const E L = lap3_at(x + (int64_t)m * N, k, i, j, l, nx, ny, nz, scaled, c);
+        out[e] = SCALE ? cs_scale(L, w) : L;
     }
 }
 
@@ -328,17 +348,17 @@ __global__ void k_lap3(int nx, int ny, int nz, int nc, bool scaled, double3 c, c
 // finished into alpha by the last block.  (Small blocks: a 48 x 48 x 24
 // grid still spreads over about three blocks per SM.)
 constexpr int kQThreads3 = 128;
-template <typename R, int NC>
+template <typename R, int NC, typename E>
 __global__ void __launch_bounds__(kQThreads3)
 k_grid3_q(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restrict__ cunit_off,
-          const V2<R> *__restrict__ cell_part, double scale, const double *__restrict__ l2,
-          const double *__restrict__ p, double *__restrict__ q, double *__restrict__ pq_part, CsScal *sc)
+          const V2<R> *__restrict__ cell_part, E scale, const E *__restrict__ l2, const E *__restrict__ p,
+          E *__restrict__ q, double *__restrict__ pq_part, CsScal *sc)
 {
     __shared__ double sh[kQThreads3 / 32];
     __shared__ bool last;
     const int N = nx * ny * nz;  // < 2^27
     const int node = blockIdx.x * kQThreads3 + threadIdx.x;
-    double acc = 0.0;
+    CsDot<E> acc{};
     if (node < N) {
         const int i = node % nx, j = (node / nx) % ny, l = node / (nx * ny);
         SumAcc<R> sum[NC] = {};
@@ -346,27 +366,27 @@ k_grid3_q(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restri
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
             const int64_t e = (int64_t)m * N + node;
-            const double qe = fma(sum[m].value(), scale, l2[e]);
+            const E qe = cs_sum_scale_add(sum[m], scale, l2[e]);
             q[e] = qe;
-            acc += p[e] * qe;
+            acc.add(p[e], qe);
         }
     }
-    acc = block_sum<double, kQThreads3>(acc, sh);
-    if (threadIdx.x == 0) pq_part[blockIdx.x] = acc;
+    const double tot = block_sum<double, kQThreads3>(acc.value(), sh);
+    if (threadIdx.x == 0) pq_part[blockIdx.x] = tot;
     cs_finish_pq<kQThreads3>(pq_part, gridDim.x, sc, sh, &last);
 }
 
 // Ahat and its trace (all channels: A_00 + A_11 + A_22; channel k: A_kk,
 // component k of the stored row (A_k0, A_k1, A_k2)).
-template <typename R>
-__global__ void k_grid3_output(int64_t N, int ch, const double *__restrict__ x, R *__restrict__ A,
-                               R *__restrict__ tr)
+template <typename R, typename E>
+__global__ void k_grid3_output(int64_t N, int ch, const E *__restrict__ x, R *__restrict__ A, R *__restrict__ tr)
 {
     const int nc = ch < 0 ? 9 : 3;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
          e += (int64_t)gridDim.x * blockDim.x) {
-        for (int m = 0; m < nc; ++m) A[m * N + e] = R(x[m * N + e]);
-        tr[e] = ch < 0 ? R(x[e] + x[4 * N + e] + x[8 * N + e]) : R(x[ch * N + e]);
+        for (int m = 0; m < nc; ++m) A[m * N + e] = R(cs_to_double(x[m * N + e]));
+        tr[e] = ch < 0 ? R(cs_to_double(cs_add(cs_add(x[e], x[4 * N + e]), x[8 * N + e])))
+                       : R(cs_to_double(x[ch * N + e]));
     }
 }
 
@@ -550,7 +570,8 @@ int launch_interp3_T(const G3 &g, int64_t T, const R *s_sorted, const Bins3 &b, 
 // (through the FP32 copy of p on the FP32 path) and the transpose's unit
 // and cell sums; then one pass forms q and the <p, q> partials (k_grid3_q).
 template <typename R>
-struct GridOp3 final : CoreStageOp {
+struct GridOp3 final : CoreStageOp<typename CsElem<R>::type> {
+    using E = typename CsElem<R>::type;
     const G3 &g;
     int64_t T;
     int ch, nc;
@@ -562,9 +583,11 @@ struct GridOp3 final : CoreStageOp {
     GridOp3(const G3 &g_, int64_t T_, int ch_, const Bins3 &b_, R *s_tmp_, float4 *p_il_, bool scaled_)
         : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 9 : 3), bins(b_), s_tmp(s_tmp_), p_il(p_il_),
           invT(T_ > 0 ? 1.0 / double(T_) : 0.0), scaled(scaled_) {}
-    double3 lap_coef() const
+    Coef3<E> lap_coef() const
     {
-        return make_double3(1.0 / (g.dx * g.dx), 1.0 / (g.dy * g.dy), 1.0 / (g.dz * g.dz));
+        E *tag = nullptr;
+        return Coef3<E>{cs_host_scalar(1.0 / (g.dx * g.dx), tag), cs_host_scalar(1.0 / (g.dy * g.dy), tag),
+                        cs_host_scalar(1.0 / (g.dz * g.dz), tag)};
     }
     P32 p32() const override
     {
@@ -573,15 +596,18 @@ struct GridOp3 final : CoreStageOp {
         return P32{};
     }
     int pq_blocks(int64_t) const override { return (int)((g.n() + kQThreads3 - 1) / kQThreads3); }
-    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1, double *l2,
-               const StepFork &fk, cudaStream_t st) override
+    int step_q(const E *p, double gamma, E *q, double *pq_part, CsScal *sc, E *l1, E *l2, const StepFork &fk,
+               cudaStream_t st) override
     {
+        E *tag = nullptr;
         const int lb = grid_blocks(nc * g.n());
         MPI_TRY_CUDA(cudaEventRecord(fk.fork, st));
         MPI_TRY_CUDA(cudaStreamWaitEvent(fk.side, fk.fork, 0));
-        k_lap3<false><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), p, l1, 1.0);
+        k_lap3<E, false><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), p, l1,
+                                                 cs_host_scalar(1.0, tag));
         MPI_CHECK_LAUNCH();
-        k_lap3<true><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), l1, l2, gamma);
+        k_lap3<E, true><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, g.nz, nc, scaled, lap_coef(), l1, l2,
+                                                cs_host_scalar(gamma, tag));
         MPI_CHECK_LAUNCH();
         MPI_TRY_CUDA(cudaEventRecord(fk.join, fk.side));
         const InterpRec3<R> *rec = static_cast<const InterpRec3<R> *>(bins.rec);
@@ -590,17 +616,19 @@ struct GridOp3 final : CoreStageOp {
             MPI_TRY((launch_interp3<R, float>(g, T, nullptr, vs, reinterpret_cast<const float *>(p_il), s_tmp, st,
                                               ch, rec, true)));
         else
-            MPI_TRY((launch_interp3<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
+            MPI_TRY((launch_interp3<R, double>(g, T, nullptr, vs, reinterpret_cast<const double *>(p), s_tmp, st,
+                                               ch, rec)));
         MPI_TRY(launch_interp3_T_units<R>(T, s_tmp, bins, st, ch));
         MPI_TRY_CUDA(cudaStreamWaitEvent(st, fk.join, 0));
         const unsigned blocks = (unsigned)pq_blocks(0);
         const V2<R> *cpart = static_cast<const V2<R> *>(bins.cell_part);
+        const E sc_T = cs_host_scalar(invT, tag);
         if (ch < 0)
-            k_grid3_q<R, 9><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,
-                                                          bins.cunit_off, cpart, invT, l2, p, q, pq_part, sc);
+            k_grid3_q<R, 9, E><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,
+                                                             bins.cunit_off, cpart, sc_T, l2, p, q, pq_part, sc);
         else
-            k_grid3_q<R, 3><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,
-                                                          bins.cunit_off, cpart, invT, l2, p, q, pq_part, sc);
+            k_grid3_q<R, 3, E><<<blocks, kQThreads3, 0, st>>>(g.nx, g.ny, g.nz, bins.ncx, bins.ncy, bins.ncz,
+                                                             bins.cunit_off, cpart, sc_T, l2, p, q, pq_part, sc);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }
@@ -621,12 +649,13 @@ int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid
     const size_t o_bins = scr.reserve(bins3_bytes<R>(T, g));
     const size_t o_s = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_sd = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
-    const size_t o_b = scr.reserve(sizeof(double) * nv), o_x = scr.reserve(sizeof(double) * nv);
+    using E = typename CsElem<R>::type;
+    const size_t o_b = scr.reserve(sizeof(E) * nv), o_x = scr.reserve(sizeof(E) * nv);
     const size_t o_pr = scr.reserve(sizeof(R) == 4 ? sizeof(float4) * rows * N : 0);
     MPI_TRY(scr.allocate());
     Bins3 bins = bins3_carve<R>(scr.at<char>(o_bins), T, g);
     R *s_data = scr.at<R>(o_sd);
-    double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x);
+    E *b = scr.at<E>(o_b), *x = scr.at<E>(o_x);
 
     MPI_TRY(build_bins3<R>(g, T, r, v, bins, st));
     MPI_TRY(gather_rows<R>(T, rows, bins.list, s, s_data, st));
@@ -644,9 +673,9 @@ int grid3_impl(const G3 &g, const mpi_traj *tr, const void *s_in, const mpi_grid
         bins.n_units = n_units;
     }
     GridOp3<R> op(g, T, ch, bins, scr.at<R>(o_s), scr.at<float4>(o_pr), o.lap_scaled != 0);
-    MPI_TRY((launch_interp3_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
-    MPI_TRY(core_stage_cg(op, nv, b, o, x, n_iter_out, st));
-    k_grid3_output<R><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
+    MPI_TRY((launch_interp3_T<R, E>(g, T, s_data, bins, b, op.invT, st, ch)));
+    MPI_TRY(core_stage_cg<E>(op, nv, b, o, x, n_iter_out, st));
+    k_grid3_output<R, E><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }

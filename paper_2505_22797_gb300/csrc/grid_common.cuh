@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "pnp_ops.cuh"
 
 namespace mpi {
@@ -74,6 +75,7 @@ int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st)
 struct CsScal {
     double rr;            // r.r of the current residual
     double alpha, beta;   // the step's coefficients
+    float2 alpha_df, beta_df;  // the same as double-float pairs (double-float vectors)
     double bnorm, tol;    // ||b|| and the stop threshold on ||r|| (< 0: none)
     unsigned cnt[4];      // arrival counters of the reductions (zero between launches)
     int done;             // set once the solve has stopped
@@ -122,11 +124,86 @@ __device__ __forceinline__ void cs_finish_pq(const double *pq_part, int n, CsSca
     const double pq = cs_sum_parts<NT>(pq_part, n, sh);
     if (threadIdx.x == 0) {
         const double rr = sc->rr;
-        if (sc->done != 0 || rr == 0.0 || pq == 0.0 || (sc->tol >= 0.0 && sqrt(rr) <= sc->tol)) sc->done = 1;
-        else sc->alpha = rr / pq;
+        if (sc->done != 0 || rr == 0.0 || pq == 0.0 || (sc->tol >= 0.0 && sqrt(rr) <= sc->tol)) {
+            sc->done = 1;
+        } else {
+            sc->alpha = rr / pq;
+            sc->alpha_df = df_from_double(sc->alpha);
+        }
     }
 }
+
+// Element arithmetic of the CG vectors: FP64, or double-float pairs (the
+// FP32 path).  Scalars enter as FP64 or as double-float pairs.
+__device__ __forceinline__ double cs_add(double a, double b) { return a + b; }
+__device__ __forceinline__ df cs_add(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ double cs_axpy(double x, double a, double y) { return x + a * y; }  // x + a y
+__device__ __forceinline__ df cs_axpy(df x, df a, df y) { return df_axpy(x, a, y); }
+__device__ __forceinline__ double cs_scale(double x, double a) { return a * x; }
+__device__ __forceinline__ df cs_scale(df x, df a) { return df_mul(x, a); }
+template <typename E> __device__ __forceinline__ E cs_zero();
+template <> __device__ __forceinline__ double cs_zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ df cs_zero<df>() { return make_float2(0.0f, 0.0f); }
+__device__ __forceinline__ double cs_neg(double a) { return -a; }
+__device__ __forceinline__ df cs_neg(df a) { return df_neg(a); }
+// The step's alpha / beta as the element type's scalar operand.
+template <typename E> __device__ __forceinline__ E cs_alpha(const CsScal *sc);
+template <> __device__ __forceinline__ double cs_alpha<double>(const CsScal *sc) { return sc->alpha; }
+template <> __device__ __forceinline__ df cs_alpha<df>(const CsScal *sc) { return sc->alpha_df; }
+template <typename E> __device__ __forceinline__ E cs_beta(const CsScal *sc);
+template <> __device__ __forceinline__ double cs_beta<double>(const CsScal *sc) { return sc->beta; }
+template <> __device__ __forceinline__ df cs_beta<df>(const CsScal *sc) { return sc->beta_df; }
+// Per-thread accumulator of an inner product of element vectors.
+template <typename E> struct CsDot;
+template <> struct CsDot<double> {
+    double s;
+    __device__ __forceinline__ void add(double a, double b) { s += a * b; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct CsDot<df> {
+    F2Sum s;
+    __device__ __forceinline__ void add(df a, df b) { df_dot_add(s, a, b); }
+    __device__ __forceinline__ double value() const { return s.value(); }
+};
+// An element as FP64 / from FP64 (right-hand sides and outputs).
+__device__ __forceinline__ double cs_to_double(double a) { return a; }
+__device__ __forceinline__ double cs_to_double(df a) { return df_to_double(a); }
+template <typename E> __device__ __forceinline__ E cs_from_double(double v);
+template <> __device__ __forceinline__ double cs_from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ df cs_from_double<df>(double v) { return df_from_double(v); }
+// scale * s + add for a transpose sum s: FP64, or as a double-float pair
+// (the error-free FP32 pair of the sum, scaled and added without rounding
+// to FP64).
+template <typename R>
+__device__ __forceinline__ double cs_sum_scale_add(const SumAcc<R> &s, double scale, double add)
+{
+    return fma(s.value(), scale, add);
+}
+__device__ __forceinline__ df cs_sum_scale_add(const SumAcc<float> &s, df scale, df add)
+{
+    return df_add(df_mul(make_float2(s.s.hi, s.s.lo), scale), add);
+}
+// Stores an FP64 value as FP32, FP64 or a double-float pair.
+__device__ __forceinline__ void cs_store(float &d, double v) { d = float(v); }
+__device__ __forceinline__ void cs_store(double &d, double v) { d = v; }
+__device__ __forceinline__ void cs_store(float2 &d, double v) { d = df_from_double(v); }
+// An element rounded to FP32 (the operator's FP32 copy; outputs).
+__device__ __forceinline__ float cs_to_float(double a) { return float(a); }
+__device__ __forceinline__ float cs_to_float(df a) { return __fadd_rn(a.x, a.y); }
 #endif
+
+// The CG element type of a Core Stage in precision R: FP64 vectors for the
+// FP64 path, double-float pairs for the FP32 path.
+template <typename R> struct CsElem { using type = double; };
+template <> struct CsElem<float> { using type = float2; };
+
+// A host FP64 scalar as the element type's scalar operand.
+inline double cs_host_scalar(double a, double *) { return a; }
+inline float2 cs_host_scalar(double a, float2 *)
+{
+    const float hi = float(a);
+    return float2{hi, float(a - double(hi))};
+}
 
 // Layouts of the FP32 copy of the CG direction an operator reads (FP32
 // path), for N nodes: kP32Node4 / kP32Node2: a node's 4 / 2 components as one
@@ -148,8 +225,10 @@ struct StepFork {
     cudaEvent_t fork, join;
 };
 
-// The operator of one Core Stage solve on nv FP64 unknowns (all components
-// of all nodes).  Its methods only enqueue.
+// The operator of one Core Stage solve on nv unknowns (all components of all
+// nodes) of element type E: FP64, or double-float pairs on the FP32 path.
+// Its methods only enqueue.
+template <typename E>
 struct CoreStageOp {
     virtual ~CoreStageOp() = default;
     // The FP32 copy of p the operator reads (buf null: it reads p in FP64).
@@ -158,19 +237,21 @@ struct CoreStageOp {
     virtual P32 p32() const { return P32{}; }
     // q = (1/T) M^T M p + gamma Lap Lap p and the partial sums of <p, q> in
     // pq_blocks(nv) fixed blocks, finished by the producing kernel with
-    // cs_finish_pq on sc.  l1, l2: FP64 work vectors of nv values.
+    // cs_finish_pq on sc.  l1, l2: work vectors of nv values.
     virtual int pq_blocks(int64_t nv) const = 0;
-    virtual int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1,
-                       double *l2, const StepFork &fk, cudaStream_t st) = 0;
+    virtual int step_q(const E *p, double gamma, E *q, double *pq_part, CsScal *sc, E *l1, E *l2,
+                       const StepFork &fk, cudaStream_t st) = 0;
 };
 
 // CG from x = 0 on ((1/T) M^T M + gamma Lap Lap) x = b (Eq. first:step; Lap is
 // symmetric, so Lap^T Lap = Lap Lap) with opts' gamma, iteration limit and
-// relative tolerance; writes x (nv FP64 values).  With a tolerance the host
-// polls the device stop flag every 16 steps.  With n_iter_out (host) the
-// stream is synchronised and the number of CG updates stored.
-int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_opts &o, double *x,
-                  int *n_iter_out, cudaStream_t st);
+// relative tolerance; writes x (nv values of type E: double, or float2
+// double-float pairs).  With a tolerance the host polls the device stop flag
+// every 16 steps.  With n_iter_out (host) the stream is synchronised and the
+// number of CG updates stored.
+template <typename E>
+int core_stage_cg(CoreStageOp<E> &op, int64_t nv, const E *b, const mpi_grid_opts &o, E *x, int *n_iter_out,
+                  cudaStream_t st);
 
 // rec[q] = rec_t[list[q]] and vs[q] = v[list[q]] (D velocity components):
 // the records and velocities of the samples in list (cell) order.

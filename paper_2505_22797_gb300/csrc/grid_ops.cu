@@ -313,7 +313,7 @@ __global__ void k_interp_T_cell_combine(int nx, int ny, int ncx, int ncy, const 
             }
         }
 #pragma unroll
-        for (int m = 0; m < NC; ++m) A[(int64_t)m * N + node] = OUT(acc[m].value() * scale);
+        for (int m = 0; m < NC; ++m) cs_store(A[(int64_t)m * N + node], acc[m].value() * scale);
     }
 }
 
@@ -509,17 +509,32 @@ __device__ __forceinline__ double lap2_at(const double *__restrict__ f, int k, i
     }
     return f[j * nx + im] + f[j * nx + ip] + f[jm * nx + i] + f[jp * nx + i] - 4.0 * f[k];
 }
+// The same in double-float arithmetic (cx, cy as double-float pairs).
+__device__ __forceinline__ df lap2_at(const df *__restrict__ f, int k, int i, int j, int nx, int ny, bool scaled,
+                                      df cx, df cy)
+{
+    const int im = i > 0 ? i - 1 : 0, ip = i < nx - 1 ? i + 1 : nx - 1;
+    const int jm = j > 0 ? j - 1 : 0, jp = j < ny - 1 ? j + 1 : ny - 1;
+    const df c0 = f[k];
+    const df sx = df_add(f[j * nx + im], f[j * nx + ip]), sy = df_add(f[jm * nx + i], f[jp * nx + i]);
+    if (scaled) {
+        const df m2 = make_float2(-2.0f, 0.0f);
+        return df_add(df_mul(df_axpy(sx, m2, c0), cx), df_mul(df_axpy(sy, m2, c0), cy));
+    }
+    return df_axpy(df_add(sx, sy), make_float2(-4.0f, 0.0f), c0);
+}
 
-// out_m = Lap x_m for the nc components (SCALE: w Lap x_m).
-template <bool SCALE>
-__global__ void k_lap(int nx, int ny, int nc, bool scaled, double cx, double cy, const double *__restrict__ x,
-                      double *__restrict__ out, double w)
+// out_m = Lap x_m for the nc components (SCALE: w Lap x_m); E: FP64 or
+// double-float elements (and scalars).
+template <typename E, bool SCALE>
+__global__ void k_lap(int nx, int ny, int nc, bool scaled, E cx, E cy, const E *__restrict__ x, E *__restrict__ out,
+                      E w)
 {
     const int N = nx * ny;  // nc N < 2^31 (grids of at most 2^28 nodes)
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * N; e += gridDim.x * blockDim.x) {
         const int m = e / N, k = e - m * N;
-        const double L = lap2_at(x + (int64_t)m * N, k, k % nx, k / nx, nx, ny, scaled, cx, cy);
-        out[e] = SCALE ? w * L : L;
+        const E L = lap2_at(x + (int64_t)m * N, k, k % nx, k / nx, nx, ny, scaled, cx, cy);
+        out[e] = SCALE ? cs_scale(L, w) : L;
     }
 }
 
@@ -530,17 +545,17 @@ __global__ void k_lap(int nx, int ny, int nc, bool scaled, double cx, double cy,
 // blocks of kQThreads consecutive nodes, finished into alpha by the last
 // block.
 constexpr int kQThreads = 256;
-template <typename R, int NC>
+template <typename R, int NC, typename E>
 __global__ void __launch_bounds__(kQThreads)
 k_grid_q(int nx, int ny, int ncx, int ncy, const int *__restrict__ cunit_off, const R *__restrict__ unit_part,
-         double scale, const double *__restrict__ l2, const double *__restrict__ p, double *__restrict__ q,
-         double *__restrict__ pq_part, CsScal *sc)
+         E scale, const E *__restrict__ l2, const E *__restrict__ p, E *__restrict__ q, double *__restrict__ pq_part,
+         CsScal *sc)
 {
     __shared__ double sh[kQThreads / 32];
     __shared__ bool last;
     const int N = nx * ny;  // <= 2^28
     const int node = blockIdx.x * kQThreads + threadIdx.x;
-    double acc = 0.0;
+    CsDot<E> acc{};
     if (node < N) {
         const int i = node % nx, j = node / nx;
         SumAcc<R> sum[NC] = {};
@@ -558,13 +573,13 @@ k_grid_q(int nx, int ny, int ncx, int ncy, const int *__restrict__ cunit_off, co
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
             const int64_t e = (int64_t)m * N + node;
-            const double qe = fma(sum[m].value(), scale, l2[e]);
+            const E qe = cs_sum_scale_add(sum[m], scale, l2[e]);
             q[e] = qe;
-            acc += p[e] * qe;
+            acc.add(p[e], qe);
         }
     }
-    acc = block_sum<double, kQThreads>(acc, sh);
-    if (threadIdx.x == 0) pq_part[blockIdx.x] = acc;
+    const double tot = block_sum<double, kQThreads>(acc.value(), sh);
+    if (threadIdx.x == 0) pq_part[blockIdx.x] = tot;
     cs_finish_pq<kQThreads>(pq_part, gridDim.x, sc, sh, &last);
 }
 
@@ -576,26 +591,28 @@ constexpr int kCsThreads = 256, kCsPer = 2048;
 inline int cs_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kCsPer - 1) / kCsPer); }
 
 // r = b, p = b (x = 0), r.r, ||b|| and the stop threshold rel_tol ||b||.
+// E: the element type of the vectors (double, or double-float pairs).
+template <typename E>
 __global__ void __launch_bounds__(kCsThreads)
-k_cs_init(int64_t n, const double *__restrict__ b, double *__restrict__ r, double *__restrict__ p,
-          double *__restrict__ rr_part, double rel_tol, CsScal *sc)
+k_cs_init(int64_t n, const E *__restrict__ b, E *__restrict__ r, E *__restrict__ p, double *__restrict__ rr_part,
+          double rel_tol, CsScal *sc)
 {
     __shared__ double sh[kCsThreads / 32];
     __shared__ bool last;
     const int64_t e0 = (int64_t)blockIdx.x * kCsPer;
-    double acc = 0.0;
+    CsDot<E> acc{};
 #pragma unroll
     for (int u = 0; u < kCsPer / kCsThreads; ++u) {
         const int64_t e = e0 + u * kCsThreads + threadIdx.x;
         if (e < n) {
-            const double be = b[e];
+            const E be = b[e];
             r[e] = be;
             p[e] = be;
-            acc += be * be;
+            acc.add(be, be);
         }
     }
-    acc = block_sum<double, kCsThreads>(acc, sh);
-    if (threadIdx.x == 0) rr_part[blockIdx.x] = acc;
+    const double tot = block_sum<double, kCsThreads>(acc.value(), sh);
+    if (threadIdx.x == 0) rr_part[blockIdx.x] = tot;
     if (!cs_last_block(&sc->cnt[kCntInit], &last)) return;
     const double rr = cs_sum_parts<kCsThreads>(rr_part, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -609,9 +626,10 @@ k_cs_init(int64_t n, const double *__restrict__ b, double *__restrict__ r, doubl
 
 // x += alpha p, r -= alpha q, the new r.r and beta = r.r(new) / r.r(old);
 // counts the update.  Nothing once the solve has stopped.
+template <typename E>
 __global__ void __launch_bounds__(kCsThreads)
-k_cs_step1(int64_t n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-           const double *__restrict__ q, double *__restrict__ rr_part, CsScal *sc)
+k_cs_step1(int64_t n, E *__restrict__ x, E *__restrict__ r, const E *__restrict__ p, const E *__restrict__ q,
+           double *__restrict__ rr_part, CsScal *sc)
 {
     __shared__ double sh[kCsThreads / 32];
     __shared__ bool last;
@@ -619,51 +637,53 @@ k_cs_step1(int64_t n, double *__restrict__ x, double *__restrict__ r, const doub
     const int64_t e0 = (int64_t)blockIdx.x * kCsPer + threadIdx.x;
     // the vectors are loaded before the stop flag is read: the flag comes
     // from the previous kernel and would otherwise add a round trip
-    double xv[U], pv[U], rv[U], qv[U];
+    E xv[U], pv[U], rv[U], qv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int64_t e = e0 + u * kCsThreads;
         const bool in = e < n;
-        xv[u] = in ? x[e] : 0.0;
-        pv[u] = in ? p[e] : 0.0;
-        rv[u] = in ? r[e] : 0.0;
-        qv[u] = in ? q[e] : 0.0;
+        xv[u] = in ? x[e] : cs_zero<E>();
+        pv[u] = in ? p[e] : cs_zero<E>();
+        rv[u] = in ? r[e] : cs_zero<E>();
+        qv[u] = in ? q[e] : cs_zero<E>();
     }
     if (sc->done) return;
-    const double alpha = sc->alpha;
-    double acc = 0.0;
+    const E alpha = cs_alpha<E>(sc), nalpha = cs_neg(alpha);
+    CsDot<E> acc{};
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int64_t e = e0 + u * kCsThreads;
         if (e < n) {
-            x[e] = xv[u] + alpha * pv[u];
-            const double re = rv[u] - alpha * qv[u];
+            x[e] = cs_axpy(xv[u], alpha, pv[u]);
+            const E re = cs_axpy(rv[u], nalpha, qv[u]);
             r[e] = re;
-            acc += re * re;
+            acc.add(re, re);
         }
     }
-    acc = block_sum<double, kCsThreads>(acc, sh);
-    if (threadIdx.x == 0) rr_part[blockIdx.x] = acc;
+    const double tot = block_sum<double, kCsThreads>(acc.value(), sh);
+    if (threadIdx.x == 0) rr_part[blockIdx.x] = tot;
     if (!cs_last_block(&sc->cnt[kCntRr], &last)) return;
     const double rr = cs_sum_parts<kCsThreads>(rr_part, gridDim.x, sh);
     if (threadIdx.x == 0) {
         sc->beta = rr / sc->rr;
+        sc->beta_df = df_from_double(sc->beta);
         sc->rr = rr;
         sc->iters += 1;
     }
 }
 
 // p = r + beta p.
+template <typename E>
 __global__ void __launch_bounds__(kCsThreads)
-k_cs_step2(int64_t n, const double *__restrict__ r, double *__restrict__ p, const CsScal *sc)
+k_cs_step2(int64_t n, const E *__restrict__ r, E *__restrict__ p, const CsScal *sc)
 {
     if (sc->done) return;
-    const double beta = sc->beta;
+    const E beta = cs_beta<E>(sc);
     const int64_t e0 = (int64_t)blockIdx.x * kCsPer;
 #pragma unroll
     for (int u = 0; u < kCsPer / kCsThreads; ++u) {
         const int64_t e = e0 + u * kCsThreads + threadIdx.x;
-        if (e < n) p[e] = r[e] + beta * p[e];
+        if (e < n) p[e] = cs_axpy(r[e], beta, p[e]);
     }
 }
 
@@ -693,73 +713,80 @@ __device__ __forceinline__ void p32_store(float *buf, int64_t node, const float 
 }
 
 // buf = p rounded to FP32 (one thread per node, all its components).
-template <int L>
-__global__ void __launch_bounds__(kCsThreads) k_cs_round(int64_t N, const double *__restrict__ p, float *buf)
+template <typename E, int L>
+__global__ void __launch_bounds__(kCsThreads) k_cs_round(int64_t N, const E *__restrict__ p, float *buf)
 {
     constexpr int NC = p32_nc<L>();
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < N;
          node += (int64_t)gridDim.x * blockDim.x) {
         float v[NC];
 #pragma unroll
-        for (int m = 0; m < NC; ++m) v[m] = float(p[m * N + node]);
+        for (int m = 0; m < NC; ++m) v[m] = cs_to_float(p[m * N + node]);
         p32_store<L>(buf, node, v);
     }
 }
 
 // p = r + beta p and its FP32 copy (one thread per node, all its components).
-template <int L>
+template <typename E, int L>
 __global__ void __launch_bounds__(kCsThreads)
-k_cs_step2_p32(int64_t N, const double *__restrict__ r, double *__restrict__ p, const CsScal *sc, float *buf)
+k_cs_step2_p32(int64_t N, const E *__restrict__ r, E *__restrict__ p, const CsScal *sc, float *buf)
 {
     constexpr int NC = p32_nc<L>();
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < N;
          node += (int64_t)gridDim.x * blockDim.x) {
-        double rv[NC], pv[NC];
+        E rv[NC], pv[NC];
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
             rv[m] = r[m * N + node];
             pv[m] = p[m * N + node];
         }
         if (sc->done) return;  // (read after the vector loads are issued)
-        const double beta = sc->beta;
+        const E beta = cs_beta<E>(sc);
         float v[NC];
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
-            const double pe = rv[m] + beta * pv[m];
+            const E pe = cs_axpy(rv[m], beta, pv[m]);
             p[m * N + node] = pe;
-            v[m] = float(pe);
+            v[m] = cs_to_float(pe);
         }
         p32_store<L>(buf, node, v);
     }
 }
 
-static int cs_round_launch(const P32 &d, const double *p, cudaStream_t st)
+template <typename E>
+static int cs_round_launch(const P32 &d, const E *p, cudaStream_t st)
 {
     const int blocks = grid_blocks(d.N);
     switch (d.layout) {
-        case kP32Node4: k_cs_round<kP32Node4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
-        case kP32Node2: k_cs_round<kP32Node2><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
-        case kP32Rows3x4: k_cs_round<kP32Rows3x4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
-        default: k_cs_round<kP32Rows1x4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
+        case kP32Node4: k_cs_round<E, kP32Node4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
+        case kP32Node2: k_cs_round<E, kP32Node2><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
+        case kP32Rows3x4: k_cs_round<E, kP32Rows3x4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
+        default: k_cs_round<E, kP32Rows1x4><<<blocks, kCsThreads, 0, st>>>(d.N, p, d.buf); break;
     }
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
 
-static int cs_step2_launch(const P32 &d, int64_t nv, const double *r, double *p, const CsScal *sc,
-                           cudaStream_t st)
+template <typename E>
+static int cs_step2_launch(const P32 &d, int64_t nv, const E *r, E *p, const CsScal *sc, cudaStream_t st)
 {
     if (!d.buf) {
-        k_cs_step2<<<cs_blocks(nv), kCsThreads, 0, st>>>(nv, r, p, sc);
+        k_cs_step2<E><<<cs_blocks(nv), kCsThreads, 0, st>>>(nv, r, p, sc);
     } else {
         const int blocks = grid_blocks(d.N);
         switch (d.layout) {
-            case kP32Node4: k_cs_step2_p32<kP32Node4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf); break;
-            case kP32Node2: k_cs_step2_p32<kP32Node2><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf); break;
-            case kP32Rows3x4:
-                k_cs_step2_p32<kP32Rows3x4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf);
+            case kP32Node4:
+                k_cs_step2_p32<E, kP32Node4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf);
                 break;
-            default: k_cs_step2_p32<kP32Rows1x4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf); break;
+            case kP32Node2:
+                k_cs_step2_p32<E, kP32Node2><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf);
+                break;
+            case kP32Rows3x4:
+                k_cs_step2_p32<E, kP32Rows3x4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf);
+                break;
+            default:
+                k_cs_step2_p32<E, kP32Rows1x4><<<blocks, kCsThreads, 0, st>>>(d.N, r, p, sc, d.buf);
+                break;
         }
     }
     MPI_CHECK_LAUNCH();
@@ -768,25 +795,27 @@ static int cs_step2_launch(const P32 &d, int64_t nv, const double *r, double *p,
 
 // Ahat and its trace (both channels: A_00 + A_11; one channel k: A_kk,
 // which is component k of the stored pair (A_k0, A_k1)).
-template <typename R>
-__global__ void k_grid_output(int64_t N, int ch, const double *__restrict__ x, R *__restrict__ A,
+template <typename R, typename E>
+__global__ void k_grid_output(int64_t N, int ch, const E *__restrict__ x, R *__restrict__ A,
                               R *__restrict__ tr)
 {
     const int nc = ch < 0 ? 4 : 2;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
          e += (int64_t)gridDim.x * blockDim.x) {
-        for (int m = 0; m < nc; ++m) A[m * N + e] = R(x[m * N + e]);
-        tr[e] = ch < 0 ? R(x[e] + x[3 * N + e]) : R(x[ch * N + e]);
+        for (int m = 0; m < nc; ++m) A[m * N + e] = R(cs_to_double(x[m * N + e]));
+        tr[e] = ch < 0 ? R(cs_to_double(cs_add(x[e], x[3 * N + e]))) : R(cs_to_double(x[ch * N + e]));
     }
 }
 
 // The 2-D Core Stage operator: (1/T) M^T M through the binned records and
 // the 5-point Laplacian of each component.  A step: l2 = gamma Lap Lap p on
-// the side stream (two FP64-bound passes) while the main chain runs M p
-// (through the FP32 copy of p on the FP32 path) and the transpose's unit
-// sums; then one pass forms q and the <p, q> partials (k_grid_q).
+// the side stream (two passes) while the main chain runs M p (through the
+// FP32 copy of p on the FP32 path) and the transpose's unit sums; then one
+// pass forms q and the <p, q> partials (k_grid_q).  The CG vectors are FP64
+// (FP64 path) or double-float pairs (FP32 path: E = float2).
 template <typename R>
-struct GridOp2 final : CoreStageOp {
+struct GridOp2 final : CoreStageOp<typename CsElem<R>::type> {
+    using E = typename CsElem<R>::type;
     const GridH &g;
     int64_t T;
     int ch, nc;
@@ -805,32 +834,35 @@ struct GridOp2 final : CoreStageOp {
         return P32{};
     }
     int pq_blocks(int64_t) const override { return (int)((int64_t(g.nx) * g.ny + kQThreads - 1) / kQThreads); }
-    int step_q(const double *p, double gamma, double *q, double *pq_part, CsScal *sc, double *l1, double *l2,
-               const StepFork &fk, cudaStream_t st) override
+    int step_q(const E *p, double gamma, E *q, double *pq_part, CsScal *sc, E *l1, E *l2, const StepFork &fk,
+               cudaStream_t st) override
     {
-        const double cx = 1.0 / (g.dx * g.dx), cy = 1.0 / (g.dy * g.dy);
+        E *tag = nullptr;
+        const E cx = cs_host_scalar(1.0 / (g.dx * g.dx), tag), cy = cs_host_scalar(1.0 / (g.dy * g.dy), tag);
         const int lb = grid_blocks(int64_t(nc) * g.nx * g.ny);
         MPI_TRY_CUDA(cudaEventRecord(fk.fork, st));
         MPI_TRY_CUDA(cudaStreamWaitEvent(fk.side, fk.fork, 0));
-        k_lap<false><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, p, l1, 1.0);
+        k_lap<E, false><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, p, l1, cs_host_scalar(1.0, tag));
         MPI_CHECK_LAUNCH();
-        k_lap<true><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, l1, l2, gamma);
+        k_lap<E, true><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, l1, l2, cs_host_scalar(gamma, tag));
         MPI_CHECK_LAUNCH();
         MPI_TRY_CUDA(cudaEventRecord(fk.join, fk.side));
         const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(bins.rec);
         const R *vs = static_cast<const R *>(bins.vs);
         if constexpr (sizeof(R) == 4) MPI_TRY((launch_interp<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec, true)));
-        else MPI_TRY((launch_interp<R, double>(g, T, nullptr, vs, p, s_tmp, st, ch, rec)));
+        else MPI_TRY((launch_interp<R, double>(g, T, nullptr, vs, reinterpret_cast<const double *>(p), s_tmp, st,
+                                               ch, rec)));
         MPI_TRY(launch_interp_T_units<R>(T, s_tmp, bins, st, ch));
         MPI_TRY_CUDA(cudaStreamWaitEvent(st, fk.join, 0));
         const unsigned blocks = (unsigned)pq_blocks(0);
         const R *part = static_cast<const R *>(bins.unit_part);
+        const E sc_T = cs_host_scalar(invT, tag);
         if (ch < 0)
-            k_grid_q<R, 4><<<blocks, kQThreads, 0, st>>>(g.nx, g.ny, bins.ncx, bins.ncy, bins.cunit_off, part, invT,
-                                                        l2, p, q, pq_part, sc);
+            k_grid_q<R, 4, E><<<blocks, kQThreads, 0, st>>>(g.nx, g.ny, bins.ncx, bins.ncy, bins.cunit_off, part,
+                                                           sc_T, l2, p, q, pq_part, sc);
         else
-            k_grid_q<R, 2><<<blocks, kQThreads, 0, st>>>(g.nx, g.ny, bins.ncx, bins.ncy, bins.cunit_off, part, invT,
-                                                        l2, p, q, pq_part, sc);
+            k_grid_q<R, 2, E><<<blocks, kQThreads, 0, st>>>(g.nx, g.ny, bins.ncx, bins.ncy, bins.cunit_off, part,
+                                                           sc_T, l2, p, q, pq_part, sc);
         MPI_CHECK_LAUNCH();
         return MPI_OK;
     }
@@ -851,12 +883,13 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     const size_t o_bins = scr.reserve(bins_bytes<R>(T, g.nx, g.ny));
     const size_t o_s = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_sd = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
-    const size_t o_b = scr.reserve(sizeof(double) * n4), o_x = scr.reserve(sizeof(double) * n4);
+    using E = typename CsElem<R>::type;
+    const size_t o_b = scr.reserve(sizeof(E) * n4), o_x = scr.reserve(sizeof(E) * n4);
     const size_t o_pr = scr.reserve(sizeof(R) == 4 ? sizeof(R) * n4 : 0);
     MPI_TRY(scr.allocate());
     Bins bins = bins_carve<R>(scr.at<char>(o_bins), T, g.nx, g.ny);
     R *s_data = scr.at<R>(o_sd);
-    double *b = scr.at<double>(o_b), *x = scr.at<double>(o_x);
+    E *b = scr.at<E>(o_b), *x = scr.at<E>(o_x);
 
     MPI_TRY(build_bins<R>(g, T, r, v, bins, st));
     // The sample vectors of the solve live in list (cell) order.
@@ -876,9 +909,9 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
     }
     GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_s), scr.at<R>(o_pr), o.lap_scaled != 0);
     // b = (1/T) M^T s
-    MPI_TRY((launch_interp_T<R, double>(g, T, s_data, bins, b, op.invT, st, ch)));
-    MPI_TRY(core_stage_cg(op, n4, b, o, x, n_iter_out, st));
-    k_grid_output<R><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
+    MPI_TRY((launch_interp_T<R, E>(g, T, s_data, bins, b, op.invT, st, ch)));
+    MPI_TRY(core_stage_cg<E>(op, n4, b, o, x, n_iter_out, st));
+    k_grid_output<R, E><<<grid_blocks(N), 256, 0, st>>>(N, ch, x, static_cast<R *>(Ahat), static_cast<R *>(trace));
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
@@ -941,21 +974,22 @@ int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st)
 }
 
 
-int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_opts &o, double *x,
-                  int *n_iter_out, cudaStream_t st)
+template <typename E>
+int core_stage_cg(CoreStageOp<E> &op, int64_t nv, const E *b, const mpi_grid_opts &o, E *x, int *n_iter_out,
+                  cudaStream_t st)
 {
     const int ncs = cs_blocks(nv);
     const int npq = op.pq_blocks(nv);
     const P32 p32 = op.p32();
     Scratch scr(st);
-    const size_t vb = sizeof(double) * nv;
+    const size_t vb = sizeof(E) * nv;
     const size_t o_r = scr.reserve(vb), o_p = scr.reserve(vb), o_q = scr.reserve(vb), o_l1 = scr.reserve(vb),
                  o_l2 = scr.reserve(vb);
     const size_t o_pq = scr.reserve(sizeof(double) * npq), o_rr = scr.reserve(sizeof(double) * ncs);
     const size_t o_sc = scr.reserve(sizeof(CsScal));
     MPI_TRY(scr.allocate());
-    double *rr = scr.at<double>(o_r), *p = scr.at<double>(o_p), *q = scr.at<double>(o_q),
-           *l1 = scr.at<double>(o_l1), *l2 = scr.at<double>(o_l2);
+    E *rr = scr.at<E>(o_r), *p = scr.at<E>(o_p), *q = scr.at<E>(o_q), *l1 = scr.at<E>(o_l1),
+      *l2 = scr.at<E>(o_l2);
     double *pq_part = scr.at<double>(o_pq), *rr_part = scr.at<double>(o_rr);
     CsScal *sc = scr.at<CsScal>(o_sc);
 
@@ -980,7 +1014,7 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
     MPI_TRY_CUDA(cudaMemsetAsync(x, 0, vb, st));
     MPI_TRY_CUDA(cudaMemsetAsync(sc, 0, sizeof(CsScal), st));
     // r = b, p = b, r.r, ||b|| and the threshold
-    k_cs_init<<<ncs, kCsThreads, 0, st>>>(nv, b, rr, p, rr_part, o.rel_tol, sc);
+    k_cs_init<E><<<ncs, kCsThreads, 0, st>>>(nv, b, rr, p, rr_part, o.rel_tol, sc);
     MPI_CHECK_LAUNCH();
     if (p32.buf) MPI_TRY(cs_round_launch(p32, p, st));
 
@@ -998,7 +1032,7 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
     // FP32 copy).
     auto enqueue_step = [&](int, cudaStream_t s) -> int {
         MPI_TRY(op.step_q(p, o.gamma, q, pq_part, sc, l1, l2, fk.f, s));
-        k_cs_step1<<<ncs, kCsThreads, 0, s>>>(nv, x, rr, p, q, rr_part, sc);
+        k_cs_step1<E><<<ncs, kCsThreads, 0, s>>>(nv, x, rr, p, q, rr_part, sc);
         MPI_CHECK_LAUNCH();
         return cs_step2_launch(p32, nv, rr, p, sc, s);
     };
@@ -1041,6 +1075,10 @@ int core_stage_cg(CoreStageOp &op, int64_t nv, const double *b, const mpi_grid_o
     }
     return MPI_OK;
 }
+template int core_stage_cg<double>(CoreStageOp<double> &, int64_t, const double *, const mpi_grid_opts &, double *,
+                                   int *, cudaStream_t);
+template int core_stage_cg<float2>(CoreStageOp<float2> &, int64_t, const float2 *, const mpi_grid_opts &, float2 *,
+                                   int *, cudaStream_t);
 
 }  // namespace mpi
 
