@@ -163,6 +163,21 @@ int mpi_interp(const mpi_grid_desc *grid, const mpi_traj *traj, mpi_dtype dtype,
 int mpi_interp_adjoint(const mpi_grid_desc *grid, const mpi_traj *traj,
                        mpi_dtype dtype, const void *s, void *Ahat, void *stream);
 
+/* Binning step of the Core Stage (Eq. first:step): the samples ordered by
+ * interpolation cell.  The Core Stage solves (mpi_grid, mpi_grid3,
+ * mpi_interp_adjoint) order their samples this way once per call, so that a
+ * cell's samples form one contiguous run and every sum over them has a fixed
+ * order; this entry exposes that step on its own.
+ *   list[offset[c] .. offset[c + 1]) = the samples t with cell_of[t] = c, ascending
+ * cell_of: device int [T], values in [0, n_cells).  list: device int [T]
+ * (must not overlap cell_of).  offset: device int [n_cells + 1], or NULL when
+ * only the order is wanted; offset[n_cells] = T.  The order is that of a
+ * stable sort by cell (bit-identical on every run).  0 <= T < 2^31,
+ * 1 <= n_cells < 2^31, else MPI_ERR_INVALID before any launch.  Values of
+ * cell_of outside [0, n_cells) leave list and offset unspecified but are
+ * never used as addresses.  Allocates scratch (about 16 B per sample). */
+int mpi_cell_order(int64_t T, const int *cell_of, int n_cells, int *list, int *offset, void *stream);
+
 /* ---- Preprocessing: transfer-function correction ------------------------- */
 
 /* The measured signal is the model signal convolved in time with the receive

@@ -124,6 +124,7 @@ _SIGS = {
     "mpi_conv_component": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 3,
     "mpi_interp": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_interp_adjoint": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 3,
+    "mpi_cell_order": [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3,
     "mpi_grid": [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 6,
     "mpi_denoise_gaussian5": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -406,6 +407,22 @@ def mpi_interp_adjoint(grid, r, v, s, Ahat=None, stream=None):
                                      _dev(s, dt, "s") if s.numel() else None,
                                      _dev(Ahat, dt, "Ahat"), _stream(stream)))
     return Ahat
+
+
+def mpi_cell_order(cell_of, n_cells, with_offset=True, stream=None):
+    """Binning step of the Core Stage: the samples ordered by cell (a stable
+    sort of cell_of, int32 on the device) and, with with_offset, the start of
+    each cell's run (offset[n_cells] = T).  Returns (list, offset or None)."""
+    if cell_of.dtype != torch.int32 or not cell_of.is_cuda:
+        raise TypeError("cell_of must be an int32 CUDA tensor")
+    cell_of = cell_of.contiguous()
+    T = cell_of.numel()
+    lst = torch.empty(T, dtype=torch.int32, device=cell_of.device)
+    off = torch.empty(int(n_cells) + 1, dtype=torch.int32, device=cell_of.device) if with_offset else None
+    _check(load().mpi_cell_order(int(T), cell_of.data_ptr() if T else None, int(n_cells),
+                                 lst.data_ptr() if T else None, off.data_ptr() if off is not None else None,
+                                 _stream(stream)))
+    return lst, off
 
 
 def mpi_grid(grid, r, v, s, gamma=1e-7, max_iter=10000, rel_tol=1e-3, Ahat=None, trace=None,

@@ -115,13 +115,17 @@ template <typename R>
 __global__ void k_cell_count3(int64_t T, const R *__restrict__ r, Axes3 ax, int ncx, int ncy,
                               int *__restrict__ cell_of, int *__restrict__ count, InterpRec3<R> *__restrict__ rec)
 {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const InterpRec3<R> q = make_rec3<R>(r[3 * t], r[3 * t + 1], r[3 * t + 2], ax);
-        rec[t] = q;
-        const int c = (q.l0 * ncy + q.j0) * ncx + q.i0;
-        cell_of[t] = c;
-        atomicAdd(&count[c], 1);
+    // every lane of a warp runs the same iterations (warp_count_add)
+    for (int64_t t0 = int64_t(blockIdx.x) * blockDim.x; t0 < T; t0 += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t t = t0 + threadIdx.x;
+        int c = -1;
+        if (t < T) {
+            const InterpRec3<R> q = make_rec3<R>(r[3 * t], r[3 * t + 1], r[3 * t + 2], ax);
+            rec[t] = q;
+            c = (q.l0 * ncy + q.j0) * ncx + q.i0;
+            cell_of[t] = c;
+        }
+        warp_count_add(count, c);
     }
 }
 
@@ -392,9 +396,10 @@ __global__ void k_grid3_output(int64_t N, int ch, const E *__restrict__ x, R *__
 
 // Binning scratch: as the 2-D one, with 3-D records and velocities.
 struct Bins3 {
-    int *cell_of, *count, *offset, *cursor, *list;
+    int *cell_of, *count, *offset, *list;
+    void *sort_tmp;  // scratch of the ordering and the scans
     void *rec_t, *rec, *vs;
-    int *cunit_cnt, *cunit_off, *cunit_cursor, *unit_cell;  // transpose work units per cell
+    int *cunit_cnt, *cunit_off, *unit_cell;  // transpose work units per cell
     void *unit_part;  // 8 corners x (9 or 3) sums per unit
     void *cell_part;  // V2<R>: the cell's corner sums, at its first unit's slot
     unsigned *cell_cnt;  // per-cell arrival counters of the units
@@ -418,8 +423,9 @@ size_t bins3_bytes(int64_t T, const G3 &g)
     const size_t nc = size_t(std::max(g.nx - 1, 1)) * std::max(g.ny - 1, 1) * std::max(g.nz - 1, 1);
     const size_t U = size_t(units_bound3(T, int64_t(nc)));
     const size_t T1 = size_t(std::max<int64_t>(T, 1));
-    return up256(sizeof(int) * T1) * 2 + up256(sizeof(int) * nc) * 2 + up256(sizeof(int) * (nc + 1)) +
-           2 * up256(sizeof(InterpRec3<R>) * T1) + up256(3 * sizeof(R) * T1) + up256(sizeof(int) * nc) * 2 +
+    return up256(sizeof(int) * T1) * 2 + up256(sizeof(int) * nc) + up256(sizeof(int) * (nc + 1)) +
+           up256(std::max(cell_order_bytes(T), cell_scan_bytes(int64_t(nc)))) +
+           2 * up256(sizeof(InterpRec3<R>) * T1) + up256(3 * sizeof(R) * T1) + up256(sizeof(int) * nc) +
            up256(sizeof(int) * (nc + 1)) + up256(sizeof(int) * U) + up256(8 * 9 * sizeof(R) * U) +
            up256(8 * 9 * sizeof(V2<R>) * U) + up256(sizeof(unsigned) * nc);
 }
@@ -436,14 +442,13 @@ Bins3 bins3_carve(char *p, int64_t T, const G3 &g)
     b.cell_of = reinterpret_cast<int *>(p); p += up256(sizeof(int) * T1);
     b.list = reinterpret_cast<int *>(p); p += up256(sizeof(int) * T1);
     b.count = reinterpret_cast<int *>(p); p += up256(sizeof(int) * nc);
-    b.cursor = reinterpret_cast<int *>(p); p += up256(sizeof(int) * nc);
     b.offset = reinterpret_cast<int *>(p); p += up256(sizeof(int) * (nc + 1));
+    b.sort_tmp = p; p += up256(std::max(cell_order_bytes(T), cell_scan_bytes(int64_t(nc))));
     b.rec_t = p; p += up256(sizeof(InterpRec3<R>) * T1);
     b.rec = p; p += up256(sizeof(InterpRec3<R>) * T1);
     b.vs = p; p += up256(3 * sizeof(R) * T1);
     b.n_units_max = units_bound3(T, int64_t(nc));
     b.cunit_cnt = reinterpret_cast<int *>(p); p += up256(sizeof(int) * nc);
-    b.cunit_cursor = reinterpret_cast<int *>(p); p += up256(sizeof(int) * nc);
     b.cunit_off = reinterpret_cast<int *>(p); p += up256(sizeof(int) * (nc + 1));
     b.unit_cell = reinterpret_cast<int *>(p); p += up256(sizeof(int) * size_t(b.n_units_max));
     b.unit_part = p; p += up256(8 * 9 * sizeof(R) * size_t(b.n_units_max));
@@ -469,10 +474,9 @@ int build_bins3(const G3 &g, int64_t T, const R *r, const R *v, const Bins3 &b, 
                                                           static_cast<InterpRec3<R> *>(b.rec_t));
         MPI_CHECK_LAUNCH();
     }
-    MPI_TRY(cell_scan_launch(b.count, nc, b.offset, b.cursor, st));
+    MPI_TRY(cell_scan_launch(b.count, nc, b.offset, b.sort_tmp, st));
     if (T > 0) {
-        MPI_TRY(cell_fill_launch(T, b.cell_of, b.cursor, b.list, st));
-        MPI_TRY(cell_sort_launch(nc, b.offset, b.list, st));
+        MPI_TRY(cell_order_launch(T, b.cell_of, nc, b.list, b.sort_tmp, st));
         k_sort_records<InterpRec3<R>, R, 3><<<grid_blocks(T), 256, 0, st>>>(
             T, b.list, static_cast<const InterpRec3<R> *>(b.rec_t), v, static_cast<InterpRec3<R> *>(b.rec),
             static_cast<R *>(b.vs));
@@ -481,7 +485,7 @@ int build_bins3(const G3 &g, int64_t T, const R *r, const R *v, const Bins3 &b, 
     // Work units of the transpose.
     k_cunit_count3<<<grid_blocks(nc), 256, 0, st>>>(nc, b.offset, b.cunit_cnt);
     MPI_CHECK_LAUNCH();
-    MPI_TRY(cell_scan_launch(b.cunit_cnt, nc, b.cunit_off, b.cunit_cursor, st));
+    MPI_TRY(cell_scan_launch(b.cunit_cnt, nc, b.cunit_off, b.sort_tmp, st));
     k_cunit_fill3<<<grid_blocks(nc), 256, 0, st>>>(nc, b.cunit_off, b.unit_cell);
     MPI_CHECK_LAUNCH();
     return MPI_OK;

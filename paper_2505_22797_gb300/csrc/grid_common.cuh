@@ -1,7 +1,7 @@
 // Pieces of the Core Stage (Eq. first:step) shared by the two- and the
 // three-dimensional solves: the one-dimensional cosine weights of the
 // interpolation, the binning of samples by interpolation cell (count, scan,
-// fill, per-cell sort), the work units of the transpose and their ordered
+// stable ordering), the work units of the transpose and their ordered
 // combine, and the CG solve over a Core Stage operator.  The non-template
 // kernels live in grid_ops.cu behind the launchers declared here.
 #pragma once
@@ -55,17 +55,26 @@ constexpr int kInterpSPT = 4;     // samples per thread of the interpolation (ga
 constexpr int kUnitLen = 128;
 constexpr int kUnitLanes = 8;     // lanes per unit
 constexpr int kUnitThreads = 256;
-constexpr int kScanThreads = 1024;
 
 inline int grid_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
 
-// Exclusive scan of count[0..n) into offset[0..n] (one block, deterministic);
-// also copies the offsets to cursor.
-int cell_scan_launch(const int *count, int n, int *offset, int *cursor, cudaStream_t st);
-// list[cursor[cell_of[t]]++] = t for every sample.
-int cell_fill_launch(int64_t T, const int *cell_of, int *cursor, int *list, cudaStream_t st);
-// Sorts each cell's run of list ascending.
-int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st);
+// count[c] += 1 for each lane's cell c (c < 0: none); lanes that hold the
+// same cell add once.  All 32 lanes of the warp call it together.
+__device__ __forceinline__ void warp_count_add(int *count, int c)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    if (c >= 0 && int(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[c], __popc(peers));
+}
+
+// Binning (binning.cu).  Exclusive scan of count[0..n) into offset[0..n]
+// (deterministic; tmp: cell_scan_bytes(n) of device scratch).
+size_t cell_scan_bytes(int64_t n);
+int cell_scan_launch(const int *count, int64_t n, int *offset, void *tmp, cudaStream_t st);
+// list = the samples 0..T-1 ordered by cell_of, ascending sample index within
+// a cell (a stable radix sort; tmp: cell_order_bytes(T) of device scratch,
+// which also serves cell_scan_launch's scans of up to n_cells + 1 entries).
+size_t cell_order_bytes(int64_t T);
+int cell_order_launch(int64_t T, const int *cell_of, int n_cells, int *list, void *tmp, cudaStream_t st);
 
 // Device scalars of one Core Stage CG solve.  A reduction's partial sums are
 // added once per step, in a fixed order, by the block of the producing

@@ -126,81 +126,17 @@ __global__ void k_cell_count(int64_t T, const R *__restrict__ r, AxisMap ax, Axi
                              int *__restrict__ cell_of, int *__restrict__ count,
                              InterpRec<R> *__restrict__ rec)
 {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const InterpRec<R> q = make_rec<R>(r[2 * t], r[2 * t + 1], ax, ay);
-        rec[t] = q;
-        const int c = q.j0 * ncx + q.i0;
-        cell_of[t] = c;
-        atomicAdd(&count[c], 1);
-    }
-}
-
-// Exclusive scan of n ints by one block (deterministic); also copies the
-// offsets to `cursor`.
-__global__ void __launch_bounds__(kScanThreads)
-k_scan(const int *__restrict__ count, int n, int *__restrict__ offset, int *__restrict__ cursor)
-{
-    __shared__ int sh[kScanThreads];
-    const int per = (n + kScanThreads - 1) / kScanThreads;
-    const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
-    int local = 0;
-    for (int k = b0; k < b1; ++k) local += count[k];
-    sh[threadIdx.x] = local;
-    __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        const int add = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-        __syncthreads();
-        sh[threadIdx.x] += add;
-        __syncthreads();
-    }
-    int run = sh[threadIdx.x] - local;
-    for (int k = b0; k < b1; ++k) {
-        offset[k] = run;
-        cursor[k] = run;
-        run += count[k];
-    }
-    if (threadIdx.x == kScanThreads - 1) offset[n] = sh[kScanThreads - 1];
-}
-
-__global__ void k_cell_fill(int64_t T, const int *__restrict__ cell_of, int *__restrict__ cursor,
-                            int *__restrict__ list)
-{
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
-         t += (int64_t)gridDim.x * blockDim.x)
-        list[atomicAdd(&cursor[cell_of[t]], 1)] = (int)t;
-}
-
-// Sort each cell's sample list ascending: insertion sort for short lists,
-// heap sort (O(n log n), in place) for long ones.
-__global__ void k_cell_sort(int n_cells, const int *__restrict__ offset, int *__restrict__ list)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_cells) return;
-    int *a = list + offset[c];
-    const int n = offset[c + 1] - offset[c];
-    if (n <= 32) {
-        for (int i = 1; i < n; ++i) {
-            const int key = a[i];
-            int j = i - 1;
-            while (j >= 0 && a[j] > key) { a[j + 1] = a[j]; --j; }
-            a[j + 1] = key;
+    // every lane of a warp runs the same iterations (warp_count_add)
+    for (int64_t t0 = int64_t(blockIdx.x) * blockDim.x; t0 < T; t0 += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t t = t0 + threadIdx.x;
+        int c = -1;
+        if (t < T) {
+            const InterpRec<R> q = make_rec<R>(r[2 * t], r[2 * t + 1], ax, ay);
+            rec[t] = q;
+            c = q.j0 * ncx + q.i0;
+            cell_of[t] = c;
         }
-        return;
-    }
-    auto sift = [&](int root, int end) {
-        while (2 * root + 1 < end) {
-            int child = 2 * root + 1;
-            if (child + 1 < end && a[child] < a[child + 1]) ++child;
-            if (a[root] >= a[child]) return;
-            const int tmp = a[root]; a[root] = a[child]; a[child] = tmp;
-            root = child;
-        }
-    };
-    for (int s = n / 2 - 1; s >= 0; --s) sift(s, n);
-    for (int end = n - 1; end > 0; --end) {
-        const int tmp = a[0]; a[0] = a[end]; a[end] = tmp;
-        sift(0, end);
+        warp_count_add(count, c);
     }
 }
 
@@ -324,14 +260,15 @@ __global__ void k_interp_T_cell_combine(int nx, int ny, int ncx, int ncy, const 
 // cell's samples are one contiguous run of every per-sample array (the Core
 // Stage keeps its sample vectors in this order as well).
 struct Bins {
-    int *cell_of, *count, *offset, *cursor, *list;
+    int *cell_of, *count, *offset, *list;
+    void *sort_tmp;  // scratch of the ordering and the scans
     void *rec_t;  // InterpRec<R>[T], sample order (scratch of the binning)
     void *rec;    // InterpRec<R>[T], list order
     void *vs;     // R[T][2], list order
     // Work units of the transpose (see kUnitLen): per cell cunit_off[c] ..
     // cunit_off[c + 1] (cunit_off[n_cells] = the number of units); the cell
     // of each unit; 4 corners x 4 partial sums per unit.
-    int *cunit_cnt, *cunit_off, *cunit_cursor, *unit_cell;
+    int *cunit_cnt, *cunit_off, *unit_cell;
     void *unit_part;
     int n_units_max;   // bound on the units (allocation)
     int n_units = -1;  // the exact count when read back to the host, else -1
@@ -352,10 +289,10 @@ static size_t bins_bytes(int64_t T, int nx, int ny)
     const size_t nc = size_t(std::max(nx - 1, 1)) * std::max(ny - 1, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t U = size_t(units_bound(T, nx, ny));
-    return up(sizeof(int) * std::max<int64_t>(T, 1)) * 2 + up(sizeof(int) * nc) * 2 +
-           up(sizeof(int) * (nc + 1)) + 2 * up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1)) +
-           up(2 * sizeof(R) * std::max<int64_t>(T, 1)) + up(sizeof(int) * nc) * 2 + up(sizeof(int) * (nc + 1)) +
-           up(sizeof(int) * U) + up(16 * sizeof(R) * U);
+    return up(sizeof(int) * std::max<int64_t>(T, 1)) * 2 + up(sizeof(int) * nc) +
+           up(sizeof(int) * (nc + 1)) + up(std::max(cell_order_bytes(T), cell_scan_bytes(int64_t(nc)))) +
+           2 * up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1)) + up(2 * sizeof(R) * std::max<int64_t>(T, 1)) +
+           up(sizeof(int) * nc) + up(sizeof(int) * (nc + 1)) + up(sizeof(int) * U) + up(16 * sizeof(R) * U);
 }
 
 template <typename R>
@@ -369,14 +306,13 @@ static Bins bins_carve(char *p, int64_t T, int nx, int ny)
     b.cell_of = reinterpret_cast<int *>(p); p += up(sizeof(int) * std::max<int64_t>(T, 1));
     b.list = reinterpret_cast<int *>(p); p += up(sizeof(int) * std::max<int64_t>(T, 1));
     b.count = reinterpret_cast<int *>(p); p += up(sizeof(int) * nc);
-    b.cursor = reinterpret_cast<int *>(p); p += up(sizeof(int) * nc);
     b.offset = reinterpret_cast<int *>(p); p += up(sizeof(int) * (nc + 1));
+    b.sort_tmp = p; p += up(std::max(cell_order_bytes(T), cell_scan_bytes(int64_t(nc))));
     b.rec_t = p; p += up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1));
     b.rec = p; p += up(sizeof(InterpRec<R>) * std::max<int64_t>(T, 1));
     b.vs = p; p += up(2 * sizeof(R) * std::max<int64_t>(T, 1));
     b.n_units_max = units_bound(T, nx, ny);
     b.cunit_cnt = reinterpret_cast<int *>(p); p += up(sizeof(int) * nc);
-    b.cunit_cursor = reinterpret_cast<int *>(p); p += up(sizeof(int) * nc);
     b.cunit_off = reinterpret_cast<int *>(p); p += up(sizeof(int) * (nc + 1));
     b.unit_cell = reinterpret_cast<int *>(p); p += up(sizeof(int) * size_t(b.n_units_max));
     b.unit_part = p;
@@ -396,13 +332,9 @@ static int build_bins(const GridH &g, int64_t T, const R *r, const R *v, const B
                                                          static_cast<InterpRec<R> *>(b.rec_t));
         MPI_CHECK_LAUNCH();
     }
-    k_scan<<<1, kScanThreads, 0, st>>>(b.count, nc, b.offset, b.cursor);
-    MPI_CHECK_LAUNCH();
+    MPI_TRY(cell_scan_launch(b.count, nc, b.offset, b.sort_tmp, st));
     if (T > 0) {
-        k_cell_fill<<<grid_blocks(T), 256, 0, st>>>(T, b.cell_of, b.cursor, b.list);
-        MPI_CHECK_LAUNCH();
-        k_cell_sort<<<(nc + 127) / 128, 128, 0, st>>>(nc, b.offset, b.list);
-        MPI_CHECK_LAUNCH();
+        MPI_TRY(cell_order_launch(T, b.cell_of, nc, b.list, b.sort_tmp, st));
         k_sort_records<InterpRec<R>, R, 2><<<grid_blocks(T), 256, 0, st>>>(T, b.list, static_cast<const InterpRec<R> *>(b.rec_t),
                                                           v, static_cast<InterpRec<R> *>(b.rec),
                                                           static_cast<R *>(b.vs));
@@ -411,8 +343,7 @@ static int build_bins(const GridH &g, int64_t T, const R *r, const R *v, const B
     // Work units of the transpose.
     k_cunit_count<<<grid_blocks(nc), 256, 0, st>>>(nc, b.offset, b.cunit_cnt);
     MPI_CHECK_LAUNCH();
-    k_scan<<<1, kScanThreads, 0, st>>>(b.cunit_cnt, nc, b.cunit_off, b.cunit_cursor);
-    MPI_CHECK_LAUNCH();
+    MPI_TRY(cell_scan_launch(b.cunit_cnt, nc, b.cunit_off, b.sort_tmp, st));
     k_cunit_fill<<<grid_blocks(nc), 256, 0, st>>>(nc, b.cunit_off, b.unit_cell);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
@@ -949,30 +880,6 @@ static int check_interp_args(const mpi_grid_desc *grid, const mpi_traj *traj, mp
     }
     return MPI_OK;
 }
-
-// Launchers of the binning kernels for the 3-D Core Stage.
-int cell_scan_launch(const int *count, int n, int *offset, int *cursor, cudaStream_t st)
-{
-    k_scan<<<1, kScanThreads, 0, st>>>(count, n, offset, cursor);
-    MPI_CHECK_LAUNCH();
-    return MPI_OK;
-}
-
-int cell_fill_launch(int64_t T, const int *cell_of, int *cursor, int *list, cudaStream_t st)
-{
-    if (T == 0) return MPI_OK;
-    k_cell_fill<<<grid_blocks(T), 256, 0, st>>>(T, cell_of, cursor, list);
-    MPI_CHECK_LAUNCH();
-    return MPI_OK;
-}
-
-int cell_sort_launch(int n_cells, const int *offset, int *list, cudaStream_t st)
-{
-    k_cell_sort<<<(n_cells + 127) / 128, 128, 0, st>>>(n_cells, offset, list);
-    MPI_CHECK_LAUNCH();
-    return MPI_OK;
-}
-
 
 template <typename E>
 int core_stage_cg(CoreStageOp<E> &op, int64_t nv, const E *b, const mpi_grid_opts &o, E *x, int *n_iter_out,

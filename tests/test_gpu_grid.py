@@ -32,8 +32,7 @@ def test_interp_and_transpose(orc, dt, shape):
 @pytest.mark.parametrize("dt", DTYPES)
 def test_interp_T_dense_cell(dt):
     """Thousands of samples in one cell (a trajectory that dwells): the
-    per-cell ordering takes the long-list path and the cell's run spans many
-    work units; result matches FP64 sums."""
+    cell's run spans many work units; result matches FP64 sums."""
     g = syn.square_grid(8, 8.0)
     T = 5000
     rng = np.random.default_rng(0)
@@ -43,6 +42,32 @@ def test_interp_T_dense_cell(dt):
     from oracle import oracle as orc
     assert rel_l2(host(api.mpi_interp_adjoint(g, dev(r, dt), dev(v, dt), dev(s, dt))),
                   orc.interp_T(g, r, v, s)) <= tol(dt)
+
+
+@pytest.mark.parametrize("T, n_cells, run", [(0, 1, 1), (1, 1, 1), (3000, 1, 1), (2047, 5, 9),
+                                             (2049, 255, 3), (5000, 256, 40), (9001, 70000, 12),
+                                             (1 << 20, 511 * 511, 30), (1 << 20, 47 * 47 * 23, 2000)])
+def test_cell_order_stable(T, n_cells, run):
+    """The binning step on its own: bit-equal to a stable sort by cell (zero
+    to three radix passes, a ragged last tile, runs of one cell as a
+    trajectory leaves them, up to thousands long) and run offsets equal to
+    the cumulative cell counts."""
+    rng = np.random.default_rng(T + n_cells + run)
+    lengths = rng.integers(1, run + 1, size=T + 1)
+    keys = np.repeat(rng.integers(0, n_cells, size=T + 1), lengths)[:T].astype(np.int32)
+    lst, off = api.mpi_cell_order(torch.from_numpy(keys).cuda(), n_cells)
+    torch.cuda.synchronize()
+    assert np.array_equal(lst.cpu().numpy(), np.argsort(keys, kind="stable"))
+    want = np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=n_cells))])
+    assert np.array_equal(off.cpu().numpy(), want)
+    lst2, none = api.mpi_cell_order(torch.from_numpy(keys).cuda(), n_cells, with_offset=False)
+    assert none is None and torch.equal(lst2, lst)
+
+
+def test_cell_order_rejects_bad_arguments():
+    keys = torch.zeros(10, dtype=torch.int32, device="cuda")
+    with pytest.raises(api.MPIError):
+        api.mpi_cell_order(keys, 0)
 
 
 @pytest.mark.parametrize("dt", DTYPES)
