@@ -18,7 +18,9 @@
 //    Stockham FFT, a tiled transpose and row passes again; the kernel's
 //    spectrum kept in
 //    the transposed layout, the inverse by the conjugation identity
-//    IDFT(Y) = conj(DFT(conj Y)) / n.  O(N log N) instead of N^2.
+//    IDFT(Y) = conj(DFT(conj Y)) / n.  O(N log N) instead of N^2.  Grids whose
+//    transforms fit in shared memory take the three-launch form of
+//    conv_fft2.cu (real rows in pairs, half spectra, fused column pass).
 #include <algorithm>
 
 #include "conv_ops.cuh"
@@ -158,6 +160,12 @@ int launch_conv(const GridH &g, const R *K, const IN *in, OUT *out, cudaStream_t
 #endif
 #ifndef MPI_CONV_FFT_MIN_N64
 #define MPI_CONV_FFT_MIN_N64 1024
+#endif
+
+// The three-launch route for the grids it fits (conv_fft2.cu); 0 keeps the
+// nine-launch route everywhere.
+#ifndef MPI_CONV_FUSED
+#define MPI_CONV_FUSED 1
 #endif
 
 // Padded length: the power of two >= n (radix-4/2 passes only; measured on
@@ -307,7 +315,13 @@ int conv_plan_prepare(const ModelH &m, const GridH &g, void *scratch, ConvPlan<R
     // The sampled kernel in FP64 is the first piece of the scratch.
     k_conv_circ<C2><<<elem_blocks(n), 256, 0, st>>>(g.nx, g.ny, P.NX, P.NY, static_cast<const double *>(scratch), P.a);
     MPI_CHECK_LAUNCH();
-    return dft2_to_t(P, P.a, P.Kh, st);
+    MPI_TRY(dft2_to_t(P, P.a, P.Kh, st));
+    if (MPI_CONV_FUSED && conv_fused_fits(P.NX, P.NY)) {
+        P.fused = true;
+        P.LD = conv_fused_ld(P.NX, sizeof(R));
+        MPI_TRY(conv_fused_kernel<C2>(P.NX, P.NY, P.LD, P.Kh, P.a, st));
+    }
+    return MPI_OK;
 }
 
 template <typename R, typename IN, typename OUT>
@@ -319,8 +333,9 @@ int conv_apply(const ConvPlan<R> &P, const IN *in, OUT *out, cudaStream_t st)
         g.ny = P.ny;
         return launch_conv<R, IN, OUT>(g, P.K, in, out, st);
     }
-    const int64_t n = (int64_t)P.NX * P.NY;
     ProfScope prof(kProfConv, st);
+    if (P.fused) return conv_apply_fused<R, IN, OUT>(P, in, out, st);
+    const int64_t n = (int64_t)P.NX * P.NY;
     using C2 = typename ConvPlan<R>::C2;
     k_conv_load<IN, C2><<<elem_blocks(n), 256, 0, st>>>(P.nx, P.ny, P.NX, P.NY, in, P.a);
     MPI_CHECK_LAUNCH();

@@ -31,6 +31,10 @@ struct ConvPlan {
     int NX = 0, NY = 0;    // FFT route: circular grid
     FftPlan px, py;
     C2 *WX = nullptr, *WY = nullptr, *Kh = nullptr, *a = nullptr, *t = nullptr;
+    // Three-launch form (conv_fft2.cu): Kh holds the kernel spectrum's
+    // columns kx < LD row-major, [NY][LD]; a and t the half spectra.
+    bool fused = false;
+    int LD = 0;
 };
 bool conv_uses_fft(int nx, int ny, int elem_bytes);
 size_t conv_plan_bytes(int nx, int ny, int elem_bytes);
@@ -43,6 +47,18 @@ int transpose_cx(int rows, int cols, const float2 *src, float2 *dst, cudaStream_
 int transpose_cx(int rows, int cols, const double2 *src, double2 *dst, cudaStream_t st);
 int spec_mul_conj(int64_t n, float2 *t, const float2 *kh, cudaStream_t st);
 int spec_mul_conj(int64_t n, double2 *t, const double2 *kh, cudaStream_t st);
+
+// Three-launch FFT route (conv_fft2.cu): power-of-two circular grids with
+// 4 <= NX <= 4096 and 4 <= NY <= 2048 (every transform in shared memory).
+bool conv_fused_fits(int NX, int NY);
+// Row length of the half spectra: NX/2 + 1 rounded up to whole column groups.
+int conv_fused_ld(int NX, int elem_bytes);
+// Rearranges the plan's transposed kernel spectrum Kh ([NX][NY]) into the
+// [NY][LD] layout of the column launch, in place (tmp: NY x LD scratch).
+template <typename C>
+int conv_fused_kernel(int NX, int NY, int LD, C *Kh, C *tmp, cudaStream_t st);
+template <typename R, typename IN, typename OUT>
+int conv_apply_fused(const ConvPlan<R> &P, const IN *in, OUT *out, cudaStream_t st);
 
 // out = C in.  The FFT route uses the plan's buffers: one application at a
 // time per plan (calls on one stream are ordered).

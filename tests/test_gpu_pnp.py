@@ -255,6 +255,21 @@ def test_conv_fft_route(orc, dt, shape):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("shape", [(512, 512), (2048, 4), (8, 1024), (4, 1100)])
+def test_conv_fft_route_large(orc, dt, shape):
+    """The three-launch FFT route at 512 x 512 and at its limits (4096-point
+    rows, 2048-point columns), and a grid past them (4096-point columns: the
+    nine-launch route), every output against the oracle's FFT realisation of
+    the same linear convolution."""
+    nx, ny = shape
+    g = syn.square_grid(nx, 24.0, ny)
+    m = syn.default_model()
+    x = rounded(np.random.default_rng(nx * 3 + ny).normal(size=(ny, nx)), dt)
+    want = orc.conv_fft(orc.conv_kernel(m, g), x)
+    assert rel_l2(host(api.mpi_conv(m, g, dev(x, dt))), want) <= tol(dt)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
 def test_pnp_conv_fft_route(orc, dt):
     """Algorithm 1 with C on a 100 x 100 grid (FFT route), few steps."""
     g = syn.square_grid(100, 24.0)
