@@ -134,41 +134,60 @@ k_cf_rows_fwd(int nx, int ny, int lg_nx, int lg_rp, int LD, const IN *__restrict
     }
 }
 
-// Launch 2: per group of 2^LG_CB adjacent kx, the column DFTs of the half
-// spectra (rows j >= ny are zero), the product with the kernel's spectrum
-// Kh2[ky][kx], and the inverse column DFTs kept for j < ny (unscaled):
-//   Y2[j][kx] = sum_ky Kh2[ky][kx] sum_j' X1[j'][kx] W^(j' ky) W^(-j ky).
-template <typename C, int LG_CB>
+// Column pass (launch 2 in 2-D; the y and z passes in 3-D): a block takes
+// 2^LG_CB adjacent kx (one 32-byte sector per element) of one outer index o
+// (blockIdx.x = group + n_groups o) and transforms along a column of n = 2^lg_n
+// elements at distance `stride`:
+//   in  element e < n_in at in  + o in_outer  + e in_stride  + kx (zero for e >= n_in),
+//   out element e < n_out at out + o out_outer + e out_stride + kx,
+// MODE kCfFwd:   out = DFT(in);
+// MODE kCfFused: out = IDFT(DFT(in) K) (unscaled), K element e at Kh + o k_outer + e k_stride + kx;
+// MODE kCfInv:   out = IDFT(in) (unscaled), by IDFT(V) = conj(DFT(conj V)).
+struct CfColArgs {
+    int lg_n, n_in, n_out, n_groups;
+    int64_t in_outer, in_stride, out_outer, out_stride, k_outer, k_stride;
+};
+
+template <typename C, int LG_CB, int MODE>
 __global__ void __launch_bounds__(kCfMaxThreads)
-k_cf_cols(int ny, int lg_ny, int LD, const C *__restrict__ X1, const C *__restrict__ Kh2,
-          const C *__restrict__ W, C *__restrict__ Y2)
+k_cf_cols(CfColArgs d, const C *__restrict__ in, const C *__restrict__ Kh, const C *__restrict__ W,
+          C *__restrict__ out)
 {
     using R = decltype(C{}.x);
     constexpr int CB = 1 << LG_CB;
     extern __shared__ __align__(16) unsigned char cf_smem[];
-    const int NY = 1 << lg_ny;
+    const int n = 1 << d.lg_n;
     C *A = reinterpret_cast<C *>(cf_smem);
-    C *B = A + (NY << LG_CB);
-    const int kx0 = blockIdx.x * CB;
-    for (int q = threadIdx.x; q < (NY << LG_CB); q += blockDim.x) {
-        const int c = q & (CB - 1), j = q >> LG_CB;
-        A[q] = j < ny ? X1[(int64_t)j * LD + kx0 + c] : cxv(R(0), R(0));
+    C *B = A + (n << LG_CB);
+    const int o = blockIdx.x / d.n_groups;
+    const int kx0 = (blockIdx.x - o * d.n_groups) * CB;
+    const C *src = in + o * d.in_outer + kx0;
+    for (int q = threadIdx.x; q < (n << LG_CB); q += blockDim.x) {
+        const int c = q & (CB - 1), e = q >> LG_CB;
+        C v = cxv(R(0), R(0));
+        if (e < d.n_in) v = src[e * d.in_stride + c];
+        if (MODE == kCfInv) v.y = -v.y;
+        A[q] = v;
     }
     __syncthreads();
-    C *F = smem_dft(A, B, lg_ny, LG_CB, W);
-    C *G = F == A ? B : A;
-    // conj(F Kh2), so that a second forward DFT gives the conjugated inverse
-    for (int q = threadIdx.x; q < (NY << LG_CB); q += blockDim.x) {
-        const int c = q & (CB - 1), ky = q >> LG_CB;
-        const C p = cmul(F[q], Kh2[(int64_t)ky * LD + kx0 + c]);
-        F[q] = cxv(p.x, -p.y);
+    C *F = smem_dft(A, B, d.lg_n, LG_CB, W);
+    if constexpr (MODE == kCfFused) {
+        // conj(F K), so that a second forward DFT gives the conjugated inverse
+        C *G = F == A ? B : A;
+        const C *kc = Kh + o * d.k_outer + kx0;
+        for (int q = threadIdx.x; q < (n << LG_CB); q += blockDim.x) {
+            const int c = q & (CB - 1), e = q >> LG_CB;
+            const C p = cmul(F[q], kc[e * d.k_stride + c]);
+            F[q] = cxv(p.x, -p.y);
+        }
+        __syncthreads();
+        F = smem_dft(F, G, d.lg_n, LG_CB, W);
     }
-    __syncthreads();
-    const C *H = smem_dft(F, G, lg_ny, LG_CB, W);
-    for (int q = threadIdx.x; q < (ny << LG_CB); q += blockDim.x) {
-        const int c = q & (CB - 1), j = q >> LG_CB;
-        const C h = H[q];
-        Y2[(int64_t)j * LD + kx0 + c] = cxv(h.x, -h.y);
+    C *dst = out + o * d.out_outer + kx0;
+    for (int q = threadIdx.x; q < (d.n_out << LG_CB); q += blockDim.x) {
+        const int c = q & (CB - 1), e = q >> LG_CB;
+        const C h = F[q];
+        dst[e * d.out_stride + c] = MODE == kCfFwd ? h : cxv(h.x, -h.y);
     }
 }
 
@@ -263,6 +282,70 @@ int allow_smem(K kernel, size_t bytes)
 
 }  // namespace
 
+template <typename C, typename IN>
+int cf_rows_fwd(int nx, int n_rows, int NX, int LD, const IN *in, const C *W, C *X1, cudaStream_t st)
+{
+    if (n_rows <= 0) return MPI_OK;
+    const int lg_nx = ilog2(NX), lg_rp = rows_lg_rp(NX);
+    const unsigned blocks = (unsigned)(((n_rows + 1) / 2 + (1 << lg_rp) - 1) >> lg_rp);
+    const size_t smem = 2 * sizeof(C) * (size_t(NX) << lg_rp);
+    MPI_TRY(allow_smem(k_cf_rows_fwd<C, IN>, smem));
+    k_cf_rows_fwd<C, IN><<<blocks, block_threads(lg_nx, lg_rp), smem, st>>>(nx, n_rows, lg_nx, lg_rp, LD, in, W, X1);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+template <typename C, typename OUT>
+int cf_rows_inv(int nx, int n_rows, int NX, int LD, const C *Y, const C *W, double scale, OUT *out, cudaStream_t st)
+{
+    if (n_rows <= 0) return MPI_OK;
+    const int lg_nx = ilog2(NX), lg_rp = rows_lg_rp(NX);
+    const unsigned blocks = (unsigned)(((n_rows + 1) / 2 + (1 << lg_rp) - 1) >> lg_rp);
+    const size_t smem = 2 * sizeof(C) * (size_t(NX) << lg_rp);
+    MPI_TRY(allow_smem(k_cf_rows_inv<C, OUT>, smem));
+    k_cf_rows_inv<C, OUT><<<blocks, block_threads(lg_nx, lg_rp), smem, st>>>(nx, n_rows, lg_nx, lg_rp, LD, Y, W, scale,
+                                                                             out);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+template <typename C>
+int cf_cols(const CfCols &c, const C *in, const C *Kh, const C *W, C *out, cudaStream_t st)
+{
+    constexpr int LG_CB = cols_lg_cb<C>();
+    if (c.n_outer <= 0 || c.n_out <= 0) return MPI_OK;
+    CfColArgs d{};
+    d.lg_n = ilog2(c.n);
+    d.n_in = c.n_in;
+    d.n_out = c.n_out;
+    d.n_groups = c.LD >> LG_CB;
+    d.in_outer = c.in_outer;
+    d.in_stride = c.in_stride;
+    d.out_outer = c.out_outer;
+    d.out_stride = c.out_stride;
+    d.k_outer = c.k_outer;
+    d.k_stride = c.k_stride;
+    const unsigned blocks = (unsigned)(int64_t(d.n_groups) * c.n_outer);
+    const size_t smem = 2 * sizeof(C) * (size_t(c.n) << LG_CB);
+    const unsigned threads = block_threads(d.lg_n, LG_CB);
+    switch (c.mode) {
+        case kCfFwd:
+            MPI_TRY(allow_smem(k_cf_cols<C, LG_CB, kCfFwd>, smem));
+            k_cf_cols<C, LG_CB, kCfFwd><<<blocks, threads, smem, st>>>(d, in, Kh, W, out);
+            break;
+        case kCfFused:
+            MPI_TRY(allow_smem(k_cf_cols<C, LG_CB, kCfFused>, smem));
+            k_cf_cols<C, LG_CB, kCfFused><<<blocks, threads, smem, st>>>(d, in, Kh, W, out);
+            break;
+        default:
+            MPI_TRY(allow_smem(k_cf_cols<C, LG_CB, kCfInv>, smem));
+            k_cf_cols<C, LG_CB, kCfInv><<<blocks, threads, smem, st>>>(d, in, Kh, W, out);
+            break;
+    }
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
 bool conv_fused_fits(int NX, int NY) { return NX >= 4 && NY >= 4 && NX <= 4096 && NY <= 2048; }
 
 int conv_fused_ld(int NX, int elem_bytes)
@@ -287,27 +370,31 @@ template <typename R, typename IN, typename OUT>
 int conv_apply_fused(const ConvPlan<R> &P, const IN *in, OUT *out, cudaStream_t st)
 {
     using C = typename ConvPlan<R>::C2;
-    const int lg_nx = ilog2(P.NX), lg_ny = ilog2(P.NY);
-    const int lg_rp = rows_lg_rp(P.NX);
-    const int pairs = (P.ny + 1) / 2;
-    const unsigned rblocks = (unsigned)((pairs + (1 << lg_rp) - 1) >> lg_rp);
-    const size_t rsmem = 2 * sizeof(C) * (size_t(P.NX) << lg_rp);
-    constexpr int LG_CB = cols_lg_cb<C>();
-    const size_t csmem = 2 * sizeof(C) * (size_t(P.NY) << LG_CB);
-    MPI_TRY(allow_smem(k_cf_rows_fwd<C, IN>, rsmem));
-    MPI_TRY(allow_smem(k_cf_cols<C, LG_CB>, csmem));
-    MPI_TRY(allow_smem(k_cf_rows_inv<C, OUT>, rsmem));
-    const unsigned rthreads = block_threads(lg_nx, lg_rp), cthreads = block_threads(lg_ny, LG_CB);
-    k_cf_rows_fwd<C, IN><<<rblocks, rthreads, rsmem, st>>>(P.nx, P.ny, lg_nx, lg_rp, P.LD, in, P.WX, P.a);
-    MPI_CHECK_LAUNCH();
-    k_cf_cols<C, LG_CB><<<(unsigned)(P.LD >> LG_CB), cthreads, csmem, st>>>(P.ny, lg_ny, P.LD, P.a, P.Kh, P.WY, P.t);
-    MPI_CHECK_LAUNCH();
-    k_cf_rows_inv<C, OUT><<<rblocks, rthreads, rsmem, st>>>(P.nx, P.ny, lg_nx, lg_rp, P.LD, P.t, P.WX,
-                                                            1.0 / (double(P.NX) * double(P.NY)), out);
-    MPI_CHECK_LAUNCH();
-    return MPI_OK;
+    MPI_TRY((cf_rows_fwd<C, IN>(P.nx, P.ny, P.NX, P.LD, in, P.WX, P.a, st)));
+    CfCols c{};
+    c.mode = kCfFused;
+    c.n = P.NY;
+    c.n_in = c.n_out = P.ny;
+    c.n_outer = 1;
+    c.LD = P.LD;
+    c.in_stride = c.out_stride = c.k_stride = P.LD;
+    MPI_TRY(cf_cols<C>(c, P.a, P.Kh, P.WY, P.t, st));
+    return cf_rows_inv<C, OUT>(P.nx, P.ny, P.NX, P.LD, P.t, P.WX, 1.0 / (double(P.NX) * double(P.NY)), out, st);
 }
 
+template int cf_rows_fwd<float2, float>(int, int, int, int, const float *, const float2 *, float2 *, cudaStream_t);
+template int cf_rows_fwd<float2, double>(int, int, int, int, const double *, const float2 *, float2 *, cudaStream_t);
+template int cf_rows_fwd<double2, double>(int, int, int, int, const double *, const double2 *, double2 *,
+                                          cudaStream_t);
+template int cf_rows_inv<float2, float>(int, int, int, int, const float2 *, const float2 *, double, float *,
+                                        cudaStream_t);
+template int cf_rows_inv<float2, double>(int, int, int, int, const float2 *, const float2 *, double, double *,
+                                         cudaStream_t);
+template int cf_rows_inv<double2, double>(int, int, int, int, const double2 *, const double2 *, double, double *,
+                                          cudaStream_t);
+template int cf_cols<float2>(const CfCols &, const float2 *, const float2 *, const float2 *, float2 *, cudaStream_t);
+template int cf_cols<double2>(const CfCols &, const double2 *, const double2 *, const double2 *, double2 *,
+                              cudaStream_t);
 template int conv_fused_kernel<float2>(int, int, int, float2 *, float2 *, cudaStream_t);
 template int conv_fused_kernel<double2>(int, int, int, double2 *, double2 *, cudaStream_t);
 template int conv_apply_fused<float, float, float>(const ConvPlan<float> &, const float *, float *, cudaStream_t);

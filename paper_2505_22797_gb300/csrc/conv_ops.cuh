@@ -60,6 +60,30 @@ int conv_fused_kernel(int NX, int NY, int LD, C *Kh, C *tmp, cudaStream_t st);
 template <typename R, typename IN, typename OUT>
 int conv_apply_fused(const ConvPlan<R> &P, const IN *in, OUT *out, cudaStream_t st);
 
+// Pieces of the shared-memory FFT routes (conv_fft2.cu), shared by the 2-D
+// and 3-D convolutions.  Row launches: n_rows real rows of nx values (row r
+// at in + r nx) <-> their half spectra (row r at X + r LD, LD entries, bins
+// above NX/2 zero), NX = 2^k <= 4096; the inverse extends each half by
+// Hermitian symmetry, crops to nx and scales.
+template <typename C, typename IN>
+int cf_rows_fwd(int nx, int n_rows, int NX, int LD, const IN *in, const C *W, C *X, cudaStream_t st);
+template <typename C, typename OUT>
+int cf_rows_inv(int nx, int n_rows, int NX, int LD, const C *Y, const C *W, double scale, OUT *out, cudaStream_t st);
+// Column launch: for every outer index o < n_outer and every group of
+// adjacent kx < LD, a DFT of length n (2^k <= 2048) over the elements
+// e < n_in at in + o in_outer + e in_stride + kx (zero above), written for
+// e < n_out at out + o out_outer + e out_stride + kx.  mode: kCfFwd (DFT),
+// kCfFused (IDFT(DFT(x) K), K at Kh + o k_outer + e k_stride + kx), kCfInv
+// (IDFT); inverses unscaled.
+constexpr int kCfFwd = 0, kCfFused = 1, kCfInv = 2;
+struct CfCols {
+    int mode = kCfFwd;
+    int n = 0, n_in = 0, n_out = 0, n_outer = 0, LD = 0;
+    int64_t in_outer = 0, in_stride = 0, out_outer = 0, out_stride = 0, k_outer = 0, k_stride = 0;
+};
+template <typename C>
+int cf_cols(const CfCols &c, const C *in, const C *Kh, const C *W, C *out, cudaStream_t st);
+
 // out = C in.  The FFT route uses the plan's buffers: one application at a
 // time per plan (calls on one stream are ordered).
 template <typename R, typename IN, typename OUT>

@@ -781,7 +781,32 @@ struct Conv3Plan {
     int NX = 0, NY = 0, NZ = 0;
     FftPlan px, py, pz;
     C2 *WX = nullptr, *WY = nullptr, *WZ = nullptr, *Kh = nullptr, *a = nullptr, *t = nullptr;
+    // Five-launch form (shared-memory transforms, conv_fft2.cu): Kh holds the
+    // kernel spectrum's kx < LD, [NZ][NY][LD]; a and t the half spectra.
+    bool fused = false;
+    int LD = 0;
 };
+
+// The five-launch form: every transform in shared memory.
+#ifndef MPI_CONV3_FUSED
+#define MPI_CONV3_FUSED 1
+#endif
+static bool conv3_fused_fits(int NX, int NY, int NZ)
+{
+    return MPI_CONV3_FUSED && NX >= 4 && NY >= 4 && NZ >= 4 && NX <= 4096 && NY <= 2048 && NZ <= 2048;
+}
+
+// Kh3[kz][ky][kx] = Kh[ky][kx][kz] for kx < LD (the layout dft3 leaves, half of it).
+template <typename C>
+__global__ void k_conv3_kh_half(int NX, int NY, int NZ, int LD, const C *__restrict__ Kh, C *__restrict__ Kh3)
+{
+    const int64_t n = (int64_t)NZ * NY * LD;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(e % LD), ky = (int)((e / LD) % NY), kz = (int)(e / ((int64_t)LD * NY));
+        Kh3[e] = Kh[((int64_t)ky * NX + kx) * NZ + kz];
+    }
+}
 
 static bool conv3_uses_fft(const Grid3H &g, int elem)
 {
@@ -895,7 +920,64 @@ static int conv3_plan_prepare(const Model3H &m, const Grid3H &g, int kernel, voi
     // The sampled kernel in FP64 is the first piece of the scratch.
     k_conv3_circ<C2><<<conv3_blocks(n), 256, 0, st>>>(g, P.NX, P.NY, P.NZ, static_cast<const double *>(scratch), P.Kh);
     MPI_CHECK_LAUNCH();
-    return dft3(P, P.Kh, P.a, st);
+    MPI_TRY(dft3(P, P.Kh, P.a, st));
+    if (conv3_fused_fits(P.NX, P.NY, P.NZ)) {
+        P.fused = true;
+        P.LD = conv_fused_ld(P.NX, sizeof(R));
+        const int64_t nh = (int64_t)P.NZ * P.NY * P.LD;
+        k_conv3_kh_half<C2><<<conv3_blocks(nh), 256, 0, st>>>(P.NX, P.NY, P.NZ, P.LD, P.Kh, P.a);
+        MPI_CHECK_LAUNCH();
+        MPI_TRY_CUDA(cudaMemcpyAsync(P.Kh, P.a, sizeof(C2) * size_t(nh), cudaMemcpyDeviceToDevice, st));
+    }
+    return MPI_OK;
+}
+
+// The five-launch form of the FFT route: real rows along x in pairs to half
+// spectra (the nz ny non-zero rows), the DFT along y of the ny non-zero rows
+// per (z, kx group), the fused pass along z (DFT of the nz non-zero planes,
+// the spectrum product, inverse DFT, nz kept), the inverse DFT along y (ny
+// kept), and the inverse rows along x (cropped to nx, scaled).  The product
+// spectrum is Hermitian (real input, point-symmetric kernel), so the half
+// kx = 0 .. NX/2 carries it.
+template <typename R, typename IN, typename OUT>
+static int conv3_apply_fused(const Conv3Plan<R> &P, const IN *in, OUT *out, cudaStream_t st)
+{
+    using C2 = typename Conv3Plan<R>::C2;
+    const Grid3H &g = P.g;
+    const int64_t LD = P.LD;
+    MPI_TRY((cf_rows_fwd<C2, IN>(g.nx, g.nz * g.ny, P.NX, P.LD, in, P.WX, P.a, st)));  // a: [nz][ny][LD]
+    CfCols c{};
+    c.LD = P.LD;
+    c.mode = kCfFwd;  // along y: t = [nz][NY][LD]
+    c.n = P.NY;
+    c.n_in = g.ny;
+    c.n_out = P.NY;
+    c.n_outer = g.nz;
+    c.in_outer = g.ny * LD;
+    c.in_stride = LD;
+    c.out_outer = P.NY * LD;
+    c.out_stride = LD;
+    MPI_TRY(cf_cols<C2>(c, P.a, nullptr, P.WY, P.t, st));
+    c.mode = kCfFused;  // along z, outer index ky: a = [nz][NY][LD]
+    c.n = P.NZ;
+    c.n_in = c.n_out = g.nz;
+    c.n_outer = P.NY;
+    c.in_outer = c.out_outer = c.k_outer = LD;
+    c.in_stride = c.out_stride = c.k_stride = P.NY * LD;
+    MPI_TRY(cf_cols<C2>(c, P.t, P.Kh, P.WZ, P.a, st));
+    c.mode = kCfInv;  // along y: t = [nz][ny][LD]
+    c.n = P.NY;
+    c.n_in = P.NY;
+    c.n_out = g.ny;
+    c.n_outer = g.nz;
+    c.in_outer = P.NY * LD;
+    c.in_stride = LD;
+    c.out_outer = g.ny * LD;
+    c.out_stride = LD;
+    c.k_outer = c.k_stride = 0;
+    MPI_TRY(cf_cols<C2>(c, P.a, nullptr, P.WY, P.t, st));
+    return cf_rows_inv<C2, OUT>(g.nx, g.nz * g.ny, P.NX, P.LD, P.t, P.WX,
+                                1.0 / (double(P.NX) * double(P.NY) * double(P.NZ)), out, st);
 }
 
 // out = C in (3-D), by the direct sum or the FFT route of the plan.
@@ -906,6 +988,7 @@ static int conv3_apply(const Conv3Plan<R> &P, const IN *in, OUT *out, cudaStream
     using C2 = typename Conv3Plan<R>::C2;
     const int64_t n = (int64_t)P.NX * P.NY * P.NZ;
     ProfScope prof(kProfConv, st);
+    if (P.fused) return conv3_apply_fused<R, IN, OUT>(P, in, out, st);
     k_conv3_load<IN, C2><<<conv3_blocks(n), 256, 0, st>>>(P.g, P.NX, P.NY, P.NZ, in, P.a);
     MPI_CHECK_LAUNCH();
     MPI_TRY(dft3(P, P.a, P.t, st));

@@ -198,6 +198,20 @@ def test_conv3_fft_route(orc, dt, shape):
         assert rel_l2(host(api.mpi_conv3(m, g, dev(x, dt))), want) <= tol(dt)
 
 
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("shape", [(48, 48, 24), (100, 90, 1), (3, 3, 1100)])
+def test_conv3_fft_route_sizes(orc, dt, shape):
+    """The five-launch route on the 3-D workload's 48 x 48 x 24 volume, and
+    volumes past its size rule (one plane; 1100 planes, 4096-point z
+    transforms) on the multi-pass route: every output against the oracle."""
+    nx, ny, nz = shape
+    g = syn.box_grid3(nx, ny, nz)
+    m = dict(syn.default_model3(), G=G_GEN)
+    x = rounded(np.random.default_rng(nx + 7 * nz).normal(size=(nz, ny, nx)), dt)
+    want = orc.conv3(g, orc.conv_kernel3(m, g), x)
+    assert rel_l2(host(api.mpi_conv3(m, g, dev(x, dt))), want) <= tol(dt)
+
+
 def test_pnp3_conv_fft_route(orc):
     dt = torch.float32
     g = syn.box_grid3(24, 20, 18)
