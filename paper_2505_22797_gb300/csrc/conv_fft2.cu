@@ -34,6 +34,7 @@ namespace {
 constexpr int kCfMinThreads = 64;
 constexpr int kCfMaxThreads = 1024;
 constexpr int kCfRowThreads = 256;  // a row launch's sequences per block fill this many
+constexpr int kCfPre = 4;           // kernel-spectrum elements per thread held in registers
 
 // Forward DFT of 2^lg_c sequences of length n = 2^lg_n held interleaved in
 // shared memory, A -> B -> A ...: Stockham passes of radix 4 (one radix-2
@@ -162,7 +163,20 @@ k_cf_cols(CfColArgs d, const C *__restrict__ in, const C *__restrict__ Kh, const
     const int o = blockIdx.x / d.n_groups;
     const int kx0 = (blockIdx.x - o * d.n_groups) * CB;
     const C *src = in + o * d.in_outer + kx0;
-    for (int q = threadIdx.x; q < (n << LG_CB); q += blockDim.x) {
+    const int tot = n << LG_CB;
+    // the kernel spectrum's first kCfPre elements of each thread, loaded
+    // before the forward DFT so that their latency overlaps it
+    const C *kc = Kh + o * d.k_outer + kx0;
+    constexpr int PRE = sizeof(C) == 8 ? kCfPre : kCfPre / 2;  // FP64: within the 1024-thread register budget
+    C kv[MODE == kCfFused ? PRE : 1];
+    if constexpr (MODE == kCfFused) {
+#pragma unroll
+        for (int u = 0; u < PRE; ++u) {
+            const int q = threadIdx.x + u * blockDim.x;
+            if (q < tot) kv[u] = kc[(q >> LG_CB) * d.k_stride + (q & (CB - 1))];
+        }
+    }
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
         const int c = q & (CB - 1), e = q >> LG_CB;
         C v = cxv(R(0), R(0));
         if (e < d.n_in) v = src[e * d.in_stride + c];
@@ -174,10 +188,16 @@ k_cf_cols(CfColArgs d, const C *__restrict__ in, const C *__restrict__ Kh, const
     if constexpr (MODE == kCfFused) {
         // conj(F K), so that a second forward DFT gives the conjugated inverse
         C *G = F == A ? B : A;
-        const C *kc = Kh + o * d.k_outer + kx0;
-        for (int q = threadIdx.x; q < (n << LG_CB); q += blockDim.x) {
-            const int c = q & (CB - 1), e = q >> LG_CB;
-            const C p = cmul(F[q], kc[e * d.k_stride + c]);
+#pragma unroll
+        for (int u = 0; u < PRE; ++u) {
+            const int q = threadIdx.x + u * blockDim.x;
+            if (q < tot) {
+                const C p = cmul(F[q], kv[u]);
+                F[q] = cxv(p.x, -p.y);
+            }
+        }
+        for (int q = threadIdx.x + PRE * blockDim.x; q < tot; q += blockDim.x) {
+            const C p = cmul(F[q], kc[(q >> LG_CB) * d.k_stride + (q & (CB - 1))]);
             F[q] = cxv(p.x, -p.y);
         }
         __syncthreads();

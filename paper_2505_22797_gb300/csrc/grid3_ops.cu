@@ -375,7 +375,7 @@ k_grid3_q(int nx, int ny, int nz, int ncx, int ncy, int ncz, const int *__restri
             acc.add(p[e], qe);
         }
     }
-    const double tot = block_sum<double, kQThreads3>(acc.value(), sh);
+    const double tot = acc.template block_total<kQThreads3>(sh);
     if (threadIdx.x == 0) pq_part[blockIdx.x] = tot;
     cs_finish_pq<kQThreads3>(pq_part, gridDim.x, sc, sh, &last);
 }

@@ -163,16 +163,50 @@ template <typename E> __device__ __forceinline__ E cs_beta(const CsScal *sc);
 template <> __device__ __forceinline__ double cs_beta<double>(const CsScal *sc) { return sc->beta; }
 template <> __device__ __forceinline__ df cs_beta<df>(const CsScal *sc) { return sc->beta_df; }
 // Per-thread accumulator of an inner product of element vectors.
+// Sum over a block of NT threads of their double-float accumulators, on the
+// FP32 pipe (a fixed butterfly per warp, then thread 0 over the warps in
+// order), converted to FP64 once: the total at thread 0 (0 elsewhere); sh is
+// reusable on return, as with block_sum.
+template <int NT>
+__device__ __forceinline__ double block_sum_f2(F2Sum v, double *sh /* >= NT/32 */)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        F2Sum t;
+        t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v.add(t);
+    }
+    F2Sum *w = reinterpret_cast<F2Sum *>(sh);
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        F2Sum s = w[0];
+#pragma unroll
+        for (int k = 1; k < NT / 32; ++k) s.add(w[k]);
+        t = s.value();
+    }
+    __syncthreads();
+    return t;
+}
+
 template <typename E> struct CsDot;
 template <> struct CsDot<double> {
     double s;
     __device__ __forceinline__ void add(double a, double b) { s += a * b; }
-    __device__ __forceinline__ double value() const { return s; }
+    template <int NT> __device__ __forceinline__ double block_total(double *sh) const
+    {
+        return block_sum<double, NT>(s, sh);
+    }
 };
 template <> struct CsDot<df> {
     F2Sum s;
     __device__ __forceinline__ void add(df a, df b) { df_dot_add(s, a, b); }
-    __device__ __forceinline__ double value() const { return s.value(); }
+    template <int NT> __device__ __forceinline__ double block_total(double *sh) const
+    {
+        return block_sum_f2<NT>(s, sh);
+    }
 };
 // An element as FP64 / from FP64 (right-hand sides and outputs).
 __device__ __forceinline__ double cs_to_double(double a) { return a; }

@@ -509,7 +509,7 @@ k_grid_q(int nx, int ny, int ncx, int ncy, const int *__restrict__ cunit_off, co
             acc.add(p[e], qe);
         }
     }
-    const double tot = block_sum<double, kQThreads>(acc.value(), sh);
+    const double tot = acc.template block_total<kQThreads>(sh);
     if (threadIdx.x == 0) pq_part[blockIdx.x] = tot;
     cs_finish_pq<kQThreads>(pq_part, gridDim.x, sc, sh, &last);
 }
@@ -542,7 +542,7 @@ k_cs_init(int64_t n, const E *__restrict__ b, E *__restrict__ r, E *__restrict__
             acc.add(be, be);
         }
     }
-    const double tot = block_sum<double, kCsThreads>(acc.value(), sh);
+    const double tot = acc.template block_total<kCsThreads>(sh);
     if (threadIdx.x == 0) rr_part[blockIdx.x] = tot;
     if (!cs_last_block(&sc->cnt[kCntInit], &last)) return;
     const double rr = cs_sum_parts<kCsThreads>(rr_part, gridDim.x, sh);
@@ -591,7 +591,7 @@ k_cs_step1(int64_t n, E *__restrict__ x, E *__restrict__ r, const E *__restrict_
             acc.add(re, re);
         }
     }
-    const double tot = block_sum<double, kCsThreads>(acc.value(), sh);
+    const double tot = acc.template block_total<kCsThreads>(sh);
     if (threadIdx.x == 0) rr_part[blockIdx.x] = tot;
     if (!cs_last_block(&sc->cnt[kCntRr], &last)) return;
     const double rr = cs_sum_parts<kCsThreads>(rr_part, gridDim.x, sh);
