@@ -226,6 +226,96 @@ k_interp_T_cells(const InterpRec<R> *__restrict__ rec, const R *__restrict__ vs,
     }
 }
 
+// The Core Stage's normal product by cell, M^T M p, without forming M p: the
+// samples of a unit all lie in its cell, so the unit loads the cell's four
+// corner nodes of the field p once, and per sample forms
+//   s_k = sum_m I[p_{2k+m}](r_t) v_m(t)
+// in registers (the arithmetic of k_interp) and adds w_corner v_m s_k to the
+// corner sums (that of k_interp_T_cells).  The unit sums are those of the two
+// kernels but for the rounding of s, which is not stored; a sample is read
+// once (record and velocity) instead of gathered, stored and read again.
+// IL: the field node-interleaved in R (NC components per node), else
+// component-major in AT; CH = k: only channel k (two components).
+template <typename R, typename AT, int CH, bool IL>
+__global__ void __launch_bounds__(kUnitThreads)
+k_interp_normal_cells(const InterpRec<R> *__restrict__ rec, const R *__restrict__ vs, const AT *__restrict__ A,
+                      int nx, int ny, int ncx, const int *__restrict__ offset, const int *__restrict__ cunit_off,
+                      const int *__restrict__ unit_cell, const int *__restrict__ n_units_dev, int n_iter,
+                      R *__restrict__ unit_part)
+{
+    constexpr int K = CH < 0 ? 2 : 1;
+    constexpr int NC = 2 * K;
+    constexpr int G = kUnitLanes;
+    constexpr int per_block = kUnitThreads / G;
+    const int sub = threadIdx.x % G;
+    const int n_units = *n_units_dev;
+    const int64_t N = (int64_t)nx * ny;
+    for (int base = blockIdx.x * per_block; base < n_iter; base += gridDim.x * per_block) {
+        const int w = base + (int)threadIdx.x / G;
+        R acc[4][NC];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) acc[k][m] = R(0);
+        if (w < n_units) {
+            const int c = unit_cell[w];
+            const int i0 = c % ncx, j0 = c / ncx;
+            const int i1 = nx > 1 ? i0 + 1 : i0, j1 = ny > 1 ? j0 + 1 : j0;
+            // corners: 0 = (i0, j0), 1 = (i1, j0), 2 = (i0, j1), 3 = (i1, j1)
+            const int64_t nodes[4] = {(int64_t)j0 * nx + i0, (int64_t)j0 * nx + i1, (int64_t)j1 * nx + i0,
+                                      (int64_t)j1 * nx + i1};
+            R f[4][NC];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if constexpr (IL) {
+                    load_node<R, NC>(reinterpret_cast<const R *>(A), nodes[k], f[k]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < NC; ++e) f[k][e] = R(A[(int64_t)e * N + nodes[k]]);
+                }
+            }
+            const int q0 = offset[c] + (w - cunit_off[c]) * kUnitLen;
+            const int q1 = min(offset[c + 1], q0 + kUnitLen);
+#pragma unroll 2
+            for (int q = q0 + sub; q < q1; q += G) {
+                const InterpRec<R> rc = rec[q];
+                const R wx1 = rc.wx1, wy1 = rc.wy1, wx0 = R(1) - wx1, wy0 = R(1) - wy1;
+                const R wt[4] = {wy0 * wx0, wy0 * wx1, wy1 * wx0, wy1 * wx1};
+                const R vx = vs[2 * q], vy = vs[2 * q + 1];
+                R pr[NC];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    R sk = R(0);
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        const int e = 2 * k + m;
+                        const R val = wy0 * (wx0 * f[0][e] + wx1 * f[1][e]) + wy1 * (wx0 * f[2][e] + wx1 * f[3][e]);
+                        sk += val * (m == 0 ? vx : vy);
+                    }
+                    pr[2 * k] = vx * sk;
+                    pr[2 * k + 1] = vy * sk;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) acc[k][m] += wt[k] * pr[m];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int m = 0; m < NC; ++m)
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) acc[k][m] += __shfl_xor_sync(0xffffffffu, acc[k][m], o);
+        if (sub == 0 && w < n_units) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int m = 0; m < NC; ++m) unit_part[((int64_t)w * 4 + k) * NC + m] = acc[k][m];
+        }
+    }
+}
+
 // Ahat_m(node) = scale * the sum, over the node's adjacent cells (row-major
 // cell order) and their units in order, of the unit sums of the corner the
 // node is in that cell (FP32 unit sums as error-free double-float pairs).
@@ -420,6 +510,29 @@ static int launch_interp_T(const GridH &g, int64_t T, const R *s_sorted, const B
     else
         k_interp_T_cell_combine<R, OUT, 2><<<grid_blocks(N), 256, 0, st>>>(g.nx, g.ny, b.ncx, b.ncy, b.cunit_off,
                                                                           part, A, scale);
+    MPI_CHECK_LAUNCH();
+    return MPI_OK;
+}
+
+// Unit sums of M^T M p (k_interp_normal_cells) for the Core Stage step.
+template <typename R, typename AT, bool IL>
+static int launch_normal_units(const GridH &g, const Bins &b, const AT *A, int ch, cudaStream_t st)
+{
+    const int nc = b.ncx * b.ncy;
+    constexpr int per_block = kUnitThreads / kUnitLanes;
+    const int units = b.n_units >= 0 ? b.n_units : b.n_units_max;
+    const int n_iter = (units + per_block - 1) / per_block * per_block;
+    const unsigned blocks = (unsigned)std::max(1, std::min(n_iter / per_block, 65535));
+    const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(b.rec);
+    const R *vs = static_cast<const R *>(b.vs);
+    R *part = static_cast<R *>(b.unit_part);
+    const int *n_units = b.cunit_off + nc;
+    if (ch < 0)
+        k_interp_normal_cells<R, AT, -1, IL><<<blocks, kUnitThreads, 0, st>>>(
+            rec, vs, A, g.nx, g.ny, b.ncx, b.offset, b.cunit_off, b.unit_cell, n_units, n_iter, part);
+    else
+        k_interp_normal_cells<R, AT, 0, IL><<<blocks, kUnitThreads, 0, st>>>(
+            rec, vs, A, g.nx, g.ny, b.ncx, b.offset, b.cunit_off, b.unit_cell, n_units, n_iter, part);
     MPI_CHECK_LAUNCH();
     return MPI_OK;
 }
@@ -751,12 +864,11 @@ struct GridOp2 final : CoreStageOp<typename CsElem<R>::type> {
     int64_t T;
     int ch, nc;
     const Bins &bins;
-    R *s_tmp;
     R *p_r;  // FP32 path: the FP32 copy of p, node-interleaved (nc N values); FP64: unused
     double invT;
     bool scaled;
-    GridOp2(const GridH &g_, int64_t T_, int ch_, const Bins &b_, R *s_tmp_, R *p_r_, bool scaled_)
-        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 4 : 2), bins(b_), s_tmp(s_tmp_), p_r(p_r_),
+    GridOp2(const GridH &g_, int64_t T_, int ch_, const Bins &b_, R *p_r_, bool scaled_)
+        : g(g_), T(T_), ch(ch_), nc(ch_ < 0 ? 4 : 2), bins(b_), p_r(p_r_),
           invT(T_ > 0 ? 1.0 / double(T_) : 0.0), scaled(scaled_) {}
     P32 p32() const override
     {
@@ -778,12 +890,9 @@ struct GridOp2 final : CoreStageOp<typename CsElem<R>::type> {
         k_lap<E, true><<<lb, 256, 0, fk.side>>>(g.nx, g.ny, nc, scaled, cx, cy, l1, l2, cs_host_scalar(gamma, tag));
         MPI_CHECK_LAUNCH();
         MPI_TRY_CUDA(cudaEventRecord(fk.join, fk.side));
-        const InterpRec<R> *rec = static_cast<const InterpRec<R> *>(bins.rec);
-        const R *vs = static_cast<const R *>(bins.vs);
-        if constexpr (sizeof(R) == 4) MPI_TRY((launch_interp<R, R>(g, T, nullptr, vs, p_r, s_tmp, st, ch, rec, true)));
-        else MPI_TRY((launch_interp<R, double>(g, T, nullptr, vs, reinterpret_cast<const double *>(p), s_tmp, st,
-                                               ch, rec)));
-        MPI_TRY(launch_interp_T_units<R>(T, s_tmp, bins, st, ch));
+        // main branch: the unit sums of M^T M p, one pass over the samples
+        if constexpr (sizeof(R) == 4) MPI_TRY((launch_normal_units<R, R, true>(g, bins, p_r, ch, st)));
+        else MPI_TRY((launch_normal_units<R, double, false>(g, bins, reinterpret_cast<const double *>(p), ch, st)));
         MPI_TRY_CUDA(cudaStreamWaitEvent(st, fk.join, 0));
         const unsigned blocks = (unsigned)pq_blocks(0);
         const R *part = static_cast<const R *>(bins.unit_part);
@@ -812,7 +921,6 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
 
     Scratch scr(st);
     const size_t o_bins = scr.reserve(bins_bytes<R>(T, g.nx, g.ny));
-    const size_t o_s = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     const size_t o_sd = scr.reserve(sizeof(R) * rows * std::max<int64_t>(T, 1));
     using E = typename CsElem<R>::type;
     const size_t o_b = scr.reserve(sizeof(E) * n4), o_x = scr.reserve(sizeof(E) * n4);
@@ -838,7 +946,7 @@ static int grid_impl(const GridH &g, const mpi_traj *tr, const void *s_in, const
         }
         bins.n_units = n_units;
     }
-    GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_s), scr.at<R>(o_pr), o.lap_scaled != 0);
+    GridOp2<R> op(g, T, ch, bins, scr.at<R>(o_pr), o.lap_scaled != 0);
     // b = (1/T) M^T s
     MPI_TRY((launch_interp_T<R, E>(g, T, s_data, bins, b, op.invT, st, ch)));
     MPI_TRY(core_stage_cg<E>(op, n4, b, o, x, n_iter_out, st));
