@@ -148,7 +148,7 @@ def test_core_stage_argument_validation_without_gpu(lib):
 
 def test_other_entry_points_validate_without_gpu():
     """3-D operators, the convolution entries, the transfer correction, the
-    PnP options and the batch plan reject bad arguments on the host with
+    PnP options, the binning step and the batch plan reject bad arguments on the host with
     MPI_ERR_INVALID (or MPI_ERR_UNSUPPORTED) and a message, before any CUDA
     call."""
     from paper_2505_22797_gb300 import api, build
@@ -206,6 +206,11 @@ def test_other_entry_points_validate_without_gpu():
          b"NULL"),
         ("pnp opts NULL", lambda: lib.mpi_pnp_solve(ref(m2), ref(g2), ref(tr0), 0, buf, None, no_cb, None,
                                                     buf, None, None), -1, b""),
+        ("cell order n_cells 0", lambda: lib.mpi_cell_order(8, buf, 0, buf, None, None), -1, b"cell ordering"),
+        ("cell order T < 0", lambda: lib.mpi_cell_order(-1, buf, 4, buf, None, None), -1, b"cell ordering"),
+        ("cell order T >= 2^31", lambda: lib.mpi_cell_order(1 << 31, buf, 4, buf, None, None), -1,
+         b"cell ordering"),
+        ("cell order list NULL", lambda: lib.mpi_cell_order(8, buf, 4, None, None, None), -1, b"cell ordering"),
         ("batch 0 frames", lambda: lib.mpi_batch_plan_create(0, ref(m2), ref(g2), None, None, ref(pnp), 0,
                                                              ctypes.byref(ctypes.c_void_p())), -1, b""),
         ("batch 65 frames", lambda: lib.mpi_batch_plan_create(65, ref(m2), ref(g2), None, None, ref(pnp), 0,
