@@ -64,6 +64,28 @@ def test_cell_order_stable(T, n_cells, run):
     assert none is None and torch.equal(lst2, lst)
 
 
+def test_core_stage_full_size_fp32(orc):
+    """The 512 x 512 / 2^20-sample geometry (cells of up to ~1900 samples,
+    each spread over many work units of the one-pass normal product): 20 CG
+    steps of the FP32 solve against the oracle.  The data are the oracle's
+    measurement of a smooth 4-component field with 1 % noise."""
+    dt = torch.float32
+    cfg = syn.config("c5")
+    g = cfg["grid"]
+    r, v = rounded(cfg["r"], dt), rounded(cfg["v"], dt)
+    ys, xs = np.meshgrid(*[np.linspace(-1, 1, n) for n in (g["ny"], g["nx"])], indexing="ij")
+    rng = np.random.default_rng(21)
+    A_true = np.stack([np.exp(-((xs - a) ** 2 + (ys - b) ** 2) / 0.2) for a, b in rng.uniform(-0.5, 0.5, (4, 2))])
+    s = orc.interp(g, r, v, A_true)
+    s = rounded(s + 0.01 * np.abs(s).max() * rng.normal(size=s.shape), dt)
+    want, want_u, _ = orc.core_stage(g, r, v, s, 1e-7, max_iter=20)
+    A, u, n = api.mpi_grid(g, dev(r, dt), dev(v, dt), dev(s, dt), gamma=1e-7, max_iter=20, rel_tol=0.0,
+                           return_iters=True)
+    assert n == 20
+    assert rel_l2(host(A), want) <= tol(dt)
+    assert rel_l2(host(u), want_u) <= tol(dt)
+
+
 def test_cell_order_rejects_bad_arguments():
     keys = torch.zeros(10, dtype=torch.int32, device="cuda")
     with pytest.raises(api.MPIError):
