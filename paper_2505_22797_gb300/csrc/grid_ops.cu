@@ -316,6 +316,32 @@ k_interp_normal_cells(const InterpRec<R> *__restrict__ rec, const R *__restrict_
     }
 }
 
+// sum[m] += the unit sums of `corner` of units w0 .. w1 - 1, in unit order.
+// Four units' values are loaded before they are added: the additions depend
+// on one another, the loads do not, and a node beside a dense cell adds tens
+// of units (one L2 round trip each when every load waits for the previous
+// addition).
+template <typename R, int NC>
+__device__ __forceinline__ void add_unit_sums(const R *__restrict__ unit_part, int w0, int w1, int corner,
+                                              SumAcc<R> (&sum)[NC])
+{
+    int w = w0;
+    for (; w + 4 <= w1; w += 4) {
+        R v[4][NC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) v[u][m] = unit_part[((int64_t)(w + u) * 4 + corner) * NC + m];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) sum[m].add(v[u][m]);
+    }
+    for (; w < w1; ++w)
+#pragma unroll
+        for (int m = 0; m < NC; ++m) sum[m].add(unit_part[((int64_t)w * 4 + corner) * NC + m]);
+}
+
 // Ahat_m(node) = scale * the sum, over the node's adjacent cells (row-major
 // cell order) and their units in order, of the unit sums of the corner the
 // node is in that cell (FP32 unit sums as error-free double-float pairs).
@@ -333,9 +359,7 @@ __global__ void k_interp_T_cell_combine(int nx, int ny, int ncx, int ncy, const 
                 if (ci < 0 || ci >= ncx) continue;
                 const int c = cj * ncx + ci;
                 const int corner = (i - ci) + 2 * (j - cj);
-                for (int w = cunit_off[c]; w < cunit_off[c + 1]; ++w)
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) acc[m].add(unit_part[((int64_t)w * 4 + corner) * NC + m]);
+                add_unit_sums<R, NC>(unit_part, cunit_off[c], cunit_off[c + 1], corner, acc);
             }
         }
 #pragma unroll
@@ -609,9 +633,7 @@ k_grid_q(int nx, int ny, int ncx, int ncy, const int *__restrict__ cunit_off, co
                 if (ci < 0 || ci >= ncx) continue;
                 const int c = cj * ncx + ci;
                 const int corner = (i - ci) + 2 * (j - cj);
-                for (int w = cunit_off[c]; w < cunit_off[c + 1]; ++w)
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) sum[m].add(unit_part[((int64_t)w * 4 + corner) * NC + m]);
+                add_unit_sums<R, NC>(unit_part, cunit_off[c], cunit_off[c + 1], corner, sum);
             }
         }
 #pragma unroll
